@@ -104,7 +104,7 @@ def lib():
         _lib.orc_sort_perm.argtypes = [i64, P, P, P]
         _lib.orc_density.restype = i32
         _lib.orc_density.argtypes = [ctypes.POINTER(_Params), i64, P, P, P, P, P, i64, P,
-                                     P, P, P, P, P, P]
+                                     P, P, P, P, P, P, P]
         _lib.orc_neighbors.argtypes = [ctypes.POINTER(_Params), i32, i64, P, P, P, P, i64, P,
                                        P, P, P]
         _lib.orc_eos.argtypes = [i64, d, P, P, P, P]
@@ -190,6 +190,7 @@ class DensityResult:
     nnb: np.ndarray
     sweeps: np.ndarray
     flags: np.ndarray
+    pairs: np.ndarray = None     # neighbour pairs summed over the evaluations
     status: int = 0
 
 
@@ -206,10 +207,11 @@ def density(params: Params, x, y, z, m, h_seed, targets=None) -> DensityResult:
     nnb = np.zeros(n, dtype=np.int32)
     sw = np.zeros(n, dtype=np.int32)
     fl = np.zeros(n, dtype=np.int32)
+    pr = np.zeros(n, dtype=np.int64)
     pc = params.c()
     st = lib().orc_density(ctypes.byref(pc), n, _p(x), _p(y), _p(z), _p(m), _p(h_seed), nt, _p(tg),
-                           _p(h), _p(rho), _p(dr), _p(nnb), _p(sw), _p(fl))
-    return DensityResult(h, rho, dr, nnb, sw, fl, int(st))
+                           _p(h), _p(rho), _p(dr), _p(nnb), _p(sw), _p(fl), _p(pr))
+    return DensityResult(h, rho, dr, nnb, sw, fl, pr, int(st))
 
 
 def neighbors(params: Params, kind: int, x, y, z, h, targets=None):
@@ -369,8 +371,8 @@ def cfl_dt(s: State, cfl: float = 0.3) -> float:
 
 
 # --------------------------------------------------------------------------- h-predictor MLP
-# Not in the paper: a 5 -> 64 -> 64 -> 1 network with SiLU activations that
-# predicts s = log(h_next / h_prev).  Parameter layout (flat): W1[64,5], b1[64],
+# Not in the paper: a 5 -> 64 -> 64 -> 1 network with SiLU activations whose
+# output y gives the predicted s = log(h_next / h_prev) = f3 * y.  Parameter layout (flat): W1[64,5], b1[64],
 # W2[64,64], b2[64], W3[1,64], b3[1]; row-major, output index first.
 HNET_SHAPES = [(64, 5), (64,), (64, 64), (64,), (1, 64), (1,)]
 HNET_NPARAM = sum(int(np.prod(s)) for s in HNET_SHAPES)
@@ -402,15 +404,26 @@ def hnet_forward(theta, feats):
     return y, (X, z1, a1, z2, a2)
 
 
+def hnet_predict(theta, feats):
+    """Predicted log(h_next/h) of the h-predictor: s = f3 * y(f), the network
+    output scaled by the feature f3 = div v * dt, so that a particle at rest
+    keeps its h exactly and the network learns the gain of the continuity
+    estimate (d ln h = div v dt / 3 for a uniform compression)."""
+    y, _ = hnet_forward(theta, feats)
+    return np.asarray(feats, dtype=np.float64)[:, 3] * y
+
+
 def hnet_loss_grad(theta, feats, target):
-    """Mean squared error L = mean((y - t)^2) and its gradient by backprop."""
+    """Mean squared error L = mean((s - t)^2) of the prediction s = f3 y and
+    its gradient with respect to the parameters by backprop."""
     W1, b1, W2, b2, W3, b3 = hnet_unpack(theta)
     y, (X, z1, a1, z2, a2) = hnet_forward(theta, feats)
     t = np.asarray(target, dtype=np.float64)
     B = X.shape[0]
-    r = y - t
+    gain = X[:, 3]
+    r = gain * y - t
     loss = float(np.mean(r * r))
-    d3 = (2.0 / B) * r[:, None]                 # dL/dy
+    d3 = ((2.0 / B) * r * gain)[:, None]        # dL/dy
     gW3 = d3.T @ a2
     gb3 = d3.sum(axis=0)
     s2 = _sigmoid(z2)
@@ -441,3 +454,18 @@ def bf16_round(a):
     lsb = (u >> np.uint64(16)) & np.uint64(1)
     u = (u + np.uint64(0x7FFF) + lsb) & np.uint64(0xFFFF0000)
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def hnet_features(h, hprev, nnb, rho, m, divv, dt, eta, rho_ref=1.0):
+    """Network inputs per particle: log(h/hbar) with hbar = eta (m/rho_ref)^(1/3),
+    log(max(nnb, 1/2)/nbar) with nbar = 32 pi eta^3/3 (the neighbour count of
+    a uniform medium inside 2h), log(rho h^3/(m eta^3)) (the fixed-point
+    ratio of Eq. 9), div v * dt, and log(h/hprev) (0 when hprev <= 0)."""
+    h, hprev, rho, m, divv = map(lambda a: np.asarray(a, dtype=np.float64), (h, hprev, rho, m, divv))
+    nnb = np.asarray(nnb, dtype=np.float64)
+    eta3 = eta ** 3
+    hbar = eta * np.cbrt(m / rho_ref)
+    nbar = 32.0 * math.pi * eta3 / 3.0
+    f4 = np.where(hprev > 0, np.log(np.where(hprev > 0, h / np.where(hprev > 0, hprev, 1.0), 1.0)), 0.0)
+    return np.stack([np.log(h / hbar), np.log(np.maximum(nnb, 0.5) / nbar), np.log(rho * h ** 3 / (m * eta3)),
+                     divv * dt, f4], axis=1)

@@ -235,8 +235,9 @@ static void density_sum(const orc_params *p, int64_t n, const double *x, const d
  *   f(h)  = m eta^3 / h^3 - rho(h),   f'(h) = -3 m eta^3 / h^4 - drho/dh,
  * one density evaluation per sweep, with a bracket [lo, hi] of evaluated
  * smoothing lengths kept from the sign of f (f > 0 means the root lies above
- * h; the bracket starts as [0, inf)).  A Newton step outside
- * (max(lo, h/2), min(hi, 2h)) or with f' >= 0 is replaced by the midpoint
+ * h; the bracket starts as [0, inf)).  A Newton step outside the closed
+ * interval [max(lo, h/2), min(hi, 2h)] or with f' >= 0 is replaced by the
+ * midpoint
  * between h and the nearer admissible end in the direction the sign of f
  * points.  The result is clamped to [h_min, h_max].  When |h_new - h| <
  * h_tol * h the step is applied and one more evaluation at the final h gives
@@ -247,7 +248,7 @@ int orc_density(const orc_params *p, int64_t n, const double *x, const double *y
                 const double *z, const double *m, const double *h_seed,
                 int64_t nt, const int64_t *targets,
                 double *h_out, double *rho_out, double *drho_out, int32_t *nnb_out,
-                int32_t *sweeps_out, int32_t *flags_out)
+                int32_t *sweeps_out, int32_t *flags_out, int64_t *pairs_out)
 {
     const double eta3 = p->eta * p->eta * p->eta;
     int worst = 0;
@@ -258,9 +259,11 @@ int orc_density(const orc_params *p, int64_t n, const double *x, const double *y
         double lo = 0.0, hi = INFINITY;  /* evaluated bracket ends */
         double rho = 0.0, drho = 0.0;
         int32_t cnt = 0, sweeps = 0, flags = 0, final_eval = p->fixed_h ? 1 : 0;
+        int64_t pairs = 0;   /* neighbour pairs over all evaluations */
         for (;;) {
             density_sum(p, n, x, y, z, m, a, h, &rho, &drho, &cnt);
             ++sweeps;
+            pairs += cnt;
             if (final_eval) { flags |= ORC_DONE; break; }
             double ma = m[a];
             double f = ma * eta3 / (h * h * h) - rho;
@@ -275,7 +278,7 @@ int orc_density(const orc_params *p, int64_t n, const double *x, const double *y
             int newton_ok = 0;
             if (fp < 0.0) {
                 hn = h - f / fp;
-                newton_ok = (hn > a_lo) && (hn < a_hi);
+                newton_ok = (hn >= a_lo) && (hn <= a_hi);
             }
             if (!newton_ok) hn = f > 0.0 ? 0.5 * (h + a_hi) : 0.5 * (h + a_lo);
             if (hn < p->h_min) hn = p->h_min;
@@ -292,6 +295,7 @@ int orc_density(const orc_params *p, int64_t n, const double *x, const double *y
         if (nnb_out) nnb_out[a] = cnt;
         if (sweeps_out) sweeps_out[a] = sweeps;
         if (flags_out) flags_out[a] = flags;
+        if (pairs_out) pairs_out[a] = pairs;
         worst |= flags & (ORC_NOT_CONVERGED | ORC_H_BOUNDS);
     }
     return worst;

@@ -50,6 +50,18 @@ def test_forward_hand_set_weights(orc):
     assert y[1] == pytest.approx(silu(silu(-2.0)) + 0.25, rel=1e-14)
 
 
+def test_prediction_is_gain_times_output(orc):
+    th = _theta(orc, 3)
+    X = np.random.default_rng(9).normal(size=(7, 5))
+    X[2, 3] = 0.0                                   # at rest: no change of h
+    y, _ = orc.hnet_forward(th, X)
+    s = orc.hnet_predict(th, X)
+    assert s[2] == 0.0
+    assert np.allclose(s, X[:, 3] * y, rtol=0, atol=0)
+    loss, _ = orc.hnet_loss_grad(th, X, np.zeros(7))
+    assert loss == pytest.approx(np.mean(s * s), rel=1e-15)
+
+
 def test_adam_first_step_closed_form(orc):
     rng = np.random.default_rng(4)
     th = rng.normal(size=50)
