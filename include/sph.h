@@ -1,0 +1,263 @@
+/*
+ * sph.h - C ABI of the GB300 (sm_103a) SPH hydro right-hand side.
+ *
+ * The library computes, on one GPU, the smoothed-particle-hydrodynamics
+ * right-hand side described in Sec. 2.1-2.2.1 of the FleCSPH paper
+ * (arXiv 2007.03097):
+ *   - Morton (Z-order) keys with a leading 1 bit and a (key, id) sort
+ *     (Sec. 2.1, Tree topology; Fig. 1),
+ *   - an octree of leaf cells over the sorted particles for neighbour search
+ *     within the kernel support 2h (Sec. 2.1, group tree traversal),
+ *   - the density sum rho_a = sum_b m_b W(r_ab, h_a) (Eq. 7) solved jointly
+ *     with h_a = eta (m_a / rho_a)^(1/3) (Eq. 9, C = 1, D = 3),
+ *   - the momentum and internal-energy equations with artificial viscosity
+ *     (Eqs. 5-6, g = 0),
+ *   - a kick-drift-kick leapfrog step around them.
+ * All pointers named "device" must be device memory of the current CUDA
+ * device; "host" pointers are ordinary host memory.  Every call is ordered on
+ * the CUDA stream passed as `stream` (a cudaStream_t; NULL = legacy default
+ * stream).  Calls that fill a host stats struct synchronise that stream.
+ *
+ * Errors: every int-returning call returns an sph_status; no call aborts or
+ * throws.  sph_last_error() gives a message for the last failing call on a
+ * context.  On error the contents of output arrays are unspecified, but no
+ * call writes outside the arrays it was given.
+ *
+ * Ownership: the caller owns every particle array.  The context owns all
+ * scratch memory, allocated once by sph_create for at most n_max particles;
+ * no later call allocates device memory.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sph_ctx sph_ctx;
+
+typedef enum {
+    SPH_OK = 0,
+    SPH_ERR_ARG = -1,            /* invalid argument or parameter              */
+    SPH_ERR_CUDA = -2,           /* a CUDA runtime call failed                 */
+    SPH_ERR_CAPACITY = -3,       /* a context capacity would be exceeded       */
+    SPH_ERR_NOT_CONVERGED = -4,  /* h-rho iteration hit max_sweeps             */
+    SPH_ERR_H_BOUNDS = -5,       /* a converged h sits on h_min or h_max       */
+    SPH_ERR_NONFINITE = -6,      /* NaN or Inf in an input array               */
+    SPH_ERR_STATE = -7           /* call order violated (e.g. no tree yet)     */
+} sph_status;
+
+/* Smoothing kernels, 3D, support radius 2h, q = r/h (the paper offers several
+ * kernels without printing them, Sec. 2.1; these are the standard forms). */
+typedef enum {
+    SPH_KERNEL_M4 = 0,   /* cubic spline, Monaghan 1992                         */
+    SPH_KERNEL_WC2 = 1,  /* Wendland C2, Dehnen & Aly 2012                      */
+    SPH_KERNEL_WC4 = 2   /* Wendland C4                                          */
+} sph_kernel;
+
+/* Arithmetic of the pair sums.
+ * SPH_FP64:  every particle field and every pair term in FP64.
+ * SPH_MIXED: positions x, y, z stay FP64 (and so do the leapfrog position
+ *            update and the conserved totals); every other field is FP32 and
+ *            the pair terms are evaluated in FP32 on relative coordinates
+ *            formed from a two-float split of the FP64 positions.           */
+typedef enum { SPH_FP64 = 0, SPH_MIXED = 1 } sph_precision;
+
+typedef struct {
+    int32_t kernel;      /* sph_kernel                                          */
+    int32_t precision;   /* sph_precision                                       */
+    int32_t periodic;    /* 1: periodic box [box_lo, box_hi), minimum image     */
+    int32_t fixed_h;     /* 1: h is an input; one density evaluation            */
+    double box_lo[3];    /* periodic box; must be a cube when periodic          */
+    double box_hi[3];
+    double gamma;        /* ideal gas: P = (gamma-1) rho u, c = sqrt(gamma (gamma-1) u) */
+    double eta;          /* h = eta (m/rho)^(1/3)  (Eq. 9 with C = 1, D = 3)    */
+    double alpha, beta;  /* Monaghan viscosity coefficients                     */
+    double eps_visc;     /* mu_ab = h_ab v_ab.r_ab / (r_ab^2 + eps_visc h_ab^2) */
+    double cfl;          /* dt = cfl * min_a h_a / vsig_a                       */
+    double h_tol;        /* converged when |h_new - h| < h_tol * h              */
+    int32_t max_sweeps;  /* cap on density evaluations per particle (>= 1)      */
+    int32_t leaf_size;   /* max particles per octree leaf, 1..32                */
+    double h_min, h_max; /* clamp of the h iteration                            */
+    double skin;         /* density lists cover 2h (1 + skin); >= 0             */
+    double rho_ref;      /* density scale of the h-predictor feature log(h/hbar) */
+    int64_t nb_capacity; /* neighbour-list entries to reserve; 0 = 256 n_max    */
+    double hnet_lr;      /* Adam learning rate of online h-predictor training   */
+    int32_t hnet_batch;  /* samples per online training step (strided subset)   */
+    int32_t hnet_iters;  /* Adam steps per sph_step when training online        */
+} sph_params;
+
+/* Particle arrays, structure of arrays, length n, caller-owned DEVICE memory.
+ * x, y, z are always double.  Every pointer typed void* points to double in
+ * SPH_FP64 and to float in SPH_MIXED.  Arrays must be 16-byte aligned.
+ * State (in/out):   x y z vx vy vz m h u hprev id
+ * Derived (out):    rho omega(=drho/dh) P c ax ay az dudt divv vsig nnb
+ * A NULL derived array is allowed where stated; NULL state arrays are not.
+ * id is any set of unique 32-bit labels; sph_build_tree permutes it with the
+ * particles so the caller can map results back to its own order.          */
+typedef struct {
+    int64_t n;
+    double *x, *y, *z;
+    void *vx, *vy, *vz;
+    void *m, *h, *u;
+    void *hprev;                     /* h of the previous step (h-predictor)     */
+    void *rho, *omega, *P, *c;
+    void *ax, *ay, *az, *dudt, *divv, *vsig;
+    int32_t *nnb;                    /* neighbours b != a with r_ab < 2 h_a      */
+    uint32_t *id;
+} sph_particles;
+
+typedef struct {
+    int32_t sweeps;          /* density evaluations (kernel launches)               */
+    int32_t list_builds;     /* neighbour-list constructions                        */
+    int64_t n_unconverged;   /* particles that hit max_sweeps                       */
+    int64_t n_hbounds;       /* converged particles sitting on h_min / h_max        */
+    int64_t interactions;    /* pairs b != a with r_ab < 2 h_a, summed over sweeps  */
+    int64_t list_entries;    /* list slots (incl. padding) of the last build        */
+    int64_t evaluations;     /* particle density evaluations, summed over sweeps    */
+    int64_t launches;        /* kernels launched by the call                        */
+    double ms;               /* device time of the call (CUDA events)               */
+    double kernel_ms;        /* device time of the density-sum kernels alone        */
+} sph_density_stats;
+
+typedef struct {
+    int64_t interactions;    /* pairs b != a with r_ab < h_a + h_b                  */
+    int64_t list_entries;
+    int64_t launches;        /* kernels launched by the call                        */
+    double ms;
+    double kernel_ms;        /* device time of the pair-force kernel alone          */
+} sph_force_stats;
+
+typedef struct {
+    double dt;               /* step used                                           */
+    double dt_next;          /* cfl * min h / vsig after the step                   */
+    double momentum[3];      /* sum m v (end of step)                               */
+    double force[3];         /* sum m a                                             */
+    double energy;           /* sum m (v^2/2 + u) (end of step)                     */
+    double power;            /* sum m (v_pred . a + du/dt), 0 up to roundoff        */
+    int32_t hnet_used;       /* 1 if the h-predictor seeded the iteration           */
+    int32_t hnet_fallback;   /* particles reseeded from h after a bad prediction    */
+    float hnet_loss;         /* loss of the last online training step (or 0)        */
+    int32_t pad;
+    int64_t launches;        /* kernels launched by the step                        */
+    sph_density_stats density;
+    sph_force_stats forces;
+    double ms_tree, ms_hnet, ms_total;
+} sph_step_stats;
+
+/* ---- context --------------------------------------------------------------- */
+
+/* Validate *params and allocate every scratch buffer for up to n_max
+ * particles on the current device.  On success *out owns them. */
+int sph_create(const sph_params *params, int64_t n_max, sph_ctx **out);
+void sph_destroy(sph_ctx *ctx);
+/* Replace the parameters (same validation; precision and capacity fixed). */
+int sph_set_params(sph_ctx *ctx, const sph_params *params);
+const char *sph_last_error(const sph_ctx *ctx);
+/* Library build string, e.g. "sph sm_103a". */
+const char *sph_version(void);
+
+/* ---- hot path ---------------------------------------------------------------- */
+
+/* Sec. 2.1 (Tree topology): Morton keys of the FP64 positions in the cubic
+ * key domain (the periodic box, or the bounding cube of an open set), sort of
+ * (key, id), in-place permutation of every particle array into key order,
+ * octree leaves of at most leaf_size particles and the search hierarchy.
+ * Returns SPH_ERR_NONFINITE for NaN/Inf positions or h. */
+int sph_build_tree(sph_ctx *ctx, sph_particles *p, void *stream);
+
+/* Eqs. 7 and 9: Newton iteration on h_a until |dh| < h_tol h, then rho,
+ * omega = drho/dh and nnb at the final h; P and c from u.  Seeds: h_seed
+ * (device, FP64 or FP32 per precision) if not NULL, else the current h.
+ * With fixed_h, one evaluation at the given h.  Needs sph_build_tree first. */
+int sph_density(sph_ctx *ctx, sph_particles *p, const void *h_seed,
+                sph_density_stats *stats, void *stream);
+
+/* Eqs. 5-6 with Monaghan viscosity: a, du/dt, div v (Eq. 2's div v estimate
+ * with W(r, h_a)), vsig.  Uses rho, P, c from sph_density. */
+int sph_forces(sph_ctx *ctx, sph_particles *p, sph_force_stats *stats, void *stream);
+
+/* One kick-drift-kick step of length dt (dt <= 0: the stored CFL dt):
+ * half kick with the stored a, du/dt; FP64 drift and periodic wrap;
+ * sph_build_tree; sph_density; forces at v + a dt/2, u + du dt/2; closing
+ * half kick; FP64 totals and next CFL dt.  use_hnet is a bit set:
+ *   SPH_HNET_SEED  seed the h iteration from the h-predictor (particles whose
+ *                  prediction is non-finite or changes h by more than a
+ *                  factor 2 keep the current h; if the seeded iteration fails
+ *                  to converge it is rerun from the current h),
+ *   SPH_HNET_TRAIN after convergence, take hnet_iters Adam steps on the
+ *                  step's features and targets log(h_new/h_old) (a strided
+ *                  subset of hnet_batch particles).
+ * The particle set must already carry a, du/dt from an earlier force pass. */
+#define SPH_HNET_SEED 1
+#define SPH_HNET_TRAIN 2
+int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet,
+             sph_step_stats *stats, void *stream);
+
+/* FP64 totals of the current arrays: out[0..2] = sum m v, out[3..5] = sum m a,
+ * out[6] = sum m (v^2/2 + u), out[7] = sum m (v . a + du/dt).  Host output. */
+int sph_totals(sph_ctx *ctx, const sph_particles *p, double out[8], void *stream);
+
+/* ---- stages exposed for verification ------------------------------------------ */
+
+/* Morton keys of p's current positions into keys (device, n), and the key
+ * domain (lo_x, lo_y, lo_z, L) into dom (host, 4 doubles). */
+int sph_morton_keys(sph_ctx *ctx, const sph_particles *p, uint64_t *keys,
+                    double dom[4], void *stream);
+
+/* Permutation perm (device, n) with (keys[perm[i]], ids[perm[i]]) ascending. */
+int sph_sort_keys(sph_ctx *ctx, int64_t n, const uint64_t *keys, const uint32_t *ids,
+                  uint32_t *perm, void *stream);
+
+/* After sph_build_tree: number of leaves and of target groups (host out). */
+int sph_tree_info(sph_ctx *ctx, int64_t *n_leaves, int64_t *n_groups);
+
+/* After sph_build_tree: leaf_begin (device, n_leaves + 1 entries, the last is
+ * n) and level (device, n_leaves; octree level of each leaf cell). */
+int sph_export_leaves(sph_ctx *ctx, int32_t *leaf_begin, int32_t *level, void *stream);
+
+/* Exact neighbour sets of the current state, kind 0: b != a with
+ * r_ab^2 < 4 h_a^2; kind 1: b != a with r_ab^2 < (h_a + h_b)^2 or
+ * r_ab^2 < 4 h_a^2, with r_ab^2 = (dx dx + dy dy) + dz dz in the arithmetic of
+ * the precision mode (no fused multiply-add in FP64).  counts (device, n)
+ * always; if offsets (device, n + 1) is not NULL the indices (current order)
+ * are written to idx (device) at offsets[a] (unsorted within a target). */
+int sph_neighbors(sph_ctx *ctx, const sph_particles *p, int kind, int64_t *counts,
+                  const int64_t *offsets, uint32_t *idx, void *stream);
+
+/* ---- h-predictor network (not in the paper) --------------------------------------
+ * y = W3 silu(W2 silu(W1 f + b1) + b2) + b3, 5 -> 64 -> 64 -> 1.  The
+ * context keeps FP32 master weights and the BF16 copy the kernels read.
+ * Flat layout (SPH_HNET_NPARAM floats): W1[64][5], b1[64], W2[64][64], b2[64],
+ * W3[1][64], b3[1], row-major with the output index first.
+ * Features f (FP32, nb x 5, row-major): log(h/hbar) with
+ * hbar = eta (m/rho_ref)^(1/3), log(nnb/nbar) with nbar = 32 pi eta^3 / 3,
+ * log(rho h^3 / (m eta^3)), div v * dt, log(h/hprev); target
+ * log(h_next / h). */
+#define SPH_HNET_NPARAM 4609
+
+int sph_hnet_set_weights(sph_ctx *ctx, const float *params_host, int64_t count);
+int sph_hnet_get_weights(sph_ctx *ctx, float *params_host, int64_t count);
+/* features of the current particles (device, n x 5) for step length dt */
+int sph_hnet_features(sph_ctx *ctx, const sph_particles *p, double dt, float *feats,
+                      void *stream);
+/* predicted log(h_next/h) s = f3 * y (device, nb) from features (device,
+ * nb x 5) with the BF16 weights; f3 = div v * dt, so s = 0 at rest */
+int sph_hnet_infer(sph_ctx *ctx, const float *feats, int64_t nb, float *y, void *stream);
+/* loss = mean (f3 y - t)^2 and its gradient (host, SPH_HNET_NPARAM) at the
+ * BF16 weights, FP32 accumulation; no update. */
+int sph_hnet_grad(sph_ctx *ctx, const float *feats, const float *target, int64_t nb,
+                  float *grad_host, float *loss_host, void *stream);
+/* one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the FP32 master weights,
+ * then refresh the BF16 copy; loss before the step to *loss_host (may be NULL) */
+int sph_hnet_train_step(sph_ctx *ctx, const float *feats, const float *target, int64_t nb,
+                        float lr, float *loss_host, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPH_H */

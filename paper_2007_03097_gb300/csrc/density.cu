@@ -1,0 +1,341 @@
+// Density and smoothing length (Eqs. 7 and 9): rho_a = sum_b m_b W(r_ab, h_a)
+// with the self term, solved jointly with h_a = eta (m_a/rho_a)^(1/3) by a
+// per-particle Newton iteration, one density evaluation per sweep:
+//   f(h) = m eta^3 / h^3 - rho(h),  f'(h) = -3 m eta^3 / h^4 - drho/dh,
+// bracketed by the evaluated smoothing lengths on either side of the root;
+// a step leaving the closed interval [max(lo, h/2), min(hi, 2h)] (closed, so
+// that a particle already at its root takes the zero step) or with f' >= 0
+// is replaced by
+// the midpoint towards the admissible end the sign of f points to; the
+// result is clamped to [h_min, h_max].  When |h_new - h| < h_tol h the step
+// is applied and one more evaluation at the final h gives rho, drho/dh and
+// the neighbour count.  The paper states the fixed point but not the solver.
+//
+// One warp per target group, one lane per target; each lane walks its own
+// neighbour list (slot-major, coalesced) and re-tests every entry exactly:
+// FP64 r^2 without fused multiply-add in SPH_FP64, FP32 on two-float relative
+// coordinates in SPH_MIXED.  Groups whose particles are all done drop out of
+// the next sweep.
+#include "sph_internal.cuh"
+
+namespace {
+
+constexpr int DW = 4;   // warps per block
+
+struct DensArgs {
+    const int32_t *act;
+    int n_act;
+    int32_t *act_next;
+    const int32_t *group_begin;
+    const int64_t *goff;
+    const int32_t *gwidth;
+    const uint32_t *nbl;
+    int64_t cap;
+    const double *x, *y, *z;
+    const float *xh, *xl, *yh, *yl, *zh, *zl;
+    void *h;
+    const void *m;
+    void *rho, *omega;
+    int32_t *nnb;
+    double *it_lo, *it_hi;
+    int32_t *it_flags, *it_sweeps;
+    const float *cov;
+    int kernel, periodic, fixed_h, max_sweeps;
+    double L, eta3, h_tol, h_min, h_max;
+    DevCounters *cnt;
+};
+
+template <typename T, bool FP64POS>
+__global__ void __launch_bounds__(DW * 32) k_density(DensArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int gi = blockIdx.x * DW + (threadIdx.x >> 5);
+    if (gi >= a.n_act) return;
+    const int g = a.act[gi];
+    const int gb = a.group_begin[g], ge = a.group_begin[g + 1];
+    const bool tgt = lane < ge - gb;
+    const int i = gb + (tgt ? lane : 0);
+    T *hp = (T *)a.h;
+    const T *mp = (const T *)a.m;
+    int32_t flags = tgt ? a.it_flags[i] : IT_DONE;
+    const bool active = !(flags & IT_DONE);
+    const T h = active ? hp[i] : T(1);
+    const T hinv = T(1) / h;
+    const int64_t off = a.goff[g];
+    int width = a.gwidth[g];
+    if (off + 32 * (int64_t)width > a.cap) width = 0;    // never read past the lists
+
+    T sum_w = T(0), sum_dh = T(0);
+    int cnt = 0;
+    if (active) {
+        if (FP64POS) {
+            const double xa = a.x[i], ya = a.y[i], za = a.z[i];
+            const double L = a.L, half = 0.5 * a.L;
+            const double thr = __dmul_rn(__dmul_rn(4.0, (double)h), (double)h);
+            for (int k = 0; k < width; ++k) {
+                const uint32_t b = a.nbl[off + (int64_t)k * 32 + lane];
+                if (b == SPH_SENTINEL) continue;
+                const double dx = sep_d(xa, a.x[b], a.periodic, L, half);
+                const double dy = sep_d(ya, a.y[b], a.periodic, L, half);
+                const double dz = sep_d(za, a.z[b], a.periodic, L, half);
+                const double r2 = r2_d(dx, dy, dz);
+                if (!(r2 < thr)) continue;
+                const T q = (T)sqrt(r2) * hinv;
+                T w, dw;
+                kern_wdw<T>(a.kernel, q, w, dw);
+                const T mb = mp[b];
+                sum_w += mb * w;
+                sum_dh += mb * (T(3) * w + q * dw);
+                ++cnt;
+            }
+        } else {
+            const float xah = a.xh[i], xal = a.xl[i], yah = a.yh[i], yal = a.yl[i], zah = a.zh[i], zal = a.zl[i];
+            const float L = (float)a.L, half = 0.5f * L;
+            const float hf = (float)h;
+            const float thr = __fmul_rn(__fmul_rn(4.f, hf), hf);
+            for (int k = 0; k < width; ++k) {
+                const uint32_t b = a.nbl[off + (int64_t)k * 32 + lane];
+                if (b == SPH_SENTINEL) continue;
+                const float dx = sep_f(xah, xal, a.xh[b], a.xl[b], a.periodic, L, half);
+                const float dy = sep_f(yah, yal, a.yh[b], a.yl[b], a.periodic, L, half);
+                const float dz = sep_f(zah, zal, a.zh[b], a.zl[b], a.periodic, L, half);
+                const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                if (!(r2 < thr)) continue;
+                const T q = (T)sqrtf(r2) * hinv;
+                T w, dw;
+                kern_wdw<T>(a.kernel, q, w, dw);
+                const T mb = mp[b];
+                sum_w += mb * w;
+                sum_dh += mb * (T(3) * w + q * dw);
+                ++cnt;
+            }
+        }
+    }
+
+    bool still = false;
+    if (active) {
+        const T ma = mp[i];
+        sum_w += ma;                    // self term, w(0) = 1 for every kernel
+        sum_dh += T(3) * ma;            // 3 w(0) + 0 w'(0)
+        const T sig = kern_sigma<T>(a.kernel);
+        const T h3i = hinv * hinv * hinv;
+        const T rho = sig * h3i * sum_w;
+        const T drho = -sig * h3i * hinv * sum_dh;
+        const int sweeps = a.it_sweeps[i] + 1;
+        a.it_sweeps[i] = sweeps;
+        bool done = false;
+        T hn = h;
+        if (flags & IT_FINAL) {
+            done = true;
+        } else {
+            const T eta3 = (T)a.eta3;
+            const T f = ma * eta3 / (h * h * h) - rho;
+            if (f == T(0)) {
+                done = true;
+            } else if (sweeps >= a.max_sweeps) {
+                done = true;
+                flags |= IT_NOT_CONV;
+            } else {
+                const T fp = T(-3) * ma * eta3 / (h * h * h * h) - drho;
+                double lo = a.it_lo[i], hi = a.it_hi[i];
+                if (f > T(0)) { if ((double)h > lo) lo = (double)h; }
+                else { if ((double)h < hi) hi = (double)h; }
+                const T alo = T(0.5) * h > (T)lo ? T(0.5) * h : (T)lo;
+                const T ahi = T(2) * h < (T)hi ? T(2) * h : (T)hi;
+                bool ok = false;
+                if (fp < T(0)) {
+                    hn = h - f / fp;
+                    ok = (hn >= alo) && (hn <= ahi);
+                }
+                if (!ok) hn = f > T(0) ? T(0.5) * (h + ahi) : T(0.5) * (h + alo);
+                if (hn < (T)a.h_min) hn = (T)a.h_min;
+                if (hn > (T)a.h_max) hn = (T)a.h_max;
+                const bool conv = fabs((double)(hn - h)) < a.h_tol * (double)h;
+                a.it_lo[i] = lo;
+                a.it_hi[i] = hi;
+                hp[i] = hn;
+                if (conv) flags |= IT_FINAL;
+                if ((double)(2 * hn) > (double)a.cov[i]) {
+                    flags |= IT_UNCOVERED;
+                    atomicAdd(&a.cnt->n_uncovered, 1);
+                }
+            }
+        }
+        if (done) {
+            flags |= IT_DONE;
+            if (flags & IT_NOT_CONV) atomicAdd(&a.cnt->n_not_conv, 1);
+            else if (!a.fixed_h && ((double)h <= a.h_min || (double)h >= a.h_max)) {
+                flags |= IT_H_BOUNDS;
+                atomicAdd(&a.cnt->n_hbounds, 1);
+            }
+        }
+        ((T *)a.rho)[i] = rho;
+        ((T *)a.omega)[i] = drho;
+        a.nnb[i] = cnt;
+        a.it_flags[i] = flags & ~IT_UNCOVERED;
+        still = !done;
+    }
+    int c = cnt;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    const unsigned amask = __ballot_sync(0xffffffffu, active);
+    const unsigned smask = __ballot_sync(0xffffffffu, still);
+    if (lane == 0) {
+        atomicAdd(&a.cnt->interactions, (unsigned long long)c);
+        atomicAdd(&a.cnt->evaluations, (unsigned long long)__popc(amask));
+        if (smask) a.act_next[atomicAdd(&a.cnt->n_active_groups, 1)] = g;
+    }
+}
+
+template <typename T>
+__global__ void k_dens_init(T *__restrict__ h, const T *__restrict__ seed, int64_t n, int fixed_h,
+                            int32_t *__restrict__ flags, int32_t *__restrict__ sweeps, double *__restrict__ lo,
+                            double *__restrict__ hi)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (seed) h[i] = seed[i];
+    flags[i] = fixed_h ? IT_FINAL : 0;
+    sweeps[i] = 0;
+    lo[i] = 0.0;
+    hi[i] = __longlong_as_double(0x7ff0000000000000ll);   // +inf
+}
+
+__global__ void k_iota_i32(int32_t *v, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = (int32_t)i;
+}
+
+__global__ void k_reset_sweep(DevCounters *c)
+{
+    c->interactions = 0;
+    c->evaluations = 0;
+    c->n_active_groups = 0;
+    c->n_uncovered = 0;
+}
+
+__global__ void k_reset_status(DevCounters *c)
+{
+    c->n_not_conv = 0;
+    c->n_hbounds = 0;
+    c->err = 0;
+}
+
+// Ideal-gas EOS: P = (gamma-1) rho u, c = sqrt(gamma (gamma-1) u), and P/rho^2.
+template <typename T>
+__global__ void k_eos(const T *__restrict__ rho, const T *__restrict__ u, int64_t n, double gamma,
+                      T *__restrict__ P, T *__restrict__ c, T *__restrict__ pr2)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T g = (T)gamma, g1 = (T)(gamma - 1.0);
+    const T r = rho[i], ui = u[i];
+    const T p = g1 * r * ui;
+    P[i] = p;
+    c[i] = sqrt(g * g1 * ui);
+    pr2[i] = p / (r * r);
+}
+
+template <typename T>
+int run_impl(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats *st, cudaStream_t s)
+{
+    const int64_t n = p->n;
+    const sph_params &q = ctx->prm;
+    const int64_t launches0 = ctx->launches;
+    double kernel_ms = 0.0;
+    k_reset_status<<<1, 1, 0, s>>>(ctx->dcnt);
+    k_dens_init<T><<<grid_for(n, 256), 256, 0, s>>>((T *)p->h, (const T *)seed, n, q.fixed_h, ctx->it_flags,
+                                                     ctx->it_sweeps, ctx->it_lo, ctx->it_hi);
+    SPH_CHECK_LAUNCH();
+    SPH_TRY(lists_build(ctx, p, 0, s));
+    int builds = 1;
+    int n_act = (int)ctx->n_groups;
+    k_iota_i32<<<grid_for(n_act, 256), 256, 0, s>>>(ctx->act_groups[0], n_act);
+    SPH_CHECK_LAUNCH();
+    DensArgs a{};
+    a.group_begin = ctx->group_begin;
+    a.goff = ctx->group_off;
+    a.gwidth = ctx->group_width;
+    a.nbl = ctx->nbl;
+    a.cap = ctx->nbl_cap;
+    a.x = p->x; a.y = p->y; a.z = p->z;
+    a.xh = ctx->xh; a.xl = ctx->xl; a.yh = ctx->yh; a.yl = ctx->yl; a.zh = ctx->zh; a.zl = ctx->zl;
+    a.h = p->h; a.m = p->m; a.rho = p->rho; a.omega = p->omega; a.nnb = p->nnb;
+    a.it_lo = ctx->it_lo; a.it_hi = ctx->it_hi; a.it_flags = ctx->it_flags; a.it_sweeps = ctx->it_sweeps;
+    a.cov = ctx->cov;
+    a.kernel = q.kernel; a.periodic = q.periodic; a.fixed_h = q.fixed_h; a.max_sweeps = q.max_sweeps;
+    a.L = ctx->dom[3];
+    a.eta3 = q.eta * q.eta * q.eta;
+    a.h_tol = q.h_tol; a.h_min = q.h_min; a.h_max = q.h_max;
+    a.cnt = ctx->dcnt;
+    int cur = 0, sweeps = 0;
+    int64_t inter = 0, evals = 0;
+    for (;;) {
+        k_reset_sweep<<<1, 1, 0, s>>>(ctx->dcnt);
+        a.act = ctx->act_groups[cur];
+        a.act_next = ctx->act_groups[cur ^ 1];
+        a.n_act = n_act;
+        SPH_CUDA(cudaEventRecord(ctx->kev[0], s));
+        if (ctx->fp64) k_density<T, true><<<grid_for(n_act, DW), DW * 32, 0, s>>>(a);
+        else k_density<T, false><<<grid_for(n_act, DW), DW * 32, 0, s>>>(a);
+        SPH_CHECK_LAUNCH();
+        SPH_CUDA(cudaEventRecord(ctx->kev[1], s));
+        ++sweeps;
+        SPH_TRY(sync_counters(ctx, s));
+        {
+            float f = 0.f;
+            SPH_CUDA(cudaEventElapsedTime(&f, ctx->kev[0], ctx->kev[1]));
+            kernel_ms += f;
+        }
+        inter += (int64_t)ctx->hcnt->interactions;
+        evals += (int64_t)ctx->hcnt->evaluations;
+        if (ctx->hcnt->err & (ERRB_LIST_CAPACITY | ERRB_STACK))
+            return sph_fail(ctx, SPH_ERR_CAPACITY, "sph_density: neighbour-list capacity exceeded");
+        n_act = ctx->hcnt->n_active_groups;
+        if (n_act == 0 || sweeps > q.max_sweeps + 1) break;
+        if (ctx->hcnt->n_uncovered > 0) {
+            SPH_TRY(lists_build(ctx, p, 0, s));
+            ++builds;
+        }
+        cur ^= 1;
+    }
+    SPH_TRY(eos_run(ctx, p, p->u, s));
+    if (st) {
+        st->sweeps = sweeps;
+        st->list_builds = builds;
+        st->n_unconverged = ctx->hcnt->n_not_conv;
+        st->n_hbounds = ctx->hcnt->n_hbounds;
+        st->interactions = inter;
+        st->list_entries = (int64_t)ctx->hcnt->list_total;
+        st->evaluations = evals;
+        st->kernel_ms = kernel_ms;
+        st->launches = ctx->launches - launches0;
+    }
+    if (ctx->hcnt->n_not_conv > 0)
+        return sph_fail(ctx, SPH_ERR_NOT_CONVERGED, "sph_density: h iteration reached max_sweeps for " +
+                                                        std::to_string(ctx->hcnt->n_not_conv) + " particles");
+    if (ctx->hcnt->n_hbounds > 0)
+        return sph_fail(ctx, SPH_ERR_H_BOUNDS, "sph_density: converged h on h_min/h_max for " +
+                                                   std::to_string(ctx->hcnt->n_hbounds) + " particles");
+    return SPH_OK;
+}
+
+}  // namespace
+
+int density_run(sph_ctx *ctx, sph_particles *p, const void *h_seed, sph_density_stats *st, cudaStream_t s)
+{
+    return ctx->fp64 ? run_impl<double>(ctx, p, h_seed, st, s) : run_impl<float>(ctx, p, h_seed, st, s);
+}
+
+int eos_run(sph_ctx *ctx, sph_particles *p, const void *u, cudaStream_t s)
+{
+    const double g = ctx->prm.gamma;
+    if (ctx->fp64)
+        k_eos<double><<<grid_for(p->n, 256), 256, 0, s>>>((const double *)p->rho, (const double *)u, p->n, g,
+                                                          (double *)p->P, (double *)p->c, (double *)ctx->pr2);
+    else
+        k_eos<float><<<grid_for(p->n, 256), 256, 0, s>>>((const float *)p->rho, (const float *)u, p->n, g,
+                                                         (float *)p->P, (float *)p->c, (float *)ctx->pr2);
+    SPH_CHECK_LAUNCH();
+    return SPH_OK;
+}

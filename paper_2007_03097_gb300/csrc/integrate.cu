@@ -1,0 +1,188 @@
+// Kick-drift-kick leapfrog around the right-hand side (the paper names no
+// integrator), FP64 position update and periodic wrap, and deterministic FP64
+// totals: sum m v, sum m a, sum m (v^2/2 + u), sum m (v . a + du/dt) and the
+// CFL minimum of h / vsig.
+#include <cfloat>
+
+#include "sph_internal.cuh"
+
+namespace {
+
+template <typename T>
+__global__ void k_kick_drift(double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
+                             T *__restrict__ vx, T *__restrict__ vy, T *__restrict__ vz, T *__restrict__ u,
+                             const T *__restrict__ ax, const T *__restrict__ ay, const T *__restrict__ az,
+                             const T *__restrict__ du, int64_t n, double dt, int periodic, double3 lo,
+                             double3 hi)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T hdt = (T)(0.5 * dt);
+    const T vxh = vx[i] + ax[i] * hdt, vyh = vy[i] + ay[i] * hdt, vzh = vz[i] + az[i] * hdt;
+    vx[i] = vxh; vy[i] = vyh; vz[i] = vzh;
+    u[i] = u[i] + du[i] * hdt;
+    double px = x[i] + (double)vxh * dt, py = y[i] + (double)vyh * dt, pz = z[i] + (double)vzh * dt;
+    if (periodic) {
+        if (px >= hi.x) px -= hi.x - lo.x; else if (px < lo.x) px += hi.x - lo.x;
+        if (py >= hi.y) py -= hi.y - lo.y; else if (py < lo.y) py += hi.y - lo.y;
+        if (pz >= hi.z) pz -= hi.z - lo.z; else if (pz < lo.z) pz += hi.z - lo.z;
+    }
+    x[i] = px; y[i] = py; z[i] = pz;
+}
+
+// predicted v and u at the end of the step from the old rates
+template <typename T>
+__global__ void k_predict(const T *__restrict__ vx, const T *__restrict__ vy, const T *__restrict__ vz,
+                          const T *__restrict__ u, const T *__restrict__ ax, const T *__restrict__ ay,
+                          const T *__restrict__ az, const T *__restrict__ du, int64_t n, double dt,
+                          T *__restrict__ px, T *__restrict__ py, T *__restrict__ pz, T *__restrict__ pu)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T hdt = (T)(0.5 * dt);
+    px[i] = vx[i] + ax[i] * hdt;
+    py[i] = vy[i] + ay[i] * hdt;
+    pz[i] = vz[i] + az[i] * hdt;
+    pu[i] = u[i] + du[i] * hdt;
+}
+
+template <typename T>
+__global__ void k_kick(T *__restrict__ vx, T *__restrict__ vy, T *__restrict__ vz, T *__restrict__ u,
+                       const T *__restrict__ ax, const T *__restrict__ ay, const T *__restrict__ az,
+                       const T *__restrict__ du, int64_t n, double dt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T hdt = (T)(0.5 * dt);
+    vx[i] = vx[i] + ax[i] * hdt;
+    vy[i] = vy[i] + ay[i] * hdt;
+    vz[i] = vz[i] + az[i] * hdt;
+    u[i] = u[i] + du[i] * hdt;
+}
+
+constexpr int NT = 9;   // 8 sums + 1 min
+
+// Per-block partial totals in FP64 (fixed grid, fixed order: deterministic).
+template <typename T>
+__global__ void k_totals_partial(const T *__restrict__ m, const T *__restrict__ vx, const T *__restrict__ vy,
+                                 const T *__restrict__ vz, const T *__restrict__ u, const T *__restrict__ ax,
+                                 const T *__restrict__ ay, const T *__restrict__ az, const T *__restrict__ du,
+                                 const T *__restrict__ pvx, const T *__restrict__ pvy,
+                                 const T *__restrict__ pvz, const T *__restrict__ h,
+                                 const T *__restrict__ vsig, int64_t n, double *__restrict__ part)
+{
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double mn = DBL_MAX;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double mi = m[i], vxi = vx[i], vyi = vy[i], vzi = vz[i];
+        const double axi = ax[i], ayi = ay[i], azi = az[i];
+        acc[0] += mi * vxi; acc[1] += mi * vyi; acc[2] += mi * vzi;
+        acc[3] += mi * axi; acc[4] += mi * ayi; acc[5] += mi * azi;
+        acc[6] += mi * (0.5 * (vxi * vxi + vyi * vyi + vzi * vzi) + (double)u[i]);
+        const double wx = pvx ? (double)pvx[i] : vxi, wy = pvx ? (double)pvy[i] : vyi, wz = pvx ? (double)pvz[i] : vzi;
+        acc[7] += mi * (wx * axi + wy * ayi + wz * azi + (double)du[i]);
+        if (vsig) { const double v = vsig[i]; if (v > 0) mn = fmin(mn, (double)h[i] / v); }
+    }
+    __shared__ double s[NT][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = 0; k < 8; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s[k][warp] = v;
+    }
+    for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    if (lane == 0) s[8][warp] = mn;
+    __syncthreads();
+    if (threadIdx.x < NT) {
+        double v = s[threadIdx.x][0];
+        for (int w = 1; w < nw; ++w) v = threadIdx.x < 8 ? v + s[threadIdx.x][w] : fmin(v, s[threadIdx.x][w]);
+        part[blockIdx.x * NT + threadIdx.x] = v;
+    }
+}
+
+__global__ void k_totals_final(const double *__restrict__ part, int nb, DevCounters *cnt)
+{
+    if (threadIdx.x >= NT) return;
+    double v = part[threadIdx.x];
+    for (int b = 1; b < nb; ++b) v = threadIdx.x < 8 ? v + part[b * NT + threadIdx.x] : fmin(v, part[b * NT + threadIdx.x]);
+    if (threadIdx.x < 8) cnt->totals[threadIdx.x] = v;
+    else cnt->min_dt = v;
+}
+
+template <typename T>
+int kd_impl(sph_ctx *ctx, sph_particles *p, double dt, cudaStream_t s)
+{
+    const sph_params &q = ctx->prm;
+    k_kick_drift<T><<<grid_for(p->n, 256), 256, 0, s>>>(
+        p->x, p->y, p->z, (T *)p->vx, (T *)p->vy, (T *)p->vz, (T *)p->u, (const T *)p->ax, (const T *)p->ay,
+        (const T *)p->az, (const T *)p->dudt, p->n, dt, q.periodic, make_double3(q.box_lo[0], q.box_lo[1], q.box_lo[2]),
+        make_double3(q.box_hi[0], q.box_hi[1], q.box_hi[2]));
+    SPH_CHECK_LAUNCH();
+    return SPH_OK;
+}
+
+template <typename T>
+int pred_impl(sph_ctx *ctx, sph_particles *p, double dt, cudaStream_t s)
+{
+    k_predict<T><<<grid_for(p->n, 256), 256, 0, s>>>(
+        (const T *)p->vx, (const T *)p->vy, (const T *)p->vz, (const T *)p->u, (const T *)p->ax, (const T *)p->ay,
+        (const T *)p->az, (const T *)p->dudt, p->n, dt, (T *)ctx->vpx, (T *)ctx->vpy, (T *)ctx->vpz, (T *)ctx->upred);
+    SPH_CHECK_LAUNCH();
+    return SPH_OK;
+}
+
+template <typename T>
+int kick_impl(sph_ctx *ctx, sph_particles *p, double dt, cudaStream_t s)
+{
+    k_kick<T><<<grid_for(p->n, 256), 256, 0, s>>>((T *)p->vx, (T *)p->vy, (T *)p->vz, (T *)p->u, (const T *)p->ax,
+                                                  (const T *)p->ay, (const T *)p->az, (const T *)p->dudt, p->n, dt);
+    SPH_CHECK_LAUNCH();
+    return SPH_OK;
+}
+
+template <typename T>
+int totals_impl(sph_ctx *ctx, const sph_particles *p, const void *pvx, const void *pvy, const void *pvz,
+                const void *u, cudaStream_t s)
+{
+    const int nb = ctx->red_blocks;
+    k_totals_partial<T><<<nb, 256, 0, s>>>((const T *)p->m, (const T *)p->vx, (const T *)p->vy, (const T *)p->vz,
+                                           (const T *)u, (const T *)p->ax, (const T *)p->ay, (const T *)p->az,
+                                           (const T *)p->dudt, (const T *)pvx, (const T *)pvy, (const T *)pvz,
+                                           (const T *)p->h, (const T *)p->vsig, p->n, ctx->red);
+    SPH_CHECK_LAUNCH();
+    k_totals_final<<<1, 32, 0, s>>>(ctx->red, nb, ctx->dcnt);
+    SPH_CHECK_LAUNCH();
+    return SPH_OK;
+}
+
+}  // namespace
+
+int kick_drift(sph_ctx *ctx, sph_particles *p, double dt, cudaStream_t s)
+{
+    return ctx->fp64 ? kd_impl<double>(ctx, p, dt, s) : kd_impl<float>(ctx, p, dt, s);
+}
+
+int predict(sph_ctx *ctx, sph_particles *p, double dt, cudaStream_t s)
+{
+    return ctx->fp64 ? pred_impl<double>(ctx, p, dt, s) : pred_impl<float>(ctx, p, dt, s);
+}
+
+int kick(sph_ctx *ctx, sph_particles *p, double dt, cudaStream_t s)
+{
+    return ctx->fp64 ? kick_impl<double>(ctx, p, dt, s) : kick_impl<float>(ctx, p, dt, s);
+}
+
+// totals of p with u; power uses the predicted velocities (pvx..) when given
+int totals_run(sph_ctx *ctx, const sph_particles *p, const void *pvx, const void *pvy, const void *pvz,
+               const void *u, cudaStream_t s)
+{
+    return ctx->fp64 ? totals_impl<double>(ctx, p, pvx, pvy, pvz, u, s)
+                     : totals_impl<float>(ctx, p, pvx, pvy, pvz, u, s);
+}
+
+int sync_counters(sph_ctx *ctx, cudaStream_t s)
+{
+    SPH_CUDA(cudaMemcpyAsync(ctx->hcnt, ctx->dcnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(cudaStreamSynchronize(s));
+    return SPH_OK;
+}

@@ -1,0 +1,383 @@
+// Neighbour lists (Sec. 2.1, group tree traversal): one warp per target group
+// of at most 32 Morton-consecutive particles walks the radix tree over the
+// leaf cells, pruning with the group's box, and stages the particles of every
+// accepted leaf into a shared-memory source tile.  Each lane owns one target
+// and tests the tile's sources in FP32 on two-float relative coordinates
+// with a small relative margin, so the list is a superset of the exact set.
+// The exact FP64 (or FP32) decision is taken again by the pass that uses the
+// list.  Lists are stored slot-major per group (entry (slot, lane) at
+// off[g] + 32 slot + lane) so that the consumers read them coalesced.
+//   kind 0 (density): b with r_ab <= cov_a, the coverage radius 2 h_a (1+skin)
+//   kind 1 (force):   b with r_ab <= max(2 h_a, h_a + h_b)
+#include "sph_internal.cuh"
+
+namespace {
+
+constexpr int LW = 4;              // warps per block
+constexpr int STACK = 1024;        // traversal stack entries per warp
+constexpr int TILE = 64;           // source tile entries per warp
+constexpr float MARGIN = 2e-5f;    // relative margin of the FP32 tests
+
+struct ListArgs {
+    const float *xh, *xl, *yh, *yl, *zh, *zl;
+    const void *h;
+    const float *cov;
+    const int32_t *group_begin;
+    const float4 *group_lo, *group_hi;
+    const int32_t *leaf_begin;
+    const float4 *leaf_lo, *leaf_hi;
+    int n_leaves, n_groups;
+    const int32_t *child;
+    const float4 *node_lo, *node_hi;
+    int periodic;
+    float L, half, slack;
+    int32_t *group_width;
+    const int64_t *group_off;
+    uint32_t *nbl;
+    int64_t cap;
+    DevCounters *cnt;
+};
+
+// gap between two boxes along one axis (periodic: minimum image of centres)
+__device__ __forceinline__ float axis_gap(float alo, float ahi, float blo, float bhi, int periodic, float L,
+                                          float half)
+{
+    float ca = 0.5f * (alo + ahi), ea = 0.5f * (ahi - alo);
+    float cb = 0.5f * (blo + bhi), eb = 0.5f * (bhi - blo);
+    float d = cb - ca;
+    if (periodic) d -= L * rintf(d / L);     // |d| <= L/2: the nearest image
+    return fmaxf(0.f, fabsf(d) - ea - eb);
+}
+
+template <typename T>
+__device__ __forceinline__ float h_up(const T *h, int i)
+{
+    if (sizeof(T) == 8) return __double2float_ru((double)h[i]);
+    return (float)h[i];
+}
+
+template <typename T, int KIND, bool FILL>
+__global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
+{
+    __shared__ int32_t s_stack[LW][STACK];
+    __shared__ float s_src[LW][7][TILE];
+    __shared__ int32_t s_idx[LW][TILE];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int g = blockIdx.x * LW + w;
+    if (g >= a.n_groups) return;
+    int32_t *stack = s_stack[w];
+    float(*src)[TILE] = s_src[w];
+    int32_t *sidx = s_idx[w];
+    const T *h = (const T *)a.h;
+
+    const int gb = a.group_begin[g], ge = a.group_begin[g + 1];
+    const bool tgt = lane < ge - gb;
+    const int ia = gb + (tgt ? lane : 0);
+    const float axh = a.xh[ia], axl = a.xl[ia], ayh = a.yh[ia], ayl = a.yl[ia], azh = a.zh[ia], azl = a.zl[ia];
+    const float ha = h_up(h, ia);
+    float thr_own;                                 // density: cov^2, force: (2 h_a)^2
+    if (KIND == 0) { float c = a.cov[ia]; thr_own = c * c * (1.f + MARGIN); }
+    else thr_own = 4.f * ha * ha * (1.f + MARGIN);
+    const float4 qlo = a.group_lo[g], qhi = a.group_hi[g];
+    const float ghmax = qlo.w;
+    float qrad;                                    // density: max coverage in the group
+    if (KIND == 0) {
+        float c = tgt ? a.cov[ia] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) c = fmaxf(c, __shfl_xor_sync(0xffffffffu, c, o));
+        qrad = c;
+    } else {
+        qrad = 2.f * ghmax;
+    }
+
+    int64_t off = 0;
+    int width = 0;
+    bool fits = true;
+    if (FILL) {
+        off = a.group_off[g];
+        width = a.group_width[g];
+        fits = off + 32 * (int64_t)width <= a.cap;
+        if (!fits) width = 0;                      // flagged below; nothing written
+    }
+    int count = 0;
+    bool overflow = false;
+
+    auto process = [&](int ns) {
+        for (int k = 0; k < ns; ++k) {
+            const int b = sidx[k];
+            float dx = sep_f(axh, axl, src[0][k], src[1][k], a.periodic, a.L, a.half);
+            float dy = sep_f(ayh, ayl, src[2][k], src[3][k], a.periodic, a.L, a.half);
+            float dz = sep_f(azh, azl, src[4][k], src[5][k], a.periodic, a.L, a.half);
+            float r2 = (dx * dx + dy * dy) + dz * dz;
+            float thr = thr_own;
+            if (KIND == 1) { float hs = ha + src[6][k]; thr = fmaxf(thr, hs * hs * (1.f + MARGIN)); }
+            if (tgt && b != ia && r2 <= thr) {
+                if (FILL && count < width) a.nbl[off + (int64_t)count * 32 + lane] = (uint32_t)b;
+                ++count;
+            }
+        }
+    };
+
+    int sp = 0;
+    if (lane == 0) stack[0] = a.n_leaves > 1 ? 0 : (int)0x80000000;
+    sp = 1;
+    int ns = 0;
+    // a correct radix tree visits each node at most once; the bound guards a
+    // corrupted tree against an endless walk
+    int64_t budget = 4 * (int64_t)a.n_leaves + 64;
+    __syncwarp();
+    while (sp > 0) {
+        if (--budget < 0) { overflow = true; break; }
+        const int take = sp < 32 ? sp : 32;
+        sp -= take;
+        const int node = lane < take ? stack[sp + lane] : 0;
+        __syncwarp();
+        bool acc = false;
+        const bool leaf = node < 0;
+        if (lane < take) {
+            const int id = node & 0x7fffffff;
+            float4 lo, hi;
+            if (leaf) { lo = a.leaf_lo[id]; hi = a.leaf_hi[id]; }
+            else { lo = a.node_lo[id]; hi = a.node_hi[id]; }
+            float r = KIND == 0 ? qrad : fmaxf(qrad, ghmax + lo.w);
+            float gx = axis_gap(qlo.x, qhi.x, lo.x, hi.x, a.periodic, a.L, a.half);
+            float gy = axis_gap(qlo.y, qhi.y, lo.y, hi.y, a.periodic, a.L, a.half);
+            float gz = axis_gap(qlo.z, qhi.z, lo.z, hi.z, a.periodic, a.L, a.half);
+            gx = fmaxf(0.f, gx - a.slack);
+            gy = fmaxf(0.f, gy - a.slack);
+            gz = fmaxf(0.f, gz - a.slack);
+            acc = (gx * gx + gy * gy) + gz * gz <= r * r * (1.f + MARGIN);
+        }
+        const unsigned mint = __ballot_sync(0xffffffffu, acc && !leaf);
+        if (acc && !leaf) {
+            const int pos = sp + 2 * __popc(mint & ((1u << lane) - 1u));
+            if (pos + 1 < STACK) {
+                stack[pos] = a.child[2 * node];
+                stack[pos + 1] = a.child[2 * node + 1];
+            }
+        }
+        sp += 2 * __popc(mint);
+        if (sp > STACK) { overflow = true; sp = 0; }
+        __syncwarp();
+        unsigned mleaf = __ballot_sync(0xffffffffu, acc && leaf);
+        while (mleaf) {
+            const int l = __ffs(mleaf) - 1;
+            mleaf &= mleaf - 1;
+            const int id = __shfl_sync(0xffffffffu, node, l) & 0x7fffffff;
+            const int lb = a.leaf_begin[id], le = a.leaf_begin[id + 1];
+            const int cnt = le - lb;
+            if (lane < cnt) {
+                const int j = lb + lane;
+                const int t = ns + lane;
+                src[0][t] = a.xh[j]; src[1][t] = a.xl[j];
+                src[2][t] = a.yh[j]; src[3][t] = a.yl[j];
+                src[4][t] = a.zh[j]; src[5][t] = a.zl[j];
+                src[6][t] = KIND == 1 ? h_up(h, j) : 0.f;
+                sidx[t] = j;
+            }
+            ns += cnt;
+            __syncwarp();
+            if (ns >= 32) {
+                process(32);
+                __syncwarp();
+                const int rest = ns - 32;
+                if (lane < rest) {
+                    for (int c = 0; c < 7; ++c) src[c][lane] = src[c][32 + lane];
+                    sidx[lane] = sidx[32 + lane];
+                }
+                ns = rest;
+                __syncwarp();
+            }
+        }
+    }
+    if (ns > 0) process(ns);
+
+    if (overflow && lane == 0) atomicOr(&a.cnt->err, ERRB_STACK);
+    int wmax = count;
+    for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+    if (!FILL) {
+        if (lane == 0) a.group_width[g] = wmax;
+    } else {
+        if ((!fits || wmax > width) && lane == 0) atomicOr(&a.cnt->err, ERRB_LIST_CAPACITY);
+        for (int k = count; k < width; ++k) a.nbl[off + (int64_t)k * 32 + lane] = SPH_SENTINEL;
+    }
+}
+
+// slots of group g: 32 * width
+__global__ void k_slots(const int32_t *__restrict__ width, int ng, int32_t *__restrict__ slots)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < ng) slots[g] = 32 * width[g];
+}
+
+__global__ void k_list_total(const int64_t *__restrict__ off, const int32_t *__restrict__ width, int ng,
+                             int64_t cap, int64_t *__restrict__ off_end, DevCounters *cnt)
+{
+    const int64_t total = off[ng - 1] + 32 * (int64_t)width[ng - 1];
+    off_end[0] = total;
+    cnt->list_total = (unsigned long long)total;
+    if (total > cap) atomicOr(&cnt->err, ERRB_LIST_CAPACITY);
+}
+
+// After an overflowed build no list is valid: empty every group so that no
+// consumer reads past the list buffer before the host sees the error.
+__global__ void k_guard_widths(int32_t *__restrict__ width, int ng, const DevCounters *cnt)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < ng && (cnt->err & (ERRB_LIST_CAPACITY | ERRB_STACK))) width[g] = 0;
+}
+
+// Exact neighbour sets from the lists (kind 0 density, kind 1 force).
+template <typename T, int KIND, bool FP64POS>
+__global__ void k_export(const int32_t *__restrict__ group_begin, int ng, const int64_t *__restrict__ goff,
+                         const int32_t *__restrict__ gwidth, const uint32_t *__restrict__ nbl,
+                         const double *__restrict__ x, const double *__restrict__ y,
+                         const double *__restrict__ z, const float *__restrict__ xh,
+                         const float *__restrict__ xl, const float *__restrict__ yh,
+                         const float *__restrict__ yl, const float *__restrict__ zh,
+                         const float *__restrict__ zl, const T *__restrict__ h, int periodic, double L,
+                         int64_t cap, int64_t *__restrict__ counts, const int64_t *__restrict__ offsets,
+                         uint32_t *__restrict__ idx)
+{
+    const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (g >= ng) return;
+    const int gb = group_begin[g], ge = group_begin[g + 1];
+    if (lane >= ge - gb) return;
+    const int ia = gb + lane;
+    const int64_t off = goff[g];
+    int width = gwidth[g];
+    if (off + 32 * (int64_t)width > cap) width = 0;
+    const T ha = h[ia];
+    int64_t c = 0;
+    const int64_t o = offsets ? offsets[ia] : 0;
+    for (int k = 0; k < width; ++k) {
+        const uint32_t b = nbl[off + (int64_t)k * 32 + lane];
+        if (b == SPH_SENTINEL) continue;
+        bool in;
+        if (FP64POS) {
+            const double half = 0.5 * L;
+            double dx = sep_d(x[ia], x[b], periodic, L, half);
+            double dy = sep_d(y[ia], y[b], periodic, L, half);
+            double dz = sep_d(z[ia], z[b], periodic, L, half);
+            double r2 = r2_d(dx, dy, dz);
+            double hd = (double)ha;
+            in = r2 < __dmul_rn(__dmul_rn(4.0, hd), hd);
+            if (KIND == 1) {
+                double hs = __dadd_rn(hd, (double)h[b]);
+                in = in || r2 < __dmul_rn(hs, hs);
+            }
+        } else {
+            const float Lf = (float)L, hf = 0.5f * Lf;
+            float dx = sep_f(xh[ia], xl[ia], xh[b], xl[b], periodic, Lf, hf);
+            float dy = sep_f(yh[ia], yl[ia], yh[b], yl[b], periodic, Lf, hf);
+            float dz = sep_f(zh[ia], zl[ia], zh[b], zl[b], periodic, Lf, hf);
+            float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+            float hfa = (float)ha;
+            in = r2 < __fmul_rn(__fmul_rn(4.f, hfa), hfa);
+            if (KIND == 1) {
+                float hs = __fadd_rn(hfa, (float)h[b]);
+                in = in || r2 < __fmul_rn(hs, hs);
+            }
+        }
+        if (!in) continue;
+        if (offsets) idx[o + c] = b;
+        ++c;
+    }
+    counts[ia] = c;
+}
+
+template <typename T>
+int build_impl(sph_ctx *ctx, const sph_particles *p, int kind, cudaStream_t s)
+{
+    const int ng = (int)ctx->n_groups;
+    ListArgs a{};
+    a.xh = ctx->xh; a.xl = ctx->xl; a.yh = ctx->yh; a.yl = ctx->yl; a.zh = ctx->zh; a.zl = ctx->zl;
+    a.h = p->h;
+    a.cov = ctx->cov;
+    a.group_begin = ctx->group_begin;
+    a.group_lo = ctx->group_lo; a.group_hi = ctx->group_hi;
+    a.leaf_begin = ctx->leaf_begin;
+    a.leaf_lo = ctx->leaf_lo; a.leaf_hi = ctx->leaf_hi;
+    a.n_leaves = (int)ctx->n_leaves;
+    a.n_groups = ng;
+    a.child = ctx->node_child;
+    a.node_lo = ctx->node_lo; a.node_hi = ctx->node_hi;
+    a.periodic = ctx->prm.periodic;
+    a.L = (float)ctx->dom[3];
+    a.half = 0.5f * a.L;
+    a.slack = (float)(1e-6 * ctx->dom[3]);
+    a.group_width = ctx->group_width;
+    a.group_off = ctx->group_off;
+    a.nbl = ctx->nbl;
+    a.cap = ctx->nbl_cap;
+    a.cnt = ctx->dcnt;
+    const unsigned grid = grid_for(ng, LW);
+    if (kind == 0) k_lists<T, 0, false><<<grid, LW * 32, 0, s>>>(a);
+    else k_lists<T, 1, false><<<grid, LW * 32, 0, s>>>(a);
+    SPH_CHECK_LAUNCH();
+    k_slots<<<grid_for(ng, 256), 256, 0, s>>>(ctx->group_width, ng, ctx->itmp0);
+    SPH_CHECK_LAUNCH();
+    SPH_TRY(scan_exclusive_i64(ctx, ctx->itmp0, ctx->group_off, ng, s));
+    k_list_total<<<1, 1, 0, s>>>(ctx->group_off, ctx->group_width, ng, ctx->nbl_cap, ctx->group_off + ng,
+                                 ctx->dcnt);
+    SPH_CHECK_LAUNCH();
+    if (kind == 0) k_lists<T, 0, true><<<grid, LW * 32, 0, s>>>(a);
+    else k_lists<T, 1, true><<<grid, LW * 32, 0, s>>>(a);
+    SPH_CHECK_LAUNCH();
+    k_guard_widths<<<grid_for(ng, 256), 256, 0, s>>>(ctx->group_width, ng, ctx->dcnt);
+    SPH_CHECK_LAUNCH();
+    return SPH_OK;
+}
+
+// coverage radius of each particle's density list: 2 h (1 + skin), rounded down
+template <typename T>
+__global__ void k_coverage(const T *__restrict__ h, int64_t n, double f, float *__restrict__ cov)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cov[i] = __double2float_rd(2.0 * (double)h[i] * f);
+}
+
+}  // namespace
+
+int lists_build(sph_ctx *ctx, const sph_particles *p, int kind, cudaStream_t s)
+{
+    if (kind == 0) {
+        const double f = 1.0 + ctx->prm.skin;
+        if (ctx->fp64) k_coverage<double><<<grid_for(p->n, 256), 256, 0, s>>>((const double *)p->h, p->n, f, ctx->cov);
+        else k_coverage<float><<<grid_for(p->n, 256), 256, 0, s>>>((const float *)p->h, p->n, f, ctx->cov);
+        SPH_CHECK_LAUNCH();
+    }
+    return ctx->fp64 ? build_impl<double>(ctx, p, kind, s) : build_impl<float>(ctx, p, kind, s);
+}
+
+int neighbors_export(sph_ctx *ctx, const sph_particles *p, int kind, int64_t *counts, const int64_t *offsets,
+                     uint32_t *idx, cudaStream_t s)
+{
+    SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->err, 0, sizeof(uint32_t), s));
+    if (kind == 1) SPH_TRY(tree_refit_h(ctx, p, s));
+    SPH_TRY(lists_build(ctx, p, kind, s));
+    const int ng = (int)ctx->n_groups;
+    const unsigned grid = grid_for((int64_t)ng * 32, 128);
+    const int per = ctx->prm.periodic;
+    const double L = ctx->dom[3];
+#define SPH_EXPORT_ARGS                                                                               \
+    ctx->group_begin, ng, ctx->group_off, ctx->group_width, ctx->nbl, p->x, p->y, p->z, ctx->xh, ctx->xl, \
+        ctx->yh, ctx->yl, ctx->zh, ctx->zl
+    if (ctx->fp64) {
+        if (kind == 0)
+            k_export<double, 0, true><<<grid, 128, 0, s>>>(SPH_EXPORT_ARGS, (const double *)p->h, per, L, ctx->nbl_cap, counts, offsets, idx);
+        else
+            k_export<double, 1, true><<<grid, 128, 0, s>>>(SPH_EXPORT_ARGS, (const double *)p->h, per, L, ctx->nbl_cap, counts, offsets, idx);
+    } else {
+        if (kind == 0)
+            k_export<float, 0, false><<<grid, 128, 0, s>>>(SPH_EXPORT_ARGS, (const float *)p->h, per, L, ctx->nbl_cap, counts, offsets, idx);
+        else
+            k_export<float, 1, false><<<grid, 128, 0, s>>>(SPH_EXPORT_ARGS, (const float *)p->h, per, L, ctx->nbl_cap, counts, offsets, idx);
+    }
+#undef SPH_EXPORT_ARGS
+    SPH_CHECK_LAUNCH();
+    SPH_TRY(sync_counters(ctx, s));
+    if (ctx->hcnt->err & (ERRB_LIST_CAPACITY | ERRB_STACK))
+        return sph_fail(ctx, SPH_ERR_CAPACITY, "sph_neighbors: neighbour-list capacity exceeded");
+    return SPH_OK;
+}

@@ -1,0 +1,285 @@
+// Internal declarations of the GB300 SPH library: the context, device
+// counters, and the small device helpers shared by the kernels (smoothing
+// kernels, minimum image, two-float positions).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "sph.h"
+
+#define SPH_WARP 32
+#define SPH_SENTINEL 0xFFFFFFFFu
+
+// bits of DevCounters::err
+enum : uint32_t {
+    ERRB_NONFINITE = 1u,
+    ERRB_LEAF_DEGENERATE = 2u,   // more than leaf_size particles share one key
+    ERRB_LIST_CAPACITY = 4u,     // neighbour lists exceed nb_capacity
+    ERRB_STACK = 8u,             // traversal stack overflow
+    ERRB_TIE_RUN = 16u,          // equal-key run too long to order by id
+};
+
+// per-particle density iteration flags
+enum : int32_t {
+    IT_DONE = 1,          // rho, omega, nnb final
+    IT_FINAL = 2,         // h converged; next evaluation is the final one
+    IT_NOT_CONV = 4,
+    IT_H_BOUNDS = 8,
+    IT_UNCOVERED = 16,    // 2h exceeds the list coverage radius
+};
+
+// Device-side counters, mirrored into pinned host memory at sync points.
+struct DevCounters {
+    unsigned long long interactions;   // accepted pairs of the last pass/sweep
+    unsigned long long evaluations;    // particle evaluations of the last sweep
+    unsigned long long list_total;     // list slots of the last build
+    uint32_t err;
+    int32_t n_active_groups;           // groups with a particle not yet done
+    int32_t n_uncovered;               // particles whose 2h left the coverage
+    int32_t n_not_conv;
+    int32_t n_hbounds;
+    int32_t n_leaves;
+    int32_t n_groups;
+    int32_t hnet_fallback;
+    double dom[4];                     // key domain lo_x, lo_y, lo_z, L
+    double totals[8];                  // conserved totals
+    double min_dt;                     // min h / vsig
+    float loss;
+    int32_t pad;
+};
+
+struct sph_ctx {
+    sph_params prm{};
+    int64_t n_max = 0;
+    int device = 0;
+    int num_sms = 0;
+    bool fp64 = true;
+    std::string err;
+
+    // tree of the current particle order
+    int64_t n = 0;
+    int64_t n_leaves = 0, n_groups = 0;
+    bool tree_valid = false;
+    double dom[4] = {0, 0, 0, 1};
+    double dt_cfl = 0.0;
+
+    // ---- sort / keys
+    uint64_t *key_a = nullptr, *key_b = nullptr;
+    uint32_t *val_a = nullptr, *val_b = nullptr;
+    uint32_t *hist = nullptr;           // radix histograms, 256 x tiles
+    int64_t hist_cap = 0;
+    // ---- tree
+    uint8_t *dlev = nullptr;            // first differing level with predecessor
+    uint8_t *plev = nullptr;            // leaf level of each particle
+    int32_t *itmp0 = nullptr, *itmp1 = nullptr;   // per-particle int scratch
+    int32_t *itmp2 = nullptr, *itmp3 = nullptr;
+    int32_t *leaf_begin = nullptr;      // n_leaves + 1
+    int32_t *leaf_level = nullptr;
+    int32_t *group_begin = nullptr;     // n_groups + 1
+    float4 *leaf_lo = nullptr, *leaf_hi = nullptr;   // box; .w of lo = h_max
+    int32_t *node_child = nullptr;      // 2 per internal node; leaf = idx | 1<<31
+    int32_t *node_parent = nullptr;     // internal nodes
+    int32_t *leaf_parent = nullptr;
+    uint32_t *node_visit = nullptr;
+    float4 *node_lo = nullptr, *node_hi = nullptr;   // .w of lo = h_max
+    float4 *group_lo = nullptr, *group_hi = nullptr; // .w of lo = h_max
+    // ---- two-float split of the positions (padded)
+    float *xh = nullptr, *xl = nullptr, *yh = nullptr, *yl = nullptr, *zh = nullptr, *zl = nullptr;
+    // ---- neighbour lists (group slabs, slot-major within a group)
+    uint32_t *nbl = nullptr;
+    int64_t nbl_cap = 0;
+    int32_t *group_width = nullptr;
+    int64_t *group_off = nullptr;       // n_groups + 1
+    // ---- density iteration state
+    double *it_lo = nullptr, *it_hi = nullptr;
+    int32_t *it_flags = nullptr;
+    int32_t *it_sweeps = nullptr;
+    float *cov = nullptr;               // coverage radius of each particle's list
+    int32_t *act_groups[2] = {nullptr, nullptr};
+    // ---- force pass / step scratch (precision-typed, 8 bytes per entry)
+    void *vpx = nullptr, *vpy = nullptr, *vpz = nullptr, *upred = nullptr;
+    void *pr2 = nullptr;                // P / rho^2
+    void *hold = nullptr;               // h before the density iteration
+    void *hseed = nullptr;              // h-predictor seeds
+    // ---- gather scratch
+    unsigned char *gbuf = nullptr;
+    size_t gbuf_bytes = 0;
+    // ---- scans and reductions
+    void *scan_tmp = nullptr;
+    size_t scan_tmp_bytes = 0;
+    double *red = nullptr;              // block partials of reductions
+    int red_blocks = 0;
+    // ---- counters
+    DevCounters *dcnt = nullptr;        // device
+    DevCounters *hcnt = nullptr;        // pinned host mirror
+    // ---- h-predictor network
+    float *hn_master = nullptr;         // FP32 master weights
+    __nv_bfloat16 *hn_bf16 = nullptr;   // copy read by the kernels
+    float *hn_m = nullptr, *hn_v = nullptr;  // Adam moments
+    float *hn_grad = nullptr;           // reduced gradient
+    float *hn_part = nullptr;           // per-block partial gradients
+    int hn_part_blocks = 0;
+    int64_t hn_step = 0;
+    float *feats = nullptr;             // n_max x 5
+    float *hn_y = nullptr;              // n_max
+    float *hn_sample = nullptr;         // hnet_batch x 6 (features, target)
+    // ---- timing and launch accounting
+    cudaEvent_t ev[8] = {};
+    cudaEvent_t kev[2 * 64] = {};       // per-sweep density kernel events
+    int64_t launches = 0;               // kernels launched so far
+};
+
+// ------------------------------------------------------------------ helpers
+#define SPH_CUDA(call)                                                             \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);         \
+            return SPH_ERR_CUDA;                                                   \
+        }                                                                          \
+    } while (0)
+
+#define SPH_CHECK_LAUNCH()                                                         \
+    do {                                                                           \
+        ++ctx->launches;                                                           \
+        cudaError_t e_ = cudaGetLastError();                                       \
+        if (e_ != cudaSuccess) {                                                   \
+            ctx->err = std::string("kernel launch: ") + cudaGetErrorString(e_);    \
+            return SPH_ERR_CUDA;                                                   \
+        }                                                                          \
+    } while (0)
+
+#define SPH_TRY(expr)                                                              \
+    do {                                                                           \
+        int s_ = (expr);                                                           \
+        if (s_ != SPH_OK) return s_;                                               \
+    } while (0)
+
+static inline int sph_fail(sph_ctx *ctx, int code, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+static inline unsigned grid_for(int64_t n, int block)
+{
+    int64_t g = (n + block - 1) / block;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+// ---------------------------------------------------- smoothing kernel math
+// W(r, h) = sigma / h^3 w(q), q = r / h, support q < 2 (the same published
+// forms as the oracle, evaluated here in Horner form).
+//   M4:  w = 1 - 3/2 q^2 + 3/4 q^3 (q < 1),  (2 - q)^3 / 4 (1 <= q < 2)
+//   WC2: w = (1 - q/2)^4 (1 + 2q)
+//   WC4: w = (1 - q/2)^6 (1 + 3q + 35/12 q^2)
+// kern_wdw returns w(q) and dw/dq.
+#define SPH_PI 3.14159265358979323846
+template <typename T>
+__device__ __forceinline__ T kern_sigma(int k)
+{
+    return k == SPH_KERNEL_M4 ? T(1.0 / SPH_PI)
+         : k == SPH_KERNEL_WC2 ? T(21.0 / (16.0 * SPH_PI))
+                               : T(495.0 / (256.0 * SPH_PI));
+}
+
+template <typename T>
+__device__ __forceinline__ void kern_wdw(int k, T q, T &w, T &dw)
+{
+    if (k == SPH_KERNEL_M4) {
+        if (q < T(1)) {
+            w = T(1) + q * q * (T(-1.5) + T(0.75) * q);
+            dw = q * (T(-3) + T(2.25) * q);
+        } else {
+            T t = T(2) - q;
+            w = T(0.25) * t * t * t;
+            dw = T(-0.75) * t * t;
+        }
+    } else if (k == SPH_KERNEL_WC2) {
+        T s = T(1) - T(0.5) * q;
+        T s2 = s * s;
+        T s3 = s2 * s;
+        w = s3 * s * (T(1) + T(2) * q);
+        dw = T(-5) * q * s3;
+    } else {
+        T s = T(1) - T(0.5) * q;
+        T s2 = s * s;
+        T s5 = s2 * s2 * s;
+        w = s5 * s * (T(1) + q * (T(3) + q * T(35.0 / 12.0)));
+        dw = T(-14.0 / 3.0) * q * (T(1) + T(2.5) * q) * s5;
+    }
+}
+
+// Minimum-image separation, FP64 without contraction (bit-identical to the
+// plain expression xa - xb; if > L/2 subtract L; if < -L/2 add L).
+__device__ __forceinline__ double sep_d(double xa, double xb, int periodic, double L, double half)
+{
+    double d = __dsub_rn(xa, xb);
+    if (periodic) {
+        if (d > half) d = __dsub_rn(d, L);
+        else if (d < -half) d = __dadd_rn(d, L);
+    }
+    return d;
+}
+
+// r^2 = (dx dx + dy dy) + dz dz in FP64 without fused multiply-add
+__device__ __forceinline__ double r2_d(double dx, double dy, double dz)
+{
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// Separation from two-float positions: (hi_a - hi_b) + (lo_a - lo_b), then
+// the minimum image in FP32.
+__device__ __forceinline__ float sep_f(float ha, float la, float hb, float lb, int periodic,
+                                       float L, float half)
+{
+    float d = (ha - hb) + (la - lb);
+    if (periodic) {
+        if (d > half) d -= L;
+        else if (d < -half) d += L;
+    }
+    return d;
+}
+
+// ------------------------------------------------------------ launchers
+// tree.cu
+int tree_build(sph_ctx *ctx, sph_particles *p, cudaStream_t s);
+int tree_keys(sph_ctx *ctx, const sph_particles *p, uint64_t *keys_out, cudaStream_t s);
+int tree_sort(sph_ctx *ctx, int64_t n, const uint64_t *keys, const uint32_t *ids, uint32_t *perm,
+              cudaStream_t s);
+int tree_refit_h(sph_ctx *ctx, const sph_particles *p, cudaStream_t s);
+// scan.cu
+int scan_exclusive_i32(sph_ctx *ctx, const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
+int scan_exclusive_i64(sph_ctx *ctx, const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
+int scan_inclusive_max_i32(sph_ctx *ctx, const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
+size_t scan_tmp_bytes(int64_t n);
+// neighbors.cu
+int lists_build(sph_ctx *ctx, const sph_particles *p, int kind, cudaStream_t s);
+int neighbors_export(sph_ctx *ctx, const sph_particles *p, int kind, int64_t *counts,
+                     const int64_t *offsets, uint32_t *idx, cudaStream_t s);
+// density.cu
+int density_run(sph_ctx *ctx, sph_particles *p, const void *h_seed, sph_density_stats *st,
+                cudaStream_t s);
+int eos_run(sph_ctx *ctx, sph_particles *p, const void *u, cudaStream_t s);
+// forces.cu
+int forces_run(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, const void *vz,
+               sph_force_stats *st, cudaStream_t s);
+// integrate.cu
+int kick_drift(sph_ctx *ctx, sph_particles *p, double dt, cudaStream_t s);
+int predict(sph_ctx *ctx, sph_particles *p, double dt, cudaStream_t s);
+int kick(sph_ctx *ctx, sph_particles *p, double dt, cudaStream_t s);
+int totals_run(sph_ctx *ctx, const sph_particles *p, const void *vx, const void *vy,
+               const void *vz, const void *u, cudaStream_t s);
+int sync_counters(sph_ctx *ctx, cudaStream_t s);
+// hnet.cu
+int hnet_init(sph_ctx *ctx);
+int hnet_features(sph_ctx *ctx, const sph_particles *p, double dt, float *feats, cudaStream_t s);
+int hnet_infer(sph_ctx *ctx, const float *feats, int64_t nb, float *y, cudaStream_t s);
+int hnet_grad(sph_ctx *ctx, const float *feats, const float *target, int64_t nb, cudaStream_t s);
+int hnet_adam(sph_ctx *ctx, float lr, cudaStream_t s);
+int hnet_seed(sph_ctx *ctx, sph_particles *p, const float *y, void *h_seed, cudaStream_t s);
+int hnet_online(sph_ctx *ctx, const sph_particles *p, cudaStream_t s);

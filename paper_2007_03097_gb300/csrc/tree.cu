@@ -1,0 +1,645 @@
+// Tree build (Sec. 2.1, Tree topology): Morton keys with a leading 1 bit,
+// LSD radix sort of (key, index) with equal keys ordered by particle id,
+// in-place permutation of every particle array into key order, octree leaf
+// cells of at most leaf_size particles, target groups of at most 32
+// particles, and a binary radix tree over the leaves (Karras 2012) with
+// bounding boxes and maximal h for pruning the neighbour search.
+//
+// The paper builds a hashed octree by inserting particles one by one and
+// refining nodes.  Here the octree is implicit in the sorted keys: a leaf is
+// the shallowest key-prefix cell holding at most leaf_size particles, found
+// per particle from the levels at which neighbouring keys first differ.
+#include <cfloat>
+
+#include "sph_internal.cuh"
+
+namespace {
+
+// ------------------------------------------------------------------ domain
+__global__ void k_bbox_partial(const double *__restrict__ x, const double *__restrict__ y,
+                               const double *__restrict__ z, int64_t n, double *part)
+{
+    double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double c[3] = {x[i], y[i], z[i]};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) { mn[d] = fmin(mn[d], c[d]); mx[d] = fmax(mx[d], c[d]); }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[d] = fmin(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+            mx[d] = fmax(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+        }
+    }
+    __shared__ double s[32][6];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+        for (int d = 0; d < 3; ++d) { s[warp][d] = mn[d]; s[warp][3 + d] = mx[d]; }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double v = s[0][threadIdx.x];
+        for (int w = 1; w < nw; ++w)
+            v = threadIdx.x < 3 ? fmin(v, s[w][threadIdx.x]) : fmax(v, s[w][threadIdx.x]);
+        part[blockIdx.x * 6 + threadIdx.x] = v;
+    }
+}
+
+// Key domain: periodic box, or lo = bounding-box minimum and
+// L = (largest extent) * (1 + 2^-20) for an open set.
+__global__ void k_domain(const double *part, int nparts, int periodic, double blx, double bly,
+                         double blz, double boxL, DevCounters *cnt)
+{
+    if (threadIdx.x != 0) return;
+    if (periodic) {
+        cnt->dom[0] = blx; cnt->dom[1] = bly; cnt->dom[2] = blz; cnt->dom[3] = boxL;
+        return;
+    }
+    double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    for (int b = 0; b < nparts; ++b)
+        for (int d = 0; d < 3; ++d) {
+            mn[d] = fmin(mn[d], part[b * 6 + d]);
+            mx[d] = fmax(mx[d], part[b * 6 + 3 + d]);
+        }
+    double ext = fmax(fmax(__dsub_rn(mx[0], mn[0]), __dsub_rn(mx[1], mn[1])), __dsub_rn(mx[2], mn[2]));
+    double L = __dmul_rn(ext, 1.0 + 0x1p-20);
+    if (!(L > 0.0)) L = 1.0;
+    cnt->dom[0] = mn[0]; cnt->dom[1] = mn[1]; cnt->dom[2] = mn[2]; cnt->dom[3] = L;
+}
+
+// ------------------------------------------------------------------ keys
+__device__ __forceinline__ uint64_t spread3(uint64_t v)
+{
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+__device__ __forceinline__ uint64_t cell_of(double c, double lo, double scale)
+{
+    double f = floor(__dmul_rn(__dsub_rn(c, lo), scale));
+    if (!(f >= 0.0)) f = 0.0;
+    if (f > 2097151.0) f = 2097151.0;
+    return (uint64_t)f;
+}
+
+template <typename T>
+__global__ void k_keys(const double *__restrict__ x, const double *__restrict__ y,
+                       const double *__restrict__ z, const T *__restrict__ h,
+                       const T *__restrict__ m, int64_t n, DevCounters *cnt,
+                       uint64_t *__restrict__ keys, uint32_t *__restrict__ vals)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double lx = cnt->dom[0], ly = cnt->dom[1], lz = cnt->dom[2];
+    const double scale = 2097152.0 / cnt->dom[3];
+    const double xi = x[i], yi = y[i], zi = z[i];
+    bool ok = isfinite(xi) && isfinite(yi) && isfinite(zi);
+    if (h) ok = ok && isfinite((double)h[i]) && (double)h[i] > 0.0;
+    if (m) ok = ok && isfinite((double)m[i]);
+    if (!ok) atomicOr(&cnt->err, ERRB_NONFINITE);
+    uint64_t key = spread3(cell_of(xi, lx, scale)) | (spread3(cell_of(yi, ly, scale)) << 1) |
+                   (spread3(cell_of(zi, lz, scale)) << 2) | (1ull << 63);
+    keys[i] = key;
+    if (vals) vals[i] = (uint32_t)i;
+}
+
+// ------------------------------------------------------------------ radix sort
+constexpr int RS_THREADS = 256;
+constexpr int RS_ROUNDS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;   // 4096 keys per tile
+constexpr int RS_BINS = 256;
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *__restrict__ keys, int64_t n,
+                                                        int shift, uint32_t *__restrict__ hist,
+                                                        int ntiles)
+{
+    __shared__ uint32_t hs[RS_BINS];
+    hs[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+#pragma unroll 4
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        int64_t i = base + r * RS_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&hs[(keys[i] >> shift) & 0xff], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = hs[threadIdx.x];
+}
+
+// Stable scatter: elements keep their input order within a digit.  Within
+// a tile, each round of 256 consecutive keys is ranked per warp with
+// __match_any_sync and per digit across the 8 warps in shared memory.
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__restrict__ kin,
+                                                           const uint32_t *__restrict__ vin,
+                                                           uint64_t *__restrict__ kout,
+                                                           uint32_t *__restrict__ vout, int64_t n,
+                                                           int shift, const uint32_t *__restrict__ hist,
+                                                           int ntiles)
+{
+    __shared__ uint32_t run[RS_BINS];
+    __shared__ uint32_t wc[RS_THREADS / 32][RS_BINS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    run[tid] = hist[(int64_t)tid * ntiles + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < RS_THREADS / 32; ++w) wc[w][tid] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        const int64_t i = base + r * RS_THREADS + tid;
+        const bool valid = i < n;
+        uint64_t key = valid ? kin[i] : 0ull;
+        uint32_t val = valid ? vin[i] : 0u;
+        const uint32_t digit = valid ? (uint32_t)((key >> shift) & 0xff) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, digit);
+        const uint32_t rank = __popc(peers & lt);
+        if (valid && lane == __ffs(peers) - 1) wc[warp][digit] = __popc(peers);
+        __syncthreads();
+        uint32_t acc = 0;
+#pragma unroll
+        for (int w = 0; w < RS_THREADS / 32; ++w) {
+            uint32_t c = wc[w][tid];
+            wc[w][tid] = acc;
+            acc += c;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint32_t pos = run[digit] + wc[warp][digit] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+        run[tid] += acc;
+#pragma unroll
+        for (int w = 0; w < RS_THREADS / 32; ++w) wc[w][tid] = 0;
+        __syncthreads();
+    }
+}
+
+// Runs of equal keys are ordered by particle id (Sec. 2.1: ids resolve
+// equal keys).  Runs are tiny in practice; longer than 64 is flagged.
+__global__ void k_fix_ties(const uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                           const uint32_t *__restrict__ ids, int64_t n, DevCounters *cnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t k = keys[i];
+    if (i > 0 && keys[i - 1] == k) return;
+    if (i + 1 >= n || keys[i + 1] != k) return;
+    int64_t e = i + 1;
+    while (e < n && keys[e] == k && e - i <= 64) ++e;
+    if (e - i > 64) { atomicOr(&cnt->err, ERRB_TIE_RUN); return; }
+    for (int64_t a = i + 1; a < e; ++a) {
+        uint32_t v = vals[a];
+        uint32_t idv = ids ? ids[v] : v;
+        int64_t b = a - 1;
+        while (b >= i && (ids ? ids[vals[b]] : vals[b]) > idv) { vals[b + 1] = vals[b]; --b; }
+        vals[b + 1] = v;
+    }
+}
+
+// ------------------------------------------------------------------ gather
+constexpr int MAX_FIELDS = 24;
+struct FieldTable {
+    const void *src[MAX_FIELDS];
+    void *dst[MAX_FIELDS];
+    int size[MAX_FIELDS];
+    int nf;
+};
+
+// Permute every field: dst_f[i] = src_f[perm[i]] into scratch, and form the
+// two-float split (hi = float(x), lo = float(x - hi)) of the positions.
+__global__ void k_gather(FieldTable t, const uint32_t *__restrict__ perm, int64_t n,
+                         float *xh, float *xl, float *yh, float *yl, float *zh, float *zl)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t p = perm[i];
+    for (int f = 0; f < t.nf; ++f) {
+        if (t.size[f] == 8) {
+            double v = ((const double *)t.src[f])[p];
+            ((double *)t.dst[f])[i] = v;
+            if (f < 3) {
+                float hi = (float)v;
+                float lo = (float)(v - (double)hi);
+                float *H = f == 0 ? xh : f == 1 ? yh : zh;
+                float *Lo = f == 0 ? xl : f == 1 ? yl : zl;
+                H[i] = hi;
+                Lo[i] = lo;
+            }
+        } else {
+            ((uint32_t *)t.dst[f])[i] = ((const uint32_t *)t.src[f])[p];
+        }
+    }
+}
+
+__global__ void k_copy_back(FieldTable t, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int f = 0; f < t.nf; ++f) {
+        if (t.size[f] == 8) ((double *)t.src[f])[i] = ((const double *)t.dst[f])[i];
+        else ((uint32_t *)t.src[f])[i] = ((const uint32_t *)t.dst[f])[i];
+    }
+}
+
+// ------------------------------------------------------------------ leaves and groups
+// dlev[i]: octree level at which key i first differs from key i-1
+// (1 = top split, 21 = finest; 22 = identical; 0 for i = 0).
+__global__ void k_dlev(const uint64_t *__restrict__ keys, int64_t n, uint8_t *__restrict__ dlev)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (i == 0) { dlev[0] = 0; return; }
+    const uint64_t x = keys[i - 1] ^ keys[i];
+    dlev[i] = x ? (uint8_t)(21 - (63 - __clzll((long long)x)) / 3) : (uint8_t)22;
+}
+
+// Leaf level of particle i: the shallowest level l whose cell around i holds
+// at most S particles.  With B(t) = min dlev[i-t..i] and F(t) = min
+// dlev[i+1..i+t] (0 outside [0, n)), the run at level l has at most S
+// particles iff max(B(tb), F(S - tb)) <= l for some tb in [0, S).
+__global__ void k_leaf_level(const uint8_t *__restrict__ dlev, int64_t n, int S,
+                             uint8_t *__restrict__ plev, DevCounters *cnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint8_t F[33];
+    uint8_t m = 255;
+    for (int t = 1; t <= S; ++t) {
+        int64_t j = i + t;
+        uint8_t d = j < n ? dlev[j] : 0;
+        m = d < m ? d : m;
+        F[t] = m;
+    }
+    uint8_t B = 255, best = 255;
+    for (int tb = 0; tb < S; ++tb) {
+        int64_t j = i - tb;
+        uint8_t d = j >= 0 ? dlev[j] : 0;
+        B = d < B ? d : B;
+        uint8_t c = B > F[S - tb] ? B : F[S - tb];
+        best = c < best ? c : best;
+    }
+    if (best > 21) { atomicOr(&cnt->err, ERRB_LEAF_DEGENERATE); best = 21; }
+    plev[i] = best;
+}
+
+// leaf start flag (itmp0) and sibling-segment start index (itmp1, -1 if none)
+__global__ void k_mark(const uint8_t *__restrict__ dlev, const uint8_t *__restrict__ plev, int64_t n,
+                       int32_t *__restrict__ leaf_start, int32_t *__restrict__ seg_val)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int L = plev[i], d = dlev[i];
+    const bool ls = (i == 0) || d <= L;
+    const bool seg = ls && ((i == 0) || d <= L - 1 || plev[i - 1] != L);
+    leaf_start[i] = ls ? 1 : 0;
+    seg_val[i] = seg ? (int32_t)i : -1;
+}
+
+// group start: a sibling-segment start, or every 32nd particle inside one
+__global__ void k_mark_groups(int32_t *__restrict__ segbeg_to_flag, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t sb = segbeg_to_flag[i];
+    segbeg_to_flag[i] = (((int32_t)i - sb) % SPH_WARP) == 0 ? 1 : 0;
+}
+
+__global__ void k_emit(const int32_t *__restrict__ leaf_start, const int32_t *__restrict__ grp_start,
+                       const int32_t *__restrict__ leaf_idx, const int32_t *__restrict__ grp_idx,
+                       const uint8_t *__restrict__ plev, int64_t n, int32_t *__restrict__ leaf_begin,
+                       int32_t *__restrict__ leaf_level, int32_t *__restrict__ group_begin,
+                       DevCounters *cnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (leaf_start[i]) { leaf_begin[leaf_idx[i]] = (int32_t)i; leaf_level[leaf_idx[i]] = plev[i]; }
+    if (grp_start[i]) group_begin[grp_idx[i]] = (int32_t)i;
+    if (i == n - 1) {
+        const int32_t nl = leaf_idx[i] + leaf_start[i];
+        const int32_t ng = grp_idx[i] + grp_start[i];
+        leaf_begin[nl] = (int32_t)n;
+        group_begin[ng] = (int32_t)n;
+        cnt->n_leaves = nl;
+        cnt->n_groups = ng;
+    }
+}
+
+// Bounding box (outward-rounded to float) and maximal h of each range
+// [begin[r], begin[r+1]) of at most 32 particles; one warp per range.
+template <typename T>
+__global__ void k_range_boxes(const int32_t *__restrict__ begin, int nr, const double *__restrict__ x,
+                              const double *__restrict__ y, const double *__restrict__ z,
+                              const T *__restrict__ h, float4 *__restrict__ lo4, float4 *__restrict__ hi4)
+{
+    const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= nr) return;
+    const int b = begin[r], e = begin[r + 1];
+    double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    double hm = 0.0;
+    for (int i = b + lane; i < e; i += 32) {
+        double c[3] = {x[i], y[i], z[i]};
+        for (int d = 0; d < 3; ++d) { mn[d] = fmin(mn[d], c[d]); mx[d] = fmax(mx[d], c[d]); }
+        hm = fmax(hm, (double)h[i]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        for (int d = 0; d < 3; ++d) {
+            mn[d] = fmin(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+            mx[d] = fmax(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+        }
+        hm = fmax(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+    }
+    if (lane == 0) {
+        lo4[r] = make_float4(__double2float_rd(mn[0]), __double2float_rd(mn[1]), __double2float_rd(mn[2]),
+                             __double2float_ru(hm));
+        hi4[r] = make_float4(__double2float_ru(mx[0]), __double2float_ru(mx[1]), __double2float_ru(mx[2]), 0.f);
+    }
+}
+
+// ------------------------------------------------------------------ radix tree over leaves
+__device__ __forceinline__ int delta_key(const uint64_t *__restrict__ keys, const int32_t *__restrict__ lb,
+                                         int nl, int i, int j)
+{
+    if (j < 0 || j >= nl) return -1;
+    uint64_t a = keys[lb[i]], b = keys[lb[j]];
+    if (a == b) return 64 + __clz(i ^ j);
+    return __clzll((long long)(a ^ b));
+}
+
+// Karras (2012) construction: internal node i covers a leaf range whose
+// split is the first differing bit; children with index bit 31 are leaves.
+__global__ void k_radix_tree(const uint64_t *__restrict__ keys, const int32_t *__restrict__ lb, int nl,
+                             int32_t *__restrict__ child, int32_t *__restrict__ node_parent,
+                             int32_t *__restrict__ leaf_parent)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nl - 1) return;
+    const int d = (delta_key(keys, lb, nl, i, i + 1) - delta_key(keys, lb, nl, i, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = delta_key(keys, lb, nl, i, i - d);
+    int lmax = 2;
+    while (delta_key(keys, lb, nl, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta_key(keys, lb, nl, i, i + (l + t) * d) > dmin) l += t;
+    const int j = i + l * d;
+    const int dnode = delta_key(keys, lb, nl, i, j);
+    int s = 0;
+    int t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta_key(keys, lb, nl, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    const int gamma = i + s * d + (d < 0 ? -1 : 0);
+    const int lo = i < j ? i : j, hi = i < j ? j : i;
+    int c0, c1;
+    if (lo == gamma) { c0 = gamma | (int)0x80000000; leaf_parent[gamma] = i; }
+    else { c0 = gamma; node_parent[gamma] = i; }
+    if (hi == gamma + 1) { c1 = (gamma + 1) | (int)0x80000000; leaf_parent[gamma + 1] = i; }
+    else { c1 = gamma + 1; node_parent[gamma + 1] = i; }
+    child[2 * i] = c0;
+    child[2 * i + 1] = c1;
+    if (i == 0) node_parent[0] = -1;
+}
+
+__device__ __forceinline__ void load_box(int c, const float4 *leaf_lo, const float4 *leaf_hi,
+                                         const float4 *node_lo, const float4 *node_hi, float4 &lo,
+                                         float4 &hi)
+{
+    if (c < 0) {
+        const int id = c & 0x7fffffff;
+        lo = __ldcg(leaf_lo + id);
+        hi = __ldcg(leaf_hi + id);
+    } else {
+        lo = __ldcg(node_lo + c);
+        hi = __ldcg(node_hi + c);
+    }
+}
+
+// Bottom-up boxes: the second child to arrive at a node merges both.
+__global__ void k_refit(int nl, const int32_t *__restrict__ child, const int32_t *__restrict__ node_parent,
+                        const int32_t *__restrict__ leaf_parent, unsigned *__restrict__ visit,
+                        const float4 *__restrict__ leaf_lo, const float4 *__restrict__ leaf_hi,
+                        float4 *node_lo, float4 *node_hi)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nl) return;
+    int node = leaf_parent[l];
+    for (int depth = 0; node >= 0 && depth < 4096; ++depth) {
+        __threadfence();
+        if (atomicAdd(&visit[node], 1u) == 0) return;
+        __threadfence();
+        float4 alo, ahi, blo, bhi;
+        load_box(child[2 * node], leaf_lo, leaf_hi, node_lo, node_hi, alo, ahi);
+        load_box(child[2 * node + 1], leaf_lo, leaf_hi, node_lo, node_hi, blo, bhi);
+        float4 lo = make_float4(fminf(alo.x, blo.x), fminf(alo.y, blo.y), fminf(alo.z, blo.z), fmaxf(alo.w, blo.w));
+        float4 hi = make_float4(fmaxf(ahi.x, bhi.x), fmaxf(ahi.y, bhi.y), fmaxf(ahi.z, bhi.z), 0.f);
+        __stcg(node_lo + node, lo);
+        __stcg(node_hi + node, hi);
+        node = node_parent[node];
+    }
+}
+
+template <typename T>
+int boxes_and_refit(sph_ctx *ctx, const sph_particles *p, cudaStream_t s)
+{
+    const T *h = (const T *)p->h;
+    const int nl = (int)ctx->n_leaves, ng = (int)ctx->n_groups;
+    k_range_boxes<T><<<grid_for((int64_t)nl * 32, 256), 256, 0, s>>>(ctx->leaf_begin, nl, p->x, p->y, p->z, h,
+                                                                     ctx->leaf_lo, ctx->leaf_hi);
+    SPH_CHECK_LAUNCH();
+    k_range_boxes<T><<<grid_for((int64_t)ng * 32, 256), 256, 0, s>>>(ctx->group_begin, ng, p->x, p->y, p->z, h,
+                                                                     ctx->group_lo, ctx->group_hi);
+    SPH_CHECK_LAUNCH();
+    if (nl > 1) {
+        SPH_CUDA(cudaMemsetAsync(ctx->node_visit, 0, sizeof(unsigned) * (size_t)(nl - 1), s));
+        k_refit<<<grid_for(nl, 256), 256, 0, s>>>(nl, ctx->node_child, ctx->node_parent, ctx->leaf_parent,
+                                                  ctx->node_visit, ctx->leaf_lo, ctx->leaf_hi, ctx->node_lo,
+                                                  ctx->node_hi);
+        SPH_CHECK_LAUNCH();
+    }
+    return SPH_OK;
+}
+
+template <typename T>
+void add_field(FieldTable &t, unsigned char *&buf, int64_t nmax, const void *ptr)
+{
+    if (!ptr) return;
+    t.src[t.nf] = ptr;
+    t.dst[t.nf] = buf;
+    t.size[t.nf] = (int)sizeof(T);
+    buf += ((size_t)nmax * sizeof(T) + 255) & ~(size_t)255;
+    ++t.nf;
+}
+
+template <typename T>
+FieldTable make_table(sph_ctx *ctx, const sph_particles *p)
+{
+    FieldTable t{};
+    unsigned char *buf = ctx->gbuf;
+    const int64_t nm = ctx->n_max;
+    add_field<double>(t, buf, nm, p->x);
+    add_field<double>(t, buf, nm, p->y);
+    add_field<double>(t, buf, nm, p->z);
+    const void *tf[] = {p->vx, p->vy, p->vz, p->m, p->h, p->u, p->hprev, p->rho, p->omega, p->P, p->c,
+                        p->ax, p->ay, p->az, p->dudt, p->divv, p->vsig};
+    for (const void *f : tf) add_field<T>(t, buf, nm, f);
+    add_field<int32_t>(t, buf, nm, p->nnb);
+    add_field<uint32_t>(t, buf, nm, p->id);
+    return t;
+}
+
+int radix_sort(sph_ctx *ctx, int64_t n, cudaStream_t s)
+{
+    const int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
+    uint64_t *ka = ctx->key_a, *kb = ctx->key_b;
+    uint32_t *va = ctx->val_a, *vb = ctx->val_b;
+    for (int pass = 0; pass < 8; ++pass) {
+        const int shift = 8 * pass;
+        k_rs_hist<<<ntiles, RS_THREADS, 0, s>>>(ka, n, shift, ctx->hist, ntiles);
+        SPH_CHECK_LAUNCH();
+        SPH_TRY(scan_exclusive_i32(ctx, (const int32_t *)ctx->hist, (int32_t *)ctx->hist,
+                                   (int64_t)RS_BINS * ntiles, s));
+        k_rs_scatter<<<ntiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, ctx->hist, ntiles);
+        SPH_CHECK_LAUNCH();
+        uint64_t *tk = ka; ka = kb; kb = tk;
+        uint32_t *tv = va; va = vb; vb = tv;
+    }
+    return SPH_OK;   // 8 passes: the result is back in key_a / val_a
+}
+
+int compute_domain(sph_ctx *ctx, const sph_particles *p, cudaStream_t s)
+{
+    const sph_params &q = ctx->prm;
+    if (q.periodic) {
+        k_domain<<<1, 32, 0, s>>>(nullptr, 0, 1, q.box_lo[0], q.box_lo[1], q.box_lo[2],
+                                  q.box_hi[0] - q.box_lo[0], ctx->dcnt);
+    } else {
+        const int nb = ctx->red_blocks;
+        k_bbox_partial<<<nb, 256, 0, s>>>(p->x, p->y, p->z, p->n, ctx->red);
+        SPH_CHECK_LAUNCH();
+        k_domain<<<1, 32, 0, s>>>(ctx->red, nb, 0, 0, 0, 0, 0, ctx->dcnt);
+    }
+    SPH_CHECK_LAUNCH();
+    return SPH_OK;
+}
+
+template <typename T>
+int keys_impl(sph_ctx *ctx, const sph_particles *p, uint64_t *keys, uint32_t *vals, cudaStream_t s)
+{
+    SPH_TRY(compute_domain(ctx, p, s));
+    k_keys<T><<<grid_for(p->n, 256), 256, 0, s>>>(p->x, p->y, p->z, (const T *)p->h, (const T *)p->m, p->n,
+                                                  ctx->dcnt, keys, vals);
+    SPH_CHECK_LAUNCH();
+    return SPH_OK;
+}
+
+template <typename T>
+int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
+{
+    const int64_t n = p->n;
+    ctx->tree_valid = false;
+    SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->err, 0, sizeof(uint32_t), s));
+    SPH_TRY(keys_impl<T>(ctx, p, ctx->key_a, ctx->val_a, s));
+    SPH_TRY(radix_sort(ctx, n, s));
+    k_fix_ties<<<grid_for(n, 256), 256, 0, s>>>(ctx->key_a, ctx->val_a, p->id, n, ctx->dcnt);
+    SPH_CHECK_LAUNCH();
+    // permute every particle array into key order
+    FieldTable t = make_table<T>(ctx, p);
+    k_gather<<<grid_for(n, 256), 256, 0, s>>>(t, ctx->val_a, n, ctx->xh, ctx->xl, ctx->yh, ctx->yl, ctx->zh,
+                                              ctx->zl);
+    SPH_CHECK_LAUNCH();
+    k_copy_back<<<grid_for(n, 256), 256, 0, s>>>(t, n);
+    SPH_CHECK_LAUNCH();
+    // octree leaves and target groups
+    k_dlev<<<grid_for(n, 256), 256, 0, s>>>(ctx->key_a, n, ctx->dlev);
+    SPH_CHECK_LAUNCH();
+    k_leaf_level<<<grid_for(n, 128), 128, 0, s>>>(ctx->dlev, n, ctx->prm.leaf_size, ctx->plev, ctx->dcnt);
+    SPH_CHECK_LAUNCH();
+    int32_t *ls = ctx->itmp0, *gs = ctx->itmp1;
+    int32_t *lidx = ctx->itmp2, *gidx = ctx->itmp3;
+    k_mark<<<grid_for(n, 256), 256, 0, s>>>(ctx->dlev, ctx->plev, n, ls, gs);
+    SPH_CHECK_LAUNCH();
+    SPH_TRY(scan_inclusive_max_i32(ctx, gs, gs, n, s));
+    k_mark_groups<<<grid_for(n, 256), 256, 0, s>>>(gs, n);
+    SPH_CHECK_LAUNCH();
+    SPH_TRY(scan_exclusive_i32(ctx, ls, lidx, n, s));
+    SPH_TRY(scan_exclusive_i32(ctx, gs, gidx, n, s));
+    k_emit<<<grid_for(n, 256), 256, 0, s>>>(ls, gs, lidx, gidx, ctx->plev, n, ctx->leaf_begin, ctx->leaf_level,
+                                            ctx->group_begin, ctx->dcnt);
+    SPH_CHECK_LAUNCH();
+    SPH_TRY(sync_counters(ctx, s));
+    const uint32_t err = ctx->hcnt->err;
+    for (int d = 0; d < 4; ++d) ctx->dom[d] = ctx->hcnt->dom[d];
+    if (err & ERRB_NONFINITE)
+        return sph_fail(ctx, SPH_ERR_NONFINITE, "sph_build_tree: NaN/Inf position, mass or h (or h <= 0)");
+    if (err & (ERRB_LEAF_DEGENERATE | ERRB_TIE_RUN))
+        return sph_fail(ctx, SPH_ERR_CAPACITY,
+                        "sph_build_tree: more than leaf_size particles share one 63-bit Morton key");
+    ctx->n = n;
+    ctx->n_leaves = ctx->hcnt->n_leaves;
+    ctx->n_groups = ctx->hcnt->n_groups;
+    const int nl = (int)ctx->n_leaves;
+    if (nl > 1) {
+        k_radix_tree<<<grid_for(nl - 1, 256), 256, 0, s>>>(ctx->key_a, ctx->leaf_begin, nl, ctx->node_child,
+                                                           ctx->node_parent, ctx->leaf_parent);
+        SPH_CHECK_LAUNCH();
+    }
+    SPH_TRY(boxes_and_refit<T>(ctx, p, s));
+    ctx->tree_valid = true;
+    return SPH_OK;
+}
+
+}  // namespace
+
+int tree_build(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
+{
+    return ctx->fp64 ? build_impl<double>(ctx, p, s) : build_impl<float>(ctx, p, s);
+}
+
+// Recompute boxes and maximal h after h changed (positions unchanged).
+int tree_refit_h(sph_ctx *ctx, const sph_particles *p, cudaStream_t s)
+{
+    return ctx->fp64 ? boxes_and_refit<double>(ctx, p, s) : boxes_and_refit<float>(ctx, p, s);
+}
+
+int tree_keys(sph_ctx *ctx, const sph_particles *p, uint64_t *keys_out, cudaStream_t s)
+{
+    SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->err, 0, sizeof(uint32_t), s));
+    SPH_TRY(ctx->fp64 ? keys_impl<double>(ctx, p, keys_out, nullptr, s) : keys_impl<float>(ctx, p, keys_out, nullptr, s));
+    SPH_TRY(sync_counters(ctx, s));
+    for (int d = 0; d < 4; ++d) ctx->dom[d] = ctx->hcnt->dom[d];
+    if (ctx->hcnt->err & ERRB_NONFINITE)
+        return sph_fail(ctx, SPH_ERR_NONFINITE, "sph_morton_keys: NaN/Inf position, mass or h");
+    return SPH_OK;
+}
+
+__global__ void k_iota(uint32_t *v, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = (uint32_t)i;
+}
+
+int tree_sort(sph_ctx *ctx, int64_t n, const uint64_t *keys, const uint32_t *ids, uint32_t *perm,
+              cudaStream_t s)
+{
+    SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->err, 0, sizeof(uint32_t), s));
+    SPH_CUDA(cudaMemcpyAsync(ctx->key_a, keys, sizeof(uint64_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    k_iota<<<grid_for(n, 256), 256, 0, s>>>(ctx->val_a, n);
+    SPH_CHECK_LAUNCH();
+    SPH_TRY(radix_sort(ctx, n, s));
+    k_fix_ties<<<grid_for(n, 256), 256, 0, s>>>(ctx->key_a, ctx->val_a, ids, n, ctx->dcnt);
+    SPH_CHECK_LAUNCH();
+    SPH_CUDA(cudaMemcpyAsync(perm, ctx->val_a, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    SPH_TRY(sync_counters(ctx, s));
+    if (ctx->hcnt->err & ERRB_TIE_RUN)
+        return sph_fail(ctx, SPH_ERR_CAPACITY, "sph_sort_keys: a run of more than 64 equal keys");
+    return SPH_OK;
+}

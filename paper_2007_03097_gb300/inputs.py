@@ -176,7 +176,7 @@ def polytrope(n: int = 1 << 20, seed: int = 3001, precision: str = "mixed") -> W
     K = 2.0 / math.pi
     m = 1.0 / n
     eta = 1.2
-    rho_s = np.maximum(rho, 1e-3 * rho.max())
+    rho_s = np.maximum(rho, 0.05 * (math.pi / 4.0))   # floor: a seed, not the SPH density
     h = eta * (m / rho_s) ** (1.0 / 3.0)
     zeros = np.zeros(n)
     params = _base_params(kernel=WC2, periodic=False, gamma=2.0, eta=eta, h_min=1e-6, h_max=20.0,

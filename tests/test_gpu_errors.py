@@ -1,0 +1,99 @@
+"""Failure handling of the C ABI on the GPU, all made on the host side: bad
+arguments, non-finite inputs, exhausted capacity, an iteration cap and h
+bounds return their status codes and leave the context usable."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import need_gpu
+from paper_2007_03097_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def test_call_order_and_sizes():
+    B = need_gpu()
+    w = inputs.lattice(6)
+    ctx = B.Context(w.params, w.n)
+    p = B.Particles.from_workload(w, fp64=True)
+    with pytest.raises(B.SphError) as e:
+        B.sph_density(ctx, p)
+    assert e.value.code == B.SPH_ERR_STATE
+    big = B.Particles.from_workload(inputs.lattice(7), fp64=True)
+    with pytest.raises(B.SphError) as e:
+        B.sph_build_tree(ctx, big)
+    assert e.value.code == B.SPH_ERR_ARG
+
+
+def test_nonfinite_input_is_reported_and_context_recovers():
+    B = need_gpu()
+    w = inputs.lattice(8)
+    ctx = B.Context(w.params, w.n)
+    p = B.Particles.from_workload(w, fp64=True)
+    p.x[17] = float("nan")
+    with pytest.raises(B.SphError) as e:
+        B.sph_build_tree(ctx, p)
+    assert e.value.code == B.SPH_ERR_NONFINITE
+    p2 = B.Particles.from_workload(w, fp64=True)
+    B.sph_build_tree(ctx, p2)
+    B.sph_density(ctx, p2)
+    assert torch.isfinite(p2.rho).all()
+
+
+def test_list_capacity_exhausted():
+    B = need_gpu()
+    w = inputs.lattice(10)
+    w.params["nb_capacity"] = 1000
+    ctx = B.Context(w.params, w.n)
+    p = B.Particles.from_workload(w, fp64=True)
+    B.sph_build_tree(ctx, p)
+    with pytest.raises(B.SphError) as e:
+        B.sph_density(ctx, p)
+    assert e.value.code == B.SPH_ERR_CAPACITY
+
+
+def test_iteration_cap_and_h_bounds():
+    B = need_gpu()
+    w = inputs.sedov(10)
+    w.params["max_sweeps"] = 2
+    w.params["nb_capacity"] = 600 * w.n
+    ctx = B.Context(w.params, w.n)
+    p = B.Particles.from_workload(w, fp64=True)
+    p.h.mul_(1.3)
+    B.sph_build_tree(ctx, p)
+    with pytest.raises(B.SphError) as e:
+        B.sph_density(ctx, p)
+    assert e.value.code == B.SPH_ERR_NOT_CONVERGED
+    w2 = inputs.sedov(10)
+    w2.params["h_max"] = 0.5 * w2.h[0]
+    ctx2 = B.Context(w2.params, w2.n)
+    p2 = B.Particles.from_workload(w2, fp64=True)
+    p2.h.mul_(0.4)
+    B.sph_build_tree(ctx2, p2)
+    st = B.sph_density(ctx2, p2)                  # H_BOUNDS is allowed through by default
+    assert st["status"] == B.SPH_ERR_H_BOUNDS and st["n_hbounds"] > 0
+    assert torch.all(p2.h <= 0.5 * w2.h[0])
+
+
+def test_degenerate_positions_rejected():
+    B = need_gpu()
+    w = inputs.lattice(4)
+    w.x[:] = 0.5; w.y[:] = 0.5; w.z[:] = 0.5          # 64 particles on one point
+    ctx = B.Context(w.params, w.n)
+    p = B.Particles.from_workload(w, fp64=True)
+    with pytest.raises(B.SphError) as e:
+        B.sph_build_tree(ctx, p)
+    assert e.value.code == B.SPH_ERR_CAPACITY
+
+
+def test_single_particle():
+    B = need_gpu()
+    w = inputs.lattice(1, jitter=0.0, h_factor=0.2)
+    ctx = B.Context(w.params, 1)
+    p = B.Particles.from_workload(w, fp64=True)
+    B.sph_build_tree(ctx, p)
+    B.sph_density(ctx, p)
+    B.sph_forces(ctx, p)
+    assert p.nnb.item() == 0
+    assert p.rho.item() == pytest.approx(w.m[0] / (np.pi * w.h[0] ** 3), rel=1e-14)
+    assert p.ax.item() == 0.0

@@ -1,0 +1,96 @@
+"""The h-predictor network on the GPU against the FP64 oracle network at the
+same BF16-rounded weights: inference, loss gradient (FP32 accumulation) and
+the Adam update; features against their definition."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_helpers import need_gpu
+from paper_2007_03097_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(n=4096):
+    B = need_gpu()
+    return B, B.Context({}, n)
+
+
+def _theta(seed=0):
+    rng = np.random.default_rng(seed)
+    th = rng.normal(scale=0.25, size=oracle.HNET_NPARAM).astype(np.float32)
+    return th
+
+
+def test_inference_matches_oracle():
+    B, ctx = _ctx()
+    th = _theta()
+    B.sph_hnet_set_weights(ctx, th)
+    X = np.random.default_rng(1).normal(size=(3001, 5)).astype(np.float32)
+    X[5, 3] = 0.0
+    y = B.sph_hnet_infer(ctx, torch.from_numpy(X).cuda()).cpu().numpy()
+    ref = oracle.hnet_predict(oracle.bf16_round(th), X.astype(np.float64))
+    assert y[5] == 0.0
+    assert np.max(np.abs(y - ref)) < 2e-5 * max(1.0, np.abs(ref).max())
+    assert np.array_equal(B.sph_hnet_get_weights(ctx), th)
+
+
+@pytest.mark.parametrize("nb", [1, 63, 64, 1000, 20001])
+def test_gradient_matches_oracle(nb):
+    B, ctx = _ctx(max(nb, 64))
+    th = _theta(2)
+    B.sph_hnet_set_weights(ctx, th)
+    rng = np.random.default_rng(nb)
+    X = rng.normal(size=(nb, 5)).astype(np.float32)
+    t = rng.normal(scale=0.1, size=nb).astype(np.float32)
+    loss, g = B.sph_hnet_grad(ctx, torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda())
+    rl, rg = oracle.hnet_loss_grad(oracle.bf16_round(th), X.astype(np.float64), t.astype(np.float64))
+    assert loss == pytest.approx(rl, rel=1e-4)
+    assert np.max(np.abs(g - rg)) < 1e-4 * np.abs(rg).max()
+
+
+def test_adam_step_matches_oracle():
+    B, ctx = _ctx()
+    th = _theta(3)
+    B.sph_hnet_set_weights(ctx, th)
+    rng = np.random.default_rng(7)
+    X = rng.normal(size=(512, 5)).astype(np.float32)
+    t = rng.normal(scale=0.1, size=512).astype(np.float32)
+    Xt, tt = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
+    _, g = B.sph_hnet_grad(ctx, Xt, tt)
+    B.sph_hnet_train_step(ctx, Xt, tt, 1e-3)
+    new = B.sph_hnet_get_weights(ctx)
+    ref, _, _ = oracle.adam_update(th.astype(np.float64), g.astype(np.float64), np.zeros(th.size),
+                                   np.zeros(th.size), 1, 1e-3)
+    assert np.max(np.abs(new - ref)) < 1e-6
+
+
+def test_training_reduces_loss():
+    B, ctx = _ctx(8192)
+    rng = np.random.default_rng(8)
+    th = (rng.normal(size=oracle.HNET_NPARAM) * 0.1).astype(np.float32)
+    B.sph_hnet_set_weights(ctx, th)
+    X = rng.normal(size=(8192, 5)).astype(np.float32)
+    t = (X[:, 3] * (0.33 - 0.1 * X[:, 4] + 0.05 * np.tanh(X[:, 0]))).astype(np.float32)
+    Xt, tt = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
+    first = B.sph_hnet_train_step(ctx, Xt, tt, 3e-3)
+    for _ in range(300):
+        last = B.sph_hnet_train_step(ctx, Xt, tt, 3e-3)
+    assert last < 0.05 * first
+
+
+def test_features_match_definition():
+    B = need_gpu()
+    w = inputs.sedov(10)
+    ctx = B.Context(w.params, w.n)
+    p = B.Particles.from_workload(w, fp64=True)
+    B.sph_build_tree(ctx, p)
+    B.sph_density(ctx, p)
+    B.sph_forces(ctx, p)
+    p.hprev.copy_(p.h * 0.99)
+    dt = 1e-3
+    f = B.sph_hnet_features(ctx, p, dt).cpu().numpy()
+    g = p.numpy()
+    ref = oracle.hnet_features(g["h"], g["hprev"], g["nnb"], g["rho"], g["m"], g["divv"], dt, w.params["eta"], 1.0)
+    assert np.max(np.abs(f - ref)) < 1e-5
