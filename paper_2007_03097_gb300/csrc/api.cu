@@ -119,6 +119,8 @@ int allocate(sph_ctx *c, int64_t N)
     SPH_TRY(alloc(c, &c->node_hi, N));
     float **split[] = {&c->xh, &c->xl, &c->yh, &c->yl, &c->zh, &c->zl};
     for (float **s : split) SPH_TRY(alloc(c, s, N + 32));
+    float4 **packs[] = {&c->srcA, &c->srcB, &c->srcC, &c->srcD, &c->srcE, &c->srcF};
+    for (float4 **s : packs) SPH_TRY(alloc(c, s, N));
     c->nbl_cap = c->prm.nb_capacity > 0 ? c->prm.nb_capacity : 256 * N;
     SPH_TRY(alloc(c, &c->nbl, (size_t)c->nbl_cap));
     SPH_TRY(alloc(c, &c->group_width, N));
@@ -170,7 +172,8 @@ void release(sph_ctx *c)
     void *ptrs[] = {c->key_a, c->key_b, c->val_a, c->val_b, c->hist, c->dlev, c->plev, c->itmp0, c->itmp1,
                     c->itmp2, c->itmp3, c->leaf_begin, c->leaf_level, c->group_begin, c->leaf_lo, c->leaf_hi,
                     c->group_lo, c->group_hi, c->node_child, c->node_parent, c->leaf_parent, c->node_visit,
-                    c->node_lo, c->node_hi, c->xh, c->xl, c->yh, c->yl, c->zh, c->zl, c->nbl, c->group_width,
+                    c->node_lo, c->node_hi, c->xh, c->xl, c->yh, c->yl, c->zh, c->zl, c->srcA, c->srcB,
+                    c->srcC, c->srcD, c->srcE, c->srcF, c->nbl, c->group_width,
                     c->group_off, c->it_lo, c->it_hi, c->it_flags, c->it_sweeps, c->cov, c->act_groups[0],
                     c->act_groups[1], c->vpx, c->vpy, c->vpz, c->upred, c->pr2, c->hold, c->hseed, c->gbuf,
                     c->scan_tmp, c->red, c->dcnt, c->hn_master, c->hn_bf16, c->hn_m, c->hn_v, c->hn_grad,

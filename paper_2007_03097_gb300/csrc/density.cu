@@ -12,10 +12,14 @@
 // the neighbour count.  The paper states the fixed point but not the solver.
 //
 // One warp per target group, one lane per target; each lane walks its own
-// neighbour list (slot-major, coalesced) and re-tests every entry exactly:
-// FP64 r^2 without fused multiply-add in SPH_FP64, FP32 on two-float relative
-// coordinates in SPH_MIXED.  Groups whose particles are all done drop out of
-// the next sweep.
+// neighbour list (slot-major, coalesced).  SPH_MIXED: FP32 on two-float
+// relative coordinates.  SPH_FP64: the pair terms are evaluated in
+// double-float on the FP32 pipes (dfloat.cuh); the neighbour decision
+// r^2 < 4 h^2 is taken in FP32 outside a relative band of 1e-5 around the
+// threshold and inside it by the exact FP64 r^2 = (dx dx + dy dy) + dz dz
+// without fused multiply-add, so the neighbour sets are those of plain FP64.
+// Groups whose particles are all done drop out of the next sweep.
+#include "dfloat.cuh"
 #include "sph_internal.cuh"
 
 namespace {
@@ -33,6 +37,7 @@ struct DensArgs {
     int64_t cap;
     const double *x, *y, *z;
     const float *xh, *xl, *yh, *yl, *zh, *zl;
+    const float4 *srcA, *srcB;   // {xh, xl, yh, yl}, {zh, zl, m_hi, m_lo}
     void *h;
     const void *m;
     void *rho, *omega;
@@ -69,25 +74,53 @@ __global__ void __launch_bounds__(DW * 32) k_density(DensArgs a)
     int cnt = 0;
     if (active) {
         if (FP64POS) {
-            const double xa = a.x[i], ya = a.y[i], za = a.z[i];
-            const double L = a.L, half = 0.5 * a.L;
-            const double thr = __dmul_rn(__dmul_rn(4.0, (double)h), (double)h);
+            const float4 A = a.srcA[i], Bz = a.srcB[i];
+            const double hd = (double)h;
+            const double thr = __dmul_rn(__dmul_rn(4.0, hd), hd);
+            const float thr_f = (float)thr;
+            const float thr_hi = thr_f * (1.f + 1e-5f), thr_lo = thr_f * (1.f - 1e-5f);
+            const float Lf = (float)a.L, half = 0.5f * Lf, guard = 0.45f * Lf;
+            const df Ld = df_from_double(a.L);
+            const df hinv_df = df_from_double((double)hinv);
+            df sw = df{0.f, 0.f}, sd = df{0.f, 0.f};
             for (int k = 0; k < width; ++k) {
                 const uint32_t b = a.nbl[off + (int64_t)k * 32 + lane];
                 if (b == SPH_SENTINEL) continue;
-                const double dx = sep_d(xa, a.x[b], a.periodic, L, half);
-                const double dy = sep_d(ya, a.y[b], a.periodic, L, half);
-                const double dz = sep_d(za, a.z[b], a.periodic, L, half);
-                const double r2 = r2_d(dx, dy, dz);
-                if (!(r2 < thr)) continue;
-                const T q = (T)sqrt(r2) * hinv;
-                T w, dw;
-                kern_wdw<T>(a.kernel, q, w, dw);
-                const T mb = mp[b];
-                sum_w += mb * w;
-                sum_dh += mb * (T(3) * w + q * dw);
+                const float4 P = a.srcA[b], Q = a.srcB[b];
+                float dxf = (A.x - P.x) + (A.y - P.y);
+                float dyf = (A.z - P.z) + (A.w - P.w);
+                float dzf = (Bz.x - Q.x) + (Bz.y - Q.y);
+                int wx = 0, wy = 0, wz = 0;
+                if (a.periodic) {
+                    if (dxf > half) { dxf -= Lf; wx = -1; } else if (dxf < -half) { dxf += Lf; wx = 1; }
+                    if (dyf > half) { dyf -= Lf; wy = -1; } else if (dyf < -half) { dyf += Lf; wy = 1; }
+                    if (dzf > half) { dzf -= Lf; wz = -1; } else if (dzf < -half) { dzf += Lf; wz = 1; }
+                }
+                const float r2f = (dxf * dxf + dyf * dyf) + dzf * dzf;
+                if (r2f > thr_hi) continue;
+                if (r2f >= thr_lo ||
+                    (a.periodic && fmaxf(fmaxf(fabsf(dxf), fabsf(dyf)), fabsf(dzf)) > guard)) {
+                    // knife edge: the exact FP64 decision of the plain definition
+                    const double L = a.L, hl = 0.5 * a.L;
+                    const double dx = sep_d(a.x[i], a.x[b], a.periodic, L, hl);
+                    const double dy = sep_d(a.y[i], a.y[b], a.periodic, L, hl);
+                    const double dz = sep_d(a.z[i], a.z[b], a.periodic, L, hl);
+                    if (!(r2_d(dx, dy, dz) < thr)) continue;
+                }
+                const df dx = df_sep(A.x, A.y, P.x, P.y, wx, Ld);
+                const df dy = df_sep(A.z, A.w, P.z, P.w, wy, Ld);
+                const df dz = df_sep(Bz.x, Bz.y, Q.x, Q.y, wz, Ld);
+                const df r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+                const df q = df_mul(df_sqrt(r2), hinv_df);
+                df w, g3;
+                df_kern_w_g3(a.kernel, q, w, g3);
+                const df mb = df{Q.z, Q.w};
+                sw = df_add(sw, df_mul(mb, w));
+                sd = df_add(sd, df_mul(mb, g3));
                 ++cnt;
             }
+            sum_w = (T)df_to_double(sw);
+            sum_dh = (T)df_to_double(sd);
         } else {
             const float xah = a.xh[i], xal = a.xl[i], yah = a.yh[i], yal = a.yl[i], zah = a.zh[i], zal = a.zl[i];
             const float L = (float)a.L, half = 0.5f * L;
@@ -260,6 +293,7 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
     a.cap = ctx->nbl_cap;
     a.x = p->x; a.y = p->y; a.z = p->z;
     a.xh = ctx->xh; a.xl = ctx->xl; a.yh = ctx->yh; a.yl = ctx->yl; a.zh = ctx->zh; a.zl = ctx->zl;
+    a.srcA = ctx->srcA; a.srcB = ctx->srcB;
     a.h = p->h; a.m = p->m; a.rho = p->rho; a.omega = p->omega; a.nnb = p->nnb;
     a.it_lo = ctx->it_lo; a.it_hi = ctx->it_hi; a.it_flags = ctx->it_flags; a.it_sweeps = ctx->it_sweeps;
     a.cov = ctx->cov;

@@ -9,6 +9,10 @@
 // and the signal speed vsig_a = max_b (c_a + c_b - 3 min(0, v_ab . rhat_ab)).
 // One warp per target group, one lane per target, each lane walking its own
 // force list (b with r_ab <= max(2 h_a, h_a + h_b)) and testing it exactly.
+// SPH_MIXED: FP32 throughout.  SPH_FP64: pair terms in double-float on the
+// FP32 pipes, membership decided in FP32 outside a 1e-5 relative band around
+// each threshold and by the exact FP64 r^2 inside it.
+#include "dfloat.cuh"
 #include "sph_internal.cuh"
 
 namespace {
@@ -24,6 +28,7 @@ struct ForceArgs {
     int n_groups;
     const double *x, *y, *z;
     const float *xh, *xl, *yh, *yl, *zh, *zl;
+    const float4 *srcA, *srcB, *srcC, *srcD, *srcE, *srcF;
     const void *vx, *vy, *vz, *m, *h, *rho, *pr2, *c;
     void *ax, *ay, *az, *dudt, *divv, *vsig;
     int kernel, periodic;
@@ -135,6 +140,152 @@ __global__ void __launch_bounds__(FW * 32) k_forces(ForceArgs a)
     if (lane == 0) atomicAdd(&a.cnt->interactions, (unsigned long long)nint);
 }
 
+
+// SPH_FP64 force pass in double-float (see the file comment).
+__global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int g = blockIdx.x * FW + (threadIdx.x >> 5);
+    if (g >= a.n_groups) return;
+    const int gb = a.group_begin[g], ge = a.group_begin[g + 1];
+    const bool tgt = lane < ge - gb;
+    const int i = gb + (tgt ? lane : 0);
+    const double *h64 = (const double *)a.h;
+    const int64_t off = a.goff[g];
+    int width = tgt ? a.gwidth[g] : 0;
+    if (off + 32 * (int64_t)width > a.cap) width = 0;
+
+    const float4 A = a.srcA[i], Bz = a.srcB[i], C = a.srcC[i], D = a.srcD[i], E = a.srcE[i], F = a.srcF[i];
+    const double had = h64[i];
+    const double thr_d = __dmul_rn(__dmul_rn(4.0, had), had);
+    const float thr_f = (float)thr_d;
+    const float thr_hi = thr_f * (1.f + 1e-5f), thr_lo = thr_f * (1.f - 1e-5f);
+    const float Lf = (float)a.L, half = 0.5f * Lf, guard = 0.45f * Lf;
+    const df Ld = df_from_double(a.L);
+    const double sig_d = a.kernel == 0 ? 1.0 / SPH_PI : a.kernel == 1 ? 21.0 / (16.0 * SPH_PI) : 495.0 / (256.0 * SPH_PI);
+    const df sig = df_from_double(sig_d);
+    const df ha = df{D.z, D.w};
+    const df hainv = df_from_double(1.0 / had);
+    const df hai2 = df_sqr(hainv);
+    const df sig_hai4 = df_mul(sig, df_sqr(hai2));
+    const df vxa = df{C.x, C.y}, vya = df{C.z, C.w}, vza = df{D.x, D.y};
+    const df rhoa = df{E.x, E.y}, pra = df{E.z, E.w}, ca = df{F.x, F.y};
+    const df alpha = df_from_double(a.alpha), beta = df_from_double(a.beta), eps = df_from_double(a.eps);
+
+    df accx = df{0.f, 0.f}, accy = accx, accz = accx, du = accx, dv = accx, vs = ca;
+    int nint = 0;
+    for (int k = 0; k < width; ++k) {
+        const uint32_t b = a.nbl[off + (int64_t)k * 32 + lane];
+        if (b == SPH_SENTINEL) continue;
+        const float4 P = a.srcA[b], Q = a.srcB[b], Db = a.srcD[b];
+        float dxf = (A.x - P.x) + (A.y - P.y);
+        float dyf = (A.z - P.z) + (A.w - P.w);
+        float dzf = (Bz.x - Q.x) + (Bz.y - Q.y);
+        int wx = 0, wy = 0, wz = 0;
+        if (a.periodic) {
+            if (dxf > half) { dxf -= Lf; wx = -1; } else if (dxf < -half) { dxf += Lf; wx = 1; }
+            if (dyf > half) { dyf -= Lf; wy = -1; } else if (dyf < -half) { dyf += Lf; wy = 1; }
+            if (dzf > half) { dzf -= Lf; wz = -1; } else if (dzf < -half) { dzf += Lf; wz = 1; }
+        }
+        const float r2f = (dxf * dxf + dyf * dyf) + dzf * dzf;
+        const float hsf = D.z + Db.z;
+        const float thf = hsf * hsf;
+        const bool out_d = r2f > thr_hi, out_f = r2f > thf * (1.f + 1e-5f);
+        if (out_d && out_f) continue;
+        bool in_d = r2f < thr_lo, in_f = r2f < thf * (1.f - 1e-5f);
+        const bool edge = (!in_d && !out_d) || (!in_f && !out_f) ||
+                          (a.periodic && fmaxf(fmaxf(fabsf(dxf), fabsf(dyf)), fabsf(dzf)) > guard);
+        if (edge) {
+            // knife edge: the exact FP64 decisions of the plain definition
+            const double L = a.L, hl = 0.5 * a.L;
+            const double dx = sep_d(a.x[i], a.x[b], a.periodic, L, hl);
+            const double dy = sep_d(a.y[i], a.y[b], a.periodic, L, hl);
+            const double dz = sep_d(a.z[i], a.z[b], a.periodic, L, hl);
+            const double rr = r2_d(dx, dy, dz);
+            const double hs = __dadd_rn(had, h64[b]);
+            in_f = rr < __dmul_rn(hs, hs);
+            in_d = rr < thr_d;
+            if (!in_f && !in_d) continue;
+        }
+        const float4 Cb = a.srcC[b], Eb = a.srcE[b], Fb = a.srcF[b];
+        const df dx = df_sep(A.x, A.y, P.x, P.y, wx, Ld);
+        const df dy = df_sep(A.z, A.w, P.z, P.w, wy, Ld);
+        const df dz = df_sep(Bz.x, Bz.y, Q.x, Q.y, wz, Ld);
+        const df r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+        const df r = df_sqrt(r2);
+        const df rinv = df_rcp(r);
+        const df vabx = df_sub(vxa, df{Cb.x, Cb.y}), vaby = df_sub(vya, df{Cb.z, Cb.w}), vabz = df_sub(vza, df{Db.x, Db.y});
+        const df vdotr = df_add(df_add(df_mul(vabx, dx), df_mul(vaby, dy)), df_mul(vabz, dz));
+        const df mb = df{Q.z, Q.w};
+        if (in_d) {
+            const df dwq = df_kern_dw(a.kernel, df_mul(r, hainv));
+            dv = df_add(dv, df_mul(df_mul(mb, df_mul(sig_hai4, dwq)), df_mul(rinv, vdotr)));
+        }
+        if (in_f) {
+            const df hb = df{Db.z, Db.w};
+            const df hab = df_scale(df_add(ha, hb), 0.5f);
+            const df habinv = df_rcp(hab);
+            const df dwq = df_kern_dw(a.kernel, df_mul(r, habinv));
+            const df hi2 = df_sqr(habinv);
+            const df gr = df_mul(df_mul(sig, df_sqr(hi2)), df_mul(dwq, rinv));     // grad_a W = gr r_ab
+            df Pi = df{0.f, 0.f};
+            if (df_lt0(vdotr)) {
+                const df mu = df_mul(df_mul(hab, vdotr), df_rcp(df_add(r2, df_mul(eps, df_sqr(hab)))));
+                const df cbar = df_scale(df_add(ca, df{Fb.x, Fb.y}), 0.5f);
+                const df rbar = df_scale(df_add(rhoa, df{Eb.x, Eb.y}), 0.5f);
+                Pi = df_mul(df_add(df_neg(df_mul(df_mul(alpha, cbar), mu)), df_mul(beta, df_sqr(mu))), df_rcp(rbar));
+            }
+            const df coef = df_mul(mb, df_mul(df_add(df_add(pra, df{Eb.z, Eb.w}), Pi), gr));
+            accx = df_sub(accx, df_mul(coef, dx));
+            accy = df_sub(accy, df_mul(coef, dy));
+            accz = df_sub(accz, df_mul(coef, dz));
+            du = df_add(du, df_mul(df_mul(mb, df_add(pra, df_scale(Pi, 0.5f))), df_mul(gr, vdotr)));
+            const df vr = df_mul(vdotr, rinv);
+            df sg = df_add(ca, df{Fb.x, Fb.y});
+            if (df_lt0(vr)) sg = df_sub(sg, df_mul_f(vr, 3.f));
+            if (df_gt(sg, vs)) vs = sg;
+            ++nint;
+        }
+    }
+    if (tgt) {
+        ((double *)a.ax)[i] = df_to_double(accx);
+        ((double *)a.ay)[i] = df_to_double(accy);
+        ((double *)a.az)[i] = df_to_double(accz);
+        ((double *)a.dudt)[i] = df_to_double(du);
+        ((double *)a.divv)[i] = -df_to_double(dv) / ((const double *)a.rho)[i];
+        ((double *)a.vsig)[i] = df_to_double(vs);
+    }
+    for (int o = 16; o > 0; o >>= 1) nint += __shfl_xor_sync(0xffffffffu, nint, o);
+    if (lane == 0) atomicAdd(&a.cnt->interactions, (unsigned long long)nint);
+}
+
+__device__ __forceinline__ float2 split2(double v)
+{
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+
+// packed force-pass sources: C {vx, vy}, D {vz, h}, E {rho, P/rho^2}, F {c, 0}
+__global__ void k_pack_force(const double *__restrict__ vx, const double *__restrict__ vy,
+                             const double *__restrict__ vz, const double *__restrict__ h,
+                             const double *__restrict__ rho, const double *__restrict__ P,
+                             const double *__restrict__ c, int64_t n, double *__restrict__ pr2,
+                             float4 *__restrict__ C, float4 *__restrict__ D, float4 *__restrict__ E,
+                             float4 *__restrict__ F)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double r = rho[i];
+    const double q = P[i] / (r * r);
+    pr2[i] = q;
+    const float2 a = split2(vx[i]), b = split2(vy[i]), cz = split2(vz[i]), hh = split2(h[i]);
+    const float2 rr = split2(r), qq = split2(q), cc = split2(c[i]);
+    C[i] = make_float4(a.x, a.y, b.x, b.y);
+    D[i] = make_float4(cz.x, cz.y, hh.x, hh.y);
+    E[i] = make_float4(rr.x, rr.y, qq.x, qq.y);
+    F[i] = make_float4(cc.x, cc.y, 0.f, 0.f);
+}
+
 template <typename T>
 __global__ void k_pr2(const T *__restrict__ P, const T *__restrict__ rho, int64_t n, T *__restrict__ pr2)
 {
@@ -154,7 +305,13 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
 {
     const int64_t launches0 = ctx->launches;
     k_reset_inter<<<1, 1, 0, s>>>(ctx->dcnt);
-    k_pr2<T><<<grid_for(p->n, 256), 256, 0, s>>>((const T *)p->P, (const T *)p->rho, p->n, (T *)ctx->pr2);
+    if (ctx->fp64)
+        k_pack_force<<<grid_for(p->n, 256), 256, 0, s>>>(
+            (const double *)vx, (const double *)vy, (const double *)vz, (const double *)p->h, (const double *)p->rho,
+            (const double *)p->P, (const double *)p->c, p->n, (double *)ctx->pr2, ctx->srcC, ctx->srcD, ctx->srcE,
+            ctx->srcF);
+    else
+        k_pr2<T><<<grid_for(p->n, 256), 256, 0, s>>>((const T *)p->P, (const T *)p->rho, p->n, (T *)ctx->pr2);
     SPH_CHECK_LAUNCH();
     SPH_TRY(tree_refit_h(ctx, p, s));
     SPH_TRY(lists_build(ctx, p, 1, s));
@@ -167,6 +324,8 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
     a.n_groups = (int)ctx->n_groups;
     a.x = p->x; a.y = p->y; a.z = p->z;
     a.xh = ctx->xh; a.xl = ctx->xl; a.yh = ctx->yh; a.yl = ctx->yl; a.zh = ctx->zh; a.zl = ctx->zl;
+    a.srcA = ctx->srcA; a.srcB = ctx->srcB; a.srcC = ctx->srcC; a.srcD = ctx->srcD; a.srcE = ctx->srcE;
+    a.srcF = ctx->srcF;
     a.vx = vx; a.vy = vy; a.vz = vz; a.m = p->m; a.h = p->h; a.rho = p->rho; a.pr2 = ctx->pr2; a.c = p->c;
     a.ax = p->ax; a.ay = p->ay; a.az = p->az; a.dudt = p->dudt; a.divv = p->divv; a.vsig = p->vsig;
     a.kernel = ctx->prm.kernel;
@@ -175,7 +334,7 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
     a.alpha = ctx->prm.alpha; a.beta = ctx->prm.beta; a.eps = ctx->prm.eps_visc;
     a.cnt = ctx->dcnt;
     SPH_CUDA(cudaEventRecord(ctx->kev[2], s));
-    if (ctx->fp64) k_forces<T, true><<<grid_for(ctx->n_groups, FW), FW * 32, 0, s>>>(a);
+    if (ctx->fp64) k_forces_df<<<grid_for(ctx->n_groups, FW), FW * 32, 0, s>>>(a);
     else k_forces<T, false><<<grid_for(ctx->n_groups, FW), FW * 32, 0, s>>>(a);
     SPH_CHECK_LAUNCH();
     SPH_CUDA(cudaEventRecord(ctx->kev[3], s));

@@ -89,6 +89,9 @@ struct sph_ctx {
     float4 *group_lo = nullptr, *group_hi = nullptr; // .w of lo = h_max
     // ---- two-float split of the positions (padded)
     float *xh = nullptr, *xl = nullptr, *yh = nullptr, *yl = nullptr, *zh = nullptr, *zl = nullptr;
+    // packed per-particle sources of the pair kernels (two-float pairs):
+    // A {x, y}, B {z, m}, C {vx, vy}, D {vz, h}, E {rho, P/rho^2}, F {c, -}
+    float4 *srcA = nullptr, *srcB = nullptr, *srcC = nullptr, *srcD = nullptr, *srcE = nullptr, *srcF = nullptr;
     // ---- neighbour lists (group slabs, slot-major within a group)
     uint32_t *nbl = nullptr;
     int64_t nbl_cap = 0;

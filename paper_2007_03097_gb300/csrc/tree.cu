@@ -239,6 +239,25 @@ __global__ void k_gather(FieldTable t, const uint32_t *__restrict__ perm, int64_
     }
 }
 
+// two-float split v = hi + lo of a value given in double
+__device__ __forceinline__ float2 split2(double v)
+{
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+
+// packed pair-kernel sources: {xh, xl, yh, yl} and {zh, zl, m_hi, m_lo}
+template <typename T>
+__global__ void k_pack_pos(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+                           const T *__restrict__ m, int64_t n, float4 *__restrict__ A, float4 *__restrict__ B)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float2 sx = split2(x[i]), sy = split2(y[i]), sz = split2(z[i]), sm = split2((double)m[i]);
+    A[i] = make_float4(sx.x, sx.y, sy.x, sy.y);
+    B[i] = make_float4(sz.x, sz.y, sm.x, sm.y);
+}
+
 __global__ void k_copy_back(FieldTable t, int64_t n)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -557,6 +576,8 @@ int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
                                               ctx->zl);
     SPH_CHECK_LAUNCH();
     k_copy_back<<<grid_for(n, 256), 256, 0, s>>>(t, n);
+    SPH_CHECK_LAUNCH();
+    k_pack_pos<T><<<grid_for(n, 256), 256, 0, s>>>(p->x, p->y, p->z, (const T *)p->m, n, ctx->srcA, ctx->srcB);
     SPH_CHECK_LAUNCH();
     // octree leaves and target groups
     k_dlev<<<grid_for(n, 256), 256, 0, s>>>(ctx->key_a, n, ctx->dlev);
