@@ -280,7 +280,7 @@ int sph_forces(sph_ctx *ctx, sph_particles *p, sph_force_stats *stats, void *str
     cudaStream_t s = S(stream);
     sph_force_stats local{};
     SPH_CUDA(cudaEventRecord(ctx->ev[0], s));
-    SPH_TRY(forces_run(ctx, p, p->vx, p->vy, p->vz, &local, s));
+    SPH_TRY(forces_run(ctx, p, p->vx, p->vy, p->vz, &local, false, s));
     SPH_CUDA(cudaEventRecord(ctx->ev[1], s));
     SPH_CUDA(cudaEventSynchronize(ctx->ev[1]));
     SPH_TRY(elapsed(ctx, ctx->ev[0], ctx->ev[1], &local.ms));
@@ -338,7 +338,7 @@ int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet, sph_step_s
     SPH_TRY(copy_field(ctx, p->hprev, ctx->hold, p->n, s));
     SPH_TRY(predict(ctx, p, dt, s));
     SPH_TRY(eos_run(ctx, p, ctx->upred, s));
-    SPH_TRY(forces_run(ctx, p, ctx->vpx, ctx->vpy, ctx->vpz, &local.forces, s));
+    SPH_TRY(forces_run(ctx, p, ctx->vpx, ctx->vpy, ctx->vpz, &local.forces, true, s));
     SPH_TRY(kick(ctx, p, dt, s));
     SPH_TRY(totals_run(ctx, p, ctx->vpx, ctx->vpy, ctx->vpz, p->u, s));
     SPH_CUDA(cudaEventRecord(ev[4], s));

@@ -280,7 +280,7 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
     k_dens_init<T><<<grid_for(n, 256), 256, 0, s>>>((T *)p->h, (const T *)seed, n, q.fixed_h, ctx->it_flags,
                                                      ctx->it_sweeps, ctx->it_lo, ctx->it_hi);
     SPH_CHECK_LAUNCH();
-    SPH_TRY(lists_build(ctx, p, 0, s));
+    SPH_TRY(lists_build(ctx, p, s));
     int builds = 1;
     int n_act = (int)ctx->n_groups;
     k_iota_i32<<<grid_for(n_act, 256), 256, 0, s>>>(ctx->act_groups[0], n_act);
@@ -328,7 +328,7 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
         n_act = ctx->hcnt->n_active_groups;
         if (n_act == 0 || sweeps > q.max_sweeps + 1) break;
         if (ctx->hcnt->n_uncovered > 0) {
-            SPH_TRY(lists_build(ctx, p, 0, s));
+            SPH_TRY(lists_build(ctx, p, s));
             ++builds;
         }
         cur ^= 1;

@@ -8,7 +8,7 @@
 // Also: div v_a = -(1/rho_a) sum_{r_ab < 2 h_a} m_b v_ab . grad_a W(r_ab, h_a)
 // and the signal speed vsig_a = max_b (c_a + c_b - 3 min(0, v_ab . rhat_ab)).
 // One warp per target group, one lane per target, each lane walking its own
-// force list (b with r_ab <= max(2 h_a, h_a + h_b)) and testing it exactly.
+// neighbour list and testing every entry exactly.
 // SPH_MIXED: FP32 throughout.  SPH_FP64: pair terms in double-float on the
 // FP32 pipes, membership decided in FP32 outside a 1e-5 relative band around
 // each threshold and by the exact FP64 r^2 inside it.
@@ -301,7 +301,7 @@ __global__ void k_reset_inter(DevCounters *c)
 
 template <typename T>
 int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, const void *vz,
-             sph_force_stats *st, cudaStream_t s)
+             sph_force_stats *st, bool reuse_lists, cudaStream_t s)
 {
     const int64_t launches0 = ctx->launches;
     k_reset_inter<<<1, 1, 0, s>>>(ctx->dcnt);
@@ -313,8 +313,7 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
     else
         k_pr2<T><<<grid_for(p->n, 256), 256, 0, s>>>((const T *)p->P, (const T *)p->rho, p->n, (T *)ctx->pr2);
     SPH_CHECK_LAUNCH();
-    SPH_TRY(tree_refit_h(ctx, p, s));
-    SPH_TRY(lists_build(ctx, p, 1, s));
+    if (!reuse_lists || !ctx->lists_valid) SPH_TRY(lists_build(ctx, p, s));
     ForceArgs a{};
     a.group_begin = ctx->group_begin;
     a.goff = ctx->group_off;
@@ -354,8 +353,11 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
 
 }  // namespace
 
+// reuse_lists: the lists of the h iteration that just ended still cover 2h
+// of every particle (sph_step); otherwise they are rebuilt for the current h.
 int forces_run(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, const void *vz,
-               sph_force_stats *st, cudaStream_t s)
+               sph_force_stats *st, bool reuse_lists, cudaStream_t s)
 {
-    return ctx->fp64 ? run_impl<double>(ctx, p, vx, vy, vz, st, s) : run_impl<float>(ctx, p, vx, vy, vz, st, s);
+    return ctx->fp64 ? run_impl<double>(ctx, p, vx, vy, vz, st, reuse_lists, s)
+                     : run_impl<float>(ctx, p, vx, vy, vz, st, reuse_lists, s);
 }

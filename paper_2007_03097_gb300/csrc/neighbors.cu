@@ -7,8 +7,12 @@
 // The exact FP64 (or FP32) decision is taken again by the pass that uses the
 // list.  Lists are stored slot-major per group (entry (slot, lane) at
 // off[g] + 32 slot + lane) so that the consumers read them coalesced.
-//   kind 0 (density): b with r_ab <= cov_a, the coverage radius 2 h_a (1+skin)
-//   kind 1 (force):   b with r_ab <= max(2 h_a, h_a + h_b)
+// One symmetric list serves the whole step: b is listed for a when
+// r_ab <= max(cov_a, cov_b) with the coverage radius cov = 2 h (1 + skin).
+// While 2h <= cov for every particle it holds every density pair
+// (r < 2 h_a) and every force pair (r < max(2 h_a, h_a + h_b)
+// <= max(2 h_a, 2 h_b)), so the h iteration and the force pass share it and
+// it is rebuilt only when some h outgrows its coverage.
 #include "sph_internal.cuh"
 
 namespace {
@@ -19,8 +23,7 @@ constexpr int TILE = 64;           // source tile entries per warp
 constexpr float MARGIN = 2e-5f;    // relative margin of the FP32 tests
 
 struct ListArgs {
-    const float *xh, *xl, *yh, *yl, *zh, *zl;
-    const void *h;
+    const float4 *srcA, *srcB;     // two-float positions {xh, xl, yh, yl}, {zh, zl, .., ..}
     const float *cov;
     const int32_t *group_begin;
     const float4 *group_lo, *group_hi;
@@ -49,14 +52,7 @@ __device__ __forceinline__ float axis_gap(float alo, float ahi, float blo, float
     return fmaxf(0.f, fabsf(d) - ea - eb);
 }
 
-template <typename T>
-__device__ __forceinline__ float h_up(const T *h, int i)
-{
-    if (sizeof(T) == 8) return __double2float_ru((double)h[i]);
-    return (float)h[i];
-}
-
-template <typename T, int KIND, bool FILL>
+template <bool FILL>
 __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
 {
     __shared__ int32_t s_stack[LW][STACK];
@@ -68,26 +64,14 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
     int32_t *stack = s_stack[w];
     float(*src)[TILE] = s_src[w];
     int32_t *sidx = s_idx[w];
-    const T *h = (const T *)a.h;
 
     const int gb = a.group_begin[g], ge = a.group_begin[g + 1];
     const bool tgt = lane < ge - gb;
     const int ia = gb + (tgt ? lane : 0);
-    const float axh = a.xh[ia], axl = a.xl[ia], ayh = a.yh[ia], ayl = a.yl[ia], azh = a.zh[ia], azl = a.zl[ia];
-    const float ha = h_up(h, ia);
-    float thr_own;                                 // density: cov^2, force: (2 h_a)^2
-    if (KIND == 0) { float c = a.cov[ia]; thr_own = c * c * (1.f + MARGIN); }
-    else thr_own = 4.f * ha * ha * (1.f + MARGIN);
+    const float4 PA = a.srcA[ia], PB = a.srcB[ia];
+    const float ca = a.cov[ia];
     const float4 qlo = a.group_lo[g], qhi = a.group_hi[g];
-    const float ghmax = qlo.w;
-    float qrad;                                    // density: max coverage in the group
-    if (KIND == 0) {
-        float c = tgt ? a.cov[ia] : 0.f;
-        for (int o = 16; o > 0; o >>= 1) c = fmaxf(c, __shfl_xor_sync(0xffffffffu, c, o));
-        qrad = c;
-    } else {
-        qrad = 2.f * ghmax;
-    }
+    const float qcov = qlo.w;                      // largest coverage in the group
 
     int64_t off = 0;
     int width = 0;
@@ -104,13 +88,12 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
     auto process = [&](int ns) {
         for (int k = 0; k < ns; ++k) {
             const int b = sidx[k];
-            float dx = sep_f(axh, axl, src[0][k], src[1][k], a.periodic, a.L, a.half);
-            float dy = sep_f(ayh, ayl, src[2][k], src[3][k], a.periodic, a.L, a.half);
-            float dz = sep_f(azh, azl, src[4][k], src[5][k], a.periodic, a.L, a.half);
+            float dx = sep_f(PA.x, PA.y, src[0][k], src[1][k], a.periodic, a.L, a.half);
+            float dy = sep_f(PA.z, PA.w, src[2][k], src[3][k], a.periodic, a.L, a.half);
+            float dz = sep_f(PB.x, PB.y, src[4][k], src[5][k], a.periodic, a.L, a.half);
             float r2 = (dx * dx + dy * dy) + dz * dz;
-            float thr = thr_own;
-            if (KIND == 1) { float hs = ha + src[6][k]; thr = fmaxf(thr, hs * hs * (1.f + MARGIN)); }
-            if (tgt && b != ia && r2 <= thr) {
+            const float c = fmaxf(ca, src[6][k]);
+            if (tgt && b != ia && r2 <= c * c * (1.f + MARGIN)) {
                 if (FILL && count < width) a.nbl[off + (int64_t)count * 32 + lane] = (uint32_t)b;
                 ++count;
             }
@@ -138,7 +121,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
             float4 lo, hi;
             if (leaf) { lo = a.leaf_lo[id]; hi = a.leaf_hi[id]; }
             else { lo = a.node_lo[id]; hi = a.node_hi[id]; }
-            float r = KIND == 0 ? qrad : fmaxf(qrad, ghmax + lo.w);
+            const float r = fmaxf(qcov, lo.w);
             float gx = axis_gap(qlo.x, qhi.x, lo.x, hi.x, a.periodic, a.L, a.half);
             float gy = axis_gap(qlo.y, qhi.y, lo.y, hi.y, a.periodic, a.L, a.half);
             float gz = axis_gap(qlo.z, qhi.z, lo.z, hi.z, a.periodic, a.L, a.half);
@@ -168,10 +151,11 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
             if (lane < cnt) {
                 const int j = lb + lane;
                 const int t = ns + lane;
-                src[0][t] = a.xh[j]; src[1][t] = a.xl[j];
-                src[2][t] = a.yh[j]; src[3][t] = a.yl[j];
-                src[4][t] = a.zh[j]; src[5][t] = a.zl[j];
-                src[6][t] = KIND == 1 ? h_up(h, j) : 0.f;
+                const float4 qa = a.srcA[j], qb = a.srcB[j];
+                src[0][t] = qa.x; src[1][t] = qa.y;
+                src[2][t] = qa.z; src[3][t] = qa.w;
+                src[4][t] = qb.x; src[5][t] = qb.y;
+                src[6][t] = a.cov[j];
                 sidx[t] = j;
             }
             ns += cnt;
@@ -286,13 +270,12 @@ __global__ void k_export(const int32_t *__restrict__ group_begin, int ng, const 
     counts[ia] = c;
 }
 
-template <typename T>
-int build_impl(sph_ctx *ctx, const sph_particles *p, int kind, cudaStream_t s)
+int build_impl(sph_ctx *ctx, cudaStream_t s)
 {
     const int ng = (int)ctx->n_groups;
+    SPH_TRY(tree_boxes(ctx, s));
     ListArgs a{};
-    a.xh = ctx->xh; a.xl = ctx->xl; a.yh = ctx->yh; a.yl = ctx->yl; a.zh = ctx->zh; a.zl = ctx->zl;
-    a.h = p->h;
+    a.srcA = ctx->srcA; a.srcB = ctx->srcB;
     a.cov = ctx->cov;
     a.group_begin = ctx->group_begin;
     a.group_lo = ctx->group_lo; a.group_hi = ctx->group_hi;
@@ -312,8 +295,7 @@ int build_impl(sph_ctx *ctx, const sph_particles *p, int kind, cudaStream_t s)
     a.cap = ctx->nbl_cap;
     a.cnt = ctx->dcnt;
     const unsigned grid = grid_for(ng, LW);
-    if (kind == 0) k_lists<T, 0, false><<<grid, LW * 32, 0, s>>>(a);
-    else k_lists<T, 1, false><<<grid, LW * 32, 0, s>>>(a);
+    k_lists<false><<<grid, LW * 32, 0, s>>>(a);
     SPH_CHECK_LAUNCH();
     k_slots<<<grid_for(ng, 256), 256, 0, s>>>(ctx->group_width, ng, ctx->itmp0);
     SPH_CHECK_LAUNCH();
@@ -321,11 +303,11 @@ int build_impl(sph_ctx *ctx, const sph_particles *p, int kind, cudaStream_t s)
     k_list_total<<<1, 1, 0, s>>>(ctx->group_off, ctx->group_width, ng, ctx->nbl_cap, ctx->group_off + ng,
                                  ctx->dcnt);
     SPH_CHECK_LAUNCH();
-    if (kind == 0) k_lists<T, 0, true><<<grid, LW * 32, 0, s>>>(a);
-    else k_lists<T, 1, true><<<grid, LW * 32, 0, s>>>(a);
+    k_lists<true><<<grid, LW * 32, 0, s>>>(a);
     SPH_CHECK_LAUNCH();
     k_guard_widths<<<grid_for(ng, 256), 256, 0, s>>>(ctx->group_width, ng, ctx->dcnt);
     SPH_CHECK_LAUNCH();
+    ctx->lists_valid = true;
     return SPH_OK;
 }
 
@@ -339,23 +321,20 @@ __global__ void k_coverage(const T *__restrict__ h, int64_t n, double f, float *
 
 }  // namespace
 
-int lists_build(sph_ctx *ctx, const sph_particles *p, int kind, cudaStream_t s)
+int lists_build(sph_ctx *ctx, const sph_particles *p, cudaStream_t s)
 {
-    if (kind == 0) {
-        const double f = 1.0 + ctx->prm.skin;
-        if (ctx->fp64) k_coverage<double><<<grid_for(p->n, 256), 256, 0, s>>>((const double *)p->h, p->n, f, ctx->cov);
-        else k_coverage<float><<<grid_for(p->n, 256), 256, 0, s>>>((const float *)p->h, p->n, f, ctx->cov);
-        SPH_CHECK_LAUNCH();
-    }
-    return ctx->fp64 ? build_impl<double>(ctx, p, kind, s) : build_impl<float>(ctx, p, kind, s);
+    const double f = 1.0 + ctx->prm.skin;
+    if (ctx->fp64) k_coverage<double><<<grid_for(p->n, 256), 256, 0, s>>>((const double *)p->h, p->n, f, ctx->cov);
+    else k_coverage<float><<<grid_for(p->n, 256), 256, 0, s>>>((const float *)p->h, p->n, f, ctx->cov);
+    SPH_CHECK_LAUNCH();
+    return build_impl(ctx, s);
 }
 
 int neighbors_export(sph_ctx *ctx, const sph_particles *p, int kind, int64_t *counts, const int64_t *offsets,
                      uint32_t *idx, cudaStream_t s)
 {
     SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->err, 0, sizeof(uint32_t), s));
-    if (kind == 1) SPH_TRY(tree_refit_h(ctx, p, s));
-    SPH_TRY(lists_build(ctx, p, kind, s));
+    SPH_TRY(lists_build(ctx, p, s));
     const int ng = (int)ctx->n_groups;
     const unsigned grid = grid_for((int64_t)ng * 32, 128);
     const int per = ctx->prm.periodic;

@@ -64,6 +64,7 @@ struct sph_ctx {
     int64_t n = 0;
     int64_t n_leaves = 0, n_groups = 0;
     bool tree_valid = false;
+    bool lists_valid = false;           // lists cover 2h of every particle
     double dom[4] = {0, 0, 0, 1};
     double dt_cfl = 0.0;
 
@@ -80,13 +81,13 @@ struct sph_ctx {
     int32_t *leaf_begin = nullptr;      // n_leaves + 1
     int32_t *leaf_level = nullptr;
     int32_t *group_begin = nullptr;     // n_groups + 1
-    float4 *leaf_lo = nullptr, *leaf_hi = nullptr;   // box; .w of lo = h_max
+    float4 *leaf_lo = nullptr, *leaf_hi = nullptr;   // box; .w of lo = max coverage
     int32_t *node_child = nullptr;      // 2 per internal node; leaf = idx | 1<<31
     int32_t *node_parent = nullptr;     // internal nodes
     int32_t *leaf_parent = nullptr;
     uint32_t *node_visit = nullptr;
-    float4 *node_lo = nullptr, *node_hi = nullptr;   // .w of lo = h_max
-    float4 *group_lo = nullptr, *group_hi = nullptr; // .w of lo = h_max
+    float4 *node_lo = nullptr, *node_hi = nullptr;   // .w of lo = max coverage
+    float4 *group_lo = nullptr, *group_hi = nullptr; // .w of lo = max coverage
     // ---- two-float split of the positions (padded)
     float *xh = nullptr, *xl = nullptr, *yh = nullptr, *yl = nullptr, *zh = nullptr, *zl = nullptr;
     // packed per-particle sources of the pair kernels (two-float pairs):
@@ -254,14 +255,14 @@ int tree_build(sph_ctx *ctx, sph_particles *p, cudaStream_t s);
 int tree_keys(sph_ctx *ctx, const sph_particles *p, uint64_t *keys_out, cudaStream_t s);
 int tree_sort(sph_ctx *ctx, int64_t n, const uint64_t *keys, const uint32_t *ids, uint32_t *perm,
               cudaStream_t s);
-int tree_refit_h(sph_ctx *ctx, const sph_particles *p, cudaStream_t s);
+int tree_boxes(sph_ctx *ctx, cudaStream_t s);
 // scan.cu
 int scan_exclusive_i32(sph_ctx *ctx, const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
 int scan_exclusive_i64(sph_ctx *ctx, const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
 int scan_inclusive_max_i32(sph_ctx *ctx, const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
 size_t scan_tmp_bytes(int64_t n);
 // neighbors.cu
-int lists_build(sph_ctx *ctx, const sph_particles *p, int kind, cudaStream_t s);
+int lists_build(sph_ctx *ctx, const sph_particles *p, cudaStream_t s);
 int neighbors_export(sph_ctx *ctx, const sph_particles *p, int kind, int64_t *counts,
                      const int64_t *offsets, uint32_t *idx, cudaStream_t s);
 // density.cu
@@ -270,7 +271,7 @@ int density_run(sph_ctx *ctx, sph_particles *p, const void *h_seed, sph_density_
 int eos_run(sph_ctx *ctx, sph_particles *p, const void *u, cudaStream_t s);
 // forces.cu
 int forces_run(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, const void *vz,
-               sph_force_stats *st, cudaStream_t s);
+               sph_force_stats *st, bool reuse_lists, cudaStream_t s);
 // integrate.cu
 int kick_drift(sph_ctx *ctx, sph_particles *p, double dt, cudaStream_t s);
 int predict(sph_ctx *ctx, sph_particles *p, double dt, cudaStream_t s);

@@ -3,7 +3,7 @@
 // in-place permutation of every particle array into key order, octree leaf
 // cells of at most leaf_size particles, target groups of at most 32
 // particles, and a binary radix tree over the leaves (Karras 2012) with
-// bounding boxes and maximal h for pruning the neighbour search.
+// bounding boxes and maximal coverage radius for pruning the neighbour search.
 //
 // The paper builds a hashed octree by inserting particles one by one and
 // refining nodes.  Here the octree is implicit in the sorted keys: a leaf is
@@ -351,35 +351,36 @@ __global__ void k_emit(const int32_t *__restrict__ leaf_start, const int32_t *__
     }
 }
 
-// Bounding box (outward-rounded to float) and maximal h of each range
-// [begin[r], begin[r+1]) of at most 32 particles; one warp per range.
-template <typename T>
-__global__ void k_range_boxes(const int32_t *__restrict__ begin, int nr, const double *__restrict__ x,
-                              const double *__restrict__ y, const double *__restrict__ z,
-                              const T *__restrict__ h, float4 *__restrict__ lo4, float4 *__restrict__ hi4)
+// Bounding box of each range [begin[r], begin[r+1]) of at most 32 particles
+// from the FP32 high parts of the two-float positions, widened by one ulp
+// (x lies within half an ulp of its high part), and the largest coverage
+// radius in the range (.w of lo); one warp per range.
+__global__ void k_range_boxes(const int32_t *__restrict__ begin, int nr, const float4 *__restrict__ A,
+                              const float4 *__restrict__ B, const float *__restrict__ cov,
+                              float4 *__restrict__ lo4, float4 *__restrict__ hi4)
 {
     const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= nr) return;
     const int b = begin[r], e = begin[r + 1];
-    double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
-    double hm = 0.0;
+    float mn[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, mx[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    float cm = 0.f;
     for (int i = b + lane; i < e; i += 32) {
-        double c[3] = {x[i], y[i], z[i]};
-        for (int d = 0; d < 3; ++d) { mn[d] = fmin(mn[d], c[d]); mx[d] = fmax(mx[d], c[d]); }
-        hm = fmax(hm, (double)h[i]);
+        const float4 a = A[i];
+        const float c[3] = {a.x, a.z, B[i].x};
+        for (int d = 0; d < 3; ++d) { mn[d] = fminf(mn[d], c[d]); mx[d] = fmaxf(mx[d], c[d]); }
+        cm = fmaxf(cm, cov[i]);
     }
     for (int o = 16; o > 0; o >>= 1) {
         for (int d = 0; d < 3; ++d) {
-            mn[d] = fmin(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
-            mx[d] = fmax(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+            mn[d] = fminf(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+            mx[d] = fmaxf(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
         }
-        hm = fmax(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+        cm = fmaxf(cm, __shfl_xor_sync(0xffffffffu, cm, o));
     }
     if (lane == 0) {
-        lo4[r] = make_float4(__double2float_rd(mn[0]), __double2float_rd(mn[1]), __double2float_rd(mn[2]),
-                             __double2float_ru(hm));
-        hi4[r] = make_float4(__double2float_ru(mx[0]), __double2float_ru(mx[1]), __double2float_ru(mx[2]), 0.f);
+        lo4[r] = make_float4(nextafterf(mn[0], -FLT_MAX), nextafterf(mn[1], -FLT_MAX), nextafterf(mn[2], -FLT_MAX), cm);
+        hi4[r] = make_float4(nextafterf(mx[0], FLT_MAX), nextafterf(mx[1], FLT_MAX), nextafterf(mx[2], FLT_MAX), 0.f);
     }
 }
 
@@ -466,16 +467,14 @@ __global__ void k_refit(int nl, const int32_t *__restrict__ child, const int32_t
     }
 }
 
-template <typename T>
-int boxes_and_refit(sph_ctx *ctx, const sph_particles *p, cudaStream_t s)
+int boxes_and_refit(sph_ctx *ctx, cudaStream_t s)
 {
-    const T *h = (const T *)p->h;
     const int nl = (int)ctx->n_leaves, ng = (int)ctx->n_groups;
-    k_range_boxes<T><<<grid_for((int64_t)nl * 32, 256), 256, 0, s>>>(ctx->leaf_begin, nl, p->x, p->y, p->z, h,
-                                                                     ctx->leaf_lo, ctx->leaf_hi);
+    k_range_boxes<<<grid_for((int64_t)nl * 32, 256), 256, 0, s>>>(ctx->leaf_begin, nl, ctx->srcA, ctx->srcB, ctx->cov,
+                                                                  ctx->leaf_lo, ctx->leaf_hi);
     SPH_CHECK_LAUNCH();
-    k_range_boxes<T><<<grid_for((int64_t)ng * 32, 256), 256, 0, s>>>(ctx->group_begin, ng, p->x, p->y, p->z, h,
-                                                                     ctx->group_lo, ctx->group_hi);
+    k_range_boxes<<<grid_for((int64_t)ng * 32, 256), 256, 0, s>>>(ctx->group_begin, ng, ctx->srcA, ctx->srcB, ctx->cov,
+                                                                  ctx->group_lo, ctx->group_hi);
     SPH_CHECK_LAUNCH();
     if (nl > 1) {
         SPH_CUDA(cudaMemsetAsync(ctx->node_visit, 0, sizeof(unsigned) * (size_t)(nl - 1), s));
@@ -613,8 +612,8 @@ int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
                                                            ctx->node_parent, ctx->leaf_parent);
         SPH_CHECK_LAUNCH();
     }
-    SPH_TRY(boxes_and_refit<T>(ctx, p, s));
     ctx->tree_valid = true;
+    ctx->lists_valid = false;
     return SPH_OK;
 }
 
@@ -625,11 +624,9 @@ int tree_build(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
     return ctx->fp64 ? build_impl<double>(ctx, p, s) : build_impl<float>(ctx, p, s);
 }
 
-// Recompute boxes and maximal h after h changed (positions unchanged).
-int tree_refit_h(sph_ctx *ctx, const sph_particles *p, cudaStream_t s)
-{
-    return ctx->fp64 ? boxes_and_refit<double>(ctx, p, s) : boxes_and_refit<float>(ctx, p, s);
-}
+// Boxes of leaves, groups and radix-tree nodes with the largest coverage
+// radius below each (positions of the current tree, coverage of the lists).
+int tree_boxes(sph_ctx *ctx, cudaStream_t s) { return boxes_and_refit(ctx, s); }
 
 int tree_keys(sph_ctx *ctx, const sph_particles *p, uint64_t *keys_out, cudaStream_t s)
 {
