@@ -256,6 +256,33 @@ int sph_hnet_grad(sph_ctx *ctx, const float *feats, const float *target, int64_t
 int sph_hnet_train_step(sph_ctx *ctx, const float *feats, const float *target, int64_t nb,
                         float lr, float *loss_host, void *stream);
 
+/* ---- allocation-free sort ------------------------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory: code running under a framework whose caching
+ * allocator owns the device memory budget, plugins that their host forbids to
+ * allocate, and latency-critical paths that cannot afford cudaMalloc (which can
+ * synchronise the whole device).  Such callers cannot create an sph_ctx.
+ *
+ * sph_sort_keys_noalloc computes the same permutation as sph_sort_keys
+ * ((keys[perm[i]], ids[perm[i]]) ascending; ids may be NULL, then ties keep
+ * index order) with no context.  keys (n), ids (n) and perm (n) are caller
+ * device arrays.  Its scratch is one static device array of about 6.1 MB in
+ * the library, present on every device that loads the library until the
+ * process exits; the call itself never calls cudaMalloc or cudaFree.
+ *   - n must be in [1, SPH_SORT_NOALLOC_MAX]; larger n returns
+ *     SPH_ERR_CAPACITY without touching the GPU.  A run of more than 64 equal
+ *     keys also returns SPH_ERR_CAPACITY.
+ *   - The first call on a device looks up the device address of the static
+ *     array; make that first call before any stream capture on the device.
+ *   - Every call uses the same scratch and leaves the last call's contents in
+ *     it.  Calls that overlap on the GPU (other streams, other threads, same
+ *     device) race: serialise them.
+ *   - The call synchronises `stream` before returning (it reads a status word).
+ */
+#define SPH_SORT_NOALLOC_MAX 262144
+int sph_sort_keys_noalloc(int64_t n, const uint64_t *keys, const uint32_t *ids, uint32_t *perm,
+                          void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -79,7 +79,8 @@ EXPORTED = ["sph_create", "sph_destroy", "sph_set_params", "sph_last_error", "sp
             "sph_density", "sph_forces", "sph_step", "sph_totals", "sph_morton_keys", "sph_sort_keys",
             "sph_tree_info", "sph_export_leaves", "sph_neighbors", "sph_hnet_set_weights",
             "sph_hnet_get_weights", "sph_hnet_features", "sph_hnet_infer", "sph_hnet_grad",
-            "sph_hnet_train_step"]
+            "sph_hnet_train_step", "sph_sort_keys_noalloc"]
+SPH_SORT_NOALLOC_MAX = 262144
 
 
 def library_path() -> str:
@@ -119,6 +120,7 @@ def load(path: str | None = None):
         "sph_hnet_infer": ([V, V, I64, V, V], I32),
         "sph_hnet_grad": ([V, V, V, I64, V, V, V], I32),
         "sph_hnet_train_step": ([V, V, V, I64, _c.c_float, V, V], I32),
+        "sph_sort_keys_noalloc": ([I64, V, V, V, V], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -329,6 +331,18 @@ def sph_sort_keys(ctx: Context, keys: torch.Tensor, ids: torch.Tensor | None, st
     perm = torch.empty(n, dtype=torch.int32, device=keys.device)
     _check(ctx, load().sph_sort_keys(ctx.handle, n, keys.data_ptr(), ids.data_ptr() if ids is not None else None,
                                      perm.data_ptr(), _stream(stream)))
+    return perm
+
+
+def sph_sort_keys_noalloc(keys: torch.Tensor, ids: torch.Tensor | None, stream=None) -> torch.Tensor:
+    """(key, id) sort permutation without a context or any device allocation
+    by the library (the permutation tensor here is the caller's own)."""
+    n = keys.numel()
+    perm = torch.empty(n, dtype=torch.int32, device=keys.device)
+    st = load().sph_sort_keys_noalloc(n, keys.data_ptr(), ids.data_ptr() if ids is not None else None,
+                                       perm.data_ptr(), _stream(stream))
+    if st != SPH_OK:
+        raise SphError(st, "sph_sort_keys_noalloc failed (n must be in [1, %d])" % SPH_SORT_NOALLOC_MAX)
     return perm
 
 
