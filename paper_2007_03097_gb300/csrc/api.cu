@@ -338,11 +338,12 @@ int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet, sph_step_s
     SPH_TRY(copy_field(ctx, p->hprev, ctx->hold, p->n, s));
     SPH_TRY(predict(ctx, p, dt, s));
     SPH_TRY(eos_run(ctx, p, ctx->upred, s));
-    SPH_TRY(forces_run(ctx, p, ctx->vpx, ctx->vpy, ctx->vpz, &local.forces, true, s));
+    SPH_TRY(forces_run(ctx, p, ctx->vpx, ctx->vpy, ctx->vpz, nullptr, true, s));
     SPH_TRY(kick(ctx, p, dt, s));
     SPH_TRY(totals_run(ctx, p, ctx->vpx, ctx->vpy, ctx->vpz, p->u, s));
     SPH_CUDA(cudaEventRecord(ev[4], s));
     SPH_TRY(sync_counters(ctx, s));
+    SPH_TRY(forces_collect(ctx, &local.forces));
     const DevCounters &h = *ctx->hcnt;
     for (int k = 0; k < 3; ++k) { local.momentum[k] = h.totals[k]; local.force[k] = h.totals[3 + k]; }
     local.energy = h.totals[6];

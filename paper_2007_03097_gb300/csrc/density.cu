@@ -19,6 +19,8 @@
 // threshold and inside it by the exact FP64 r^2 = (dx dx + dy dy) + dz dz
 // without fused multiply-add, so the neighbour sets are those of plain FP64.
 // Groups whose particles are all done drop out of the next sweep.
+#include <algorithm>
+
 #include "dfloat.cuh"
 #include "sph_internal.cuh"
 
@@ -27,9 +29,10 @@ namespace {
 constexpr int DW = 4;   // warps per block
 
 struct DensArgs {
-    const int32_t *act;
-    int n_act;
-    int32_t *act_next;
+    const int32_t *act;            // active groups of this sweep ...
+    const int32_t *act_count;      // ... and their number (device)
+    int32_t *act_next;             // groups still active after it ...
+    int32_t *act_next_count;       // ... and their number (zeroed before the sweep)
     const int32_t *group_begin;
     const int64_t *goff;
     const int32_t *gwidth;
@@ -51,20 +54,24 @@ struct DensArgs {
 };
 
 template <typename T, bool FP64POS>
-__global__ void __launch_bounds__(DW * 32) k_density(DensArgs a)
+__device__ __forceinline__ void density_group(const DensArgs &a, const int g, const int lane)
 {
-    const int lane = threadIdx.x & 31;
-    const int gi = blockIdx.x * DW + (threadIdx.x >> 5);
-    if (gi >= a.n_act) return;
-    const int g = a.act[gi];
     const int gb = a.group_begin[g], ge = a.group_begin[g + 1];
     const bool tgt = lane < ge - gb;
     const int i = gb + (tgt ? lane : 0);
     T *hp = (T *)a.h;
     const T *mp = (const T *)a.m;
     int32_t flags = tgt ? a.it_flags[i] : IT_DONE;
-    const bool active = !(flags & IT_DONE);
+    bool active = !(flags & IT_DONE);
     const T h = active ? hp[i] : T(1);
+    // a particle whose support 2h left its list waits (state unchanged) for
+    // the list rebuild the host makes between sweep batches
+    bool waiting = false;
+    if (active && (double)(T(2) * h) > (double)a.cov[i]) {
+        waiting = true;
+        active = false;
+        atomicAdd(&a.cnt->n_uncovered, 1);
+    }
     const T hinv = T(1) / h;
     const int64_t off = a.goff[g];
     int width = a.gwidth[g];
@@ -188,10 +195,6 @@ __global__ void __launch_bounds__(DW * 32) k_density(DensArgs a)
                 a.it_hi[i] = hi;
                 hp[i] = hn;
                 if (conv) flags |= IT_FINAL;
-                if ((double)(2 * hn) > (double)a.cov[i]) {
-                    flags |= IT_UNCOVERED;
-                    atomicAdd(&a.cnt->n_uncovered, 1);
-                }
             }
         }
         if (done) {
@@ -205,9 +208,10 @@ __global__ void __launch_bounds__(DW * 32) k_density(DensArgs a)
         ((T *)a.rho)[i] = rho;
         ((T *)a.omega)[i] = drho;
         a.nnb[i] = cnt;
-        a.it_flags[i] = flags & ~IT_UNCOVERED;
+        a.it_flags[i] = flags;
         still = !done;
     }
+    if (waiting) still = true;
     int c = cnt;
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     const unsigned amask = __ballot_sync(0xffffffffu, active);
@@ -215,8 +219,20 @@ __global__ void __launch_bounds__(DW * 32) k_density(DensArgs a)
     if (lane == 0) {
         atomicAdd(&a.cnt->interactions, (unsigned long long)c);
         atomicAdd(&a.cnt->evaluations, (unsigned long long)__popc(amask));
-        if (smask) a.act_next[atomicAdd(&a.cnt->n_active_groups, 1)] = g;
+        if (smask) a.act_next[atomicAdd(a.act_next_count, 1)] = g;
     }
+}
+
+// One sweep: warps stride over the active groups, whose number is read on
+// the device, so sweeps can be queued without a host round trip.
+template <typename T, bool FP64POS>
+__global__ void __launch_bounds__(DW * 32) k_density(DensArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int n_act = *a.act_count;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && n_act > 0) atomicAdd(&a.cnt->sweeps_done, 1);
+    for (int gi = blockIdx.x * DW + (threadIdx.x >> 5); gi < n_act; gi += gridDim.x * DW)
+        density_group<T, FP64POS>(a, a.act[gi], lane);
 }
 
 template <typename T>
@@ -239,19 +255,21 @@ __global__ void k_iota_i32(int32_t *v, int64_t n)
     if (i < n) v[i] = (int32_t)i;
 }
 
-__global__ void k_reset_sweep(DevCounters *c)
-{
-    c->interactions = 0;
-    c->evaluations = 0;
-    c->n_active_groups = 0;
-    c->n_uncovered = 0;
-}
+// before a sweep: nothing active yet for the next one
+__global__ void k_begin_sweep(DevCounters *c, int next) { c->act_count[next] = 0; }
 
-__global__ void k_reset_status(DevCounters *c)
+__global__ void k_clear_uncovered(DevCounters *c) { c->n_uncovered = 0; }
+
+__global__ void k_reset_status(DevCounters *c, int n_groups)
 {
     c->n_not_conv = 0;
     c->n_hbounds = 0;
     c->err = 0;
+    c->interactions = 0;
+    c->evaluations = 0;
+    c->sweeps_done = 0;
+    c->n_uncovered = 0;
+    c->act_count[0] = n_groups;
 }
 
 // Ideal-gas EOS: P = (gamma-1) rho u, c = sqrt(gamma (gamma-1) u), and P/rho^2.
@@ -275,15 +293,14 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
     const int64_t n = p->n;
     const sph_params &q = ctx->prm;
     const int64_t launches0 = ctx->launches;
-    double kernel_ms = 0.0;
-    k_reset_status<<<1, 1, 0, s>>>(ctx->dcnt);
+    const int ng = (int)ctx->n_groups;
+    k_reset_status<<<1, 1, 0, s>>>(ctx->dcnt, ng);
+    SPH_CHECK_LAUNCH();
     k_dens_init<T><<<grid_for(n, 256), 256, 0, s>>>((T *)p->h, (const T *)seed, n, q.fixed_h, ctx->it_flags,
                                                      ctx->it_sweeps, ctx->it_lo, ctx->it_hi);
     SPH_CHECK_LAUNCH();
     SPH_TRY(lists_build(ctx, p, s));
-    int builds = 1;
-    int n_act = (int)ctx->n_groups;
-    k_iota_i32<<<grid_for(n_act, 256), 256, 0, s>>>(ctx->act_groups[0], n_act);
+    k_iota_i32<<<grid_for(ng, 256), 256, 0, s>>>(ctx->act_groups[0], ng);
     SPH_CHECK_LAUNCH();
     DensArgs a{};
     a.group_begin = ctx->group_begin;
@@ -302,49 +319,62 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
     a.eta3 = q.eta * q.eta * q.eta;
     a.h_tol = q.h_tol; a.h_min = q.h_min; a.h_max = q.h_max;
     a.cnt = ctx->dcnt;
-    int cur = 0, sweeps = 0;
-    int64_t inter = 0, evals = 0;
+    // sweeps are queued in batches without a host round trip: each reads the
+    // number of active groups left by the previous one on the device.  A
+    // particle whose 2h outgrew its list sits out (unchanged) until the host
+    // rebuilds the lists at the end of the batch.
+    const unsigned grid = std::min<unsigned>(grid_for(ng, DW), (unsigned)ctx->num_sms * 16u);
+    const int max_launch = 4 * (q.max_sweeps + 2);
+    const int batch = q.fixed_h ? 1 : 4;
+    int cur = 0, launched = 0, rebuilds = 0;
     for (;;) {
-        k_reset_sweep<<<1, 1, 0, s>>>(ctx->dcnt);
-        a.act = ctx->act_groups[cur];
-        a.act_next = ctx->act_groups[cur ^ 1];
-        a.n_act = n_act;
-        SPH_CUDA(cudaEventRecord(ctx->kev[0], s));
-        if (ctx->fp64) k_density<T, true><<<grid_for(n_act, DW), DW * 32, 0, s>>>(a);
-        else k_density<T, false><<<grid_for(n_act, DW), DW * 32, 0, s>>>(a);
-        SPH_CHECK_LAUNCH();
-        SPH_CUDA(cudaEventRecord(ctx->kev[1], s));
-        ++sweeps;
-        SPH_TRY(sync_counters(ctx, s));
-        {
-            float f = 0.f;
-            SPH_CUDA(cudaEventElapsedTime(&f, ctx->kev[0], ctx->kev[1]));
-            kernel_ms += f;
+        for (int j = 0; j < batch && launched < max_launch; ++j) {
+            k_begin_sweep<<<1, 1, 0, s>>>(ctx->dcnt, cur ^ 1);
+            SPH_CHECK_LAUNCH();
+            a.act = ctx->act_groups[cur];
+            a.act_count = &ctx->dcnt->act_count[cur];
+            a.act_next = ctx->act_groups[cur ^ 1];
+            a.act_next_count = &ctx->dcnt->act_count[cur ^ 1];
+            if (launched < 64) SPH_CUDA(cudaEventRecord(ctx->kev[2 * launched], s));
+            if (ctx->fp64) k_density<T, true><<<grid, DW * 32, 0, s>>>(a);
+            else k_density<T, false><<<grid, DW * 32, 0, s>>>(a);
+            SPH_CHECK_LAUNCH();
+            if (launched < 64) SPH_CUDA(cudaEventRecord(ctx->kev[2 * launched + 1], s));
+            cur ^= 1;
+            ++launched;
         }
-        inter += (int64_t)ctx->hcnt->interactions;
-        evals += (int64_t)ctx->hcnt->evaluations;
+        SPH_TRY(sync_counters(ctx, s));
         if (ctx->hcnt->err & (ERRB_LIST_CAPACITY | ERRB_STACK))
             return sph_fail(ctx, SPH_ERR_CAPACITY, "sph_density: neighbour-list capacity exceeded");
-        n_act = ctx->hcnt->n_active_groups;
-        if (n_act == 0 || sweeps > q.max_sweeps + 1) break;
+        if (ctx->hcnt->act_count[cur] == 0 || launched >= max_launch) break;
         if (ctx->hcnt->n_uncovered > 0) {
             SPH_TRY(lists_build(ctx, p, s));
-            ++builds;
+            k_clear_uncovered<<<1, 1, 0, s>>>(ctx->dcnt);
+            SPH_CHECK_LAUNCH();
+            ++rebuilds;
         }
-        cur ^= 1;
+    }
+    double kernel_ms = 0.0;
+    for (int k = 0; k < launched && k < 64; ++k) {
+        float f = 0.f;
+        SPH_CUDA(cudaEventElapsedTime(&f, ctx->kev[2 * k], ctx->kev[2 * k + 1]));
+        kernel_ms += f;
     }
     SPH_TRY(eos_run(ctx, p, p->u, s));
     if (st) {
-        st->sweeps = sweeps;
-        st->list_builds = builds;
+        st->sweeps = ctx->hcnt->sweeps_done;
+        st->list_builds = 1 + rebuilds;
         st->n_unconverged = ctx->hcnt->n_not_conv;
         st->n_hbounds = ctx->hcnt->n_hbounds;
-        st->interactions = inter;
+        st->interactions = (int64_t)ctx->hcnt->interactions;
         st->list_entries = (int64_t)ctx->hcnt->list_total;
-        st->evaluations = evals;
+        st->evaluations = (int64_t)ctx->hcnt->evaluations;
         st->kernel_ms = kernel_ms;
         st->launches = ctx->launches - launches0;
     }
+    if (ctx->hcnt->act_count[cur] > 0)
+        return sph_fail(ctx, SPH_ERR_NOT_CONVERGED, "sph_density: sweep budget exhausted with " +
+                                                        std::to_string(ctx->hcnt->act_count[cur]) + " groups active");
     if (ctx->hcnt->n_not_conv > 0)
         return sph_fail(ctx, SPH_ERR_NOT_CONVERGED, "sph_density: h iteration reached max_sweeps for " +
                                                         std::to_string(ctx->hcnt->n_not_conv) + " particles");

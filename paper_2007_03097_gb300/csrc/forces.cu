@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(FW * 32) k_forces(ForceArgs a)
         ((T *)a.vsig)[i] = vs;
     }
     for (int o = 16; o > 0; o >>= 1) nint += __shfl_xor_sync(0xffffffffu, nint, o);
-    if (lane == 0) atomicAdd(&a.cnt->interactions, (unsigned long long)nint);
+    if (lane == 0) atomicAdd(&a.cnt->force_interactions, (unsigned long long)nint);
 }
 
 
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
         ((double *)a.vsig)[i] = df_to_double(vs);
     }
     for (int o = 16; o > 0; o >>= 1) nint += __shfl_xor_sync(0xffffffffu, nint, o);
-    if (lane == 0) atomicAdd(&a.cnt->interactions, (unsigned long long)nint);
+    if (lane == 0) atomicAdd(&a.cnt->force_interactions, (unsigned long long)nint);
 }
 
 __device__ __forceinline__ float2 split2(double v)
@@ -293,11 +293,7 @@ __global__ void k_pr2(const T *__restrict__ P, const T *__restrict__ rho, int64_
     if (i < n) { const T r = rho[i]; pr2[i] = P[i] / (r * r); }
 }
 
-__global__ void k_reset_inter(DevCounters *c)
-{
-    c->interactions = 0;
-    c->err = 0;
-}
+__global__ void k_reset_inter(DevCounters *c) { c->force_interactions = 0; }
 
 template <typename T>
 int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, const void *vz,
@@ -332,26 +328,33 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
     a.L = ctx->dom[3];
     a.alpha = ctx->prm.alpha; a.beta = ctx->prm.beta; a.eps = ctx->prm.eps_visc;
     a.cnt = ctx->dcnt;
-    SPH_CUDA(cudaEventRecord(ctx->kev[2], s));
+    SPH_CUDA(cudaEventRecord(ctx->ev[5], s));
     if (ctx->fp64) k_forces_df<<<grid_for(ctx->n_groups, FW), FW * 32, 0, s>>>(a);
     else k_forces<T, false><<<grid_for(ctx->n_groups, FW), FW * 32, 0, s>>>(a);
     SPH_CHECK_LAUNCH();
-    SPH_CUDA(cudaEventRecord(ctx->kev[3], s));
+    SPH_CUDA(cudaEventRecord(ctx->ev[6], s));
+    ctx->force_launches = ctx->launches - launches0;
     if (st) {
         SPH_TRY(sync_counters(ctx, s));
-        float f = 0.f;
-        SPH_CUDA(cudaEventElapsedTime(&f, ctx->kev[2], ctx->kev[3]));
-        st->kernel_ms = f;
-        st->launches = ctx->launches - launches0;
-        st->interactions = (int64_t)ctx->hcnt->interactions;
-        st->list_entries = (int64_t)ctx->hcnt->list_total;
-        if (ctx->hcnt->err & (ERRB_LIST_CAPACITY | ERRB_STACK))
-            return sph_fail(ctx, SPH_ERR_CAPACITY, "sph_forces: neighbour-list capacity exceeded");
+        SPH_TRY(forces_collect(ctx, st));
     }
     return SPH_OK;
 }
 
 }  // namespace
+
+int forces_collect(sph_ctx *ctx, sph_force_stats *st)
+{
+    float f = 0.f;
+    SPH_CUDA(cudaEventElapsedTime(&f, ctx->ev[5], ctx->ev[6]));
+    st->kernel_ms = f;
+    st->launches = ctx->force_launches;
+    st->interactions = (int64_t)ctx->hcnt->force_interactions;
+    st->list_entries = (int64_t)ctx->hcnt->list_total;
+    if (ctx->hcnt->err & (ERRB_LIST_CAPACITY | ERRB_STACK))
+        return sph_fail(ctx, SPH_ERR_CAPACITY, "sph_forces: neighbour-list capacity exceeded");
+    return SPH_OK;
+}
 
 // reuse_lists: the lists of the h iteration that just ended still cover 2h
 // of every particle (sph_step); otherwise they are rebuilt for the current h.

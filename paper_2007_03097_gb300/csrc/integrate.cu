@@ -100,13 +100,22 @@ __global__ void k_totals_partial(const T *__restrict__ m, const T *__restrict__ 
     }
 }
 
+// Block partials combined in a fixed order: warp k sums quantity k over the
+// partials with a strided loop and a shuffle tree (deterministic).
 __global__ void k_totals_final(const double *__restrict__ part, int nb, DevCounters *cnt)
 {
-    if (threadIdx.x >= NT) return;
-    double v = part[threadIdx.x];
-    for (int b = 1; b < nb; ++b) v = threadIdx.x < 8 ? v + part[b * NT + threadIdx.x] : fmin(v, part[b * NT + threadIdx.x]);
-    if (threadIdx.x < 8) cnt->totals[threadIdx.x] = v;
-    else cnt->min_dt = v;
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (k >= NT) return;
+    double v = k < 8 ? 0.0 : DBL_MAX;
+    for (int b = lane; b < nb; b += 32) v = k < 8 ? v + part[b * NT + k] : fmin(v, part[b * NT + k]);
+    for (int o = 16; o > 0; o >>= 1) {
+        const double w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = k < 8 ? v + w : fmin(v, w);
+    }
+    if (lane == 0) {
+        if (k < 8) cnt->totals[k] = v;
+        else cnt->min_dt = v;
+    }
 }
 
 template <typename T>
@@ -150,7 +159,7 @@ int totals_impl(sph_ctx *ctx, const sph_particles *p, const void *pvx, const voi
                                            (const T *)p->dudt, (const T *)pvx, (const T *)pvy, (const T *)pvz,
                                            (const T *)p->h, (const T *)p->vsig, p->n, ctx->red);
     SPH_CHECK_LAUNCH();
-    k_totals_final<<<1, 32, 0, s>>>(ctx->red, nb, ctx->dcnt);
+    k_totals_final<<<1, 32 * NT, 0, s>>>(ctx->red, nb, ctx->dcnt);
     SPH_CHECK_LAUNCH();
     return SPH_OK;
 }

@@ -311,7 +311,7 @@ int build_impl(sph_ctx *ctx, cudaStream_t s)
     return SPH_OK;
 }
 
-// coverage radius of each particle's density list: 2 h (1 + skin), rounded down
+// coverage radius of each particle's list: 2 h (1 + skin), rounded down
 template <typename T>
 __global__ void k_coverage(const T *__restrict__ h, int64_t n, double f, float *__restrict__ cov)
 {

@@ -29,7 +29,6 @@ enum : int32_t {
     IT_FINAL = 2,         // h converged; next evaluation is the final one
     IT_NOT_CONV = 4,
     IT_H_BOUNDS = 8,
-    IT_UNCOVERED = 16,    // 2h exceeds the list coverage radius
 };
 
 // Device-side counters, mirrored into pinned host memory at sync points.
@@ -38,8 +37,7 @@ struct DevCounters {
     unsigned long long evaluations;    // particle evaluations of the last sweep
     unsigned long long list_total;     // list slots of the last build
     uint32_t err;
-    int32_t n_active_groups;           // groups with a particle not yet done
-    int32_t n_uncovered;               // particles whose 2h left the coverage
+    int32_t n_uncovered;               // evaluations skipped: 2h outgrew the list
     int32_t n_not_conv;
     int32_t n_hbounds;
     int32_t n_leaves;
@@ -49,7 +47,10 @@ struct DevCounters {
     double totals[8];                  // conserved totals
     double min_dt;                     // min h / vsig
     float loss;
-    int32_t pad;
+    int32_t sweeps_done;               // sweeps that evaluated at least one particle
+    int32_t act_count[2];              // active groups read / written by the sweeps
+    int32_t pad2[2];
+    unsigned long long force_interactions;
 };
 
 struct sph_ctx {
@@ -135,6 +136,7 @@ struct sph_ctx {
     cudaEvent_t ev[8] = {};
     cudaEvent_t kev[2 * 64] = {};       // per-sweep density kernel events
     int64_t launches = 0;               // kernels launched so far
+    int64_t force_launches = 0;         // kernels of the last force pass
 };
 
 // ------------------------------------------------------------------ helpers
@@ -272,6 +274,8 @@ int eos_run(sph_ctx *ctx, sph_particles *p, const void *u, cudaStream_t s);
 // forces.cu
 int forces_run(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, const void *vz,
                sph_force_stats *st, bool reuse_lists, cudaStream_t s);
+// after a sync_counters that follows a forces_run with st == nullptr
+int forces_collect(sph_ctx *ctx, sph_force_stats *st);
 // integrate.cu
 int kick_drift(sph_ctx *ctx, sph_particles *p, double dt, cudaStream_t s);
 int predict(sph_ctx *ctx, sph_particles *p, double dt, cudaStream_t s);
