@@ -119,7 +119,7 @@ def run_sph(args):
     build.build()
     w = inputs.sedov(args.n_side)
     params = dict(w.params)
-    params.update(hnet_batch=32768, hnet_iters=1, hnet_lr=1e-3)
+    params.update(hnet_batch=8192, hnet_iters=1, hnet_lr=1e-3)
     ctx = B.Context(params, w.n)
     p = B.Particles.from_workload(w, fp64=True)
     stream = torch.cuda.current_stream()

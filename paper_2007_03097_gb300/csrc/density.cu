@@ -114,20 +114,19 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                     const double dz = sep_d(a.z[i], a.z[b], a.periodic, L, hl);
                     if (!(r2_d(dx, dy, dz) < thr)) continue;
                 }
-                const df dx = df_sep(A.x, A.y, P.x, P.y, wx, Ld);
-                const df dy = df_sep(A.z, A.w, P.z, P.w, wy, Ld);
-                const df dz = df_sep(Bz.x, Bz.y, Q.x, Q.y, wz, Ld);
-                const df r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
-                const df q = df_mul(df_sqrt(r2), hinv_df);
+                const df dx = df_sep_fast(A.x, A.y, P.x, P.y, wx, Ld);
+                const df dy = df_sep_fast(A.z, A.w, P.z, P.w, wy, Ld);
+                const df dz = df_sep_fast(Bz.x, Bz.y, Q.x, Q.y, wz, Ld);
+                const df q = df_mul(df_sqrt_fast(df_norm2(dx, dy, dz)), hinv_df);
                 df w, g3;
                 df_kern_w_g3(a.kernel, q, w, g3);
                 const df mb = df{Q.z, Q.w};
-                sw = df_add(sw, df_mul(mb, w));
-                sd = df_add(sd, df_mul(mb, g3));
+                df_acc(sw, df_mul(mb, w));
+                df_acc(sd, df_mul(mb, g3));
                 ++cnt;
             }
-            sum_w = (T)df_to_double(sw);
-            sum_dh = (T)df_to_double(sd);
+            sum_w = (T)df_to_double(df_norm(sw));
+            sum_dh = (T)df_to_double(df_norm(sd));
         } else {
             const float xah = a.xh[i], xal = a.xl[i], yah = a.yh[i], yal = a.yl[i], zah = a.zh[i], zal = a.zl[i];
             const float L = (float)a.L, half = 0.5f * L;
@@ -161,6 +160,7 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
         const T h3i = hinv * hinv * hinv;
         const T rho = sig * h3i * sum_w;
         const T drho = -sig * h3i * hinv * sum_dh;
+        const T meta3 = ma * (T)a.eta3;
         const int sweeps = a.it_sweeps[i] + 1;
         a.it_sweeps[i] = sweeps;
         bool done = false;
@@ -168,15 +168,14 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
         if (flags & IT_FINAL) {
             done = true;
         } else {
-            const T eta3 = (T)a.eta3;
-            const T f = ma * eta3 / (h * h * h) - rho;
+            const T f = meta3 * h3i - rho;
             if (f == T(0)) {
                 done = true;
             } else if (sweeps >= a.max_sweeps) {
                 done = true;
                 flags |= IT_NOT_CONV;
             } else {
-                const T fp = T(-3) * ma * eta3 / (h * h * h * h) - drho;
+                const T fp = T(-3) * meta3 * h3i * hinv - drho;
                 double lo = a.it_lo[i], hi = a.it_hi[i];
                 if (f > T(0)) { if ((double)h > lo) lo = (double)h; }
                 else { if ((double)h < hi) hi = (double)h; }

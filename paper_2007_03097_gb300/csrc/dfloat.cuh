@@ -105,6 +105,64 @@ __device__ __forceinline__ bool df_lt0(df a) { return a.hi < 0.f || (a.hi == 0.f
 
 __device__ __forceinline__ bool df_gt(df a, df b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
 
+// Faster variants for the pair loops: hardware approximations (about 22
+// correct bits) refined by one correction step, about 2^-44 relative error.
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ df df_sqrt_fast(df a)
+{
+    if (!(a.hi > 0.f)) return df{0.f, 0.f};
+    const float t = rsqrt_approx(a.hi);
+    const float y = __fmul_rn(a.hi, t);
+    const df y2 = two_prod(y, y);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, y2.hi), y2.lo), a.lo);
+    return fast_two_sum(y, __fmul_rn(r, __fmul_rn(0.5f, t)));
+}
+
+__device__ __forceinline__ df df_rcp_fast(df a)
+{
+    const float y = rcp_approx(a.hi);
+    const float e = __fmaf_rn(-a.lo, y, __fmaf_rn(-a.hi, y, 1.f));     // 1 - a y
+    return fast_two_sum(y, __fmul_rn(y, e));
+}
+
+// dx^2 + dy^2 + dz^2: exact squares of the high parts, cross terms in FP32
+__device__ __forceinline__ df df_norm2(df x, df y, df z)
+{
+    const df px = two_prod(x.hi, x.hi), py = two_prod(y.hi, y.hi), pz = two_prod(z.hi, z.hi);
+    const df s1 = two_sum(px.hi, py.hi);
+    const df s2 = two_sum(s1.hi, pz.hi);
+    float lo = __fadd_rn(__fadd_rn(px.lo, py.lo), pz.lo);
+    lo = __fmaf_rn(__fmul_rn(2.f, x.hi), x.lo, lo);
+    lo = __fmaf_rn(__fmul_rn(2.f, y.hi), y.lo, lo);
+    lo = __fmaf_rn(__fmul_rn(2.f, z.hi), z.lo, lo);
+    lo = __fadd_rn(lo, __fadd_rn(s1.lo, s2.lo));
+    return fast_two_sum(s2.hi, lo);
+}
+
+// accumulator update acc += x without renormalising acc (lo collects the
+// rounding errors of hi; renormalise with fast_two_sum when done)
+__device__ __forceinline__ void df_acc(df &acc, df x)
+{
+    const df s = two_sum(acc.hi, x.hi);
+    acc.hi = s.hi;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, x.lo));
+}
+
+__device__ __forceinline__ df df_norm(df a) { return fast_two_sum(a.hi, a.lo); }
+
 // conversions (FP64 pipe; keep them out of inner loops)
 __device__ __forceinline__ df df_from_double(double d)
 {
@@ -113,6 +171,17 @@ __device__ __forceinline__ df df_from_double(double d)
 }
 
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+// x_a - x_b from two-float positions with a minimum-image shift: the exact
+// difference of the high parts plus the difference of the low parts
+__device__ __forceinline__ df df_sep_fast(float ah, float al, float bh, float bl, int wrap, df L)
+{
+    df d = two_sum(ah, -bh);
+    d = fast_two_sum(d.hi, __fadd_rn(d.lo, __fsub_rn(al, bl)));
+    if (wrap > 0) d = df_add(d, L);
+    else if (wrap < 0) d = df_sub(d, L);
+    return d;
+}
 
 // ------------------------------------------------------------------ pair helpers
 // Separation x_a - x_b from two-float positions as a double-float, with the

@@ -208,38 +208,38 @@ __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
             if (!in_f && !in_d) continue;
         }
         const float4 Cb = a.srcC[b], Eb = a.srcE[b], Fb = a.srcF[b];
-        const df dx = df_sep(A.x, A.y, P.x, P.y, wx, Ld);
-        const df dy = df_sep(A.z, A.w, P.z, P.w, wy, Ld);
-        const df dz = df_sep(Bz.x, Bz.y, Q.x, Q.y, wz, Ld);
-        const df r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
-        const df r = df_sqrt(r2);
-        const df rinv = df_rcp(r);
+        const df dx = df_sep_fast(A.x, A.y, P.x, P.y, wx, Ld);
+        const df dy = df_sep_fast(A.z, A.w, P.z, P.w, wy, Ld);
+        const df dz = df_sep_fast(Bz.x, Bz.y, Q.x, Q.y, wz, Ld);
+        const df r2 = df_norm2(dx, dy, dz);
+        const df r = df_sqrt_fast(r2);
+        const df rinv = df_rcp_fast(r);
         const df vabx = df_sub(vxa, df{Cb.x, Cb.y}), vaby = df_sub(vya, df{Cb.z, Cb.w}), vabz = df_sub(vza, df{Db.x, Db.y});
         const df vdotr = df_add(df_add(df_mul(vabx, dx), df_mul(vaby, dy)), df_mul(vabz, dz));
         const df mb = df{Q.z, Q.w};
         if (in_d) {
             const df dwq = df_kern_dw(a.kernel, df_mul(r, hainv));
-            dv = df_add(dv, df_mul(df_mul(mb, df_mul(sig_hai4, dwq)), df_mul(rinv, vdotr)));
+            df_acc(dv, df_mul(df_mul(mb, df_mul(sig_hai4, dwq)), df_mul(rinv, vdotr)));
         }
         if (in_f) {
             const df hb = df{Db.z, Db.w};
             const df hab = df_scale(df_add(ha, hb), 0.5f);
-            const df habinv = df_rcp(hab);
+            const df habinv = df_rcp_fast(hab);
             const df dwq = df_kern_dw(a.kernel, df_mul(r, habinv));
             const df hi2 = df_sqr(habinv);
             const df gr = df_mul(df_mul(sig, df_sqr(hi2)), df_mul(dwq, rinv));     // grad_a W = gr r_ab
             df Pi = df{0.f, 0.f};
             if (df_lt0(vdotr)) {
-                const df mu = df_mul(df_mul(hab, vdotr), df_rcp(df_add(r2, df_mul(eps, df_sqr(hab)))));
+                const df mu = df_mul(df_mul(hab, vdotr), df_rcp_fast(df_add(r2, df_mul(eps, df_sqr(hab)))));
                 const df cbar = df_scale(df_add(ca, df{Fb.x, Fb.y}), 0.5f);
                 const df rbar = df_scale(df_add(rhoa, df{Eb.x, Eb.y}), 0.5f);
-                Pi = df_mul(df_add(df_neg(df_mul(df_mul(alpha, cbar), mu)), df_mul(beta, df_sqr(mu))), df_rcp(rbar));
+                Pi = df_mul(df_add(df_neg(df_mul(df_mul(alpha, cbar), mu)), df_mul(beta, df_sqr(mu))), df_rcp_fast(rbar));
             }
             const df coef = df_mul(mb, df_mul(df_add(df_add(pra, df{Eb.z, Eb.w}), Pi), gr));
-            accx = df_sub(accx, df_mul(coef, dx));
-            accy = df_sub(accy, df_mul(coef, dy));
-            accz = df_sub(accz, df_mul(coef, dz));
-            du = df_add(du, df_mul(df_mul(mb, df_add(pra, df_scale(Pi, 0.5f))), df_mul(gr, vdotr)));
+            df_acc(accx, df_neg(df_mul(coef, dx)));
+            df_acc(accy, df_neg(df_mul(coef, dy)));
+            df_acc(accz, df_neg(df_mul(coef, dz)));
+            df_acc(du, df_mul(df_mul(mb, df_add(pra, df_scale(Pi, 0.5f))), df_mul(gr, vdotr)));
             const df vr = df_mul(vdotr, rinv);
             df sg = df_add(ca, df{Fb.x, Fb.y});
             if (df_lt0(vr)) sg = df_sub(sg, df_mul_f(vr, 3.f));
@@ -248,11 +248,11 @@ __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
         }
     }
     if (tgt) {
-        ((double *)a.ax)[i] = df_to_double(accx);
-        ((double *)a.ay)[i] = df_to_double(accy);
-        ((double *)a.az)[i] = df_to_double(accz);
-        ((double *)a.dudt)[i] = df_to_double(du);
-        ((double *)a.divv)[i] = -df_to_double(dv) / ((const double *)a.rho)[i];
+        ((double *)a.ax)[i] = df_to_double(df_norm(accx));
+        ((double *)a.ay)[i] = df_to_double(df_norm(accy));
+        ((double *)a.az)[i] = df_to_double(df_norm(accz));
+        ((double *)a.dudt)[i] = df_to_double(df_norm(du));
+        ((double *)a.divv)[i] = -df_to_double(df_norm(dv)) / ((const double *)a.rho)[i];
         ((double *)a.vsig)[i] = df_to_double(vs);
     }
     for (int o = 16; o > 0; o >>= 1) nint += __shfl_xor_sync(0xffffffffu, nint, o);

@@ -51,11 +51,14 @@ __global__ void k_features(const T *__restrict__ h, const T *__restrict__ hprev,
 }
 
 // ---------------------------------------------------------------- inference
-// One thread per sample.  The 64 layer-2 pre-activations stay in registers;
-// layer-1 units are produced one at a time and scattered into them through
-// the transposed W2 held in shared memory (float4 broadcast reads).
-__global__ void __launch_bounds__(256) k_infer(const __nv_bfloat16 *__restrict__ wb, const float *__restrict__ f,
-                                               int64_t nb, float *__restrict__ y)
+// One thread per sample.  Half of the 64 layer-2 pre-activations at a time
+// stay in registers; the layer-1 units are recomputed for each half (5 FMAs
+// each) and scattered into them through the transposed W2 held in shared
+// memory (float4 broadcast reads).
+constexpr int HALF = H / 2;
+
+__global__ void __launch_bounds__(256, 3) k_infer(const __nv_bfloat16 *__restrict__ wb, const float *__restrict__ f,
+                                                  int64_t nb, float *__restrict__ y)
 {
     __shared__ __align__(16) float w[NP + 3];
     for (int k = threadIdx.x; k < NP; k += blockDim.x) {
@@ -71,28 +74,31 @@ __global__ void __launch_bounds__(256) k_infer(const __nv_bfloat16 *__restrict__
         float x[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) x[k] = f[5 * s + k];
-        float z2[H];
-#pragma unroll
-        for (int j = 0; j < H; ++j) z2[j] = w[O_B2 + j];
-#pragma unroll 1
-        for (int k = 0; k < H; ++k) {
-            float z = w[O_B1 + k];
-#pragma unroll
-            for (int c = 0; c < 5; ++c) z += w[O_W1 + 5 * k + c] * x[c];
-            const float a = z * sigm(z);
-            const float4 *col = reinterpret_cast<const float4 *>(w + O_W2 + H * k);
-#pragma unroll
-            for (int j = 0; j < H / 4; ++j) {
-                const float4 r = col[j];
-                z2[4 * j] += r.x * a;
-                z2[4 * j + 1] += r.y * a;
-                z2[4 * j + 2] += r.z * a;
-                z2[4 * j + 3] += r.w * a;
-            }
-        }
         float out = w[O_B3];
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            float z2[HALF];
 #pragma unroll
-        for (int j = 0; j < H; ++j) out += w[O_W3 + j] * (z2[j] * sigm(z2[j]));
+            for (int j = 0; j < HALF; ++j) z2[j] = w[O_B2 + half * HALF + j];
+#pragma unroll 1
+            for (int k = 0; k < H; ++k) {
+                float z = w[O_B1 + k];
+#pragma unroll
+                for (int c = 0; c < 5; ++c) z += w[O_W1 + 5 * k + c] * x[c];
+                const float a = z * sigm(z);
+                const float4 *col = reinterpret_cast<const float4 *>(w + O_W2 + H * k + half * HALF);
+#pragma unroll
+                for (int j = 0; j < HALF / 4; ++j) {
+                    const float4 r = col[j];
+                    z2[4 * j] += r.x * a;
+                    z2[4 * j + 1] += r.y * a;
+                    z2[4 * j + 2] += r.z * a;
+                    z2[4 * j + 3] += r.w * a;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < HALF; ++j) out += w[O_W3 + half * HALF + j] * (z2[j] * sigm(z2[j]));
+        }
         y[s] = x[3] * out;                      // s = f3 * y
     }
 }

@@ -56,14 +56,13 @@ template <bool FILL>
 __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
 {
     __shared__ int32_t s_stack[LW][STACK];
-    __shared__ float s_src[LW][7][TILE];
-    __shared__ int32_t s_idx[LW][TILE];
+    __shared__ float4 s_pa[LW][TILE], s_pb[LW][TILE];   // {xh, xl, yh, yl}, {zh, zl, cov, index}
+    __shared__ int32_t s_lb[LW][32], s_incl[LW][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int g = blockIdx.x * LW + w;
     if (g >= a.n_groups) return;
     int32_t *stack = s_stack[w];
-    float(*src)[TILE] = s_src[w];
-    int32_t *sidx = s_idx[w];
+    float4 *pa = s_pa[w], *pb = s_pb[w];
 
     const int gb = a.group_begin[g], ge = a.group_begin[g + 1];
     const bool tgt = lane < ge - gb;
@@ -87,12 +86,13 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
 
     auto process = [&](int ns) {
         for (int k = 0; k < ns; ++k) {
-            const int b = sidx[k];
-            float dx = sep_f(PA.x, PA.y, src[0][k], src[1][k], a.periodic, a.L, a.half);
-            float dy = sep_f(PA.z, PA.w, src[2][k], src[3][k], a.periodic, a.L, a.half);
-            float dz = sep_f(PB.x, PB.y, src[4][k], src[5][k], a.periodic, a.L, a.half);
+            const float4 qa = pa[k], qb = pb[k];
+            const int b = __float_as_int(qb.w);
+            float dx = sep_f(PA.x, PA.y, qa.x, qa.y, a.periodic, a.L, a.half);
+            float dy = sep_f(PA.z, PA.w, qa.z, qa.w, a.periodic, a.L, a.half);
+            float dz = sep_f(PB.x, PB.y, qb.x, qb.y, a.periodic, a.L, a.half);
             float r2 = (dx * dx + dy * dy) + dz * dz;
-            const float c = fmaxf(ca, src[6][k]);
+            const float c = fmaxf(ca, qb.z);
             if (tgt && b != ia && r2 <= c * c * (1.f + MARGIN)) {
                 if (FILL && count < width) a.nbl[off + (int64_t)count * 32 + lane] = (uint32_t)b;
                 ++count;
@@ -116,9 +116,9 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
         __syncwarp();
         bool acc = false;
         const bool leaf = node < 0;
+        float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
         if (lane < take) {
             const int id = node & 0x7fffffff;
-            float4 lo, hi;
             if (leaf) { lo = a.leaf_lo[id]; hi = a.leaf_hi[id]; }
             else { lo = a.node_lo[id]; hi = a.node_hi[id]; }
             const float r = fmaxf(qcov, lo.w);
@@ -141,32 +141,67 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
         sp += 2 * __popc(mint);
         if (sp > STACK) { overflow = true; sp = 0; }
         __syncwarp();
-        unsigned mleaf = __ballot_sync(0xffffffffu, acc && leaf);
-        while (mleaf) {
-            const int l = __ffs(mleaf) - 1;
-            mleaf &= mleaf - 1;
-            const int id = __shfl_sync(0xffffffffu, node, l) & 0x7fffffff;
-            const int lb = a.leaf_begin[id], le = a.leaf_begin[id + 1];
-            const int cnt = le - lb;
-            if (lane < cnt) {
-                const int j = lb + lane;
+        // per-target culling: keep an accepted leaf only if some target of
+        // the group is within max(cov_target, cov of the leaf) of its box
+        bool keep = false;
+        for (unsigned m = __ballot_sync(0xffffffffu, acc && leaf); m; m &= m - 1) {
+            const int l = __ffs(m) - 1;
+            const float lx = __shfl_sync(0xffffffffu, lo.x, l), ly = __shfl_sync(0xffffffffu, lo.y, l);
+            const float lz = __shfl_sync(0xffffffffu, lo.z, l), lc = __shfl_sync(0xffffffffu, lo.w, l);
+            const float hx = __shfl_sync(0xffffffffu, hi.x, l), hy = __shfl_sync(0xffffffffu, hi.y, l);
+            const float hz = __shfl_sync(0xffffffffu, hi.z, l);
+            float gx = fmaxf(0.f, axis_gap(PA.x, PA.x, lx, hx, a.periodic, a.L, a.half) - a.slack);
+            float gy = fmaxf(0.f, axis_gap(PA.z, PA.z, ly, hy, a.periodic, a.L, a.half) - a.slack);
+            float gz = fmaxf(0.f, axis_gap(PB.x, PB.x, lz, hz, a.periodic, a.L, a.half) - a.slack);
+            const float r = fmaxf(ca, lc);
+            const bool need = tgt && (gx * gx + gy * gy) + gz * gz <= r * r * (1.f + MARGIN);
+            if (__any_sync(0xffffffffu, need) && lane == l) keep = true;
+        }
+        // particles of all kept leaves, loaded in warp-wide waves: lane L
+        // owns a leaf range [lb, lb + cnt) placed at [incl - cnt, incl) of
+        // the step's item sequence
+        int lb = 0, cnt = 0;
+        if (keep) {
+            const int id = node & 0x7fffffff;
+            lb = a.leaf_begin[id];
+            cnt = a.leaf_begin[id + 1] - lb;
+        }
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        s_lb[w][lane] = lb;
+        s_incl[w][lane] = incl;
+        __syncwarp();
+        for (int base = 0; base < total; base += 32) {
+            const int item = base + lane;
+            const int take2 = min(32, total - base);
+            if (lane < take2) {
+                // owner: first lane whose inclusive end exceeds item
+                int lo2 = 0, hi2 = 31;
+                while (lo2 < hi2) {
+                    const int mid = (lo2 + hi2) >> 1;
+                    if (s_incl[w][mid] > item) hi2 = mid; else lo2 = mid + 1;
+                }
+                const int start = lo2 > 0 ? s_incl[w][lo2 - 1] : 0;       // exclusive start of the owner
+                const int j = s_lb[w][lo2] + (item - start);
                 const int t = ns + lane;
                 const float4 qa = a.srcA[j], qb = a.srcB[j];
-                src[0][t] = qa.x; src[1][t] = qa.y;
-                src[2][t] = qa.z; src[3][t] = qa.w;
-                src[4][t] = qb.x; src[5][t] = qb.y;
-                src[6][t] = a.cov[j];
-                sidx[t] = j;
+                pa[t] = qa;
+                pb[t] = make_float4(qb.x, qb.y, a.cov[j], __int_as_float(j));
             }
-            ns += cnt;
+            ns += take2;
             __syncwarp();
             if (ns >= 32) {
                 process(32);
                 __syncwarp();
                 const int rest = ns - 32;
                 if (lane < rest) {
-                    for (int c = 0; c < 7; ++c) src[c][lane] = src[c][32 + lane];
-                    sidx[lane] = sidx[32 + lane];
+                    pa[lane] = pa[32 + lane];
+                    pb[lane] = pb[32 + lane];
                 }
                 ns = rest;
                 __syncwarp();
