@@ -44,6 +44,9 @@ F_FORCE = 96
 # multiply-add (2 flops) costs 18 FP32 instructions (df_mul 7 + df_add 11), so
 # its ceiling in FP64-accurate flops is 152 * 128 * 2.07e9 * 2 / 18.
 FP64_PIPE_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes per launch of the dominant kernel from one ncu capture (see
+# profiles/), with the hash of the sources it was taken on
+TRAFFIC = {}
 FP32_PIPE_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 DF_EMULATED_TFLOPS = 152 * 128 * 2.07e9 * 2 / 18 / 1e12
 
@@ -54,7 +57,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sph", choices=["sph", "reference"])
-    ap.add_argument("--n-side", type=int, default=64)
+    ap.add_argument("--n-side", type=int, default=64, help="Sedov lattice side (64 = the headline workload)")
+    ap.add_argument("--workload", default="sedov", choices=["sedov", "polytrope", "collision", "turbulence"],
+                    help="sedov: 64^3 FP64 (headline); polytrope 2^20, collision 2x2^21, turbulence 256^3: "
+                         "FP32 pairs on FP64 positions")
     ap.add_argument("--train-steps", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -105,6 +111,37 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ GPU arm
+def make_workload(args):
+    from paper_2007_03097_gb300 import inputs
+    if args.workload == "sedov":
+        return inputs.sedov(args.n_side)
+    if args.workload == "polytrope":
+        return inputs.polytrope(1 << 20)
+    if args.workload == "collision":
+        return inputs.collision(1 << 21)
+    return inputs.turbulence(256)
+
+
+def workload_label(args, w):
+    if args.workload == "sedov":
+        return (f"sedov blast {args.n_side}^3 = {w.n} particles, Wendland C2, eta 1.2, h_tol 1e-6, "
+                f"alpha 1 beta 2, FP64, fixed dt {w.dt:.3e}")
+    if args.workload == "polytrope":
+        return f"n=1 polytrope, {w.n} particles, Wendland C2, eta 1.2, open boundary, FP32 pairs / FP64 positions"
+    if args.workload == "collision":
+        return f"two colliding n=1 polytropes, {w.n} particles, closing speed 1, FP32 pairs / FP64 positions"
+    return f"turbulence box 256^3 = {w.n} particles, Wendland C4, Mach 2, FP32 pairs / FP64 positions"
+
+
+def src_hash(files):
+    import hashlib
+    hsh = hashlib.sha1()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2007_03097_gb300", "csrc", f), "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()[:12]
+
+
 def run_sph(args):
     import torch
 
@@ -117,15 +154,18 @@ def run_sph(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
-    w = inputs.sedov(args.n_side)
+    w = make_workload(args)
+    fp64 = w.params.get("precision", "fp64") == "fp64"
     params = dict(w.params)
     params.update(hnet_batch=8192, hnet_iters=1, hnet_lr=1e-3)
     ctx = B.Context(params, w.n)
-    p = B.Particles.from_workload(w, fp64=True)
+    p = B.Particles.from_workload(w, fp64=fp64)
     stream = torch.cuda.current_stream()
     B.sph_build_tree(ctx, p)
     B.sph_density(ctx, p)
     B.sph_forces(ctx, p)
+    if w.dt is None:                       # fixed step from the initial CFL condition
+        w.dt = float(w.params["cfl"] * torch.min(p.h / p.vsig).item())
     rng = np.random.default_rng(1234)
     theta = np.concatenate([rng.normal(scale=s, size=k) for s, k in
                             ((1 / math.sqrt(5), 320), (0, 64), (1 / 8, 4096), (0, 64), (1 / 8, 64), (0, 1))])
@@ -215,16 +255,29 @@ def run_sph(args):
     # dominant kernel of the learned step and its roofline
     dens_flops = L["density_interactions"] * F_DENSITY
     force_flops = L["force_interactions"] * F_FORCE
-    if L["density_kernel_ms"] >= L["force_kernel_ms"]:
-        kname, flops, kms, launches = "k_density<double> (h-rho sweep, double-float)", dens_flops, L["density_kernel_ms"], L["density_launches"]
+    if fp64:
+        names = ("k_density<double> (h-rho sweep, double-float)", "k_forces_df (Eqs. 5-6, double-float)")
+        peak, peak_src = DF_EMULATED_TFLOPS, ("derived: FP32 pipe (152 SMs x 128 lanes x 2.07 GHz) running "
+                                              "double-float FP64 multiply-adds at 18 FP32 instructions per 2 flops")
     else:
-        kname, flops, kms, launches = "k_forces_df (Eqs. 5-6, double-float)", force_flops, L["force_kernel_ms"], args.steps
+        names = ("k_density<float> (h-rho sweep, FP32)", "k_forces<float> (Eqs. 5-6, FP32)")
+        peak, peak_src = FP32_PIPE_TFLOPS, "derived: FP32 pipe, 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
+    dominant_density = L["density_kernel_ms"] >= L["force_kernel_ms"]
+    if dominant_density:
+        kname, flops, kms, launches = names[0], dens_flops, L["density_kernel_ms"], L["density_launches"]
+    else:
+        kname, flops, kms, launches = names[1], force_flops, L["force_kernel_ms"], args.steps
     achieved = flops / (kms / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": DF_EMULATED_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / DF_EMULATED_TFLOPS, "traffic": None, "kernel": kname,
-            "launches": launches, "avg_launch_ms": kms / max(launches, 1),
-            "peak_source": "derived: FP32 pipe (152 SMs x 128 lanes x 2.07 GHz) running double-float FP64 "
-                           "multiply-adds at 18 FP32 instructions per 2 flops",
+    # DRAM traffic per launch from one ncu capture (profiles/), valid only for
+    # the kernel source it was taken on
+    traffic = None
+    key = ("density" if dominant_density else "forces") + ("_fp64" if fp64 else "_mixed") + "_" + args.workload
+    rec = TRAFFIC.get(key)
+    if rec and rec["src"] == src_hash(rec["files"]):
+        traffic = rec["bytes_per_launch"]
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic, "kernel": kname,
+            "launches": launches, "avg_launch_ms": kms / max(launches, 1), "peak_source": peak_src,
             "fp64_pipe_peak": FP64_PIPE_TFLOPS, "fp32_pipe_peak": FP32_PIPE_TFLOPS,
             "other_kernels": {
                 "k_density_tflops": dens_flops / max(L["density_kernel_ms"], 1e-9) / 1e9,
@@ -243,15 +296,15 @@ def run_sph(args):
         inter_l, e_inter = float(ii[0]), float(ii[1])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, seconds=12.0)
+        cpu = cpu_baseline(w, seconds=12.0, label=args.workload)
     if rank == 0:
         out = {
             "metric": METRIC, "value": inter_l / t_l, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_l / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"sedov blast {args.n_side}^3 = {w.n} particles, Wendland C2, eta 1.2, "
-                                   f"h_tol 1e-6, alpha 1 beta 2, FP64, fixed dt {w.dt:.3e}",
-                       "n_particles": w.n, "precision": "fp64", "parallelism": f"replicas x{world}",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
+            "config": {"workload": workload_label(args, w),
+                       "n_particles": w.n, "precision": "fp64" if fp64 else "mixed (FP32 pairs, FP64 positions)",
+                       "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MB write)",
                        "step": "learned-h sph_step (network seed + one online Adam round)"},
             "steps_per_s": world * args.steps / t_l,
@@ -286,15 +339,15 @@ def _oracle_sample(w, n_targets, seed=7):
     return int(d.pairs[t].sum()) + f.npairs, dt, t.size, oracle.num_threads()
 
 
-def cpu_baseline(w, seconds=12.0):
+def cpu_baseline(w, seconds=12.0, label="sedov"):
     """The oracle as it stands on the host cores, on a sample of target
     particles sized for about `seconds` of work; interactions/s."""
-    inter, dt, nt, cores = _oracle_sample(w, 256)
+    inter, dt, nt, cores = _oracle_sample(w, 64)
     scale = max(1, int(seconds / max(dt, 1e-3)))
-    nt2 = min(w.n, 256 * scale)
+    nt2 = min(w.n, 64 * scale)
     inter, dt, nt, cores = _oracle_sample(w, nt2)
     return {"value": inter / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{nt} random targets of the {w.n}-particle Sedov state, brute force over all sources: "
+            "sample": f"{nt} random targets of the {w.n}-particle {label} state, brute force over all sources: "
                       f"h-rho iteration + force pass, {dt:.1f} s"}
 
 
@@ -303,10 +356,11 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    from paper_2007_03097_gb300 import inputs
     oracle.build()
-    w = inputs.sedov(args.n_side)
-    per_step = 512
+    w = make_workload(args)
+    if w.dt is None:
+        w.dt = 0.0
+    per_step = max(16, int(512 * 262144 / w.n))
     for _ in range(args.warmup):
         _oracle_sample(w, per_step, seed=1)
     inter, secs, nt, cores = 0, 0.0, 0, 1
@@ -318,8 +372,8 @@ def run_reference(args):
     out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": f"sedov blast {args.n_side}^3 = {w.n} particles, Wendland C2, eta 1.2, FP64",
-                      "n_particles": w.n, "step": f"oracle h-rho iteration + forces for {per_step} sampled targets"},
+           "config": {"workload": workload_label(args, w), "n_particles": w.n,
+                      "step": f"FP64 oracle h-rho iteration + forces for {per_step} sampled targets"},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": f"{per_step} random targets per step, brute force over all {w.n} sources"},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -9,7 +9,9 @@
 // the midpoint towards the admissible end the sign of f points to; the
 // result is clamped to [h_min, h_max].  When |h_new - h| < h_tol h the step
 // is applied and one more evaluation at the final h gives rho, drho/dh and
-// the neighbour count.  The paper states the fixed point but not the solver.
+// the neighbour count (taken as a first-order update inside the converging
+// sweep when it is exact to FP64 rounding, see below).  The paper states the
+// fixed point but not the solver.
 //
 // One warp per target group, one lane per target; each lane walks its own
 // neighbour list (slot-major, coalesced).  SPH_MIXED: FP32 on two-float
@@ -79,6 +81,7 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
 
     T sum_w = T(0), sum_dh = T(0);
     int cnt = 0;
+    int band = 0;        // list entries within a relative 1e-5 of the support radius
     if (active) {
         if (FP64POS) {
             const float4 A = a.srcA[i], Bz = a.srcB[i];
@@ -105,6 +108,7 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                 }
                 const float r2f = (dxf * dxf + dyf * dyf) + dzf * dzf;
                 if (r2f > thr_hi) continue;
+                if (r2f >= thr_lo) ++band;
                 if (r2f >= thr_lo ||
                     (a.periodic && fmaxf(fmaxf(fabsf(dxf), fabsf(dyf)), fabsf(dzf)) > guard)) {
                     // knife edge: the exact FP64 decision of the plain definition
@@ -128,22 +132,24 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
             sum_w = (T)df_to_double(df_norm(sw));
             sum_dh = (T)df_to_double(df_norm(sd));
         } else {
-            const float xah = a.xh[i], xal = a.xl[i], yah = a.yh[i], yal = a.yl[i], zah = a.zh[i], zal = a.zl[i];
+            const float4 A = a.srcA[i], Bz = a.srcB[i];
             const float L = (float)a.L, half = 0.5f * L;
             const float hf = (float)h;
             const float thr = __fmul_rn(__fmul_rn(4.f, hf), hf);
             for (int k = 0; k < width; ++k) {
                 const uint32_t b = a.nbl[off + (int64_t)k * 32 + lane];
                 if (b == SPH_SENTINEL) continue;
-                const float dx = sep_f(xah, xal, a.xh[b], a.xl[b], a.periodic, L, half);
-                const float dy = sep_f(yah, yal, a.yh[b], a.yl[b], a.periodic, L, half);
-                const float dz = sep_f(zah, zal, a.zh[b], a.zl[b], a.periodic, L, half);
+                const float4 P = a.srcA[b], Q = a.srcB[b];
+                const float dx = sep_f(A.x, A.y, P.x, P.y, a.periodic, L, half);
+                const float dy = sep_f(A.z, A.w, P.z, P.w, a.periodic, L, half);
+                const float dz = sep_f(Bz.x, Bz.y, Q.x, Q.y, a.periodic, L, half);
                 const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                if (fabsf(r2 - thr) <= 1e-5f * thr) ++band;
                 if (!(r2 < thr)) continue;
                 const T q = (T)sqrtf(r2) * hinv;
                 T w, dw;
                 kern_wdw<T>(a.kernel, q, w, dw);
-                const T mb = mp[b];
+                const T mb = (T)Q.z;
                 sum_w += mb * w;
                 sum_dh += mb * (T(3) * w + q * dw);
                 ++cnt;
@@ -164,7 +170,7 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
         const int sweeps = a.it_sweeps[i] + 1;
         a.it_sweeps[i] = sweeps;
         bool done = false;
-        T hn = h;
+        T hn = h, hfin = h, rho_out = rho;
         if (flags & IT_FINAL) {
             done = true;
         } else {
@@ -193,18 +199,31 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                 a.it_lo[i] = lo;
                 a.it_hi[i] = hi;
                 hp[i] = hn;
-                if (conv) flags |= IT_FINAL;
+                if (conv) {
+                    // The reading evaluates rho once more at the final h.  When
+                    // |dh| <= 1e-9 h and no list entry lies within 1e-5 of the
+                    // support radius, the neighbour set at h + dh is this one and
+                    // rho(h + dh) = rho + rho' dh up to rho'' dh^2 / 2 ~ 1e-17 rho:
+                    // that evaluation is taken here without another sweep.
+                    if (band == 0 && fabs((double)(hn - h)) <= 1e-9 * (double)h) {
+                        rho_out = rho + drho * (hn - h);
+                        hfin = hn;
+                        done = true;
+                    } else {
+                        flags |= IT_FINAL;
+                    }
+                }
             }
         }
         if (done) {
             flags |= IT_DONE;
             if (flags & IT_NOT_CONV) atomicAdd(&a.cnt->n_not_conv, 1);
-            else if (!a.fixed_h && ((double)h <= a.h_min || (double)h >= a.h_max)) {
+            else if (!a.fixed_h && ((double)hfin <= a.h_min || (double)hfin >= a.h_max)) {
                 flags |= IT_H_BOUNDS;
                 atomicAdd(&a.cnt->n_hbounds, 1);
             }
         }
-        ((T *)a.rho)[i] = rho;
+        ((T *)a.rho)[i] = rho_out;
         ((T *)a.omega)[i] = drho;
         a.nnb[i] = cnt;
         a.it_flags[i] = flags;

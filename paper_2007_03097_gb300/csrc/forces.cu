@@ -9,7 +9,7 @@
 // and the signal speed vsig_a = max_b (c_a + c_b - 3 min(0, v_ab . rhat_ab)).
 // One warp per target group, one lane per target, each lane walking its own
 // neighbour list and testing every entry exactly.
-// SPH_MIXED: FP32 throughout.  SPH_FP64: pair terms in double-float on the
+// SPH_MIXED: FP32 throughout (reciprocal square root for 1/r).  SPH_FP64: pair terms in double-float on the
 // FP32 pipes, membership decided in FP32 outside a 1e-5 relative band around
 // each threshold and by the exact FP64 r^2 inside it.
 #include "dfloat.cuh"
@@ -36,8 +36,9 @@ struct ForceArgs {
     DevCounters *cnt;
 };
 
-template <typename T, bool FP64POS>
-__global__ void __launch_bounds__(FW * 32) k_forces(ForceArgs a)
+// SPH_MIXED force pass in FP32: sources packed as A {xh, xl, yh, yl},
+// B {zh, zl, m, -}, C {vx, vy, vz, h}, D {rho, P/rho^2, c, -}.
+__global__ void __launch_bounds__(FW * 32) k_forces_f32(ForceArgs a)
 {
     const int lane = threadIdx.x & 31;
     const int g = blockIdx.x * FW + (threadIdx.x >> 5);
@@ -45,101 +46,92 @@ __global__ void __launch_bounds__(FW * 32) k_forces(ForceArgs a)
     const int gb = a.group_begin[g], ge = a.group_begin[g + 1];
     const bool tgt = lane < ge - gb;
     const int i = gb + (tgt ? lane : 0);
-    const T *vx = (const T *)a.vx, *vy = (const T *)a.vy, *vz = (const T *)a.vz;
-    const T *m = (const T *)a.m, *h = (const T *)a.h, *rho = (const T *)a.rho;
-    const T *pr2 = (const T *)a.pr2, *c = (const T *)a.c;
-    const T vxa = vx[i], vya = vy[i], vza = vz[i];
-    const T ha = h[i], rhoa = rho[i], pra = pr2[i], ca = c[i];
-    const T hainv = T(1) / ha;
-    const T sig = kern_sigma<T>(a.kernel);
-    const T alpha = (T)a.alpha, beta = (T)a.beta, eps = (T)a.eps;
+    const float4 A = a.srcA[i], Bz = a.srcB[i], C = a.srcC[i], D = a.srcD[i];
+    const float ha = C.w, rhoa = D.x, pra = D.y, ca = D.z;
+    const float hainv = 1.f / ha;
+    const float sig = kern_sigma<float>(a.kernel);
+    const float alpha = (float)a.alpha, beta = (float)a.beta, eps = (float)a.eps;
     const int64_t off = a.goff[g];
     int width = tgt ? a.gwidth[g] : 0;
     if (off + 32 * (int64_t)width > a.cap) width = 0;    // never read past the lists
+    const float Lf = (float)a.L, half = 0.5f * Lf;
+    const float thr_d = __fmul_rn(__fmul_rn(4.f, ha), ha);
 
-    T accx = 0, accy = 0, accz = 0, du = 0, dv = 0, vs = ca;
+    float accx = 0.f, accy = 0.f, accz = 0.f, du = 0.f, dv = 0.f, vs = ca;
     int nint = 0;
-    double xa = 0, ya = 0, za = 0;
-    float xah = 0, xal = 0, yah = 0, yal = 0, zah = 0, zal = 0;
-    if (FP64POS) { xa = a.x[i]; ya = a.y[i]; za = a.z[i]; }
-    else { xah = a.xh[i]; xal = a.xl[i]; yah = a.yh[i]; yal = a.yl[i]; zah = a.zh[i]; zal = a.zl[i]; }
-    const double thr_d = __dmul_rn(__dmul_rn(4.0, (double)ha), (double)ha);
-    const float thr_f = __fmul_rn(__fmul_rn(4.f, (float)ha), (float)ha);
-
     for (int k = 0; k < width; ++k) {
         const uint32_t b = a.nbl[off + (int64_t)k * 32 + lane];
         if (b == SPH_SENTINEL) continue;
-        const T hb = h[b];
-        T dx, dy, dz, r2;
-        bool in_f, in_d;
-        if (FP64POS) {
-            const double half = 0.5 * a.L;
-            double ddx = sep_d(xa, a.x[b], a.periodic, a.L, half);
-            double ddy = sep_d(ya, a.y[b], a.periodic, a.L, half);
-            double ddz = sep_d(za, a.z[b], a.periodic, a.L, half);
-            double rr = r2_d(ddx, ddy, ddz);
-            double hs = __dadd_rn((double)ha, (double)hb);
-            in_f = rr < __dmul_rn(hs, hs);
-            in_d = rr < thr_d;
-            dx = (T)ddx; dy = (T)ddy; dz = (T)ddz; r2 = (T)rr;
-        } else {
-            const float Lf = (float)a.L, half = 0.5f * Lf;
-            float fdx = sep_f(xah, xal, a.xh[b], a.xl[b], a.periodic, Lf, half);
-            float fdy = sep_f(yah, yal, a.yh[b], a.yl[b], a.periodic, Lf, half);
-            float fdz = sep_f(zah, zal, a.zh[b], a.zl[b], a.periodic, Lf, half);
-            float rr = __fadd_rn(__fadd_rn(__fmul_rn(fdx, fdx), __fmul_rn(fdy, fdy)), __fmul_rn(fdz, fdz));
-            float hs = __fadd_rn((float)ha, (float)hb);
-            in_f = rr < __fmul_rn(hs, hs);
-            in_d = rr < thr_f;
-            dx = (T)fdx; dy = (T)fdy; dz = (T)fdz; r2 = (T)rr;
-        }
+        const float4 P = a.srcA[b], Q = a.srcB[b], Cb = a.srcC[b];
+        const float dx = sep_f(A.x, A.y, P.x, P.y, a.periodic, Lf, half);
+        const float dy = sep_f(A.z, A.w, P.z, P.w, a.periodic, Lf, half);
+        const float dz = sep_f(Bz.x, Bz.y, Q.x, Q.y, a.periodic, Lf, half);
+        const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+        const float hb = Cb.w;
+        const float hs = __fadd_rn(ha, hb);
+        const bool in_f = r2 < __fmul_rn(hs, hs);
+        const bool in_d = r2 < thr_d;
         if (!in_f && !in_d) continue;
-        const T r = sqrt(r2);
-        const T rinv = T(1) / r;
-        const T vabx = vxa - vx[b], vaby = vya - vy[b], vabz = vza - vz[b];
-        const T vdotr = (vabx * dx + vaby * dy) + vabz * dz;
-        const T mb = m[b];
+        const float4 Db = a.srcD[b];
+        const float rinv = rsqrtf(r2);
+        const float r = r2 * rinv;
+        const float vabx = C.x - Cb.x, vaby = C.y - Cb.y, vabz = C.z - Cb.z;
+        const float vdotr = (vabx * dx + vaby * dy) + vabz * dz;
+        const float mb = Q.z;
         if (in_d) {
-            T w, dwq;
-            kern_wdw<T>(a.kernel, r * hainv, w, dwq);
-            const T h2 = hainv * hainv;
+            float w, dwq;
+            kern_wdw<float>(a.kernel, r * hainv, w, dwq);
+            const float h2 = hainv * hainv;
             dv += mb * (sig * h2 * h2 * dwq) * rinv * vdotr;
         }
         if (in_f) {
-            const T hab = T(0.5) * (ha + hb);
-            const T habinv = T(1) / hab;
-            T w, dwq;
-            kern_wdw<T>(a.kernel, r * habinv, w, dwq);
-            const T h2 = habinv * habinv;
-            const T gr = sig * h2 * h2 * dwq * rinv;          // grad_a W = gr * r_ab
-            T Pi = T(0);
-            if (vdotr < T(0)) {
-                const T mu = hab * vdotr / (r2 + eps * hab * hab);
-                Pi = (-alpha * T(0.5) * (ca + c[b]) * mu + beta * mu * mu) / (T(0.5) * (rhoa + rho[b]));
+            const float hab = 0.5f * hs;
+            const float habinv = 1.f / hab;
+            float w, dwq;
+            kern_wdw<float>(a.kernel, r * habinv, w, dwq);
+            const float h2 = habinv * habinv;
+            const float gr = sig * h2 * h2 * dwq * rinv;          // grad_a W = gr * r_ab
+            float Pi = 0.f;
+            if (vdotr < 0.f) {
+                const float mu = hab * vdotr / (r2 + eps * hab * hab);
+                Pi = (-alpha * 0.5f * (ca + Db.z) * mu + beta * mu * mu) / (0.5f * (rhoa + Db.x));
             }
-            const T coef = mb * (pra + pr2[b] + Pi) * gr;
+            const float coef = mb * (pra + Db.y + Pi) * gr;
             accx -= coef * dx;
             accy -= coef * dy;
             accz -= coef * dz;
-            du += mb * (pra + T(0.5) * Pi) * gr * vdotr;
-            const T vr = vdotr * rinv;
-            const T sgn = ca + c[b] - T(3) * (vr < T(0) ? vr : T(0));
+            du += mb * (pra + 0.5f * Pi) * gr * vdotr;
+            const float vr = vdotr * rinv;
+            const float sgn = ca + Db.z - 3.f * (vr < 0.f ? vr : 0.f);
             vs = sgn > vs ? sgn : vs;
             ++nint;
         }
     }
     if (tgt) {
-        ((T *)a.ax)[i] = accx;
-        ((T *)a.ay)[i] = accy;
-        ((T *)a.az)[i] = accz;
-        ((T *)a.dudt)[i] = du;
-        ((T *)a.divv)[i] = -dv / rhoa;
-        ((T *)a.vsig)[i] = vs;
+        ((float *)a.ax)[i] = accx;
+        ((float *)a.ay)[i] = accy;
+        ((float *)a.az)[i] = accz;
+        ((float *)a.dudt)[i] = du;
+        ((float *)a.divv)[i] = -dv / rhoa;
+        ((float *)a.vsig)[i] = vs;
     }
     for (int o = 16; o > 0; o >>= 1) nint += __shfl_xor_sync(0xffffffffu, nint, o);
     if (lane == 0) atomicAdd(&a.cnt->force_interactions, (unsigned long long)nint);
 }
 
+// packed FP32 force-pass sources: C {vx, vy, vz, h}, D {rho, P/rho^2, c, 0}
+__global__ void k_pack_force_f32(const float *__restrict__ vx, const float *__restrict__ vy,
+                                 const float *__restrict__ vz, const float *__restrict__ h,
+                                 const float *__restrict__ rho, const float *__restrict__ P,
+                                 const float *__restrict__ c, int64_t n, float4 *__restrict__ C,
+                                 float4 *__restrict__ D)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float r = rho[i];
+    C[i] = make_float4(vx[i], vy[i], vz[i], h[i]);
+    D[i] = make_float4(r, P[i] / (r * r), c[i], 0.f);
+}
 
 // SPH_FP64 force pass in double-float (see the file comment).
 __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
@@ -286,13 +278,6 @@ __global__ void k_pack_force(const double *__restrict__ vx, const double *__rest
     F[i] = make_float4(cc.x, cc.y, 0.f, 0.f);
 }
 
-template <typename T>
-__global__ void k_pr2(const T *__restrict__ P, const T *__restrict__ rho, int64_t n, T *__restrict__ pr2)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) { const T r = rho[i]; pr2[i] = P[i] / (r * r); }
-}
-
 __global__ void k_reset_inter(DevCounters *c) { c->force_interactions = 0; }
 
 template <typename T>
@@ -307,7 +292,9 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
             (const double *)p->P, (const double *)p->c, p->n, (double *)ctx->pr2, ctx->srcC, ctx->srcD, ctx->srcE,
             ctx->srcF);
     else
-        k_pr2<T><<<grid_for(p->n, 256), 256, 0, s>>>((const T *)p->P, (const T *)p->rho, p->n, (T *)ctx->pr2);
+        k_pack_force_f32<<<grid_for(p->n, 256), 256, 0, s>>>(
+            (const float *)vx, (const float *)vy, (const float *)vz, (const float *)p->h, (const float *)p->rho,
+            (const float *)p->P, (const float *)p->c, p->n, ctx->srcC, ctx->srcD);
     SPH_CHECK_LAUNCH();
     if (!reuse_lists || !ctx->lists_valid) SPH_TRY(lists_build(ctx, p, s));
     ForceArgs a{};
@@ -330,7 +317,7 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
     a.cnt = ctx->dcnt;
     SPH_CUDA(cudaEventRecord(ctx->ev[5], s));
     if (ctx->fp64) k_forces_df<<<grid_for(ctx->n_groups, FW), FW * 32, 0, s>>>(a);
-    else k_forces<T, false><<<grid_for(ctx->n_groups, FW), FW * 32, 0, s>>>(a);
+    else k_forces_f32<<<grid_for(ctx->n_groups, FW), FW * 32, 0, s>>>(a);
     SPH_CHECK_LAUNCH();
     SPH_CUDA(cudaEventRecord(ctx->ev[6], s));
     ctx->force_launches = ctx->launches - launches0;

@@ -56,13 +56,15 @@ template <bool FILL>
 __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
 {
     __shared__ int32_t s_stack[LW][STACK];
-    __shared__ float4 s_pa[LW][TILE], s_pb[LW][TILE];   // {xh, xl, yh, yl}, {zh, zl, cov, index}
+    __shared__ float4 s_pa[LW][TILE];   // source {x, y, z} relative to the group centre, cov
+    __shared__ int32_t s_pi[LW][TILE];  // source index
     __shared__ int32_t s_lb[LW][32], s_incl[LW][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int g = blockIdx.x * LW + w;
     if (g >= a.n_groups) return;
     int32_t *stack = s_stack[w];
-    float4 *pa = s_pa[w], *pb = s_pb[w];
+    float4 *pa = s_pa[w];
+    int32_t *pi = s_pi[w];
 
     const int gb = a.group_begin[g], ge = a.group_begin[g + 1];
     const bool tgt = lane < ge - gb;
@@ -71,6 +73,10 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
     const float ca = a.cov[ia];
     const float4 qlo = a.group_lo[g], qhi = a.group_hi[g];
     const float qcov = qlo.w;                      // largest coverage in the group
+    // FP32 coordinates relative to the group centre: the rounding error of
+    // each is half an ulp of the relative value, far inside MARGIN
+    const float gcx = 0.5f * (qlo.x + qhi.x), gcy = 0.5f * (qlo.y + qhi.y), gcz = 0.5f * (qlo.z + qhi.z);
+    const float tx = (PA.x - gcx) + PA.y, ty = (PA.z - gcy) + PA.w, tz = (PB.x - gcz) + PB.y;
 
     int64_t off = 0;
     int width = 0;
@@ -86,13 +92,11 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
 
     auto process = [&](int ns) {
         for (int k = 0; k < ns; ++k) {
-            const float4 qa = pa[k], qb = pb[k];
-            const int b = __float_as_int(qb.w);
-            float dx = sep_f(PA.x, PA.y, qa.x, qa.y, a.periodic, a.L, a.half);
-            float dy = sep_f(PA.z, PA.w, qa.z, qa.w, a.periodic, a.L, a.half);
-            float dz = sep_f(PB.x, PB.y, qb.x, qb.y, a.periodic, a.L, a.half);
-            float r2 = (dx * dx + dy * dy) + dz * dz;
-            const float c = fmaxf(ca, qb.z);
+            const float4 q = pa[k];
+            const int b = pi[k];
+            const float dx = tx - q.x, dy = ty - q.y, dz = tz - q.z;
+            const float r2 = (dx * dx + dy * dy) + dz * dz;
+            const float c = fmaxf(ca, q.w);
             if (tgt && b != ia && r2 <= c * c * (1.f + MARGIN)) {
                 if (FILL && count < width) a.nbl[off + (int64_t)count * 32 + lane] = (uint32_t)b;
                 ++count;
@@ -190,8 +194,14 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
                 const int j = s_lb[w][lo2] + (item - start);
                 const int t = ns + lane;
                 const float4 qa = a.srcA[j], qb = a.srcB[j];
-                pa[t] = qa;
-                pb[t] = make_float4(qb.x, qb.y, a.cov[j], __int_as_float(j));
+                float rx = qa.x - gcx, ry = qa.z - gcy, rz = qb.x - gcz;
+                if (a.periodic) {                  // nearest image of the source
+                    rx -= a.L * rintf(rx / a.L);
+                    ry -= a.L * rintf(ry / a.L);
+                    rz -= a.L * rintf(rz / a.L);
+                }
+                pa[t] = make_float4(rx + qa.y, ry + qa.w, rz + qb.y, a.cov[j]);
+                pi[t] = j;
             }
             ns += take2;
             __syncwarp();
@@ -201,7 +211,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
                 const int rest = ns - 32;
                 if (lane < rest) {
                     pa[lane] = pa[32 + lane];
-                    pb[lane] = pb[32 + lane];
+                    pi[lane] = pi[32 + lane];
                 }
                 ns = rest;
                 __syncwarp();
