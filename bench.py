@@ -57,7 +57,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sph", choices=["sph", "reference"])
-    ap.add_argument("--n-side", type=int, default=64, help="Sedov lattice side (64 = the headline workload)")
+    ap.add_argument("--n-side", type=int, default=None,
+                    help="lattice side of the sedov (default 64, the headline workload) and turbulence (default 256) "
+                         "workloads; smaller sides serve profiling captures")
     ap.add_argument("--workload", default="sedov", choices=["sedov", "polytrope", "collision", "turbulence"],
                     help="sedov: 64^3 FP64 (headline); polytrope 2^20, collision 2x2^21, turbulence 256^3: "
                          "FP32 pairs on FP64 positions")
@@ -114,23 +116,23 @@ class ClockSampler:
 def make_workload(args):
     from paper_2007_03097_gb300 import inputs
     if args.workload == "sedov":
-        return inputs.sedov(args.n_side)
+        return inputs.sedov(args.n_side or 64)
     if args.workload == "polytrope":
         return inputs.polytrope(1 << 20)
     if args.workload == "collision":
         return inputs.collision(1 << 21)
-    return inputs.turbulence(256)
+    return inputs.turbulence(args.n_side or 256)
 
 
 def workload_label(args, w):
     if args.workload == "sedov":
-        return (f"sedov blast {args.n_side}^3 = {w.n} particles, Wendland C2, eta 1.2, h_tol 1e-6, "
+        return (f"sedov blast {args.n_side or 64}^3 = {w.n} particles, Wendland C2, eta 1.2, h_tol 1e-6, "
                 f"alpha 1 beta 2, FP64, fixed dt {w.dt:.3e}")
     if args.workload == "polytrope":
         return f"n=1 polytrope, {w.n} particles, Wendland C2, eta 1.2, open boundary, FP32 pairs / FP64 positions"
     if args.workload == "collision":
         return f"two colliding n=1 polytropes, {w.n} particles, closing speed 1, FP32 pairs / FP64 positions"
-    return f"turbulence box 256^3 = {w.n} particles, Wendland C4, Mach 2, FP32 pairs / FP64 positions"
+    return f"turbulence box {args.n_side or 256}^3 = {w.n} particles, Wendland C4, Mach 2, FP32 pairs / FP64 positions"
 
 
 def src_hash(files):
@@ -260,7 +262,7 @@ def run_sph(args):
         peak, peak_src = DF_EMULATED_TFLOPS, ("derived: FP32 pipe (152 SMs x 128 lanes x 2.07 GHz) running "
                                               "double-float FP64 multiply-adds at 18 FP32 instructions per 2 flops")
     else:
-        names = ("k_density<float> (h-rho sweep, FP32)", "k_forces<float> (Eqs. 5-6, FP32)")
+        names = ("k_density<float> (h-rho sweep, FP32)", "k_forces_f32 (Eqs. 5-6, FP32)")
         peak, peak_src = FP32_PIPE_TFLOPS, "derived: FP32 pipe, 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
     dominant_density = L["density_kernel_ms"] >= L["force_kernel_ms"]
     if dominant_density:
@@ -294,6 +296,8 @@ def run_sph(args):
         ii = torch.tensor([inter_l, e_inter], device="cuda", dtype=torch.float64)
         dist.all_reduce(ii, op=dist.ReduceOp.SUM)
         inter_l, e_inter = float(ii[0]), float(ii[1])
+    lists = B.sph_list_info(ctx)
+    lists["slots_per_particle"] = lists["slots_used"] / w.n
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, seconds=12.0, label=args.workload)
@@ -313,6 +317,7 @@ def run_sph(args):
             "e2e": {"value": e_inter / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
                     "steps_per_s": world * args.steps / e2e_s},
             "gpu_launches": L["launches"],
+            "neighbour_lists": lists,
             "roofline": roof,
             "clocks": clk,
             "cpu_baseline": cpu,

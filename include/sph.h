@@ -84,7 +84,10 @@ typedef struct {
     double h_min, h_max; /* clamp of the h iteration                            */
     double skin;         /* density lists cover 2h (1 + skin); >= 0             */
     double rho_ref;      /* density scale of the h-predictor feature log(h/hbar) */
-    int64_t nb_capacity; /* neighbour-list entries to reserve; 0 = 256 n_max    */
+    int64_t nb_capacity; /* neighbour-list slots to reserve; 0 = 640 n_max.  A
+                            build sizes each list by the particles of the leaves
+                            within reach and, when those bounds exceed the
+                            capacity, by exact counts from then on            */
     double hnet_lr;      /* Adam learning rate of online h-predictor training   */
     int32_t hnet_batch;  /* samples per online training step (strided subset)   */
     int32_t hnet_iters;  /* Adam steps per sph_step when training online        */
@@ -214,6 +217,14 @@ int sph_sort_keys(sph_ctx *ctx, int64_t n, const uint64_t *keys, const uint32_t 
 
 /* After sph_build_tree: number of leaves and of target groups (host out). */
 int sph_tree_info(sph_ctx *ctx, int64_t *n_leaves, int64_t *n_groups);
+
+/* Neighbour-list storage of the last list build, as of the last call that
+ * returned (host out, each may be NULL): slots reserved (32 x the per-group
+ * widths the build sized: leaf bounds, or exact counts once exact_sizing is
+ * set), slots holding the exact lists, and whether exact sizing is on (set
+ * for the rest of the context's life when leaf bounds exceeded nb_capacity).
+ * Implementation detail of the list builder; the paper has no counterpart. */
+int sph_list_info(sph_ctx *ctx, int64_t *slots_reserved, int64_t *slots_used, int32_t *exact_sizing);
 
 /* After sph_build_tree: leaf_begin (device, n_leaves + 1 entries, the last is
  * n) and level (device, n_leaves; octree level of each leaf cell). */

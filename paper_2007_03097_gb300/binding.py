@@ -77,7 +77,7 @@ class sph_step_stats(_c.Structure):
 
 EXPORTED = ["sph_create", "sph_destroy", "sph_set_params", "sph_last_error", "sph_version", "sph_build_tree",
             "sph_density", "sph_forces", "sph_step", "sph_totals", "sph_morton_keys", "sph_sort_keys",
-            "sph_tree_info", "sph_export_leaves", "sph_neighbors", "sph_hnet_set_weights",
+            "sph_tree_info", "sph_list_info", "sph_export_leaves", "sph_neighbors", "sph_hnet_set_weights",
             "sph_hnet_get_weights", "sph_hnet_features", "sph_hnet_infer", "sph_hnet_grad",
             "sph_hnet_train_step", "sph_sort_keys_noalloc"]
 SPH_SORT_NOALLOC_MAX = 262144
@@ -112,6 +112,7 @@ def load(path: str | None = None):
         "sph_morton_keys": ([V, _c.POINTER(sph_particles), V, _c.POINTER(_c.c_double), V], I32),
         "sph_sort_keys": ([V, I64, V, V, V, V], I32),
         "sph_tree_info": ([V, _c.POINTER(I64), _c.POINTER(I64)], I32),
+        "sph_list_info": ([V, _c.POINTER(I64), _c.POINTER(I64), _c.POINTER(I32)], I32),
         "sph_export_leaves": ([V, V, V, V], I32),
         "sph_neighbors": ([V, _c.POINTER(sph_particles), I32, V, V, V, V], I32),
         "sph_hnet_set_weights": ([V, V, I64], I32),
@@ -350,6 +351,14 @@ def sph_tree_info(ctx: Context):
     nl, ng = _c.c_int64(), _c.c_int64()
     _check(ctx, load().sph_tree_info(ctx.handle, _c.byref(nl), _c.byref(ng)))
     return int(nl.value), int(ng.value)
+
+
+def sph_list_info(ctx: Context) -> dict:
+    """Neighbour-list slots reserved and used by the last build, and whether
+    the context sizes lists by exact counts."""
+    r, u, e = _c.c_int64(), _c.c_int64(), _c.c_int32()
+    _check(ctx, load().sph_list_info(ctx.handle, _c.byref(r), _c.byref(u), _c.byref(e)))
+    return {"slots_reserved": int(r.value), "slots_used": int(u.value), "exact_sizing": bool(e.value)}
 
 
 def sph_export_leaves(ctx: Context, stream=None):

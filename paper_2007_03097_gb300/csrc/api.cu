@@ -121,7 +121,7 @@ int allocate(sph_ctx *c, int64_t N)
     for (float **s : split) SPH_TRY(alloc(c, s, N + 32));
     float4 **packs[] = {&c->srcA, &c->srcB, &c->srcC, &c->srcD, &c->srcE, &c->srcF};
     for (float4 **s : packs) SPH_TRY(alloc(c, s, N));
-    c->nbl_cap = c->prm.nb_capacity > 0 ? c->prm.nb_capacity : 256 * N;
+    c->nbl_cap = c->prm.nb_capacity > 0 ? c->prm.nb_capacity : 640 * N;
     SPH_TRY(alloc(c, &c->nbl, (size_t)c->nbl_cap));
     SPH_TRY(alloc(c, &c->group_width, N));
     SPH_TRY(alloc(c, &c->group_off, N + 1));
@@ -133,7 +133,8 @@ int allocate(sph_ctx *c, int64_t N)
     SPH_TRY(alloc(c, &c->act_groups[0], N));
     SPH_TRY(alloc(c, &c->act_groups[1], N));
     double **d8[] = {(double **)&c->vpx, (double **)&c->vpy, (double **)&c->vpz, (double **)&c->upred,
-                     (double **)&c->pr2, (double **)&c->hold, (double **)&c->hseed};
+                     (double **)&c->pr2, (double **)&c->hold, (double **)&c->hseed,
+                     (double **)&c->hstart};
     for (double **d : d8) SPH_TRY(alloc(c, d, N));
     c->gbuf_bytes = 24 * (((size_t)N * 8 + 255) & ~(size_t)255);
     SPH_TRY(alloc(c, &c->gbuf, c->gbuf_bytes));
@@ -175,7 +176,7 @@ void release(sph_ctx *c)
                     c->node_lo, c->node_hi, c->xh, c->xl, c->yh, c->yl, c->zh, c->zl, c->srcA, c->srcB,
                     c->srcC, c->srcD, c->srcE, c->srcF, c->nbl, c->group_width,
                     c->group_off, c->it_lo, c->it_hi, c->it_flags, c->it_sweeps, c->cov, c->act_groups[0],
-                    c->act_groups[1], c->vpx, c->vpy, c->vpz, c->upred, c->pr2, c->hold, c->hseed, c->gbuf,
+                    c->act_groups[1], c->vpx, c->vpy, c->vpz, c->upred, c->pr2, c->hold, c->hseed, c->hstart, c->gbuf,
                     c->scan_tmp, c->red, c->dcnt, c->hn_master, c->hn_bf16, c->hn_m, c->hn_v, c->hn_grad,
                     c->hn_part, c->feats, c->hn_y, c->hn_sample};
     for (void *p : ptrs)
@@ -189,13 +190,13 @@ void release(sph_ctx *c)
 
 inline cudaStream_t S(void *stream) { return (cudaStream_t)stream; }
 
+}  // namespace
+
 int copy_field(sph_ctx *ctx, void *dst, const void *src, int64_t n, cudaStream_t s)
 {
     SPH_CUDA(cudaMemcpyAsync(dst, src, (size_t)n * (ctx->fp64 ? 8 : 4), cudaMemcpyDeviceToDevice, s));
     return SPH_OK;
 }
-
-}  // namespace
 
 extern "C" {
 
@@ -402,6 +403,15 @@ int sph_tree_info(sph_ctx *ctx, int64_t *n_leaves, int64_t *n_groups)
     if (!ctx->tree_valid) return sph_fail(ctx, SPH_ERR_STATE, "no tree: call sph_build_tree first");
     if (n_leaves) *n_leaves = ctx->n_leaves;
     if (n_groups) *n_groups = ctx->n_groups;
+    return SPH_OK;
+}
+
+int sph_list_info(sph_ctx *ctx, int64_t *slots_reserved, int64_t *slots_used, int32_t *exact_sizing)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    if (slots_reserved) *slots_reserved = (int64_t)ctx->hcnt->list_total;
+    if (slots_used) *slots_used = (int64_t)ctx->hcnt->list_used;
+    if (exact_sizing) *exact_sizing = ctx->lists_exact ? 1 : 0;
     return SPH_OK;
 }
 

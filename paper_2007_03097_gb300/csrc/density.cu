@@ -35,6 +35,7 @@ struct DensArgs {
     const int32_t *act_count;      // ... and their number (device)
     int32_t *act_next;             // groups still active after it ...
     int32_t *act_next_count;       // ... and their number (zeroed before the sweep)
+    int32_t *work;                 // group claim counter (zeroed before the sweep)
     const int32_t *group_begin;
     const int64_t *goff;
     const int32_t *gwidth;
@@ -93,10 +94,8 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
             const df Ld = df_from_double(a.L);
             const df hinv_df = df_from_double((double)hinv);
             df sw = df{0.f, 0.f}, sd = df{0.f, 0.f};
-            for (int k = 0; k < width; ++k) {
-                const uint32_t b = a.nbl[off + (int64_t)k * 32 + lane];
-                if (b == SPH_SENTINEL) continue;
-                const float4 P = a.srcA[b], Q = a.srcB[b];
+            walk_list<true>(a.nbl, off, width, lane, (uint32_t)i, a.srcA, a.srcB,
+                            [&](uint32_t b, const float4 &P, const float4 &Q) {
                 float dxf = (A.x - P.x) + (A.y - P.y);
                 float dyf = (A.z - P.z) + (A.w - P.w);
                 float dzf = (Bz.x - Q.x) + (Bz.y - Q.y);
@@ -107,7 +106,7 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                     if (dzf > half) { dzf -= Lf; wz = -1; } else if (dzf < -half) { dzf += Lf; wz = 1; }
                 }
                 const float r2f = (dxf * dxf + dyf * dyf) + dzf * dzf;
-                if (r2f > thr_hi) continue;
+                if (r2f > thr_hi) return;
                 if (r2f >= thr_lo) ++band;
                 if (r2f >= thr_lo ||
                     (a.periodic && fmaxf(fmaxf(fabsf(dxf), fabsf(dyf)), fabsf(dzf)) > guard)) {
@@ -116,7 +115,7 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                     const double dx = sep_d(a.x[i], a.x[b], a.periodic, L, hl);
                     const double dy = sep_d(a.y[i], a.y[b], a.periodic, L, hl);
                     const double dz = sep_d(a.z[i], a.z[b], a.periodic, L, hl);
-                    if (!(r2_d(dx, dy, dz) < thr)) continue;
+                    if (!(r2_d(dx, dy, dz) < thr)) return;
                 }
                 const df dx = df_sep_fast(A.x, A.y, P.x, P.y, wx, Ld);
                 const df dy = df_sep_fast(A.z, A.w, P.z, P.w, wy, Ld);
@@ -128,7 +127,7 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                 df_acc(sw, df_mul(mb, w));
                 df_acc(sd, df_mul(mb, g3));
                 ++cnt;
-            }
+            });
             sum_w = (T)df_to_double(df_norm(sw));
             sum_dh = (T)df_to_double(df_norm(sd));
         } else {
@@ -136,16 +135,14 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
             const float L = (float)a.L, half = 0.5f * L;
             const float hf = (float)h;
             const float thr = __fmul_rn(__fmul_rn(4.f, hf), hf);
-            for (int k = 0; k < width; ++k) {
-                const uint32_t b = a.nbl[off + (int64_t)k * 32 + lane];
-                if (b == SPH_SENTINEL) continue;
-                const float4 P = a.srcA[b], Q = a.srcB[b];
+            walk_list<false>(a.nbl, off, width, lane, (uint32_t)i, a.srcA, a.srcB,
+                             [&](uint32_t, const float4 &P, const float4 &Q) {
                 const float dx = sep_f(A.x, A.y, P.x, P.y, a.periodic, L, half);
                 const float dy = sep_f(A.z, A.w, P.z, P.w, a.periodic, L, half);
                 const float dz = sep_f(Bz.x, Bz.y, Q.x, Q.y, a.periodic, L, half);
                 const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
                 if (fabsf(r2 - thr) <= 1e-5f * thr) ++band;
-                if (!(r2 < thr)) continue;
+                if (!(r2 < thr)) return;
                 const T q = (T)sqrtf(r2) * hinv;
                 T w, dw;
                 kern_wdw<T>(a.kernel, q, w, dw);
@@ -153,7 +150,7 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                 sum_w += mb * w;
                 sum_dh += mb * (T(3) * w + q * dw);
                 ++cnt;
-            }
+            });
         }
     }
 
@@ -241,16 +238,23 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
     }
 }
 
-// One sweep: warps stride over the active groups, whose number is read on
-// the device, so sweeps can be queued without a host round trip.
+// One sweep over the active groups, whose number is read on the device, so
+// sweeps can be queued without a host round trip.  The grid is sized to the
+// resident blocks; each warp claims its next group from a counter, so groups
+// of unequal list widths balance across the SMs.
 template <typename T, bool FP64POS>
 __global__ void __launch_bounds__(DW * 32) k_density(DensArgs a)
 {
     const int lane = threadIdx.x & 31;
     const int n_act = *a.act_count;
     if (blockIdx.x == 0 && threadIdx.x == 0 && n_act > 0) atomicAdd(&a.cnt->sweeps_done, 1);
-    for (int gi = blockIdx.x * DW + (threadIdx.x >> 5); gi < n_act; gi += gridDim.x * DW)
+    for (;;) {
+        int gi = 0;
+        if (lane == 0) gi = atomicAdd(a.work, 1);
+        gi = __shfl_sync(0xffffffffu, gi, 0);
+        if (gi >= n_act) break;
         density_group<T, FP64POS>(a, a.act[gi], lane);
+    }
 }
 
 template <typename T>
@@ -274,7 +278,11 @@ __global__ void k_iota_i32(int32_t *v, int64_t n)
 }
 
 // before a sweep: nothing active yet for the next one
-__global__ void k_begin_sweep(DevCounters *c, int next) { c->act_count[next] = 0; }
+__global__ void k_begin_sweep(DevCounters *c, int next)
+{
+    c->act_count[next] = 0;
+    c->work[next ^ 1] = 0;
+}
 
 __global__ void k_clear_uncovered(DevCounters *c) { c->n_uncovered = 0; }
 
@@ -305,8 +313,24 @@ __global__ void k_eos(const T *__restrict__ rho, const T *__restrict__ u, int64_
     pr2[i] = p / (r * r);
 }
 
+// resident blocks per SM of the sweep kernel (from the occupancy calculator)
 template <typename T>
-int run_impl(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats *st, cudaStream_t s)
+unsigned resident_blocks(bool fp64pos)
+{
+    static int cached[2] = {0, 0};
+    int &c = cached[fp64pos ? 1 : 0];
+    if (c == 0) {
+        int nb = 0;
+        const cudaError_t e = fp64pos
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_density<T, true>, DW * 32, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_density<T, false>, DW * 32, 0);
+        c = (e == cudaSuccess && nb > 0) ? nb : 8;
+    }
+    return (unsigned)c;
+}
+
+template <typename T>
+int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats *st, cudaStream_t s)
 {
     const int64_t n = p->n;
     const sph_params &q = ctx->prm;
@@ -341,7 +365,7 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
     // number of active groups left by the previous one on the device.  A
     // particle whose 2h outgrew its list sits out (unchanged) until the host
     // rebuilds the lists at the end of the batch.
-    const unsigned grid = std::min<unsigned>(grid_for(ng, DW), (unsigned)ctx->num_sms * 16u);
+    const unsigned grid = std::min<unsigned>(grid_for(ng, DW), (unsigned)ctx->num_sms * resident_blocks<T>(ctx->fp64));
     const int max_launch = 4 * (q.max_sweeps + 2);
     const int batch = q.fixed_h ? 1 : 4;
     int cur = 0, launched = 0, rebuilds = 0;
@@ -353,6 +377,7 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
             a.act_count = &ctx->dcnt->act_count[cur];
             a.act_next = ctx->act_groups[cur ^ 1];
             a.act_next_count = &ctx->dcnt->act_count[cur ^ 1];
+            a.work = &ctx->dcnt->work[cur];
             if (launched < 64) SPH_CUDA(cudaEventRecord(ctx->kev[2 * launched], s));
             if (ctx->fp64) k_density<T, true><<<grid, DW * 32, 0, s>>>(a);
             else k_density<T, false><<<grid, DW * 32, 0, s>>>(a);
@@ -385,7 +410,7 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
         st->n_unconverged = ctx->hcnt->n_not_conv;
         st->n_hbounds = ctx->hcnt->n_hbounds;
         st->interactions = (int64_t)ctx->hcnt->interactions;
-        st->list_entries = (int64_t)ctx->hcnt->list_total;
+        st->list_entries = (int64_t)ctx->hcnt->list_used;
         st->evaluations = (int64_t)ctx->hcnt->evaluations;
         st->kernel_ms = kernel_ms;
         st->launches = ctx->launches - launches0;
@@ -400,6 +425,25 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
         return sph_fail(ctx, SPH_ERR_H_BOUNDS, "sph_density: converged h on h_min/h_max for " +
                                                    std::to_string(ctx->hcnt->n_hbounds) + " particles");
     return SPH_OK;
+}
+
+// Lists sized by leaf bounds can exceed nb_capacity where exact counts fit:
+// the context then sizes them exactly from now on and the iteration restarts
+// from its first guess.
+template <typename T>
+int run_impl(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats *st, cudaStream_t s)
+{
+    const bool bounded = !ctx->lists_exact;
+    const void *first = seed;
+    if (bounded && !seed) {
+        SPH_TRY(copy_field(ctx, ctx->hstart, p->h, p->n, s));
+        first = ctx->hstart;
+    }
+    const int r = run_once<T>(ctx, p, seed, st, s);
+    if (r != SPH_ERR_CAPACITY || !bounded) return r;
+    ctx->lists_exact = true;
+    ctx->err.clear();
+    return run_once<T>(ctx, p, first, st, s);
 }
 
 }  // namespace

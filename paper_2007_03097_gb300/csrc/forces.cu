@@ -337,7 +337,7 @@ int forces_collect(sph_ctx *ctx, sph_force_stats *st)
     st->kernel_ms = f;
     st->launches = ctx->force_launches;
     st->interactions = (int64_t)ctx->hcnt->force_interactions;
-    st->list_entries = (int64_t)ctx->hcnt->list_total;
+    st->list_entries = (int64_t)ctx->hcnt->list_used;
     if (ctx->hcnt->err & (ERRB_LIST_CAPACITY | ERRB_STACK))
         return sph_fail(ctx, SPH_ERR_CAPACITY, "sph_forces: neighbour-list capacity exceeded");
     return SPH_OK;
@@ -348,6 +348,17 @@ int forces_collect(sph_ctx *ctx, sph_force_stats *st)
 int forces_run(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, const void *vz,
                sph_force_stats *st, bool reuse_lists, cudaStream_t s)
 {
-    return ctx->fp64 ? run_impl<double>(ctx, p, vx, vy, vz, st, reuse_lists, s)
-                     : run_impl<float>(ctx, p, vx, vy, vz, st, reuse_lists, s);
+    auto run = [&]() {
+        return ctx->fp64 ? run_impl<double>(ctx, p, vx, vy, vz, st, reuse_lists, s)
+                         : run_impl<float>(ctx, p, vx, vy, vz, st, reuse_lists, s);
+    };
+    const bool bounded = !ctx->lists_exact;
+    const int r = run();
+    // lists sized by leaf bounds overflowed nb_capacity: size them exactly
+    if (r != SPH_ERR_CAPACITY || !bounded || !st) return r;
+    ctx->lists_exact = true;
+    ctx->lists_valid = false;
+    ctx->err.clear();
+    SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->err, 0, sizeof(uint32_t), s));
+    return run();
 }

@@ -52,11 +52,18 @@ __device__ __forceinline__ float axis_gap(float alo, float ahi, float blo, float
     return fmaxf(0.f, fabsf(d) - ea - eb);
 }
 
-template <bool FILL>
+// Modes of one traversal: LM_BOUND sizes each lane's list by the particles of
+// the leaves within its reach (no particle tests), LM_EXACT counts the list
+// exactly, LM_FILL writes it into the slots the count sized and records the
+// exact width.
+enum { LM_BOUND = 0, LM_EXACT = 1, LM_FILL = 2 };
+
+template <int MODE>
 __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
 {
+    constexpr bool FILL = MODE == LM_FILL;
     __shared__ int32_t s_stack[LW][STACK];
-    __shared__ float4 s_pa[LW][TILE];   // source {x, y, z} relative to the group centre, cov
+    __shared__ float4 s_pa[LW][TILE];   // source {x, y, z} relative to the group centre, cov^2 (1 + MARGIN)
     __shared__ int32_t s_pi[LW][TILE];  // source index
     __shared__ int32_t s_lb[LW][32], s_incl[LW][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -90,16 +97,20 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
     int count = 0;
     bool overflow = false;
 
+    // a non-target lane tests against a zero radius and accepts nothing
+    // but its own coincident copies, which the b != ia check removes
+    const float ca2 = tgt ? ca * ca * (1.f + MARGIN) : -1.f;
     auto process = [&](int ns) {
         for (int k = 0; k < ns; ++k) {
-            const float4 q = pa[k];
-            const int b = pi[k];
+            const float4 q = pa[k];                    // .w = cov^2 (1 + MARGIN)
             const float dx = tx - q.x, dy = ty - q.y, dz = tz - q.z;
             const float r2 = (dx * dx + dy * dy) + dz * dz;
-            const float c = fmaxf(ca, q.w);
-            if (tgt && b != ia && r2 <= c * c * (1.f + MARGIN)) {
-                if (FILL && count < width) a.nbl[off + (int64_t)count * 32 + lane] = (uint32_t)b;
-                ++count;
+            if (r2 <= fmaxf(ca2, q.w)) {
+                const int b = pi[k];
+                if (tgt && b != ia) {
+                    if (FILL && count < width) a.nbl[off + (int64_t)count * 32 + lane] = (uint32_t)b;
+                    ++count;
+                }
             }
         }
     };
@@ -146,8 +157,9 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
         if (sp > STACK) { overflow = true; sp = 0; }
         __syncwarp();
         // per-target culling: keep an accepted leaf only if some target of
-        // the group is within max(cov_target, cov of the leaf) of its box
-        bool keep = false;
+        // the group is within max(cov_target, cov of the leaf) of its box;
+        // need = the targets within reach of this lane's leaf
+        unsigned need = 0;
         for (unsigned m = __ballot_sync(0xffffffffu, acc && leaf); m; m &= m - 1) {
             const int l = __ffs(m) - 1;
             const float lx = __shfl_sync(0xffffffffu, lo.x, l), ly = __shfl_sync(0xffffffffu, lo.y, l);
@@ -158,8 +170,25 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
             float gy = fmaxf(0.f, axis_gap(PA.z, PA.z, ly, hy, a.periodic, a.L, a.half) - a.slack);
             float gz = fmaxf(0.f, axis_gap(PB.x, PB.x, lz, hz, a.periodic, a.L, a.half) - a.slack);
             const float r = fmaxf(ca, lc);
-            const bool need = tgt && (gx * gx + gy * gy) + gz * gz <= r * r * (1.f + MARGIN);
-            if (__any_sync(0xffffffffu, need) && lane == l) keep = true;
+            const unsigned nm =
+                __ballot_sync(0xffffffffu, tgt && (gx * gx + gy * gy) + gz * gz <= r * r * (1.f + MARGIN));
+            if (lane == l) need = nm;
+        }
+        const bool keep = need != 0;
+        if (MODE == LM_BOUND) {
+            // every particle of a leaf within a target's reach may be listed for it
+            int cnt = 0;
+            if (keep) {
+                const int id = node & 0x7fffffff;
+                cnt = a.leaf_begin[id + 1] - a.leaf_begin[id];
+            }
+            for (unsigned m = __ballot_sync(0xffffffffu, keep); m; m &= m - 1) {
+                const int l = __ffs(m) - 1;
+                const unsigned nm = __shfl_sync(0xffffffffu, need, l);
+                const int c = __shfl_sync(0xffffffffu, cnt, l);
+                if ((nm >> lane) & 1u) count += c;
+            }
+            continue;
         }
         // particles of all kept leaves, loaded in warp-wide waves: lane L
         // owns a leaf range [lb, lb + cnt) placed at [incl - cnt, incl) of
@@ -200,7 +229,8 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
                     ry -= a.L * rintf(ry / a.L);
                     rz -= a.L * rintf(rz / a.L);
                 }
-                pa[t] = make_float4(rx + qa.y, ry + qa.w, rz + qb.y, a.cov[j]);
+                const float cj = a.cov[j];
+                pa[t] = make_float4(rx + qa.y, ry + qa.w, rz + qb.y, cj * cj * (1.f + MARGIN));
                 pi[t] = j;
             }
             ns += take2;
@@ -218,7 +248,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
             }
         }
     }
-    if (ns > 0) process(ns);
+    if (MODE != LM_BOUND && ns > 0) process(ns);
 
     if (overflow && lane == 0) atomicOr(&a.cnt->err, ERRB_STACK);
     int wmax = count;
@@ -227,7 +257,12 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
         if (lane == 0) a.group_width[g] = wmax;
     } else {
         if ((!fits || wmax > width) && lane == 0) atomicOr(&a.cnt->err, ERRB_LIST_CAPACITY);
-        for (int k = count; k < width; ++k) a.nbl[off + (int64_t)k * 32 + lane] = SPH_SENTINEL;
+        const int used = min(wmax, width);
+        for (int k = count; k < used; ++k) a.nbl[off + (int64_t)k * 32 + lane] = SPH_SENTINEL;
+        if (lane == 0) {
+            a.group_width[g] = used;          // the exact width, within the sized slots
+            atomicAdd(&a.cnt->list_used, 32ull * (unsigned long long)used);
+        }
     }
 }
 
@@ -244,6 +279,7 @@ __global__ void k_list_total(const int64_t *__restrict__ off, const int32_t *__r
     const int64_t total = off[ng - 1] + 32 * (int64_t)width[ng - 1];
     off_end[0] = total;
     cnt->list_total = (unsigned long long)total;
+    cnt->list_used = 0;
     if (total > cap) atomicOr(&cnt->err, ERRB_LIST_CAPACITY);
 }
 
@@ -340,7 +376,8 @@ int build_impl(sph_ctx *ctx, cudaStream_t s)
     a.cap = ctx->nbl_cap;
     a.cnt = ctx->dcnt;
     const unsigned grid = grid_for(ng, LW);
-    k_lists<false><<<grid, LW * 32, 0, s>>>(a);
+    if (ctx->lists_exact) k_lists<LM_EXACT><<<grid, LW * 32, 0, s>>>(a);
+    else k_lists<LM_BOUND><<<grid, LW * 32, 0, s>>>(a);
     SPH_CHECK_LAUNCH();
     k_slots<<<grid_for(ng, 256), 256, 0, s>>>(ctx->group_width, ng, ctx->itmp0);
     SPH_CHECK_LAUNCH();
@@ -348,7 +385,7 @@ int build_impl(sph_ctx *ctx, cudaStream_t s)
     k_list_total<<<1, 1, 0, s>>>(ctx->group_off, ctx->group_width, ng, ctx->nbl_cap, ctx->group_off + ng,
                                  ctx->dcnt);
     SPH_CHECK_LAUNCH();
-    k_lists<true><<<grid, LW * 32, 0, s>>>(a);
+    k_lists<LM_FILL><<<grid, LW * 32, 0, s>>>(a);
     SPH_CHECK_LAUNCH();
     k_guard_widths<<<grid_for(ng, 256), 256, 0, s>>>(ctx->group_width, ng, ctx->dcnt);
     SPH_CHECK_LAUNCH();
@@ -375,8 +412,10 @@ int lists_build(sph_ctx *ctx, const sph_particles *p, cudaStream_t s)
     return build_impl(ctx, s);
 }
 
-int neighbors_export(sph_ctx *ctx, const sph_particles *p, int kind, int64_t *counts, const int64_t *offsets,
-                     uint32_t *idx, cudaStream_t s)
+namespace {
+
+int export_once(sph_ctx *ctx, const sph_particles *p, int kind, int64_t *counts, const int64_t *offsets,
+                uint32_t *idx, cudaStream_t s)
 {
     SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->err, 0, sizeof(uint32_t), s));
     SPH_TRY(lists_build(ctx, p, s));
@@ -404,4 +443,18 @@ int neighbors_export(sph_ctx *ctx, const sph_particles *p, int kind, int64_t *co
     if (ctx->hcnt->err & (ERRB_LIST_CAPACITY | ERRB_STACK))
         return sph_fail(ctx, SPH_ERR_CAPACITY, "sph_neighbors: neighbour-list capacity exceeded");
     return SPH_OK;
+}
+
+}  // namespace
+
+int neighbors_export(sph_ctx *ctx, const sph_particles *p, int kind, int64_t *counts, const int64_t *offsets,
+                     uint32_t *idx, cudaStream_t s)
+{
+    const bool bounded = !ctx->lists_exact;
+    const int r = export_once(ctx, p, kind, counts, offsets, idx, s);
+    // lists sized by leaf bounds overflowed nb_capacity: size them exactly
+    if (r != SPH_ERR_CAPACITY || !bounded) return r;
+    ctx->lists_exact = true;
+    ctx->err.clear();
+    return export_once(ctx, p, kind, counts, offsets, idx, s);
 }

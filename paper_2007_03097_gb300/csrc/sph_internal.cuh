@@ -14,6 +14,43 @@
 #define SPH_WARP 32
 #define SPH_SENTINEL 0xFFFFFFFFu
 
+// Walks one lane's slot-major neighbour list off + 32 k + lane, k < width,
+// calling proc(b, A[b], B[b]) for every non-sentinel entry b.  PIPELINED: the
+// index of entry k + 2 and the two source records of entry k + 1 are in
+// flight while entry k is processed (a sentinel's records are fetched from
+// `self`, a valid index, and never processed).  This pays for the long
+// double-float pair arithmetic; the short FP32 one runs faster without it.
+template <bool PIPELINED, class Proc>
+__device__ __forceinline__ void walk_list(const uint32_t *__restrict__ nbl, int64_t off, int width, int lane,
+                                          uint32_t self, const float4 *__restrict__ A,
+                                          const float4 *__restrict__ B, Proc &&proc)
+{
+    if (!PIPELINED) {
+        for (int k = 0; k < width; ++k) {
+            const uint32_t b = nbl[off + (int64_t)k * 32 + lane];
+            if (b == SPH_SENTINEL) continue;
+            proc(b, A[b], B[b]);
+        }
+        return;
+    }
+    if (width <= 0) return;
+    const uint32_t *l = nbl + off + lane;
+    uint32_t b1 = __ldg(l);
+    uint32_t b2 = width > 1 ? __ldg(l + 32) : SPH_SENTINEL;
+    uint32_t j = b1 == SPH_SENTINEL ? self : b1;
+    float4 P = __ldg(A + j), Q = __ldg(B + j);
+    for (int k = 0; k < width; ++k) {
+        const uint32_t b = b1;
+        const float4 Pc = P, Qc = Q;
+        b1 = b2;
+        b2 = k + 2 < width ? __ldg(l + (int64_t)(k + 2) * 32) : SPH_SENTINEL;
+        j = b1 == SPH_SENTINEL ? self : b1;
+        P = __ldg(A + j);
+        Q = __ldg(B + j);
+        if (b != SPH_SENTINEL) proc(b, Pc, Qc);
+    }
+}
+
 // bits of DevCounters::err
 enum : uint32_t {
     ERRB_NONFINITE = 1u,
@@ -49,8 +86,9 @@ struct DevCounters {
     float loss;
     int32_t sweeps_done;               // sweeps that evaluated at least one particle
     int32_t act_count[2];              // active groups read / written by the sweeps
-    int32_t pad2[2];
+    int32_t work[2];                   // next active-group slot a sweep's warps claim
     unsigned long long force_interactions;
+    unsigned long long list_used;      // list slots holding the exact lists of the last build
 };
 
 struct sph_ctx {
@@ -66,6 +104,7 @@ struct sph_ctx {
     int64_t n_leaves = 0, n_groups = 0;
     bool tree_valid = false;
     bool lists_valid = false;           // lists cover 2h of every particle
+    bool lists_exact = false;           // size lists by exact counts (set once leaf bounds overflowed)
     double dom[4] = {0, 0, 0, 1};
     double dt_cfl = 0.0;
 
@@ -109,6 +148,7 @@ struct sph_ctx {
     void *vpx = nullptr, *vpy = nullptr, *vpz = nullptr, *upred = nullptr;
     void *pr2 = nullptr;                // P / rho^2
     void *hold = nullptr;               // h before the density iteration
+    void *hstart = nullptr;             // first guess of the running iteration (for a restart)
     void *hseed = nullptr;              // h-predictor seeds
     // ---- gather scratch
     unsigned char *gbuf = nullptr;
@@ -265,6 +305,8 @@ int scan_inclusive_max_i32(sph_ctx *ctx, const int32_t *in, int32_t *out, int64_
 size_t scan_tmp_bytes(int64_t n);
 // neighbors.cu
 int lists_build(sph_ctx *ctx, const sph_particles *p, cudaStream_t s);
+// device copy of n elements of the context's precision
+int copy_field(sph_ctx *ctx, void *dst, const void *src, int64_t n, cudaStream_t s);
 int neighbors_export(sph_ctx *ctx, const sph_particles *p, int kind, int64_t *counts,
                      const int64_t *offsets, uint32_t *idx, cudaStream_t s);
 // density.cu

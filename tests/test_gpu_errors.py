@@ -52,6 +52,36 @@ def test_list_capacity_exhausted():
     assert e.value.code == B.SPH_ERR_CAPACITY
 
 
+def test_bounded_lists_fall_back_to_exact_sizing():
+    """Lists are first sized by the particles of the leaves within reach; a
+    capacity that holds the exact lists but not those bounds makes the
+    context switch to exact counts and restart, with the same result."""
+    B = need_gpu()
+    w = inputs.sedov(16)
+    ctx = B.Context(w.params, w.n)
+    p = B.Particles.from_workload(w, fp64=True)
+    B.sph_build_tree(ctx, p)
+    st = B.sph_density(ctx, p)
+    fa = B.sph_forces(ctx, p)
+    used = max(st["list_entries"], fa["list_entries"])   # sph_forces rebuilds for the converged h
+    assert used > 0
+    info = B.sph_list_info(ctx)
+    assert not info["exact_sizing"] and info["slots_reserved"] > info["slots_used"] == fa["list_entries"]
+    tight = dict(w.params, nb_capacity=int(used * 1.05))
+    ctx2 = B.Context(tight, w.n)
+    q = B.Particles.from_workload(w, fp64=True)
+    B.sph_build_tree(ctx2, q)
+    st2 = B.sph_density(ctx2, q)
+    fb = B.sph_forces(ctx2, q)
+    assert st2["list_entries"] == st["list_entries"] and fb["list_entries"] == fa["list_entries"]
+    for f in ("h", "rho", "omega", "nnb", "ax", "ay", "az", "dudt"):
+        assert torch.equal(getattr(p, f), getattr(q, f)), f
+    assert B.sph_list_info(ctx2)["exact_sizing"]
+    # the exact sizing persists: a step on the tight context succeeds
+    B.sph_step(ctx2, q, w.dt)
+    assert B.sph_list_info(ctx2)["slots_reserved"] == B.sph_list_info(ctx2)["slots_used"]
+
+
 def test_iteration_cap_and_h_bounds():
     B = need_gpu()
     w = inputs.sedov(10)
