@@ -256,7 +256,12 @@ int sph_hnet_get_weights(sph_ctx *ctx, float *params_host, int64_t count);
 int sph_hnet_features(sph_ctx *ctx, const sph_particles *p, double dt, float *feats,
                       void *stream);
 /* predicted log(h_next/h) s = f3 * y (device, nb) from features (device,
- * nb x 5) with the BF16 weights; f3 = div v * dt, so s = 0 at rest */
+ * nb x 5) with the BF16 weights; f3 = div v * dt, so s = 0 at rest.  The
+ * 64 x 64 layer runs on the tensor cores (tcgen05, FP32 accumulation of the
+ * exact products of the BF16 weights with a three-term BF16 split of the
+ * FP32 activations).  Synchronises the stream; SPH_ERR_CUDA if an MMA did
+ * not complete within 1 s (the kernel then frees its tensor memory and
+ * returns). */
 int sph_hnet_infer(sph_ctx *ctx, const float *feats, int64_t nb, float *y, void *stream);
 /* loss = mean (f3 y - t)^2 and its gradient (host, SPH_HNET_NPARAM) at the
  * BF16 weights, FP32 accumulation; no update. */

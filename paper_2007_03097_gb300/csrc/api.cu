@@ -310,6 +310,7 @@ int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet, sph_step_s
     if (seed_net || train_net) SPH_TRY(hnet_features(ctx, p, dt, ctx->feats, s));
     if (seed_net) {
         SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->hnet_fallback, 0, sizeof(int32_t), s));
+        SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->hnet_err, 0, sizeof(uint32_t), s));
         SPH_TRY(hnet_infer(ctx, ctx->feats, p->n, ctx->hn_y, s));
         SPH_TRY(hnet_seed(ctx, p, ctx->hn_y, ctx->hseed, s));
         seed = ctx->hseed;
@@ -318,6 +319,8 @@ int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet, sph_step_s
     SPH_CUDA(cudaEventRecord(ev[2], s));
     int st = density_run(ctx, p, seed, &local.density, s);
     if (seed_net) local.hnet_fallback = ctx->hcnt->hnet_fallback;
+    if (seed_net && ctx->hcnt->hnet_err)
+        return sph_fail(ctx, SPH_ERR_CUDA, "sph_step: an h-predictor tensor-core MMA did not complete within 1 s");
     if (st == SPH_ERR_NOT_CONVERGED && seed_net) {
         // the plain iteration is the fallback: restart from the previous h
         local.hnet_fallback += (int32_t)local.density.n_unconverged;
@@ -474,7 +477,13 @@ int sph_hnet_infer(sph_ctx *ctx, const float *feats, int64_t nb, float *y, void 
 {
     if (!ctx) return SPH_ERR_ARG;
     if (!feats || !y || nb < 1) return sph_fail(ctx, SPH_ERR_ARG, "feats, y and nb >= 1 required");
-    return hnet_infer(ctx, feats, nb, y, S(stream));
+    cudaStream_t s = S(stream);
+    SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->hnet_err, 0, sizeof(uint32_t), s));
+    SPH_TRY(hnet_infer(ctx, feats, nb, y, s));
+    SPH_TRY(sync_counters(ctx, s));
+    if (ctx->hcnt->hnet_err)
+        return sph_fail(ctx, SPH_ERR_CUDA, "sph_hnet_infer: a tensor-core MMA did not complete within 1 s");
+    return SPH_OK;
 }
 
 int sph_hnet_grad(sph_ctx *ctx, const float *feats, const float *target, int64_t nb, float *grad_host,

@@ -2,12 +2,13 @@
 // h-rho iteration of Eq. 9, which stays the judge of the converged h):
 //   y = W3 silu(W2 silu(W1 f + b1) + b2) + b3,  5 -> 64 -> 64 -> 1,
 // BF16 weights read by the kernels, FP32 master weights and Adam moments,
-// FP32 activations and accumulation.  The prediction of log(h_next / h) is
+// FP32 activations and accumulation (inference: layer 2 on the tensor cores).  The prediction of log(h_next / h) is
 // s = f3 * y with f3 = div v * dt: a particle at rest keeps its h exactly, and
 // the network learns the gain of the continuity estimate div v dt / 3.
 #include <cmath>
 
 #include "sph_internal.cuh"
+#include "tc.cuh"
 
 namespace {
 
@@ -50,56 +51,165 @@ __global__ void k_features(const T *__restrict__ h, const T *__restrict__ hprev,
     o[4] = hp > 0.f ? logf(hi / hp) : 0.f;
 }
 
-// ---------------------------------------------------------------- inference
-// One thread per sample.  Half of the 64 layer-2 pre-activations at a time
-// stay in registers; the layer-1 units are recomputed for each half (5 FMAs
-// each) and scattered into them through the transposed W2 held in shared
-// memory (float4 broadcast reads).
-constexpr int HALF = H / 2;
+// ------------------------------------------------- inference, tensor cores
+// One warpgroup per tile of 128 samples (a persistent loop over tiles).  Each
+// thread owns one sample: it evaluates layer 1 (5 -> 64, FP32) and writes the
+// activations to shared memory as the A operand of the layer-2 contraction,
+// split into three BF16 terms a = hi + mid + lo (hi = bf16(a), mid =
+// bf16(a - hi), lo = bf16(a - hi - mid)), which carry the FP32 activation to
+// within 2^-24 of its value.  One thread issues the 12 tcgen05 MMAs
+// (M = 128, N = 64, K = 16 each; three terms x four K steps) that accumulate
+// z2 = a1 W2^T in FP32 in tensor memory; each thread then reads its sample's
+// row back (tcgen05.ld), applies b2, SiLU and layer 3 and writes f3 * y.
+// The products with the BF16 weights are exact and accumulate in FP32, as in
+// the CUDA-core evaluation.
+constexpr int TM = 128;                          // samples per tile (MMA M)
+constexpr int NSPLIT = 3;                        // BF16 terms per activation
+constexpr uint32_t CM_LBO = 128;                 // K-adjacent core matrices
+constexpr uint32_t CM_SBO = (H / 8) * 128;       // next 8 rows: 1024 bytes
+constexpr int A_TILE = TM * H * 2;               // 16 KB per term
+constexpr int B_TILE = H * H * 2;                // 8 KB
+constexpr int B_PAD = 1024;                      // slack after B
+constexpr int WF = 320 + 64 + 64 + 64 + 1;       // FP32 W1, b1, b2, w3, b3
+constexpr uint32_t TM_COLS = 64;                 // TMEM columns: D is 128 x 64 FP32
+constexpr uint64_t MMA_WAIT_NS = 1000000000ull;  // give up on an MMA after 1 s
 
-__global__ void __launch_bounds__(256, 3) k_infer(const __nv_bfloat16 *__restrict__ wb, const float *__restrict__ f,
-                                                  int64_t nb, float *__restrict__ y)
+__host__ __device__ constexpr int infer_tc_smem()
 {
-    __shared__ __align__(16) float w[NP + 3];
-    for (int k = threadIdx.x; k < NP; k += blockDim.x) {
-        int dst = k;
-        if (k >= O_W2 && k < O_B2) {              // store W2 transposed: [k][j]
-            const int j = (k - O_W2) / H, c = (k - O_W2) % H;
-            dst = O_W2 + H * c + j;
-        }
-        w[dst] = __bfloat162float(wb[k]);
+    return 1024 + B_TILE + B_PAD + NSPLIT * A_TILE + WF * 4 + 16;
+}
+
+// byte offset of element (row, k) in a K-major no-swizzle operand of 64 columns
+__device__ __forceinline__ uint32_t cm_off(int row, int k)
+{
+    return (uint32_t)((row >> 3) * CM_SBO + (k >> 3) * CM_LBO + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__global__ void __launch_bounds__(TM) k_infer_tc(const __nv_bfloat16 *__restrict__ wb, const float *__restrict__ f,
+                                                 int64_t nb, float *__restrict__ y, DevCounters *cnt)
+{
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)sm_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sB = base;
+    unsigned char *sA = base + B_TILE + B_PAD;
+    float *wf = (float *)(sA + NSPLIT * A_TILE);
+    float *W1 = wf, *b1 = wf + 320, *b2 = wf + 384, *w3 = wf + 448, *b3 = wf + 512;
+    uint64_t *bar = (uint64_t *)(wf + WF + ((WF & 1) ? 1 : 0));
+    __shared__ uint32_t tslot;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // weights: W2 as the B operand (row n = output unit, K = input unit), the rest FP32
+    for (int idx = tid; idx < H * H; idx += TM) {
+        const int n = idx / H, k = idx % H;
+        *reinterpret_cast<__nv_bfloat16 *>(sB + cm_off(n, k)) = wb[O_W2 + idx];
     }
+    for (int k = tid; k < 320 + 64; k += TM) wf[k] = __bfloat162float(wb[O_W1 + k]);          // W1, b1
+    for (int k = tid; k < 64 + 64 + 1; k += TM) wf[384 + k] = __bfloat162float(wb[O_B2 + k]);  // b2, W3, b3
+    const uint32_t bar_a = tc::smem_addr(bar);
+    if (tid == 0) tc::mbar_init(bar_a, 1);
+    if (warp == 0) tc::tmem_alloc(&tslot, TM_COLS);
+    tc::fence_async_shared();
+    tc::fence_before_sync();
     __syncthreads();
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nb; s += (int64_t)gridDim.x * blockDim.x) {
+    tc::fence_after_sync();
+    const uint32_t tbase = tslot;
+    const uint32_t sA_a = tc::smem_addr(sA), sB_a = tc::smem_addr(sB);
+    constexpr uint32_t IDESC = tc::idesc_bf16_f32(TM, H);
+
+    const int64_t ntiles = (nb + TM - 1) / TM;
+    uint32_t parity = 0;
+    bool failed = false;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t s = tile * TM + tid;
+        const bool valid = s < nb;
         float x[5];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) x[k] = f[5 * s + k];
-        float out = w[O_B3];
+        for (int k = 0; k < 5; ++k) x[k] = valid ? f[5 * s + k] : 0.f;
+        // layer 1 and the three-term split, 8 units (one 16-byte row of a core matrix) at a time
 #pragma unroll 1
-        for (int half = 0; half < 2; ++half) {
-            float z2[HALF];
+        for (int c = 0; c < H / 8; ++c) {
+            uint32_t q[NSPLIT][4];
 #pragma unroll
-            for (int j = 0; j < HALF; ++j) z2[j] = w[O_B2 + half * HALF + j];
-#pragma unroll 1
-            for (int k = 0; k < H; ++k) {
-                float z = w[O_B1 + k];
+            for (int e = 0; e < 8; e += 2) {
+                float a[2];
 #pragma unroll
-                for (int c = 0; c < 5; ++c) z += w[O_W1 + 5 * k + c] * x[c];
-                const float a = z * sigm(z);
-                const float4 *col = reinterpret_cast<const float4 *>(w + O_W2 + H * k + half * HALF);
+                for (int u = 0; u < 2; ++u) {
+                    const int j = 8 * c + e + u;
+                    float z = b1[j];
 #pragma unroll
-                for (int j = 0; j < HALF / 4; ++j) {
-                    const float4 r = col[j];
-                    z2[4 * j] += r.x * a;
-                    z2[4 * j + 1] += r.y * a;
-                    z2[4 * j + 2] += r.z * a;
-                    z2[4 * j + 3] += r.w * a;
+                    for (int k = 0; k < 5; ++k) z += W1[5 * j + k] * x[k];
+                    a[u] = z * sigm(z);
                 }
+                const __nv_bfloat162 hi = __floats2bfloat162_rn(a[0], a[1]);
+                const float r0 = a[0] - __low2float(hi), r1 = a[1] - __high2float(hi);
+                const __nv_bfloat162 mid = __floats2bfloat162_rn(r0, r1);
+                q[0][e / 2] = *reinterpret_cast<const uint32_t *>(&hi);
+                q[1][e / 2] = *reinterpret_cast<const uint32_t *>(&mid);
+                q[2][e / 2] = pack_bf16(r0 - __low2float(mid), r1 - __high2float(mid));
             }
 #pragma unroll
-            for (int j = 0; j < HALF; ++j) out += w[O_W3 + half * HALF + j] * (z2[j] * sigm(z2[j]));
+            for (int t = 0; t < NSPLIT; ++t)
+                *reinterpret_cast<uint4 *>(sA + t * A_TILE + cm_off(tid, 8 * c)) =
+                    make_uint4(q[t][0], q[t][1], q[t][2], q[t][3]);
         }
-        y[s] = x[3] * out;                      // s = f3 * y
+        tc::fence_async_shared();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+#pragma unroll
+            for (int t = 0; t < NSPLIT; ++t)
+#pragma unroll
+                for (int kk = 0; kk < H / 16; ++kk) {
+                    const uint64_t ad = tc::smem_desc(sA_a + t * A_TILE + kk * 2 * CM_LBO, CM_LBO, CM_SBO);
+                    const uint64_t bd = tc::smem_desc(sB_a + kk * 2 * CM_LBO, CM_LBO, CM_SBO);
+                    tc::mma_bf16(tbase, ad, bd, IDESC, t > 0 || kk > 0);
+                }
+            tc::mma_commit(bar_a);
+        }
+        const bool ok = tc::mbar_wait(bar_a, parity, MMA_WAIT_NS);
+        parity ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        tc::fence_after_sync();
+        // epilogue: this thread's row of z2 (TMEM lane = tid), b2, SiLU, layer 3
+        const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
+        float out = b3[0];
+#pragma unroll
+        for (int cc = 0; cc < H / 16; ++cc) {
+            float v[16];
+            tc::tmem_ld16(trow + 16 * cc, v);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const float z = v[e] + b2[16 * cc + e];
+                out += w3[16 * cc + e] * (z * sigm(z));
+            }
+        }
+        if (valid) y[s] = x[3] * out;             // s = f3 * y
+        tc::fence_before_sync();
+        __syncthreads();                          // TMEM read and A tiles free before the next MMA
+    }
+    if (failed) {
+        // an MMA did not complete in time: report, give it one more bounded
+        // wait, then release the tensor memory
+        if (tid == 0) {
+            atomicOr(&cnt->hnet_err, 1u);
+            tc::mbar_wait(bar_a, parity ^ 1u, MMA_WAIT_NS);
+        }
+        __syncthreads();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tbase, TM_COLS);
     }
 }
 
@@ -269,6 +379,7 @@ size_t grad_smem() { return sizeof(float) * (NP + 3 + GS * 5 + 4 * GS * ST + GS)
 int hnet_init(sph_ctx *ctx)
 {
     SPH_CUDA(cudaFuncSetAttribute(k_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem()));
+    SPH_CUDA(cudaFuncSetAttribute(k_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, infer_tc_smem()));
     return SPH_OK;
 }
 
@@ -289,11 +400,11 @@ int hnet_features(sph_ctx *ctx, const sph_particles *p, double dt, float *feats,
 
 int hnet_infer(sph_ctx *ctx, const float *feats, int64_t nb, float *y, cudaStream_t s)
 {
-    int64_t blocks = (nb + 255) / 256;
-    const int64_t cap = (int64_t)ctx->num_sms * 8;
+    if (nb <= 0) return SPH_OK;
+    int64_t blocks = (nb + TM - 1) / TM;
+    const int64_t cap = (int64_t)ctx->num_sms * 3;       // 3 resident blocks of ~60 KB per SM
     if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    k_infer<<<(unsigned)blocks, 256, 0, s>>>(ctx->hn_bf16, feats, nb, y);
+    k_infer_tc<<<(unsigned)blocks, TM, infer_tc_smem(), s>>>(ctx->hn_bf16, feats, nb, y, ctx->dcnt);
     SPH_CHECK_LAUNCH();
     return SPH_OK;
 }

@@ -89,6 +89,8 @@ struct DevCounters {
     int32_t work[2];                   // next active-group slot a sweep's warps claim
     unsigned long long force_interactions;
     unsigned long long list_used;      // list slots holding the exact lists of the last build
+    uint32_t hnet_err;                 // h-predictor tensor-core kernel: an MMA timed out
+    uint32_t pad3;
 };
 
 struct sph_ctx {
