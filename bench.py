@@ -226,7 +226,8 @@ def run_sph(args):
                     density_launches=sum(s["density"]["sweeps"] for s in st),
                     launches=sum(s["launches"] for s in st),
                     hnet_fallback=sum(s["hnet_fallback"] for s in st),
-                    hnet_loss=st[-1]["hnet_loss"], ms_tree=sum(s["ms_tree"] for s in st) / len(st))
+                    hnet_loss=st[-1]["hnet_loss"], ms_tree=sum(s["ms_tree"] for s in st) / len(st),
+                    tree_moved=[s["tree_moved"] for s in st])
 
     L = summarize(ms_l, st_l)
     P = summarize(ms_p, st_p)

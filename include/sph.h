@@ -144,7 +144,8 @@ typedef struct {
     int32_t hnet_used;       /* 1 if the h-predictor seeded the iteration           */
     int32_t hnet_fallback;   /* particles reseeded from h after a bad prediction    */
     float hnet_loss;         /* loss of the last online training step (or 0)        */
-    int32_t pad;
+    int32_t tree_moved;      /* particles the key-order rebuild moved: 0 when the
+                                previous order held, -1 after a full sort          */
     int64_t launches;        /* kernels launched by the step                        */
     sph_density_stats density;
     sph_force_stats forces;

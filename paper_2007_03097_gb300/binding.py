@@ -70,7 +70,7 @@ class sph_step_stats(_c.Structure):
     _fields_ = [("dt", _c.c_double), ("dt_next", _c.c_double), ("momentum", _c.c_double * 3),
                 ("force", _c.c_double * 3), ("energy", _c.c_double), ("power", _c.c_double),
                 ("hnet_used", _c.c_int32), ("hnet_fallback", _c.c_int32), ("hnet_loss", _c.c_float),
-                ("pad", _c.c_int32), ("launches", _c.c_int64), ("density", sph_density_stats),
+                ("tree_moved", _c.c_int32), ("launches", _c.c_int64), ("density", sph_density_stats),
                 ("forces", sph_force_stats), ("ms_tree", _c.c_double), ("ms_hnet", _c.c_double),
                 ("ms_total", _c.c_double)]
 

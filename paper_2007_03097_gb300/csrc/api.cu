@@ -3,6 +3,9 @@
 #include <cmath>
 #include <cstring>
 
+#include <algorithm>
+#include <climits>
+
 #include "sph_internal.cuh"
 
 int hnet_refresh_bf16(sph_ctx *ctx, cudaStream_t s);
@@ -98,6 +101,7 @@ int allocate(sph_ctx *c, int64_t N)
     SPH_TRY(alloc(c, &c->val_a, N));
     SPH_TRY(alloc(c, &c->val_b, N));
     SPH_TRY(alloc(c, &c->hist, (size_t)c->hist_cap));
+    SPH_TRY(alloc(c, &c->ns_tiles, (size_t)(N / 1024 + 2)));
     SPH_TRY(alloc(c, &c->dlev, N));
     SPH_TRY(alloc(c, &c->plev, N));
     SPH_TRY(alloc(c, &c->itmp0, N + 1));
@@ -117,8 +121,6 @@ int allocate(sph_ctx *c, int64_t N)
     SPH_TRY(alloc(c, &c->node_visit, N));
     SPH_TRY(alloc(c, &c->node_lo, N));
     SPH_TRY(alloc(c, &c->node_hi, N));
-    float **split[] = {&c->xh, &c->xl, &c->yh, &c->yl, &c->zh, &c->zl};
-    for (float **s : split) SPH_TRY(alloc(c, s, N + 32));
     float4 **packs[] = {&c->srcA, &c->srcB, &c->srcC, &c->srcD, &c->srcE, &c->srcF};
     for (float4 **s : packs) SPH_TRY(alloc(c, s, N));
     c->nbl_cap = c->prm.nb_capacity > 0 ? c->prm.nb_capacity : 640 * N;
@@ -170,10 +172,10 @@ int allocate(sph_ctx *c, int64_t N)
 
 void release(sph_ctx *c)
 {
-    void *ptrs[] = {c->key_a, c->key_b, c->val_a, c->val_b, c->hist, c->dlev, c->plev, c->itmp0, c->itmp1,
+    void *ptrs[] = {c->key_a, c->key_b, c->val_a, c->val_b, c->hist, c->ns_tiles, c->dlev, c->plev, c->itmp0, c->itmp1,
                     c->itmp2, c->itmp3, c->leaf_begin, c->leaf_level, c->group_begin, c->leaf_lo, c->leaf_hi,
                     c->group_lo, c->group_hi, c->node_child, c->node_parent, c->leaf_parent, c->node_visit,
-                    c->node_lo, c->node_hi, c->xh, c->xl, c->yh, c->yl, c->zh, c->zl, c->srcA, c->srcB,
+                    c->node_lo, c->node_hi, c->srcA, c->srcB,
                     c->srcC, c->srcD, c->srcE, c->srcF, c->nbl, c->group_width,
                     c->group_off, c->it_lo, c->it_hi, c->it_flags, c->it_sweeps, c->cov, c->act_groups[0],
                     c->act_groups[1], c->vpx, c->vpy, c->vpz, c->upred, c->pr2, c->hold, c->hseed, c->hstart, c->gbuf,
@@ -304,6 +306,7 @@ int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet, sph_step_s
     SPH_CUDA(cudaEventRecord(ev[0], s));
     SPH_TRY(kick_drift(ctx, p, dt, s));
     SPH_TRY(tree_build(ctx, p, s));
+    local.tree_moved = (int32_t)std::min<int64_t>(ctx->ns_moved, INT32_MAX);
     SPH_CUDA(cudaEventRecord(ev[1], s));
     const void *seed = nullptr;
     SPH_TRY(copy_field(ctx, ctx->hold, p->h, p->n, s));

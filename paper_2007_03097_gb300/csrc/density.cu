@@ -42,7 +42,6 @@ struct DensArgs {
     const uint32_t *nbl;
     int64_t cap;
     const double *x, *y, *z;
-    const float *xh, *xl, *yh, *yl, *zh, *zl;
     const float4 *srcA, *srcB;   // {xh, xl, yh, yl}, {zh, zl, m_hi, m_lo}
     void *h;
     const void *m;
@@ -351,7 +350,6 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
     a.nbl = ctx->nbl;
     a.cap = ctx->nbl_cap;
     a.x = p->x; a.y = p->y; a.z = p->z;
-    a.xh = ctx->xh; a.xl = ctx->xl; a.yh = ctx->yh; a.yl = ctx->yl; a.zh = ctx->zh; a.zl = ctx->zl;
     a.srcA = ctx->srcA; a.srcB = ctx->srcB;
     a.h = p->h; a.m = p->m; a.rho = p->rho; a.omega = p->omega; a.nnb = p->nnb;
     a.it_lo = ctx->it_lo; a.it_hi = ctx->it_hi; a.it_flags = ctx->it_flags; a.it_sweeps = ctx->it_sweeps;

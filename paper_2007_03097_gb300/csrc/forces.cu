@@ -27,7 +27,6 @@ struct ForceArgs {
     int64_t cap;
     int n_groups;
     const double *x, *y, *z;
-    const float *xh, *xl, *yh, *yl, *zh, *zl;
     const float4 *srcA, *srcB, *srcC, *srcD, *srcE, *srcF;
     const void *vx, *vy, *vz, *m, *h, *rho, *pr2, *c;
     void *ax, *ay, *az, *dudt, *divv, *vsig;
@@ -305,7 +304,6 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
     a.cap = ctx->nbl_cap;
     a.n_groups = (int)ctx->n_groups;
     a.x = p->x; a.y = p->y; a.z = p->z;
-    a.xh = ctx->xh; a.xl = ctx->xl; a.yh = ctx->yh; a.yl = ctx->yl; a.zh = ctx->zh; a.zl = ctx->zl;
     a.srcA = ctx->srcA; a.srcB = ctx->srcB; a.srcC = ctx->srcC; a.srcD = ctx->srcD; a.srcE = ctx->srcE;
     a.srcF = ctx->srcF;
     a.vx = vx; a.vy = vy; a.vz = vz; a.m = p->m; a.h = p->h; a.rho = p->rho; a.pr2 = ctx->pr2; a.c = p->c;

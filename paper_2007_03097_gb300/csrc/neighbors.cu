@@ -296,10 +296,8 @@ template <typename T, int KIND, bool FP64POS>
 __global__ void k_export(const int32_t *__restrict__ group_begin, int ng, const int64_t *__restrict__ goff,
                          const int32_t *__restrict__ gwidth, const uint32_t *__restrict__ nbl,
                          const double *__restrict__ x, const double *__restrict__ y,
-                         const double *__restrict__ z, const float *__restrict__ xh,
-                         const float *__restrict__ xl, const float *__restrict__ yh,
-                         const float *__restrict__ yl, const float *__restrict__ zh,
-                         const float *__restrict__ zl, const T *__restrict__ h, int periodic, double L,
+                         const double *__restrict__ z, const float4 *__restrict__ srcA,
+                         const float4 *__restrict__ srcB, const T *__restrict__ h, int periodic, double L,
                          int64_t cap, int64_t *__restrict__ counts, const int64_t *__restrict__ offsets,
                          uint32_t *__restrict__ idx)
 {
@@ -333,9 +331,10 @@ __global__ void k_export(const int32_t *__restrict__ group_begin, int ng, const 
             }
         } else {
             const float Lf = (float)L, hf = 0.5f * Lf;
-            float dx = sep_f(xh[ia], xl[ia], xh[b], xl[b], periodic, Lf, hf);
-            float dy = sep_f(yh[ia], yl[ia], yh[b], yl[b], periodic, Lf, hf);
-            float dz = sep_f(zh[ia], zl[ia], zh[b], zl[b], periodic, Lf, hf);
+            const float4 A = srcA[ia], Bz = srcB[ia], P = srcA[b], Q = srcB[b];
+            float dx = sep_f(A.x, A.y, P.x, P.y, periodic, Lf, hf);
+            float dy = sep_f(A.z, A.w, P.z, P.w, periodic, Lf, hf);
+            float dz = sep_f(Bz.x, Bz.y, Q.x, Q.y, periodic, Lf, hf);
             float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
             float hfa = (float)ha;
             in = r2 < __fmul_rn(__fmul_rn(4.f, hfa), hfa);
@@ -424,8 +423,7 @@ int export_once(sph_ctx *ctx, const sph_particles *p, int kind, int64_t *counts,
     const int per = ctx->prm.periodic;
     const double L = ctx->dom[3];
 #define SPH_EXPORT_ARGS                                                                               \
-    ctx->group_begin, ng, ctx->group_off, ctx->group_width, ctx->nbl, p->x, p->y, p->z, ctx->xh, ctx->xl, \
-        ctx->yh, ctx->yl, ctx->zh, ctx->zl
+    ctx->group_begin, ng, ctx->group_off, ctx->group_width, ctx->nbl, p->x, p->y, p->z, ctx->srcA, ctx->srcB
     if (ctx->fp64) {
         if (kind == 0)
             k_export<double, 0, true><<<grid, 128, 0, s>>>(SPH_EXPORT_ARGS, (const double *)p->h, per, L, ctx->nbl_cap, counts, offsets, idx);

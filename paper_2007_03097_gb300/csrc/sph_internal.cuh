@@ -91,6 +91,19 @@ struct DevCounters {
     unsigned long long list_used;      // list slots holding the exact lists of the last build
     uint32_t hnet_err;                 // h-predictor tensor-core kernel: an MMA timed out
     uint32_t pad3;
+    long long ns_total;                // misplaced keys found by the near-sorted pass
+};
+
+// near-sorted key pass: (key, id) pairs and per-tile extremes, prefix
+// maximum, suffix minimum and misplaced counts
+struct NsKey {
+    uint64_t k;
+    uint32_t i;
+    uint32_t pad;
+};
+struct NsTile {
+    NsKey mx, mn, pre, suf;
+    int32_t cnt, off, pad[2];
 };
 
 struct sph_ctx {
@@ -115,6 +128,8 @@ struct sph_ctx {
     uint32_t *val_a = nullptr, *val_b = nullptr;
     uint32_t *hist = nullptr;           // radix histograms, 256 x tiles
     int64_t hist_cap = 0;
+    NsTile *ns_tiles = nullptr;         // near-sorted pass, one per 1024 keys
+    int64_t ns_moved = -1;              // particles the last build moved (-1: full sort)
     // ---- tree
     uint8_t *dlev = nullptr;            // first differing level with predecessor
     uint8_t *plev = nullptr;            // leaf level of each particle
@@ -131,7 +146,6 @@ struct sph_ctx {
     float4 *node_lo = nullptr, *node_hi = nullptr;   // .w of lo = max coverage
     float4 *group_lo = nullptr, *group_hi = nullptr; // .w of lo = max coverage
     // ---- two-float split of the positions (padded)
-    float *xh = nullptr, *xl = nullptr, *yh = nullptr, *yl = nullptr, *zh = nullptr, *zl = nullptr;
     // packed per-particle sources of the pair kernels (two-float pairs):
     // A {x, y}, B {z, m}, C {vx, vy}, D {vz, h}, E {rho, P/rho^2}, F {c, -}
     float4 *srcA = nullptr, *srcB = nullptr, *srcC = nullptr, *srcD = nullptr, *srcE = nullptr, *srcF = nullptr;

@@ -11,6 +11,8 @@
 // per particle from the levels at which neighbouring keys first differ.
 #include <cfloat>
 
+#include <algorithm>
+
 #include "sph_internal.cuh"
 
 namespace {
@@ -213,29 +215,15 @@ struct FieldTable {
     int nf;
 };
 
-// Permute every field: dst_f[i] = src_f[perm[i]] into scratch, and form the
-// two-float split (hi = float(x), lo = float(x - hi)) of the positions.
-__global__ void k_gather(FieldTable t, const uint32_t *__restrict__ perm, int64_t n,
-                         float *xh, float *xl, float *yh, float *yl, float *zh, float *zl)
+// Permute every field: dst_f[i] = src_f[perm[i]] into scratch.
+__global__ void k_gather(FieldTable t, const uint32_t *__restrict__ perm, int64_t n)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t p = perm[i];
     for (int f = 0; f < t.nf; ++f) {
-        if (t.size[f] == 8) {
-            double v = ((const double *)t.src[f])[p];
-            ((double *)t.dst[f])[i] = v;
-            if (f < 3) {
-                float hi = (float)v;
-                float lo = (float)(v - (double)hi);
-                float *H = f == 0 ? xh : f == 1 ? yh : zh;
-                float *Lo = f == 0 ? xl : f == 1 ? yl : zl;
-                H[i] = hi;
-                Lo[i] = lo;
-            }
-        } else {
-            ((uint32_t *)t.dst[f])[i] = ((const uint32_t *)t.src[f])[p];
-        }
+        if (t.size[f] == 8) ((double *)t.dst[f])[i] = ((const double *)t.src[f])[p];
+        else ((uint32_t *)t.dst[f])[i] = ((const uint32_t *)t.src[f])[p];
     }
 }
 
@@ -265,6 +253,292 @@ __global__ void k_copy_back(FieldTable t, int64_t n)
     for (int f = 0; f < t.nf; ++f) {
         if (t.size[f] == 8) ((double *)t.src[f])[i] = ((const double *)t.dst[f])[i];
         else ((uint32_t *)t.src[f])[i] = ((const uint32_t *)t.dst[f])[i];
+    }
+}
+
+// ------------------------------------------------------------------ near-sorted keys
+// Between steps the particles stay in the previous key order and move little,
+// so most of the new (key, id) sequence is already in its final order.  An
+// element is in place iff every element before it is smaller and every one
+// after it is larger: its rank is its position.  The misplaced elements
+// occupy the remaining positions in ascending order, so it suffices to rank
+// them among themselves (brute force; they are few) and to move only them.
+// The result is the (key, id) order of the full sort.
+using KI = NsKey;
+__device__ __forceinline__ bool ki_lt(const KI &a, const KI &b) { return a.k < b.k || (a.k == b.k && a.i < b.i); }
+__device__ __forceinline__ KI ki_max(const KI &a, const KI &b) { return ki_lt(a, b) ? b : a; }
+__device__ __forceinline__ KI ki_min(const KI &a, const KI &b) { return ki_lt(a, b) ? a : b; }
+__device__ __forceinline__ KI ki_shfl_xor(const KI &a, int o)
+{
+    KI r;
+    r.k = __shfl_xor_sync(0xffffffffu, a.k, o);
+    r.i = __shfl_xor_sync(0xffffffffu, a.i, o);
+    r.pad = 0;
+    return r;
+}
+__device__ __forceinline__ KI ki_shfl_up(const KI &a, int o)
+{
+    KI r;
+    r.k = __shfl_up_sync(0xffffffffu, a.k, o);
+    r.i = __shfl_up_sync(0xffffffffu, a.i, o);
+    r.pad = 0;
+    return r;
+}
+__device__ __forceinline__ KI ki_shfl_down(const KI &a, int o)
+{
+    KI r;
+    r.k = __shfl_down_sync(0xffffffffu, a.k, o);
+    r.i = __shfl_down_sync(0xffffffffu, a.i, o);
+    r.pad = 0;
+    return r;
+}
+__device__ __forceinline__ KI ki_low() { return KI{0ull, 0u, 0u}; }          // keys carry bit 63
+__device__ __forceinline__ KI ki_high() { return KI{~0ull, ~0u, 0u}; }
+
+constexpr int NS_THREADS = 256, NS_PER = 4, NS_TILE = NS_THREADS * NS_PER;
+constexpr int64_t NS_LIMIT = 32768;   // misplaced elements ranked by brute force at most
+
+// per tile: maximum and minimum element
+__global__ void __launch_bounds__(NS_THREADS) k_ns_tiles(const uint64_t *__restrict__ keys,
+                                                         const uint32_t *__restrict__ ids, int64_t n,
+                                                         NsTile *__restrict__ t)
+{
+    __shared__ KI smx[NS_THREADS / 32], smn[NS_THREADS / 32];
+    const int64_t b0 = (int64_t)blockIdx.x * NS_TILE + NS_PER * threadIdx.x;
+    KI mx = ki_low(), mn = ki_high();
+#pragma unroll
+    for (int u = 0; u < NS_PER; ++u) {
+        const int64_t i = b0 + u;
+        if (i < n) {
+            const KI e{keys[i], ids[i], 0u};
+            mx = ki_max(mx, e);
+            mn = ki_min(mn, e);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = ki_max(mx, ki_shfl_xor(mx, o));
+        mn = ki_min(mn, ki_shfl_xor(mn, o));
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { smx[w] = mx; smn[w] = mn; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < NS_THREADS / 32; ++k) { mx = ki_max(mx, smx[k]); mn = ki_min(mn, smn[k]); }
+        t[blockIdx.x].mx = mx;
+        t[blockIdx.x].mn = mn;
+    }
+}
+
+// Block-wide exclusive scan of one KI per thread, with max from the left
+// (DIR = +1) or min from the right (DIR = -1); blockDim.x a multiple of 32,
+// at most 1024; sh holds 64 entries.
+template <int DIR>
+__device__ KI ki_block_exscan(KI v, KI ident, KI *sh)
+{
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+    KI x = v;                                    // inclusive scan within the warp
+    for (int o = 1; o < 32; o <<= 1) {
+        const KI y = DIR > 0 ? ki_shfl_up(x, o) : ki_shfl_down(x, o);
+        const bool take = DIR > 0 ? lane >= o : lane + o < 32;
+        if (take) x = DIR > 0 ? ki_max(x, y) : ki_min(x, y);
+    }
+    if (DIR > 0 ? lane == 31 : lane == 0) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {                                // inclusive scan over the warps
+        KI c = lane < nw ? sh[lane] : ident;
+        for (int o = 1; o < 32; o <<= 1) {
+            const KI y = DIR > 0 ? ki_shfl_up(c, o) : ki_shfl_down(c, o);
+            const bool take = DIR > 0 ? lane >= o : lane + o < 32;
+            if (take) c = DIR > 0 ? ki_max(c, y) : ki_min(c, y);
+        }
+        sh[32 + lane] = c;
+    }
+    __syncthreads();
+    KI before = ident;                           // the warps ahead in the scan direction
+    if (DIR > 0 && w > 0) before = sh[32 + w - 1];
+    if (DIR < 0 && w < nw - 1) before = sh[32 + w + 1];
+    KI ex = DIR > 0 ? ki_shfl_up(x, 1) : ki_shfl_down(x, 1);
+    if (DIR > 0 ? lane == 0 : lane == 31) ex = ident;
+    __syncthreads();                             // sh free for the next call
+    return DIR > 0 ? ki_max(before, ex) : ki_min(before, ex);
+}
+
+// exclusive prefix maximum and suffix minimum over the tiles (one block)
+__global__ void __launch_bounds__(1024) k_ns_prefix(NsTile *__restrict__ t, int nt)
+{
+    __shared__ KI sh[64];
+    const int tid = threadIdx.x;
+    const int chunk = (nt + 1023) / 1024;
+    const int q0 = min(nt, tid * chunk), q1 = min(nt, q0 + chunk);
+    KI mx = ki_low(), mn = ki_high();
+    for (int q = q0; q < q1; ++q) { mx = ki_max(mx, t[q].mx); mn = ki_min(mn, t[q].mn); }
+    KI run = ki_block_exscan<1>(mx, ki_low(), sh);
+    for (int q = q0; q < q1; ++q) { t[q].pre = run; run = ki_max(run, t[q].mx); }
+    run = ki_block_exscan<-1>(mn, ki_high(), sh);
+    for (int q = q1 - 1; q >= q0; --q) { t[q].suf = run; run = ki_min(run, t[q].mn); }
+}
+
+// flag the misplaced elements; count them per tile
+__global__ void __launch_bounds__(NS_THREADS) k_ns_mark(const uint64_t *__restrict__ keys,
+                                                        const uint32_t *__restrict__ ids, int64_t n,
+                                                        NsTile *__restrict__ t, uint8_t *__restrict__ flag)
+{
+    __shared__ KI sh[64];
+    __shared__ int scnt[NS_THREADS / 32];
+    const int64_t b0 = (int64_t)blockIdx.x * NS_TILE + NS_PER * threadIdx.x;
+    KI e[NS_PER];
+#pragma unroll
+    for (int u = 0; u < NS_PER; ++u) {
+        const int64_t i = b0 + u;
+        e[u] = i < n ? KI{keys[i], ids[i], 0u} : ki_high();
+    }
+    KI tmx = ki_low(), tmn = ki_high();
+#pragma unroll
+    for (int u = 0; u < NS_PER; ++u) { tmx = ki_max(tmx, e[u]); tmn = ki_min(tmn, e[u]); }
+    KI pre = ki_block_exscan<1>(tmx, ki_low(), sh);
+    KI suf = ki_block_exscan<-1>(tmn, ki_high(), sh);
+    pre = ki_max(pre, t[blockIdx.x].pre);
+    suf = ki_min(suf, t[blockIdx.x].suf);
+    KI sufs[NS_PER];
+#pragma unroll
+    for (int u = NS_PER - 1; u >= 0; --u) { sufs[u] = suf; suf = ki_min(suf, e[u]); }
+    int c = 0;
+#pragma unroll
+    for (int u = 0; u < NS_PER; ++u) {
+        const int64_t i = b0 + u;
+        const bool in_place = ki_lt(pre, e[u]) && ki_lt(e[u], sufs[u]);
+        pre = ki_max(pre, e[u]);
+        if (i < n) {
+            flag[i] = in_place ? 0 : 1;
+            c += in_place ? 0 : 1;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) scnt[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int k = 0; k < NS_THREADS / 32; ++k) tot += scnt[k];
+        t[blockIdx.x].cnt = tot;
+    }
+}
+
+// exclusive scan of the per-tile counts (one block); total -> cnt->ns_total
+__global__ void __launch_bounds__(1024) k_ns_offsets(NsTile *__restrict__ t, int nt, DevCounters *cnt)
+{
+    __shared__ long long sh[1024];
+    const int tid = threadIdx.x;
+    const int chunk = (nt + 1023) / 1024;
+    const int q0 = min(nt, tid * chunk), q1 = min(nt, q0 + chunk);
+    long long loc = 0;
+    for (int q = q0; q < q1; ++q) loc += t[q].cnt;
+    sh[tid] = loc;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const long long v = tid >= o ? sh[tid - o] : 0;
+        __syncthreads();
+        sh[tid] += v;
+        __syncthreads();
+    }
+    long long run = sh[tid] - loc;
+    for (int q = q0; q < q1; ++q) { t[q].off = (int32_t)run; run += t[q].cnt; }
+    if (tid == 1023) cnt->ns_total = sh[1023];
+}
+
+// misplaced elements (key, id, position) in position order
+__global__ void __launch_bounds__(NS_THREADS) k_ns_compact(const uint64_t *__restrict__ keys,
+                                                           const uint32_t *__restrict__ ids, int64_t n,
+                                                           const NsTile *__restrict__ t,
+                                                           const uint8_t *__restrict__ flag,
+                                                           uint64_t *__restrict__ mk, uint32_t *__restrict__ mi,
+                                                           int32_t *__restrict__ mpos)
+{
+    __shared__ int sw[NS_THREADS / 32];
+    const int64_t b0 = (int64_t)blockIdx.x * NS_TILE + NS_PER * threadIdx.x;
+    int f[NS_PER], c = 0;
+#pragma unroll
+    for (int u = 0; u < NS_PER; ++u) {
+        const int64_t i = b0 + u;
+        f[u] = (i < n) ? flag[i] : 0;
+        c += f[u];
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sw[w] = x;
+    __syncthreads();
+    int before = 0;
+    for (int k = 0; k < w; ++k) before += sw[k];
+    int o = t[blockIdx.x].off + before + x - c;
+#pragma unroll
+    for (int u = 0; u < NS_PER; ++u) {
+        if (!f[u]) continue;
+        const int64_t i = b0 + u;
+        mk[o] = keys[i];
+        mi[o] = ids[i];
+        mpos[o] = (int32_t)i;
+        ++o;
+    }
+}
+
+// rank of each misplaced element among the misplaced ones (equal (key, id)
+// pairs ordered by position); it goes to the rank-th misplaced position
+constexpr int NS_RANK_T = 256;
+__global__ void __launch_bounds__(NS_RANK_T) k_ns_rank(const uint64_t *__restrict__ mk,
+                                                       const uint32_t *__restrict__ mi,
+                                                       const int32_t *__restrict__ mpos, int m,
+                                                       uint64_t *__restrict__ keys_out,
+                                                       uint32_t *__restrict__ src_pos)
+{
+    __shared__ uint64_t sk[NS_RANK_T];
+    __shared__ uint32_t si[NS_RANK_T];
+    const int e = blockIdx.x * NS_RANK_T + threadIdx.x;
+    const bool valid = e < m;
+    const uint64_t ke = valid ? mk[e] : 0;
+    const uint32_t ie = valid ? mi[e] : 0;
+    int r = 0;
+    for (int base = 0; base < m; base += NS_RANK_T) {
+        const int f = base + threadIdx.x;
+        __syncthreads();
+        if (f < m) { sk[threadIdx.x] = mk[f]; si[threadIdx.x] = mi[f]; }
+        __syncthreads();
+        const int lim = min(NS_RANK_T, m - base);
+        for (int k = 0; k < lim; ++k) {
+            const uint64_t kf = sk[k];
+            const uint32_t jf = si[k];
+            r += (kf < ke || (kf == ke && (jf < ie || (jf == ie && base + k < e)))) ? 1 : 0;
+        }
+    }
+    if (valid) {
+        const int32_t dest = mpos[r];
+        keys_out[dest] = ke;
+        src_pos[r] = (uint32_t)mpos[e];
+    }
+}
+
+// move only the misplaced particles: gather into scratch, then put back
+__global__ void k_ns_gather(FieldTable t, const uint32_t *__restrict__ src_pos, int m)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    const uint32_t p = src_pos[k];
+    for (int f = 0; f < t.nf; ++f) {
+        if (t.size[f] == 8) ((double *)t.dst[f])[k] = ((const double *)t.src[f])[p];
+        else ((uint32_t *)t.dst[f])[k] = ((const uint32_t *)t.src[f])[p];
+    }
+}
+
+__global__ void k_ns_put(FieldTable t, const int32_t *__restrict__ mpos, int m)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    const int32_t d = mpos[k];
+    for (int f = 0; f < t.nf; ++f) {
+        if (t.size[f] == 8) ((double *)t.src[f])[d] = ((const double *)t.dst[f])[k];
+        else ((uint32_t *)t.src[f])[d] = ((const uint32_t *)t.dst[f])[k];
     }
 }
 
@@ -559,6 +833,45 @@ int keys_impl(sph_ctx *ctx, const sph_particles *p, uint64_t *keys, uint32_t *va
     return SPH_OK;
 }
 
+// The near-sorted path: *moved = number of particles it moved (0: already in
+// key order), or -1 when more than the limit are misplaced and the full sort
+// is needed (nothing has been moved then).
+int near_sorted(sph_ctx *ctx, sph_particles *p, const FieldTable &t, int64_t *moved, cudaStream_t s)
+{
+    const int64_t n = p->n;
+    *moved = -1;
+    const int nt = (int)((n + NS_TILE - 1) / NS_TILE);
+    k_ns_tiles<<<nt, NS_THREADS, 0, s>>>(ctx->key_a, p->id, n, ctx->ns_tiles);
+    SPH_CHECK_LAUNCH();
+    k_ns_prefix<<<1, 1024, 0, s>>>(ctx->ns_tiles, nt);
+    SPH_CHECK_LAUNCH();
+    k_ns_mark<<<nt, NS_THREADS, 0, s>>>(ctx->key_a, p->id, n, ctx->ns_tiles, ctx->dlev);
+    SPH_CHECK_LAUNCH();
+    k_ns_offsets<<<1, 1024, 0, s>>>(ctx->ns_tiles, nt, ctx->dcnt);
+    SPH_CHECK_LAUNCH();
+    SPH_TRY(sync_counters(ctx, s));
+    const int64_t m = ctx->hcnt->ns_total;
+    const int64_t limit = std::min<int64_t>(NS_LIMIT, std::max<int64_t>(n / 4, 1024));
+    if (m > limit) return SPH_OK;
+    if (m > 0) {
+        uint64_t *mk = ctx->key_b;
+        uint32_t *mi = ctx->val_b;
+        int32_t *mpos = ctx->itmp0;
+        uint32_t *src_pos = (uint32_t *)ctx->itmp1;
+        k_ns_compact<<<nt, NS_THREADS, 0, s>>>(ctx->key_a, p->id, n, ctx->ns_tiles, ctx->dlev, mk, mi, mpos);
+        SPH_CHECK_LAUNCH();
+        const int mi32 = (int)m;
+        k_ns_rank<<<(mi32 + NS_RANK_T - 1) / NS_RANK_T, NS_RANK_T, 0, s>>>(mk, mi, mpos, mi32, ctx->key_a, src_pos);
+        SPH_CHECK_LAUNCH();
+        k_ns_gather<<<grid_for(m, 256), 256, 0, s>>>(t, src_pos, mi32);
+        SPH_CHECK_LAUNCH();
+        k_ns_put<<<grid_for(m, 256), 256, 0, s>>>(t, mpos, mi32);
+        SPH_CHECK_LAUNCH();
+    }
+    *moved = m;
+    return SPH_OK;
+}
+
 template <typename T>
 int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
 {
@@ -566,16 +879,20 @@ int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
     ctx->tree_valid = false;
     SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->err, 0, sizeof(uint32_t), s));
     SPH_TRY(keys_impl<T>(ctx, p, ctx->key_a, ctx->val_a, s));
-    SPH_TRY(radix_sort(ctx, n, s));
-    k_fix_ties<<<grid_for(n, 256), 256, 0, s>>>(ctx->key_a, ctx->val_a, p->id, n, ctx->dcnt);
-    SPH_CHECK_LAUNCH();
-    // permute every particle array into key order
     FieldTable t = make_table<T>(ctx, p);
-    k_gather<<<grid_for(n, 256), 256, 0, s>>>(t, ctx->val_a, n, ctx->xh, ctx->xl, ctx->yh, ctx->yl, ctx->zh,
-                                              ctx->zl);
-    SPH_CHECK_LAUNCH();
-    k_copy_back<<<grid_for(n, 256), 256, 0, s>>>(t, n);
-    SPH_CHECK_LAUNCH();
+    int64_t m = -1;
+    SPH_TRY(near_sorted(ctx, p, t, &m, s));
+    if (m < 0) {
+        // full sort, then permute every particle array into key order
+        SPH_TRY(radix_sort(ctx, n, s));
+        k_fix_ties<<<grid_for(n, 256), 256, 0, s>>>(ctx->key_a, ctx->val_a, p->id, n, ctx->dcnt);
+        SPH_CHECK_LAUNCH();
+        k_gather<<<grid_for(n, 256), 256, 0, s>>>(t, ctx->val_a, n);
+        SPH_CHECK_LAUNCH();
+        k_copy_back<<<grid_for(n, 256), 256, 0, s>>>(t, n);
+        SPH_CHECK_LAUNCH();
+    }
+    ctx->ns_moved = m;
     k_pack_pos<T><<<grid_for(n, 256), 256, 0, s>>>(p->x, p->y, p->z, (const T *)p->m, n, ctx->srcA, ctx->srcB);
     SPH_CHECK_LAUNCH();
     // octree leaves and target groups

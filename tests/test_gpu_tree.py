@@ -106,3 +106,40 @@ def test_build_tree_order_and_leaves(name, leaf_size):
     assert np.array_equal(lv, lvl[np.array(start)])
     nl, ng = B.sph_tree_info(ctx)
     assert nl == len(start) and 1 <= ng <= w.n
+
+
+@pytest.mark.parametrize("moved", [0, 1, 50, 3000, 20000])
+def test_rebuild_of_nearly_sorted_particles(moved):
+    """A rebuild after small moves (the state of every step after the first)
+    finds most particles in place and moves only the misplaced ones; the
+    order must still be the (key, id) sort of the current keys.  Large moves
+    take the full sort."""
+    B = need_gpu()
+    w = inputs.lattice(24, jitter=0.1)                  # 13,824 particles
+    rng = np.random.default_rng(moved + 11)
+    w.u = rng.random(w.n) + 0.5
+    ctx = B.Context(w.params, w.n)
+    p = B.Particles.from_workload(w, fp64=True)
+    B.sph_build_tree(ctx, p)                             # key order of the initial state
+    g = p.numpy()
+    x, y, z = g["x"].copy(), g["y"].copy(), g["z"].copy()
+    k = min(moved, w.n)
+    sel = rng.choice(w.n, size=k, replace=False)
+    spacing = 1.0 / 24
+    x[sel] = np.mod(x[sel] + rng.uniform(-1.5, 1.5, k) * spacing, 1.0)
+    y[sel] = np.mod(y[sel] + rng.uniform(-1.5, 1.5, k) * spacing, 1.0)
+    if k > 1:                                            # two particles on one key: ties by id
+        x[sel[1]], y[sel[1]], z[sel[1]] = x[sel[0]], y[sel[0]], z[sel[0]]
+    for f, v in (("x", x), ("y", y), ("z", z)):
+        getattr(p, f).copy_(torch.from_numpy(v))
+    B.sph_build_tree(ctx, p)
+    op = to_oracle_params(oracle, w.params)
+    lo, L = oracle.domain(x, y, z, op)
+    keys = oracle.morton_keys(x, y, z, lo, L)
+    perm = oracle.sort_perm(keys, g["id"])
+    h = p.numpy()
+    assert np.array_equal(h["id"], g["id"][perm])
+    assert np.array_equal(h["x"], x[perm]) and np.array_equal(h["y"], y[perm])
+    assert np.array_equal(h["u"], g["u"][perm])
+    lb, _ = B.sph_export_leaves(ctx)
+    assert lb[-1] == w.n and np.all(np.diff(lb) > 0)
