@@ -221,10 +221,16 @@ __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
             const df gr = df_mul(df_mul(sig, df_sqr(hi2)), df_mul(dwq, rinv));     // grad_a W = gr r_ab
             df Pi = df{0.f, 0.f};
             if (df_lt0(vdotr)) {
-                const df mu = df_mul(df_mul(hab, vdotr), df_rcp_fast(df_add(r2, df_mul(eps, df_sqr(hab)))));
-                const df cbar = df_scale(df_add(ca, df{Fb.x, Fb.y}), 0.5f);
+                // mu = hab v.r / den, Pi = (-alpha cbar mu + beta mu^2) / rbar with
+                // den = r^2 + eps hab^2, through one reciprocal X = 1 / (den rbar):
+                // mu / rbar = hab v.r X, mu = (mu / rbar) rbar
+                const df hv = df_mul(hab, vdotr);
+                const df den = df_add(r2, df_mul(eps, df_sqr(hab)));
                 const df rbar = df_scale(df_add(rhoa, df{Eb.x, Eb.y}), 0.5f);
-                Pi = df_mul(df_add(df_neg(df_mul(df_mul(alpha, cbar), mu)), df_mul(beta, df_sqr(mu))), df_rcp_fast(rbar));
+                const df mu_r = df_mul(hv, df_rcp_fast(df_mul(den, rbar)));
+                const df mu = df_mul(mu_r, rbar);
+                const df cbar = df_scale(df_add(ca, df{Fb.x, Fb.y}), 0.5f);
+                Pi = df_mul(mu_r, df_sub(df_mul(beta, mu), df_mul(alpha, cbar)));
             }
             const df coef = df_mul(mb, df_mul(df_add(df_add(pra, df{Eb.z, Eb.w}), Pi), gr));
             df_acc(accx, df_neg(df_mul(coef, dx)));

@@ -13,16 +13,12 @@
 namespace {
 
 constexpr int NP = SPH_HNET_NPARAM;
-constexpr int O_W1 = 0, O_B1 = 320, O_W2 = 384, O_B2 = 4480, O_W3 = 4544, O_B3 = 4608;
+// parameter layout: W1 [64][5] at 0, b1 at 320, W2 [64][64] at 384, b2 at 4480, W3 at 4544, b3 at 4608
+constexpr int O_W1 = 0, O_W2 = 384, O_B2 = 4480;
 constexpr int H = 64;
 
-__device__ __forceinline__ float sigm(float z) { return 1.f / (1.f + __expf(-z)); }
-
-__device__ void load_weights(const __nv_bfloat16 *__restrict__ w, float *s)
-{
-    for (int k = threadIdx.x; k < NP; k += blockDim.x) s[k] = __bfloat162float(w[k]);
-    __syncthreads();
-}
+// logistic function with the hardware exponential and reciprocal (a few ulp)
+__device__ __forceinline__ float sigm(float z) { return __fdividef(1.f, 1.f + __expf(-z)); }
 
 // ---------------------------------------------------------------- features
 // f0 = log(h / hbar), hbar = eta (m / rho_ref)^(1/3)
@@ -214,102 +210,199 @@ __global__ void __launch_bounds__(TM) k_infer_tc(const __nv_bfloat16 *__restrict
 }
 
 // ---------------------------------------------------------------- gradient
-// Each block processes chunks of S samples: one thread per sample runs the
-// forward and backward pass and leaves x, a1, a2, d1, d2 (d = dL/dz) in shared
-// memory; then every thread accumulates a fixed subset of the 4609 gradient
-// entries over the chunk.  Block partials are reduced in a fixed order.
-constexpr int GS = 64;           // samples per chunk = threads per block
-constexpr int ST = 65;           // row stride (conflict-free)
+// Blocks of GT threads take chunks of GS samples.  Per chunk the three layers
+// run as shared-memory products in which each thread owns a 4 x 4 tile
+// (4 samples x 4 units): forward z1, a1 = silu(z1), z2 = a1 W2^T + b2,
+// a2 = silu(z2), y = w3 . a2 + b3; residual r = f3 y - t, d3 = 2 r f3 / B;
+// backward d2 = d3 w3 silu'(z2), d1 = (d2 W2) silu'(z1).  The W2 gradient
+// sum_s d2 a1^T accumulates in a 4 x 4 register tile per thread over the
+// block's chunks, the 513 smaller entries in up to three registers per
+// thread; each block writes its partial gradient once, and the partials are
+// reduced in a fixed order.
+constexpr int GT = 256;          // threads per block
+constexpr int GS = 64;           // samples per chunk
+constexpr int ST = 68;           // row stride of the per-sample arrays (16-byte rows)
+constexpr int NSMALL = 320 + 64 + 64 + 64 + 1;   // W1, b1, b2, W3, b3
 
-__global__ void __launch_bounds__(GS) k_grad(const __nv_bfloat16 *__restrict__ wb, const float *__restrict__ f,
+__host__ __device__ constexpr int grad_smem_floats()
+{
+    return H * ST + 320 + 64 + 64 + 64 + 4 + GS * 8 + 4 * GS * ST + 2 * GS;
+}
+
+__global__ void __launch_bounds__(GT) k_grad(const __nv_bfloat16 *__restrict__ wb, const float *__restrict__ f,
                                             const float *__restrict__ t, int64_t nb, float *__restrict__ part)
 {
     extern __shared__ __align__(16) float sm[];
-    float *w = sm;                           // NP (+3)
-    float *sx = w + NP + 3;                  // GS x 5
-    float *sa1 = sx + GS * 5;                // GS x ST
-    float *sa2 = sa1 + GS * ST;
-    float *sd1 = sa2 + GS * ST;
-    float *sd2 = sd1 + GS * ST;
-    float *sd3 = sd2 + GS * ST;              // GS
-    load_weights(wb, w);
+    float *W2 = sm;                          // [n][ST]: W2[n][k]
+    float *W1 = W2 + H * ST;                 // [j][5]
+    float *b1 = W1 + 320, *b2 = b1 + 64, *w3 = b2 + 64, *b3 = w3 + 64;
+    float *X = b3 + 4;                       // [s][8]
+    float *A1 = X + GS * 8;                  // [s][ST]
+    float *A2 = A1 + GS * ST;
+    float *D2 = A2 + GS * ST;
+    float *D1 = D2 + GS * ST;
+    float *d3 = D1 + GS * ST;                // [s]
+    float *ys = d3 + GS;                     // [s]
     const int tid = threadIdx.x;
-    // this block's partial row; entries p = tid, tid + GS, ... belong to this thread
-    float *out = part + (int64_t)blockIdx.x * (NP + 1);
-    for (int p = tid; p < NP; p += GS) out[p] = 0.f;
+    for (int k = tid; k < H * H; k += GT) W2[(k / H) * ST + k % H] = __bfloat162float(wb[O_W2 + k]);
+    for (int k = tid; k < 320 + 64; k += GT) W1[k] = __bfloat162float(wb[O_W1 + k]);      // W1, b1
+    for (int k = tid; k < 64 + 64 + 1; k += GT) b2[k] = __bfloat162float(wb[O_B2 + k]);  // b2, w3, b3
+    __syncthreads();
+
+    const int r0 = 4 * (tid / 16), c0 = 4 * (tid % 16);   // this thread's tile: rows r0.., columns c0..
+    float gw2[4][4] = {};                                 // dL/dW2[r0 + i][c0 + j]
+    float gsm[3] = {0.f, 0.f, 0.f};                       // small entries q = tid, tid + 256, tid + 512
     float lsum = 0.f;
     const float inv_b = 1.f / (float)nb;
     const int64_t nchunks = (nb + GS - 1) / GS;
     for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const int64_t s = c * GS + tid;
-        const bool valid = s < nb;
-        float x[5];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) x[k] = valid ? f[5 * s + k] : 0.f;
-        float *a1 = sa1 + tid * ST, *a2 = sa2 + tid * ST, *d1 = sd1 + tid * ST, *d2 = sd2 + tid * ST;
-        for (int j = 0; j < H; ++j) {
-            float z = w[O_B1 + j];
-#pragma unroll
-            for (int k = 0; k < 5; ++k) z += w[O_W1 + 5 * j + k] * x[k];
-            d1[j] = z;                       // keep z1 until the backward pass
-            a1[j] = z * sigm(z);
+        const int64_t s0 = c * GS;
+        for (int k = tid; k < GS * 5; k += GT) {
+            const int u = k / 5, q = k % 5;
+            X[u * 8 + q] = s0 + u < nb ? f[5 * (s0 + u) + q] : 0.f;
         }
-        float y = w[O_B3];
-        for (int j = 0; j < H; ++j) {
-            float z = w[O_B2 + j];
-            for (int k = 0; k < H; ++k) z += w[O_W2 + H * j + k] * a1[k];
-            const float sg = sigm(z);
-            a2[j] = z * sg;
-            d2[j] = sg * (1.f + z * (1.f - sg));   // silu'(z2), scaled below
-            y += w[O_W3 + j] * a2[j];
-        }
-        const float r = valid ? x[3] * y - t[s] : 0.f;      // prediction f3 * y
-        lsum += r * r;
-        const float d3 = 2.f * r * x[3] * inv_b;
-        sd3[tid] = d3;
-        for (int j = 0; j < H; ++j) d2[j] *= d3 * w[O_W3 + j];
-        for (int k = 0; k < H; ++k) {
-            float g = 0.f;
-            for (int j = 0; j < H; ++j) g += w[O_W2 + H * j + k] * d2[j];
-            const float z = d1[k];
-            const float sg = sigm(z);
-            d1[k] = g * sg * (1.f + z * (1.f - sg));
-        }
-#pragma unroll
-        for (int k = 0; k < 5; ++k) sx[tid * 5 + k] = x[k];
         __syncthreads();
-#pragma unroll 1
-        for (int p = tid; p < NP; p += GS) {
-            float g = 0.f;
-            if (p < O_B1) {                          // W1[j][k]
-                const int j = p / 5, k = p % 5;
-                for (int u = 0; u < GS; ++u) g += sd1[u * ST + j] * sx[u * 5 + k];
-            } else if (p < O_W2) {                   // b1[j]
-                const int j = p - O_B1;
-                for (int u = 0; u < GS; ++u) g += sd1[u * ST + j];
-            } else if (p < O_B2) {                   // W2[j][k]
-                const int j = (p - O_W2) / H, k = (p - O_W2) % H;
-                for (int u = 0; u < GS; ++u) g += sd2[u * ST + j] * sa1[u * ST + k];
-            } else if (p < O_W3) {                   // b2[j]
-                const int j = p - O_B2;
-                for (int u = 0; u < GS; ++u) g += sd2[u * ST + j];
-            } else if (p < O_B3) {                   // W3[0][j]
-                const int j = p - O_W3;
-                for (int u = 0; u < GS; ++u) g += sd3[u] * sa2[u * ST + j];
-            } else {                                 // b3
-                for (int u = 0; u < GS; ++u) g += sd3[u];
+        // layer 1 (tile: samples r0.., units c0..); keep silu'(z1)
+        float p1[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int u = c0 + j;
+                float z = b1[u];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) z += W1[5 * u + q] * X[(r0 + i) * 8 + q];
+                const float sg = sigm(z);
+                A1[(r0 + i) * ST + u] = z * sg;
+                p1[i][j] = sg * (1.f + z * (1.f - sg));
             }
-            out[p] += g;
+        __syncthreads();
+        // layer 2 (tile: samples r0.., units c0..)
+        float z2[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) z2[i][j] = b2[c0 + j];
+#pragma unroll 4
+        for (int k = 0; k < H; k += 4) {
+            float4 av[4], wv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = *reinterpret_cast<const float4 *>(A1 + (r0 + i) * ST + k);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) wv[j] = *reinterpret_cast<const float4 *>(W2 + (c0 + j) * ST + k);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    z2[i][j] += av[i].x * wv[j].x + av[i].y * wv[j].y + av[i].z * wv[j].z + av[i].w * wv[j].w;
+        }
+        float p2[4][4], yp[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            yp[i] = 0.f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float z = z2[i][j], sg = sigm(z);
+                const float a2 = z * sg;
+                A2[(r0 + i) * ST + c0 + j] = a2;
+                p2[i][j] = sg * (1.f + z * (1.f - sg));
+                yp[i] += w3[c0 + j] * a2;
+            }
+        }
+        // y: sum over the 16 threads of a row block (lanes 16 apart share none)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            for (int o = 8; o > 0; o >>= 1) yp[i] += __shfl_xor_sync(0xffffffffu, yp[i], o);
+        if ((tid & 15) == 0)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ys[r0 + i] = b3[0] + yp[i];
+        __syncthreads();
+        if (tid < GS) {
+            const bool valid = s0 + tid < nb;
+            const float f3 = X[tid * 8 + 3];
+            const float r = valid ? f3 * ys[tid] - t[s0 + tid] : 0.f;     // prediction f3 * y
+            lsum += r * r;
+            d3[tid] = 2.f * r * f3 * inv_b;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) D2[(r0 + i) * ST + c0 + j] = p2[i][j] * d3[r0 + i] * w3[c0 + j];
+        __syncthreads();
+        // backward through W2 (tile: samples r0.., inputs c0..)
+        float g1[4][4] = {};
+#pragma unroll 4
+        for (int n = 0; n < H; n += 4) {
+            float4 dv[4], wv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) dv[i] = *reinterpret_cast<const float4 *>(D2 + (r0 + i) * ST + n);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) wv[m] = *reinterpret_cast<const float4 *>(W2 + (n + m) * ST + c0);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                g1[i][0] += dv[i].x * wv[0].x + dv[i].y * wv[1].x + dv[i].z * wv[2].x + dv[i].w * wv[3].x;
+                g1[i][1] += dv[i].x * wv[0].y + dv[i].y * wv[1].y + dv[i].z * wv[2].y + dv[i].w * wv[3].y;
+                g1[i][2] += dv[i].x * wv[0].z + dv[i].y * wv[1].z + dv[i].z * wv[2].z + dv[i].w * wv[3].z;
+                g1[i][3] += dv[i].x * wv[0].w + dv[i].y * wv[1].w + dv[i].z * wv[2].w + dv[i].w * wv[3].w;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) D1[(r0 + i) * ST + c0 + j] = g1[i][j] * p1[i][j];
+        __syncthreads();
+        // W2 gradient: tile (outputs n = r0.., inputs k = c0..), sum over the chunk
+#pragma unroll 4
+        for (int u = 0; u < GS; ++u) {
+            const float4 dn = *reinterpret_cast<const float4 *>(D2 + u * ST + r0);
+            const float4 ak = *reinterpret_cast<const float4 *>(A1 + u * ST + c0);
+            const float dd[4] = {dn.x, dn.y, dn.z, dn.w}, aa[4] = {ak.x, ak.y, ak.z, ak.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) gw2[i][j] += dd[i] * aa[j];
+        }
+        // the 513 small entries
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const int q = tid + GT * e;
+            if (q >= NSMALL) break;
+            float g = 0.f;
+            if (q < 320) {
+                const int j = q / 5, qq = q % 5;
+                for (int u = 0; u < GS; ++u) g += D1[u * ST + j] * X[u * 8 + qq];
+            } else if (q < 384) {
+                for (int u = 0; u < GS; ++u) g += D1[u * ST + q - 320];
+            } else if (q < 448) {
+                for (int u = 0; u < GS; ++u) g += D2[u * ST + q - 384];
+            } else if (q < 512) {
+                for (int u = 0; u < GS; ++u) g += d3[u] * A2[u * ST + q - 448];
+            } else {
+                for (int u = 0; u < GS; ++u) g += d3[u];
+            }
+            gsm[e] += g;
         }
         __syncthreads();
     }
+    float *out = part + (int64_t)blockIdx.x * (NP + 1);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) out[O_W2 + (r0 + i) * H + c0 + j] = gw2[i][j];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int q = tid + GT * e;
+        if (q >= NSMALL) break;
+        out[q < 384 ? q : O_B2 + (q - 384)] = gsm[e];
+    }
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-    __shared__ float ls[GS / 32];
+    __shared__ float ls[GT / 32];
     if ((tid & 31) == 0) ls[tid >> 5] = lsum;
     __syncthreads();
     if (tid == 0) {
         float v = 0.f;
-        for (int k = 0; k < GS / 32; ++k) v += ls[k];
+        for (int k = 0; k < GT / 32; ++k) v += ls[k];
         out[NP] = v;
     }
 }
@@ -372,7 +465,7 @@ __global__ void k_sample(const float *__restrict__ feats, const T *__restrict__ 
     st[k] = (float)log((double)h[i] / (double)hold[i]);
 }
 
-size_t grad_smem() { return sizeof(float) * (NP + 3 + GS * 5 + 4 * GS * ST + GS); }
+size_t grad_smem() { return sizeof(float) * (size_t)grad_smem_floats(); }
 
 }  // namespace
 
@@ -414,7 +507,7 @@ int hnet_grad(sph_ctx *ctx, const float *feats, const float *target, int64_t nb,
     int64_t blocks = (nb + GS - 1) / GS;
     if (blocks > ctx->hn_part_blocks) blocks = ctx->hn_part_blocks;
     if (blocks < 1) blocks = 1;
-    k_grad<<<(unsigned)blocks, GS, grad_smem(), s>>>(ctx->hn_bf16, feats, target, nb, ctx->hn_part);
+    k_grad<<<(unsigned)blocks, GT, grad_smem(), s>>>(ctx->hn_bf16, feats, target, nb, ctx->hn_part);
     SPH_CHECK_LAUNCH();
     k_grad_reduce<<<grid_for(NP + 1, 256), 256, 0, s>>>(ctx->hn_part, (int)blocks, nb, ctx->hn_grad, ctx->dcnt);
     SPH_CHECK_LAUNCH();
