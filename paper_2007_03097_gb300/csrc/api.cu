@@ -157,8 +157,6 @@ int allocate(sph_ctx *c, int64_t N)
     SPH_TRY(alloc(c, &c->hn_grad, SPH_HNET_NPARAM));
     c->hn_part_blocks = 4 * c->num_sms;
     SPH_TRY(alloc(c, &c->hn_part, (size_t)c->hn_part_blocks * (SPH_HNET_NPARAM + 1)));
-    SPH_TRY(alloc(c, &c->feats, 5 * N));
-    SPH_TRY(alloc(c, &c->hn_y, N));
     SPH_TRY(alloc(c, &c->hn_sample, 6 * (size_t)c->prm.hnet_batch));
     SPH_CUDA(cudaMemset(c->hn_master, 0, sizeof(float) * SPH_HNET_NPARAM));
     SPH_CUDA(cudaMemset(c->hn_bf16, 0, sizeof(__nv_bfloat16) * SPH_HNET_NPARAM));
@@ -180,7 +178,7 @@ void release(sph_ctx *c)
                     c->group_off, c->it_lo, c->it_hi, c->it_flags, c->it_sweeps, c->cov, c->act_groups[0],
                     c->act_groups[1], c->vpx, c->vpy, c->vpz, c->upred, c->pr2, c->hold, c->hseed, c->hstart, c->gbuf,
                     c->scan_tmp, c->red, c->dcnt, c->hn_master, c->hn_bf16, c->hn_m, c->hn_v, c->hn_grad,
-                    c->hn_part, c->feats, c->hn_y, c->hn_sample};
+                    c->hn_part, c->hn_sample};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->hcnt) cudaFreeHost(c->hcnt);
@@ -310,14 +308,14 @@ int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet, sph_step_s
     SPH_CUDA(cudaEventRecord(ev[1], s));
     const void *seed = nullptr;
     SPH_TRY(copy_field(ctx, ctx->hold, p->h, p->n, s));
-    if (seed_net || train_net) SPH_TRY(hnet_features(ctx, p, dt, ctx->feats, s));
     if (seed_net) {
         SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->hnet_fallback, 0, sizeof(int32_t), s));
         SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->hnet_err, 0, sizeof(uint32_t), s));
-        SPH_TRY(hnet_infer(ctx, ctx->feats, p->n, ctx->hn_y, s));
-        SPH_TRY(hnet_seed(ctx, p, ctx->hn_y, ctx->hseed, s));
+        SPH_TRY(hnet_seed_from_fields(ctx, p, dt, train_net, ctx->hseed, s));
         seed = ctx->hseed;
         local.hnet_used = 1;
+    } else if (train_net) {
+        SPH_TRY(hnet_sample_features(ctx, p, dt, s));
     }
     SPH_CUDA(cudaEventRecord(ev[2], s));
     int st = density_run(ctx, p, seed, &local.density, s);

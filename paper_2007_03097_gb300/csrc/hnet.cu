@@ -27,24 +27,38 @@ __device__ __forceinline__ float sigm(float z) { return __fdividef(1.f, 1.f + __
 // f3 = div v * dt
 // f4 = log(h / hprev)  (0 when hprev <= 0)
 template <typename T>
-__global__ void k_features(const T *__restrict__ h, const T *__restrict__ hprev, const int32_t *__restrict__ nnb,
-                           const T *__restrict__ rho, const T *__restrict__ m, const T *__restrict__ divv,
-                           int64_t n, float dt, float eta, float rho_ref, float *__restrict__ f)
+struct FeatArgs {
+    const T *h, *hprev, *rho, *m, *divv;
+    const int32_t *nnb;
+    float dt, eta, rho_ref;
+};
+
+template <typename T>
+__device__ __forceinline__ void features_of(const FeatArgs<T> &fa, int64_t i, float *o)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float hi = (float)h[i], mi = (float)m[i], ri = (float)rho[i];
-    const float eta3 = eta * eta * eta;
-    const float hbar = eta * cbrtf(mi / rho_ref);
+    const float hi = (float)fa.h[i], mi = (float)fa.m[i], ri = (float)fa.rho[i];
+    const float eta3 = fa.eta * fa.eta * fa.eta;
+    const float hbar = fa.eta * cbrtf(mi / fa.rho_ref);
     const float nbar = 32.f * 3.14159265358979f * eta3 / 3.f;
-    const float nb = fmaxf((float)nnb[i], 0.5f);
-    const float hp = (float)hprev[i];
-    float *o = f + 5 * i;
+    const float nb = fmaxf((float)fa.nnb[i], 0.5f);
+    const float hp = (float)fa.hprev[i];
     o[0] = logf(hi / hbar);
     o[1] = logf(nb / nbar);
     o[2] = logf(ri * hi * hi * hi / (mi * eta3));
-    o[3] = (float)divv[i] * dt;
+    o[3] = (float)fa.divv[i] * fa.dt;
     o[4] = hp > 0.f ? logf(hi / hp) : 0.f;
+}
+
+// features of particles i = k * stride, k < count, into f[5 k ..]
+template <typename T>
+__global__ void k_features(FeatArgs<T> fa, int64_t stride, int64_t count, float *__restrict__ f)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    float o[5];
+    features_of(fa, k * stride, o);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) f[5 * k + c] = o[c];
 }
 
 // ------------------------------------------------- inference, tensor cores
@@ -87,8 +101,20 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
+// Step-path result: the seed h exp(s) of each particle (h itself, counted as
+// a fallback, when s is not finite or changes h by more than a factor 2),
+// and the features of the training samples i = k * stride, k < ns.
+template <typename T>
+struct SeedOut {
+    T *seed;
+    float *sf;
+    int64_t stride, ns;
+};
+
+template <bool FIELDS, typename T>
 __global__ void __launch_bounds__(TM) k_infer_tc(const __nv_bfloat16 *__restrict__ wb, const float *__restrict__ f,
-                                                 int64_t nb, float *__restrict__ y, DevCounters *cnt)
+                                                 FeatArgs<T> fa, int64_t nb, float *__restrict__ y, SeedOut<T> so,
+                                                 DevCounters *cnt)
 {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)sm_raw + 1023) & ~(uintptr_t)1023);
@@ -124,9 +150,19 @@ __global__ void __launch_bounds__(TM) k_infer_tc(const __nv_bfloat16 *__restrict
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t s = tile * TM + tid;
         const bool valid = s < nb;
-        float x[5];
+        float x[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        if (valid) {
+            if (FIELDS) {
+                features_of(fa, s, x);
+                if (s % so.stride == 0 && s / so.stride < so.ns) {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) x[k] = valid ? f[5 * s + k] : 0.f;
+                    for (int k = 0; k < 5; ++k) so.sf[5 * (s / so.stride) + k] = x[k];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 5; ++k) x[k] = f[5 * s + k];
+            }
+        }
         // layer 1 and the three-term split, 8 units (one 16-byte row of a core matrix) at a time
 #pragma unroll 1
         for (int c = 0; c < H / 8; ++c) {
@@ -188,7 +224,17 @@ __global__ void __launch_bounds__(TM) k_infer_tc(const __nv_bfloat16 *__restrict
                 out += w3[16 * cc + e] * (z * sigm(z));
             }
         }
-        if (valid) y[s] = x[3] * out;             // s = f3 * y
+        if (valid) {
+            const float sp = x[3] * out;          // s = f3 * y
+            if (FIELDS) {
+                const bool ok = isfinite(sp) && fabsf(sp) <= 0.69314718f;
+                const T hs = fa.h[s];
+                so.seed[s] = ok ? (T)((double)hs * exp((double)sp)) : hs;
+                if (!ok) atomicAdd(&cnt->hnet_fallback, 1);
+            } else {
+                y[s] = sp;
+            }
+        }
         tc::fence_before_sync();
         __syncthreads();                          // TMEM read and A tiles free before the next MMA
     }
@@ -418,6 +464,30 @@ __global__ void k_grad_reduce(const float *__restrict__ part, int nblk, int64_t 
     else cnt->loss = v / (float)nb;
 }
 
+// the reduction of k_grad_reduce followed by the Adam update of k_adam
+__global__ void k_reduce_adam(const float *__restrict__ part, int nblk, int64_t nb, float *__restrict__ g,
+                              DevCounters *cnt, float *__restrict__ th, float *__restrict__ m,
+                              float *__restrict__ v, __nv_bfloat16 *__restrict__ wb, float lr, float bc1,
+                              float bc2)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > NP) return;
+    float gi = 0.f;
+    for (int b = 0; b < nblk; ++b) gi += part[(int64_t)b * (NP + 1) + p];
+    if (p == NP) {
+        cnt->loss = gi / (float)nb;
+        return;
+    }
+    g[p] = gi;
+    const float mi = 0.9f * m[p] + 0.1f * gi;
+    const float vi = 0.999f * v[p] + 0.001f * gi * gi;
+    m[p] = mi;
+    v[p] = vi;
+    const float t = th[p] - lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
+    th[p] = t;
+    wb[p] = __float2bfloat16_rn(t);
+}
+
 __global__ void k_adam(float *__restrict__ th, float *__restrict__ m, float *__restrict__ v,
                        const float *__restrict__ g, __nv_bfloat16 *__restrict__ wb, float lr, float bc1, float bc2)
 {
@@ -439,30 +509,33 @@ __global__ void k_to_bf16(const float *__restrict__ th, __nv_bfloat16 *__restric
     if (p < NP) wb[p] = __float2bfloat16_rn(th[p]);
 }
 
-// h seed = h exp(y); a non-finite y or a change beyond a factor 2 keeps h.
+// targets log(h_new / h_old) of the training samples i = k * stride
 template <typename T>
-__global__ void k_seed(const T *__restrict__ h, const float *__restrict__ y, int64_t n, T *__restrict__ seed,
-                       DevCounters *cnt)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float s = y[i];
-    const bool ok = isfinite(s) && fabsf(s) <= 0.69314718f;
-    seed[i] = ok ? (T)((double)h[i] * exp((double)s)) : h[i];
-    if (!ok) atomicAdd(&cnt->hnet_fallback, 1);
-}
-
-// strided subset of the step's features with targets log(h_new / h_old)
-template <typename T>
-__global__ void k_sample(const float *__restrict__ feats, const T *__restrict__ h, const T *__restrict__ hold,
-                         int64_t n, int64_t stride, int64_t nb, float *__restrict__ sf, float *__restrict__ st)
+__global__ void k_targets(const T *__restrict__ h, const T *__restrict__ hold, int64_t stride, int64_t nb,
+                          float *__restrict__ st)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nb) return;
-    const int64_t i = (k * stride) % n;
-#pragma unroll
-    for (int c = 0; c < 5; ++c) sf[5 * k + c] = feats[5 * i + c];
+    const int64_t i = k * stride;
     st[k] = (float)log((double)h[i] / (double)hold[i]);
+}
+
+template <typename T>
+FeatArgs<T> feat_args(const sph_ctx *ctx, const sph_particles *p, double dt)
+{
+    FeatArgs<T> fa{};
+    fa.h = (const T *)p->h; fa.hprev = (const T *)p->hprev; fa.rho = (const T *)p->rho; fa.m = (const T *)p->m;
+    fa.divv = (const T *)p->divv; fa.nnb = p->nnb;
+    fa.dt = (float)dt; fa.eta = (float)ctx->prm.eta; fa.rho_ref = (float)ctx->prm.rho_ref;
+    return fa;
+}
+
+// training samples of a step: every stride-th particle, at most hnet_batch
+void sample_layout(const sph_ctx *ctx, int64_t n, int64_t *nb, int64_t *stride)
+{
+    *nb = n < ctx->prm.hnet_batch ? n : ctx->prm.hnet_batch;
+    *stride = n / *nb;
+    if (*stride < 1) *stride = 1;
 }
 
 size_t grad_smem() { return sizeof(float) * (size_t)grad_smem_floats(); }
@@ -472,32 +545,72 @@ size_t grad_smem() { return sizeof(float) * (size_t)grad_smem_floats(); }
 int hnet_init(sph_ctx *ctx)
 {
     SPH_CUDA(cudaFuncSetAttribute(k_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem()));
-    SPH_CUDA(cudaFuncSetAttribute(k_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, infer_tc_smem()));
+    SPH_CUDA(cudaFuncSetAttribute(k_infer_tc<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  infer_tc_smem()));
+    SPH_CUDA(cudaFuncSetAttribute(k_infer_tc<true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  infer_tc_smem()));
+    SPH_CUDA(cudaFuncSetAttribute(k_infer_tc<true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  infer_tc_smem()));
     return SPH_OK;
 }
 
 int hnet_features(sph_ctx *ctx, const sph_particles *p, double dt, float *feats, cudaStream_t s)
 {
-    const float eta = (float)ctx->prm.eta, rr = (float)ctx->prm.rho_ref;
     if (ctx->fp64)
-        k_features<double><<<grid_for(p->n, 256), 256, 0, s>>>((const double *)p->h, (const double *)p->hprev, p->nnb,
-                                                               (const double *)p->rho, (const double *)p->m,
-                                                               (const double *)p->divv, p->n, (float)dt, eta, rr, feats);
+        k_features<double><<<grid_for(p->n, 256), 256, 0, s>>>(feat_args<double>(ctx, p, dt), 1, p->n, feats);
     else
-        k_features<float><<<grid_for(p->n, 256), 256, 0, s>>>((const float *)p->h, (const float *)p->hprev, p->nnb,
-                                                              (const float *)p->rho, (const float *)p->m,
-                                                              (const float *)p->divv, p->n, (float)dt, eta, rr, feats);
+        k_features<float><<<grid_for(p->n, 256), 256, 0, s>>>(feat_args<float>(ctx, p, dt), 1, p->n, feats);
     SPH_CHECK_LAUNCH();
     return SPH_OK;
 }
 
+namespace {
+unsigned infer_blocks(const sph_ctx *ctx, int64_t nb)
+{
+    int64_t blocks = (nb + TM - 1) / TM;
+    const int64_t cap = (int64_t)ctx->num_sms * 3;       // 3 resident blocks of ~60 KB per SM
+    return (unsigned)(blocks > cap ? cap : blocks);
+}
+}  // namespace
+
 int hnet_infer(sph_ctx *ctx, const float *feats, int64_t nb, float *y, cudaStream_t s)
 {
     if (nb <= 0) return SPH_OK;
-    int64_t blocks = (nb + TM - 1) / TM;
-    const int64_t cap = (int64_t)ctx->num_sms * 3;       // 3 resident blocks of ~60 KB per SM
-    if (blocks > cap) blocks = cap;
-    k_infer_tc<<<(unsigned)blocks, TM, infer_tc_smem(), s>>>(ctx->hn_bf16, feats, nb, y, ctx->dcnt);
+    k_infer_tc<false, float><<<infer_blocks(ctx, nb), TM, infer_tc_smem(), s>>>(ctx->hn_bf16, feats, FeatArgs<float>{},
+                                                                               nb, y, SeedOut<float>{}, ctx->dcnt);
+    SPH_CHECK_LAUNCH();
+    return SPH_OK;
+}
+
+template <typename T>
+int seed_impl(sph_ctx *ctx, const sph_particles *p, double dt, bool train, void *h_seed, cudaStream_t s)
+{
+    int64_t nb, stride;
+    sample_layout(ctx, p->n, &nb, &stride);
+    SeedOut<T> so{(T *)h_seed, ctx->hn_sample, stride, train ? nb : 0};
+    k_infer_tc<true, T><<<infer_blocks(ctx, p->n), TM, infer_tc_smem(), s>>>(
+        ctx->hn_bf16, nullptr, feat_args<T>(ctx, p, dt), p->n, nullptr, so, ctx->dcnt);
+    SPH_CHECK_LAUNCH();
+    return SPH_OK;
+}
+
+// the step's seed h exp(s) straight from the particle fields (features, network
+// and seed in one kernel); with train, the features of the training samples too
+int hnet_seed_from_fields(sph_ctx *ctx, const sph_particles *p, double dt, bool train, void *h_seed,
+                          cudaStream_t s)
+{
+    return ctx->fp64 ? seed_impl<double>(ctx, p, dt, train, h_seed, s) : seed_impl<float>(ctx, p, dt, train, h_seed, s);
+}
+
+// features of the training samples only (a step that trains without seeding)
+int hnet_sample_features(sph_ctx *ctx, const sph_particles *p, double dt, cudaStream_t s)
+{
+    int64_t nb, stride;
+    sample_layout(ctx, p->n, &nb, &stride);
+    if (ctx->fp64)
+        k_features<double><<<grid_for(nb, 256), 256, 0, s>>>(feat_args<double>(ctx, p, dt), stride, nb, ctx->hn_sample);
+    else
+        k_features<float><<<grid_for(nb, 256), 256, 0, s>>>(feat_args<float>(ctx, p, dt), stride, nb, ctx->hn_sample);
     SPH_CHECK_LAUNCH();
     return SPH_OK;
 }
@@ -532,33 +645,33 @@ int hnet_refresh_bf16(sph_ctx *ctx, cudaStream_t s)
     return SPH_OK;
 }
 
+// one online training round on the samples whose features the seeding (or
+// hnet_sample_features) recorded, with targets log(h_new / h_old)
 int hnet_online(sph_ctx *ctx, const sph_particles *p, cudaStream_t s)
 {
-    const int64_t n = p->n;
-    const int64_t nb = n < ctx->prm.hnet_batch ? n : ctx->prm.hnet_batch;
-    int64_t stride = n / nb;
-    if (stride < 1) stride = 1;
+    int64_t nb, stride;
+    sample_layout(ctx, p->n, &nb, &stride);
     float *sf = ctx->hn_sample, *st = ctx->hn_sample + 5 * (int64_t)ctx->prm.hnet_batch;
     if (ctx->fp64)
-        k_sample<double><<<grid_for(nb, 256), 256, 0, s>>>(ctx->feats, (const double *)p->h, (const double *)ctx->hold,
-                                                           n, stride, nb, sf, st);
+        k_targets<double><<<grid_for(nb, 256), 256, 0, s>>>((const double *)p->h, (const double *)ctx->hold, stride,
+                                                            nb, st);
     else
-        k_sample<float><<<grid_for(nb, 256), 256, 0, s>>>(ctx->feats, (const float *)p->h, (const float *)ctx->hold,
-                                                          n, stride, nb, sf, st);
+        k_targets<float><<<grid_for(nb, 256), 256, 0, s>>>((const float *)p->h, (const float *)ctx->hold, stride,
+                                                           nb, st);
     SPH_CHECK_LAUNCH();
+    int64_t blocks = (nb + GS - 1) / GS;
+    if (blocks > ctx->hn_part_blocks) blocks = ctx->hn_part_blocks;
+    if (blocks < 1) blocks = 1;
     for (int it = 0; it < ctx->prm.hnet_iters; ++it) {
-        SPH_TRY(hnet_grad(ctx, sf, st, nb, s));
-        SPH_TRY(hnet_adam(ctx, (float)ctx->prm.hnet_lr, s));
+        k_grad<<<(unsigned)blocks, GT, grad_smem(), s>>>(ctx->hn_bf16, sf, st, nb, ctx->hn_part);
+        SPH_CHECK_LAUNCH();
+        ctx->hn_step += 1;
+        const float bc1 = (float)(1.0 - std::pow(0.9, (double)ctx->hn_step));
+        const float bc2 = (float)(1.0 - std::pow(0.999, (double)ctx->hn_step));
+        k_reduce_adam<<<grid_for(NP + 1, 256), 256, 0, s>>>(ctx->hn_part, (int)blocks, nb, ctx->hn_grad, ctx->dcnt,
+                                                            ctx->hn_master, ctx->hn_m, ctx->hn_v, ctx->hn_bf16,
+                                                            (float)ctx->prm.hnet_lr, bc1, bc2);
+        SPH_CHECK_LAUNCH();
     }
-    return SPH_OK;
-}
-
-int hnet_seed(sph_ctx *ctx, sph_particles *p, const float *y, void *h_seed, cudaStream_t s)
-{
-    if (ctx->fp64)
-        k_seed<double><<<grid_for(p->n, 256), 256, 0, s>>>((const double *)p->h, y, p->n, (double *)h_seed, ctx->dcnt);
-    else
-        k_seed<float><<<grid_for(p->n, 256), 256, 0, s>>>((const float *)p->h, y, p->n, (float *)h_seed, ctx->dcnt);
-    SPH_CHECK_LAUNCH();
     return SPH_OK;
 }

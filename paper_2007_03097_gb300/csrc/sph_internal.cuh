@@ -185,8 +185,6 @@ struct sph_ctx {
     float *hn_part = nullptr;           // per-block partial gradients
     int hn_part_blocks = 0;
     int64_t hn_step = 0;
-    float *feats = nullptr;             // n_max x 5
-    float *hn_y = nullptr;              // n_max
     float *hn_sample = nullptr;         // hnet_batch x 6 (features, target)
     // ---- timing and launch accounting
     cudaEvent_t ev[8] = {};
@@ -347,5 +345,7 @@ int hnet_features(sph_ctx *ctx, const sph_particles *p, double dt, float *feats,
 int hnet_infer(sph_ctx *ctx, const float *feats, int64_t nb, float *y, cudaStream_t s);
 int hnet_grad(sph_ctx *ctx, const float *feats, const float *target, int64_t nb, cudaStream_t s);
 int hnet_adam(sph_ctx *ctx, float lr, cudaStream_t s);
-int hnet_seed(sph_ctx *ctx, sph_particles *p, const float *y, void *h_seed, cudaStream_t s);
+int hnet_seed_from_fields(sph_ctx *ctx, const sph_particles *p, double dt, bool train, void *h_seed,
+                          cudaStream_t s);
+int hnet_sample_features(sph_ctx *ctx, const sph_particles *p, double dt, cudaStream_t s);
 int hnet_online(sph_ctx *ctx, const sph_particles *p, cudaStream_t s);
