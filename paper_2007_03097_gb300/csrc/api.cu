@@ -135,7 +135,7 @@ int allocate(sph_ctx *c, int64_t N)
     SPH_TRY(alloc(c, &c->act_groups[0], N));
     SPH_TRY(alloc(c, &c->act_groups[1], N));
     double **d8[] = {(double **)&c->vpx, (double **)&c->vpy, (double **)&c->vpz, (double **)&c->upred,
-                     (double **)&c->pr2, (double **)&c->hold, (double **)&c->hseed,
+                     (double **)&c->hold, (double **)&c->hseed,
                      (double **)&c->hstart};
     for (double **d : d8) SPH_TRY(alloc(c, d, N));
     c->gbuf_bytes = 24 * (((size_t)N * 8 + 255) & ~(size_t)255);
@@ -176,7 +176,7 @@ void release(sph_ctx *c)
                     c->node_lo, c->node_hi, c->srcA, c->srcB,
                     c->srcC, c->srcD, c->srcE, c->srcF, c->nbl, c->group_width,
                     c->group_off, c->it_lo, c->it_hi, c->it_flags, c->it_sweeps, c->cov, c->act_groups[0],
-                    c->act_groups[1], c->vpx, c->vpy, c->vpz, c->upred, c->pr2, c->hold, c->hseed, c->hstart, c->gbuf,
+                    c->act_groups[1], c->vpx, c->vpy, c->vpz, c->upred, c->hold, c->hseed, c->hstart, c->gbuf,
                     c->scan_tmp, c->red, c->dcnt, c->hn_master, c->hn_bf16, c->hn_m, c->hn_v, c->hn_grad,
                     c->hn_part, c->hn_sample};
     for (void *p : ptrs)
@@ -281,7 +281,7 @@ int sph_forces(sph_ctx *ctx, sph_particles *p, sph_force_stats *stats, void *str
     cudaStream_t s = S(stream);
     sph_force_stats local{};
     SPH_CUDA(cudaEventRecord(ctx->ev[0], s));
-    SPH_TRY(forces_run(ctx, p, p->vx, p->vy, p->vz, &local, false, s));
+    SPH_TRY(forces_run(ctx, p, p->vx, p->vy, p->vz, p->u, &local, false, s));
     SPH_CUDA(cudaEventRecord(ctx->ev[1], s));
     SPH_CUDA(cudaEventSynchronize(ctx->ev[1]));
     SPH_TRY(elapsed(ctx, ctx->ev[0], ctx->ev[1], &local.ms));
@@ -318,7 +318,7 @@ int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet, sph_step_s
         SPH_TRY(hnet_sample_features(ctx, p, dt, s));
     }
     SPH_CUDA(cudaEventRecord(ev[2], s));
-    int st = density_run(ctx, p, seed, &local.density, s);
+    int st = density_run(ctx, p, seed, &local.density, s, false);
     if (seed_net) local.hnet_fallback = ctx->hcnt->hnet_fallback;
     if (seed_net && ctx->hcnt->hnet_err)
         return sph_fail(ctx, SPH_ERR_CUDA, "sph_step: an h-predictor tensor-core MMA did not complete within 1 s");
@@ -326,7 +326,7 @@ int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet, sph_step_s
         // the plain iteration is the fallback: restart from the previous h
         local.hnet_fallback += (int32_t)local.density.n_unconverged;
         sph_density_stats again{};
-        st = density_run(ctx, p, ctx->hold, &again, s);
+        st = density_run(ctx, p, ctx->hold, &again, s, false);
         local.density.sweeps += again.sweeps;
         local.density.list_builds += again.list_builds;
         local.density.interactions += again.interactions;
@@ -342,8 +342,7 @@ int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet, sph_step_s
     SPH_CUDA(cudaEventRecord(ev[3], s));
     SPH_TRY(copy_field(ctx, p->hprev, ctx->hold, p->n, s));
     SPH_TRY(predict(ctx, p, dt, s));
-    SPH_TRY(eos_run(ctx, p, ctx->upred, s));
-    SPH_TRY(forces_run(ctx, p, ctx->vpx, ctx->vpy, ctx->vpz, nullptr, true, s));
+    SPH_TRY(forces_run(ctx, p, ctx->vpx, ctx->vpy, ctx->vpz, ctx->upred, nullptr, true, s));
     SPH_TRY(kick(ctx, p, dt, s));
     SPH_TRY(totals_run(ctx, p, ctx->vpx, ctx->vpy, ctx->vpz, p->u, s));
     SPH_CUDA(cudaEventRecord(ev[4], s));

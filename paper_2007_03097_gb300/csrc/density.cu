@@ -52,10 +52,12 @@ struct DensArgs {
     const float *cov;
     int kernel, periodic, fixed_h, max_sweeps;
     double L, eta3, h_tol, h_min, h_max;
+    df Ld, sig_d, eta3_d, hmin_d, hmax_d;   // the same constants as double-floats
     DevCounters *cnt;
 };
 
-template <typename T, bool FP64POS>
+// SPH_MIXED sweep of one group: FP32 pair terms, FP32 Newton update.
+template <typename T>
 __device__ __forceinline__ void density_group(const DensArgs &a, const int g, const int lane)
 {
     const int gb = a.group_begin[g], ge = a.group_begin[g + 1];
@@ -83,53 +85,7 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
     int cnt = 0;
     int band = 0;        // list entries within a relative 1e-5 of the support radius
     if (active) {
-        if (FP64POS) {
-            const float4 A = a.srcA[i], Bz = a.srcB[i];
-            const double hd = (double)h;
-            const double thr = __dmul_rn(__dmul_rn(4.0, hd), hd);
-            const float thr_f = (float)thr;
-            const float thr_hi = thr_f * (1.f + 1e-5f), thr_lo = thr_f * (1.f - 1e-5f);
-            const float Lf = (float)a.L, half = 0.5f * Lf, guard = 0.45f * Lf;
-            const df Ld = df_from_double(a.L);
-            const df hinv_df = df_from_double((double)hinv);
-            df sw = df{0.f, 0.f}, sd = df{0.f, 0.f};
-            walk_list<true>(a.nbl, off, width, lane, (uint32_t)i, a.srcA, a.srcB,
-                            [&](uint32_t b, const float4 &P, const float4 &Q) {
-                float dxf = (A.x - P.x) + (A.y - P.y);
-                float dyf = (A.z - P.z) + (A.w - P.w);
-                float dzf = (Bz.x - Q.x) + (Bz.y - Q.y);
-                int wx = 0, wy = 0, wz = 0;
-                if (a.periodic) {
-                    if (dxf > half) { dxf -= Lf; wx = -1; } else if (dxf < -half) { dxf += Lf; wx = 1; }
-                    if (dyf > half) { dyf -= Lf; wy = -1; } else if (dyf < -half) { dyf += Lf; wy = 1; }
-                    if (dzf > half) { dzf -= Lf; wz = -1; } else if (dzf < -half) { dzf += Lf; wz = 1; }
-                }
-                const float r2f = (dxf * dxf + dyf * dyf) + dzf * dzf;
-                if (r2f > thr_hi) return;
-                if (r2f >= thr_lo) ++band;
-                if (r2f >= thr_lo ||
-                    (a.periodic && fmaxf(fmaxf(fabsf(dxf), fabsf(dyf)), fabsf(dzf)) > guard)) {
-                    // knife edge: the exact FP64 decision of the plain definition
-                    const double L = a.L, hl = 0.5 * a.L;
-                    const double dx = sep_d(a.x[i], a.x[b], a.periodic, L, hl);
-                    const double dy = sep_d(a.y[i], a.y[b], a.periodic, L, hl);
-                    const double dz = sep_d(a.z[i], a.z[b], a.periodic, L, hl);
-                    if (!(r2_d(dx, dy, dz) < thr)) return;
-                }
-                const df dx = df_sep_fast(A.x, A.y, P.x, P.y, wx, Ld);
-                const df dy = df_sep_fast(A.z, A.w, P.z, P.w, wy, Ld);
-                const df dz = df_sep_fast(Bz.x, Bz.y, Q.x, Q.y, wz, Ld);
-                const df q = df_mul(df_sqrt_fast(df_norm2(dx, dy, dz)), hinv_df);
-                df w, g3;
-                df_kern_w_g3(a.kernel, q, w, g3);
-                const df mb = df{Q.z, Q.w};
-                df_acc(sw, df_mul(mb, w));
-                df_acc(sd, df_mul(mb, g3));
-                ++cnt;
-            });
-            sum_w = (T)df_to_double(df_norm(sw));
-            sum_dh = (T)df_to_double(df_norm(sd));
-        } else {
+        {
             const float4 A = a.srcA[i], Bz = a.srcB[i];
             const float L = (float)a.L, half = 0.5f * L;
             const float hf = (float)h;
@@ -237,6 +193,168 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
     }
 }
 
+// SPH_FP64 sweep of one group.  GB300 executes FP64 at 1/64 of the FP32
+// rate, so besides the pair terms the per-particle Newton update also runs in
+// double-float (about 48 significant bits); FP64 instructions remain only for
+// reading and writing the caller's double arrays and for the exact neighbour
+// decisions near the support radius.  The iteration bracket of FP64 mode is
+// kept as double-floats in the 8-byte slots of it_lo / it_hi.
+__device__ __forceinline__ bool df_lt(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ df df_ld(const double *p) { const float2 v = *reinterpret_cast<const float2 *>(p); return df{v.x, v.y}; }
+__device__ __forceinline__ void df_st(double *p, df v) { *reinterpret_cast<float2 *>(p) = make_float2(v.hi, v.lo); }
+
+__device__ __forceinline__ void density_group_df(const DensArgs &a, const int g, const int lane)
+{
+    const int gb = a.group_begin[g], ge = a.group_begin[g + 1];
+    const bool tgt = lane < ge - gb;
+    const int i = gb + (tgt ? lane : 0);
+    double *hp = (double *)a.h;
+    int32_t flags = tgt ? a.it_flags[i] : IT_DONE;
+    bool active = !(flags & IT_DONE);
+    const double hd = active ? hp[i] : 1.0;
+    const df h = df_from_double(hd);
+    // a particle whose support 2h left its list waits (state unchanged) for
+    // the list rebuild the host makes between sweep batches
+    bool waiting = false;
+    if (active && df_lt(df{a.cov[i], 0.f}, df_scale(h, 2.f))) {
+        waiting = true;
+        active = false;
+        atomicAdd(&a.cnt->n_uncovered, 1);
+    }
+    const df hinv = df_rcp(h);
+    const int64_t off = a.goff[g];
+    int width = a.gwidth[g];
+    if (off + 32 * (int64_t)width > a.cap) width = 0;    // never read past the lists
+
+    df sw = df{0.f, 0.f}, sd = df{0.f, 0.f};
+    int cnt = 0;
+    int band = 0;        // list entries within a relative 1e-5 of the support radius
+    const float4 A = a.srcA[i], Bz = a.srcB[i];
+    if (active) {
+        const float thr_f = df_scale(df_sqr(h), 4.f).hi;
+        const float thr_hi = thr_f * (1.f + 1e-5f), thr_lo = thr_f * (1.f - 1e-5f);
+        const float Lf = (float)a.L, half = 0.5f * Lf, guard = 0.45f * Lf;
+        const df Ld = a.Ld;
+        walk_list<true>(a.nbl, off, width, lane, (uint32_t)i, a.srcA, a.srcB,
+                        [&](uint32_t b, const float4 &P, const float4 &Q) {
+            float dxf = (A.x - P.x) + (A.y - P.y);
+            float dyf = (A.z - P.z) + (A.w - P.w);
+            float dzf = (Bz.x - Q.x) + (Bz.y - Q.y);
+            int wx = 0, wy = 0, wz = 0;
+            if (a.periodic) {
+                if (dxf > half) { dxf -= Lf; wx = -1; } else if (dxf < -half) { dxf += Lf; wx = 1; }
+                if (dyf > half) { dyf -= Lf; wy = -1; } else if (dyf < -half) { dyf += Lf; wy = 1; }
+                if (dzf > half) { dzf -= Lf; wz = -1; } else if (dzf < -half) { dzf += Lf; wz = 1; }
+            }
+            const float r2f = (dxf * dxf + dyf * dyf) + dzf * dzf;
+            if (r2f > thr_hi) return;
+            if (r2f >= thr_lo) ++band;
+            if (r2f >= thr_lo || (a.periodic && fmaxf(fmaxf(fabsf(dxf), fabsf(dyf)), fabsf(dzf)) > guard)) {
+                // knife edge: the exact FP64 decision of the plain definition
+                const double L = a.L, hl = 0.5 * a.L;
+                const double dx = sep_d(a.x[i], a.x[b], a.periodic, L, hl);
+                const double dy = sep_d(a.y[i], a.y[b], a.periodic, L, hl);
+                const double dz = sep_d(a.z[i], a.z[b], a.periodic, L, hl);
+                if (!(r2_d(dx, dy, dz) < __dmul_rn(__dmul_rn(4.0, hd), hd))) return;
+            }
+            const df dx = df_sep_fast(A.x, A.y, P.x, P.y, wx, Ld);
+            const df dy = df_sep_fast(A.z, A.w, P.z, P.w, wy, Ld);
+            const df dz = df_sep_fast(Bz.x, Bz.y, Q.x, Q.y, wz, Ld);
+            const df q = df_mul(df_sqrt_fast(df_norm2(dx, dy, dz)), hinv);
+            df w, g3;
+            df_kern_w_g3(a.kernel, q, w, g3);
+            const df mb = df{Q.z, Q.w};
+            df_acc(sw, df_mul(mb, w));
+            df_acc(sd, df_mul(mb, g3));
+            ++cnt;
+        });
+    }
+
+    bool still = false;
+    if (active) {
+        const df ma = df{Bz.z, Bz.w};
+        sw = df_add(df_norm(sw), ma);                   // self term, w(0) = 1 for every kernel
+        sd = df_add(df_norm(sd), df_mul_f(ma, 3.f));    // 3 w(0) + 0 w'(0)
+        const df h3i = df_mul(df_sqr(hinv), hinv);
+        const df sh3 = df_mul(a.sig_d, h3i);
+        const df rho = df_mul(sh3, sw);
+        const df drho = df_neg(df_mul(df_mul(sh3, hinv), sd));
+        const df meta3 = df_mul(ma, a.eta3_d);
+        const int sweeps = a.it_sweeps[i] + 1;
+        a.it_sweeps[i] = sweeps;
+        bool done = false;
+        df hn = h, hfin = h, rho_out = rho;
+        if (flags & IT_FINAL) {
+            done = true;
+        } else {
+            const df mh3 = df_mul(meta3, h3i);
+            const df f = df_sub(mh3, rho);
+            if (f.hi == 0.f) {
+                done = true;
+            } else if (sweeps >= a.max_sweeps) {
+                done = true;
+                flags |= IT_NOT_CONV;
+            } else {
+                const df fp = df_sub(df_mul_f(df_mul(mh3, hinv), -3.f), drho);
+                df lo = df_ld(a.it_lo + i), hi = df_ld(a.it_hi + i);
+                if (f.hi > 0.f) { if (df_lt(lo, h)) lo = h; }
+                else { if (df_lt(h, hi)) hi = h; }
+                const df h2 = df_scale(h, 0.5f), h_2 = df_scale(h, 2.f);
+                const df alo = df_lt(lo, h2) ? h2 : lo;
+                const df ahi = df_lt(h_2, hi) ? h_2 : hi;
+                bool ok = false;
+                if (df_lt0(fp)) {
+                    hn = df_sub(h, df_mul(f, df_rcp(fp)));
+                    ok = !df_lt(hn, alo) && !df_lt(ahi, hn);
+                }
+                if (!ok) hn = df_scale(df_add(h, f.hi > 0.f ? ahi : alo), 0.5f);
+                int clamp = 0;                           // the bounds are written exactly
+                if (df_lt(hn, a.hmin_d)) { hn = a.hmin_d; clamp = -1; }
+                if (df_lt(a.hmax_d, hn)) { hn = a.hmax_d; clamp = 1; }
+                const df dh = df_sub(hn, h);
+                const float adh = fabsf(dh.hi);
+                const bool conv = adh < (float)a.h_tol * h.hi;
+                df_st(a.it_lo + i, lo);
+                df_st(a.it_hi + i, hi);
+                hp[i] = clamp < 0 ? a.h_min : clamp > 0 ? a.h_max : df_to_double(hn);
+                if (conv) {
+                    // first-order finalization as in the mixed path (see there)
+                    if (band == 0 && adh <= 1e-9f * h.hi) {
+                        rho_out = df_add(rho, df_mul(drho, dh));
+                        hfin = hn;
+                        done = true;
+                    } else {
+                        flags |= IT_FINAL;
+                    }
+                }
+            }
+        }
+        if (done) {
+            flags |= IT_DONE;
+            if (flags & IT_NOT_CONV) atomicAdd(&a.cnt->n_not_conv, 1);
+            else if (!a.fixed_h && (!df_lt(a.hmin_d, hfin) || !df_lt(hfin, a.hmax_d))) {
+                flags |= IT_H_BOUNDS;
+                atomicAdd(&a.cnt->n_hbounds, 1);
+            }
+        }
+        ((double *)a.rho)[i] = df_to_double(rho_out);
+        ((double *)a.omega)[i] = df_to_double(drho);
+        a.nnb[i] = cnt;
+        a.it_flags[i] = flags;
+        still = !done;
+    }
+    if (waiting) still = true;
+    int c = cnt;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    const unsigned amask = __ballot_sync(0xffffffffu, active);
+    const unsigned smask = __ballot_sync(0xffffffffu, still);
+    if (lane == 0) {
+        atomicAdd(&a.cnt->interactions, (unsigned long long)c);
+        atomicAdd(&a.cnt->evaluations, (unsigned long long)__popc(amask));
+        if (smask) a.act_next[atomicAdd(a.act_next_count, 1)] = g;
+    }
+}
+
 // One sweep over the active groups, whose number is read on the device, so
 // sweeps can be queued without a host round trip.  The grid is sized to the
 // resident blocks; each warp claims its next group from a counter, so groups
@@ -252,22 +370,28 @@ __global__ void __launch_bounds__(DW * 32) k_density(DensArgs a)
         if (lane == 0) gi = atomicAdd(a.work, 1);
         gi = __shfl_sync(0xffffffffu, gi, 0);
         if (gi >= n_act) break;
-        density_group<T, FP64POS>(a, a.act[gi], lane);
+        if constexpr (FP64POS) density_group_df(a, a.act[gi], lane);
+        else density_group<T>(a, a.act[gi], lane);
     }
 }
 
 template <typename T>
 __global__ void k_dens_init(T *__restrict__ h, const T *__restrict__ seed, int64_t n, int fixed_h,
                             int32_t *__restrict__ flags, int32_t *__restrict__ sweeps, double *__restrict__ lo,
-                            double *__restrict__ hi)
+                            double *__restrict__ hi, int df_bracket)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (seed) h[i] = seed[i];
     flags[i] = fixed_h ? IT_FINAL : 0;
     sweeps[i] = 0;
-    lo[i] = 0.0;
-    hi[i] = __longlong_as_double(0x7ff0000000000000ll);   // +inf
+    if (df_bracket) {                               // double-float {0, 0} and {+inf, 0}
+        df_st(lo + i, df{0.f, 0.f});
+        df_st(hi + i, df{__int_as_float(0x7f800000), 0.f});
+    } else {
+        lo[i] = 0.0;
+        hi[i] = __longlong_as_double(0x7ff0000000000000ll);   // +inf
+    }
 }
 
 __global__ void k_iota_i32(int32_t *v, int64_t n)
@@ -297,19 +421,17 @@ __global__ void k_reset_status(DevCounters *c, int n_groups)
     c->act_count[0] = n_groups;
 }
 
-// Ideal-gas EOS: P = (gamma-1) rho u, c = sqrt(gamma (gamma-1) u), and P/rho^2.
+// Ideal-gas EOS: P = (gamma-1) rho u, c = sqrt(gamma (gamma-1) u).
 template <typename T>
 __global__ void k_eos(const T *__restrict__ rho, const T *__restrict__ u, int64_t n, double gamma,
-                      T *__restrict__ P, T *__restrict__ c, T *__restrict__ pr2)
+                      T *__restrict__ P, T *__restrict__ c)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const T g = (T)gamma, g1 = (T)(gamma - 1.0);
-    const T r = rho[i], ui = u[i];
-    const T p = g1 * r * ui;
-    P[i] = p;
+    const T ui = u[i];
+    P[i] = g1 * rho[i] * ui;
     c[i] = sqrt(g * g1 * ui);
-    pr2[i] = p / (r * r);
 }
 
 // resident blocks per SM of the sweep kernel (from the occupancy calculator)
@@ -329,7 +451,7 @@ unsigned resident_blocks(bool fp64pos)
 }
 
 template <typename T>
-int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats *st, cudaStream_t s)
+int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats *st, bool eos, cudaStream_t s)
 {
     const int64_t n = p->n;
     const sph_params &q = ctx->prm;
@@ -338,7 +460,7 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
     k_reset_status<<<1, 1, 0, s>>>(ctx->dcnt, ng);
     SPH_CHECK_LAUNCH();
     k_dens_init<T><<<grid_for(n, 256), 256, 0, s>>>((T *)p->h, (const T *)seed, n, q.fixed_h, ctx->it_flags,
-                                                     ctx->it_sweeps, ctx->it_lo, ctx->it_hi);
+                                                     ctx->it_sweeps, ctx->it_lo, ctx->it_hi, ctx->fp64 ? 1 : 0);
     SPH_CHECK_LAUNCH();
     SPH_TRY(lists_build(ctx, p, s));
     k_iota_i32<<<grid_for(ng, 256), 256, 0, s>>>(ctx->act_groups[0], ng);
@@ -358,6 +480,10 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
     a.L = ctx->dom[3];
     a.eta3 = q.eta * q.eta * q.eta;
     a.h_tol = q.h_tol; a.h_min = q.h_min; a.h_max = q.h_max;
+    const double sig = q.kernel == SPH_KERNEL_M4 ? 1.0 / SPH_PI
+                     : q.kernel == SPH_KERNEL_WC2 ? 21.0 / (16.0 * SPH_PI) : 495.0 / (256.0 * SPH_PI);
+    a.Ld = df_host(a.L); a.sig_d = df_host(sig); a.eta3_d = df_host(a.eta3);
+    a.hmin_d = df_host(q.h_min); a.hmax_d = df_host(q.h_max);
     a.cnt = ctx->dcnt;
     // sweeps are queued in batches without a host round trip: each reads the
     // number of active groups left by the previous one on the device.  A
@@ -401,7 +527,7 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
         SPH_CUDA(cudaEventElapsedTime(&f, ctx->kev[2 * k], ctx->kev[2 * k + 1]));
         kernel_ms += f;
     }
-    SPH_TRY(eos_run(ctx, p, p->u, s));
+    if (eos) SPH_TRY(eos_run(ctx, p, p->u, s));
     if (st) {
         st->sweeps = ctx->hcnt->sweeps_done;
         st->list_builds = 1 + rebuilds;
@@ -429,7 +555,7 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
 // the context then sizes them exactly from now on and the iteration restarts
 // from its first guess.
 template <typename T>
-int run_impl(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats *st, cudaStream_t s)
+int run_impl(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats *st, bool eos, cudaStream_t s)
 {
     const bool bounded = !ctx->lists_exact;
     const void *first = seed;
@@ -437,18 +563,19 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
         SPH_TRY(copy_field(ctx, ctx->hstart, p->h, p->n, s));
         first = ctx->hstart;
     }
-    const int r = run_once<T>(ctx, p, seed, st, s);
+    const int r = run_once<T>(ctx, p, seed, st, eos, s);
     if (r != SPH_ERR_CAPACITY || !bounded) return r;
     ctx->lists_exact = true;
     ctx->err.clear();
-    return run_once<T>(ctx, p, first, st, s);
+    return run_once<T>(ctx, p, first, st, eos, s);
 }
 
 }  // namespace
 
-int density_run(sph_ctx *ctx, sph_particles *p, const void *h_seed, sph_density_stats *st, cudaStream_t s)
+int density_run(sph_ctx *ctx, sph_particles *p, const void *h_seed, sph_density_stats *st, cudaStream_t s,
+                bool eos)
 {
-    return ctx->fp64 ? run_impl<double>(ctx, p, h_seed, st, s) : run_impl<float>(ctx, p, h_seed, st, s);
+    return ctx->fp64 ? run_impl<double>(ctx, p, h_seed, st, eos, s) : run_impl<float>(ctx, p, h_seed, st, eos, s);
 }
 
 int eos_run(sph_ctx *ctx, sph_particles *p, const void *u, cudaStream_t s)
@@ -456,10 +583,10 @@ int eos_run(sph_ctx *ctx, sph_particles *p, const void *u, cudaStream_t s)
     const double g = ctx->prm.gamma;
     if (ctx->fp64)
         k_eos<double><<<grid_for(p->n, 256), 256, 0, s>>>((const double *)p->rho, (const double *)u, p->n, g,
-                                                          (double *)p->P, (double *)p->c, (double *)ctx->pr2);
+                                                          (double *)p->P, (double *)p->c);
     else
         k_eos<float><<<grid_for(p->n, 256), 256, 0, s>>>((const float *)p->rho, (const float *)u, p->n, g,
-                                                         (float *)p->P, (float *)p->c, (float *)ctx->pr2);
+                                                         (float *)p->P, (float *)p->c);
     SPH_CHECK_LAUNCH();
     return SPH_OK;
 }

@@ -172,6 +172,13 @@ __device__ __forceinline__ df df_from_double(double d)
 
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 
+// the same split on the host (kernel arguments)
+inline df df_host(double d)
+{
+    const float hi = (float)d;
+    return df{hi, (float)(d - (double)hi)};
+}
+
 // x_a - x_b from two-float positions with a minimum-image shift: the exact
 // difference of the high parts plus the difference of the low parts
 __device__ __forceinline__ df df_sep_fast(float ah, float al, float bh, float bl, int wrap, df L)

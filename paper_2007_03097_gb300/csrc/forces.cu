@@ -28,7 +28,7 @@ struct ForceArgs {
     int n_groups;
     const double *x, *y, *z;
     const float4 *srcA, *srcB, *srcC, *srcD, *srcE, *srcF;
-    const void *vx, *vy, *vz, *m, *h, *rho, *pr2, *c;
+    const void *vx, *vy, *vz, *m, *h, *rho, *c;
     void *ax, *ay, *az, *dudt, *divv, *vsig;
     int kernel, periodic;
     double L, alpha, beta, eps;
@@ -118,18 +118,23 @@ __global__ void __launch_bounds__(FW * 32) k_forces_f32(ForceArgs a)
     if (lane == 0) atomicAdd(&a.cnt->force_interactions, (unsigned long long)nint);
 }
 
-// packed FP32 force-pass sources: C {vx, vy, vz, h}, D {rho, P/rho^2, c, 0}
+// Equation of state and packed FP32 force-pass sources: P = (gamma-1) rho u,
+// c = sqrt(gamma (gamma-1) u) to the caller's P and c, and the records
+// C {vx, vy, vz, h}, D {rho, P/rho^2, c, 0}.
 __global__ void k_pack_force_f32(const float *__restrict__ vx, const float *__restrict__ vy,
                                  const float *__restrict__ vz, const float *__restrict__ h,
-                                 const float *__restrict__ rho, const float *__restrict__ P,
-                                 const float *__restrict__ c, int64_t n, float4 *__restrict__ C,
+                                 const float *__restrict__ rho, const float *__restrict__ u, float g1, float gg1,
+                                 int64_t n, float *__restrict__ P, float *__restrict__ c, float4 *__restrict__ C,
                                  float4 *__restrict__ D)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float r = rho[i];
+    const float r = rho[i], ui = u[i];
+    const float pi = g1 * r * ui, ci = sqrtf(gg1 * ui);
+    P[i] = pi;
+    c[i] = ci;
     C[i] = make_float4(vx[i], vy[i], vz[i], h[i]);
-    D[i] = make_float4(r, P[i] / (r * r), c[i], 0.f);
+    D[i] = make_float4(r, pi / (r * r), ci, 0.f);
 }
 
 // SPH_FP64 force pass in double-float (see the file comment).
@@ -262,44 +267,51 @@ __device__ __forceinline__ float2 split2(double v)
     return make_float2(hi, (float)(v - (double)hi));
 }
 
-// packed force-pass sources: C {vx, vy}, D {vz, h}, E {rho, P/rho^2}, F {c, 0}
+// Equation of state and packed force-pass sources (FP64 mode): P = (gamma-1)
+// rho u in FP64 and c = sqrt(gamma (gamma-1) u) in double-float, written to the
+// caller's P and c, and the records C {vx, vy}, D {vz, h}, E {rho, P/rho^2},
+// F {c, 0} as two-float pairs.
 __global__ void k_pack_force(const double *__restrict__ vx, const double *__restrict__ vy,
                              const double *__restrict__ vz, const double *__restrict__ h,
-                             const double *__restrict__ rho, const double *__restrict__ P,
-                             const double *__restrict__ c, int64_t n, double *__restrict__ pr2,
-                             float4 *__restrict__ C, float4 *__restrict__ D, float4 *__restrict__ E,
-                             float4 *__restrict__ F)
+                             const double *__restrict__ rho, const double *__restrict__ u, double g1d, df gg1,
+                             int64_t n, double *__restrict__ P, double *__restrict__ c, float4 *__restrict__ C,
+                             float4 *__restrict__ D, float4 *__restrict__ E, float4 *__restrict__ F)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double r = rho[i];
-    const double q = P[i] / (r * r);
-    pr2[i] = q;
+    const double rd = rho[i], ud = u[i];
+    const double pd = __dmul_rn(__dmul_rn(g1d, rd), ud);      // P exactly as the FP64 definition
+    const df r = df_from_double(rd), ui = df_from_double(ud), pi = df_from_double(pd);
+    const df ci = df_sqrt(df_mul(gg1, ui));
+    const df q = df_mul(pi, df_sqr(df_rcp(r)));
+    P[i] = pd;
+    c[i] = df_to_double(ci);
     const float2 a = split2(vx[i]), b = split2(vy[i]), cz = split2(vz[i]), hh = split2(h[i]);
-    const float2 rr = split2(r), qq = split2(q), cc = split2(c[i]);
     C[i] = make_float4(a.x, a.y, b.x, b.y);
     D[i] = make_float4(cz.x, cz.y, hh.x, hh.y);
-    E[i] = make_float4(rr.x, rr.y, qq.x, qq.y);
-    F[i] = make_float4(cc.x, cc.y, 0.f, 0.f);
+    E[i] = make_float4(r.hi, r.lo, q.hi, q.lo);
+    F[i] = make_float4(ci.hi, ci.lo, 0.f, 0.f);
 }
 
 __global__ void k_reset_inter(DevCounters *c) { c->force_interactions = 0; }
 
 template <typename T>
-int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, const void *vz,
+int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, const void *vz, const void *u,
              sph_force_stats *st, bool reuse_lists, cudaStream_t s)
 {
     const int64_t launches0 = ctx->launches;
     k_reset_inter<<<1, 1, 0, s>>>(ctx->dcnt);
+    const double g = ctx->prm.gamma;
     if (ctx->fp64)
         k_pack_force<<<grid_for(p->n, 256), 256, 0, s>>>(
             (const double *)vx, (const double *)vy, (const double *)vz, (const double *)p->h, (const double *)p->rho,
-            (const double *)p->P, (const double *)p->c, p->n, (double *)ctx->pr2, ctx->srcC, ctx->srcD, ctx->srcE,
-            ctx->srcF);
+            (const double *)u, g - 1.0, df_host(g * (g - 1.0)), p->n, (double *)p->P, (double *)p->c,
+            ctx->srcC, ctx->srcD, ctx->srcE, ctx->srcF);
     else
         k_pack_force_f32<<<grid_for(p->n, 256), 256, 0, s>>>(
             (const float *)vx, (const float *)vy, (const float *)vz, (const float *)p->h, (const float *)p->rho,
-            (const float *)p->P, (const float *)p->c, p->n, ctx->srcC, ctx->srcD);
+            (const float *)u, (float)(g - 1.0), (float)(g * (g - 1.0)), p->n, (float *)p->P, (float *)p->c, ctx->srcC,
+            ctx->srcD);
     SPH_CHECK_LAUNCH();
     if (!reuse_lists || !ctx->lists_valid) SPH_TRY(lists_build(ctx, p, s));
     ForceArgs a{};
@@ -312,7 +324,7 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
     a.x = p->x; a.y = p->y; a.z = p->z;
     a.srcA = ctx->srcA; a.srcB = ctx->srcB; a.srcC = ctx->srcC; a.srcD = ctx->srcD; a.srcE = ctx->srcE;
     a.srcF = ctx->srcF;
-    a.vx = vx; a.vy = vy; a.vz = vz; a.m = p->m; a.h = p->h; a.rho = p->rho; a.pr2 = ctx->pr2; a.c = p->c;
+    a.vx = vx; a.vy = vy; a.vz = vz; a.m = p->m; a.h = p->h; a.rho = p->rho; a.c = p->c;
     a.ax = p->ax; a.ay = p->ay; a.az = p->az; a.dudt = p->dudt; a.divv = p->divv; a.vsig = p->vsig;
     a.kernel = ctx->prm.kernel;
     a.periodic = ctx->prm.periodic;
@@ -349,12 +361,12 @@ int forces_collect(sph_ctx *ctx, sph_force_stats *st)
 
 // reuse_lists: the lists of the h iteration that just ended still cover 2h
 // of every particle (sph_step); otherwise they are rebuilt for the current h.
-int forces_run(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, const void *vz,
+int forces_run(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, const void *vz, const void *u,
                sph_force_stats *st, bool reuse_lists, cudaStream_t s)
 {
     auto run = [&]() {
-        return ctx->fp64 ? run_impl<double>(ctx, p, vx, vy, vz, st, reuse_lists, s)
-                         : run_impl<float>(ctx, p, vx, vy, vz, st, reuse_lists, s);
+        return ctx->fp64 ? run_impl<double>(ctx, p, vx, vy, vz, u, st, reuse_lists, s)
+                         : run_impl<float>(ctx, p, vx, vy, vz, u, st, reuse_lists, s);
     };
     const bool bounded = !ctx->lists_exact;
     const int r = run();

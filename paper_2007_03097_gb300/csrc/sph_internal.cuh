@@ -162,7 +162,6 @@ struct sph_ctx {
     int32_t *act_groups[2] = {nullptr, nullptr};
     // ---- force pass / step scratch (precision-typed, 8 bytes per entry)
     void *vpx = nullptr, *vpy = nullptr, *vpz = nullptr, *upred = nullptr;
-    void *pr2 = nullptr;                // P / rho^2
     void *hold = nullptr;               // h before the density iteration
     void *hstart = nullptr;             // first guess of the running iteration (for a restart)
     void *hseed = nullptr;              // h-predictor seeds
@@ -324,11 +323,11 @@ int copy_field(sph_ctx *ctx, void *dst, const void *src, int64_t n, cudaStream_t
 int neighbors_export(sph_ctx *ctx, const sph_particles *p, int kind, int64_t *counts,
                      const int64_t *offsets, uint32_t *idx, cudaStream_t s);
 // density.cu
-int density_run(sph_ctx *ctx, sph_particles *p, const void *h_seed, sph_density_stats *st,
-                cudaStream_t s);
+int density_run(sph_ctx *ctx, sph_particles *p, const void *h_seed, sph_density_stats *st, cudaStream_t s,
+                bool eos = true);
 int eos_run(sph_ctx *ctx, sph_particles *p, const void *u, cudaStream_t s);
 // forces.cu
-int forces_run(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, const void *vz,
+int forces_run(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, const void *vz, const void *u,
                sph_force_stats *st, bool reuse_lists, cudaStream_t s);
 // after a sync_counters that follows a forces_run with st == nullptr
 int forces_collect(sph_ctx *ctx, sph_force_stats *st);
