@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(TM) k_infer_tc(const __nv_bfloat16 *__restrict
             if (FIELDS) {
                 const bool ok = isfinite(sp) && fabsf(sp) <= 0.69314718f;
                 const T hs = fa.h[s];
-                so.seed[s] = ok ? (T)((double)hs * exp((double)sp)) : hs;
+                so.seed[s] = ok ? hs * (T)__expf(sp) : hs;   // a first guess: FP32 exp suffices
                 if (!ok) atomicAdd(&cnt->hnet_fallback, 1);
             } else {
                 y[s] = sp;
