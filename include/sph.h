@@ -143,7 +143,8 @@ typedef struct {
     double power;            /* sum m (v_pred . a + du/dt), 0 up to roundoff        */
     int32_t hnet_used;       /* 1 if the h-predictor seeded the iteration           */
     int32_t hnet_fallback;   /* particles reseeded from h after a bad prediction    */
-    float hnet_loss;         /* loss of the last online training step (or 0)        */
+    float hnet_loss;         /* loss of the most recent completed online training
+                                round (the round of a step overlaps its force pass) */
     int32_t tree_moved;      /* particles the key-order rebuild moved: 0 when the
                                 previous order held, -1 after a full sort          */
     int64_t launches;        /* kernels launched by the step                        */

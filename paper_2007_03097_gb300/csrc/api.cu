@@ -163,6 +163,9 @@ int allocate(sph_ctx *c, int64_t N)
     SPH_CUDA(cudaMemset(c->hn_m, 0, sizeof(float) * SPH_HNET_NPARAM));
     SPH_CUDA(cudaMemset(c->hn_v, 0, sizeof(float) * SPH_HNET_NPARAM));
     for (cudaEvent_t &e : c->ev) SPH_CUDA(cudaEventCreate(&e));
+    SPH_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    SPH_CUDA(cudaEventCreateWithFlags(&c->ev_dens, cudaEventDisableTiming));
+    SPH_CUDA(cudaEventCreateWithFlags(&c->ev_train, cudaEventDisableTiming));
     for (cudaEvent_t &e : c->kev) SPH_CUDA(cudaEventCreate(&e));
     SPH_TRY(hnet_init(c));
     return SPH_OK;
@@ -181,6 +184,12 @@ void release(sph_ctx *c)
                     c->hn_part, c->hn_sample};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    if (c->ev_dens) cudaEventDestroy(c->ev_dens);
+    if (c->ev_train) cudaEventDestroy(c->ev_train);
     if (c->hcnt) cudaFreeHost(c->hcnt);
     for (cudaEvent_t e : c->ev)
         if (e) cudaEventDestroy(e);
@@ -195,6 +204,15 @@ inline cudaStream_t S(void *stream) { return (cudaStream_t)stream; }
 int copy_field(sph_ctx *ctx, void *dst, const void *src, int64_t n, cudaStream_t s)
 {
     SPH_CUDA(cudaMemcpyAsync(dst, src, (size_t)n * (ctx->fp64 ? 8 : 4), cudaMemcpyDeviceToDevice, s));
+    return SPH_OK;
+}
+
+int join_side(sph_ctx *ctx, cudaStream_t s, bool host)
+{
+    if (!ctx->side_pending) return SPH_OK;
+    if (host) SPH_CUDA(cudaEventSynchronize(ctx->ev_train));
+    else SPH_CUDA(cudaStreamWaitEvent(s, ctx->ev_train, 0));
+    ctx->side_pending = false;
     return SPH_OK;
 }
 
@@ -258,6 +276,7 @@ const char *sph_last_error(const sph_ctx *ctx) { return ctx ? ctx->err.c_str() :
 int sph_build_tree(sph_ctx *ctx, sph_particles *p, void *stream)
 {
     SPH_TRY(check_particles(ctx, p, false));
+    SPH_TRY(join_side(ctx, S(stream)));
     return tree_build(ctx, p, S(stream));
 }
 
@@ -265,6 +284,7 @@ int sph_density(sph_ctx *ctx, sph_particles *p, const void *h_seed, sph_density_
 {
     SPH_TRY(check_particles(ctx, p, true));
     cudaStream_t s = S(stream);
+    SPH_TRY(join_side(ctx, s));
     sph_density_stats local{};
     SPH_CUDA(cudaEventRecord(ctx->ev[0], s));
     int st = density_run(ctx, p, h_seed, &local, s);
@@ -279,6 +299,7 @@ int sph_forces(sph_ctx *ctx, sph_particles *p, sph_force_stats *stats, void *str
 {
     SPH_TRY(check_particles(ctx, p, true));
     cudaStream_t s = S(stream);
+    SPH_TRY(join_side(ctx, s));
     sph_force_stats local{};
     SPH_CUDA(cudaEventRecord(ctx->ev[0], s));
     SPH_TRY(forces_run(ctx, p, p->vx, p->vy, p->vz, p->u, &local, false, s));
@@ -293,6 +314,7 @@ int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet, sph_step_s
 {
     SPH_TRY(check_particles(ctx, p, false));
     cudaStream_t s = S(stream);
+    SPH_TRY(join_side(ctx, s));
     if (!(dt > 0.0)) dt = ctx->dt_cfl;
     if (!(dt > 0.0) || !std::isfinite(dt))
         return sph_fail(ctx, SPH_ERR_STATE, "sph_step: dt <= 0 and no CFL step known yet (run sph_step with dt > 0 first)");
@@ -338,7 +360,15 @@ int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet, sph_step_s
     }
     if (st != SPH_OK && st != SPH_ERR_H_BOUNDS) return st;
     const int dens_status = st;
-    if (train_net) SPH_TRY(hnet_online(ctx, p, s));
+    if (train_net) {
+        // the training round reads h and the pre-iteration h (hold), which
+        // nothing writes before the next call joins it
+        SPH_CUDA(cudaEventRecord(ctx->ev_dens, s));
+        SPH_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_dens, 0));
+        SPH_TRY(hnet_online(ctx, p, ctx->side));
+        SPH_CUDA(cudaEventRecord(ctx->ev_train, ctx->side));
+        ctx->side_pending = true;
+    }
     SPH_CUDA(cudaEventRecord(ev[3], s));
     SPH_TRY(copy_field(ctx, p->hprev, ctx->hold, p->n, s));
     SPH_TRY(predict(ctx, p, dt, s));
@@ -375,6 +405,7 @@ int sph_totals(sph_ctx *ctx, const sph_particles *p, double out[8], void *stream
     SPH_TRY(check_particles(ctx, p, false));
     if (!out) return sph_fail(ctx, SPH_ERR_ARG, "out is NULL");
     cudaStream_t s = S(stream);
+    SPH_TRY(join_side(ctx, s));
     SPH_TRY(totals_run(ctx, p, nullptr, nullptr, nullptr, p->u, s));
     SPH_TRY(sync_counters(ctx, s));
     for (int k = 0; k < 8; ++k) out[k] = ctx->hcnt->totals[k];
@@ -383,6 +414,7 @@ int sph_totals(sph_ctx *ctx, const sph_particles *p, double out[8], void *stream
 
 int sph_morton_keys(sph_ctx *ctx, const sph_particles *p, uint64_t *keys, double dom[4], void *stream)
 {
+    SPH_TRY(join_side(ctx, S(stream)));
     SPH_TRY(check_particles(ctx, p, false));
     if (!keys) return sph_fail(ctx, SPH_ERR_ARG, "keys is NULL");
     SPH_TRY(tree_keys(ctx, p, keys, S(stream)));
@@ -394,6 +426,7 @@ int sph_morton_keys(sph_ctx *ctx, const sph_particles *p, uint64_t *keys, double
 int sph_sort_keys(sph_ctx *ctx, int64_t n, const uint64_t *keys, const uint32_t *ids, uint32_t *perm, void *stream)
 {
     if (!ctx) return SPH_ERR_ARG;
+    SPH_TRY(join_side(ctx, S(stream)));
     if (n < 1 || n > ctx->n_max) return sph_fail(ctx, SPH_ERR_ARG, "n must be in [1, n_max]");
     if (!keys || !perm) return sph_fail(ctx, SPH_ERR_ARG, "keys and perm must be device arrays");
     ctx->tree_valid = false;
@@ -423,6 +456,7 @@ int sph_export_leaves(sph_ctx *ctx, int32_t *leaf_begin, int32_t *level, void *s
     if (!ctx) return SPH_ERR_ARG;
     if (!ctx->tree_valid) return sph_fail(ctx, SPH_ERR_STATE, "no tree: call sph_build_tree first");
     cudaStream_t s = S(stream);
+    SPH_TRY(join_side(ctx, s));
     if (leaf_begin)
         SPH_CUDA(cudaMemcpyAsync(leaf_begin, ctx->leaf_begin, sizeof(int32_t) * (size_t)(ctx->n_leaves + 1),
                                  cudaMemcpyDeviceToDevice, s));
@@ -436,6 +470,7 @@ int sph_export_leaves(sph_ctx *ctx, int32_t *leaf_begin, int32_t *level, void *s
 int sph_neighbors(sph_ctx *ctx, const sph_particles *p, int kind, int64_t *counts, const int64_t *offsets,
                   uint32_t *idx, void *stream)
 {
+    SPH_TRY(join_side(ctx, S(stream)));
     SPH_TRY(check_particles(ctx, p, true));
     if (kind != 0 && kind != 1) return sph_fail(ctx, SPH_ERR_ARG, "kind must be 0 (density) or 1 (force)");
     if (!counts || (offsets && !idx)) return sph_fail(ctx, SPH_ERR_ARG, "counts (and idx with offsets) required");
@@ -445,6 +480,7 @@ int sph_neighbors(sph_ctx *ctx, const sph_particles *p, int kind, int64_t *count
 int sph_hnet_set_weights(sph_ctx *ctx, const float *params_host, int64_t count)
 {
     if (!ctx) return SPH_ERR_ARG;
+    SPH_TRY(join_side(ctx, nullptr, true));
     if (!params_host || count != SPH_HNET_NPARAM) return sph_fail(ctx, SPH_ERR_ARG, "expected SPH_HNET_NPARAM floats");
     for (int64_t k = 0; k < count; ++k)
         if (!std::isfinite(params_host[k])) return sph_fail(ctx, SPH_ERR_NONFINITE, "non-finite network weight");
@@ -460,6 +496,7 @@ int sph_hnet_set_weights(sph_ctx *ctx, const float *params_host, int64_t count)
 int sph_hnet_get_weights(sph_ctx *ctx, float *params_host, int64_t count)
 {
     if (!ctx) return SPH_ERR_ARG;
+    SPH_TRY(join_side(ctx, nullptr, true));
     if (!params_host || count != SPH_HNET_NPARAM) return sph_fail(ctx, SPH_ERR_ARG, "expected SPH_HNET_NPARAM floats");
     SPH_CUDA(cudaDeviceSynchronize());
     SPH_CUDA(cudaMemcpy(params_host, ctx->hn_master, sizeof(float) * SPH_HNET_NPARAM, cudaMemcpyDeviceToHost));
@@ -470,6 +507,7 @@ int sph_hnet_features(sph_ctx *ctx, const sph_particles *p, double dt, float *fe
 {
     SPH_TRY(check_particles(ctx, p, false));
     if (!feats) return sph_fail(ctx, SPH_ERR_ARG, "feats is NULL");
+    SPH_TRY(join_side(ctx, S(stream)));
     return hnet_features(ctx, p, dt, feats, S(stream));
 }
 
@@ -478,6 +516,7 @@ int sph_hnet_infer(sph_ctx *ctx, const float *feats, int64_t nb, float *y, void 
     if (!ctx) return SPH_ERR_ARG;
     if (!feats || !y || nb < 1) return sph_fail(ctx, SPH_ERR_ARG, "feats, y and nb >= 1 required");
     cudaStream_t s = S(stream);
+    SPH_TRY(join_side(ctx, s));
     SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->hnet_err, 0, sizeof(uint32_t), s));
     SPH_TRY(hnet_infer(ctx, feats, nb, y, s));
     SPH_TRY(sync_counters(ctx, s));
@@ -492,6 +531,7 @@ int sph_hnet_grad(sph_ctx *ctx, const float *feats, const float *target, int64_t
     if (!ctx) return SPH_ERR_ARG;
     if (!feats || !target || nb < 1) return sph_fail(ctx, SPH_ERR_ARG, "feats, target and nb >= 1 required");
     cudaStream_t s = S(stream);
+    SPH_TRY(join_side(ctx, s));
     SPH_TRY(hnet_grad(ctx, feats, target, nb, s));
     SPH_TRY(sync_counters(ctx, s));
     if (grad_host)
@@ -506,6 +546,7 @@ int sph_hnet_train_step(sph_ctx *ctx, const float *feats, const float *target, i
     if (!ctx) return SPH_ERR_ARG;
     if (!feats || !target || nb < 1 || !(lr > 0.f)) return sph_fail(ctx, SPH_ERR_ARG, "feats, target, nb >= 1, lr > 0 required");
     cudaStream_t s = S(stream);
+    SPH_TRY(join_side(ctx, s));
     SPH_TRY(hnet_grad(ctx, feats, target, nb, s));
     SPH_TRY(hnet_adam(ctx, lr, s));
     if (loss_host) {

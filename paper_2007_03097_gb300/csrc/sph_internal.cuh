@@ -187,6 +187,11 @@ struct sph_ctx {
     float *hn_sample = nullptr;         // hnet_batch x 6 (features, target)
     // ---- timing and launch accounting
     cudaEvent_t ev[8] = {};
+    // the online training of a step runs on a side stream, overlapping the
+    // force pass; the next call on the context waits for it
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_dens = nullptr, ev_train = nullptr;
+    bool side_pending = false;
     cudaEvent_t kev[2 * 64] = {};       // per-sweep density kernel events
     int64_t launches = 0;               // kernels launched so far
     int64_t force_launches = 0;         // kernels of the last force pass
@@ -320,6 +325,9 @@ size_t scan_tmp_bytes(int64_t n);
 int lists_build(sph_ctx *ctx, const sph_particles *p, cudaStream_t s);
 // device copy of n elements of the context's precision
 int copy_field(sph_ctx *ctx, void *dst, const void *src, int64_t n, cudaStream_t s);
+// order stream s (or the host, for s == nullptr with host = true) after the
+// pending side-stream training of the previous step
+int join_side(sph_ctx *ctx, cudaStream_t s, bool host = false);
 int neighbors_export(sph_ctx *ctx, const sph_particles *p, int kind, int64_t *counts,
                      const int64_t *offsets, uint32_t *idx, cudaStream_t s);
 // density.cu
