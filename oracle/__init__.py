@@ -109,6 +109,7 @@ def lib():
                                        P, P, P]
         _lib.orc_eos.argtypes = [i64, d, P, P, P, P]
         _lib.orc_forces.argtypes = [ctypes.POINTER(_Params), i64] + [P] * 11 + [i64, P] + [P] * 8 + [P]
+        _lib.orc_energy_rate.argtypes = [ctypes.POINTER(_Params), i64] + [P] * 11 + [i64, P] + [P] * 2
         _lib.orc_num_threads.restype = i32
     return _lib
 
@@ -267,6 +268,20 @@ def forces(params: Params, x, y, z, vx, vy, vz, m, h, rho, P, c, targets=None) -
     return ForceResult(*outs, npairs=int(npairs.value))
 
 
+def energy_rate(params: Params, x, y, z, vx, vy, vz, m, h, rho, P, c, targets=None):
+    """Thermokinetic energy equation (Eq. thermo): de/dt of the specific total
+    energy e = u + v^2/2 and its cancellation scale S_e, for all particles or
+    for ``targets``."""
+    arrs = list(map(_f64, (x, y, z, vx, vy, vz, m, h, rho, P, c)))
+    n = arrs[0].size
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    nt = n if tg is None else tg.size
+    dedt, se = np.full(n, np.nan), np.full(n, np.nan)
+    pc = params.c()
+    lib().orc_energy_rate(ctypes.byref(pc), n, *[_p(a) for a in arrs], nt, _p(tg), _p(dedt), _p(se))
+    return dedt, se
+
+
 # --------------------------------------------------------------------------- leapfrog
 @dataclass
 class State:
@@ -284,6 +299,7 @@ class State:
     ay: np.ndarray = None
     az: np.ndarray = None
     dudt: np.ndarray = None
+    dedt: np.ndarray = None
     rho: np.ndarray = None
     divv: np.ndarray = None
     vsig: np.ndarray = None
@@ -296,9 +312,10 @@ class State:
         return State(**kw, extra=dict(self.extra))
 
 
-def evaluate(params: Params, s: State, vx=None, vy=None, vz=None, u=None):
+def evaluate(params: Params, s: State, vx=None, vy=None, vz=None, u=None, thermokinetic=False):
     """Density fixed point at the current positions (seeded by s.h), EOS with
-    internal energy ``u`` and force pass with velocities ``v``; fills s."""
+    internal energy ``u`` and force pass with velocities ``v``; fills s (and
+    s.dedt, the thermokinetic energy rate, when asked)."""
     vx = s.vx if vx is None else vx
     vy = s.vy if vy is None else vy
     vz = s.vz if vz is None else vz
@@ -310,6 +327,9 @@ def evaluate(params: Params, s: State, vx=None, vy=None, vz=None, u=None):
     s.ax, s.ay, s.az, s.dudt, s.divv, s.vsig = f.ax, f.ay, f.az, f.dudt, f.divv, f.vsig
     s.extra.update(P=P, c=c, sweeps=d.sweeps, flags=d.flags, S_a=f.S_a, S_u=f.S_u,
                    npairs=f.npairs, density_status=d.status)
+    if thermokinetic:
+        s.dedt, se = energy_rate(params, s.x, s.y, s.z, vx, vy, vz, s.m, d.h, d.rho, P, c)
+        s.extra.update(S_e=se)
     return s
 
 
@@ -347,6 +367,35 @@ def kdk_step(params: Params, s: State, dt: float) -> State:
     s.vy = vyh + s.ay * hdt
     s.vz = vzh + s.az * hdt
     s.u = uh + s.dudt * hdt
+    return s
+
+
+def kdk_step_thermokinetic(params: Params, s: State, dt: float) -> State:
+    """The kick-drift-kick step of kdk_step with the thermokinetic formulation
+    (Eq. thermo): the kicks advance the specific total energy e = u + v^2/2
+    with de/dt, and u = e - v^2/2 is recovered after each kick; forces and
+    de/dt are evaluated at the predicted v_pred = v_half + a_old dt/2 and
+    u_pred = e_pred - v_pred^2/2 with e_pred = e_half + de_old dt/2."""
+    hdt = 0.5 * dt
+    s = s.copy()
+    ke = lambda vx, vy, vz: 0.5 * (vx * vx + vy * vy + vz * vz)
+    e = s.u + ke(s.vx, s.vy, s.vz)
+    eh = e + s.dedt * hdt
+    vxh = s.vx + s.ax * hdt
+    vyh = s.vy + s.ay * hdt
+    vzh = s.vz + s.az * hdt
+    s.x = s.x + vxh * dt
+    s.y = s.y + vyh * dt
+    s.z = s.z + vzh * dt
+    wrap(params, s)
+    vxp, vyp, vzp = vxh + s.ax * hdt, vyh + s.ay * hdt, vzh + s.az * hdt
+    up = (eh + s.dedt * hdt) - ke(vxp, vyp, vzp)
+    evaluate(params, s, vxp, vyp, vzp, up, thermokinetic=True)
+    s.extra.update(vx_pred=vxp, vy_pred=vyp, vz_pred=vzp, u_pred=up)
+    s.vx = vxh + s.ax * hdt
+    s.vy = vyh + s.ay * hdt
+    s.vz = vzh + s.az * hdt
+    s.u = (eh + s.dedt * hdt) - ke(s.vx, s.vy, s.vz)
     return s
 
 

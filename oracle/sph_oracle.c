@@ -433,6 +433,58 @@ void orc_forces(const orc_params *p, int64_t n, const double *x, const double *y
     if (npairs_out) *npairs_out = pairs;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Thermokinetic energy equation (Sec. 2.1, Eq. thermo, after Rosswog 2015):
+ * the specific total energy e_a = u_a + v_a^2 / 2 evolves with
+ *   de_a/dt = - sum_b m_b ( P_a v_b / rho_a^2 + P_b v_a / rho_b^2
+ *                          + (v_a + v_b) Pi_ab / 2 ) . grad_a W_ab,
+ * over the same pairs, with the same W_ab = W(r_ab, h_ab) and Pi_ab as
+ * orc_forces.  S_e receives the cancellation scale
+ *   sum_b m_b ( |P_a/rho_a^2| |v_b . g| + |P_b/rho_b^2| |v_a . g|
+ *               + |Pi_ab| |(v_a + v_b)/2 . g| ),  g = grad_a W_ab.        */
+void orc_energy_rate(const orc_params *p, int64_t n, const double *x, const double *y,
+                     const double *z, const double *vx, const double *vy, const double *vz,
+                     const double *m, const double *h, const double *rho, const double *P,
+                     const double *c, int64_t nt, const int64_t *targets, double *dedt, double *S_e)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; ++t) {
+        const int64_t a = targets ? targets[t] : t;
+        const double Pa_r2 = P[a] / (rho[a] * rho[a]);
+        double de = 0.0, se = 0.0;
+        for (int64_t b = 0; b < n; ++b) {
+            if (b == a) continue;
+            double dx = sep(p, 0, x[a], x[b]);
+            double dy = sep(p, 1, y[a], y[b]);
+            double dz = sep(p, 2, z[a], z[b]);
+            double r2 = (dx * dx + dy * dy) + dz * dz;
+            double hs = h[a] + h[b];
+            if (!(r2 < hs * hs)) continue;
+            double r = sqrt(r2);
+            double hab = 0.5 * hs;
+            double g = orc_dWdr(p->kernel, r, hab) / r;
+            double gx = g * dx, gy = g * dy, gz = g * dz;
+            double vabx = vx[a] - vx[b], vaby = vy[a] - vy[b], vabz = vz[a] - vz[b];
+            double vdotr = (vabx * dx + vaby * dy) + vabz * dz;
+            double Pi = 0.0;
+            if (vdotr < 0.0) {
+                double mu = hab * vdotr / (r2 + p->eps_visc * hab * hab);
+                double cbar = 0.5 * (c[a] + c[b]);
+                double rbar = 0.5 * (rho[a] + rho[b]);
+                Pi = (-p->alpha * cbar * mu + p->beta * mu * mu) / rbar;
+            }
+            double Pb_r2 = P[b] / (rho[b] * rho[b]);
+            double vb_g = (vx[b] * gx + vy[b] * gy) + vz[b] * gz;
+            double va_g = (vx[a] * gx + vy[a] * gy) + vz[a] * gz;
+            double vm_g = 0.5 * (va_g + vb_g);
+            de -= m[b] * ((Pa_r2 * vb_g + Pb_r2 * va_g) + Pi * vm_g);
+            se += m[b] * ((fabs(Pa_r2) * fabs(vb_g) + fabs(Pb_r2) * fabs(va_g)) + fabs(Pi) * fabs(vm_g));
+        }
+        dedt[a] = de;
+        if (S_e) S_e[a] = se;
+    }
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP
