@@ -66,6 +66,16 @@ typedef enum {
  *            formed from a two-float split of the FP64 positions.           */
 typedef enum { SPH_FP64 = 0, SPH_MIXED = 1 } sph_precision;
 
+/* Energy equation (Sec. 2.1).
+ * SPH_ENERGY_INTERNAL: the specific internal energy u evolves with Eq. 5.
+ * SPH_ENERGY_TOTAL:    the thermokinetic formulation (Eq. thermo): the
+ *                      specific total energy e = u + v^2/2 evolves with
+ *                      de_a/dt = -sum_b m_b (P_a v_b/rho_a^2 + P_b v_a/rho_b^2
+ *                      + (v_a + v_b) Pi_ab/2) . grad_a W_ab; the force pass
+ *                      writes de_a/dt to dudt, and sph_step advances e and
+ *                      recovers u = e - v^2/2 after each kick.             */
+typedef enum { SPH_ENERGY_INTERNAL = 0, SPH_ENERGY_TOTAL = 1 } sph_energy;
+
 typedef struct {
     int32_t kernel;      /* sph_kernel                                          */
     int32_t precision;   /* sph_precision                                       */
@@ -91,6 +101,8 @@ typedef struct {
     double hnet_lr;      /* Adam learning rate of online h-predictor training   */
     int32_t hnet_batch;  /* samples per online training step (strided subset)   */
     int32_t hnet_iters;  /* Adam steps per sph_step when training online        */
+    int32_t energy;      /* sph_energy                                          */
+    int32_t reserved;    /* 0                                                   */
 } sph_params;
 
 /* Particle arrays, structure of arrays, length n, caller-owned DEVICE memory.

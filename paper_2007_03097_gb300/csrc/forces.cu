@@ -31,6 +31,7 @@ struct ForceArgs {
     const void *vx, *vy, *vz, *m, *h, *rho, *c;
     void *ax, *ay, *az, *dudt, *divv, *vsig;
     int kernel, periodic;
+    int thermo;                       // 1: dudt receives de/dt of the thermokinetic formulation
     double L, alpha, beta, eps;
     DevCounters *cnt;
 };
@@ -99,7 +100,14 @@ __global__ void __launch_bounds__(FW * 32) k_forces_f32(ForceArgs a)
             accx -= coef * dx;
             accy -= coef * dy;
             accz -= coef * dz;
-            du += mb * (pra + 0.5f * Pi) * gr * vdotr;
+            if (a.thermo) {
+                // Eq. thermo: -m_b (P_a/rho_a^2 v_b + P_b/rho_b^2 v_a + (v_a + v_b) Pi/2) . grad_a W
+                const float vb_r = (Cb.x * dx + Cb.y * dy) + Cb.z * dz;
+                const float va_r = (C.x * dx + C.y * dy) + C.z * dz;
+                du -= mb * ((pra * vb_r + Db.y * va_r) + Pi * 0.5f * (va_r + vb_r)) * gr;
+            } else {
+                du += mb * (pra + 0.5f * Pi) * gr * vdotr;
+            }
             const float vr = vdotr * rinv;
             const float sgn = ca + Db.z - 3.f * (vr < 0.f ? vr : 0.f);
             vs = sgn > vs ? sgn : vs;
@@ -241,7 +249,17 @@ __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
             df_acc(accx, df_neg(df_mul(coef, dx)));
             df_acc(accy, df_neg(df_mul(coef, dy)));
             df_acc(accz, df_neg(df_mul(coef, dz)));
-            df_acc(du, df_mul(df_mul(mb, df_add(pra, df_scale(Pi, 0.5f))), df_mul(gr, vdotr)));
+            if (a.thermo) {
+                // Eq. thermo: -m_b (P_a/rho_a^2 v_b + P_b/rho_b^2 v_a + (v_a + v_b) Pi/2) . grad_a W
+                const df vxb = df{Cb.x, Cb.y}, vyb = df{Cb.z, Cb.w}, vzb = df{Db.x, Db.y};
+                const df vb_r = df_add(df_add(df_mul(vxb, dx), df_mul(vyb, dy)), df_mul(vzb, dz));
+                const df va_r = df_add(vdotr, vb_r);
+                const df t = df_add(df_add(df_mul(pra, vb_r), df_mul(df{Eb.z, Eb.w}, va_r)),
+                                    df_mul(df_scale(Pi, 0.5f), df_add(va_r, vb_r)));
+                df_acc(du, df_neg(df_mul(df_mul(mb, t), gr)));
+            } else {
+                df_acc(du, df_mul(df_mul(mb, df_add(pra, df_scale(Pi, 0.5f))), df_mul(gr, vdotr)));
+            }
             const df vr = df_mul(vdotr, rinv);
             df sg = df_add(ca, df{Fb.x, Fb.y});
             if (df_lt0(vr)) sg = df_sub(sg, df_mul_f(vr, 3.f));
@@ -328,6 +346,7 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
     a.ax = p->ax; a.ay = p->ay; a.az = p->az; a.dudt = p->dudt; a.divv = p->divv; a.vsig = p->vsig;
     a.kernel = ctx->prm.kernel;
     a.periodic = ctx->prm.periodic;
+    a.thermo = ctx->prm.energy == SPH_ENERGY_TOTAL;
     a.L = ctx->dom[3];
     a.alpha = ctx->prm.alpha; a.beta = ctx->prm.beta; a.eps = ctx->prm.eps_visc;
     a.cnt = ctx->dcnt;

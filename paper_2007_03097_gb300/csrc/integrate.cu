@@ -9,18 +9,25 @@
 namespace {
 
 template <typename T>
+__device__ __forceinline__ T kinetic(T vx, T vy, T vz) { return T(0.5) * (vx * vx + vy * vy + vz * vz); }
+
+// First half kick and drift.  thermo: du holds de/dt; e = u + v^2/2 gets the
+// half kick and u = e - v_half^2/2.
+template <typename T>
 __global__ void k_kick_drift(double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
                              T *__restrict__ vx, T *__restrict__ vy, T *__restrict__ vz, T *__restrict__ u,
                              const T *__restrict__ ax, const T *__restrict__ ay, const T *__restrict__ az,
                              const T *__restrict__ du, int64_t n, double dt, int periodic, double3 lo,
-                             double3 hi)
+                             double3 hi, int thermo)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const T hdt = (T)(0.5 * dt);
-    const T vxh = vx[i] + ax[i] * hdt, vyh = vy[i] + ay[i] * hdt, vzh = vz[i] + az[i] * hdt;
+    const T vx0 = vx[i], vy0 = vy[i], vz0 = vz[i];
+    const T vxh = vx0 + ax[i] * hdt, vyh = vy0 + ay[i] * hdt, vzh = vz0 + az[i] * hdt;
     vx[i] = vxh; vy[i] = vyh; vz[i] = vzh;
-    u[i] = u[i] + du[i] * hdt;
+    if (thermo) u[i] = (u[i] + kinetic(vx0, vy0, vz0) + du[i] * hdt) - kinetic(vxh, vyh, vzh);
+    else u[i] = u[i] + du[i] * hdt;
     double px = x[i] + (double)vxh * dt, py = y[i] + (double)vyh * dt, pz = z[i] + (double)vzh * dt;
     if (periodic) {
         if (px >= hi.x) px -= hi.x - lo.x; else if (px < lo.x) px += hi.x - lo.x;
@@ -30,34 +37,43 @@ __global__ void k_kick_drift(double *__restrict__ x, double *__restrict__ y, dou
     x[i] = px; y[i] = py; z[i] = pz;
 }
 
-// predicted v and u at the end of the step from the old rates
+// predicted v and u at the end of the step from the old rates (thermo: the
+// predicted e = u_half + v_half^2/2 + de dt/2, u_pred = e_pred - v_pred^2/2)
 template <typename T>
 __global__ void k_predict(const T *__restrict__ vx, const T *__restrict__ vy, const T *__restrict__ vz,
                           const T *__restrict__ u, const T *__restrict__ ax, const T *__restrict__ ay,
                           const T *__restrict__ az, const T *__restrict__ du, int64_t n, double dt,
-                          T *__restrict__ px, T *__restrict__ py, T *__restrict__ pz, T *__restrict__ pu)
+                          T *__restrict__ px, T *__restrict__ py, T *__restrict__ pz, T *__restrict__ pu,
+                          int thermo)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const T hdt = (T)(0.5 * dt);
-    px[i] = vx[i] + ax[i] * hdt;
-    py[i] = vy[i] + ay[i] * hdt;
-    pz[i] = vz[i] + az[i] * hdt;
-    pu[i] = u[i] + du[i] * hdt;
+    const T vxh = vx[i], vyh = vy[i], vzh = vz[i];
+    const T vxp = vxh + ax[i] * hdt, vyp = vyh + ay[i] * hdt, vzp = vzh + az[i] * hdt;
+    px[i] = vxp;
+    py[i] = vyp;
+    pz[i] = vzp;
+    if (thermo) pu[i] = (u[i] + kinetic(vxh, vyh, vzh) + du[i] * hdt) - kinetic(vxp, vyp, vzp);
+    else pu[i] = u[i] + du[i] * hdt;
 }
 
+// closing half kick (thermo: e = u_half + v_half^2/2 + de dt/2, u = e - v^2/2)
 template <typename T>
 __global__ void k_kick(T *__restrict__ vx, T *__restrict__ vy, T *__restrict__ vz, T *__restrict__ u,
                        const T *__restrict__ ax, const T *__restrict__ ay, const T *__restrict__ az,
-                       const T *__restrict__ du, int64_t n, double dt)
+                       const T *__restrict__ du, int64_t n, double dt, int thermo)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const T hdt = (T)(0.5 * dt);
-    vx[i] = vx[i] + ax[i] * hdt;
-    vy[i] = vy[i] + ay[i] * hdt;
-    vz[i] = vz[i] + az[i] * hdt;
-    u[i] = u[i] + du[i] * hdt;
+    const T vxh = vx[i], vyh = vy[i], vzh = vz[i];
+    const T vx1 = vxh + ax[i] * hdt, vy1 = vyh + ay[i] * hdt, vz1 = vzh + az[i] * hdt;
+    vx[i] = vx1;
+    vy[i] = vy1;
+    vz[i] = vz1;
+    if (thermo) u[i] = (u[i] + kinetic(vxh, vyh, vzh) + du[i] * hdt) - kinetic(vx1, vy1, vz1);
+    else u[i] = u[i] + du[i] * hdt;
 }
 
 constexpr int NT = 9;   // 8 sums + 1 min
@@ -69,7 +85,7 @@ __global__ void k_totals_partial(const T *__restrict__ m, const T *__restrict__ 
                                  const T *__restrict__ ay, const T *__restrict__ az, const T *__restrict__ du,
                                  const T *__restrict__ pvx, const T *__restrict__ pvy,
                                  const T *__restrict__ pvz, const T *__restrict__ h,
-                                 const T *__restrict__ vsig, int64_t n, double *__restrict__ part)
+                                 const T *__restrict__ vsig, int64_t n, double *__restrict__ part, int thermo)
 {
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     double mn = DBL_MAX;
@@ -80,7 +96,7 @@ __global__ void k_totals_partial(const T *__restrict__ m, const T *__restrict__ 
         acc[3] += mi * axi; acc[4] += mi * ayi; acc[5] += mi * azi;
         acc[6] += mi * (0.5 * (vxi * vxi + vyi * vyi + vzi * vzi) + (double)u[i]);
         const double wx = pvx ? (double)pvx[i] : vxi, wy = pvx ? (double)pvy[i] : vyi, wz = pvx ? (double)pvz[i] : vzi;
-        acc[7] += mi * (wx * axi + wy * ayi + wz * azi + (double)du[i]);
+        acc[7] += thermo ? mi * (double)du[i] : mi * (wx * axi + wy * ayi + wz * azi + (double)du[i]);
         if (vsig) { const double v = vsig[i]; if (v > 0) mn = fmin(mn, (double)h[i] / v); }
     }
     __shared__ double s[NT][32];
@@ -125,7 +141,7 @@ int kd_impl(sph_ctx *ctx, sph_particles *p, double dt, cudaStream_t s)
     k_kick_drift<T><<<grid_for(p->n, 256), 256, 0, s>>>(
         p->x, p->y, p->z, (T *)p->vx, (T *)p->vy, (T *)p->vz, (T *)p->u, (const T *)p->ax, (const T *)p->ay,
         (const T *)p->az, (const T *)p->dudt, p->n, dt, q.periodic, make_double3(q.box_lo[0], q.box_lo[1], q.box_lo[2]),
-        make_double3(q.box_hi[0], q.box_hi[1], q.box_hi[2]));
+        make_double3(q.box_hi[0], q.box_hi[1], q.box_hi[2]), q.energy == SPH_ENERGY_TOTAL);
     SPH_CHECK_LAUNCH();
     return SPH_OK;
 }
@@ -135,7 +151,8 @@ int pred_impl(sph_ctx *ctx, sph_particles *p, double dt, cudaStream_t s)
 {
     k_predict<T><<<grid_for(p->n, 256), 256, 0, s>>>(
         (const T *)p->vx, (const T *)p->vy, (const T *)p->vz, (const T *)p->u, (const T *)p->ax, (const T *)p->ay,
-        (const T *)p->az, (const T *)p->dudt, p->n, dt, (T *)ctx->vpx, (T *)ctx->vpy, (T *)ctx->vpz, (T *)ctx->upred);
+        (const T *)p->az, (const T *)p->dudt, p->n, dt, (T *)ctx->vpx, (T *)ctx->vpy, (T *)ctx->vpz, (T *)ctx->upred,
+        ctx->prm.energy == SPH_ENERGY_TOTAL);
     SPH_CHECK_LAUNCH();
     return SPH_OK;
 }
@@ -144,7 +161,8 @@ template <typename T>
 int kick_impl(sph_ctx *ctx, sph_particles *p, double dt, cudaStream_t s)
 {
     k_kick<T><<<grid_for(p->n, 256), 256, 0, s>>>((T *)p->vx, (T *)p->vy, (T *)p->vz, (T *)p->u, (const T *)p->ax,
-                                                  (const T *)p->ay, (const T *)p->az, (const T *)p->dudt, p->n, dt);
+                                                  (const T *)p->ay, (const T *)p->az, (const T *)p->dudt, p->n, dt,
+                                                  ctx->prm.energy == SPH_ENERGY_TOTAL);
     SPH_CHECK_LAUNCH();
     return SPH_OK;
 }
@@ -157,7 +175,8 @@ int totals_impl(sph_ctx *ctx, const sph_particles *p, const void *pvx, const voi
     k_totals_partial<T><<<nb, 256, 0, s>>>((const T *)p->m, (const T *)p->vx, (const T *)p->vy, (const T *)p->vz,
                                            (const T *)u, (const T *)p->ax, (const T *)p->ay, (const T *)p->az,
                                            (const T *)p->dudt, (const T *)pvx, (const T *)pvy, (const T *)pvz,
-                                           (const T *)p->h, (const T *)p->vsig, p->n, ctx->red);
+                                           (const T *)p->h, (const T *)p->vsig, p->n, ctx->red,
+                                           ctx->prm.energy == SPH_ENERGY_TOTAL);
     SPH_CHECK_LAUNCH();
     k_totals_final<<<1, 32 * NT, 0, s>>>(ctx->red, nb, ctx->dcnt);
     SPH_CHECK_LAUNCH();
