@@ -299,6 +299,8 @@ def run_sph(args):
         inter_l, e_inter = float(ii[0]), float(ii[1])
     lists = B.sph_list_info(ctx)
     lists["slots_per_particle"] = lists["slots_used"] / w.n
+    nl, ng = B.sph_tree_info(ctx)
+    lists["union_per_group"] = lists["union_used"] / max(ng, 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, seconds=12.0, label=args.workload)

@@ -235,10 +235,12 @@ int sph_tree_info(sph_ctx *ctx, int64_t *n_leaves, int64_t *n_groups);
 /* Neighbour-list storage of the last list build, as of the last call that
  * returned (host out, each may be NULL): slots reserved (32 x the per-group
  * widths the build sized: leaf bounds, or exact counts once exact_sizing is
- * set), slots holding the exact lists, and whether exact sizing is on (set
- * for the rest of the context's life when leaf bounds exceeded nb_capacity).
+ * set), slots holding the exact lists, entries of the per-group source
+ * unions the lists index, and whether exact sizing is on (set for the rest
+ * of the context's life when leaf bounds exceeded nb_capacity).
  * Implementation detail of the list builder; the paper has no counterpart. */
-int sph_list_info(sph_ctx *ctx, int64_t *slots_reserved, int64_t *slots_used, int32_t *exact_sizing);
+int sph_list_info(sph_ctx *ctx, int64_t *slots_reserved, int64_t *slots_used, int64_t *union_used,
+                  int32_t *exact_sizing);
 
 /* After sph_build_tree: leaf_begin (device, n_leaves + 1 entries, the last is
  * n) and level (device, n_leaves; octree level of each leaf cell). */

@@ -128,6 +128,11 @@ int allocate(sph_ctx *c, int64_t N)
     SPH_TRY(alloc(c, &c->nbl, (size_t)c->nbl_cap));
     SPH_TRY(alloc(c, &c->group_width, N));
     SPH_TRY(alloc(c, &c->group_off, N + 1));
+    c->uni_cap = c->prm.nb_capacity > 0 ? c->prm.nb_capacity : 128 * N;   // exact unions never exceed the exact lists
+    SPH_TRY(alloc(c, &c->uni, (size_t)c->uni_cap));
+    SPH_TRY(alloc(c, &c->group_ubound, N));
+    SPH_TRY(alloc(c, &c->union_off, N + 1));
+    SPH_TRY(alloc(c, &c->group_union, N));
     SPH_TRY(alloc(c, &c->it_lo, N));
     SPH_TRY(alloc(c, &c->it_hi, N));
     SPH_TRY(alloc(c, &c->it_flags, N));
@@ -178,7 +183,8 @@ void release(sph_ctx *c)
                     c->itmp2, c->itmp3, c->leaf_begin, c->leaf_level, c->group_begin, c->leaf_lo, c->leaf_hi,
                     c->group_lo, c->group_hi, c->node_child, c->node_parent, c->leaf_parent, c->node_visit,
                     c->node_lo, c->node_hi, c->srcA, c->srcB,
-                    c->srcC, c->srcD, c->srcE, c->srcF, c->nbl, c->group_width,
+                    c->srcC, c->srcD, c->srcE, c->srcF, c->nbl, c->group_width, c->uni, c->group_ubound,
+                    c->union_off, c->group_union,
                     c->group_off, c->it_lo, c->it_hi, c->it_flags, c->it_sweeps, c->cov, c->act_groups[0],
                     c->act_groups[1], c->vpx, c->vpy, c->vpz, c->upred, c->hold, c->hseed, c->hstart, c->gbuf,
                     c->scan_tmp, c->red, c->dcnt, c->hn_master, c->hn_bf16, c->hn_m, c->hn_v, c->hn_grad,
@@ -443,11 +449,13 @@ int sph_tree_info(sph_ctx *ctx, int64_t *n_leaves, int64_t *n_groups)
     return SPH_OK;
 }
 
-int sph_list_info(sph_ctx *ctx, int64_t *slots_reserved, int64_t *slots_used, int32_t *exact_sizing)
+int sph_list_info(sph_ctx *ctx, int64_t *slots_reserved, int64_t *slots_used, int64_t *union_used,
+                  int32_t *exact_sizing)
 {
     if (!ctx) return SPH_ERR_ARG;
     if (slots_reserved) *slots_reserved = (int64_t)ctx->hcnt->list_total;
     if (slots_used) *slots_used = (int64_t)ctx->hcnt->list_used;
+    if (union_used) *union_used = (int64_t)ctx->hcnt->union_used;
     if (exact_sizing) *exact_sizing = ctx->lists_exact ? 1 : 0;
     return SPH_OK;
 }

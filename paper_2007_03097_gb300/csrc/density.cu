@@ -28,7 +28,8 @@
 
 namespace {
 
-constexpr int DW = 4;   // warps per block
+constexpr int DW = 4;          // warps per block
+constexpr int SRC_CAP = 448;   // staged union sources per warp (mixed sweep; 7 KB)
 
 struct DensArgs {
     const int32_t *act;            // active groups of this sweep ...
@@ -39,8 +40,13 @@ struct DensArgs {
     const int32_t *group_begin;
     const int64_t *goff;
     const int32_t *gwidth;
-    const uint32_t *nbl;
+    const uint16_t *nbl;
     int64_t cap;
+    const uint32_t *uni;           // group source unions
+    const int64_t *uoff;
+    const int32_t *group_union;    // union size per group
+    const float4 *group_lo, *group_hi;
+    int src_cap;                   // union sources staged in shared memory per warp (mixed)
     const double *x, *y, *z;
     const float4 *srcA, *srcB;   // {xh, xl, yh, yl}, {zh, zl, m_hi, m_lo}
     void *h;
@@ -56,9 +62,13 @@ struct DensArgs {
     DevCounters *cnt;
 };
 
-// SPH_MIXED sweep of one group: FP32 pair terms, FP32 Newton update.
+// SPH_MIXED sweep of one group: FP32 pair terms, FP32 Newton update.  The
+// group's source union is staged in shared memory (s_src, a.src_cap entries
+// per chunk) as FP32 coordinates relative to the group-box centre, with the
+// periodic shift folded in, and the mass; each lane then reads its
+// neighbours there by their local index.
 template <typename T>
-__device__ __forceinline__ void density_group(const DensArgs &a, const int g, const int lane)
+__device__ __forceinline__ void density_group(const DensArgs &a, const int g, const int lane, float4 *s_src)
 {
     const int gb = a.group_begin[g], ge = a.group_begin[g + 1];
     const bool tgt = lane < ge - gb;
@@ -84,28 +94,66 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
     T sum_w = T(0), sum_dh = T(0);
     int cnt = 0;
     int band = 0;        // list entries within a relative 1e-5 of the support radius
-    if (active) {
-        {
-            const float4 A = a.srcA[i], Bz = a.srcB[i];
-            const float L = (float)a.L, half = 0.5f * L;
-            const float hf = (float)h;
-            const float thr = __fmul_rn(__fmul_rn(4.f, hf), hf);
-            walk_list<false>(a.nbl, off, width, lane, (uint32_t)i, a.srcA, a.srcB,
-                             [&](uint32_t, const float4 &P, const float4 &Q) {
-                const float dx = sep_f(A.x, A.y, P.x, P.y, a.periodic, L, half);
-                const float dy = sep_f(A.z, A.w, P.z, P.w, a.periodic, L, half);
-                const float dz = sep_f(Bz.x, Bz.y, Q.x, Q.y, a.periodic, L, half);
-                const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-                if (fabsf(r2 - thr) <= 1e-5f * thr) ++band;
-                if (!(r2 < thr)) return;
-                const T q = (T)sqrtf(r2) * hinv;
-                T w, dw;
-                kern_wdw<T>(a.kernel, q, w, dw);
-                const T mb = (T)Q.z;
-                sum_w += mb * w;
-                sum_dh += mb * (T(3) * w + q * dw);
-                ++cnt;
-            });
+    if (__any_sync(0xffffffffu, active)) {
+        const float4 qlo = a.group_lo[g], qhi = a.group_hi[g];
+        const float gcx = 0.5f * (qlo.x + qhi.x), gcy = 0.5f * (qlo.y + qhi.y), gcz = 0.5f * (qlo.z + qhi.z);
+        const float4 A = a.srcA[i], Bz = a.srcB[i];
+        const float tx = (A.x - gcx) + A.y, ty = (A.z - gcy) + A.w, tz = (Bz.x - gcz) + Bz.y;
+        const float L = (float)a.L;
+        const float hf = (float)h;
+        const float thr = __fmul_rn(__fmul_rn(4.f, hf), hf);
+        const int U = a.group_union[g];
+        const uint32_t *Ug = a.uni + a.uoff[g];
+        const uint16_t *l = a.nbl + off + lane;
+        for (int c0 = 0; c0 < U; c0 += a.src_cap) {
+            const int cn = min(a.src_cap, U - c0);
+            __syncwarp();
+            for (int t = lane; t < cn; t += 32) {
+                const uint32_t b = __ldg(Ug + c0 + t);
+                const float4 qa = __ldg(a.srcA + b), qb = __ldg(a.srcB + b);
+                float rx = qa.x - gcx, ry = qa.z - gcy, rz = qb.x - gcz;
+                if (a.periodic) {              // the image nearest the group
+                    rx -= L * rintf(rx / L);
+                    ry -= L * rintf(ry / L);
+                    rz -= L * rintf(rz / L);
+                }
+                s_src[t] = make_float4(rx + qa.y, ry + qa.w, rz + qb.y, qb.z);
+            }
+            __syncwarp();
+            if (active) {
+                // list entries in batches of LB, the next batch in flight
+                // while this one is processed (empty slots fall outside [0, cn))
+                constexpr int LB = 8;
+                uint32_t nx[LB];
+#pragma unroll
+                for (int u = 0; u < LB; ++u) nx[u] = u < width ? __ldg(l + (int64_t)u * 32) : SPH_LOCAL_NONE;
+                for (int k0 = 0; k0 < width; k0 += LB) {
+                    uint32_t cur[LB];
+#pragma unroll
+                    for (int u = 0; u < LB; ++u) {
+                        cur[u] = nx[u];
+                        const int kk = k0 + LB + u;
+                        nx[u] = kk < width ? __ldg(l + (int64_t)kk * 32) : SPH_LOCAL_NONE;
+                    }
+#pragma unroll
+                    for (int u = 0; u < LB; ++u) {
+                    const int le = (int)cur[u] - c0;
+                    if ((unsigned)le >= (unsigned)cn) continue;
+                    const float4 q = s_src[le];
+                    const float dx = tx - q.x, dy = ty - q.y, dz = tz - q.z;
+                    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                    if (fabsf(r2 - thr) <= 1e-5f * thr) ++band;
+                    if (!(r2 < thr)) continue;
+                    const T qq = (T)sqrtf(r2) * hinv;
+                    T w, dw;
+                    kern_wdw<T>(a.kernel, qq, w, dw);
+                    const T mb = (T)q.w;
+                    sum_w += mb * w;
+                    sum_dh += mb * (T(3) * w + qq * dw);
+                    ++cnt;
+                    }
+                }
+            }
         }
     }
 
@@ -235,7 +283,7 @@ __device__ __forceinline__ void density_group_df(const DensArgs &a, const int g,
         const float thr_hi = thr_f * (1.f + 1e-5f), thr_lo = thr_f * (1.f - 1e-5f);
         const float Lf = (float)a.L, half = 0.5f * Lf, guard = 0.45f * Lf;
         const df Ld = a.Ld;
-        walk_list<true>(a.nbl, off, width, lane, (uint32_t)i, a.srcA, a.srcB,
+        walk_list<true>(a.nbl, off, width, lane, (uint32_t)i, a.uni, a.uoff[g], a.srcA, a.srcB,
                         [&](uint32_t b, const float4 &P, const float4 &Q) {
             float dxf = (A.x - P.x) + (A.y - P.y);
             float dyf = (A.z - P.z) + (A.w - P.w);
@@ -362,7 +410,9 @@ __device__ __forceinline__ void density_group_df(const DensArgs &a, const int g,
 template <typename T, bool FP64POS>
 __global__ void __launch_bounds__(DW * 32) k_density(DensArgs a)
 {
+    extern __shared__ float4 s_dyn[];
     const int lane = threadIdx.x & 31;
+    float4 *s_src = s_dyn + (threadIdx.x >> 5) * a.src_cap;
     const int n_act = *a.act_count;
     if (blockIdx.x == 0 && threadIdx.x == 0 && n_act > 0) atomicAdd(&a.cnt->sweeps_done, 1);
     for (;;) {
@@ -371,7 +421,7 @@ __global__ void __launch_bounds__(DW * 32) k_density(DensArgs a)
         gi = __shfl_sync(0xffffffffu, gi, 0);
         if (gi >= n_act) break;
         if constexpr (FP64POS) density_group_df(a, a.act[gi], lane);
-        else density_group<T>(a, a.act[gi], lane);
+        else density_group<T>(a, a.act[gi], lane, s_src);
     }
 }
 
@@ -444,7 +494,8 @@ unsigned resident_blocks(bool fp64pos)
         int nb = 0;
         const cudaError_t e = fp64pos
             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_density<T, true>, DW * 32, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_density<T, false>, DW * 32, 0);
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_density<T, false>, DW * 32,
+                                                            sizeof(float4) * DW * SRC_CAP);
         c = (e == cudaSuccess && nb > 0) ? nb : 8;
     }
     return (unsigned)c;
@@ -471,6 +522,13 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
     a.gwidth = ctx->group_width;
     a.nbl = ctx->nbl;
     a.cap = ctx->nbl_cap;
+    a.uni = ctx->uni;
+    a.uoff = ctx->union_off;
+    a.group_union = ctx->group_union;
+    a.group_lo = ctx->group_lo;
+    a.group_hi = ctx->group_hi;
+    a.src_cap = ctx->fp64 ? 0 : SRC_CAP;
+    const size_t smem = ctx->fp64 ? 0 : sizeof(float4) * DW * SRC_CAP;
     a.x = p->x; a.y = p->y; a.z = p->z;
     a.srcA = ctx->srcA; a.srcB = ctx->srcB;
     a.h = p->h; a.m = p->m; a.rho = p->rho; a.omega = p->omega; a.nnb = p->nnb;
@@ -504,7 +562,7 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
             a.work = &ctx->dcnt->work[cur];
             if (launched < 64) SPH_CUDA(cudaEventRecord(ctx->kev[2 * launched], s));
             if (ctx->fp64) k_density<T, true><<<grid, DW * 32, 0, s>>>(a);
-            else k_density<T, false><<<grid, DW * 32, 0, s>>>(a);
+            else k_density<T, false><<<grid, DW * 32, smem, s>>>(a);
             SPH_CHECK_LAUNCH();
             if (launched < 64) SPH_CUDA(cudaEventRecord(ctx->kev[2 * launched + 1], s));
             cur ^= 1;

@@ -23,8 +23,10 @@ struct ForceArgs {
     const int32_t *group_begin;
     const int64_t *goff;
     const int32_t *gwidth;
-    const uint32_t *nbl;
+    const uint16_t *nbl;
     int64_t cap;
+    const uint32_t *uni;           // group source unions
+    const int64_t *uoff;
     int n_groups;
     const double *x, *y, *z;
     const float4 *srcA, *srcB, *srcC, *srcD, *srcE, *srcF;
@@ -33,6 +35,7 @@ struct ForceArgs {
     int kernel, periodic;
     int thermo;                       // 1: dudt receives de/dt of the thermokinetic formulation
     double L, alpha, beta, eps;
+    df Ld, sig_d, alpha_d, beta_d, eps_d;   // the same constants as double-floats
     DevCounters *cnt;
 };
 
@@ -52,6 +55,7 @@ __global__ void __launch_bounds__(FW * 32) k_forces_f32(ForceArgs a)
     const float sig = kern_sigma<float>(a.kernel);
     const float alpha = (float)a.alpha, beta = (float)a.beta, eps = (float)a.eps;
     const int64_t off = a.goff[g];
+    const uint32_t *U = a.uni + a.uoff[g];
     int width = tgt ? a.gwidth[g] : 0;
     if (off + 32 * (int64_t)width > a.cap) width = 0;    // never read past the lists
     const float Lf = (float)a.L, half = 0.5f * Lf;
@@ -59,8 +63,17 @@ __global__ void __launch_bounds__(FW * 32) k_forces_f32(ForceArgs a)
 
     float accx = 0.f, accy = 0.f, accz = 0.f, du = 0.f, dv = 0.f, vs = ca;
     int nint = 0;
+    // the list entry of slot k + 2 and the union index of slot k + 1 are in
+    // flight while slot k is processed
+    const uint16_t *l = a.nbl + off + lane;
+    auto entry = [&](int k) -> uint32_t { return k < width ? (uint32_t)__ldg(l + (int64_t)k * 32) : SPH_LOCAL_NONE; };
+    auto index = [&](uint32_t e) -> uint32_t { return e == SPH_LOCAL_NONE ? SPH_SENTINEL : __ldg(U + e); };
+    uint32_t e2 = entry(1);
+    uint32_t b1 = index(entry(0));
     for (int k = 0; k < width; ++k) {
-        const uint32_t b = a.nbl[off + (int64_t)k * 32 + lane];
+        const uint32_t b = b1;
+        b1 = index(e2);
+        e2 = entry(k + 2);
         if (b == SPH_SENTINEL) continue;
         const float4 P = a.srcA[b], Q = a.srcB[b], Cb = a.srcC[b];
         const float dx = sep_f(A.x, A.y, P.x, P.y, a.periodic, Lf, half);
@@ -156,30 +169,37 @@ __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
     const int i = gb + (tgt ? lane : 0);
     const double *h64 = (const double *)a.h;
     const int64_t off = a.goff[g];
+    const uint32_t *U = a.uni + a.uoff[g];
     int width = tgt ? a.gwidth[g] : 0;
     if (off + 32 * (int64_t)width > a.cap) width = 0;
 
     const float4 A = a.srcA[i], Bz = a.srcB[i], C = a.srcC[i], D = a.srcD[i], E = a.srcE[i], F = a.srcF[i];
-    const double had = h64[i];
-    const double thr_d = __dmul_rn(__dmul_rn(4.0, had), had);
-    const float thr_f = (float)thr_d;
+    // per-particle constants in double-float (FP64 runs at 1/64 of the FP32 rate)
+    const df ha = df{D.z, D.w};
+    const float thr_f = df_scale(df_sqr(ha), 4.f).hi;
     const float thr_hi = thr_f * (1.f + 1e-5f), thr_lo = thr_f * (1.f - 1e-5f);
     const float Lf = (float)a.L, half = 0.5f * Lf, guard = 0.45f * Lf;
-    const df Ld = df_from_double(a.L);
-    const double sig_d = a.kernel == 0 ? 1.0 / SPH_PI : a.kernel == 1 ? 21.0 / (16.0 * SPH_PI) : 495.0 / (256.0 * SPH_PI);
-    const df sig = df_from_double(sig_d);
-    const df ha = df{D.z, D.w};
-    const df hainv = df_from_double(1.0 / had);
+    const df Ld = a.Ld, sig = a.sig_d;
+    const df hainv = df_rcp(ha);
     const df hai2 = df_sqr(hainv);
     const df sig_hai4 = df_mul(sig, df_sqr(hai2));
     const df vxa = df{C.x, C.y}, vya = df{C.z, C.w}, vza = df{D.x, D.y};
     const df rhoa = df{E.x, E.y}, pra = df{E.z, E.w}, ca = df{F.x, F.y};
-    const df alpha = df_from_double(a.alpha), beta = df_from_double(a.beta), eps = df_from_double(a.eps);
+    const df alpha = a.alpha_d, beta = a.beta_d, eps = a.eps_d;
 
     df accx = df{0.f, 0.f}, accy = accx, accz = accx, du = accx, dv = accx, vs = ca;
     int nint = 0;
+    // the list entry of slot k + 2 and the union index of slot k + 1 are in
+    // flight while slot k is processed
+    const uint16_t *l = a.nbl + off + lane;
+    auto entry = [&](int k) -> uint32_t { return k < width ? (uint32_t)__ldg(l + (int64_t)k * 32) : SPH_LOCAL_NONE; };
+    auto index = [&](uint32_t e) -> uint32_t { return e == SPH_LOCAL_NONE ? SPH_SENTINEL : __ldg(U + e); };
+    uint32_t e2 = entry(1);
+    uint32_t b1 = index(entry(0));
     for (int k = 0; k < width; ++k) {
-        const uint32_t b = a.nbl[off + (int64_t)k * 32 + lane];
+        const uint32_t b = b1;
+        b1 = index(e2);
+        e2 = entry(k + 2);
         if (b == SPH_SENTINEL) continue;
         const float4 P = a.srcA[b], Q = a.srcB[b], Db = a.srcD[b];
         float dxf = (A.x - P.x) + (A.y - P.y);
@@ -206,9 +226,10 @@ __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
             const double dy = sep_d(a.y[i], a.y[b], a.periodic, L, hl);
             const double dz = sep_d(a.z[i], a.z[b], a.periodic, L, hl);
             const double rr = r2_d(dx, dy, dz);
+            const double had = h64[i];
             const double hs = __dadd_rn(had, h64[b]);
             in_f = rr < __dmul_rn(hs, hs);
-            in_d = rr < thr_d;
+            in_d = rr < __dmul_rn(__dmul_rn(4.0, had), had);
             if (!in_f && !in_d) continue;
         }
         const float4 Cb = a.srcC[b], Eb = a.srcE[b], Fb = a.srcF[b];
@@ -338,6 +359,8 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
     a.gwidth = ctx->group_width;
     a.nbl = ctx->nbl;
     a.cap = ctx->nbl_cap;
+    a.uni = ctx->uni;
+    a.uoff = ctx->union_off;
     a.n_groups = (int)ctx->n_groups;
     a.x = p->x; a.y = p->y; a.z = p->z;
     a.srcA = ctx->srcA; a.srcB = ctx->srcB; a.srcC = ctx->srcC; a.srcD = ctx->srcD; a.srcE = ctx->srcE;
@@ -349,6 +372,11 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
     a.thermo = ctx->prm.energy == SPH_ENERGY_TOTAL;
     a.L = ctx->dom[3];
     a.alpha = ctx->prm.alpha; a.beta = ctx->prm.beta; a.eps = ctx->prm.eps_visc;
+    const int kk = ctx->prm.kernel;
+    const double sig = kk == SPH_KERNEL_M4 ? 1.0 / SPH_PI : kk == SPH_KERNEL_WC2 ? 21.0 / (16.0 * SPH_PI)
+                                                                             : 495.0 / (256.0 * SPH_PI);
+    a.Ld = df_host(a.L); a.sig_d = df_host(sig);
+    a.alpha_d = df_host(a.alpha); a.beta_d = df_host(a.beta); a.eps_d = df_host(a.eps);
     a.cnt = ctx->dcnt;
     SPH_CUDA(cudaEventRecord(ctx->ev[5], s));
     if (ctx->fp64) k_forces_df<<<grid_for(ctx->n_groups, FW), FW * 32, 0, s>>>(a);

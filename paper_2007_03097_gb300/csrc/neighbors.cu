@@ -36,8 +36,13 @@ struct ListArgs {
     float L, half, slack;
     int32_t *group_width;
     const int64_t *group_off;
-    uint32_t *nbl;
+    uint16_t *nbl;
     int64_t cap;
+    int32_t *group_ubound;         // union slots of each group (sizing passes write them)
+    const int64_t *union_off;
+    int32_t *group_union;          // union size of each group (fill pass)
+    uint32_t *uni;
+    int64_t ucap;
     DevCounters *cnt;
 };
 
@@ -85,32 +90,42 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
     const float gcx = 0.5f * (qlo.x + qhi.x), gcy = 0.5f * (qlo.y + qhi.y), gcz = 0.5f * (qlo.z + qhi.z);
     const float tx = (PA.x - gcx) + PA.y, ty = (PA.z - gcy) + PA.w, tz = (PB.x - gcz) + PB.y;
 
-    int64_t off = 0;
-    int width = 0;
+    int64_t off = 0, uoff = 0;
+    int width = 0, ucap = 0;
     bool fits = true;
     if (FILL) {
         off = a.group_off[g];
         width = a.group_width[g];
-        fits = off + 32 * (int64_t)width <= a.cap;
-        if (!fits) width = 0;                      // flagged below; nothing written
+        uoff = a.union_off[g];
+        ucap = a.group_ubound[g];
+        fits = off + 32 * (int64_t)width <= a.cap && uoff + ucap <= a.ucap;
+        if (!fits) { width = 0; ucap = 0; }        // flagged below; nothing written
     }
     int count = 0;
+    int uc = 0;                                    // union members so far (warp-uniform)
+    int ub = 0;                                    // union slots needed (sizing passes)
     bool overflow = false;
 
     // a non-target lane tests against a zero radius and accepts nothing
-    // but its own coincident copies, which the b != ia check removes
+    // but its own coincident copies, which the b != ia check removes.  A
+    // source accepted by some lane joins the group's union; the lanes list
+    // its local index.
     const float ca2 = tgt ? ca * ca * (1.f + MARGIN) : -1.f;
     auto process = [&](int ns) {
         for (int k = 0; k < ns; ++k) {
             const float4 q = pa[k];                    // .w = cov^2 (1 + MARGIN)
             const float dx = tx - q.x, dy = ty - q.y, dz = tz - q.z;
             const float r2 = (dx * dx + dy * dy) + dz * dz;
-            if (r2 <= fmaxf(ca2, q.w)) {
-                const int b = pi[k];
-                if (tgt && b != ia) {
-                    if (FILL && count < width) a.nbl[off + (int64_t)count * 32 + lane] = (uint32_t)b;
-                    ++count;
+            const int b = pi[k];
+            const bool acc = r2 <= fmaxf(ca2, q.w) && tgt && b != ia;
+            if (__ballot_sync(0xffffffffu, acc)) {
+                if (FILL) {
+                    if (lane == 0 && uc < ucap) a.uni[uoff + uc] = (uint32_t)b;
+                    if (acc && count < width)
+                        a.nbl[off + (int64_t)count * 32 + lane] = (uint16_t)(uc < (int)SPH_LOCAL_NONE ? uc : 0);
                 }
+                if (acc) ++count;
+                ++uc;
             }
         }
     };
@@ -187,6 +202,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
                 const unsigned nm = __shfl_sync(0xffffffffu, need, l);
                 const int c = __shfl_sync(0xffffffffu, cnt, l);
                 if ((nm >> lane) & 1u) count += c;
+                ub += c;                         // every kept particle may join the union
             }
             continue;
         }
@@ -254,14 +270,21 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
     int wmax = count;
     for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
     if (!FILL) {
-        if (lane == 0) a.group_width[g] = wmax;
+        if (lane == 0) {
+            a.group_width[g] = wmax;
+            a.group_ubound[g] = MODE == LM_BOUND ? ub : uc;
+        }
     } else {
-        if ((!fits || wmax > width) && lane == 0) atomicOr(&a.cnt->err, ERRB_LIST_CAPACITY);
+        // local indices are 16-bit: a union beyond 65534 sources is a capacity error
+        if ((!fits || wmax > width || uc > ucap || uc >= (int)SPH_LOCAL_NONE) && lane == 0)
+            atomicOr(&a.cnt->err, ERRB_LIST_CAPACITY);
         const int used = min(wmax, width);
-        for (int k = count; k < used; ++k) a.nbl[off + (int64_t)k * 32 + lane] = SPH_SENTINEL;
+        for (int k = count; k < used; ++k) a.nbl[off + (int64_t)k * 32 + lane] = (uint16_t)SPH_LOCAL_NONE;
         if (lane == 0) {
             a.group_width[g] = used;          // the exact width, within the sized slots
+            a.group_union[g] = min(uc, ucap);
             atomicAdd(&a.cnt->list_used, 32ull * (unsigned long long)used);
+            atomicAdd(&a.cnt->union_used, (unsigned long long)min(uc, ucap));
         }
     }
 }
@@ -274,13 +297,18 @@ __global__ void k_slots(const int32_t *__restrict__ width, int ng, int32_t *__re
 }
 
 __global__ void k_list_total(const int64_t *__restrict__ off, const int32_t *__restrict__ width, int ng,
-                             int64_t cap, int64_t *__restrict__ off_end, DevCounters *cnt)
+                             int64_t cap, int64_t *__restrict__ off_end, const int64_t *__restrict__ uoff,
+                             const int32_t *__restrict__ ubound, int64_t ucap, int64_t *__restrict__ uoff_end,
+                             DevCounters *cnt)
 {
     const int64_t total = off[ng - 1] + 32 * (int64_t)width[ng - 1];
+    const int64_t utotal = uoff[ng - 1] + (int64_t)ubound[ng - 1];
     off_end[0] = total;
+    uoff_end[0] = utotal;
     cnt->list_total = (unsigned long long)total;
     cnt->list_used = 0;
-    if (total > cap) atomicOr(&cnt->err, ERRB_LIST_CAPACITY);
+    cnt->union_used = 0;
+    if (total > cap || utotal > ucap) atomicOr(&cnt->err, ERRB_LIST_CAPACITY);
 }
 
 // After an overflowed build no list is valid: empty every group so that no
@@ -294,7 +322,8 @@ __global__ void k_guard_widths(int32_t *__restrict__ width, int ng, const DevCou
 // Exact neighbour sets from the lists (kind 0 density, kind 1 force).
 template <typename T, int KIND, bool FP64POS>
 __global__ void k_export(const int32_t *__restrict__ group_begin, int ng, const int64_t *__restrict__ goff,
-                         const int32_t *__restrict__ gwidth, const uint32_t *__restrict__ nbl,
+                         const int32_t *__restrict__ gwidth, const uint16_t *__restrict__ nbl,
+                         const uint32_t *__restrict__ uni, const int64_t *__restrict__ uoff,
                          const double *__restrict__ x, const double *__restrict__ y,
                          const double *__restrict__ z, const float4 *__restrict__ srcA,
                          const float4 *__restrict__ srcB, const T *__restrict__ h, int periodic, double L,
@@ -314,8 +343,9 @@ __global__ void k_export(const int32_t *__restrict__ group_begin, int ng, const 
     int64_t c = 0;
     const int64_t o = offsets ? offsets[ia] : 0;
     for (int k = 0; k < width; ++k) {
-        const uint32_t b = nbl[off + (int64_t)k * 32 + lane];
-        if (b == SPH_SENTINEL) continue;
+        const uint32_t e = nbl[off + (int64_t)k * 32 + lane];
+        if (e == SPH_LOCAL_NONE) continue;
+        const uint32_t b = uni[uoff[g] + e];
         bool in;
         if (FP64POS) {
             const double half = 0.5 * L;
@@ -373,6 +403,11 @@ int build_impl(sph_ctx *ctx, cudaStream_t s)
     a.group_off = ctx->group_off;
     a.nbl = ctx->nbl;
     a.cap = ctx->nbl_cap;
+    a.group_ubound = ctx->group_ubound;
+    a.union_off = ctx->union_off;
+    a.group_union = ctx->group_union;
+    a.uni = ctx->uni;
+    a.ucap = ctx->uni_cap;
     a.cnt = ctx->dcnt;
     const unsigned grid = grid_for(ng, LW);
     if (ctx->lists_exact) k_lists<LM_EXACT><<<grid, LW * 32, 0, s>>>(a);
@@ -381,8 +416,9 @@ int build_impl(sph_ctx *ctx, cudaStream_t s)
     k_slots<<<grid_for(ng, 256), 256, 0, s>>>(ctx->group_width, ng, ctx->itmp0);
     SPH_CHECK_LAUNCH();
     SPH_TRY(scan_exclusive_i64(ctx, ctx->itmp0, ctx->group_off, ng, s));
+    SPH_TRY(scan_exclusive_i64(ctx, ctx->group_ubound, ctx->union_off, ng, s));
     k_list_total<<<1, 1, 0, s>>>(ctx->group_off, ctx->group_width, ng, ctx->nbl_cap, ctx->group_off + ng,
-                                 ctx->dcnt);
+                                 ctx->union_off, ctx->group_ubound, ctx->uni_cap, ctx->union_off + ng, ctx->dcnt);
     SPH_CHECK_LAUNCH();
     k_lists<LM_FILL><<<grid, LW * 32, 0, s>>>(a);
     SPH_CHECK_LAUNCH();
@@ -423,7 +459,8 @@ int export_once(sph_ctx *ctx, const sph_particles *p, int kind, int64_t *counts,
     const int per = ctx->prm.periodic;
     const double L = ctx->dom[3];
 #define SPH_EXPORT_ARGS                                                                               \
-    ctx->group_begin, ng, ctx->group_off, ctx->group_width, ctx->nbl, p->x, p->y, p->z, ctx->srcA, ctx->srcB
+    ctx->group_begin, ng, ctx->group_off, ctx->group_width, ctx->nbl, ctx->uni, ctx->union_off, p->x, p->y, \
+        p->z, ctx->srcA, ctx->srcB
     if (ctx->fp64) {
         if (kind == 0)
             k_export<double, 0, true><<<grid, 128, 0, s>>>(SPH_EXPORT_ARGS, (const double *)p->h, per, L, ctx->nbl_cap, counts, offsets, idx);

@@ -14,37 +14,46 @@
 #define SPH_WARP 32
 #define SPH_SENTINEL 0xFFFFFFFFu
 
+#define SPH_LOCAL_NONE 0xFFFFu
+
 // Walks one lane's slot-major neighbour list off + 32 k + lane, k < width,
-// calling proc(b, A[b], B[b]) for every non-sentinel entry b.  PIPELINED: the
-// index of entry k + 2 and the two source records of entry k + 1 are in
-// flight while entry k is processed (a sentinel's records are fetched from
+// whose 16-bit entries index the group's source union uni[uoff ..]; calls
+// proc(b, A[b], B[b]) for every entry's global index b.  PIPELINED: entry
+// k + 3, the index of entry k + 2 and the records of entry k + 1 are in
+// flight while entry k is processed (an empty slot's records are fetched from
 // `self`, a valid index, and never processed).  This pays for the long
 // double-float pair arithmetic; the short FP32 one runs faster without it.
 template <bool PIPELINED, class Proc>
-__device__ __forceinline__ void walk_list(const uint32_t *__restrict__ nbl, int64_t off, int width, int lane,
-                                          uint32_t self, const float4 *__restrict__ A,
-                                          const float4 *__restrict__ B, Proc &&proc)
+__device__ __forceinline__ void walk_list(const uint16_t *__restrict__ nbl, int64_t off, int width, int lane,
+                                          uint32_t self, const uint32_t *__restrict__ uni, int64_t uoff,
+                                          const float4 *__restrict__ A, const float4 *__restrict__ B, Proc &&proc)
 {
+    const uint32_t *U = uni + uoff;
     if (!PIPELINED) {
         for (int k = 0; k < width; ++k) {
-            const uint32_t b = nbl[off + (int64_t)k * 32 + lane];
-            if (b == SPH_SENTINEL) continue;
+            const uint32_t e = nbl[off + (int64_t)k * 32 + lane];
+            if (e == SPH_LOCAL_NONE) continue;
+            const uint32_t b = __ldg(U + e);
             proc(b, A[b], B[b]);
         }
         return;
     }
     if (width <= 0) return;
-    const uint32_t *l = nbl + off + lane;
-    uint32_t b1 = __ldg(l);
-    uint32_t b2 = width > 1 ? __ldg(l + 32) : SPH_SENTINEL;
-    uint32_t j = b1 == SPH_SENTINEL ? self : b1;
+    const uint16_t *l = nbl + off + lane;
+    auto entry = [&](int k) -> uint32_t { return k < width ? (uint32_t)__ldg(l + (int64_t)k * 32) : SPH_LOCAL_NONE; };
+    auto index = [&](uint32_t e) -> uint32_t { return e == SPH_LOCAL_NONE ? SPH_SENTINEL : __ldg(U + e); };
+    uint32_t e2 = entry(2);
+    uint32_t b1 = index(entry(1));
+    uint32_t b0 = index(entry(0));
+    uint32_t j = b0 == SPH_SENTINEL ? self : b0;
     float4 P = __ldg(A + j), Q = __ldg(B + j);
     for (int k = 0; k < width; ++k) {
-        const uint32_t b = b1;
+        const uint32_t b = b0;
         const float4 Pc = P, Qc = Q;
-        b1 = b2;
-        b2 = k + 2 < width ? __ldg(l + (int64_t)(k + 2) * 32) : SPH_SENTINEL;
-        j = b1 == SPH_SENTINEL ? self : b1;
+        b0 = b1;
+        b1 = index(e2);
+        e2 = entry(k + 3);
+        j = b0 == SPH_SENTINEL ? self : b0;
         P = __ldg(A + j);
         Q = __ldg(B + j);
         if (b != SPH_SENTINEL) proc(b, Pc, Qc);
@@ -92,6 +101,7 @@ struct DevCounters {
     uint32_t hnet_err;                 // h-predictor tensor-core kernel: an MMA timed out
     uint32_t pad3;
     long long ns_total;                // misplaced keys found by the near-sorted pass
+    unsigned long long union_used;     // union slots holding the group unions of the last build
 };
 
 // near-sorted key pass: (key, id) pairs and per-tile extremes, prefix
@@ -150,10 +160,17 @@ struct sph_ctx {
     // A {x, y}, B {z, m}, C {vx, vy}, D {vz, h}, E {rho, P/rho^2}, F {c, -}
     float4 *srcA = nullptr, *srcB = nullptr, *srcC = nullptr, *srcD = nullptr, *srcE = nullptr, *srcF = nullptr;
     // ---- neighbour lists (group slabs, slot-major within a group)
-    uint32_t *nbl = nullptr;
+    // lists: per group a union of its source particles (global indices) and
+    // per-lane lists of 16-bit local indices into it
+    uint16_t *nbl = nullptr;
     int64_t nbl_cap = 0;
     int32_t *group_width = nullptr;
     int64_t *group_off = nullptr;       // n_groups + 1
+    uint32_t *uni = nullptr;            // union slots
+    int64_t uni_cap = 0;
+    int32_t *group_ubound = nullptr;    // union slots sized per group
+    int64_t *union_off = nullptr;       // n_groups + 1
+    int32_t *group_union = nullptr;     // union size per group
     // ---- density iteration state
     double *it_lo = nullptr, *it_hi = nullptr;
     int32_t *it_flags = nullptr;
