@@ -13,6 +13,8 @@
 // (r < 2 h_a) and every force pair (r < max(2 h_a, h_a + h_b)
 // <= max(2 h_a, 2 h_b)), so the h iteration and the force pass share it and
 // it is rebuilt only when some h outgrows its coverage.
+#include <algorithm>
+
 #include "sph_internal.cuh"
 
 namespace {
@@ -43,6 +45,9 @@ struct ListArgs {
     int32_t *group_union;          // union size of each group (fill pass)
     uint32_t *uni;
     int64_t ucap;
+    int32_t *kept;                 // leaves kept by the sizing pass, kcap per group (0: not cached)
+    int32_t *kept_count;
+    int kcap;
     DevCounters *cnt;
 };
 
@@ -102,6 +107,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
         if (!fits) { width = 0; ucap = 0; }        // flagged below; nothing written
     }
     int count = 0;
+    int nkept = 0;                                 // leaves kept by the sizing pass (warp-uniform)
     int uc = 0;                                    // union members so far (warp-uniform)
     int ub = 0;                                    // union slots needed (sizing passes)
     bool overflow = false;
@@ -130,10 +136,79 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
         }
     };
 
+    int ns = 0;
+    auto stage = [&](bool keep, int id) {
+        // particles of all kept leaves, loaded in warp-wide waves: lane L
+        // owns a leaf range [lb, lb + cnt) placed at [incl - cnt, incl) of
+        // the step's item sequence
+        int lb = 0, cnt = 0;
+        if (keep) {
+            lb = a.leaf_begin[id];
+            cnt = a.leaf_begin[id + 1] - lb;
+        }
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        s_lb[w][lane] = lb;
+        s_incl[w][lane] = incl;
+        __syncwarp();
+        for (int base = 0; base < total; base += 32) {
+            const int item = base + lane;
+            const int take2 = min(32, total - base);
+            if (lane < take2) {
+                // owner: first lane whose inclusive end exceeds item
+                int lo2 = 0, hi2 = 31;
+                while (lo2 < hi2) {
+                    const int mid = (lo2 + hi2) >> 1;
+                    if (s_incl[w][mid] > item) hi2 = mid; else lo2 = mid + 1;
+                }
+                const int start = lo2 > 0 ? s_incl[w][lo2 - 1] : 0;       // exclusive start of the owner
+                const int j = s_lb[w][lo2] + (item - start);
+                const int t = ns + lane;
+                const float4 qa = a.srcA[j], qb = a.srcB[j];
+                float rx = qa.x - gcx, ry = qa.z - gcy, rz = qb.x - gcz;
+                if (a.periodic) {                  // nearest image of the source
+                    rx -= a.L * rintf(rx / a.L);
+                    ry -= a.L * rintf(ry / a.L);
+                    rz -= a.L * rintf(rz / a.L);
+                }
+                const float cj = a.cov[j];
+                pa[t] = make_float4(rx + qa.y, ry + qa.w, rz + qb.y, cj * cj * (1.f + MARGIN));
+                pi[t] = j;
+            }
+            ns += take2;
+            __syncwarp();
+            if (ns >= 32) {
+                process(32);
+                __syncwarp();
+                const int rest = ns - 32;
+                if (lane < rest) {
+                    pa[lane] = pa[32 + lane];
+                    pi[lane] = pi[32 + lane];
+                }
+                ns = rest;
+                __syncwarp();
+            }
+        }
+    };
+
+    // the fill pass replays the leaves the sizing pass kept (same order), or
+    // walks the tree when they were not cached
+    const bool replay = FILL && a.kcap > 0 && a.kept_count[g] <= a.kcap;
+    if (replay) {
+        const int nk = a.kept_count[g];
+        for (int c = 0; c < nk; c += 32) {
+            const bool k2 = c + lane < nk;
+            stage(k2, k2 ? a.kept[(int64_t)g * a.kcap + c + lane] : 0);
+        }
+    }
     int sp = 0;
     if (lane == 0) stack[0] = a.n_leaves > 1 ? 0 : (int)0x80000000;
-    sp = 1;
-    int ns = 0;
+    sp = replay ? 0 : 1;
     // a correct radix tree visits each node at most once; the bound guards a
     // corrupted tree against an endless walk
     int64_t budget = 4 * (int64_t)a.n_leaves + 64;
@@ -197,6 +272,13 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
                 const int id = node & 0x7fffffff;
                 cnt = a.leaf_begin[id + 1] - a.leaf_begin[id];
             }
+            // remember the kept leaves: the fill pass replays them without a walk
+            const unsigned km = __ballot_sync(0xffffffffu, keep);
+            if (keep && a.kcap > 0) {
+                const int pos = nkept + __popc(km & ((1u << lane) - 1u));
+                if (pos < a.kcap) a.kept[(int64_t)g * a.kcap + pos] = node & 0x7fffffff;
+            }
+            nkept += __popc(km);
             for (unsigned m = __ballot_sync(0xffffffffu, keep); m; m &= m - 1) {
                 const int l = __ffs(m) - 1;
                 const unsigned nm = __shfl_sync(0xffffffffu, need, l);
@@ -206,63 +288,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
             }
             continue;
         }
-        // particles of all kept leaves, loaded in warp-wide waves: lane L
-        // owns a leaf range [lb, lb + cnt) placed at [incl - cnt, incl) of
-        // the step's item sequence
-        int lb = 0, cnt = 0;
-        if (keep) {
-            const int id = node & 0x7fffffff;
-            lb = a.leaf_begin[id];
-            cnt = a.leaf_begin[id + 1] - lb;
-        }
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        s_lb[w][lane] = lb;
-        s_incl[w][lane] = incl;
-        __syncwarp();
-        for (int base = 0; base < total; base += 32) {
-            const int item = base + lane;
-            const int take2 = min(32, total - base);
-            if (lane < take2) {
-                // owner: first lane whose inclusive end exceeds item
-                int lo2 = 0, hi2 = 31;
-                while (lo2 < hi2) {
-                    const int mid = (lo2 + hi2) >> 1;
-                    if (s_incl[w][mid] > item) hi2 = mid; else lo2 = mid + 1;
-                }
-                const int start = lo2 > 0 ? s_incl[w][lo2 - 1] : 0;       // exclusive start of the owner
-                const int j = s_lb[w][lo2] + (item - start);
-                const int t = ns + lane;
-                const float4 qa = a.srcA[j], qb = a.srcB[j];
-                float rx = qa.x - gcx, ry = qa.z - gcy, rz = qb.x - gcz;
-                if (a.periodic) {                  // nearest image of the source
-                    rx -= a.L * rintf(rx / a.L);
-                    ry -= a.L * rintf(ry / a.L);
-                    rz -= a.L * rintf(rz / a.L);
-                }
-                const float cj = a.cov[j];
-                pa[t] = make_float4(rx + qa.y, ry + qa.w, rz + qb.y, cj * cj * (1.f + MARGIN));
-                pi[t] = j;
-            }
-            ns += take2;
-            __syncwarp();
-            if (ns >= 32) {
-                process(32);
-                __syncwarp();
-                const int rest = ns - 32;
-                if (lane < rest) {
-                    pa[lane] = pa[32 + lane];
-                    pi[lane] = pi[32 + lane];
-                }
-                ns = rest;
-                __syncwarp();
-            }
-        }
+        stage(keep, node & 0x7fffffff);
     }
     if (MODE != LM_BOUND && ns > 0) process(ns);
 
@@ -273,6 +299,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
         if (lane == 0) {
             a.group_width[g] = wmax;
             a.group_ubound[g] = MODE == LM_BOUND ? ub : uc;
+            if (a.kcap > 0) a.kept_count[g] = MODE == LM_BOUND ? nkept : a.kcap + 1;   // exact pass caches none
         }
     } else {
         // local indices are 16-bit: a union beyond 65534 sources is a capacity error
@@ -408,6 +435,10 @@ int build_impl(sph_ctx *ctx, cudaStream_t s)
     a.group_union = ctx->group_union;
     a.uni = ctx->uni;
     a.ucap = ctx->uni_cap;
+    a.kept = ctx->kept;
+    a.kept_count = ctx->kept_count;
+    a.kcap = (int)std::min<int64_t>(256, ctx->kept_cap / std::max(ng, 1));
+    if (a.kcap < 32) a.kcap = 0;                   // too many groups to cache: walk again
     a.cnt = ctx->dcnt;
     const unsigned grid = grid_for(ng, LW);
     if (ctx->lists_exact) k_lists<LM_EXACT><<<grid, LW * 32, 0, s>>>(a);

@@ -171,6 +171,9 @@ struct sph_ctx {
     int32_t *group_ubound = nullptr;    // union slots sized per group
     int64_t *union_off = nullptr;       // n_groups + 1
     int32_t *group_union = nullptr;     // union size per group
+    int32_t *kept = nullptr;            // leaves kept by the list sizing pass, per group
+    int32_t *kept_count = nullptr;
+    int64_t kept_cap = 0;
     // ---- density iteration state
     double *it_lo = nullptr, *it_hi = nullptr;
     int32_t *it_flags = nullptr;
