@@ -46,7 +46,12 @@ F_FORCE = 96
 FP64_PIPE_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch of the dominant kernel from one ncu capture (see
 # profiles/), with the hash of the sources it was taken on
-TRAFFIC = {}
+TRAFFIC = {
+    # k_forces_df on the Sedov 64^3 step (profiles/k_forces_df_sedov64_fp64.md):
+    # 80.68 MB read + 3.54 MB written
+    "forces_fp64_sedov": {"bytes_per_launch": 84221696, "src": "6c64a48090a8",
+                          "files": ["forces.cu", "dfloat.cuh", "sph_internal.cuh"]},
+}
 FP32_PIPE_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 DF_EMULATED_TFLOPS = 152 * 128 * 2.07e9 * 2 / 18 / 1e12
 
@@ -350,10 +355,12 @@ def _oracle_sample(w, n_targets, seed=7):
 def cpu_baseline(w, seconds=12.0, label="sedov"):
     """The oracle as it stands on the host cores, on a sample of target
     particles sized for about `seconds` of work; interactions/s."""
-    inter, dt, nt, cores = _oracle_sample(w, 64)
-    scale = max(1, int(seconds / max(dt, 1e-3)))
-    nt2 = min(w.n, 64 * scale)
-    inter, dt, nt, cores = _oracle_sample(w, nt2)
+    nt2 = 64
+    for _ in range(3):                        # grow the sample until it takes about `seconds`
+        inter, dt, nt, cores = _oracle_sample(w, nt2)
+        if dt >= 0.5 * seconds or nt2 >= w.n:
+            break
+        nt2 = min(w.n, int(nt2 * seconds / max(dt, 1e-3)))
     return {"value": inter / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{nt} random targets of the {w.n}-particle {label} state, brute force over all sources: "
                       f"h-rho iteration + force pass, {dt:.1f} s"}
