@@ -34,6 +34,7 @@ constexpr int SRC_CAP = 448;   // staged union sources per warp (mixed sweep; 7 
 struct DensArgs {
     const int32_t *act;            // active groups of this sweep ...
     const int32_t *act_count;      // ... and their number (device)
+    int32_t *group_mark;           // sweep stamp of the last append (sparse sweep)
     int32_t *act_next;             // groups still active after it ...
     int32_t *act_next_count;       // ... and their number (zeroed before the sweep)
     int32_t *work;                 // group claim counter (zeroed before the sweep)
@@ -251,25 +252,170 @@ __device__ __forceinline__ bool df_lt(df a, df b) { return a.hi < b.hi || (a.hi 
 __device__ __forceinline__ df df_ld(const double *p) { const float2 v = *reinterpret_cast<const float2 *>(p); return df{v.x, v.y}; }
 __device__ __forceinline__ void df_st(double *p, df v) { *reinterpret_cast<float2 *>(p) = make_float2(v.hi, v.lo); }
 
+// One list entry b of target i in FP64 mode: the exact neighbour decision and
+// the double-float terms m_b W and m_b (3 W + q W') of rho and drho/dh.
+struct DfTarget {
+    float4 A, Bz;                  // two-float position and mass of the target
+    double hd;                     // its h
+    df hinv;
+    float thr_hi, thr_lo;          // FP32 band around 4 h^2
+    int64_t i;
+};
+
+__device__ __forceinline__ DfTarget df_target(const DensArgs &a, int64_t i, double hd, df h)
+{
+    DfTarget t;
+    t.A = a.srcA[i];
+    t.Bz = a.srcB[i];
+    t.hd = hd;
+    t.hinv = df_rcp(h);
+    const float thr_f = df_scale(df_sqr(h), 4.f).hi;
+    t.thr_hi = thr_f * (1.f + 1e-5f);
+    t.thr_lo = thr_f * (1.f - 1e-5f);
+    t.i = i;
+    return t;
+}
+
+__device__ __forceinline__ void df_pair(const DensArgs &a, const DfTarget &t, uint32_t b, const float4 &P,
+                                        const float4 &Q, df &sw, df &sd, int &cnt, int &band)
+{
+    const float Lf = (float)a.L, half = 0.5f * Lf, guard = 0.45f * Lf;
+    float dxf = (t.A.x - P.x) + (t.A.y - P.y);
+    float dyf = (t.A.z - P.z) + (t.A.w - P.w);
+    float dzf = (t.Bz.x - Q.x) + (t.Bz.y - Q.y);
+    int wx = 0, wy = 0, wz = 0;
+    if (a.periodic) {
+        if (dxf > half) { dxf -= Lf; wx = -1; } else if (dxf < -half) { dxf += Lf; wx = 1; }
+        if (dyf > half) { dyf -= Lf; wy = -1; } else if (dyf < -half) { dyf += Lf; wy = 1; }
+        if (dzf > half) { dzf -= Lf; wz = -1; } else if (dzf < -half) { dzf += Lf; wz = 1; }
+    }
+    const float r2f = (dxf * dxf + dyf * dyf) + dzf * dzf;
+    if (r2f > t.thr_hi) return;
+    if (r2f >= t.thr_lo) ++band;
+    if (r2f >= t.thr_lo || (a.periodic && fmaxf(fmaxf(fabsf(dxf), fabsf(dyf)), fabsf(dzf)) > guard)) {
+        // knife edge: the exact FP64 decision of the plain definition
+        const double L = a.L, hl = 0.5 * a.L;
+        const double dx = sep_d(a.x[t.i], a.x[b], a.periodic, L, hl);
+        const double dy = sep_d(a.y[t.i], a.y[b], a.periodic, L, hl);
+        const double dz = sep_d(a.z[t.i], a.z[b], a.periodic, L, hl);
+        if (!(r2_d(dx, dy, dz) < __dmul_rn(__dmul_rn(4.0, t.hd), t.hd))) return;
+    }
+    const df dx = df_sep_fast(t.A.x, t.A.y, P.x, P.y, wx, a.Ld);
+    const df dy = df_sep_fast(t.A.z, t.A.w, P.z, P.w, wy, a.Ld);
+    const df dz = df_sep_fast(t.Bz.x, t.Bz.y, Q.x, Q.y, wz, a.Ld);
+    const df q = df_mul(df_sqrt_fast(df_norm2(dx, dy, dz)), t.hinv);
+    df w, g3;
+    df_kern_w_g3(a.kernel, q, w, g3);
+    const df mb = df{Q.z, Q.w};
+    df_acc(sw, df_mul(mb, w));
+    df_acc(sd, df_mul(mb, g3));
+    ++cnt;
+}
+
+// The Newton update of target t from its sums (self term added here); writes
+// h, rho, omega, nnb and the iteration state; returns whether it iterates on.
+__device__ __forceinline__ bool df_finalize(const DensArgs &a, const DfTarget &t, df h, int32_t flags, df sw,
+                                            df sd, int cnt, int band)
+{
+    const int64_t i = t.i;
+    double *hp = (double *)a.h;
+    const df hinv = t.hinv;
+    const df ma = df{t.Bz.z, t.Bz.w};
+    sw = df_add(df_norm(sw), ma);                   // self term, w(0) = 1 for every kernel
+    sd = df_add(df_norm(sd), df_mul_f(ma, 3.f));    // 3 w(0) + 0 w'(0)
+    const df h3i = df_mul(df_sqr(hinv), hinv);
+    const df sh3 = df_mul(a.sig_d, h3i);
+    const df rho = df_mul(sh3, sw);
+    const df drho = df_neg(df_mul(df_mul(sh3, hinv), sd));
+    const df meta3 = df_mul(ma, a.eta3_d);
+    const int sweeps = a.it_sweeps[i] + 1;
+    a.it_sweeps[i] = sweeps;
+    bool done = false;
+    df hn = h, hfin = h, rho_out = rho;
+    if (flags & IT_FINAL) {
+        done = true;
+    } else {
+        const df mh3 = df_mul(meta3, h3i);
+        const df f = df_sub(mh3, rho);
+        if (f.hi == 0.f) {
+            done = true;
+        } else if (sweeps >= a.max_sweeps) {
+            done = true;
+            flags |= IT_NOT_CONV;
+        } else {
+            const df fp = df_sub(df_mul_f(df_mul(mh3, hinv), -3.f), drho);
+            df lo = df_ld(a.it_lo + i), hi = df_ld(a.it_hi + i);
+            if (f.hi > 0.f) { if (df_lt(lo, h)) lo = h; }
+            else { if (df_lt(h, hi)) hi = h; }
+            const df h2 = df_scale(h, 0.5f), h_2 = df_scale(h, 2.f);
+            const df alo = df_lt(lo, h2) ? h2 : lo;
+            const df ahi = df_lt(h_2, hi) ? h_2 : hi;
+            bool ok = false;
+            if (df_lt0(fp)) {
+                hn = df_sub(h, df_mul(f, df_rcp(fp)));
+                ok = !df_lt(hn, alo) && !df_lt(ahi, hn);
+            }
+            if (!ok) hn = df_scale(df_add(h, f.hi > 0.f ? ahi : alo), 0.5f);
+            int clamp = 0;                           // the bounds are written exactly
+            if (df_lt(hn, a.hmin_d)) { hn = a.hmin_d; clamp = -1; }
+            if (df_lt(a.hmax_d, hn)) { hn = a.hmax_d; clamp = 1; }
+            const df dh = df_sub(hn, h);
+            const float adh = fabsf(dh.hi);
+            const bool conv = adh < (float)a.h_tol * h.hi;
+            df_st(a.it_lo + i, lo);
+            df_st(a.it_hi + i, hi);
+            hp[i] = clamp < 0 ? a.h_min : clamp > 0 ? a.h_max : df_to_double(hn);
+            if (conv) {
+                // first-order finalization as in the mixed path (see there)
+                if (band == 0 && adh <= 1e-9f * h.hi) {
+                    rho_out = df_add(rho, df_mul(drho, dh));
+                    hfin = hn;
+                    done = true;
+                } else {
+                    flags |= IT_FINAL;
+                }
+            }
+        }
+    }
+    if (done) {
+        flags |= IT_DONE;
+        if (flags & IT_NOT_CONV) atomicAdd(&a.cnt->n_not_conv, 1);
+        else if (!a.fixed_h && (!df_lt(a.hmin_d, hfin) || !df_lt(hfin, a.hmax_d))) {
+            flags |= IT_H_BOUNDS;
+            atomicAdd(&a.cnt->n_hbounds, 1);
+        }
+    }
+    ((double *)a.rho)[i] = df_to_double(rho_out);
+    ((double *)a.omega)[i] = df_to_double(drho);
+    a.nnb[i] = cnt;
+    a.it_flags[i] = flags;
+    return !done;
+}
+
+// a particle whose support 2h left its list waits (state unchanged) for the
+// list rebuild the host makes between sweep batches
+__device__ __forceinline__ bool df_waiting(const DensArgs &a, int64_t i, df h)
+{
+    return df_lt(df{a.cov[i], 0.f}, df_scale(h, 2.f));
+}
+
+// Dense FP64 sweep of one group: one lane per target, each walking its list.
 __device__ __forceinline__ void density_group_df(const DensArgs &a, const int g, const int lane)
 {
     const int gb = a.group_begin[g], ge = a.group_begin[g + 1];
     const bool tgt = lane < ge - gb;
     const int i = gb + (tgt ? lane : 0);
-    double *hp = (double *)a.h;
     int32_t flags = tgt ? a.it_flags[i] : IT_DONE;
     bool active = !(flags & IT_DONE);
-    const double hd = active ? hp[i] : 1.0;
+    const double hd = active ? ((const double *)a.h)[i] : 1.0;
     const df h = df_from_double(hd);
-    // a particle whose support 2h left its list waits (state unchanged) for
-    // the list rebuild the host makes between sweep batches
     bool waiting = false;
-    if (active && df_lt(df{a.cov[i], 0.f}, df_scale(h, 2.f))) {
+    if (active && df_waiting(a, i, h)) {
         waiting = true;
         active = false;
         atomicAdd(&a.cnt->n_uncovered, 1);
     }
-    const df hinv = df_rcp(h);
+    const DfTarget t = df_target(a, i, hd, h);
     const int64_t off = a.goff[g];
     int width = a.gwidth[g];
     if (off + 32 * (int64_t)width > a.cap) width = 0;    // never read past the lists
@@ -277,120 +423,11 @@ __device__ __forceinline__ void density_group_df(const DensArgs &a, const int g,
     df sw = df{0.f, 0.f}, sd = df{0.f, 0.f};
     int cnt = 0;
     int band = 0;        // list entries within a relative 1e-5 of the support radius
-    const float4 A = a.srcA[i], Bz = a.srcB[i];
-    if (active) {
-        const float thr_f = df_scale(df_sqr(h), 4.f).hi;
-        const float thr_hi = thr_f * (1.f + 1e-5f), thr_lo = thr_f * (1.f - 1e-5f);
-        const float Lf = (float)a.L, half = 0.5f * Lf, guard = 0.45f * Lf;
-        const df Ld = a.Ld;
+    if (active)
         walk_list<true>(a.nbl, off, width, lane, (uint32_t)i, a.uni, a.uoff[g], a.srcA, a.srcB,
-                        [&](uint32_t b, const float4 &P, const float4 &Q) {
-            float dxf = (A.x - P.x) + (A.y - P.y);
-            float dyf = (A.z - P.z) + (A.w - P.w);
-            float dzf = (Bz.x - Q.x) + (Bz.y - Q.y);
-            int wx = 0, wy = 0, wz = 0;
-            if (a.periodic) {
-                if (dxf > half) { dxf -= Lf; wx = -1; } else if (dxf < -half) { dxf += Lf; wx = 1; }
-                if (dyf > half) { dyf -= Lf; wy = -1; } else if (dyf < -half) { dyf += Lf; wy = 1; }
-                if (dzf > half) { dzf -= Lf; wz = -1; } else if (dzf < -half) { dzf += Lf; wz = 1; }
-            }
-            const float r2f = (dxf * dxf + dyf * dyf) + dzf * dzf;
-            if (r2f > thr_hi) return;
-            if (r2f >= thr_lo) ++band;
-            if (r2f >= thr_lo || (a.periodic && fmaxf(fmaxf(fabsf(dxf), fabsf(dyf)), fabsf(dzf)) > guard)) {
-                // knife edge: the exact FP64 decision of the plain definition
-                const double L = a.L, hl = 0.5 * a.L;
-                const double dx = sep_d(a.x[i], a.x[b], a.periodic, L, hl);
-                const double dy = sep_d(a.y[i], a.y[b], a.periodic, L, hl);
-                const double dz = sep_d(a.z[i], a.z[b], a.periodic, L, hl);
-                if (!(r2_d(dx, dy, dz) < __dmul_rn(__dmul_rn(4.0, hd), hd))) return;
-            }
-            const df dx = df_sep_fast(A.x, A.y, P.x, P.y, wx, Ld);
-            const df dy = df_sep_fast(A.z, A.w, P.z, P.w, wy, Ld);
-            const df dz = df_sep_fast(Bz.x, Bz.y, Q.x, Q.y, wz, Ld);
-            const df q = df_mul(df_sqrt_fast(df_norm2(dx, dy, dz)), hinv);
-            df w, g3;
-            df_kern_w_g3(a.kernel, q, w, g3);
-            const df mb = df{Q.z, Q.w};
-            df_acc(sw, df_mul(mb, w));
-            df_acc(sd, df_mul(mb, g3));
-            ++cnt;
-        });
-    }
-
+                        [&](uint32_t b, const float4 &P, const float4 &Q) { df_pair(a, t, b, P, Q, sw, sd, cnt, band); });
     bool still = false;
-    if (active) {
-        const df ma = df{Bz.z, Bz.w};
-        sw = df_add(df_norm(sw), ma);                   // self term, w(0) = 1 for every kernel
-        sd = df_add(df_norm(sd), df_mul_f(ma, 3.f));    // 3 w(0) + 0 w'(0)
-        const df h3i = df_mul(df_sqr(hinv), hinv);
-        const df sh3 = df_mul(a.sig_d, h3i);
-        const df rho = df_mul(sh3, sw);
-        const df drho = df_neg(df_mul(df_mul(sh3, hinv), sd));
-        const df meta3 = df_mul(ma, a.eta3_d);
-        const int sweeps = a.it_sweeps[i] + 1;
-        a.it_sweeps[i] = sweeps;
-        bool done = false;
-        df hn = h, hfin = h, rho_out = rho;
-        if (flags & IT_FINAL) {
-            done = true;
-        } else {
-            const df mh3 = df_mul(meta3, h3i);
-            const df f = df_sub(mh3, rho);
-            if (f.hi == 0.f) {
-                done = true;
-            } else if (sweeps >= a.max_sweeps) {
-                done = true;
-                flags |= IT_NOT_CONV;
-            } else {
-                const df fp = df_sub(df_mul_f(df_mul(mh3, hinv), -3.f), drho);
-                df lo = df_ld(a.it_lo + i), hi = df_ld(a.it_hi + i);
-                if (f.hi > 0.f) { if (df_lt(lo, h)) lo = h; }
-                else { if (df_lt(h, hi)) hi = h; }
-                const df h2 = df_scale(h, 0.5f), h_2 = df_scale(h, 2.f);
-                const df alo = df_lt(lo, h2) ? h2 : lo;
-                const df ahi = df_lt(h_2, hi) ? h_2 : hi;
-                bool ok = false;
-                if (df_lt0(fp)) {
-                    hn = df_sub(h, df_mul(f, df_rcp(fp)));
-                    ok = !df_lt(hn, alo) && !df_lt(ahi, hn);
-                }
-                if (!ok) hn = df_scale(df_add(h, f.hi > 0.f ? ahi : alo), 0.5f);
-                int clamp = 0;                           // the bounds are written exactly
-                if (df_lt(hn, a.hmin_d)) { hn = a.hmin_d; clamp = -1; }
-                if (df_lt(a.hmax_d, hn)) { hn = a.hmax_d; clamp = 1; }
-                const df dh = df_sub(hn, h);
-                const float adh = fabsf(dh.hi);
-                const bool conv = adh < (float)a.h_tol * h.hi;
-                df_st(a.it_lo + i, lo);
-                df_st(a.it_hi + i, hi);
-                hp[i] = clamp < 0 ? a.h_min : clamp > 0 ? a.h_max : df_to_double(hn);
-                if (conv) {
-                    // first-order finalization as in the mixed path (see there)
-                    if (band == 0 && adh <= 1e-9f * h.hi) {
-                        rho_out = df_add(rho, df_mul(drho, dh));
-                        hfin = hn;
-                        done = true;
-                    } else {
-                        flags |= IT_FINAL;
-                    }
-                }
-            }
-        }
-        if (done) {
-            flags |= IT_DONE;
-            if (flags & IT_NOT_CONV) atomicAdd(&a.cnt->n_not_conv, 1);
-            else if (!a.fixed_h && (!df_lt(a.hmin_d, hfin) || !df_lt(hfin, a.hmax_d))) {
-                flags |= IT_H_BOUNDS;
-                atomicAdd(&a.cnt->n_hbounds, 1);
-            }
-        }
-        ((double *)a.rho)[i] = df_to_double(rho_out);
-        ((double *)a.omega)[i] = df_to_double(drho);
-        a.nnb[i] = cnt;
-        a.it_flags[i] = flags;
-        still = !done;
-    }
+    if (active) still = df_finalize(a, t, h, flags, sw, sd, cnt, band);
     if (waiting) still = true;
     int c = cnt;
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
@@ -400,6 +437,72 @@ __device__ __forceinline__ void density_group_df(const DensArgs &a, const int g,
         atomicAdd(&a.cnt->interactions, (unsigned long long)c);
         atomicAdd(&a.cnt->evaluations, (unsigned long long)__popc(amask));
         if (smask) a.act_next[atomicAdd(a.act_next_count, 1)] = g;
+    }
+}
+
+// Sparse FP64 sweep, for sweeps with few active groups: a warp per target
+// still iterating, its list split over the 32 lanes (slots k = lane mod 32)
+// and the double-float sums combined by a shuffle tree.  The dense sweep puts
+// one whole list on one lane, whose serial double-float chain then bounds a
+// sweep that touches few particles.
+constexpr int SPARSE_MAX_GROUPS = 1024;   // active groups below which the sparse sweep runs
+
+__global__ void __launch_bounds__(DW * 32) k_density_sparse(DensArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int n_act = *a.act_count;
+    if (n_act >= SPARSE_MAX_GROUPS) return;
+    const int stamp = a.cnt->sweep_stamp;
+    const int items = 32 * n_act;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(a.work, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= items) break;
+        const int g = a.act[it >> 5], p = it & 31;
+        const int gb = a.group_begin[g], ge = a.group_begin[g + 1];
+        if (p >= ge - gb) continue;
+        const int i = gb + p;
+        const int32_t flags = a.it_flags[i];
+        if (flags & IT_DONE) continue;
+        const double hd = ((const double *)a.h)[i];
+        const df h = df_from_double(hd);
+        bool still;
+        if (df_waiting(a, i, h)) {
+            if (lane == 0) atomicAdd(&a.cnt->n_uncovered, 1);
+            still = true;
+        } else {
+            const DfTarget t = df_target(a, i, hd, h);
+            const int64_t off = a.goff[g];
+            int width = a.gwidth[g];
+            if (off + 32 * (int64_t)width > a.cap) width = 0;
+            const uint32_t *U = a.uni + a.uoff[g];
+            df sw = df{0.f, 0.f}, sd = df{0.f, 0.f};
+            int cnt = 0, band = 0;
+            for (int k = lane; k < width; k += 32) {
+                const uint32_t e = a.nbl[off + (int64_t)k * 32 + p];
+                if (e == SPH_LOCAL_NONE) continue;
+                const uint32_t b = __ldg(U + e);
+                df_pair(a, t, b, __ldg(a.srcA + b), __ldg(a.srcB + b), sw, sd, cnt, band);
+            }
+            sw = df_norm(sw);
+            sd = df_norm(sd);
+            for (int o = 16; o > 0; o >>= 1) {
+                sw = df_add(sw, df{__shfl_xor_sync(0xffffffffu, sw.hi, o), __shfl_xor_sync(0xffffffffu, sw.lo, o)});
+                sd = df_add(sd, df{__shfl_xor_sync(0xffffffffu, sd.hi, o), __shfl_xor_sync(0xffffffffu, sd.lo, o)});
+                cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+                band += __shfl_xor_sync(0xffffffffu, band, o);
+            }
+            still = false;
+            if (lane == 0) {
+                still = df_finalize(a, t, h, flags, sw, sd, cnt, band);
+                atomicAdd(&a.cnt->interactions, (unsigned long long)cnt);
+                atomicAdd(&a.cnt->evaluations, 1ull);
+            }
+        }
+        // the group iterates on if any of its targets does (appended once per sweep)
+        if (lane == 0 && still && atomicExch(a.group_mark + g, stamp) != stamp)
+            a.act_next[atomicAdd(a.act_next_count, 1)] = g;
     }
 }
 
@@ -415,6 +518,7 @@ __global__ void __launch_bounds__(DW * 32) k_density(DensArgs a)
     float4 *s_src = s_dyn + (threadIdx.x >> 5) * a.src_cap;
     const int n_act = *a.act_count;
     if (blockIdx.x == 0 && threadIdx.x == 0 && n_act > 0) atomicAdd(&a.cnt->sweeps_done, 1);
+    if (FP64POS && n_act < SPARSE_MAX_GROUPS) return;   // k_density_sparse takes this sweep
     for (;;) {
         int gi = 0;
         if (lane == 0) gi = atomicAdd(a.work, 1);
@@ -455,6 +559,7 @@ __global__ void k_begin_sweep(DevCounters *c, int next)
 {
     c->act_count[next] = 0;
     c->work[next ^ 1] = 0;
+    c->sweep_stamp += 1;
 }
 
 __global__ void k_clear_uncovered(DevCounters *c) { c->n_uncovered = 0; }
@@ -525,6 +630,7 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
     a.uni = ctx->uni;
     a.uoff = ctx->union_off;
     a.group_union = ctx->group_union;
+    a.group_mark = ctx->group_mark;
     a.group_lo = ctx->group_lo;
     a.group_hi = ctx->group_hi;
     a.src_cap = ctx->fp64 ? 0 : SRC_CAP;
@@ -561,8 +667,13 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
             a.act_next_count = &ctx->dcnt->act_count[cur ^ 1];
             a.work = &ctx->dcnt->work[cur];
             if (launched < 64) SPH_CUDA(cudaEventRecord(ctx->kev[2 * launched], s));
-            if (ctx->fp64) k_density<T, true><<<grid, DW * 32, 0, s>>>(a);
-            else k_density<T, false><<<grid, DW * 32, smem, s>>>(a);
+            if (ctx->fp64) {
+                k_density<T, true><<<grid, DW * 32, 0, s>>>(a);
+                SPH_CHECK_LAUNCH();
+                k_density_sparse<<<(unsigned)ctx->num_sms * 8u, DW * 32, 0, s>>>(a);
+            } else {
+                k_density<T, false><<<grid, DW * 32, smem, s>>>(a);
+            }
             SPH_CHECK_LAUNCH();
             if (launched < 64) SPH_CUDA(cudaEventRecord(ctx->kev[2 * launched + 1], s));
             cur ^= 1;

@@ -102,6 +102,8 @@ struct DevCounters {
     uint32_t pad3;
     long long ns_total;                // misplaced keys found by the near-sorted pass
     unsigned long long union_used;     // union slots holding the group unions of the last build
+    int32_t sweep_stamp;               // counts density sweeps (group append marks)
+    int32_t pad4;
 };
 
 // near-sorted key pass: (key, id) pairs and per-tile extremes, prefix
@@ -171,6 +173,7 @@ struct sph_ctx {
     int32_t *group_ubound = nullptr;    // union slots sized per group
     int64_t *union_off = nullptr;       // n_groups + 1
     int32_t *group_union = nullptr;     // union size per group
+    int32_t *group_mark = nullptr;      // sweep stamp of a group's last append to the active list
     int32_t *kept = nullptr;            // leaves kept by the list sizing pass, per group
     int32_t *kept_count = nullptr;
     int64_t kept_cap = 0;
