@@ -102,13 +102,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 }
 
 // Step-path result: the seed h exp(s) of each particle (h itself, counted as
-// a fallback, when s is not finite or changes h by more than a factor 2),
-// and the features of the training samples i = k * stride, k < ns.
+// a fallback, when s is not finite or changes h by more than a factor 2).
 template <typename T>
 struct SeedOut {
     T *seed;
-    float *sf;
-    int64_t stride, ns;
 };
 
 template <bool FIELDS, typename T>
@@ -151,27 +148,19 @@ __global__ void __launch_bounds__(TM) k_infer_tc(const __nv_bfloat16 *__restrict
         const int64_t s = tile * TM + tid;
         const bool valid = s < nb;
         float x[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        if (valid) {
-            if (FIELDS) {
-                features_of(fa, s, x);
-                if (s % so.stride == 0 && s / so.stride < so.ns) {
-#pragma unroll
-                    for (int k = 0; k < 5; ++k) so.sf[5 * (s / so.stride) + k] = x[k];
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < 5; ++k) x[k] = f[5 * s + k];
-            }
-        }
         if (FIELDS) {
             // a tile of particles at rest (|div v dt| <= 1e-10 for all) keeps h:
             // s = f3 y is then below the FP32 resolution of exp(s) - 1 for any
             // |y| < 300, so the network's seed would be h exactly
-            const bool moving = valid && fabsf(x[3]) > 1e-10f;
-            if (!__syncthreads_or(moving)) {
+            const float f3 = valid ? (float)fa.divv[s] * fa.dt : 0.f;
+            if (!__syncthreads_or(valid && fabsf(f3) > 1e-10f)) {
                 if (valid) so.seed[s] = fa.h[s];
                 continue;
             }
+            if (valid) features_of(fa, s, x);
+        } else if (valid) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) x[k] = f[5 * s + k];
         }
         // layer 1 and the three-term split, 8 units (one 16-byte row of a core matrix) at a time
 #pragma unroll 1
@@ -595,12 +584,11 @@ int hnet_infer(sph_ctx *ctx, const float *feats, int64_t nb, float *y, cudaStrea
 template <typename T>
 int seed_impl(sph_ctx *ctx, const sph_particles *p, double dt, bool train, void *h_seed, cudaStream_t s)
 {
-    int64_t nb, stride;
-    sample_layout(ctx, p->n, &nb, &stride);
-    SeedOut<T> so{(T *)h_seed, ctx->hn_sample, stride, train ? nb : 0};
+    SeedOut<T> so{(T *)h_seed};
     k_infer_tc<true, T><<<infer_blocks(ctx, p->n), TM, infer_tc_smem(), s>>>(
         ctx->hn_bf16, nullptr, feat_args<T>(ctx, p, dt), p->n, nullptr, so, ctx->dcnt);
     SPH_CHECK_LAUNCH();
+    if (train) SPH_TRY(hnet_sample_features(ctx, p, dt, s));
     return SPH_OK;
 }
 
