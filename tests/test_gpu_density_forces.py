@@ -103,3 +103,27 @@ def test_mixed_precision_polytrope():
     for k in ("ax", "ay", "az"):
         assert np.max(np.abs(g[k] - getattr(f, k)) / f.S_a) < 1e-4, k
     assert np.max(np.abs(g["dudt"] - f.dudt) / np.maximum(f.S_u, 1e-30)) < 1e-4
+
+
+@pytest.mark.parametrize("precision,tol_rho,tol_a", [("mixed", 1e-5, 1e-4), ("fp64", 1e-10, 1e-10)])
+def test_large_source_unions(precision, tol_rho, tol_a):
+    """Many neighbours (eta = 2.2, ~470 per particle): each group's source
+    union holds well over the 448 sources a warp stages at once, so the mixed
+    sweep runs in several chunks; both precisions against the oracle."""
+    w = inputs.lattice(14, jitter=0.2, kernel=1, h_factor=2.2, fixed_h=False, precision=precision)
+    w.params["nb_capacity"] = 1024 * w.n                 # ~440 list slots per particle, beyond the default
+    rng = np.random.default_rng(8)
+    w.vx, w.vy, w.vz = 0.2 * rng.standard_normal((3, w.n))
+    B, ctx, p, ds, fs = _run(w, fp64=precision == "fp64")
+    info = B.sph_list_info(ctx)
+    _, ng = B.sph_tree_info(ctx)
+    assert info["union_used"] / ng > 448
+    g = p.in_original_order()
+    op = to_oracle_params(oracle, w.params)
+    d = oracle.density(op, w.x, w.y, w.z, w.m, w.h)
+    assert np.max(np.abs(g["rho"] / d.rho - 1)) < tol_rho
+    assert np.max(np.abs(g["h"] / d.h - 1)) < tol_rho
+    P, c = oracle.eos(op.gamma, d.rho, w.u)
+    f = oracle.forces(op, w.x, w.y, w.z, w.vx, w.vy, w.vz, w.m, d.h, d.rho, P, c)
+    for k in ("ax", "ay", "az"):
+        assert np.max(np.abs(g[k] - getattr(f, k)) / f.S_a) < tol_a, k
