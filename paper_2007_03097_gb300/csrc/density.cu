@@ -100,7 +100,7 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
         const float gcx = 0.5f * (qlo.x + qhi.x), gcy = 0.5f * (qlo.y + qhi.y), gcz = 0.5f * (qlo.z + qhi.z);
         const float4 A = a.srcA[i], Bz = a.srcB[i];
         const float tx = (A.x - gcx) + A.y, ty = (A.z - gcy) + A.w, tz = (Bz.x - gcz) + Bz.y;
-        const float L = (float)a.L;
+        const float L = (float)a.L, invL = 1.f / L;
         const float hf = (float)h;
         const float thr = __fmul_rn(__fmul_rn(4.f, hf), hf);
         const int U = a.group_union[g];
@@ -114,9 +114,9 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                 const float4 qa = __ldg(a.srcA + b), qb = __ldg(a.srcB + b);
                 float rx = qa.x - gcx, ry = qa.z - gcy, rz = qb.x - gcz;
                 if (a.periodic) {              // the image nearest the group
-                    rx -= L * rintf(rx / L);
-                    ry -= L * rintf(ry / L);
-                    rz -= L * rintf(rz / L);
+                    rx -= L * rintf(rx * invL);
+                    ry -= L * rintf(ry * invL);
+                    rz -= L * rintf(rz * invL);
                 }
                 s_src[t] = make_float4(rx + qa.y, ry + qa.w, rz + qb.y, qb.z);
             }

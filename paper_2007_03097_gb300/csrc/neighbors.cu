@@ -35,7 +35,7 @@ struct ListArgs {
     const int32_t *child;
     const float4 *node_lo, *node_hi;
     int periodic;
-    float L, half, slack;
+    float L, invL, slack;
     int32_t *group_width;
     const int64_t *group_off;
     uint16_t *nbl;
@@ -53,12 +53,12 @@ struct ListArgs {
 
 // gap between two boxes along one axis (periodic: minimum image of centres)
 __device__ __forceinline__ float axis_gap(float alo, float ahi, float blo, float bhi, int periodic, float L,
-                                          float half)
+                                          float invL)
 {
     float ca = 0.5f * (alo + ahi), ea = 0.5f * (ahi - alo);
     float cb = 0.5f * (blo + bhi), eb = 0.5f * (bhi - blo);
     float d = cb - ca;
-    if (periodic) d -= L * rintf(d / L);     // |d| <= L/2: the nearest image
+    if (periodic) d -= L * rintf(d * invL);  // the nearest image (the choice only matters far from any support)
     return fmaxf(0.f, fabsf(d) - ea - eb);
 }
 
@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
     __shared__ float4 s_pa[LW][TILE];   // source {x, y, z} relative to the group centre, cov^2 (1 + MARGIN)
     __shared__ int32_t s_pi[LW][TILE];  // source index
     __shared__ int32_t s_lb[LW][32], s_incl[LW][32];
+    __shared__ float4 s_blo[LW][32], s_bhi[LW][32];   // boxes of the leaves one walk step accepted
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int g = blockIdx.x * LW + w;
     if (g >= a.n_groups) return;
@@ -172,9 +173,9 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
                 const float4 qa = a.srcA[j], qb = a.srcB[j];
                 float rx = qa.x - gcx, ry = qa.z - gcy, rz = qb.x - gcz;
                 if (a.periodic) {                  // nearest image of the source
-                    rx -= a.L * rintf(rx / a.L);
-                    ry -= a.L * rintf(ry / a.L);
-                    rz -= a.L * rintf(rz / a.L);
+                    rx -= a.L * rintf(rx * a.invL);
+                    ry -= a.L * rintf(ry * a.invL);
+                    rz -= a.L * rintf(rz * a.invL);
                 }
                 const float cj = a.cov[j];
                 pa[t] = make_float4(rx + qa.y, ry + qa.w, rz + qb.y, cj * cj * (1.f + MARGIN));
@@ -227,9 +228,9 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
             if (leaf) { lo = a.leaf_lo[id]; hi = a.leaf_hi[id]; }
             else { lo = a.node_lo[id]; hi = a.node_hi[id]; }
             const float r = fmaxf(qcov, lo.w);
-            float gx = axis_gap(qlo.x, qhi.x, lo.x, hi.x, a.periodic, a.L, a.half);
-            float gy = axis_gap(qlo.y, qhi.y, lo.y, hi.y, a.periodic, a.L, a.half);
-            float gz = axis_gap(qlo.z, qhi.z, lo.z, hi.z, a.periodic, a.L, a.half);
+            float gx = axis_gap(qlo.x, qhi.x, lo.x, hi.x, a.periodic, a.L, a.invL);
+            float gy = axis_gap(qlo.y, qhi.y, lo.y, hi.y, a.periodic, a.L, a.invL);
+            float gz = axis_gap(qlo.z, qhi.z, lo.z, hi.z, a.periodic, a.L, a.invL);
             gx = fmaxf(0.f, gx - a.slack);
             gy = fmaxf(0.f, gy - a.slack);
             gz = fmaxf(0.f, gz - a.slack);
@@ -250,16 +251,19 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
         // the group is within max(cov_target, cov of the leaf) of its box;
         // need = the targets within reach of this lane's leaf
         unsigned need = 0;
-        for (unsigned m = __ballot_sync(0xffffffffu, acc && leaf); m; m &= m - 1) {
+        const unsigned lmask = __ballot_sync(0xffffffffu, acc && leaf);
+        if (lmask) {                         // the accepted leaves' boxes, read by every lane
+            s_blo[w][lane] = lo;
+            s_bhi[w][lane] = hi;
+            __syncwarp();
+        }
+        for (unsigned m = lmask; m; m &= m - 1) {
             const int l = __ffs(m) - 1;
-            const float lx = __shfl_sync(0xffffffffu, lo.x, l), ly = __shfl_sync(0xffffffffu, lo.y, l);
-            const float lz = __shfl_sync(0xffffffffu, lo.z, l), lc = __shfl_sync(0xffffffffu, lo.w, l);
-            const float hx = __shfl_sync(0xffffffffu, hi.x, l), hy = __shfl_sync(0xffffffffu, hi.y, l);
-            const float hz = __shfl_sync(0xffffffffu, hi.z, l);
-            float gx = fmaxf(0.f, axis_gap(PA.x, PA.x, lx, hx, a.periodic, a.L, a.half) - a.slack);
-            float gy = fmaxf(0.f, axis_gap(PA.z, PA.z, ly, hy, a.periodic, a.L, a.half) - a.slack);
-            float gz = fmaxf(0.f, axis_gap(PB.x, PB.x, lz, hz, a.periodic, a.L, a.half) - a.slack);
-            const float r = fmaxf(ca, lc);
+            const float4 bl = s_blo[w][l], bh = s_bhi[w][l];
+            float gx = fmaxf(0.f, axis_gap(PA.x, PA.x, bl.x, bh.x, a.periodic, a.L, a.invL) - a.slack);
+            float gy = fmaxf(0.f, axis_gap(PA.z, PA.z, bl.y, bh.y, a.periodic, a.L, a.invL) - a.slack);
+            float gz = fmaxf(0.f, axis_gap(PB.x, PB.x, bl.z, bh.z, a.periodic, a.L, a.invL) - a.slack);
+            const float r = fmaxf(ca, bl.w);
             const unsigned nm =
                 __ballot_sync(0xffffffffu, tgt && (gx * gx + gy * gy) + gz * gz <= r * r * (1.f + MARGIN));
             if (lane == l) need = nm;
@@ -424,7 +428,7 @@ int build_impl(sph_ctx *ctx, cudaStream_t s)
     a.node_lo = ctx->node_lo; a.node_hi = ctx->node_hi;
     a.periodic = ctx->prm.periodic;
     a.L = (float)ctx->dom[3];
-    a.half = 0.5f * a.L;
+    a.invL = 1.f / a.L;
     a.slack = (float)(1e-6 * ctx->dom[3]);
     a.group_width = ctx->group_width;
     a.group_off = ctx->group_off;
