@@ -23,6 +23,7 @@ constexpr int LW = 4;              // warps per block
 constexpr int STACK = 1024;        // traversal stack entries per warp
 constexpr int TILE = 64;           // source tile entries per warp
 constexpr float MARGIN = 2e-5f;    // relative margin of the FP32 tests
+constexpr float FAR = 1e18f;       // coordinate of padding candidates and of non-target lanes
 
 struct ListArgs {
     const float4 *srcA, *srcB;     // two-float positions {xh, xl, yh, yl}, {zh, zl, .., ..}
@@ -51,15 +52,15 @@ struct ListArgs {
     DevCounters *cnt;
 };
 
-// gap between two boxes along one axis (periodic: minimum image of centres)
-__device__ __forceinline__ float axis_gap(float alo, float ahi, float blo, float bhi, int periodic, float L,
-                                          float invL)
+// gap along one axis between a box of centre c and half-extent e and a
+// point (or a box of centre p whose half-extent, plus the rounding slack, is
+// already in e); periodic: the nearest image of the centres (the choice only
+// matters far from any support)
+__device__ __forceinline__ float axis_gap(float c, float e, float p, int periodic, float L, float invL)
 {
-    float ca = 0.5f * (alo + ahi), ea = 0.5f * (ahi - alo);
-    float cb = 0.5f * (blo + bhi), eb = 0.5f * (bhi - blo);
-    float d = cb - ca;
-    if (periodic) d -= L * rintf(d * invL);  // the nearest image (the choice only matters far from any support)
-    return fmaxf(0.f, fabsf(d) - ea - eb);
+    float d = c - p;
+    if (periodic) d -= L * rintf(d * invL);
+    return fmaxf(0.f, fabsf(d) - e);
 }
 
 // Modes of one traversal: LM_BOUND sizes each lane's list by the particles of
@@ -76,7 +77,10 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
     __shared__ float4 s_pa[LW][TILE];   // source {x, y, z} relative to the group centre, cov^2 (1 + MARGIN)
     __shared__ int32_t s_pi[LW][TILE];  // source index
     __shared__ int32_t s_lb[LW][32], s_incl[LW][32];
-    __shared__ float4 s_blo[LW][32], s_bhi[LW][32];   // boxes of the leaves one walk step accepted
+    __shared__ float4 s_bc[LW][32], s_be[LW][32];     // leaves one walk step accepted: centre, cov^2 (1 + MARGIN);
+                                                      // half-extent + slack
+    __shared__ int32_t s_self[LW][32];                // batch position of each target's own particle (-1: none)
+    __shared__ int32_t s_loc[LW][32];                 // local (union) index of each batch candidate
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int g = blockIdx.x * LW + w;
     if (g >= a.n_groups) return;
@@ -94,7 +98,11 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
     // FP32 coordinates relative to the group centre: the rounding error of
     // each is half an ulp of the relative value, far inside MARGIN
     const float gcx = 0.5f * (qlo.x + qhi.x), gcy = 0.5f * (qlo.y + qhi.y), gcz = 0.5f * (qlo.z + qhi.z);
-    const float tx = (PA.x - gcx) + PA.y, ty = (PA.z - gcy) + PA.w, tz = (PB.x - gcz) + PB.y;
+    // a non-target lane sits far from every candidate and accepts none
+    const float tx = tgt ? (PA.x - gcx) + PA.y : FAR, ty = tgt ? (PA.z - gcy) + PA.w : FAR,
+                tz = tgt ? (PB.x - gcz) + PB.y : FAR;
+    const float gex = 0.5f * (qhi.x - qlo.x) + a.slack, gey = 0.5f * (qhi.y - qlo.y) + a.slack,
+                gez = 0.5f * (qhi.z - qlo.z) + a.slack;
 
     int64_t off = 0, uoff = 0;
     int width = 0, ucap = 0;
@@ -113,28 +121,53 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
     int ub = 0;                                    // union slots needed (sizing passes)
     bool overflow = false;
 
-    // a non-target lane tests against a zero radius and accepts nothing
-    // but its own coincident copies, which the b != ia check removes.  A
-    // source accepted by some lane joins the group's union; the lanes list
-    // its local index.
+    uint16_t *wp = FILL ? a.nbl + off + lane : nullptr;   // this lane's next list slot
+
+    // A batch of at most 32 staged candidates: every lane tests all of them
+    // (bit k of `bits` = candidate k within this lane's reach), its own
+    // particle is cleared, a candidate accepted by some lane joins the
+    // group's union, and each lane lists the local indices of its accepted
+    // candidates in batch order.  Padding candidates sit far away with a
+    // negative radius and are accepted by none.
     const float ca2 = tgt ? ca * ca * (1.f + MARGIN) : -1.f;
     auto process = [&](int ns) {
-        for (int k = 0; k < ns; ++k) {
+        if (lane >= ns) {
+            pa[lane] = make_float4(FAR, FAR, FAR, -1.f);
+            pi[lane] = -1;
+        }
+        s_self[w][lane] = -1;
+        __syncwarp();
+        const int j = pi[lane];
+        if (j >= gb && j < ge) s_self[w][j - gb] = lane;
+        unsigned bits = 0;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
             const float4 q = pa[k];                    // .w = cov^2 (1 + MARGIN)
             const float dx = tx - q.x, dy = ty - q.y, dz = tz - q.z;
             const float r2 = (dx * dx + dy * dy) + dz * dz;
-            const int b = pi[k];
-            const bool acc = r2 <= fmaxf(ca2, q.w) && tgt && b != ia;
-            if (__ballot_sync(0xffffffffu, acc)) {
-                if (FILL) {
-                    if (lane == 0 && uc < ucap) a.uni[uoff + uc] = (uint32_t)b;
-                    if (acc && count < width)
-                        a.nbl[off + (int64_t)count * 32 + lane] = (uint16_t)(uc < (int)SPH_LOCAL_NONE ? uc : 0);
-                }
-                if (acc) ++count;
-                ++uc;
-            }
+            if (r2 <= fmaxf(ca2, q.w)) bits |= 1u << k;
         }
+        __syncwarp();
+        const int me = s_self[w][lane];
+        if (me >= 0) bits &= ~(1u << me);
+        const unsigned any = __reduce_or_sync(0xffffffffu, bits);
+        if (FILL) {
+            const int pos = uc + __popc(any & ((1u << lane) - 1u));
+            if (((any >> lane) & 1u) && pos < ucap) a.uni[uoff + pos] = (uint32_t)j;
+            s_loc[w][lane] = pos < (int)SPH_LOCAL_NONE ? pos : 0;
+            __syncwarp();
+            for (unsigned m = bits; m; m &= m - 1) {
+                if (count < width) {
+                    *wp = (uint16_t)s_loc[w][__ffs(m) - 1];
+                    wp += 32;
+                }
+                ++count;
+            }
+        } else {
+            count += __popc(bits);
+        }
+        uc += __popc(any);
+        __syncwarp();                                  // the batch's shared arrays are reused
     };
 
     int ns = 0;
@@ -222,18 +255,19 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
         __syncwarp();
         bool acc = false;
         const bool leaf = node < 0;
-        float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+        float4 bc = make_float4(0.f, 0.f, 0.f, 0.f), be = bc;
         if (lane < take) {
+            float4 lo, hi;
             const int id = node & 0x7fffffff;
             if (leaf) { lo = a.leaf_lo[id]; hi = a.leaf_hi[id]; }
             else { lo = a.node_lo[id]; hi = a.node_hi[id]; }
             const float r = fmaxf(qcov, lo.w);
-            float gx = axis_gap(qlo.x, qhi.x, lo.x, hi.x, a.periodic, a.L, a.invL);
-            float gy = axis_gap(qlo.y, qhi.y, lo.y, hi.y, a.periodic, a.L, a.invL);
-            float gz = axis_gap(qlo.z, qhi.z, lo.z, hi.z, a.periodic, a.L, a.invL);
-            gx = fmaxf(0.f, gx - a.slack);
-            gy = fmaxf(0.f, gy - a.slack);
-            gz = fmaxf(0.f, gz - a.slack);
+            bc = make_float4(0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z),
+                             lo.w * lo.w * (1.f + MARGIN));
+            be = make_float4(0.5f * (hi.x - lo.x), 0.5f * (hi.y - lo.y), 0.5f * (hi.z - lo.z), 0.f);
+            const float gx = axis_gap(bc.x, be.x + gex, gcx, a.periodic, a.L, a.invL);
+            const float gy = axis_gap(bc.y, be.y + gey, gcy, a.periodic, a.L, a.invL);
+            const float gz = axis_gap(bc.z, be.z + gez, gcz, a.periodic, a.L, a.invL);
             acc = (gx * gx + gy * gy) + gz * gz <= r * r * (1.f + MARGIN);
         }
         const unsigned mint = __ballot_sync(0xffffffffu, acc && !leaf);
@@ -253,19 +287,18 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
         unsigned need = 0;
         const unsigned lmask = __ballot_sync(0xffffffffu, acc && leaf);
         if (lmask) {                         // the accepted leaves' boxes, read by every lane
-            s_blo[w][lane] = lo;
-            s_bhi[w][lane] = hi;
+            s_bc[w][lane] = bc;
+            s_be[w][lane] = make_float4(be.x + a.slack, be.y + a.slack, be.z + a.slack, 0.f);
             __syncwarp();
         }
         for (unsigned m = lmask; m; m &= m - 1) {
             const int l = __ffs(m) - 1;
-            const float4 bl = s_blo[w][l], bh = s_bhi[w][l];
-            float gx = fmaxf(0.f, axis_gap(PA.x, PA.x, bl.x, bh.x, a.periodic, a.L, a.invL) - a.slack);
-            float gy = fmaxf(0.f, axis_gap(PA.z, PA.z, bl.y, bh.y, a.periodic, a.L, a.invL) - a.slack);
-            float gz = fmaxf(0.f, axis_gap(PB.x, PB.x, bl.z, bh.z, a.periodic, a.L, a.invL) - a.slack);
-            const float r = fmaxf(ca, bl.w);
+            const float4 c = s_bc[w][l], e = s_be[w][l];
+            const float gx = axis_gap(c.x, e.x, PA.x, a.periodic, a.L, a.invL);
+            const float gy = axis_gap(c.y, e.y, PA.z, a.periodic, a.L, a.invL);
+            const float gz = axis_gap(c.z, e.z, PB.x, a.periodic, a.L, a.invL);
             const unsigned nm =
-                __ballot_sync(0xffffffffu, tgt && (gx * gx + gy * gy) + gz * gz <= r * r * (1.f + MARGIN));
+                __ballot_sync(0xffffffffu, tgt && (gx * gx + gy * gy) + gz * gz <= fmaxf(ca2, c.w));
             if (lane == l) need = nm;
         }
         const bool keep = need != 0;
