@@ -145,7 +145,7 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                     const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
                     if (fabsf(r2 - thr) <= 1e-5f * thr) ++band;
                     if (!(r2 < thr)) continue;
-                    const T qq = (T)sqrtf(r2) * hinv;
+                    const T qq = (T)(r2 > 0.f ? r2 * rsqrtf(r2) : 0.f) * hinv;   // r within 2 ulp
                     T w, dw;
                     kern_wdw<T>(a.kernel, qq, w, dw);
                     const T mb = (T)q.w;

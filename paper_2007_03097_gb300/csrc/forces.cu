@@ -98,16 +98,18 @@ __global__ void __launch_bounds__(FW * 32) k_forces_f32(ForceArgs a)
             dv += mb * (sig * h2 * h2 * dwq) * rinv * vdotr;
         }
         if (in_f) {
+            // approximate reciprocals (within 2 ulp): the FP32 pass is held
+            // to relative tolerances far above them
             const float hab = 0.5f * hs;
-            const float habinv = 1.f / hab;
+            const float habinv = __fdividef(1.f, hab);
             float w, dwq;
             kern_wdw<float>(a.kernel, r * habinv, w, dwq);
             const float h2 = habinv * habinv;
             const float gr = sig * h2 * h2 * dwq * rinv;          // grad_a W = gr * r_ab
             float Pi = 0.f;
             if (vdotr < 0.f) {
-                const float mu = hab * vdotr / (r2 + eps * hab * hab);
-                Pi = (-alpha * 0.5f * (ca + Db.z) * mu + beta * mu * mu) / (0.5f * (rhoa + Db.x));
+                const float mu = __fdividef(hab * vdotr, r2 + eps * hab * hab);
+                Pi = __fdividef(-alpha * 0.5f * (ca + Db.z) * mu + beta * mu * mu, 0.5f * (rhoa + Db.x));
             }
             const float coef = mb * (pra + Db.y + Pi) * gr;
             accx -= coef * dx;
