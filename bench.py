@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--workload", default="sedov", choices=["sedov", "polytrope", "collision", "turbulence"],
                     help="sedov: 64^3 FP64 (headline); polytrope 2^20, collision 2x2^21, turbulence 256^3: "
                          "FP32 pairs on FP64 positions")
+    ap.add_argument("--curve", default="morton", choices=["morton", "hilbert"],
+                    help="space-filling curve of the particle keys (Sec. 2.1, Tree topology)")
     ap.add_argument("--train-steps", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -164,7 +166,7 @@ def run_sph(args):
     w = make_workload(args)
     fp64 = w.params.get("precision", "fp64") == "fp64"
     params = dict(w.params)
-    params.update(hnet_batch=8192, hnet_iters=1, hnet_lr=1e-3)
+    params.update(hnet_batch=8192, hnet_iters=1, hnet_lr=1e-3, curve=args.curve)
     ctx = B.Context(params, w.n)
     p = B.Particles.from_workload(w, fp64=fp64)
     stream = torch.cuda.current_stream()
@@ -316,7 +318,7 @@ def run_sph(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
             "config": {"workload": workload_label(args, w),
                        "n_particles": w.n, "precision": "fp64" if fp64 else "mixed (FP32 pairs, FP64 positions)",
-                       "parallelism": f"replicas x{world}",
+                       "parallelism": f"replicas x{world}", "curve": args.curve,
                        "l2": "flushed between timed steps (256 MB write)",
                        "step": "learned-h sph_step (network seed + one online Adam round)"},
             "steps_per_s": world * args.steps / t_l,

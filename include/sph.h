@@ -76,6 +76,18 @@ typedef enum { SPH_FP64 = 0, SPH_MIXED = 1 } sph_precision;
  *                      recovers u = e - v^2/2 after each kick.             */
 typedef enum { SPH_ENERGY_INTERNAL = 0, SPH_ENERGY_TOTAL = 1 } sph_energy;
 
+/* Space-filling curve of the particle keys (Sec. 2.1, Tree topology: both
+ * the Morton and the Hilbert curve order the particles).  Either key is
+ * 1 << 63 | a 63-bit index of the particle's cell on the 2^21-per-axis grid
+ * of the key domain, three bits per octree level, so that the top 3l bits
+ * below the leading 1 name the level-l octree cell in both.
+ * SPH_CURVE_MORTON:  bits of (ix, iy, iz) interleaved, x lowest in each triple.
+ * SPH_CURVE_HILBERT: the Hilbert index of (ix, iy, iz) after J. Skilling,
+ *                    "Programming the Hilbert curve", AIP Conf. Proc. 707
+ *                    (2004): cell (0, 0, 0) first, consecutive cells face
+ *                    neighbours.                                           */
+typedef enum { SPH_CURVE_MORTON = 0, SPH_CURVE_HILBERT = 1 } sph_curve;
+
 typedef struct {
     int32_t kernel;      /* sph_kernel                                          */
     int32_t precision;   /* sph_precision                                       */
@@ -102,7 +114,7 @@ typedef struct {
     int32_t hnet_batch;  /* samples per online training step (strided subset)   */
     int32_t hnet_iters;  /* Adam steps per sph_step when training online        */
     int32_t energy;      /* sph_energy                                          */
-    int32_t reserved;    /* 0                                                   */
+    int32_t curve;       /* sph_curve                                           */
 } sph_params;
 
 /* Particle arrays, structure of arrays, length n, caller-owned DEVICE memory.
@@ -220,8 +232,9 @@ int sph_totals(sph_ctx *ctx, const sph_particles *p, double out[8], void *stream
 
 /* ---- stages exposed for verification ------------------------------------------ */
 
-/* Morton keys of p's current positions into keys (device, n), and the key
- * domain (lo_x, lo_y, lo_z, L) into dom (host, 4 doubles). */
+/* Keys of p's current positions on the context's curve (sph_params.curve:
+ * Morton or Hilbert) into keys (device, n), and the key domain
+ * (lo_x, lo_y, lo_z, L) into dom (host, 4 doubles). */
 int sph_morton_keys(sph_ctx *ctx, const sph_particles *p, uint64_t *keys,
                     double dom[4], void *stream);
 

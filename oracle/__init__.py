@@ -5,7 +5,7 @@ CPU-baseline leg of ``bench.py`` may import this package.  It shares no code wit
 the CUDA library in ``paper_2007_03097_gb300`` and never imports it.
 
 The heavy loops (brute-force O(N^2) neighbour search, density, forces, Morton
-keys) live in ``sph_oracle.c``; this module adds the parts that are plain array
+and Hilbert keys) live in ``sph_oracle.c``; this module adds the parts that are plain array
 arithmetic: the leapfrog step, conserved totals, leaf levels by definition and
 the h-predictor MLP (numpy, FP64).
 
@@ -101,6 +101,8 @@ def lib():
         _lib.orc_dWdh.argtypes = [i32, d, d]
         _lib.orc_kernel_eval.argtypes = [i32, i64, P, P, P, P, P]
         _lib.orc_morton_keys.argtypes = [i64, P, P, P, P, d, P]
+        _lib.orc_hilbert_keys.argtypes = [i64, P, P, P, P, d, P]
+        _lib.orc_hilbert_index_many.argtypes = [i64, P, P, P, i32, P]
         _lib.orc_sort_perm.argtypes = [i64, P, P, P]
         _lib.orc_density.restype = i32
         _lib.orc_density.argtypes = [ctypes.POINTER(_Params), i64, P, P, P, P, P, i64, P,
@@ -156,6 +158,30 @@ def morton_keys(x, y, z, lo, L):
     keys = np.empty(x.size, dtype=np.uint64)
     lib().orc_morton_keys(x.size, _p(x), _p(y), _p(z), _p(lo), float(L), _p(keys))
     return keys
+
+
+def hilbert_keys(x, y, z, lo, L):
+    """Hilbert keys (Sec. 2.1, Tree topology) on the Morton cells: 1 << 63 |
+    the 63-bit Hilbert index of (ix, iy, iz) after Skilling (2004)."""
+    x, y, z = _f64(x), _f64(y), _f64(z)
+    lo = _f64(lo)
+    keys = np.empty(x.size, dtype=np.uint64)
+    lib().orc_hilbert_keys(x.size, _p(x), _p(y), _p(z), _p(lo), float(L), _p(keys))
+    return keys
+
+
+def hilbert_index(ix, iy, iz, bits: int = 21):
+    """Hilbert index of integer cells with ``bits`` bits per axis (1..21)."""
+    assert 1 <= bits <= 21
+    c = [np.ascontiguousarray(a, dtype=np.uint32) for a in (ix, iy, iz)]
+    out = np.empty(c[0].size, dtype=np.uint64)
+    lib().orc_hilbert_index_many(c[0].size, _p(c[0]), _p(c[1]), _p(c[2]), int(bits), _p(out))
+    return out
+
+
+def keys(x, y, z, lo, L, curve: str = "morton"):
+    """Keys of the named curve ("morton" or "hilbert")."""
+    return hilbert_keys(x, y, z, lo, L) if curve == "hilbert" else morton_keys(x, y, z, lo, L)
 
 
 def sort_perm(keys, ids):

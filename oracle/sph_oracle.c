@@ -181,6 +181,68 @@ void orc_morton_keys(int64_t n, const double *x, const double *y, const double *
     }
 }
 
+/* Hilbert keys (Sec. 2.1, Tree topology names the Hilbert curve beside
+ * Morton's).  Index of a cell (X[0], X[1], X[2]) of `bits` bits per axis
+ * after J. Skilling, "Programming the Hilbert curve", AIP Conf. Proc. 707
+ * (2004), in the steps of that method:
+ *   1. for Q = 2^(bits-1) down to 2, with P = Q - 1, and for each axis i in
+ *      turn: if bit Q of X[i] is set, invert the bits P of X[0]; otherwise
+ *      exchange the bits P of X[0] and X[i];
+ *   2. Gray-encode the axes: X[i] ^= X[i-1] for i = 1, 2;
+ *   3. t = XOR of (Q - 1) over the bits Q >= 2 set in X[2]; X[i] ^= t;
+ *   4. the index takes, from the top bit down, the bits of X[0], X[1], X[2]
+ *      in that order.
+ * Keys use the Morton cells and the leading 1.                            */
+uint64_t orc_hilbert_index(uint32_t ix, uint32_t iy, uint32_t iz, int bits)
+{
+    uint32_t X[3] = {ix, iy, iz};
+    for (uint32_t Q = 1u << (bits - 1); Q > 1; Q >>= 1) {
+        const uint32_t P = Q - 1;
+        for (int i = 0; i < 3; ++i) {
+            if (X[i] & Q) {
+                X[0] ^= P;
+            } else {
+                const uint32_t t = (X[0] ^ X[i]) & P;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    X[1] ^= X[0];
+    X[2] ^= X[1];
+    uint32_t t = 0;
+    for (uint32_t Q = 1u << (bits - 1); Q > 1; Q >>= 1)
+        if (X[2] & Q) t ^= Q - 1;
+    for (int i = 0; i < 3; ++i) X[i] ^= t;
+    uint64_t h = 0;
+    for (int b = bits - 1; b >= 0; --b)
+        for (int i = 0; i < 3; ++i) h = (h << 1) | ((X[i] >> b) & 1u);
+    return h;
+}
+
+void orc_hilbert_index_many(int64_t n, const uint32_t *ix, const uint32_t *iy, const uint32_t *iz, int bits,
+                            uint64_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = orc_hilbert_index(ix[i], iy[i], iz[i], bits);
+}
+
+void orc_hilbert_keys(int64_t n, const double *x, const double *y, const double *z,
+                      const double lo[3], double L, uint64_t *keys)
+{
+    const double scale = 2097152.0 / L;
+    for (int64_t i = 0; i < n; ++i) {
+        const double c[3] = {x[i], y[i], z[i]};
+        uint32_t cell[3];
+        for (int d = 0; d < 3; ++d) {
+            double f = floor((c[d] - lo[d]) * scale);
+            if (!(f >= 0.0)) f = 0.0;
+            if (f > 2097151.0) f = 2097151.0;
+            cell[d] = (uint32_t)f;
+        }
+        keys[i] = orc_hilbert_index(cell[0], cell[1], cell[2], 21) | (1ull << 63);
+    }
+}
+
 /* Permutation sorting (key, id) ascending; ids are unique so the order is
  * unique (Sec. 2.1 gives every particle a unique id for this purpose).    */
 typedef struct { uint64_t key; uint32_t id; uint32_t pos; } kip;

@@ -22,6 +22,7 @@ SPH_OK, SPH_ERR_ARG, SPH_ERR_CUDA, SPH_ERR_CAPACITY = 0, -1, -2, -3
 SPH_ERR_NOT_CONVERGED, SPH_ERR_H_BOUNDS, SPH_ERR_NONFINITE, SPH_ERR_STATE = -4, -5, -6, -7
 SPH_FP64, SPH_MIXED = 0, 1
 SPH_ENERGY_INTERNAL, SPH_ENERGY_TOTAL = 0, 1
+SPH_CURVE_MORTON, SPH_CURVE_HILBERT = 0, 1
 SPH_HNET_NPARAM = 4609
 SPH_HNET_SEED, SPH_HNET_TRAIN = 1, 2
 
@@ -43,7 +44,7 @@ class sph_params(_c.Structure):
                 ("max_sweeps", _c.c_int32), ("leaf_size", _c.c_int32), ("h_min", _c.c_double),
                 ("h_max", _c.c_double), ("skin", _c.c_double), ("rho_ref", _c.c_double),
                 ("nb_capacity", _c.c_int64), ("hnet_lr", _c.c_double), ("hnet_batch", _c.c_int32),
-                ("hnet_iters", _c.c_int32), ("energy", _c.c_int32), ("reserved", _c.c_int32)]
+                ("hnet_iters", _c.c_int32), ("energy", _c.c_int32), ("curve", _c.c_int32)]
 
 
 _FIELDS = ["vx", "vy", "vz", "m", "h", "u", "hprev", "rho", "omega", "P", "c", "ax", "ay", "az", "dudt",
@@ -165,6 +166,8 @@ def make_params(p: dict) -> sph_params:
     q.hnet_batch = int(p.get("hnet_batch", 32768))
     q.hnet_iters = int(p.get("hnet_iters", 1))
     q.energy = int(p.get("energy", SPH_ENERGY_INTERNAL))
+    curve = p.get("curve", SPH_CURVE_MORTON)
+    q.curve = int({"morton": SPH_CURVE_MORTON, "hilbert": SPH_CURVE_HILBERT}.get(curve, curve))
     return q
 
 

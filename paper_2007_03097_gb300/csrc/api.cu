@@ -42,6 +42,7 @@ int check_params(const sph_params *q, std::string &why)
     if (!(q->rho_ref > 0.0)) { why = "rho_ref must be positive"; return SPH_ERR_ARG; }
     if (q->nb_capacity < 0) { why = "nb_capacity must be >= 0"; return SPH_ERR_ARG; }
     if (q->energy != SPH_ENERGY_INTERNAL && q->energy != SPH_ENERGY_TOTAL) { why = "energy must be an sph_energy"; return SPH_ERR_ARG; }
+    if (q->curve != SPH_CURVE_MORTON && q->curve != SPH_CURVE_HILBERT) { why = "curve must be an sph_curve"; return SPH_ERR_ARG; }
     if (!(q->hnet_lr > 0.0) || q->hnet_batch < 1 || q->hnet_iters < 0 || q->hnet_iters > 10000) {
         why = "need hnet_lr > 0, hnet_batch >= 1, 0 <= hnet_iters <= 10000";
         return SPH_ERR_ARG;

@@ -1,8 +1,8 @@
-// Tree build (Sec. 2.1, Tree topology): Morton keys with a leading 1 bit,
-// LSD radix sort of (key, index) with equal keys ordered by particle id,
-// in-place permutation of every particle array into key order, octree leaf
-// cells of at most leaf_size particles, target groups of at most 32
-// particles, and a binary radix tree over the leaves (Karras 2012) with
+// Tree build (Sec. 2.1, Tree topology): Morton or Hilbert keys with a
+// leading 1 bit, LSD radix sort of (key, index) with equal keys ordered by
+// particle id, in-place permutation of every particle array into key order,
+// octree leaf cells of at most leaf_size particles, target groups of at most
+// 32 particles, and a binary radix tree over the leaves (Karras 2012) with
 // bounding boxes and maximal coverage radius for pruning the neighbour search.
 //
 // The paper builds a hashed octree by inserting particles one by one and
@@ -82,6 +82,43 @@ __device__ __forceinline__ uint64_t spread3(uint64_t v)
     return v;
 }
 
+// Hilbert index of cell (x, y, z), 21 bits per axis, after J. Skilling,
+// "Programming the Hilbert curve" (AIP Conf. Proc. 707, 2004).  From the top
+// level down, each axis that has the level's bit set reflects the lower bits
+// of x, and each that has it clear swaps its lower bits with those of x; the
+// axes are then Gray-coded (y ^= x, z ^= y) and every axis is XOR-ed with
+// the mask whose bit j is the parity of the bits of z above j.  The index
+// interleaves the three words, x highest in each triple.  Written with
+// select masks so that the warp does not diverge.
+__device__ __forceinline__ uint64_t hilbert3(uint32_t x, uint32_t y, uint32_t z)
+{
+#pragma unroll
+    for (int lev = 20; lev >= 1; --lev) {
+        const uint32_t P = (1u << lev) - 1u;
+        const uint32_t sx = 0u - ((x >> lev) & 1u), sy = 0u - ((y >> lev) & 1u), sz = 0u - ((z >> lev) & 1u);
+        x ^= P & sx;                                   // x against itself: reflect or nothing
+        uint32_t t = (x ^ y) & P & ~sy;                // y: swap with x where clear
+        x ^= (P & sy) ^ t;
+        y ^= t;
+        t = (x ^ z) & P & ~sz;                         // z: the same
+        x ^= (P & sz) ^ t;
+        z ^= t;
+    }
+    y ^= x;
+    z ^= y;
+    uint32_t s = z;                                    // s_j = parity of z's bits at j and above
+    s ^= s >> 1;
+    s ^= s >> 2;
+    s ^= s >> 4;
+    s ^= s >> 8;
+    s ^= s >> 16;
+    const uint32_t t = s >> 1;                         // parity of the bits above j
+    x ^= t;
+    y ^= t;
+    z ^= t;
+    return (spread3(x) << 2) | (spread3(y) << 1) | spread3(z);
+}
+
 __device__ __forceinline__ uint64_t cell_of(double c, double lo, double scale)
 {
     double f = floor(__dmul_rn(__dsub_rn(c, lo), scale));
@@ -93,7 +130,7 @@ __device__ __forceinline__ uint64_t cell_of(double c, double lo, double scale)
 template <typename T>
 __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ y,
                        const double *__restrict__ z, const T *__restrict__ h,
-                       const T *__restrict__ m, int64_t n, DevCounters *cnt,
+                       const T *__restrict__ m, int64_t n, int curve, DevCounters *cnt,
                        uint64_t *__restrict__ keys, uint32_t *__restrict__ vals)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -105,8 +142,10 @@ __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ 
     if (h) ok = ok && isfinite((double)h[i]) && (double)h[i] > 0.0;
     if (m) ok = ok && isfinite((double)m[i]);
     if (!ok) atomicOr(&cnt->err, ERRB_NONFINITE);
-    uint64_t key = spread3(cell_of(xi, lx, scale)) | (spread3(cell_of(yi, ly, scale)) << 1) |
-                   (spread3(cell_of(zi, lz, scale)) << 2) | (1ull << 63);
+    const uint64_t cx = cell_of(xi, lx, scale), cy = cell_of(yi, ly, scale), cz = cell_of(zi, lz, scale);
+    const uint64_t key = (curve == SPH_CURVE_HILBERT ? hilbert3((uint32_t)cx, (uint32_t)cy, (uint32_t)cz)
+                                                     : spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2)) |
+                         (1ull << 63);
     keys[i] = key;
     if (vals) vals[i] = (uint32_t)i;
 }
@@ -828,7 +867,7 @@ int keys_impl(sph_ctx *ctx, const sph_particles *p, uint64_t *keys, uint32_t *va
 {
     SPH_TRY(compute_domain(ctx, p, s));
     k_keys<T><<<grid_for(p->n, 256), 256, 0, s>>>(p->x, p->y, p->z, (const T *)p->h, (const T *)p->m, p->n,
-                                                  ctx->dcnt, keys, vals);
+                                                  ctx->prm.curve, ctx->dcnt, keys, vals);
     SPH_CHECK_LAUNCH();
     return SPH_OK;
 }

@@ -28,10 +28,12 @@ def _run(w, fp64=True):
 
 
 @pytest.mark.parametrize("kind", [0, 1])
-@pytest.mark.parametrize("wname", ["lattice", "sedov", "polytrope"])
-def test_neighbour_sets_bit_exact(kind, wname):
+@pytest.mark.parametrize("wname,curve", [("lattice", "morton"), ("sedov", "morton"), ("polytrope", "morton"),
+                                         ("sedov", "hilbert"), ("polytrope", "hilbert")])
+def test_neighbour_sets_bit_exact(kind, wname, curve):
     w = {"lattice": lambda: inputs.lattice(16), "sedov": lambda: inputs.sedov(14),
          "polytrope": lambda: inputs.polytrope(6000, seed=4, precision="fp64")}[wname]()
+    w.params["curve"] = curve
     B, ctx, p, _, _ = _run(w)
     g = p.numpy()
     op = to_oracle_params(oracle, w.params)
@@ -65,9 +67,12 @@ def test_lattice_fixed_h_fp64():
     assert ds["interactions"] == int(d.nnb.sum())
 
 
-def test_sedov_variable_h_fp64():
-    """Sedov blast (reduced to 16^3), Wendland C2, h-rho iteration to 1e-6."""
+@pytest.mark.parametrize("curve", ["morton", "hilbert"])
+def test_sedov_variable_h_fp64(curve):
+    """Sedov blast (reduced to 16^3), Wendland C2, h-rho iteration to 1e-6;
+    the particles in Morton or Hilbert order."""
     w = inputs.sedov(16)
+    w.params["curve"] = curve
     rng = np.random.default_rng(1)
     w.vx, w.vy, w.vz = 0.1 * rng.standard_normal((3, w.n))     # exercise the viscosity
     B, ctx, p, ds, fs = _run(w)
@@ -86,10 +91,12 @@ def test_sedov_variable_h_fp64():
     assert np.max(np.abs(g["vsig"] / f.vsig - 1)) < 1e-10
 
 
-def test_mixed_precision_polytrope():
+@pytest.mark.parametrize("curve", ["morton", "hilbert"])
+def test_mixed_precision_polytrope(curve):
     """n = 1 polytrope, FP32 pair arithmetic on two-float relative coordinates
     with FP64 positions: rho to 1e-5, a and du/dt to 1e-4 of their scale."""
     w = inputs.polytrope(20000, seed=11, precision="mixed")
+    w.params["curve"] = curve
     rng = np.random.default_rng(2)
     w.vx, w.vy, w.vz = 0.05 * rng.standard_normal((3, w.n))
     B, ctx, p, ds, fs = _run(w, fp64=False)

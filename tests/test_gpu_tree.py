@@ -1,7 +1,7 @@
-"""GPU parity of the tree stage (Sec. 2.1, Tree topology): Morton keys and the
-(key, id) sort permutation bit-exact against the oracle, the in-place
-permutation of the particle arrays, and the octree leaves against the leaf
-definition evaluated by the oracle."""
+"""GPU parity of the tree stage (Sec. 2.1, Tree topology): Morton and Hilbert
+keys and the (key, id) sort permutation bit-exact against the oracle, the
+in-place permutation of the particle arrays, and the octree leaves against the
+leaf definition evaluated by the oracle, on either curve."""
 import numpy as np
 import pytest
 import torch
@@ -24,17 +24,21 @@ def _cloud(n, seed, periodic):
     return w
 
 
+@pytest.mark.parametrize("curve", ["morton", "hilbert"])
 @pytest.mark.parametrize("n,periodic", [(1, True), (37, True), (4097, True), (50000, False), (70001, True)])
-def test_morton_keys_bit_exact(n, periodic):
+def test_keys_bit_exact(n, periodic, curve):
     B = need_gpu()
     w = _cloud(n, 1, periodic)
+    w.params["curve"] = curve
+    if n > 2:                                            # the corner cells of the key grid
+        w.x[:2], w.y[:2], w.z[:2] = (0.0, 1.0 - 1e-12), (0.0, 1.0 - 1e-12), (0.0, 1.0 - 1e-12)
     ctx = B.Context(w.params, n)
     p = B.Particles.from_workload(w, fp64=True)
     keys, dom = B.sph_morton_keys(ctx, p)
     op = to_oracle_params(oracle, w.params)
     lo, L = oracle.domain(w.x, w.y, w.z, op)
     assert np.array_equal(dom, np.array([*lo, L]))
-    ref = oracle.morton_keys(w.x, w.y, w.z, lo, L)
+    ref = oracle.keys(w.x, w.y, w.z, lo, L, curve)
     assert np.array_equal(keys, ref)
 
 
@@ -74,11 +78,14 @@ def test_sort_permutation_many_duplicates():
     assert np.array_equal(perm, oracle.sort_perm(keys, ids))
 
 
-@pytest.mark.parametrize("name,leaf_size", [("lattice", 32), ("polytrope", 32), ("polytrope", 8)])
-def test_build_tree_order_and_leaves(name, leaf_size):
+@pytest.mark.parametrize("name,leaf_size,curve", [("lattice", 32, "morton"), ("polytrope", 32, "morton"),
+                                                  ("polytrope", 8, "morton"), ("lattice", 32, "hilbert"),
+                                                  ("polytrope", 32, "hilbert"), ("polytrope", 8, "hilbert")])
+def test_build_tree_order_and_leaves(name, leaf_size, curve):
     B = need_gpu()
     w = inputs.lattice(20, jitter=0.1) if name == "lattice" else inputs.polytrope(30000, seed=9, precision="fp64")
     w.params["leaf_size"] = leaf_size
+    w.params["curve"] = curve
     rng = np.random.default_rng(0)
     w.u = rng.random(w.n) + 0.5                          # a field to follow through the permutation
     ctx = B.Context(w.params, w.n)
@@ -88,7 +95,7 @@ def test_build_tree_order_and_leaves(name, leaf_size):
     B.sph_build_tree(ctx, p)
     op = to_oracle_params(oracle, w.params)
     lo, L = oracle.domain(w.x, w.y, w.z, op)
-    keys = oracle.morton_keys(w.x, w.y, w.z, lo, L)
+    keys = oracle.keys(w.x, w.y, w.z, lo, L, curve)
     perm = oracle.sort_perm(keys, ids)
     g = p.numpy()
     assert np.array_equal(g["id"], ids[perm])
@@ -108,8 +115,9 @@ def test_build_tree_order_and_leaves(name, leaf_size):
     assert nl == len(start) and 1 <= ng <= w.n
 
 
-@pytest.mark.parametrize("moved", [0, 1, 50, 3000, 20000])
-def test_rebuild_of_nearly_sorted_particles(moved):
+@pytest.mark.parametrize("moved,curve", [(0, "morton"), (1, "morton"), (50, "morton"), (3000, "morton"),
+                                         (20000, "morton"), (50, "hilbert"), (3000, "hilbert")])
+def test_rebuild_of_nearly_sorted_particles(moved, curve):
     """A rebuild after small moves (the state of every step after the first)
     finds most particles in place and moves only the misplaced ones; the
     order must still be the (key, id) sort of the current keys.  Large moves
@@ -118,6 +126,7 @@ def test_rebuild_of_nearly_sorted_particles(moved):
     w = inputs.lattice(24, jitter=0.1)                  # 13,824 particles
     rng = np.random.default_rng(moved + 11)
     w.u = rng.random(w.n) + 0.5
+    w.params["curve"] = curve
     ctx = B.Context(w.params, w.n)
     p = B.Particles.from_workload(w, fp64=True)
     B.sph_build_tree(ctx, p)                             # key order of the initial state
@@ -135,7 +144,7 @@ def test_rebuild_of_nearly_sorted_particles(moved):
     B.sph_build_tree(ctx, p)
     op = to_oracle_params(oracle, w.params)
     lo, L = oracle.domain(x, y, z, op)
-    keys = oracle.morton_keys(x, y, z, lo, L)
+    keys = oracle.keys(x, y, z, lo, L, curve)
     perm = oracle.sort_perm(keys, g["id"])
     h = p.numpy()
     assert np.array_equal(h["id"], g["id"][perm])
