@@ -65,9 +65,9 @@ def parse():
     ap.add_argument("--n-side", type=int, default=None,
                     help="lattice side of the sedov (default 64, the headline workload) and turbulence (default 256) "
                          "workloads; smaller sides serve profiling captures")
-    ap.add_argument("--workload", default="sedov", choices=["sedov", "polytrope", "collision", "turbulence"],
+    ap.add_argument("--workload", default="sedov", choices=["sedov", "polytrope", "collision", "turbulence", "sod"],
                     help="sedov: 64^3 FP64 (headline); polytrope 2^20, collision 2x2^21, turbulence 256^3: "
-                         "FP32 pairs on FP64 positions")
+                         "FP32 pairs on FP64 positions; sod: the 1D shock tube, 10,000 particles in the tube, FP64")
     ap.add_argument("--curve", default="morton", choices=["morton", "hilbert"],
                     help="space-filling curve of the particle keys (Sec. 2.1, Tree topology)")
     ap.add_argument("--train-steps", type=int, default=16)
@@ -128,6 +128,8 @@ def make_workload(args):
         return inputs.polytrope(1 << 20)
     if args.workload == "collision":
         return inputs.collision(1 << 21)
+    if args.workload == "sod":
+        return inputs.sod(10000)
     return inputs.turbulence(args.n_side or 256)
 
 
@@ -139,6 +141,9 @@ def workload_label(args, w):
         return f"n=1 polytrope, {w.n} particles, Wendland C2, eta 1.2, open boundary, FP32 pairs / FP64 positions"
     if args.workload == "collision":
         return f"two colliding n=1 polytropes, {w.n} particles, closing speed 1, FP32 pairs / FP64 positions"
+    if args.workload == "sod":
+        return (f"1D Sod shock tube, {w.info['n_tube']} particles in [0, 1) and its mirror image ({w.n} in the "
+                f"periodic box), M4, eta 1.2, gamma 1.4, FP64")
     return f"turbulence box {args.n_side or 256}^3 = {w.n} particles, Wendland C4, Mach 2, FP32 pairs / FP64 positions"
 
 

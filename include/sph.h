@@ -115,6 +115,12 @@ typedef struct {
     int32_t hnet_iters;  /* Adam steps per sph_step when training online        */
     int32_t energy;      /* sph_energy                                          */
     int32_t curve;       /* sph_curve                                           */
+    int32_t dim;         /* spatial dimension D, 1 or 3.  D = 1 puts every
+                            particle on the x axis (y = z = 0, else
+                            SPH_ERR_ARG from the tree build); the kernels take
+                            their 1D normalisations and shapes, and Eq. 9
+                            reads h = eta (m/rho)^(1/D)                        */
+    int32_t pad;         /* 0                                                   */
 } sph_params;
 
 /* Particle arrays, structure of arrays, length n, caller-owned DEVICE memory.

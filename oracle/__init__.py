@@ -51,7 +51,7 @@ class _Params(ctypes.Structure):
         ("gamma", ctypes.c_double), ("eta", ctypes.c_double),
         ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("eps_visc", ctypes.c_double),
         ("fixed_h", ctypes.c_int), ("h_tol", ctypes.c_double), ("max_sweeps", ctypes.c_int),
-        ("h_min", ctypes.c_double), ("h_max", ctypes.c_double),
+        ("h_min", ctypes.c_double), ("h_max", ctypes.c_double), ("dim", ctypes.c_int),
     ]
 
 
@@ -72,6 +72,7 @@ class Params:
     max_sweeps: int = 30
     h_min: float = 1e-6
     h_max: float = 0.25
+    dim: int = 3
 
     def c(self) -> _Params:
         p = _Params()
@@ -84,6 +85,7 @@ class Params:
         p.fixed_h = int(bool(self.fixed_h))
         p.h_tol, p.max_sweeps = self.h_tol, int(self.max_sweeps)
         p.h_min, p.h_max = self.h_min, self.h_max
+        p.dim = int(self.dim)
         return p
 
 
@@ -94,12 +96,12 @@ def lib():
         d, i64, i32 = ctypes.c_double, ctypes.c_int64, ctypes.c_int
         P = ctypes.c_void_p
         _lib.orc_W.restype = d
-        _lib.orc_W.argtypes = [i32, d, d]
+        _lib.orc_W.argtypes = [i32, i32, d, d]
         _lib.orc_dWdr.restype = d
-        _lib.orc_dWdr.argtypes = [i32, d, d]
+        _lib.orc_dWdr.argtypes = [i32, i32, d, d]
         _lib.orc_dWdh.restype = d
-        _lib.orc_dWdh.argtypes = [i32, d, d]
-        _lib.orc_kernel_eval.argtypes = [i32, i64, P, P, P, P, P]
+        _lib.orc_dWdh.argtypes = [i32, i32, d, d]
+        _lib.orc_kernel_eval.argtypes = [i32, i32, i64, P, P, P, P, P]
         _lib.orc_morton_keys.argtypes = [i64, P, P, P, P, d, P]
         _lib.orc_hilbert_keys.argtypes = [i64, P, P, P, P, d, P]
         _lib.orc_hilbert_index_many.argtypes = [i64, P, P, P, i32, P]
@@ -129,12 +131,13 @@ def num_threads() -> int:
 
 
 # --------------------------------------------------------------------------- kernels
-def kernel(kind: int, r, h):
-    """W, dW/dr, dW/dh of the chosen smoothing kernel (support 2h), elementwise."""
+def kernel(kind: int, r, h, dim: int = 3):
+    """W, dW/dr, dW/dh of the chosen smoothing kernel (support 2h) in D = dim
+    dimensions, elementwise."""
     r = _f64(np.broadcast_to(r, np.broadcast(r, h).shape))
     h = _f64(np.broadcast_to(h, r.shape))
     W, dr, dh = np.empty_like(r), np.empty_like(r), np.empty_like(r)
-    lib().orc_kernel_eval(kind, r.size, _p(r), _p(h), _p(W), _p(dr), _p(dh))
+    lib().orc_kernel_eval(kind, int(dim), r.size, _p(r), _p(h), _p(W), _p(dr), _p(dh))
     return W, dr, dh
 
 
@@ -531,16 +534,17 @@ def bf16_round(a):
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def hnet_features(h, hprev, nnb, rho, m, divv, dt, eta, rho_ref=1.0):
-    """Network inputs per particle: log(h/hbar) with hbar = eta (m/rho_ref)^(1/3),
-    log(max(nnb, 1/2)/nbar) with nbar = 32 pi eta^3/3 (the neighbour count of
-    a uniform medium inside 2h), log(rho h^3/(m eta^3)) (the fixed-point
-    ratio of Eq. 9), div v * dt, and log(h/hprev) (0 when hprev <= 0)."""
+def hnet_features(h, hprev, nnb, rho, m, divv, dt, eta, rho_ref=1.0, dim=3):
+    """Network inputs per particle: log(h/hbar) with hbar = eta (m/rho_ref)^(1/D),
+    log(max(nnb, 1/2)/nbar) with nbar the neighbour count of a uniform medium
+    inside 2h (32 pi eta^3/3 for D = 3, 4 eta for D = 1), log(rho h^D/(m eta^D))
+    (the fixed-point ratio of Eq. 9), div v * dt, and log(h/hprev) (0 when
+    hprev <= 0)."""
     h, hprev, rho, m, divv = map(lambda a: np.asarray(a, dtype=np.float64), (h, hprev, rho, m, divv))
     nnb = np.asarray(nnb, dtype=np.float64)
-    eta3 = eta ** 3
-    hbar = eta * np.cbrt(m / rho_ref)
-    nbar = 32.0 * math.pi * eta3 / 3.0
+    etaD = eta ** dim
+    hbar = eta * (m / rho_ref) ** (1.0 / dim) if dim != 3 else eta * np.cbrt(m / rho_ref)
+    nbar = 4.0 * eta if dim == 1 else 32.0 * math.pi * etaD / 3.0
     f4 = np.where(hprev > 0, np.log(np.where(hprev > 0, h / np.where(hprev > 0, hprev, 1.0), 1.0)), 0.0)
-    return np.stack([np.log(h / hbar), np.log(np.maximum(nnb, 0.5) / nbar), np.log(rho * h ** 3 / (m * eta3)),
+    return np.stack([np.log(h / hbar), np.log(np.maximum(nnb, 0.5) / nbar), np.log(rho * h ** dim / (m * etaD)),
                      divv * dt, f4], axis=1)

@@ -15,9 +15,10 @@
  *   Eq. 6  (Sec. 2.2.1)  dv_a/dt = -sum_b m_b (P_a/rho_a^2 + P_b/rho_b^2 + Pi_ab) grad_a W_ab
  *                        with W_ab = W(|r_a - r_b|, h_ab), h_ab = (h_a + h_b)/2
  *   Eq. 7  (Sec. 2.2.1)  rho_a = sum_b m_b W_ab (density reconstructed, not evolved)
- *   Eq. 9  (Sec. 2.2.1)  h_a = C eta (m_a/rho_a)^(1/D)
- *   Sec. 2.1 (Tree topology): Morton (Z-order) keys with a leading 1 digit,
- *                        unique particle ids to resolve equal keys.
+ *   Eq. 9  (Sec. 2.2.1)  h_a = C eta (m_a/rho_a)^(1/D), D = 1 or 3
+ *   Sec. 2.1 (Tree topology): Morton (Z-order) and Hilbert keys with a
+ *                        leading 1 digit, unique particle ids to resolve
+ *                        equal keys.
  * Readings where the paper is silent (kernels, viscosity, iteration) are
  * stated at each function.
  */
@@ -50,28 +51,39 @@ typedef struct {
     double h_tol;      /* |dh|/h convergence threshold                     */
     int max_sweeps;    /* cap on density evaluations per particle          */
     double h_min, h_max;
+    int dim;           /* spatial dimension D: 1 (particles on the x axis) or 3 */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
 /* Smoothing kernels.  The paper lists several kernels (Sec. 2.1, Physics
  * Functionalities) without printing any; the three used here are the
- * standard published 3D forms with support radius 2h, q = r/h:
- *   M4 cubic spline (Monaghan 1992):  sigma = 1/pi,
- *       w = 1 - 3/2 q^2 + 3/4 q^3 (q<1),  1/4 (2-q)^3 (1<=q<2)
- *   Wendland C2 (Dehnen & Aly 2012):  sigma = 21/(16 pi), w = (1-q/2)^4 (1+2q)
- *   Wendland C4:                       sigma = 495/(256 pi),
- *       w = (1-q/2)^6 (1 + 3q + 35/12 q^2)
- * W(r,h) = sigma/h^3 w(q).  Derivatives by differentiating these by hand:
- *   dW/dr = sigma/h^4 w'(q),  dW/dh = -sigma/h^4 (3 w(q) + q w'(q)).        */
+ * standard published forms with support radius 2h, q = r/h, s = 1 - q/2:
+ *   M4 cubic spline (Monaghan 1992), the same w in every dimension:
+ *       w = 1 - 3/2 q^2 + 3/4 q^3 (q<1),  1/4 (2-q)^3 (1<=q<2);
+ *       sigma = 1/pi (D = 3), 2/3 (D = 1)
+ *   Wendland C2 (Dehnen & Aly 2012):  D = 3: sigma = 21/(16 pi), w = s^4 (1+2q)
+ *                                     D = 1: sigma = 5/8,        w = s^3 (1+3q/2)
+ *   Wendland C4:                      D = 3: sigma = 495/(256 pi),
+ *                                            w = s^6 (1 + 3q + 35/12 q^2)
+ *                                     D = 1: sigma = 3/4, w = s^5 (1 + 5q/2 + 2q^2)
+ * (the 1D Wendland functions are (1-x)^3 (1+3x) and (1-x)^5 (1+5x+8x^2) of
+ * x = r/(2h)).  W(r,h) = sigma/h^D w(q).  Derivatives by differentiating
+ * these by hand:
+ *   dW/dr = sigma/h^(D+1) w'(q),  dW/dh = -sigma/h^(D+1) (D w(q) + q w'(q)). */
 
-static double kern_sigma(int k)
+static double kern_sigma(int k, int dim)
 {
+    if (dim == 1) {
+        if (k == ORC_M4) return 2.0 / 3.0;
+        if (k == ORC_WC2) return 5.0 / 8.0;
+        return 3.0 / 4.0;
+    }
     if (k == ORC_M4) return 1.0 / ORC_PI;
     if (k == ORC_WC2) return 21.0 / (16.0 * ORC_PI);
     return 495.0 / (256.0 * ORC_PI);
 }
 
-static double kern_w(int k, double q)
+static double kern_w(int k, int dim, double q)
 {
     if (q >= 2.0) return 0.0;
     if (k == ORC_M4) {
@@ -80,6 +92,10 @@ static double kern_w(int k, double q)
         return 0.25 * t * t * t;
     }
     double s = 1.0 - 0.5 * q;
+    if (dim == 1) {
+        if (k == ORC_WC2) return s * s * s * (1.0 + 1.5 * q);
+        return s * s * s * s * s * (1.0 + 2.5 * q + 2.0 * q * q);
+    }
     if (k == ORC_WC2) {
         double s2 = s * s;
         return s2 * s2 * (1.0 + 2.0 * q);
@@ -89,7 +105,7 @@ static double kern_w(int k, double q)
 }
 
 /* derivative of w with respect to q */
-static double kern_dw(int k, double q)
+static double kern_dw(int k, int dim, double q)
 {
     if (q >= 2.0) return 0.0;
     if (k == ORC_M4) {
@@ -98,6 +114,16 @@ static double kern_dw(int k, double q)
         return -0.75 * t * t;
     }
     double s = 1.0 - 0.5 * q;
+    if (dim == 1) {
+        if (k == ORC_WC2) {
+            /* d/dq [s^3 (1 + 3q/2)] = -3/2 s^2 (1 + 3q/2) + 3/2 s^3 = -3 q s^2 */
+            return -3.0 * q * s * s;
+        }
+        /* d/dq [s^5 P] = s^4 (-5/2 P + s P'),  P = 1 + 5q/2 + 2 q^2 */
+        double P = 1.0 + 2.5 * q + 2.0 * q * q;
+        double dP = 2.5 + 4.0 * q;
+        return s * s * s * s * (-2.5 * P + s * dP);
+    }
     if (k == ORC_WC2) {
         /* d/dq [s^4 (1+2q)] = -2 s^3 (1+2q) + 2 s^4 = -5 q s^3 */
         return -5.0 * q * s * s * s;
@@ -109,32 +135,35 @@ static double kern_dw(int k, double q)
     return s5 * (-3.0 * P + s * dP);
 }
 
-double orc_W(int k, double r, double h)
+/* h^D for D = 1 or 3 */
+static double pow_dim(double h, int dim) { return dim == 1 ? h : h * h * h; }
+
+double orc_W(int k, int dim, double r, double h)
 {
     double q = r / h;
-    return kern_sigma(k) / (h * h * h) * kern_w(k, q);
+    return kern_sigma(k, dim) / pow_dim(h, dim) * kern_w(k, dim, q);
 }
 
-double orc_dWdr(int k, double r, double h)
+double orc_dWdr(int k, int dim, double r, double h)
 {
     double q = r / h;
-    return kern_sigma(k) / (h * h * h * h) * kern_dw(k, q);
+    return kern_sigma(k, dim) / (pow_dim(h, dim) * h) * kern_dw(k, dim, q);
 }
 
-double orc_dWdh(int k, double r, double h)
+double orc_dWdh(int k, int dim, double r, double h)
 {
     double q = r / h;
-    return -kern_sigma(k) / (h * h * h * h) * (3.0 * kern_w(k, q) + q * kern_dw(k, q));
+    return -kern_sigma(k, dim) / (pow_dim(h, dim) * h) * (dim * kern_w(k, dim, q) + q * kern_dw(k, dim, q));
 }
 
 /* vectorised wrappers for the tests */
-void orc_kernel_eval(int k, int64_t n, const double *r, const double *h,
+void orc_kernel_eval(int k, int dim, int64_t n, const double *r, const double *h,
                      double *W, double *dWdr, double *dWdh)
 {
     for (int64_t i = 0; i < n; ++i) {
-        if (W) W[i] = orc_W(k, r[i], h[i]);
-        if (dWdr) dWdr[i] = orc_dWdr(k, r[i], h[i]);
-        if (dWdh) dWdh[i] = orc_dWdh(k, r[i], h[i]);
+        if (W) W[i] = orc_W(k, dim, r[i], h[i]);
+        if (dWdr) dWdr[i] = orc_dWdr(k, dim, r[i], h[i]);
+        if (dWdh) dWdh[i] = orc_dWdh(k, dim, r[i], h[i]);
     }
 }
 
@@ -283,8 +312,8 @@ static void density_sum(const orc_params *p, int64_t n, const double *x, const d
         double r2 = (dx * dx + dy * dy) + dz * dz;
         if (!(r2 < thr)) continue;
         double r = sqrt(r2);
-        r_sum += m[b] * orc_W(p->kernel, r, h);
-        d_sum += m[b] * orc_dWdh(p->kernel, r, h);
+        r_sum += m[b] * orc_W(p->kernel, p->dim, r, h);
+        d_sum += m[b] * orc_dWdh(p->kernel, p->dim, r, h);
         if (b != a) ++cnt;
     }
     *rho = r_sum;
@@ -292,9 +321,9 @@ static void density_sum(const orc_params *p, int64_t n, const double *x, const d
     *nnb = cnt;
 }
 
-/* h-rho fixed point of Eq. 9 with C = 1, D = 3: h = eta (m/rho)^(1/3).
+/* h-rho fixed point of Eq. 9 with C = 1: h = eta (m/rho)^(1/D), D = 1 or 3.
  * The paper does not say how the fixed point is solved; reading: Newton on
- *   f(h)  = m eta^3 / h^3 - rho(h),   f'(h) = -3 m eta^3 / h^4 - drho/dh,
+ *   f(h)  = m eta^D / h^D - rho(h),   f'(h) = -D m eta^D / h^(D+1) - drho/dh,
  * one density evaluation per sweep, with a bracket [lo, hi] of evaluated
  * smoothing lengths kept from the sign of f (f > 0 means the root lies above
  * h; the bracket starts as [0, inf)).  A Newton step outside the closed
@@ -312,7 +341,7 @@ int orc_density(const orc_params *p, int64_t n, const double *x, const double *y
                 double *h_out, double *rho_out, double *drho_out, int32_t *nnb_out,
                 int32_t *sweeps_out, int32_t *flags_out, int64_t *pairs_out)
 {
-    const double eta3 = p->eta * p->eta * p->eta;
+    const double etaD = p->dim == 1 ? p->eta : p->eta * p->eta * p->eta;   /* eta^D */
     int worst = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(| : worst)
     for (int64_t t = 0; t < nt; ++t) {
@@ -328,10 +357,10 @@ int orc_density(const orc_params *p, int64_t n, const double *x, const double *y
             pairs += cnt;
             if (final_eval) { flags |= ORC_DONE; break; }
             double ma = m[a];
-            double f = ma * eta3 / (h * h * h) - rho;
+            double f = ma * etaD / pow_dim(h, p->dim) - rho;
             if (f == 0.0) { flags |= ORC_DONE; break; }
             if (sweeps >= p->max_sweeps) { flags |= ORC_NOT_CONVERGED; break; }
-            double fp = -3.0 * ma * eta3 / (h * h * h * h) - drho;
+            double fp = -p->dim * ma * etaD / (pow_dim(h, p->dim) * h) - drho;
             if (f > 0.0) { if (h > lo) lo = h; }
             else { if (h < hi) hi = h; }
             double a_lo = 0.5 * h > lo ? 0.5 * h : lo;
@@ -456,12 +485,12 @@ void orc_forces(const orc_params *p, int64_t n, const double *x, const double *y
             double vdotr = (vabx * dx + vaby * dy) + vabz * dz;
             if (in_d) {
                 /* v_ab . grad_a W(r, h_a) */
-                dv += m[b] * orc_dWdr(p->kernel, r, h[a]) / r * vdotr;
+                dv += m[b] * orc_dWdr(p->kernel, p->dim, r, h[a]) / r * vdotr;
             }
             if (!in_f) continue;
             ++pairs;
             double hab = 0.5 * hs;
-            double g = orc_dWdr(p->kernel, r, hab) / r;
+            double g = orc_dWdr(p->kernel, p->dim, r, hab) / r;
             double gx = g * dx, gy = g * dy, gz = g * dz;
             double Pi = 0.0;
             if (vdotr < 0.0) {
@@ -524,7 +553,7 @@ void orc_energy_rate(const orc_params *p, int64_t n, const double *x, const doub
             if (!(r2 < hs * hs)) continue;
             double r = sqrt(r2);
             double hab = 0.5 * hs;
-            double g = orc_dWdr(p->kernel, r, hab) / r;
+            double g = orc_dWdr(p->kernel, p->dim, r, hab) / r;
             double gx = g * dx, gy = g * dy, gz = g * dz;
             double vabx = vx[a] - vx[b], vaby = vy[a] - vy[b], vabz = vz[a] - vz[b];
             double vdotr = (vabx * dx + vaby * dy) + vabz * dz;

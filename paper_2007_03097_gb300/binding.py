@@ -44,7 +44,8 @@ class sph_params(_c.Structure):
                 ("max_sweeps", _c.c_int32), ("leaf_size", _c.c_int32), ("h_min", _c.c_double),
                 ("h_max", _c.c_double), ("skin", _c.c_double), ("rho_ref", _c.c_double),
                 ("nb_capacity", _c.c_int64), ("hnet_lr", _c.c_double), ("hnet_batch", _c.c_int32),
-                ("hnet_iters", _c.c_int32), ("energy", _c.c_int32), ("curve", _c.c_int32)]
+                ("hnet_iters", _c.c_int32), ("energy", _c.c_int32), ("curve", _c.c_int32),
+                ("dim", _c.c_int32), ("pad", _c.c_int32)]
 
 
 _FIELDS = ["vx", "vy", "vz", "m", "h", "u", "hprev", "rho", "omega", "P", "c", "ax", "ay", "az", "dudt",
@@ -168,6 +169,7 @@ def make_params(p: dict) -> sph_params:
     q.energy = int(p.get("energy", SPH_ENERGY_INTERNAL))
     curve = p.get("curve", SPH_CURVE_MORTON)
     q.curve = int({"morton": SPH_CURVE_MORTON, "hilbert": SPH_CURVE_HILBERT}.get(curve, curve))
+    q.dim = int(p.get("dim", 3))
     return q
 
 

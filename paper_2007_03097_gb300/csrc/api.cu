@@ -43,6 +43,7 @@ int check_params(const sph_params *q, std::string &why)
     if (q->nb_capacity < 0) { why = "nb_capacity must be >= 0"; return SPH_ERR_ARG; }
     if (q->energy != SPH_ENERGY_INTERNAL && q->energy != SPH_ENERGY_TOTAL) { why = "energy must be an sph_energy"; return SPH_ERR_ARG; }
     if (q->curve != SPH_CURVE_MORTON && q->curve != SPH_CURVE_HILBERT) { why = "curve must be an sph_curve"; return SPH_ERR_ARG; }
+    if (q->dim != 1 && q->dim != 3) { why = "dim must be 1 or 3"; return SPH_ERR_ARG; }
     if (!(q->hnet_lr > 0.0) || q->hnet_batch < 1 || q->hnet_iters < 0 || q->hnet_iters > 10000) {
         why = "need hnet_lr > 0, hnet_batch >= 1, 0 <= hnet_iters <= 10000";
         return SPH_ERR_ARG;
@@ -134,6 +135,8 @@ int allocate(sph_ctx *c, int64_t N)
     SPH_TRY(alloc(c, &c->group_ubound, N));
     SPH_TRY(alloc(c, &c->union_off, N + 1));
     SPH_TRY(alloc(c, &c->group_union, N));
+    SPH_TRY(alloc(c, &c->group_img, N));
+    SPH_CUDA(cudaMemset(c->group_img, 0, sizeof(int32_t) * (size_t)N));
     SPH_TRY(alloc(c, &c->group_mark, N));
     SPH_CUDA(cudaMemset(c->group_mark, 0, sizeof(int32_t) * (size_t)N));
     c->kept_cap = 8 * N;
@@ -190,7 +193,7 @@ void release(sph_ctx *c)
                     c->group_lo, c->group_hi, c->node_child, c->node_parent, c->leaf_parent, c->node_visit,
                     c->node_lo, c->node_hi, c->srcA, c->srcB,
                     c->srcC, c->srcD, c->srcE, c->srcF, c->nbl, c->group_width, c->uni, c->group_ubound,
-                    c->union_off, c->group_union, c->group_mark, c->kept, c->kept_count,
+                    c->union_off, c->group_union, c->group_img, c->group_mark, c->kept, c->kept_count,
                     c->group_off, c->it_lo, c->it_hi, c->it_flags, c->it_sweeps, c->cov, c->act_groups[0],
                     c->act_groups[1], c->vpx, c->vpy, c->vpz, c->upred, c->hold, c->hseed, c->hstart, c->gbuf,
                     c->scan_tmp, c->red, c->dcnt, c->hn_master, c->hn_bf16, c->hn_m, c->hn_v, c->hn_grad,

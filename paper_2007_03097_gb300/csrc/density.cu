@@ -22,6 +22,7 @@
 // without fused multiply-add, so the neighbour sets are those of plain FP64.
 // Groups whose particles are all done drop out of the next sweep.
 #include <algorithm>
+#include <type_traits>
 
 #include "dfloat.cuh"
 #include "sph_internal.cuh"
@@ -46,6 +47,7 @@ struct DensArgs {
     const uint32_t *uni;           // group source unions
     const int64_t *uoff;
     const int32_t *group_union;    // union size per group
+    const int32_t *group_img;      // 1: the group's sources include periodic images
     const float4 *group_lo, *group_hi;
     int src_cap;                   // union sources staged in shared memory per warp (mixed)
     const double *x, *y, *z;
@@ -57,9 +59,10 @@ struct DensArgs {
     double *it_lo, *it_hi;
     int32_t *it_flags, *it_sweeps;
     const float *cov;
-    int kernel, periodic, fixed_h, max_sweeps;
-    double L, eta3, h_tol, h_min, h_max;
-    df Ld, sig_d, eta3_d, hmin_d, hmax_d;   // the same constants as double-floats
+    int kernel, periodic, fixed_h, max_sweeps;   // kernel: the kernel shape (kern_shape)
+    int dim;                                     // D = 1 or 3
+    double L, etaD, h_tol, h_min, h_max;         // etaD = eta^D
+    df Ld, sig_d, etaD_d, hmin_d, hmax_d;        // the same constants as double-floats
     DevCounters *cnt;
 };
 
@@ -68,7 +71,7 @@ struct DensArgs {
 // per chunk) as FP32 coordinates relative to the group-box centre, with the
 // periodic shift folded in, and the mass; each lane then reads its
 // neighbours there by their local index.
-template <typename T>
+template <typename T, int KS>
 __device__ __forceinline__ void density_group(const DensArgs &a, const int g, const int lane, float4 *s_src)
 {
     const int gb = a.group_begin[g], ge = a.group_begin[g + 1];
@@ -88,6 +91,7 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
         atomicAdd(&a.cnt->n_uncovered, 1);
     }
     const T hinv = T(1) / h;
+    const T Dt = T(a.dim);
     const int64_t off = a.goff[g];
     int width = a.gwidth[g];
     if (off + 32 * (int64_t)width > a.cap) width = 0;    // never read past the lists
@@ -104,6 +108,7 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
         const float hf = (float)h;
         const float thr = __fmul_rn(__fmul_rn(4.f, hf), hf);
         const int U = a.group_union[g];
+        const bool img = a.periodic && a.group_img[g];   // else every source's direct image is the nearest
         const uint32_t *Ug = a.uni + a.uoff[g];
         const uint16_t *l = a.nbl + off + lane;
         for (int c0 = 0; c0 < U; c0 += a.src_cap) {
@@ -113,10 +118,10 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                 const uint32_t b = __ldg(Ug + c0 + t);
                 const float4 qa = __ldg(a.srcA + b), qb = __ldg(a.srcB + b);
                 float rx = qa.x - gcx, ry = qa.z - gcy, rz = qb.x - gcz;
-                if (a.periodic) {              // the image nearest the group
-                    rx -= L * rintf(rx * invL);
-                    ry -= L * rintf(ry * invL);
-                    rz -= L * rintf(rz * invL);
+                if (img) {                     // the image nearest the group
+                    rx = wrap_diff(qa.x, gcx, L, invL);
+                    ry = wrap_diff(qa.z, gcy, L, invL);
+                    rz = wrap_diff(qb.x, gcz, L, invL);
                 }
                 s_src[t] = make_float4(rx + qa.y, ry + qa.w, rz + qb.y, qb.z);
             }
@@ -147,10 +152,10 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                     if (!(r2 < thr)) continue;
                     const T qq = (T)(r2 > 0.f ? r2 * rsqrtf(r2) : 0.f) * hinv;   // r within 2 ulp
                     T w, dw;
-                    kern_wdw<T>(a.kernel, qq, w, dw);
+                    kern_wdw<T>(KS, qq, w, dw);        // the kernel form fixed at compile time
                     const T mb = (T)q.w;
                     sum_w += mb * w;
-                    sum_dh += mb * (T(3) * w + qq * dw);
+                    sum_dh += mb * (Dt * w + qq * dw);
                     ++cnt;
                     }
                 }
@@ -162,12 +167,12 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
     if (active) {
         const T ma = mp[i];
         sum_w += ma;                    // self term, w(0) = 1 for every kernel
-        sum_dh += T(3) * ma;            // 3 w(0) + 0 w'(0)
+        sum_dh += Dt * ma;              // D w(0) + 0 w'(0)
         const T sig = kern_sigma<T>(a.kernel);
-        const T h3i = hinv * hinv * hinv;
-        const T rho = sig * h3i * sum_w;
-        const T drho = -sig * h3i * hinv * sum_dh;
-        const T meta3 = ma * (T)a.eta3;
+        const T hDi = inv_pow_dim(hinv, a.dim);
+        const T rho = sig * hDi * sum_w;
+        const T drho = -sig * hDi * hinv * sum_dh;
+        const T metaD = ma * (T)a.etaD;
         const int sweeps = a.it_sweeps[i] + 1;
         a.it_sweeps[i] = sweeps;
         bool done = false;
@@ -175,14 +180,14 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
         if (flags & IT_FINAL) {
             done = true;
         } else {
-            const T f = meta3 * h3i - rho;
+            const T f = metaD * hDi - rho;
             if (f == T(0)) {
                 done = true;
             } else if (sweeps >= a.max_sweeps) {
                 done = true;
                 flags |= IT_NOT_CONV;
             } else {
-                const T fp = T(-3) * meta3 * h3i * hinv - drho;
+                const T fp = -Dt * metaD * hDi * hinv - drho;
                 double lo = a.it_lo[i], hi = a.it_hi[i];
                 if (f > T(0)) { if ((double)h > lo) lo = (double)h; }
                 else { if ((double)h < hi) hi = (double)h; }
@@ -260,11 +265,13 @@ struct DfTarget {
     df hinv;
     float thr_hi, thr_lo;          // FP32 band around 4 h^2
     int64_t i;
+    int img;                       // periodic images among the group's sources
 };
 
-__device__ __forceinline__ DfTarget df_target(const DensArgs &a, int64_t i, double hd, df h)
+__device__ __forceinline__ DfTarget df_target(const DensArgs &a, int64_t i, double hd, df h, int g)
 {
     DfTarget t;
+    t.img = a.periodic && a.group_img[g];
     t.A = a.srcA[i];
     t.Bz = a.srcB[i];
     t.hd = hd;
@@ -280,19 +287,14 @@ __device__ __forceinline__ void df_pair(const DensArgs &a, const DfTarget &t, ui
                                         const float4 &Q, df &sw, df &sd, int &cnt, int &band)
 {
     const float Lf = (float)a.L, half = 0.5f * Lf, guard = 0.45f * Lf;
-    float dxf = (t.A.x - P.x) + (t.A.y - P.y);
-    float dyf = (t.A.z - P.z) + (t.A.w - P.w);
-    float dzf = (t.Bz.x - Q.x) + (t.Bz.y - Q.y);
-    int wx = 0, wy = 0, wz = 0;
-    if (a.periodic) {
-        if (dxf > half) { dxf -= Lf; wx = -1; } else if (dxf < -half) { dxf += Lf; wx = 1; }
-        if (dyf > half) { dyf -= Lf; wy = -1; } else if (dyf < -half) { dyf += Lf; wy = 1; }
-        if (dzf > half) { dzf -= Lf; wz = -1; } else if (dzf < -half) { dzf += Lf; wz = 1; }
-    }
+    int wx, wy, wz;
+    const float dxf = sep_fw(t.A.x, t.A.y, P.x, P.y, t.img, Lf, half, wx);
+    const float dyf = sep_fw(t.A.z, t.A.w, P.z, P.w, t.img, Lf, half, wy);
+    const float dzf = sep_fw(t.Bz.x, t.Bz.y, Q.x, Q.y, t.img, Lf, half, wz);
     const float r2f = (dxf * dxf + dyf * dyf) + dzf * dzf;
     if (r2f > t.thr_hi) return;
     if (r2f >= t.thr_lo) ++band;
-    if (r2f >= t.thr_lo || (a.periodic && fmaxf(fmaxf(fabsf(dxf), fabsf(dyf)), fabsf(dzf)) > guard)) {
+    if (r2f >= t.thr_lo || (t.img && fmaxf(fmaxf(fabsf(dxf), fabsf(dyf)), fabsf(dzf)) > guard)) {
         // knife edge: the exact FP64 decision of the plain definition
         const double L = a.L, hl = 0.5 * a.L;
         const double dx = sep_d(a.x[t.i], a.x[b], a.periodic, L, hl);
@@ -322,12 +324,12 @@ __device__ __forceinline__ bool df_finalize(const DensArgs &a, const DfTarget &t
     const df hinv = t.hinv;
     const df ma = df{t.Bz.z, t.Bz.w};
     sw = df_add(df_norm(sw), ma);                   // self term, w(0) = 1 for every kernel
-    sd = df_add(df_norm(sd), df_mul_f(ma, 3.f));    // 3 w(0) + 0 w'(0)
-    const df h3i = df_mul(df_sqr(hinv), hinv);
-    const df sh3 = df_mul(a.sig_d, h3i);
-    const df rho = df_mul(sh3, sw);
-    const df drho = df_neg(df_mul(df_mul(sh3, hinv), sd));
-    const df meta3 = df_mul(ma, a.eta3_d);
+    sd = df_add(df_norm(sd), df_mul_f(ma, (float)a.dim));    // D w(0) + 0 w'(0)
+    const df hDi = a.dim == 1 ? hinv : df_mul(df_sqr(hinv), hinv);
+    const df shD = df_mul(a.sig_d, hDi);
+    const df rho = df_mul(shD, sw);
+    const df drho = df_neg(df_mul(df_mul(shD, hinv), sd));
+    const df metaD = df_mul(ma, a.etaD_d);
     const int sweeps = a.it_sweeps[i] + 1;
     a.it_sweeps[i] = sweeps;
     bool done = false;
@@ -335,15 +337,15 @@ __device__ __forceinline__ bool df_finalize(const DensArgs &a, const DfTarget &t
     if (flags & IT_FINAL) {
         done = true;
     } else {
-        const df mh3 = df_mul(meta3, h3i);
-        const df f = df_sub(mh3, rho);
+        const df mhD = df_mul(metaD, hDi);
+        const df f = df_sub(mhD, rho);
         if (f.hi == 0.f) {
             done = true;
         } else if (sweeps >= a.max_sweeps) {
             done = true;
             flags |= IT_NOT_CONV;
         } else {
-            const df fp = df_sub(df_mul_f(df_mul(mh3, hinv), -3.f), drho);
+            const df fp = df_sub(df_mul_f(df_mul(mhD, hinv), -(float)a.dim), drho);
             df lo = df_ld(a.it_lo + i), hi = df_ld(a.it_hi + i);
             if (f.hi > 0.f) { if (df_lt(lo, h)) lo = h; }
             else { if (df_lt(h, hi)) hi = h; }
@@ -415,7 +417,7 @@ __device__ __forceinline__ void density_group_df(const DensArgs &a, const int g,
         active = false;
         atomicAdd(&a.cnt->n_uncovered, 1);
     }
-    const DfTarget t = df_target(a, i, hd, h);
+    const DfTarget t = df_target(a, i, hd, h, g);
     const int64_t off = a.goff[g];
     int width = a.gwidth[g];
     if (off + 32 * (int64_t)width > a.cap) width = 0;    // never read past the lists
@@ -472,7 +474,7 @@ __global__ void __launch_bounds__(DW * 32) k_density_sparse(DensArgs a)
             if (lane == 0) atomicAdd(&a.cnt->n_uncovered, 1);
             still = true;
         } else {
-            const DfTarget t = df_target(a, i, hd, h);
+            const DfTarget t = df_target(a, i, hd, h, g);
             const int64_t off = a.goff[g];
             int width = a.gwidth[g];
             if (off + 32 * (int64_t)width > a.cap) width = 0;
@@ -510,7 +512,7 @@ __global__ void __launch_bounds__(DW * 32) k_density_sparse(DensArgs a)
 // sweeps can be queued without a host round trip.  The grid is sized to the
 // resident blocks; each warp claims its next group from a counter, so groups
 // of unequal list widths balance across the SMs.
-template <typename T, bool FP64POS>
+template <typename T, bool FP64POS, int KS>
 __global__ void __launch_bounds__(DW * 32) k_density(DensArgs a)
 {
     extern __shared__ float4 s_dyn[];
@@ -525,7 +527,7 @@ __global__ void __launch_bounds__(DW * 32) k_density(DensArgs a)
         gi = __shfl_sync(0xffffffffu, gi, 0);
         if (gi >= n_act) break;
         if constexpr (FP64POS) density_group_df(a, a.act[gi], lane);
-        else density_group<T>(a, a.act[gi], lane, s_src);
+        else density_group<T, KS>(a, a.act[gi], lane, s_src);
     }
 }
 
@@ -598,8 +600,8 @@ unsigned resident_blocks(bool fp64pos)
     if (c == 0) {
         int nb = 0;
         const cudaError_t e = fp64pos
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_density<T, true>, DW * 32, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_density<T, false>, DW * 32,
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_density<double, true, 0>, DW * 32, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_density<float, false, 1>, DW * 32,
                                                             sizeof(float4) * DW * SRC_CAP);
         c = (e == cudaSuccess && nb > 0) ? nb : 8;
     }
@@ -630,6 +632,7 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
     a.uni = ctx->uni;
     a.uoff = ctx->union_off;
     a.group_union = ctx->group_union;
+    a.group_img = ctx->group_img;
     a.group_mark = ctx->group_mark;
     a.group_lo = ctx->group_lo;
     a.group_hi = ctx->group_hi;
@@ -640,13 +643,13 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
     a.h = p->h; a.m = p->m; a.rho = p->rho; a.omega = p->omega; a.nnb = p->nnb;
     a.it_lo = ctx->it_lo; a.it_hi = ctx->it_hi; a.it_flags = ctx->it_flags; a.it_sweeps = ctx->it_sweeps;
     a.cov = ctx->cov;
-    a.kernel = q.kernel; a.periodic = q.periodic; a.fixed_h = q.fixed_h; a.max_sweeps = q.max_sweeps;
+    a.kernel = kern_shape(q.kernel, q.dim); a.dim = q.dim;
+    a.periodic = q.periodic; a.fixed_h = q.fixed_h; a.max_sweeps = q.max_sweeps;
     a.L = ctx->dom[3];
-    a.eta3 = q.eta * q.eta * q.eta;
+    a.etaD = q.dim == 1 ? q.eta : q.eta * q.eta * q.eta;
     a.h_tol = q.h_tol; a.h_min = q.h_min; a.h_max = q.h_max;
-    const double sig = q.kernel == SPH_KERNEL_M4 ? 1.0 / SPH_PI
-                     : q.kernel == SPH_KERNEL_WC2 ? 21.0 / (16.0 * SPH_PI) : 495.0 / (256.0 * SPH_PI);
-    a.Ld = df_host(a.L); a.sig_d = df_host(sig); a.eta3_d = df_host(a.eta3);
+    const double sig = kern_sigma<double>(a.kernel);
+    a.Ld = df_host(a.L); a.sig_d = df_host(sig); a.etaD_d = df_host(a.etaD);
     a.hmin_d = df_host(q.h_min); a.hmax_d = df_host(q.h_max);
     a.cnt = ctx->dcnt;
     // sweeps are queued in batches without a host round trip: each reads the
@@ -667,12 +670,19 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
             a.act_next_count = &ctx->dcnt->act_count[cur ^ 1];
             a.work = &ctx->dcnt->work[cur];
             if (launched < 64) SPH_CUDA(cudaEventRecord(ctx->kev[2 * launched], s));
-            if (ctx->fp64) {
-                k_density<T, true><<<grid, DW * 32, 0, s>>>(a);
+            if constexpr (std::is_same<T, double>::value) {
+                k_density<double, true, 0><<<grid, DW * 32, 0, s>>>(a);
                 SPH_CHECK_LAUNCH();
                 k_density_sparse<<<(unsigned)ctx->num_sms * 8u, DW * 32, 0, s>>>(a);
             } else {
-                k_density<T, false><<<grid, DW * 32, smem, s>>>(a);
+                // one instantiation per kernel form keeps the hot loop small
+                switch (a.kernel) {
+                case 1: k_density<float, false, 1><<<grid, DW * 32, smem, s>>>(a); break;
+                case 2: k_density<float, false, 2><<<grid, DW * 32, smem, s>>>(a); break;
+                case 4: k_density<float, false, 4><<<grid, DW * 32, smem, s>>>(a); break;
+                case 5: k_density<float, false, 5><<<grid, DW * 32, smem, s>>>(a); break;
+                default: k_density<float, false, 0><<<grid, DW * 32, smem, s>>>(a); break;   // M4, either D
+                }
             }
             SPH_CHECK_LAUNCH();
             if (launched < 64) SPH_CUDA(cudaEventRecord(ctx->kev[2 * launched + 1], s));

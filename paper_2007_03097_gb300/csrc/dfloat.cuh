@@ -202,11 +202,44 @@ __device__ __forceinline__ df df_sep(float ah, float al, float bh, float bl, int
     return d;
 }
 
-// Smoothing kernels in double-float (the forms of sph_internal.cuh, q = r/h):
-// w(q) and g3(q) = 3 w(q) + q w'(q), or w'(q) alone.
+// Smoothing kernels in double-float (the forms and shapes of
+// sph_internal.cuh, q = r/h): w(q) and g(q) = D w(q) + q w'(q) (shapes 0-2:
+// D = 3; shapes 3-5: D = 1), or w'(q) alone.
 __device__ __forceinline__ void df_kern_w_g3(int k, df q, df &w, df &g3)
 {
     const df one = df{1.f, 0.f};
+    if (k >= 3) {
+        const df s = df_add_f(df_scale(q, -0.5f), 1.f);
+        const df q2 = df_sqr(q);
+        if (k == 3) {                                          // M4, D = 1
+            if (q.hi < 1.f) {
+                // w = 1 - 1.5 q^2 + 0.75 q^3 ; g = 1 - 4.5 q^2 + 3 q^3
+                const df q3 = df_mul(q2, q);
+                w = df_add(df_add(one, df_mul_f(q2, -1.5f)), df_mul_f(q3, 0.75f));
+                g3 = df_add(df_add(one, df_mul_f(q2, -4.5f)), df_mul_f(q3, 3.f));
+            } else {
+                // t = 2 - q ; w = t^3 / 4 ; g = t^2 (2 - 4q) / 4
+                const df t = df_add_f(df_neg(q), 2.f);
+                const df t2 = df_sqr(t);
+                w = df_scale(df_mul(t2, t), 0.25f);
+                g3 = df_scale(df_mul(t2, df_add_f(df_scale(q, -4.f), 2.f)), 0.25f);
+            }
+        } else if (k == 4) {                                   // Wendland C2, D = 1
+            // w = s^3 (1 + 1.5 q) ; g = s^2 (s (1 + 1.5 q) - 3 q^2)
+            const df s2 = df_sqr(s);
+            const df p = df_add_f(df_mul_f(q, 1.5f), 1.f);
+            w = df_mul(df_mul(s2, s), p);
+            g3 = df_mul(s2, df_sub(df_mul(s, p), df_mul_f(q2, 3.f)));
+        } else {                                               // Wendland C4, D = 1
+            // P = 1 + 2.5 q + 2 q^2 ; w = s^5 P ; g = s^4 (s P - 3.5 q^2 (1 + 2q))
+            const df s2 = df_sqr(s);
+            const df s4 = df_sqr(s2);
+            const df P = df_add(df_add_f(df_mul_f(q, 2.5f), 1.f), df_scale(q2, 2.f));
+            w = df_mul(df_mul(s4, s), P);
+            g3 = df_mul(s4, df_sub(df_mul(s, P), df_mul_f(df_mul(q2, df_add_f(df_scale(q, 2.f), 1.f)), 3.5f)));
+        }
+        return;
+    }
     if (k == 0) {                                              // M4
         const df q2 = df_sqr(q);
         if (q.hi < 1.f) {
@@ -247,7 +280,13 @@ __device__ __forceinline__ void df_kern_w_g3(int k, df q, df &w, df &g3)
 
 __device__ __forceinline__ df df_kern_dw(int k, df q)
 {
-    if (k == 0) {
+    if (k >= 4) {
+        const df s = df_add_f(df_scale(q, -0.5f), 1.f);
+        const df s2 = df_sqr(s);
+        if (k == 4) return df_mul_f(df_mul(q, s2), -3.f);                       // -3 q s^2
+        return df_mul_f(df_mul(df_mul(q, df_add_f(df_scale(q, 2.f), 1.f)), df_sqr(s2)), -3.5f);  // -3.5 q (1 + 2q) s^4
+    }
+    if (k == 0 || k == 3) {
         if (q.hi < 1.f) return df_mul(q, df_add_f(df_mul_f(q, 2.25f), -3.f));    // q (-3 + 2.25 q)
         const df t = df_add_f(df_neg(q), 2.f);
         return df_mul_f(df_sqr(t), -0.75f);                                      // -0.75 (2 - q)^2

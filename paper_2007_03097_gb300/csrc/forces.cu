@@ -27,13 +27,15 @@ struct ForceArgs {
     int64_t cap;
     const uint32_t *uni;           // group source unions
     const int64_t *uoff;
+    const int32_t *group_img;      // 1: the group's sources include periodic images
     int n_groups;
     const double *x, *y, *z;
     const float4 *srcA, *srcB, *srcC, *srcD, *srcE, *srcF;
     const void *vx, *vy, *vz, *m, *h, *rho, *c;
     void *ax, *ay, *az, *dudt, *divv, *vsig;
-    int kernel, periodic;
-    int thermo;                       // 1: dudt receives de/dt of the thermokinetic formulation
+    int kernel, periodic;          // kernel: the kernel shape (kern_shape)
+    int dim;                       // D = 1 or 3: grad W = sigma / h^(D+1) w'(q) r_ab / r
+    int thermo;                    // 1: dudt receives de/dt of the thermokinetic formulation
     double L, alpha, beta, eps;
     df Ld, sig_d, alpha_d, beta_d, eps_d;   // the same constants as double-floats
     DevCounters *cnt;
@@ -41,6 +43,7 @@ struct ForceArgs {
 
 // SPH_MIXED force pass in FP32: sources packed as A {xh, xl, yh, yl},
 // B {zh, zl, m, -}, C {vx, vy, vz, h}, D {rho, P/rho^2, c, -}.
+template <int KS>
 __global__ void __launch_bounds__(FW * 32) k_forces_f32(ForceArgs a)
 {
     const int lane = threadIdx.x & 31;
@@ -53,9 +56,11 @@ __global__ void __launch_bounds__(FW * 32) k_forces_f32(ForceArgs a)
     const float ha = C.w, rhoa = D.x, pra = D.y, ca = D.z;
     const float hainv = 1.f / ha;
     const float sig = kern_sigma<float>(a.kernel);
+    const float sig_hg = sig * inv_pow_dim(hainv, a.dim) * hainv;     // sigma / h_a^(D+1)
     const float alpha = (float)a.alpha, beta = (float)a.beta, eps = (float)a.eps;
     const int64_t off = a.goff[g];
     const uint32_t *U = a.uni + a.uoff[g];
+    const int img = a.periodic && a.group_img[g];   // else every source's direct image is the nearest
     int width = tgt ? a.gwidth[g] : 0;
     if (off + 32 * (int64_t)width > a.cap) width = 0;    // never read past the lists
     const float Lf = (float)a.L, half = 0.5f * Lf;
@@ -76,9 +81,9 @@ __global__ void __launch_bounds__(FW * 32) k_forces_f32(ForceArgs a)
         e2 = entry(k + 2);
         if (b == SPH_SENTINEL) continue;
         const float4 P = a.srcA[b], Q = a.srcB[b], Cb = a.srcC[b];
-        const float dx = sep_f(A.x, A.y, P.x, P.y, a.periodic, Lf, half);
-        const float dy = sep_f(A.z, A.w, P.z, P.w, a.periodic, Lf, half);
-        const float dz = sep_f(Bz.x, Bz.y, Q.x, Q.y, a.periodic, Lf, half);
+        const float dx = sep_f(A.x, A.y, P.x, P.y, img, Lf, half);
+        const float dy = sep_f(A.z, A.w, P.z, P.w, img, Lf, half);
+        const float dz = sep_f(Bz.x, Bz.y, Q.x, Q.y, img, Lf, half);
         const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
         const float hb = Cb.w;
         const float hs = __fadd_rn(ha, hb);
@@ -93,9 +98,8 @@ __global__ void __launch_bounds__(FW * 32) k_forces_f32(ForceArgs a)
         const float mb = Q.z;
         if (in_d) {
             float w, dwq;
-            kern_wdw<float>(a.kernel, r * hainv, w, dwq);
-            const float h2 = hainv * hainv;
-            dv += mb * (sig * h2 * h2 * dwq) * rinv * vdotr;
+            kern_wdw<float>(KS, r * hainv, w, dwq);      // the kernel form fixed at compile time
+            dv += mb * (sig_hg * dwq) * rinv * vdotr;
         }
         if (in_f) {
             // approximate reciprocals (within 2 ulp): the FP32 pass is held
@@ -103,9 +107,9 @@ __global__ void __launch_bounds__(FW * 32) k_forces_f32(ForceArgs a)
             const float hab = 0.5f * hs;
             const float habinv = __fdividef(1.f, hab);
             float w, dwq;
-            kern_wdw<float>(a.kernel, r * habinv, w, dwq);
+            kern_wdw<float>(KS, r * habinv, w, dwq);
             const float h2 = habinv * habinv;
-            const float gr = sig * h2 * h2 * dwq * rinv;          // grad_a W = gr * r_ab
+            const float gr = sig * (a.dim == 1 ? h2 : h2 * h2) * dwq * rinv;   // grad_a W = gr * r_ab
             float Pi = 0.f;
             if (vdotr < 0.f) {
                 const float mu = __fdividef(hab * vdotr, r2 + eps * hab * hab);
@@ -172,6 +176,7 @@ __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
     const double *h64 = (const double *)a.h;
     const int64_t off = a.goff[g];
     const uint32_t *U = a.uni + a.uoff[g];
+    const int img = a.periodic && a.group_img[g];   // else every source's direct image is the nearest
     int width = tgt ? a.gwidth[g] : 0;
     if (off + 32 * (int64_t)width > a.cap) width = 0;
 
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
     const df Ld = a.Ld, sig = a.sig_d;
     const df hainv = df_rcp(ha);
     const df hai2 = df_sqr(hainv);
-    const df sig_hai4 = df_mul(sig, df_sqr(hai2));
+    const df sig_hai4 = df_mul(sig, a.dim == 1 ? hai2 : df_sqr(hai2));   // sigma / h_a^(D+1)
     const df vxa = df{C.x, C.y}, vya = df{C.z, C.w}, vza = df{D.x, D.y};
     const df rhoa = df{E.x, E.y}, pra = df{E.z, E.w}, ca = df{F.x, F.y};
     const df alpha = a.alpha_d, beta = a.beta_d, eps = a.eps_d;
@@ -204,15 +209,10 @@ __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
         e2 = entry(k + 2);
         if (b == SPH_SENTINEL) continue;
         const float4 P = a.srcA[b], Q = a.srcB[b], Db = a.srcD[b];
-        float dxf = (A.x - P.x) + (A.y - P.y);
-        float dyf = (A.z - P.z) + (A.w - P.w);
-        float dzf = (Bz.x - Q.x) + (Bz.y - Q.y);
-        int wx = 0, wy = 0, wz = 0;
-        if (a.periodic) {
-            if (dxf > half) { dxf -= Lf; wx = -1; } else if (dxf < -half) { dxf += Lf; wx = 1; }
-            if (dyf > half) { dyf -= Lf; wy = -1; } else if (dyf < -half) { dyf += Lf; wy = 1; }
-            if (dzf > half) { dzf -= Lf; wz = -1; } else if (dzf < -half) { dzf += Lf; wz = 1; }
-        }
+        int wx, wy, wz;
+        const float dxf = sep_fw(A.x, A.y, P.x, P.y, img, Lf, half, wx);
+        const float dyf = sep_fw(A.z, A.w, P.z, P.w, img, Lf, half, wy);
+        const float dzf = sep_fw(Bz.x, Bz.y, Q.x, Q.y, img, Lf, half, wz);
         const float r2f = (dxf * dxf + dyf * dyf) + dzf * dzf;
         const float hsf = D.z + Db.z;
         const float thf = hsf * hsf;
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
         if (out_d && out_f) continue;
         bool in_d = r2f < thr_lo, in_f = r2f < thf * (1.f - 1e-5f);
         const bool edge = (!in_d && !out_d) || (!in_f && !out_f) ||
-                          (a.periodic && fmaxf(fmaxf(fabsf(dxf), fabsf(dyf)), fabsf(dzf)) > guard);
+                          (img && fmaxf(fmaxf(fabsf(dxf), fabsf(dyf)), fabsf(dzf)) > guard);
         if (edge) {
             // knife edge: the exact FP64 decisions of the plain definition
             const double L = a.L, hl = 0.5 * a.L;
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
             const df habinv = df_rcp_fast(hab);
             const df dwq = df_kern_dw(a.kernel, df_mul(r, habinv));
             const df hi2 = df_sqr(habinv);
-            const df gr = df_mul(df_mul(sig, df_sqr(hi2)), df_mul(dwq, rinv));     // grad_a W = gr r_ab
+            const df gr = df_mul(df_mul(sig, a.dim == 1 ? hi2 : df_sqr(hi2)), df_mul(dwq, rinv));   // grad_a W = gr r_ab
             df Pi = df{0.f, 0.f};
             if (df_lt0(vdotr)) {
                 // mu = hab v.r / den, Pi = (-alpha cbar mu + beta mu^2) / rbar with
@@ -369,20 +369,30 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
     a.srcF = ctx->srcF;
     a.vx = vx; a.vy = vy; a.vz = vz; a.m = p->m; a.h = p->h; a.rho = p->rho; a.c = p->c;
     a.ax = p->ax; a.ay = p->ay; a.az = p->az; a.dudt = p->dudt; a.divv = p->divv; a.vsig = p->vsig;
-    a.kernel = ctx->prm.kernel;
+    a.kernel = kern_shape(ctx->prm.kernel, ctx->prm.dim);
+    a.dim = ctx->prm.dim;
     a.periodic = ctx->prm.periodic;
+    a.group_img = ctx->group_img;
     a.thermo = ctx->prm.energy == SPH_ENERGY_TOTAL;
     a.L = ctx->dom[3];
     a.alpha = ctx->prm.alpha; a.beta = ctx->prm.beta; a.eps = ctx->prm.eps_visc;
-    const int kk = ctx->prm.kernel;
-    const double sig = kk == SPH_KERNEL_M4 ? 1.0 / SPH_PI : kk == SPH_KERNEL_WC2 ? 21.0 / (16.0 * SPH_PI)
-                                                                             : 495.0 / (256.0 * SPH_PI);
+    const double sig = kern_sigma<double>(a.kernel);
     a.Ld = df_host(a.L); a.sig_d = df_host(sig);
     a.alpha_d = df_host(a.alpha); a.beta_d = df_host(a.beta); a.eps_d = df_host(a.eps);
     a.cnt = ctx->dcnt;
     SPH_CUDA(cudaEventRecord(ctx->ev[5], s));
     if (ctx->fp64) k_forces_df<<<grid_for(ctx->n_groups, FW), FW * 32, 0, s>>>(a);
-    else k_forces_f32<<<grid_for(ctx->n_groups, FW), FW * 32, 0, s>>>(a);
+    else {
+        // one instantiation per kernel form keeps the pair loop small
+        const unsigned grid = grid_for(ctx->n_groups, FW);
+        switch (a.kernel) {
+        case 1: k_forces_f32<1><<<grid, FW * 32, 0, s>>>(a); break;
+        case 2: k_forces_f32<2><<<grid, FW * 32, 0, s>>>(a); break;
+        case 4: k_forces_f32<4><<<grid, FW * 32, 0, s>>>(a); break;
+        case 5: k_forces_f32<5><<<grid, FW * 32, 0, s>>>(a); break;
+        default: k_forces_f32<0><<<grid, FW * 32, 0, s>>>(a); break;   // M4, either D
+        }
+    }
     SPH_CHECK_LAUNCH();
     SPH_CUDA(cudaEventRecord(ctx->ev[6], s));
     ctx->force_launches = ctx->launches - launches0;

@@ -21,9 +21,10 @@ constexpr int H = 64;
 __device__ __forceinline__ float sigm(float z) { return __fdividef(1.f, 1.f + __expf(-z)); }
 
 // ---------------------------------------------------------------- features
-// f0 = log(h / hbar), hbar = eta (m / rho_ref)^(1/3)
-// f1 = log(max(nnb, 1/2) / nbar), nbar = 32 pi eta^3 / 3
-// f2 = log(rho h^3 / (m eta^3))
+// f0 = log(h / hbar), hbar = eta (m / rho_ref)^(1/D)
+// f1 = log(max(nnb, 1/2) / nbar), nbar = 32 pi eta^3 / 3 (D = 3), 4 eta (D = 1):
+//      the particles within 2h at h = eta (m/rho)^(1/D)
+// f2 = log(rho h^D / (m eta^D))
 // f3 = div v * dt
 // f4 = log(h / hprev)  (0 when hprev <= 0)
 template <typename T>
@@ -31,20 +32,22 @@ struct FeatArgs {
     const T *h, *hprev, *rho, *m, *divv;
     const int32_t *nnb;
     float dt, eta, rho_ref;
+    int dim;
 };
 
 template <typename T>
 __device__ __forceinline__ void features_of(const FeatArgs<T> &fa, int64_t i, float *o)
 {
     const float hi = (float)fa.h[i], mi = (float)fa.m[i], ri = (float)fa.rho[i];
-    const float eta3 = fa.eta * fa.eta * fa.eta;
-    const float hbar = fa.eta * cbrtf(mi / fa.rho_ref);
-    const float nbar = 32.f * 3.14159265358979f * eta3 / 3.f;
+    const bool d1 = fa.dim == 1;
+    const float etaD = d1 ? fa.eta : fa.eta * fa.eta * fa.eta;
+    const float hbar = d1 ? fa.eta * (mi / fa.rho_ref) : fa.eta * cbrtf(mi / fa.rho_ref);
+    const float nbar = d1 ? 4.f * fa.eta : 32.f * 3.14159265358979f * etaD / 3.f;
     const float nb = fmaxf((float)fa.nnb[i], 0.5f);
     const float hp = (float)fa.hprev[i];
     o[0] = logf(hi / hbar);
     o[1] = logf(nb / nbar);
-    o[2] = logf(ri * hi * hi * hi / (mi * eta3));
+    o[2] = logf(ri * (d1 ? hi : hi * hi * hi) / (mi * etaD));
     o[3] = (float)fa.divv[i] * fa.dt;
     o[4] = hp > 0.f ? logf(hi / hp) : 0.f;
 }
@@ -526,6 +529,7 @@ FeatArgs<T> feat_args(const sph_ctx *ctx, const sph_particles *p, double dt)
     fa.h = (const T *)p->h; fa.hprev = (const T *)p->hprev; fa.rho = (const T *)p->rho; fa.m = (const T *)p->m;
     fa.divv = (const T *)p->divv; fa.nnb = p->nnb;
     fa.dt = (float)dt; fa.eta = (float)ctx->prm.eta; fa.rho_ref = (float)ctx->prm.rho_ref;
+    fa.dim = ctx->prm.dim;
     return fa;
 }
 

@@ -44,6 +44,7 @@ struct ListArgs {
     int32_t *group_ubound;         // union slots of each group (sizing passes write them)
     const int64_t *union_off;
     int32_t *group_union;          // union size of each group (fill pass)
+    int32_t *group_img;            // 1: a candidate lies across a periodic face (fill pass)
     uint32_t *uni;
     int64_t ucap;
     int32_t *kept;                 // leaves kept by the sizing pass, kcap per group (0: not cached)
@@ -171,6 +172,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
     };
 
     int ns = 0;
+    bool img = false;                              // this lane staged a source across a periodic face
     auto stage = [&](bool keep, int id) {
         // particles of all kept leaves, loaded in warp-wide waves: lane L
         // owns a leaf range [lb, lb + cnt) placed at [incl - cnt, incl) of
@@ -205,10 +207,11 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
                 const int t = ns + lane;
                 const float4 qa = a.srcA[j], qb = a.srcB[j];
                 float rx = qa.x - gcx, ry = qa.z - gcy, rz = qb.x - gcz;
-                if (a.periodic) {                  // nearest image of the source
-                    rx -= a.L * rintf(rx * a.invL);
-                    ry -= a.L * rintf(ry * a.invL);
-                    rz -= a.L * rintf(rz * a.invL);
+                if (a.periodic && fmaxf(fmaxf(fabsf(rx), fabsf(ry)), fabsf(rz)) > 0.5f * a.L) {
+                    img = true;                    // nearest image of the source
+                    rx = wrap_diff(qa.x, gcx, a.L, a.invL);
+                    ry = wrap_diff(qa.z, gcy, a.L, a.invL);
+                    rz = wrap_diff(qb.x, gcz, a.L, a.invL);
                 }
                 const float cj = a.cov[j];
                 pa[t] = make_float4(rx + qa.y, ry + qa.w, rz + qb.y, cj * cj * (1.f + MARGIN));
@@ -339,6 +342,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
             if (a.kcap > 0) a.kept_count[g] = MODE == LM_BOUND ? nkept : a.kcap + 1;   // exact pass caches none
         }
     } else {
+        const bool any_img = __any_sync(0xffffffffu, img);
         // local indices are 16-bit: a union beyond 65534 sources is a capacity error
         if ((!fits || wmax > width || uc > ucap || uc >= (int)SPH_LOCAL_NONE) && lane == 0)
             atomicOr(&a.cnt->err, ERRB_LIST_CAPACITY);
@@ -347,6 +351,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
         if (lane == 0) {
             a.group_width[g] = used;          // the exact width, within the sized slots
             a.group_union[g] = min(uc, ucap);
+            a.group_img[g] = any_img ? 1 : 0;
             atomicAdd(&a.cnt->list_used, 32ull * (unsigned long long)used);
             atomicAdd(&a.cnt->union_used, (unsigned long long)min(uc, ucap));
         }
@@ -470,6 +475,7 @@ int build_impl(sph_ctx *ctx, cudaStream_t s)
     a.group_ubound = ctx->group_ubound;
     a.union_off = ctx->union_off;
     a.group_union = ctx->group_union;
+    a.group_img = ctx->group_img;
     a.uni = ctx->uni;
     a.ucap = ctx->uni_cap;
     a.kept = ctx->kept;

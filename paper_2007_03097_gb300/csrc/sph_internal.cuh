@@ -67,6 +67,7 @@ enum : uint32_t {
     ERRB_LIST_CAPACITY = 4u,     // neighbour lists exceed nb_capacity
     ERRB_STACK = 8u,             // traversal stack overflow
     ERRB_TIE_RUN = 16u,          // equal-key run too long to order by id
+    ERRB_OFF_AXIS = 32u,         // D = 1 with a particle off the x axis
 };
 
 // per-particle density iteration flags
@@ -173,6 +174,7 @@ struct sph_ctx {
     int32_t *group_ubound = nullptr;    // union slots sized per group
     int64_t *union_off = nullptr;       // n_groups + 1
     int32_t *group_union = nullptr;     // union size per group
+    int32_t *group_img = nullptr;       // 1: a list candidate of the group lies across a periodic face
     int32_t *group_mark = nullptr;      // sweep stamp of a group's last append to the active list
     int32_t *kept = nullptr;            // leaves kept by the list sizing pass, per group
     int32_t *kept_count = nullptr;
@@ -259,25 +261,49 @@ static inline unsigned grid_for(int64_t n, int block)
 }
 
 // ---------------------------------------------------- smoothing kernel math
-// W(r, h) = sigma / h^3 w(q), q = r / h, support q < 2 (the same published
-// forms as the oracle, evaluated here in Horner form).
-//   M4:  w = 1 - 3/2 q^2 + 3/4 q^3 (q < 1),  (2 - q)^3 / 4 (1 <= q < 2)
-//   WC2: w = (1 - q/2)^4 (1 + 2q)
-//   WC4: w = (1 - q/2)^6 (1 + 3q + 35/12 q^2)
-// kern_wdw returns w(q) and dw/dq.
+// W(r, h) = sigma / h^D w(q), q = r / h, support q < 2 (the same published
+// forms as the oracle, evaluated here in Horner form).  A kernel shape is the
+// kernel id in three dimensions and the id + 3 in one (kern_shape):
+//   0 M4    (D = 3, sigma 1/pi;  D = 1 as shape 3, sigma 2/3):
+//           w = 1 - 3/2 q^2 + 3/4 q^3 (q < 1),  (2 - q)^3 / 4 (1 <= q < 2)
+//   1 WC2   D = 3, sigma 21/(16 pi):  w = s^4 (1 + 2q),             s = 1 - q/2
+//   2 WC4   D = 3, sigma 495/(256 pi): w = s^6 (1 + 3q + 35/12 q^2)
+//   4 WC2   D = 1, sigma 5/8:          w = s^3 (1 + 3q/2)
+//   5 WC4   D = 1, sigma 3/4:          w = s^5 (1 + 5q/2 + 2 q^2)
+// (the Wendland functions of Dehnen & Aly 2012 for each dimension, support
+// 2h).  kern_wdw returns w(q) and dw/dq.
 #define SPH_PI 3.14159265358979323846
+__host__ __device__ __forceinline__ int kern_shape(int kernel, int dim) { return kernel + (dim == 1 ? 3 : 0); }
+
 template <typename T>
-__device__ __forceinline__ T kern_sigma(int k)
+__host__ __device__ __forceinline__ T kern_sigma(int shape)
 {
-    return k == SPH_KERNEL_M4 ? T(1.0 / SPH_PI)
-         : k == SPH_KERNEL_WC2 ? T(21.0 / (16.0 * SPH_PI))
-                               : T(495.0 / (256.0 * SPH_PI));
+    switch (shape) {
+    case 0: return T(1.0 / SPH_PI);
+    case 1: return T(21.0 / (16.0 * SPH_PI));
+    case 2: return T(495.0 / (256.0 * SPH_PI));
+    case 3: return T(2.0 / 3.0);
+    case 4: return T(5.0 / 8.0);
+    default: return T(3.0 / 4.0);
+    }
 }
 
 template <typename T>
 __device__ __forceinline__ void kern_wdw(int k, T q, T &w, T &dw)
 {
-    if (k == SPH_KERNEL_M4) {
+    if (k == 1) {
+        T s = T(1) - T(0.5) * q;
+        T s2 = s * s;
+        T s3 = s2 * s;
+        w = s3 * s * (T(1) + T(2) * q);
+        dw = T(-5) * q * s3;
+    } else if (k == 2) {
+        T s = T(1) - T(0.5) * q;
+        T s2 = s * s;
+        T s5 = s2 * s2 * s;
+        w = s5 * s * (T(1) + q * (T(3) + q * T(35.0 / 12.0)));
+        dw = T(-14.0 / 3.0) * q * (T(1) + T(2.5) * q) * s5;
+    } else if (k == 0 || k == 3) {
         if (q < T(1)) {
             w = T(1) + q * q * (T(-1.5) + T(0.75) * q);
             dw = q * (T(-3) + T(2.25) * q);
@@ -286,20 +312,23 @@ __device__ __forceinline__ void kern_wdw(int k, T q, T &w, T &dw)
             w = T(0.25) * t * t * t;
             dw = T(-0.75) * t * t;
         }
-    } else if (k == SPH_KERNEL_WC2) {
+    } else if (k == 4) {
         T s = T(1) - T(0.5) * q;
         T s2 = s * s;
-        T s3 = s2 * s;
-        w = s3 * s * (T(1) + T(2) * q);
-        dw = T(-5) * q * s3;
+        w = s2 * s * (T(1) + T(1.5) * q);
+        dw = T(-3) * q * s2;
     } else {
         T s = T(1) - T(0.5) * q;
         T s2 = s * s;
-        T s5 = s2 * s2 * s;
-        w = s5 * s * (T(1) + q * (T(3) + q * T(35.0 / 12.0)));
-        dw = T(-14.0 / 3.0) * q * (T(1) + T(2.5) * q) * s5;
+        T s4 = s2 * s2;
+        w = s4 * s * (T(1) + q * (T(2.5) + T(2) * q));
+        dw = T(-3.5) * q * (T(1) + T(2) * q) * s4;
     }
 }
+
+// 1 / h^D from 1 / h (D = 1 or 3)
+template <typename T>
+__device__ __forceinline__ T inv_pow_dim(T hinv, int dim) { return dim == 1 ? hinv : hinv * hinv * hinv; }
 
 // Minimum-image separation, FP64 without contraction (bit-identical to the
 // plain expression xa - xb; if > L/2 subtract L; if < -L/2 add L).
@@ -319,15 +348,44 @@ __device__ __forceinline__ double r2_d(double dx, double dy, double dz)
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
-// Separation from two-float positions: (hi_a - hi_b) + (lo_a - lo_b), then
-// the minimum image in FP32.
+// FP32 separation (ha + la) - (hb + lb) of two-float positions to the
+// nearest periodic image.  The difference of the high parts is exact for
+// nearby points (to half an ulp of the separation); for an image pair it is
+// near +-L and rounded to half an ulp of L, which would swamp a separation of
+// a few smoothing lengths, so its rounding error is recovered by two-sum and
+// the shift by L, exact by Sterbenz's lemma, comes first.  wrap: the image
+// taken (-1: L subtracted, +1: L added, 0: none).
+__device__ __forceinline__ float sep_fw(float ha, float la, float hb, float lb, int periodic, float L,
+                                        float half, int &wrap)
+{
+    float d = ha - hb;
+    wrap = 0;
+    if (periodic && fabsf(d) > half) {
+        const float bb = d - ha;
+        const float err = (ha - (d - bb)) + (-hb - bb);
+        wrap = d > 0.f ? -1 : 1;
+        d = (d + (float)wrap * L) + err;
+    }
+    return d + (la - lb);
+}
+
 __device__ __forceinline__ float sep_f(float ha, float la, float hb, float lb, int periodic,
                                        float L, float half)
 {
-    float d = (ha - hb) + (la - lb);
-    if (periodic) {
-        if (d > half) d -= L;
-        else if (d < -half) d += L;
+    int w;
+    return sep_fw(ha, la, hb, lb, periodic, L, half, w);
+}
+
+// a - c (FP32, |a - c| < L + half) to the nearest periodic image, with the
+// rounding error of an image pair's raw difference recovered as in sep_fw.
+__device__ __forceinline__ float wrap_diff(float a, float c, float L, float invL)
+{
+    float d = a - c;
+    const float k = rintf(d * invL);
+    if (k != 0.f) {
+        const float bb = d - a;
+        const float err = (a - (d - bb)) + (-c - bb);
+        d = (d - k * L) + err;
     }
     return d;
 }

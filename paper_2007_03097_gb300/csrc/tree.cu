@@ -130,7 +130,7 @@ __device__ __forceinline__ uint64_t cell_of(double c, double lo, double scale)
 template <typename T>
 __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ y,
                        const double *__restrict__ z, const T *__restrict__ h,
-                       const T *__restrict__ m, int64_t n, int curve, DevCounters *cnt,
+                       const T *__restrict__ m, int64_t n, int curve, int dim, DevCounters *cnt,
                        uint64_t *__restrict__ keys, uint32_t *__restrict__ vals)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -142,6 +142,7 @@ __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ 
     if (h) ok = ok && isfinite((double)h[i]) && (double)h[i] > 0.0;
     if (m) ok = ok && isfinite((double)m[i]);
     if (!ok) atomicOr(&cnt->err, ERRB_NONFINITE);
+    if (dim == 1 && (yi != 0.0 || zi != 0.0)) atomicOr(&cnt->err, ERRB_OFF_AXIS);
     const uint64_t cx = cell_of(xi, lx, scale), cy = cell_of(yi, ly, scale), cz = cell_of(zi, lz, scale);
     const uint64_t key = (curve == SPH_CURVE_HILBERT ? hilbert3((uint32_t)cx, (uint32_t)cy, (uint32_t)cz)
                                                      : spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2)) |
@@ -867,7 +868,7 @@ int keys_impl(sph_ctx *ctx, const sph_particles *p, uint64_t *keys, uint32_t *va
 {
     SPH_TRY(compute_domain(ctx, p, s));
     k_keys<T><<<grid_for(p->n, 256), 256, 0, s>>>(p->x, p->y, p->z, (const T *)p->h, (const T *)p->m, p->n,
-                                                  ctx->prm.curve, ctx->dcnt, keys, vals);
+                                                  ctx->prm.curve, ctx->prm.dim, ctx->dcnt, keys, vals);
     SPH_CHECK_LAUNCH();
     return SPH_OK;
 }
@@ -956,9 +957,11 @@ int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
     for (int d = 0; d < 4; ++d) ctx->dom[d] = ctx->hcnt->dom[d];
     if (err & ERRB_NONFINITE)
         return sph_fail(ctx, SPH_ERR_NONFINITE, "sph_build_tree: NaN/Inf position, mass or h (or h <= 0)");
+    if (err & ERRB_OFF_AXIS)
+        return sph_fail(ctx, SPH_ERR_ARG, "sph_build_tree: dim 1 needs y = z = 0 for every particle");
     if (err & (ERRB_LEAF_DEGENERATE | ERRB_TIE_RUN))
         return sph_fail(ctx, SPH_ERR_CAPACITY,
-                        "sph_build_tree: more than leaf_size particles share one 63-bit Morton key");
+                        "sph_build_tree: more than leaf_size particles share one 63-bit key");
     ctx->n = n;
     ctx->n_leaves = ctx->hcnt->n_leaves;
     ctx->n_groups = ctx->hcnt->n_groups;
@@ -992,6 +995,8 @@ int tree_keys(sph_ctx *ctx, const sph_particles *p, uint64_t *keys_out, cudaStre
     for (int d = 0; d < 4; ++d) ctx->dom[d] = ctx->hcnt->dom[d];
     if (ctx->hcnt->err & ERRB_NONFINITE)
         return sph_fail(ctx, SPH_ERR_NONFINITE, "sph_morton_keys: NaN/Inf position, mass or h");
+    if (ctx->hcnt->err & ERRB_OFF_AXIS)
+        return sph_fail(ctx, SPH_ERR_ARG, "sph_morton_keys: dim 1 needs y = z = 0 for every particle");
     return SPH_OK;
 }
 

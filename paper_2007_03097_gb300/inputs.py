@@ -14,6 +14,7 @@ these are synthetic stand-ins with the paper's particle distributions):
   polytrope n = 1 polytrope sampled radially (rho ~ sin(pi r)/(pi r))
   collision two polytropes approaching each other
   turbulence jittered lattice with a k^-4 solenoidal Gaussian velocity field
+  sod       1D Sod shock tube (Sec. 3), particles on the x axis
 """
 from __future__ import annotations
 
@@ -244,6 +245,44 @@ def turbulence(n_side: int = 256, seed: int = 5001, mach: float = 2.0, gamma: fl
                     np.full(n, eta / n_side), np.full(n, u0), params)
 
 
+SOD_LEFT = (1.0, 0.0, 1.0)        # (rho, v, P) for 0 < x <= 0.5 (Sec. 3, Sod shock tube)
+SOD_RIGHT = (0.125, 0.0, 0.1)     # (rho, v, P) for 0.5 < x < 1
+
+
+def sod(n_tube: int = 10000, gamma: float = 1.4, kernel: int = M4, eta: float = 1.2,
+        precision: str = "fp64") -> Workload:
+    """One-dimensional Sod shock tube: the states of SOD_LEFT on x <= 0.5 and
+    SOD_RIGHT beyond, equal-mass particles evenly spaced in each state, at
+    rest, P = (gamma - 1) rho u.  The tube [0, 1) sits in a periodic box of
+    length 2 with its mirror image on [1, 2) (the left state again on
+    [1.5, 2)), so the box holds two Riemann problems, at x = 0.5 and at
+    x = 1.5, whose waves do not reach each other before t = 0.28.  n_tube is
+    the number of particles in [0, 1) (rounded so that the spacings are 1/8
+    of each other); the box holds twice as many.  Every particle has
+    y = z = 0 and the evaluation is one-dimensional (params dim = 1)."""
+    rl, _, pl = SOD_LEFT
+    rr, _, pr = SOD_RIGHT
+    ratio = rl / rr                                  # 8: left spacing is 1/8 of the right one
+    n_r = max(1, int(round(n_tube / (ratio + 1.0))))
+    n_l = int(round(ratio * n_r))
+    dl, dr = 0.5 / n_l, 0.5 / n_r
+    xl = (np.arange(n_l) + 0.5) * dl                  # [0, 0.5)
+    xr = 0.5 + (np.arange(2 * n_r) + 0.5) * dr        # [0.5, 1.5)
+    xl2 = 1.5 + (np.arange(n_l) + 0.5) * dl           # [1.5, 2)
+    x = np.concatenate([xl, xr, xl2])
+    n = x.size
+    m = rl * dl                                       # = rr * dr
+    left = (x < 0.5) | (x >= 1.5)
+    rho = np.where(left, rl, rr)
+    u = np.where(left, pl, pr) / ((gamma - 1.0) * rho)
+    h = eta * m / rho
+    zeros = np.zeros(n)
+    params = _base_params(kernel=kernel, gamma=gamma, eta=eta, fixed_h=False, h_tol=1e-6,
+                          box_lo=(0.0, 0.0, 0.0), box_hi=(2.0, 2.0, 2.0), dim=1, precision=precision)
+    return Workload("sod", x, zeros.copy(), zeros.copy(), zeros.copy(), zeros.copy(), zeros.copy(),
+                    np.full(n, m), h, u, params, info=dict(n_left=n_l, n_right=n_r, n_tube=n_l + n_r))
+
+
 def by_name(name: str, **kw) -> Workload:
     return {"lattice": lattice, "sedov": sedov, "polytrope": polytrope, "collision": collision,
-            "turbulence": turbulence}[name](**kw)
+            "turbulence": turbulence, "sod": sod}[name](**kw)
