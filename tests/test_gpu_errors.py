@@ -116,6 +116,20 @@ def test_degenerate_positions_rejected():
     assert e.value.code == B.SPH_ERR_CAPACITY
 
 
+def test_one_dimension_needs_particles_on_the_axis():
+    B = need_gpu()
+    w = inputs.sod(200)
+    w.y[7] = 1e-3
+    ctx = B.Context(w.params, w.n)
+    p = B.Particles.from_workload(w, fp64=True)
+    with pytest.raises(B.SphError) as e:
+        B.sph_build_tree(ctx, p)
+    assert e.value.code == B.SPH_ERR_ARG
+    p.y.zero_()                                   # the context stays usable
+    B.sph_build_tree(ctx, p)
+    assert B.sph_density(ctx, p)["status"] == 0
+
+
 def test_single_particle():
     B = need_gpu()
     w = inputs.lattice(1, jitter=0.0, h_factor=0.2)

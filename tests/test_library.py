@@ -63,7 +63,7 @@ def test_invalid_params_rejected_without_gpu(libpath):
     lib = B.load(libpath)
     bad = [dict(kernel=7), dict(leaf_size=0), dict(leaf_size=33), dict(h_min=1.0, h_max=0.5),
            dict(periodic=True, box_hi=(1.0, 2.0, 1.0)), dict(max_sweeps=0), dict(gamma=1.0),
-           dict(periodic=True, h_max=0.3)]
+           dict(periodic=True, h_max=0.3), dict(dim=2), dict(dim=0), dict(curve=2), dict(energy=3)]
     for kw in bad:
         q = B.make_params(kw)
         h = ctypes.c_void_p()
