@@ -207,11 +207,15 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                 hp[i] = hn;
                 if (conv) {
                     // The reading evaluates rho once more at the final h.  When
-                    // |dh| <= 1e-9 h and no list entry lies within 1e-5 of the
-                    // support radius, the neighbour set at h + dh is this one and
-                    // rho(h + dh) = rho + rho' dh up to rho'' dh^2 / 2 ~ 1e-17 rho:
-                    // that evaluation is taken here without another sweep.
-                    if (band == 0 && fabs((double)(hn - h)) <= 1e-9 * (double)h) {
+                    // no list entry lies within 1e-5 of the support radius, the
+                    // neighbour set at h + dh is this one and rho(h + dh) =
+                    // rho + rho' dh up to rho'' dh^2 / 2, a relative
+                    // O(10 (dh/h)^2): below 1e-17 for |dh| <= 1e-9 h, and for
+                    // any converged step (|dh| < h_tol h) below the FP32
+                    // rounding of this sweep.  That evaluation is taken here
+                    // without another sweep.
+                    const double fo_tol = sizeof(T) == sizeof(float) ? a.h_tol : 1e-9;
+                    if (band == 0 && fabs((double)(hn - h)) <= fo_tol * (double)h) {
                         rho_out = rho + drho * (hn - h);
                         hfin = hn;
                         done = true;
