@@ -372,8 +372,10 @@ __device__ __forceinline__ bool df_finalize(const DensArgs &a, const DfTarget &t
             df_st(a.it_hi + i, hi);
             hp[i] = clamp < 0 ? a.h_min : clamp > 0 ? a.h_max : df_to_double(hn);
             if (conv) {
-                // first-order finalization as in the mixed path (see there)
-                if (band == 0 && adh <= 1e-9f * h.hi) {
+                // first-order finalization as in the mixed path (see there),
+                // for |dh| <= 1e-7 h: the neglected term, a relative
+                // O(10 (dh/h)^2) <= 1e-13, sits at the double-float rounding
+                if (band == 0 && adh <= 1e-7f * h.hi) {
                     rho_out = df_add(rho, df_mul(drho, dh));
                     hfin = hn;
                     done = true;
