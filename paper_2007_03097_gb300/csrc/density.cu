@@ -309,12 +309,12 @@ __device__ __forceinline__ void df_pair(const DensArgs &a, const DfTarget &t, ui
     const df dx = df_sep_fast(t.A.x, t.A.y, P.x, P.y, wx, a.Ld);
     const df dy = df_sep_fast(t.A.z, t.A.w, P.z, P.w, wy, a.Ld);
     const df dz = df_sep_fast(t.Bz.x, t.Bz.y, Q.x, Q.y, wz, a.Ld);
-    const df q = df_mul(df_sqrt_fast(df_norm2(dx, dy, dz)), t.hinv);
+    const df q = df_mul_u(df_sqrt_fast(df_norm2(dx, dy, dz)), t.hinv);
     df w, g3;
     df_kern_w_g3(a.kernel, q, w, g3);
     const df mb = df{Q.z, Q.w};
-    df_acc(sw, df_mul(mb, w));
-    df_acc(sd, df_mul(mb, g3));
+    df_acc(sw, df_mul_u(mb, w));
+    df_acc(sd, df_mul_u(mb, g3));
     ++cnt;
 }
 

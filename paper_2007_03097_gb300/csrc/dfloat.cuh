@@ -72,6 +72,29 @@ __device__ __forceinline__ df df_mul_f(df a, float b)
     return fast_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
 }
 
+// Products without the final renormalisation: hi + lo with |lo| up to a few
+// ulp(hi) keeps the same ~2^-46 relative accuracy and is a valid operand of
+// every operation here (a product cancels nothing), so chains of products
+// skip the fast_two_sum of each step.  A result is renormalised (df_norm, or
+// any df_add / df_sub) before a comparison or a store.
+__device__ __forceinline__ df df_mul_u(df a, df b)
+{
+    const df p = two_prod(a.hi, b.hi);
+    return df{p.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo))};
+}
+
+__device__ __forceinline__ df df_mul_f_u(df a, float b)
+{
+    const df p = two_prod(a.hi, b);
+    return df{p.hi, __fmaf_rn(a.lo, b, p.lo)};
+}
+
+__device__ __forceinline__ df df_sqr_u(df a)
+{
+    const df p = two_prod(a.hi, a.hi);
+    return df{p.hi, __fmaf_rn(__fmul_rn(2.f, a.hi), a.lo, p.lo)};
+}
+
 // multiplication by a power of two is exact
 __device__ __forceinline__ df df_scale(df a, float pow2) { return df{__fmul_rn(a.hi, pow2), __fmul_rn(a.lo, pow2)}; }
 
@@ -210,71 +233,71 @@ __device__ __forceinline__ void df_kern_w_g3(int k, df q, df &w, df &g3)
     const df one = df{1.f, 0.f};
     if (k >= 3) {
         const df s = df_add_f(df_scale(q, -0.5f), 1.f);
-        const df q2 = df_sqr(q);
+        const df q2 = df_sqr_u(q);
         if (k == 3) {                                          // M4, D = 1
             if (q.hi < 1.f) {
                 // w = 1 - 1.5 q^2 + 0.75 q^3 ; g = 1 - 4.5 q^2 + 3 q^3
-                const df q3 = df_mul(q2, q);
-                w = df_add(df_add(one, df_mul_f(q2, -1.5f)), df_mul_f(q3, 0.75f));
-                g3 = df_add(df_add(one, df_mul_f(q2, -4.5f)), df_mul_f(q3, 3.f));
+                const df q3 = df_mul_u(q2, q);
+                w = df_add(df_add(one, df_mul_f_u(q2, -1.5f)), df_mul_f_u(q3, 0.75f));
+                g3 = df_add(df_add(one, df_mul_f_u(q2, -4.5f)), df_mul_f_u(q3, 3.f));
             } else {
                 // t = 2 - q ; w = t^3 / 4 ; g = t^2 (2 - 4q) / 4
                 const df t = df_add_f(df_neg(q), 2.f);
-                const df t2 = df_sqr(t);
-                w = df_scale(df_mul(t2, t), 0.25f);
-                g3 = df_scale(df_mul(t2, df_add_f(df_scale(q, -4.f), 2.f)), 0.25f);
+                const df t2 = df_sqr_u(t);
+                w = df_scale(df_mul_u(t2, t), 0.25f);
+                g3 = df_scale(df_mul_u(t2, df_add_f(df_scale(q, -4.f), 2.f)), 0.25f);
             }
         } else if (k == 4) {                                   // Wendland C2, D = 1
             // w = s^3 (1 + 1.5 q) ; g = s^2 (s (1 + 1.5 q) - 3 q^2)
-            const df s2 = df_sqr(s);
-            const df p = df_add_f(df_mul_f(q, 1.5f), 1.f);
-            w = df_mul(df_mul(s2, s), p);
-            g3 = df_mul(s2, df_sub(df_mul(s, p), df_mul_f(q2, 3.f)));
+            const df s2 = df_sqr_u(s);
+            const df p = df_add_f(df_mul_f_u(q, 1.5f), 1.f);
+            w = df_mul_u(df_mul_u(s2, s), p);
+            g3 = df_mul_u(s2, df_sub(df_mul_u(s, p), df_mul_f_u(q2, 3.f)));
         } else {                                               // Wendland C4, D = 1
             // P = 1 + 2.5 q + 2 q^2 ; w = s^5 P ; g = s^4 (s P - 3.5 q^2 (1 + 2q))
-            const df s2 = df_sqr(s);
-            const df s4 = df_sqr(s2);
-            const df P = df_add(df_add_f(df_mul_f(q, 2.5f), 1.f), df_scale(q2, 2.f));
-            w = df_mul(df_mul(s4, s), P);
-            g3 = df_mul(s4, df_sub(df_mul(s, P), df_mul_f(df_mul(q2, df_add_f(df_scale(q, 2.f), 1.f)), 3.5f)));
+            const df s2 = df_sqr_u(s);
+            const df s4 = df_sqr_u(s2);
+            const df P = df_add(df_add_f(df_mul_f_u(q, 2.5f), 1.f), df_scale(q2, 2.f));
+            w = df_mul_u(df_mul_u(s4, s), P);
+            g3 = df_mul_u(s4, df_sub(df_mul_u(s, P), df_mul_f_u(df_mul_u(q2, df_add_f(df_scale(q, 2.f), 1.f)), 3.5f)));
         }
         return;
     }
     if (k == 0) {                                              // M4
-        const df q2 = df_sqr(q);
+        const df q2 = df_sqr_u(q);
         if (q.hi < 1.f) {
             // w = 1 - 1.5 q^2 + 0.75 q^3 ; g3 = 3 - 7.5 q^2 + 4.5 q^3
-            const df q3 = df_mul(q2, q);
-            w = df_add(df_add(one, df_mul_f(q2, -1.5f)), df_mul_f(q3, 0.75f));
-            g3 = df_add(df_add(df{3.f, 0.f}, df_mul_f(q2, -7.5f)), df_mul_f(q3, 4.5f));
+            const df q3 = df_mul_u(q2, q);
+            w = df_add(df_add(one, df_mul_f_u(q2, -1.5f)), df_mul_f_u(q3, 0.75f));
+            g3 = df_add(df_add(df{3.f, 0.f}, df_mul_f_u(q2, -7.5f)), df_mul_f_u(q3, 4.5f));
         } else {
             // t = 2 - q ; w = t^3 / 4 ; g3 = 0.75 t^2 (2 - 2q)
             const df t = df_add_f(df_neg(q), 2.f);
-            const df t2 = df_sqr(t);
-            w = df_scale(df_mul(t2, t), 0.25f);
-            g3 = df_mul_f(df_mul(t2, df_add_f(df_scale(q, -2.f), 2.f)), 0.75f);
+            const df t2 = df_sqr_u(t);
+            w = df_scale(df_mul_u(t2, t), 0.25f);
+            g3 = df_mul_f_u(df_mul_u(t2, df_add_f(df_scale(q, -2.f), 2.f)), 0.75f);
         }
     } else if (k == 1) {                                       // Wendland C2
         // s = 1 - q/2 ; w = s^4 (1 + 2q) ; g3 = s^3 (3 s (1 + 2q) - 5 q^2)
         const df s = df_add_f(df_scale(q, -0.5f), 1.f);
-        const df s2 = df_sqr(s);
-        const df s3 = df_mul(s2, s);
+        const df s2 = df_sqr_u(s);
+        const df s3 = df_mul_u(s2, s);
         const df p = df_add_f(df_scale(q, 2.f), 1.f);
-        w = df_mul(df_sqr(s2), p);
-        g3 = df_mul(s3, df_sub(df_mul_f(df_mul(s, p), 3.f), df_mul_f(df_sqr(q), 5.f)));
+        w = df_mul_u(df_sqr_u(s2), p);
+        g3 = df_mul_u(s3, df_sub(df_mul_f_u(df_mul_u(s, p), 3.f), df_mul_f_u(df_sqr_u(q), 5.f)));
     } else {                                                   // Wendland C4
         // P = 1 + 3q + 35/12 q^2 ; w = s^6 P ;
         // g3 = s^5 (3 s P - 14/3 q^2 (1 + 2.5 q))
         const df c35_12 = df{2.91666674613952637f, -7.94728621e-08f};
         const df c14_3 = df{4.66666650772094727f, 1.58945724e-07f};
         const df s = df_add_f(df_scale(q, -0.5f), 1.f);
-        const df s2 = df_sqr(s);
-        const df s5 = df_mul(df_sqr(s2), s);
-        const df q2 = df_sqr(q);
-        const df P = df_add(df_add_f(df_mul_f(q, 3.f), 1.f), df_mul(q2, c35_12));
-        w = df_mul(df_mul(s5, s), P);
-        const df t = df_mul(df_mul(q2, c14_3), df_add_f(df_mul_f(q, 2.5f), 1.f));
-        g3 = df_mul(s5, df_sub(df_mul_f(df_mul(s, P), 3.f), t));
+        const df s2 = df_sqr_u(s);
+        const df s5 = df_mul_u(df_sqr_u(s2), s);
+        const df q2 = df_sqr_u(q);
+        const df P = df_add(df_add_f(df_mul_f_u(q, 3.f), 1.f), df_mul_u(q2, c35_12));
+        w = df_mul_u(df_mul_u(s5, s), P);
+        const df t = df_mul_u(df_mul_u(q2, c14_3), df_add_f(df_mul_f_u(q, 2.5f), 1.f));
+        g3 = df_mul_u(s5, df_sub(df_mul_f_u(df_mul_u(s, P), 3.f), t));
     }
 }
 
@@ -282,19 +305,19 @@ __device__ __forceinline__ df df_kern_dw(int k, df q)
 {
     if (k >= 4) {
         const df s = df_add_f(df_scale(q, -0.5f), 1.f);
-        const df s2 = df_sqr(s);
-        if (k == 4) return df_mul_f(df_mul(q, s2), -3.f);                       // -3 q s^2
-        return df_mul_f(df_mul(df_mul(q, df_add_f(df_scale(q, 2.f), 1.f)), df_sqr(s2)), -3.5f);  // -3.5 q (1 + 2q) s^4
+        const df s2 = df_sqr_u(s);
+        if (k == 4) return df_mul_f_u(df_mul_u(q, s2), -3.f);                       // -3 q s^2
+        return df_mul_f_u(df_mul_u(df_mul_u(q, df_add_f(df_scale(q, 2.f), 1.f)), df_sqr_u(s2)), -3.5f);  // -3.5 q (1 + 2q) s^4
     }
     if (k == 0 || k == 3) {
-        if (q.hi < 1.f) return df_mul(q, df_add_f(df_mul_f(q, 2.25f), -3.f));    // q (-3 + 2.25 q)
+        if (q.hi < 1.f) return df_mul_u(q, df_add_f(df_mul_f_u(q, 2.25f), -3.f));    // q (-3 + 2.25 q)
         const df t = df_add_f(df_neg(q), 2.f);
-        return df_mul_f(df_sqr(t), -0.75f);                                      // -0.75 (2 - q)^2
+        return df_mul_f_u(df_sqr_u(t), -0.75f);                                      // -0.75 (2 - q)^2
     }
     const df s = df_add_f(df_scale(q, -0.5f), 1.f);
-    const df s2 = df_sqr(s);
-    if (k == 1) return df_mul_f(df_mul(q, df_mul(s2, s)), -5.f);                 // -5 q s^3
+    const df s2 = df_sqr_u(s);
+    if (k == 1) return df_mul_f_u(df_mul_u(q, df_mul_u(s2, s)), -5.f);                 // -5 q s^3
     const df c14_3 = df{4.66666650772094727f, 1.58945724e-07f};
-    const df s5 = df_mul(df_sqr(s2), s);                                         // -14/3 q (1 + 2.5q) s^5
-    return df_neg(df_mul(df_mul(df_mul(q, c14_3), df_add_f(df_mul_f(q, 2.5f), 1.f)), s5));
+    const df s5 = df_mul_u(df_sqr_u(s2), s);                                         // -14/3 q (1 + 2.5q) s^5
+    return df_neg(df_mul_u(df_mul_u(df_mul_u(q, c14_3), df_add_f(df_mul_f_u(q, 2.5f), 1.f)), s5));
 }

@@ -242,51 +242,56 @@ __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
         const df r = df_sqrt_fast(r2);
         const df rinv = df_rcp_fast(r);
         const df vabx = df_sub(vxa, df{Cb.x, Cb.y}), vaby = df_sub(vya, df{Cb.z, Cb.w}), vabz = df_sub(vza, df{Db.x, Db.y});
-        const df vdotr = df_add(df_add(df_mul(vabx, dx), df_mul(vaby, dy)), df_mul(vabz, dz));
+        const df vdotr = df_add(df_add(df_mul_u(vabx, dx), df_mul_u(vaby, dy)), df_mul_u(vabz, dz));
         const df mb = df{Q.z, Q.w};
         if (in_d) {
-            const df dwq = df_kern_dw(a.kernel, df_mul(r, hainv));
-            df_acc(dv, df_mul(df_mul(mb, df_mul(sig_hai4, dwq)), df_mul(rinv, vdotr)));
+            const df dwq = df_kern_dw(a.kernel, df_mul_u(r, hainv));
+            df_acc(dv, df_mul_u(df_mul_u(mb, df_mul_u(sig_hai4, dwq)), df_mul_u(rinv, vdotr)));
         }
         if (in_f) {
             const df hb = df{Db.z, Db.w};
             const df hab = df_scale(df_add(ha, hb), 0.5f);
             const df habinv = df_rcp_fast(hab);
-            const df dwq = df_kern_dw(a.kernel, df_mul(r, habinv));
-            const df hi2 = df_sqr(habinv);
-            const df gr = df_mul(df_mul(sig, a.dim == 1 ? hi2 : df_sqr(hi2)), df_mul(dwq, rinv));   // grad_a W = gr r_ab
+            const df dwq = df_kern_dw(a.kernel, df_mul_u(r, habinv));
+            const df hi2 = df_sqr_u(habinv);
+            const df gr = df_mul_u(df_mul_u(sig, a.dim == 1 ? hi2 : df_sqr_u(hi2)), df_mul_u(dwq, rinv));   // grad_a W = gr r_ab
             df Pi = df{0.f, 0.f};
             if (df_lt0(vdotr)) {
                 // mu = hab v.r / den, Pi = (-alpha cbar mu + beta mu^2) / rbar with
                 // den = r^2 + eps hab^2, through one reciprocal X = 1 / (den rbar):
                 // mu / rbar = hab v.r X, mu = (mu / rbar) rbar
-                const df hv = df_mul(hab, vdotr);
-                const df den = df_add(r2, df_mul(eps, df_sqr(hab)));
+                const df hv = df_mul_u(hab, vdotr);
+                const df den = df_add(r2, df_mul_u(eps, df_sqr_u(hab)));
                 const df rbar = df_scale(df_add(rhoa, df{Eb.x, Eb.y}), 0.5f);
-                const df mu_r = df_mul(hv, df_rcp_fast(df_mul(den, rbar)));
-                const df mu = df_mul(mu_r, rbar);
+                const df mu_r = df_mul_u(hv, df_rcp_fast(df_mul_u(den, rbar)));
+                const df mu = df_mul_u(mu_r, rbar);
                 const df cbar = df_scale(df_add(ca, df{Fb.x, Fb.y}), 0.5f);
-                Pi = df_mul(mu_r, df_sub(df_mul(beta, mu), df_mul(alpha, cbar)));
+                Pi = df_mul_u(mu_r, df_sub(df_mul_u(beta, mu), df_mul_u(alpha, cbar)));
             }
-            const df coef = df_mul(mb, df_mul(df_add(df_add(pra, df{Eb.z, Eb.w}), Pi), gr));
-            df_acc(accx, df_neg(df_mul(coef, dx)));
-            df_acc(accy, df_neg(df_mul(coef, dy)));
-            df_acc(accz, df_neg(df_mul(coef, dz)));
+            const df coef = df_mul_u(mb, df_mul_u(df_add(df_add(pra, df{Eb.z, Eb.w}), Pi), gr));
+            df_acc(accx, df_neg(df_mul_u(coef, dx)));
+            df_acc(accy, df_neg(df_mul_u(coef, dy)));
+            df_acc(accz, df_neg(df_mul_u(coef, dz)));
             if (a.thermo) {
                 // Eq. thermo: -m_b (P_a/rho_a^2 v_b + P_b/rho_b^2 v_a + (v_a + v_b) Pi/2) . grad_a W
                 const df vxb = df{Cb.x, Cb.y}, vyb = df{Cb.z, Cb.w}, vzb = df{Db.x, Db.y};
-                const df vb_r = df_add(df_add(df_mul(vxb, dx), df_mul(vyb, dy)), df_mul(vzb, dz));
+                const df vb_r = df_add(df_add(df_mul_u(vxb, dx), df_mul_u(vyb, dy)), df_mul_u(vzb, dz));
                 const df va_r = df_add(vdotr, vb_r);
-                const df t = df_add(df_add(df_mul(pra, vb_r), df_mul(df{Eb.z, Eb.w}, va_r)),
-                                    df_mul(df_scale(Pi, 0.5f), df_add(va_r, vb_r)));
-                df_acc(du, df_neg(df_mul(df_mul(mb, t), gr)));
+                const df t = df_add(df_add(df_mul_u(pra, vb_r), df_mul_u(df{Eb.z, Eb.w}, va_r)),
+                                    df_mul_u(df_scale(Pi, 0.5f), df_add(va_r, vb_r)));
+                df_acc(du, df_neg(df_mul_u(df_mul_u(mb, t), gr)));
             } else {
-                df_acc(du, df_mul(df_mul(mb, df_add(pra, df_scale(Pi, 0.5f))), df_mul(gr, vdotr)));
+                df_acc(du, df_mul_u(df_mul_u(mb, df_add(pra, df_scale(Pi, 0.5f))), df_mul_u(gr, vdotr)));
             }
-            const df vr = df_mul(vdotr, rinv);
-            df sg = df_add(ca, df{Fb.x, Fb.y});
-            if (df_lt0(vr)) sg = df_sub(sg, df_mul_f(vr, 3.f));
-            if (df_gt(sg, vs)) vs = sg;
+            // v_sig: an FP32 estimate (relative error below 1e-6) screens
+            // out the pairs that cannot raise the maximum
+            const float sgf = (ca.hi + Fb.x) - 3.f * fminf(0.f, vdotr.hi * rinv.hi);
+            if (sgf >= vs.hi * (1.f - 1e-5f)) {
+                const df vr = df_norm(df_mul_u(vdotr, rinv));
+                df sg = df_add(ca, df{Fb.x, Fb.y});
+                if (df_lt0(vr)) sg = df_sub(sg, df_mul_f_u(vr, 3.f));
+                if (df_gt(sg, vs)) vs = sg;
+            }
             ++nint;
         }
     }
