@@ -165,7 +165,7 @@ __global__ void k_pack_force_f32(const float *__restrict__ vx, const float *__re
 }
 
 // SPH_FP64 force pass in double-float (see the file comment).
-__global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
+__global__ void __launch_bounds__(FW * 32, 5) k_forces_df(ForceArgs a)
 {
     const int lane = threadIdx.x & 31;
     const int g = blockIdx.x * FW + (threadIdx.x >> 5);
@@ -190,6 +190,8 @@ __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
     const df hainv = df_rcp(ha);
     const df hai2 = df_sqr(hainv);
     const df sig_hai4 = df_mul(sig, a.dim == 1 ? hai2 : df_sqr(hai2));   // sigma / h_a^(D+1)
+    // the pair sums leave out the per-target factors sigma (a, du/dt) and
+    // sigma / h_a^(D+1) (div v), applied once at the end
     const df vxa = df{C.x, C.y}, vya = df{C.z, C.w}, vza = df{D.x, D.y};
     const df rhoa = df{E.x, E.y}, pra = df{E.z, E.w}, ca = df{F.x, F.y};
     const df alpha = a.alpha_d, beta = a.beta_d, eps = a.eps_d;
@@ -244,9 +246,10 @@ __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
         const df vabx = df_sub(vxa, df{Cb.x, Cb.y}), vaby = df_sub(vya, df{Cb.z, Cb.w}), vabz = df_sub(vza, df{Db.x, Db.y});
         const df vdotr = df_add(df_add(df_mul_u(vabx, dx), df_mul_u(vaby, dy)), df_mul_u(vabz, dz));
         const df mb = df{Q.z, Q.w};
+        const df rv = df_mul_u(rinv, vdotr);                  // v_ab . r_ab / r
         if (in_d) {
             const df dwq = df_kern_dw(a.kernel, df_mul_u(r, hainv));
-            df_acc(dv, df_mul_u(df_mul_u(mb, df_mul_u(sig_hai4, dwq)), df_mul_u(rinv, vdotr)));
+            df_acc(dv, df_mul_u(df_mul_u(mb, dwq), rv));
         }
         if (in_f) {
             const df hb = df{Db.z, Db.w};
@@ -254,7 +257,8 @@ __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
             const df habinv = df_rcp_fast(hab);
             const df dwq = df_kern_dw(a.kernel, df_mul_u(r, habinv));
             const df hi2 = df_sqr_u(habinv);
-            const df gr = df_mul_u(df_mul_u(sig, a.dim == 1 ? hi2 : df_sqr_u(hi2)), df_mul_u(dwq, rinv));   // grad_a W = gr r_ab
+            const df mgq = df_mul_u(mb, df_mul_u(a.dim == 1 ? hi2 : df_sqr_u(hi2), dwq));   // m_b w'(q) / h_ab^(D+1)
+            const df gr = df_mul_u(mgq, rinv);                 // m_b grad_a W / sigma = gr r_ab
             df Pi = df{0.f, 0.f};
             if (df_lt0(vdotr)) {
                 // mu = hab v.r / den, Pi = (-alpha cbar mu + beta mu^2) / rbar with
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
                 const df cbar = df_scale(df_add(ca, df{Fb.x, Fb.y}), 0.5f);
                 Pi = df_mul_u(mu_r, df_sub(df_mul_u(beta, mu), df_mul_u(alpha, cbar)));
             }
-            const df coef = df_mul_u(mb, df_mul_u(df_add(df_add(pra, df{Eb.z, Eb.w}), Pi), gr));
+            const df coef = df_mul_u(df_add(df_add(pra, df{Eb.z, Eb.w}), Pi), gr);
             df_acc(accx, df_neg(df_mul_u(coef, dx)));
             df_acc(accy, df_neg(df_mul_u(coef, dy)));
             df_acc(accz, df_neg(df_mul_u(coef, dz)));
@@ -279,15 +283,15 @@ __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
                 const df va_r = df_add(vdotr, vb_r);
                 const df t = df_add(df_add(df_mul_u(pra, vb_r), df_mul_u(df{Eb.z, Eb.w}, va_r)),
                                     df_mul_u(df_scale(Pi, 0.5f), df_add(va_r, vb_r)));
-                df_acc(du, df_neg(df_mul_u(df_mul_u(mb, t), gr)));
+                df_acc(du, df_neg(df_mul_u(t, gr)));
             } else {
-                df_acc(du, df_mul_u(df_mul_u(mb, df_add(pra, df_scale(Pi, 0.5f))), df_mul_u(gr, vdotr)));
+                df_acc(du, df_mul_u(df_mul_u(df_add(pra, df_scale(Pi, 0.5f)), mgq), rv));
             }
             // v_sig: an FP32 estimate (relative error below 1e-6) screens
             // out the pairs that cannot raise the maximum
             const float sgf = (ca.hi + Fb.x) - 3.f * fminf(0.f, vdotr.hi * rinv.hi);
             if (sgf >= vs.hi * (1.f - 1e-5f)) {
-                const df vr = df_norm(df_mul_u(vdotr, rinv));
+                const df vr = df_norm(rv);
                 df sg = df_add(ca, df{Fb.x, Fb.y});
                 if (df_lt0(vr)) sg = df_sub(sg, df_mul_f_u(vr, 3.f));
                 if (df_gt(sg, vs)) vs = sg;
@@ -296,11 +300,11 @@ __global__ void __launch_bounds__(FW * 32) k_forces_df(ForceArgs a)
         }
     }
     if (tgt) {
-        ((double *)a.ax)[i] = df_to_double(df_norm(accx));
-        ((double *)a.ay)[i] = df_to_double(df_norm(accy));
-        ((double *)a.az)[i] = df_to_double(df_norm(accz));
-        ((double *)a.dudt)[i] = df_to_double(df_norm(du));
-        ((double *)a.divv)[i] = -df_to_double(df_norm(dv)) / ((const double *)a.rho)[i];
+        ((double *)a.ax)[i] = df_to_double(df_mul(sig, df_norm(accx)));
+        ((double *)a.ay)[i] = df_to_double(df_mul(sig, df_norm(accy)));
+        ((double *)a.az)[i] = df_to_double(df_mul(sig, df_norm(accz)));
+        ((double *)a.dudt)[i] = df_to_double(df_mul(sig, df_norm(du)));
+        ((double *)a.divv)[i] = -df_to_double(df_mul(sig_hai4, df_norm(dv))) / ((const double *)a.rho)[i];
         ((double *)a.vsig)[i] = df_to_double(vs);
     }
     for (int o = 16; o > 0; o >>= 1) nint += __shfl_xor_sync(0xffffffffu, nint, o);
