@@ -174,9 +174,19 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *__restri
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = hs[threadIdx.x];
 }
 
-// Stable scatter: elements keep their input order within a digit.  Within
-// a tile, each round of 256 consecutive keys is ranked per warp with
-// __match_any_sync and per digit across the 8 warps in shared memory.
+// Stable scatter: elements keep their input order within a digit.  Each
+// warp ranks its own 512 consecutive keys of the tile (16 rounds of 32:
+// __match_any_sync within a round, a warp-private digit counter across
+// rounds), one block-wide pass turns the per-warp counts into offsets, the
+// tile is reordered by digit in shared memory and then written out with
+// consecutive threads on consecutive destinations (runs of ~16 keys per
+// digit).  The per-tile digit counts are differences of the scanned offsets
+// (digit-major layout: the entry after (d, t) is (d, t + 1), or (d + 1, 0)
+// for the last tile).
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_PER_WARP = RS_TILE / RS_WARPS;      // 512 keys, 16 per lane
+constexpr size_t RS_SCATTER_SMEM = (size_t)RS_TILE * (8 + 4) + sizeof(uint32_t) * RS_BINS * (RS_WARPS + 2);
+
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__restrict__ kin,
                                                            const uint32_t *__restrict__ vin,
                                                            uint64_t *__restrict__ kout,
@@ -184,43 +194,81 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__res
                                                            int shift, const uint32_t *__restrict__ hist,
                                                            int ntiles)
 {
-    __shared__ uint32_t run[RS_BINS];
-    __shared__ uint32_t wc[RS_THREADS / 32][RS_BINS];
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    uint64_t *skey = (uint64_t *)rs_smem;                                   // RS_TILE keys
+    uint32_t *sval = (uint32_t *)(skey + RS_TILE);                          // RS_TILE values
+    uint32_t (*wc)[RS_BINS] = (uint32_t (*)[RS_BINS])(sval + RS_TILE);     // per-warp digit counts
+    uint32_t *loff = &wc[RS_WARPS][0];                                      // tile-local digit offsets
+    uint32_t *gofs = loff + RS_BINS;                                        // global digit offsets
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    run[tid] = hist[(int64_t)tid * ntiles + blockIdx.x];
+    const int b = blockIdx.x;
+    const int64_t base = (int64_t)b * RS_TILE;
+    const int tile_n = n - base < RS_TILE ? (int)(n - base) : RS_TILE;
+    gofs[tid] = hist[(int64_t)tid * ntiles + b];
 #pragma unroll
-    for (int w = 0; w < RS_THREADS / 32; ++w) wc[w][tid] = 0;
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int q = 0; q < RS_BINS / 32; ++q) wc[warp][q * 32 + lane] = 0;
+    __syncwarp();
     const unsigned lt = (1u << lane) - 1u;
+    uint64_t key[RS_ROUNDS];
+    uint32_t val[RS_ROUNDS], rk[RS_ROUNDS];
+#pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
-        const int64_t i = base + r * RS_THREADS + tid;
-        const bool valid = i < n;
-        uint64_t key = valid ? kin[i] : 0ull;
-        uint32_t val = valid ? vin[i] : 0u;
-        const uint32_t digit = valid ? (uint32_t)((key >> shift) & 0xff) : 256u;
+        const int t = warp * RS_PER_WARP + r * 32 + lane;
+        const bool valid = t < tile_n;
+        key[r] = valid ? kin[base + t] : 0ull;
+        val[r] = valid ? vin[base + t] : 0u;
+        const uint32_t digit = valid ? (uint32_t)((key[r] >> shift) & 0xff) : 256u;
         const unsigned peers = __match_any_sync(0xffffffffu, digit);
-        const uint32_t rank = __popc(peers & lt);
-        if (valid && lane == __ffs(peers) - 1) wc[warp][digit] = __popc(peers);
-        __syncthreads();
-        uint32_t acc = 0;
-#pragma unroll
-        for (int w = 0; w < RS_THREADS / 32; ++w) {
-            uint32_t c = wc[w][tid];
-            wc[w][tid] = acc;
-            acc += c;
+        const int leader = __ffs(peers) - 1;
+        uint32_t prev = 0;
+        if (valid && lane == leader) {
+            prev = wc[warp][digit];
+            wc[warp][digit] = prev + __popc(peers);
         }
-        __syncthreads();
-        if (valid) {
-            const uint32_t pos = run[digit] + wc[warp][digit] + rank;
-            kout[pos] = key;
-            vout[pos] = val;
-        }
-        __syncthreads();
-        run[tid] += acc;
+        rk[r] = __shfl_sync(0xffffffffu, prev, leader) + __popc(peers & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+    // digit tid: offsets of the warps within the tile's run of that digit,
+    // then the tile-local start of each digit (exclusive scan of the totals)
+    uint32_t tot = 0;
 #pragma unroll
-        for (int w = 0; w < RS_THREADS / 32; ++w) wc[w][tid] = 0;
-        __syncthreads();
+    for (int w = 0; w < RS_WARPS; ++w) {
+        const uint32_t c = wc[w][tid];
+        wc[w][tid] = tot;
+        tot += c;
+    }
+    uint32_t inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane == 31) loff[warp] = inc;                  // scratch for the warp totals
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += loff[w];
+    __syncthreads();
+    loff[tid] = before + inc - tot;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        const int t = warp * RS_PER_WARP + r * 32 + lane;
+        if (t < tile_n) {
+            const uint32_t digit = (uint32_t)((key[r] >> shift) & 0xff);
+            const uint32_t lp = loff[digit] + wc[warp][digit] + rk[r];
+            skey[lp] = key[r];
+            sval[lp] = val[r];
+        }
+    }
+    __syncthreads();
+    // the tile in digit order: position j of digit d goes to gofs[d] + j - loff[d]
+    for (int t = tid; t < tile_n; t += RS_THREADS) {
+        const uint64_t k = skey[t];
+        const uint32_t d = (uint32_t)((k >> shift) & 0xff);
+        const uint32_t pos = gofs[d] + (uint32_t)t - loff[d];
+        kout[pos] = k;
+        vout[pos] = sval[t];
     }
 }
 
@@ -830,6 +878,8 @@ FieldTable make_table(sph_ctx *ctx, const sph_particles *p)
 
 int radix_sort(sph_ctx *ctx, int64_t n, cudaStream_t s)
 {
+    // the tile staging needs more than 48 KB (set on the current device)
+    SPH_CUDA(cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_SCATTER_SMEM));
     const int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
     uint64_t *ka = ctx->key_a, *kb = ctx->key_b;
     uint32_t *va = ctx->val_a, *vb = ctx->val_b;
@@ -839,7 +889,7 @@ int radix_sort(sph_ctx *ctx, int64_t n, cudaStream_t s)
         SPH_CHECK_LAUNCH();
         SPH_TRY(scan_exclusive_i32(ctx, (const int32_t *)ctx->hist, (int32_t *)ctx->hist,
                                    (int64_t)RS_BINS * ntiles, s));
-        k_rs_scatter<<<ntiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, ctx->hist, ntiles);
+        k_rs_scatter<<<ntiles, RS_THREADS, RS_SCATTER_SMEM, s>>>(ka, va, kb, vb, n, shift, ctx->hist, ntiles);
         SPH_CHECK_LAUNCH();
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
