@@ -48,8 +48,8 @@ FP64_PIPE_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # profiles/), with the hash of the sources it was taken on
 TRAFFIC = {
     # k_forces_df on the Sedov 64^3 step (profiles/k_forces_df_sedov64_fp64.md):
-    # 80.68 MB read + 3.54 MB written
-    "forces_fp64_sedov": {"bytes_per_launch": 84221696, "src": "6c64a48090a8",
+    # 80.70 MB read + 3.37 MB written
+    "forces_fp64_sedov": {"bytes_per_launch": 84078080, "src": "813023e1cc03",
                           "files": ["forces.cu", "dfloat.cuh", "sph_internal.cuh"]},
 }
 FP32_PIPE_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
