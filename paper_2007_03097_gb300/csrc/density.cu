@@ -110,7 +110,7 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
         const int U = a.group_union[g];
         const bool img = a.periodic && a.group_img[g];   // else every source's direct image is the nearest
         const uint32_t *Ug = a.uni + a.uoff[g];
-        const uint16_t *l = a.nbl + off + lane;
+        const unsigned long long *lq = reinterpret_cast<const unsigned long long *>(a.nbl + off) + lane;
         for (int c0 = 0; c0 < U; c0 += a.src_cap) {
             const int cn = min(a.src_cap, U - c0);
             __syncwarp();
@@ -127,23 +127,22 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
             }
             __syncwarp();
             if (active) {
-                // list entries in batches of LB, the next batch in flight
-                // while this one is processed (empty slots fall outside [0, cn))
+                // list entries in batches of LB = 8 (two quads), the next
+                // batch in flight while this one is processed (empty slots
+                // fall outside [0, cn))
                 constexpr int LB = 8;
-                uint32_t nx[LB];
-#pragma unroll
-                for (int u = 0; u < LB; ++u) nx[u] = u < width ? __ldg(l + (int64_t)u * 32) : SPH_LOCAL_NONE;
+                auto quad = [&](int qi) -> unsigned long long {
+                    return 4 * qi < width ? __ldg(lq + 32 * (int64_t)qi) : ~0ull;
+                };
+                unsigned long long n0 = quad(0), n1 = quad(1);
                 for (int k0 = 0; k0 < width; k0 += LB) {
-                    uint32_t cur[LB];
+                    const unsigned long long q0 = n0, q1 = n1;
+                    n0 = quad((k0 >> 2) + 2);
+                    n1 = quad((k0 >> 2) + 3);
 #pragma unroll
                     for (int u = 0; u < LB; ++u) {
-                        cur[u] = nx[u];
-                        const int kk = k0 + LB + u;
-                        nx[u] = kk < width ? __ldg(l + (int64_t)kk * 32) : SPH_LOCAL_NONE;
-                    }
-#pragma unroll
-                    for (int u = 0; u < LB; ++u) {
-                    const int le = (int)cur[u] - c0;
+                    const uint32_t e = (uint32_t)((u < 4 ? q0 : q1) >> (16 * (u & 3))) & 0xFFFFu;
+                    const int le = (int)e - c0;
                     if ((unsigned)le >= (unsigned)cn) continue;
                     const float4 q = s_src[le];
                     const float dx = tx - q.x, dy = ty - q.y, dz = tz - q.z;
@@ -488,7 +487,7 @@ __global__ void __launch_bounds__(DW * 32) k_density_sparse(DensArgs a)
             df sw = df{0.f, 0.f}, sd = df{0.f, 0.f};
             int cnt = 0, band = 0;
             for (int k = lane; k < width; k += 32) {
-                const uint32_t e = a.nbl[off + (int64_t)k * 32 + p];
+                const uint32_t e = a.nbl[slot_index(off, k, p)];
                 if (e == SPH_LOCAL_NONE) continue;
                 const uint32_t b = __ldg(U + e);
                 df_pair(a, t, b, __ldg(a.srcA + b), __ldg(a.srcB + b), sw, sd, cnt, band);

@@ -70,15 +70,15 @@ __global__ void __launch_bounds__(FW * 32) k_forces_f32(ForceArgs a)
     int nint = 0;
     // the list entry of slot k + 2 and the union index of slot k + 1 are in
     // flight while slot k is processed
-    const uint16_t *l = a.nbl + off + lane;
-    auto entry = [&](int k) -> uint32_t { return k < width ? (uint32_t)__ldg(l + (int64_t)k * 32) : SPH_LOCAL_NONE; };
+    SlotStream st(a.nbl, off, width, lane);
     auto index = [&](uint32_t e) -> uint32_t { return e == SPH_LOCAL_NONE ? SPH_SENTINEL : __ldg(U + e); };
-    uint32_t e2 = entry(1);
-    uint32_t b1 = index(entry(0));
+    const uint32_t e0 = st.next();
+    uint32_t e2 = st.next();
+    uint32_t b1 = index(e0);
     for (int k = 0; k < width; ++k) {
         const uint32_t b = b1;
         b1 = index(e2);
-        e2 = entry(k + 2);
+        e2 = st.next();
         if (b == SPH_SENTINEL) continue;
         const float4 P = a.srcA[b], Q = a.srcB[b], Cb = a.srcC[b];
         const float dx = sep_f(A.x, A.y, P.x, P.y, img, Lf, half);
@@ -200,15 +200,15 @@ __global__ void __launch_bounds__(FW * 32, 5) k_forces_df(ForceArgs a)
     int nint = 0;
     // the list entry of slot k + 2 and the union index of slot k + 1 are in
     // flight while slot k is processed
-    const uint16_t *l = a.nbl + off + lane;
-    auto entry = [&](int k) -> uint32_t { return k < width ? (uint32_t)__ldg(l + (int64_t)k * 32) : SPH_LOCAL_NONE; };
+    SlotStream st(a.nbl, off, width, lane);
     auto index = [&](uint32_t e) -> uint32_t { return e == SPH_LOCAL_NONE ? SPH_SENTINEL : __ldg(U + e); };
-    uint32_t e2 = entry(1);
-    uint32_t b1 = index(entry(0));
+    const uint32_t e0 = st.next();
+    uint32_t e2 = st.next();
+    uint32_t b1 = index(e0);
     for (int k = 0; k < width; ++k) {
         const uint32_t b = b1;
         b1 = index(e2);
-        e2 = entry(k + 2);
+        e2 = st.next();
         if (b == SPH_SENTINEL) continue;
         const float4 P = a.srcA[b], Q = a.srcB[b], Db = a.srcD[b];
         int wx, wy, wz;

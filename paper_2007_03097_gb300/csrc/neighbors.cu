@@ -5,8 +5,9 @@
 // and tests the tile's sources in FP32 on two-float relative coordinates
 // with a small relative margin, so the list is a superset of the exact set.
 // The exact FP64 (or FP32) decision is taken again by the pass that uses the
-// list.  Lists are stored slot-major per group (entry (slot, lane) at
-// off[g] + 32 slot + lane) so that the consumers read them coalesced.
+// list.  Lists are stored per group in quads of four slots per lane (see
+// slot_index), so that a lane writes four entries with one 8-byte store and
+// the consumers read them coalesced.
 // One symmetric list serves the whole step: b is listed for a when
 // r_ab <= max(cov_a, cov_b) with the coverage radius cov = 2 h (1 + skin).
 // While 2h <= cov for every particle it holds every density pair
@@ -122,7 +123,9 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
     int ub = 0;                                    // union slots needed (sizing passes)
     bool overflow = false;
 
-    uint16_t *wp = FILL ? a.nbl + off + lane : nullptr;   // this lane's next list slot
+    // this lane's quads, and the entries of the quad being filled
+    unsigned long long *qp = FILL ? reinterpret_cast<unsigned long long *>(a.nbl + off) + lane : nullptr;
+    unsigned long long pend = 0ull;
 
     // A batch of at most 32 staged candidates: every lane tests all of them
     // (bit k of `bits` = candidate k within this lane's reach), its own
@@ -159,8 +162,11 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
             __syncwarp();
             for (unsigned m = bits; m; m &= m - 1) {
                 if (count < width) {
-                    *wp = (uint16_t)s_loc[w][__ffs(m) - 1];
-                    wp += 32;
+                    pend |= (unsigned long long)s_loc[w][__ffs(m) - 1] << (16 * (count & 3));
+                    if ((count & 3) == 3) {
+                        qp[32 * (int64_t)(count >> 2)] = pend;
+                        pend = 0ull;
+                    }
                 }
                 ++count;
             }
@@ -337,7 +343,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
     for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
     if (!FILL) {
         if (lane == 0) {
-            a.group_width[g] = wmax;
+            a.group_width[g] = (wmax + 3) & ~3;          // whole quads
             a.group_ubound[g] = MODE == LM_BOUND ? ub : uc;
             if (a.kcap > 0) a.kept_count[g] = MODE == LM_BOUND ? nkept : a.kcap + 1;   // exact pass caches none
         }
@@ -346,8 +352,14 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
         // local indices are 16-bit: a union beyond 65534 sources is a capacity error
         if ((!fits || wmax > width || uc > ucap || uc >= (int)SPH_LOCAL_NONE) && lane == 0)
             atomicOr(&a.cnt->err, ERRB_LIST_CAPACITY);
-        const int used = min(wmax, width);
-        for (int k = count; k < used; ++k) a.nbl[off + (int64_t)k * 32 + lane] = (uint16_t)SPH_LOCAL_NONE;
+        const int used = (min(wmax, width) + 3) & ~3;  // width is a multiple of 4
+        int k = min(count, width);
+        if (k & 3) {                                   // the partial quad, padded with empty slots
+            for (int j = k & 3; j < 4; ++j) pend |= 0xFFFFull << (16 * j);
+            qp[32 * (int64_t)(k >> 2)] = pend;
+            k = (k + 3) & ~3;
+        }
+        for (; k < used; k += 4) qp[32 * (int64_t)(k >> 2)] = ~0ull;
         if (lane == 0) {
             a.group_width[g] = used;          // the exact width, within the sized slots
             a.group_union[g] = min(uc, ucap);
@@ -412,7 +424,7 @@ __global__ void k_export(const int32_t *__restrict__ group_begin, int ng, const 
     int64_t c = 0;
     const int64_t o = offsets ? offsets[ia] : 0;
     for (int k = 0; k < width; ++k) {
-        const uint32_t e = nbl[off + (int64_t)k * 32 + lane];
+        const uint32_t e = nbl[slot_index(off, k, lane)];
         if (e == SPH_LOCAL_NONE) continue;
         const uint32_t b = uni[uoff[g] + e];
         bool in;

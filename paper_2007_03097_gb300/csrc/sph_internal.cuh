@@ -16,7 +16,36 @@
 
 #define SPH_LOCAL_NONE 0xFFFFu
 
-// Walks one lane's slot-major neighbour list off + 32 k + lane, k < width,
+// Lists are stored in quads: slots 4q .. 4q + 3 of lane l form one 8-byte
+// word, quad q of lane l at 64-bit index off / 4 + 32 q + l (off, the group's
+// offset in 16-bit slots, is a multiple of 128 and list widths are multiples
+// of 4), so that a lane writes four entries with one store and a warp reading
+// one quad of every lane reads 256 contiguous bytes.
+__device__ __forceinline__ int64_t slot_index(int64_t off, int k, int lane)
+{
+    return off + 128 * (int64_t)(k >> 2) + 4 * lane + (k & 3);
+}
+
+// Sequential reader of one lane's slots: next() returns slots 0, 1, 2, ...
+// (SPH_LOCAL_NONE past the width), one 8-byte load per four slots.
+struct SlotStream {
+    const unsigned long long *q;
+    int width, k;
+    unsigned long long cur;
+    __device__ __forceinline__ SlotStream(const uint16_t *nbl, int64_t off, int width_, int lane)
+        : q(reinterpret_cast<const unsigned long long *>(nbl + off) + lane), width(width_), k(0), cur(~0ull)
+    {
+    }
+    __device__ __forceinline__ uint32_t next()
+    {
+        if ((k & 3) == 0) cur = k < width ? __ldg(q + 32 * (int64_t)(k >> 2)) : ~0ull;
+        const uint32_t e = (uint32_t)(cur >> (16 * (k & 3))) & 0xFFFFu;
+        ++k;
+        return e;
+    }
+};
+
+// Walks one lane's neighbour list (slots k < width in quads, see above),
 // whose 16-bit entries index the group's source union uni[uoff ..]; calls
 // proc(b, A[b], B[b]) for every entry's global index b.  PIPELINED: entry
 // k + 3, the index of entry k + 2 and the records of entry k + 1 are in
@@ -29,9 +58,10 @@ __device__ __forceinline__ void walk_list(const uint16_t *__restrict__ nbl, int6
                                           const float4 *__restrict__ A, const float4 *__restrict__ B, Proc &&proc)
 {
     const uint32_t *U = uni + uoff;
+    SlotStream st(nbl, off, width, lane);
     if (!PIPELINED) {
         for (int k = 0; k < width; ++k) {
-            const uint32_t e = nbl[off + (int64_t)k * 32 + lane];
+            const uint32_t e = st.next();
             if (e == SPH_LOCAL_NONE) continue;
             const uint32_t b = __ldg(U + e);
             proc(b, A[b], B[b]);
@@ -39,12 +69,11 @@ __device__ __forceinline__ void walk_list(const uint16_t *__restrict__ nbl, int6
         return;
     }
     if (width <= 0) return;
-    const uint16_t *l = nbl + off + lane;
-    auto entry = [&](int k) -> uint32_t { return k < width ? (uint32_t)__ldg(l + (int64_t)k * 32) : SPH_LOCAL_NONE; };
     auto index = [&](uint32_t e) -> uint32_t { return e == SPH_LOCAL_NONE ? SPH_SENTINEL : __ldg(U + e); };
-    uint32_t e2 = entry(2);
-    uint32_t b1 = index(entry(1));
-    uint32_t b0 = index(entry(0));
+    const uint32_t e0 = st.next(), e1 = st.next();
+    uint32_t e2 = st.next();
+    uint32_t b0 = index(e0);
+    uint32_t b1 = index(e1);
     uint32_t j = b0 == SPH_SENTINEL ? self : b0;
     float4 P = __ldg(A + j), Q = __ldg(B + j);
     for (int k = 0; k < width; ++k) {
@@ -52,7 +81,7 @@ __device__ __forceinline__ void walk_list(const uint16_t *__restrict__ nbl, int6
         const float4 Pc = P, Qc = Q;
         b0 = b1;
         b1 = index(e2);
-        e2 = entry(k + 3);
+        e2 = st.next();
         j = b0 == SPH_SENTINEL ? self : b0;
         P = __ldg(A + j);
         Q = __ldg(B + j);
