@@ -201,6 +201,9 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
         for (int base = 0; base < total; base += 32) {
             const int item = base + lane;
             const int take2 = min(32, total - base);
+            bool within = false;
+            float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
+            int j = 0;
             if (lane < take2) {
                 // owner: first lane whose inclusive end exceeds item
                 int lo2 = 0, hi2 = 31;
@@ -209,8 +212,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
                     if (s_incl[w][mid] > item) hi2 = mid; else lo2 = mid + 1;
                 }
                 const int start = lo2 > 0 ? s_incl[w][lo2 - 1] : 0;       // exclusive start of the owner
-                const int j = s_lb[w][lo2] + (item - start);
-                const int t = ns + lane;
+                j = s_lb[w][lo2] + (item - start);
                 const float4 qa = a.srcA[j], qb = a.srcB[j];
                 float rx = qa.x - gcx, ry = qa.z - gcy, rz = qb.x - gcz;
                 if (a.periodic && fmaxf(fmaxf(fabsf(rx), fabsf(ry)), fabsf(rz)) > 0.5f * a.L) {
@@ -220,10 +222,23 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
                     rz = wrap_diff(qb.x, gcz, a.L, a.invL);
                 }
                 const float cj = a.cov[j];
-                pa[t] = make_float4(rx + qa.y, ry + qa.w, rz + qb.y, cj * cj * (1.f + MARGIN));
+                rec = make_float4(rx + qa.y, ry + qa.w, rz + qb.y, cj * cj * (1.f + MARGIN));
+                // every target lies in the group box: a candidate farther than
+                // max(largest target coverage, its own) from the box is
+                // within no target's reach and is not staged (in a
+                // 100-neighbour run the kept leaves hold about twice the
+                // particles that some target lists)
+                const float gx = fmaxf(0.f, fabsf(rec.x) - gex), gy = fmaxf(0.f, fabsf(rec.y) - gey),
+                            gz = fmaxf(0.f, fabsf(rec.z) - gez);
+                within = (gx * gx + gy * gy) + gz * gz <= fmaxf(qcov * qcov * (1.f + MARGIN), rec.w);
+            }
+            const unsigned km = __ballot_sync(0xffffffffu, within);
+            if (within) {
+                const int t = ns + __popc(km & ((1u << lane) - 1u));
+                pa[t] = rec;
                 pi[t] = j;
             }
-            ns += take2;
+            ns += __popc(km);
             __syncwarp();
             if (ns >= 32) {
                 process(32);
