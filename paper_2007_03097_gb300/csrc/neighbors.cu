@@ -38,6 +38,7 @@ struct ListArgs {
     const float4 *node_lo, *node_hi;
     int periodic;
     float L, invL, slack;
+    float blo[3];                  // low corner of the periodic box
     int32_t *group_width;
     const int64_t *group_off;
     uint16_t *nbl;
@@ -105,6 +106,17 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
                 tz = tgt ? (PB.x - gcz) + PB.y : FAR;
     const float gex = 0.5f * (qhi.x - qlo.x) + a.slack, gey = 0.5f * (qhi.y - qlo.y) + a.slack,
                 gez = 0.5f * (qhi.z - qlo.z) + a.slack;
+    // a group whose box, grown by the largest coverage anywhere (the root's),
+    // stays inside the periodic box reaches no periodic image: its walk and
+    // culling take plain differences
+    int wrap = a.periodic;
+    if (wrap) {
+        const float rmax = (a.n_leaves > 1 ? a.node_lo[0].w : a.leaf_lo[0].w) * (1.f + MARGIN) + a.slack;
+        const float mx = gex + rmax, my = gey + rmax, mz = gez + rmax;
+        const bool inside = gcx - mx > a.blo[0] && gcx + mx < a.blo[0] + a.L && gcy - my > a.blo[1] &&
+                            gcy + my < a.blo[1] + a.L && gcz - mz > a.blo[2] && gcz + mz < a.blo[2] + a.L;
+        if (inside) wrap = 0;
+    }
 
     int64_t off = 0, uoff = 0;
     int width = 0, ucap = 0;
@@ -215,7 +227,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
                 j = s_lb[w][lo2] + (item - start);
                 const float4 qa = a.srcA[j], qb = a.srcB[j];
                 float rx = qa.x - gcx, ry = qa.z - gcy, rz = qb.x - gcz;
-                if (a.periodic && fmaxf(fmaxf(fabsf(rx), fabsf(ry)), fabsf(rz)) > 0.5f * a.L) {
+                if (wrap && fmaxf(fmaxf(fabsf(rx), fabsf(ry)), fabsf(rz)) > 0.5f * a.L) {
                     img = true;                    // nearest image of the source
                     rx = wrap_diff(qa.x, gcx, a.L, a.invL);
                     ry = wrap_diff(qa.z, gcy, a.L, a.invL);
@@ -289,9 +301,9 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
             bc = make_float4(0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z),
                              lo.w * lo.w * (1.f + MARGIN));
             be = make_float4(0.5f * (hi.x - lo.x), 0.5f * (hi.y - lo.y), 0.5f * (hi.z - lo.z), 0.f);
-            const float gx = axis_gap(bc.x, be.x + gex, gcx, a.periodic, a.L, a.invL);
-            const float gy = axis_gap(bc.y, be.y + gey, gcy, a.periodic, a.L, a.invL);
-            const float gz = axis_gap(bc.z, be.z + gez, gcz, a.periodic, a.L, a.invL);
+            const float gx = axis_gap(bc.x, be.x + gex, gcx, wrap, a.L, a.invL);
+            const float gy = axis_gap(bc.y, be.y + gey, gcy, wrap, a.L, a.invL);
+            const float gz = axis_gap(bc.z, be.z + gez, gcz, wrap, a.L, a.invL);
             acc = (gx * gx + gy * gy) + gz * gz <= r * r * (1.f + MARGIN);
         }
         const unsigned mint = __ballot_sync(0xffffffffu, acc && !leaf);
@@ -318,9 +330,9 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
         for (unsigned m = lmask; m; m &= m - 1) {
             const int l = __ffs(m) - 1;
             const float4 c = s_bc[w][l], e = s_be[w][l];
-            const float gx = axis_gap(c.x, e.x, PA.x, a.periodic, a.L, a.invL);
-            const float gy = axis_gap(c.y, e.y, PA.z, a.periodic, a.L, a.invL);
-            const float gz = axis_gap(c.z, e.z, PB.x, a.periodic, a.L, a.invL);
+            const float gx = axis_gap(c.x, e.x, PA.x, wrap, a.L, a.invL);
+            const float gy = axis_gap(c.y, e.y, PA.z, wrap, a.L, a.invL);
+            const float gz = axis_gap(c.z, e.z, PB.x, wrap, a.L, a.invL);
             const unsigned nm =
                 __ballot_sync(0xffffffffu, tgt && (gx * gx + gy * gy) + gz * gz <= fmaxf(ca2, c.w));
             if (lane == l) need = nm;
@@ -492,6 +504,7 @@ int build_impl(sph_ctx *ctx, cudaStream_t s)
     a.child = ctx->node_child;
     a.node_lo = ctx->node_lo; a.node_hi = ctx->node_hi;
     a.periodic = ctx->prm.periodic;
+    for (int d = 0; d < 3; ++d) a.blo[d] = (float)ctx->dom[d];
     a.L = (float)ctx->dom[3];
     a.invL = 1.f / a.L;
     a.slack = (float)(1e-6 * ctx->dom[3]);
