@@ -172,6 +172,8 @@ struct sph_ctx {
     int64_t hist_cap = 0;
     NsTile *ns_tiles = nullptr;         // near-sorted pass, one per 1024 keys
     int64_t ns_moved = -1;              // particles the last build moved (-1: full sort)
+    int ns_full_streak = 0;             // consecutive builds that needed the full sort
+    int ns_skip = 0;                    // builds left that go straight to the full sort
     // ---- tree
     uint8_t *dlev = nullptr;            // first differing level with predecessor
     uint8_t *plev = nullptr;            // leaf level of each particle

@@ -971,7 +971,16 @@ int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
     SPH_TRY(keys_impl<T>(ctx, p, ctx->key_a, ctx->val_a, s));
     FieldTable t = make_table<T>(ctx, p);
     int64_t m = -1;
-    SPH_TRY(near_sorted(ctx, p, t, &m, s));
+    // after two full sorts in a row (most keys displaced every step) the
+    // detection of a nearly sorted order is skipped for seven builds, then
+    // tried again
+    if (ctx->ns_skip > 0) {
+        --ctx->ns_skip;
+    } else {
+        SPH_TRY(near_sorted(ctx, p, t, &m, s));
+        ctx->ns_full_streak = m < 0 ? ctx->ns_full_streak + 1 : 0;
+        if (ctx->ns_full_streak >= 2) ctx->ns_skip = 7;
+    }
     if (m < 0) {
         // full sort, then permute every particle array into key order
         SPH_TRY(radix_sort(ctx, n, s));
