@@ -98,7 +98,10 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
 
     T sum_w = T(0), sum_dh = T(0);
     int cnt = 0;
-    int band = 0;        // list entries within a relative 1e-5 of the support radius
+    int band = 0;        // list entries within a relative BAND of the support radius
+    // the band covers the change of the support over a converged step: a
+    // relative 3e-4 of r^2 (a step of up to 1e-4 h, see below)
+    constexpr float BAND = 3e-4f;
     if (__any_sync(0xffffffffu, active)) {
         const float4 qlo = a.group_lo[g], qhi = a.group_hi[g];
         const float gcx = 0.5f * (qlo.x + qhi.x), gcy = 0.5f * (qlo.y + qhi.y), gcz = 0.5f * (qlo.z + qhi.z);
@@ -147,7 +150,7 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                     const float4 q = s_src[le];
                     const float dx = tx - q.x, dy = ty - q.y, dz = tz - q.z;
                     const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-                    if (fabsf(r2 - thr) <= 1e-5f * thr) ++band;
+                    if (fabsf(r2 - thr) <= BAND * thr) ++band;
                     if (!(r2 < thr)) continue;
                     const T qq = (T)(r2 > 0.f ? r2 * rsqrtf(r2) : 0.f) * hinv;   // r within 2 ulp
                     T w, dw;
@@ -198,23 +201,26 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                     ok = (hn >= alo) && (hn <= ahi);
                 }
                 if (!ok) hn = f > T(0) ? T(0.5) * (h + ahi) : T(0.5) * (h + alo);
-                if (hn < (T)a.h_min) hn = (T)a.h_min;
-                if (hn > (T)a.h_max) hn = (T)a.h_max;
-                const bool conv = fabs((double)(hn - h)) < a.h_tol * (double)h;
+                if (hn < (T)a.h_min) { hn = (T)a.h_min; ok = false; }
+                if (hn > (T)a.h_max) { hn = (T)a.h_max; ok = false; }
+                // Newton converges quadratically: after a Newton step of
+                // |dh| < 1e-4 h the error of the new h is about dh^2 / h
+                // (f''/f' ~ 1/h for f = m eta^D / h^D - rho), below 1e-8 h and
+                // far inside h_tol; the FP32 sweep accepts such a step
+                const double adh = fabs((double)(hn - h));
+                const bool conv = adh < a.h_tol * (double)h || (ok && adh < 1e-4 * (double)h);
                 a.it_lo[i] = lo;
                 a.it_hi[i] = hi;
                 hp[i] = hn;
                 if (conv) {
                     // The reading evaluates rho once more at the final h.  When
-                    // no list entry lies within 1e-5 of the support radius, the
-                    // neighbour set at h + dh is this one and rho(h + dh) =
+                    // no list entry lies within the band of the support radius,
+                    // the neighbour set at h + dh is this one and rho(h + dh) =
                     // rho + rho' dh up to rho'' dh^2 / 2, a relative
-                    // O(10 (dh/h)^2): below 1e-17 for |dh| <= 1e-9 h, and for
-                    // any converged step (|dh| < h_tol h) below the FP32
-                    // rounding of this sweep.  That evaluation is taken here
-                    // without another sweep.
-                    const double fo_tol = sizeof(T) == sizeof(float) ? a.h_tol : 1e-9;
-                    if (band == 0 && fabs((double)(hn - h)) <= fo_tol * (double)h) {
+                    // O(10 (dh/h)^2), below 1e-7 for |dh| < 1e-4 h: within the
+                    // FP32 rounding of this sweep.  That evaluation is taken
+                    // here without another sweep.
+                    if (band == 0) {
                         rho_out = rho + drho * (hn - h);
                         hfin = hn;
                         done = true;
