@@ -10,6 +10,7 @@
 // the shallowest key-prefix cell holding at most leaf_size particles, found
 // per particle from the levels at which neighbouring keys first differ.
 #include <cfloat>
+#include <cmath>
 
 #include <algorithm>
 
@@ -127,23 +128,53 @@ __device__ __forceinline__ uint64_t cell_of(double c, double lo, double scale)
     return (uint64_t)f;
 }
 
+// floor(c 2^sh) clamped to [0, 2^21 - 1] from the bits of c (a box with its
+// low corner at 0 and a power-of-two side, sh = 21 - log2 L): c 2^sh is then
+// exact and cell_of's FP64 arithmetic reduces to a shift of the significand.
+// Same cells as cell_of(c, 0, 2^sh) for every finite c.
+__device__ __forceinline__ uint64_t cell_pow2(double c, int sh)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(c);
+    if (b >> 63) return 0;                              // negative: the lowest cell
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e == 0) return 0;                               // zero or subnormal
+    const int p = e - 1023 + sh;                        // c 2^sh = 1.f x 2^p
+    if (p < 0) return 0;
+    if (p >= 21) return 2097151;                        // beyond the grid (or not finite)
+    return (((b & ((1ull << 52) - 1)) | (1ull << 52)) >> (52 - p));
+}
+
+__device__ __forceinline__ bool finite_bits(double v)
+{
+    return (((uint64_t)__double_as_longlong(v) >> 52) & 0x7FF) != 0x7FF;
+}
+
 template <typename T>
 __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ y,
                        const double *__restrict__ z, const T *__restrict__ h,
-                       const T *__restrict__ m, int64_t n, int curve, int dim, DevCounters *cnt,
+                       const T *__restrict__ m, int64_t n, int curve, int dim, int pow2_shift, DevCounters *cnt,
                        uint64_t *__restrict__ keys, uint32_t *__restrict__ vals)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double lx = cnt->dom[0], ly = cnt->dom[1], lz = cnt->dom[2];
-    const double scale = 2097152.0 / cnt->dom[3];
     const double xi = x[i], yi = y[i], zi = z[i];
-    bool ok = isfinite(xi) && isfinite(yi) && isfinite(zi);
-    if (h) ok = ok && isfinite((double)h[i]) && (double)h[i] > 0.0;
-    if (m) ok = ok && isfinite((double)m[i]);
+    bool ok = finite_bits(xi) && finite_bits(yi) && finite_bits(zi);
+    if (h) ok = ok && isfinite(h[i]) && h[i] > T(0);
+    if (m) ok = ok && isfinite(m[i]);
     if (!ok) atomicOr(&cnt->err, ERRB_NONFINITE);
     if (dim == 1 && (yi != 0.0 || zi != 0.0)) atomicOr(&cnt->err, ERRB_OFF_AXIS);
-    const uint64_t cx = cell_of(xi, lx, scale), cy = cell_of(yi, ly, scale), cz = cell_of(zi, lz, scale);
+    uint64_t cx, cy, cz;
+    if (pow2_shift >= 0) {
+        cx = cell_pow2(xi, pow2_shift);
+        cy = cell_pow2(yi, pow2_shift);
+        cz = cell_pow2(zi, pow2_shift);
+    } else {
+        const double lx = cnt->dom[0], ly = cnt->dom[1], lz = cnt->dom[2];
+        const double scale = 2097152.0 / cnt->dom[3];
+        cx = cell_of(xi, lx, scale);
+        cy = cell_of(yi, ly, scale);
+        cz = cell_of(zi, lz, scale);
+    }
     const uint64_t key = (curve == SPH_CURVE_HILBERT ? hilbert3((uint32_t)cx, (uint32_t)cy, (uint32_t)cz)
                                                      : spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2)) |
                          (1ull << 63);
@@ -917,8 +948,16 @@ template <typename T>
 int keys_impl(sph_ctx *ctx, const sph_particles *p, uint64_t *keys, uint32_t *vals, cudaStream_t s)
 {
     SPH_TRY(compute_domain(ctx, p, s));
+    // a periodic box at the origin with a power-of-two side: cells by shifts
+    int pow2_shift = -1;
+    const sph_params &q = ctx->prm;
+    if (q.periodic && q.box_lo[0] == 0.0 && q.box_lo[1] == 0.0 && q.box_lo[2] == 0.0) {
+        int ex = 0;
+        const double fr = std::frexp(q.box_hi[0], &ex);        // L = fr 2^ex, fr in [0.5, 1)
+        if (fr == 0.5 && 22 - ex >= 0 && 22 - ex <= 60) pow2_shift = 22 - ex;   // L = 2^(ex - 1)
+    }
     k_keys<T><<<grid_for(p->n, 256), 256, 0, s>>>(p->x, p->y, p->z, (const T *)p->h, (const T *)p->m, p->n,
-                                                  ctx->prm.curve, ctx->prm.dim, ctx->dcnt, keys, vals);
+                                                  ctx->prm.curve, ctx->prm.dim, pow2_shift, ctx->dcnt, keys, vals);
     SPH_CHECK_LAUNCH();
     return SPH_OK;
 }
