@@ -127,9 +127,11 @@ __global__ void __launch_bounds__(TM) k_infer_tc(const __nv_bfloat16 *__restrict
 
     const int tid = threadIdx.x, warp = tid >> 5;
     // weights: W2 as the B operand (row n = output unit, K = input unit), the rest FP32
-    for (int idx = tid; idx < H * H; idx += TM) {
-        const int n = idx / H, k = idx % H;
-        *reinterpret_cast<__nv_bfloat16 *>(sB + cm_off(n, k)) = wb[O_W2 + idx];
+    // eight consecutive K entries of a row are one 16-byte core-matrix row
+    // (O_W2 = 384 elements: 16-byte aligned)
+    for (int v = tid; v < H * H / 8; v += TM) {
+        const int n = v / (H / 8), k = 8 * (v % (H / 8));
+        *reinterpret_cast<uint4 *>(sB + cm_off(n, k)) = *reinterpret_cast<const uint4 *>(wb + O_W2 + n * H + k);
     }
     for (int k = tid; k < 320 + 64; k += TM) wf[k] = __bfloat162float(wb[O_W1 + k]);          // W1, b1
     for (int k = tid; k < 64 + 64 + 1; k += TM) wf[384 + k] = __bfloat162float(wb[O_B2 + k]);  // b2, W3, b3
