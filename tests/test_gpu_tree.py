@@ -152,3 +152,25 @@ def test_rebuild_of_nearly_sorted_particles(moved, curve):
     assert np.array_equal(h["u"], g["u"][perm])
     lb, _ = B.sph_export_leaves(ctx)
     assert lb[-1] == w.n and np.all(np.diff(lb) > 0)
+
+
+def test_fig1_quadtree_leaves():
+    """The ten particles of Fig. 1 (Sec. 2.1, tests/golden/fig1_quadtree.txt)
+    in the unit box at z = 0 with leaf_size 1: the library's order is the
+    figure's Z-order and its leaves are the figure's cells (level = digits
+    below the leading 1)."""
+    from helpers import fig1_quadtree
+    B = need_gpu()
+    labels, x, y, _, path = fig1_quadtree()
+    w = _cloud(len(labels), 0, True)
+    w.x, w.y, w.z = x, y, np.zeros_like(x)
+    w.params["leaf_size"] = 1
+    ctx = B.Context(w.params, w.n)
+    p = B.Particles.from_workload(w, fp64=True)
+    B.sph_build_tree(ctx, p)
+    g = p.numpy()
+    got = [labels[i] for i in g["id"]]
+    assert got == sorted(labels, key=lambda c: (path.index(c[:3]) if c[:3] in path else path.index(c[:2]), c))
+    lb, lv = B.sph_export_leaves(ctx)
+    assert np.array_equal(lb, np.arange(len(labels) + 1))
+    assert list(lv) == [len(c) - 1 for c in got]

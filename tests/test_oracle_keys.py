@@ -123,3 +123,28 @@ def test_leaf_levels_by_brute_force(orc, leaf_size):
     b = np.nonzero(start)[0]
     sizes = np.diff(np.append(b, keys.size))
     assert sizes.max() <= leaf_size
+
+
+def test_fig1_quadtree(orc):
+    """Sec. 2.1, Fig. 1 (tests/golden/fig1_quadtree.txt): with z = 0 every
+    3-bit level of a key is the figure's base-4 digit, so the leading 1 and
+    the octal digits below it spell the label of each particle's cell; the
+    particles sort in the figure's Z-order path; and refining until every
+    particle is alone in its cell (leaf_size 1) gives the figure's leaves and
+    subdivided cells."""
+    from helpers import fig1_quadtree
+    labels, x, y, refined, path = fig1_quadtree()
+    keys = orc.morton_keys(x, y, np.zeros_like(x), np.zeros(3), 1.0)
+    for lab, k in zip(labels, keys):
+        assert "1" + "".join(str((int(k) >> (63 - 3 * l)) & 7) for l in range(1, len(lab))) == lab
+    order = np.argsort(keys)
+    rank = {c: i for i, c in enumerate(path)}
+    seq = [rank[lab[:3]] if lab[:3] in rank else rank[lab[:2]] for lab in np.array(labels)[order]]
+    assert seq == sorted(seq)
+    sk = keys[order]
+    lv = orc.leaf_levels(sk, 1)
+    assert [len(lab) - 1 for lab in np.array(labels)[order]] == list(lv)
+    def label(k, level):
+        return "1" + "".join(str((int(k) >> (63 - 3 * l)) & 7) for l in range(1, level + 1))
+    inner = {label(k, a) for k, leaf in zip(sk, lv) for a in range(int(leaf))}
+    assert inner == set(refined)

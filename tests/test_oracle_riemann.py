@@ -90,3 +90,22 @@ def test_uniform_state_stays():
     assert ps == pytest.approx(2.0, rel=1e-15) and us == pytest.approx(0.3, rel=1e-15)
     r, u, p = riemann.sample(st, st, 1.4, np.linspace(-3, 3, 13))
     assert np.allclose(r, 0.7, rtol=1e-14) and np.allclose(u, 0.3, rtol=1e-14) and np.allclose(p, 2.0, rtol=1e-14)
+
+
+def test_sod_star_region_textbook_values():
+    """The star-region values of the Sod problem as printed to five decimals
+    in Toro's textbook (tests/golden/sod_star_region.txt)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sod_star_region.txt")
+    ref = {}
+    with open(path) as f:
+        for line in f:
+            t = line.split()
+            if t and not t[0].startswith("#"):
+                ref[t[0]] = float(t[1])
+    p, u = riemann.star_state(SOD_L, SOD_R, GAMMA)
+    rl = riemann.sample(SOD_L, SOD_R, GAMMA, np.array([u - 1e-9]))[0][0]
+    rr = riemann.sample(SOD_L, SOD_R, GAMMA, np.array([u + 1e-9]))[0][0]
+    got = {"p_star": p, "u_star": u, "rho_star_L": rl, "rho_star_R": rr}
+    for k, v in ref.items():
+        assert abs(got[k] - v) <= 5e-6, (k, got[k], v)

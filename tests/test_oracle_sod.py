@@ -73,3 +73,39 @@ def test_conservation_in_1d(orc):
     power = np.sum(w.m * (w.vx * f.ax + f.dudt))
     assert abs(power) < 10 * eps * np.sum(w.m * (np.abs(w.vx) * f.S_a + f.S_u))
     assert np.max(np.abs(f.ax)) > 0
+
+
+def _golden_sod():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sod_initial_state.txt")
+    rows = {}
+    with open(path) as f:
+        for line in f:
+            t = line.split()
+            if t and not t[0].startswith("#"):
+                rows[t[0]] = [float(v) for v in t[1:]]
+    return rows
+
+
+def test_sod_state_is_the_papers(orc):
+    """The workload's two states are those printed in Sec. 3
+    (tests/golden/sod_initial_state.txt), and the oracle reads them back from
+    the particles: density from the summation (up to the lattice error of M4
+    at eta = 1.2), velocity zero, and pressure from the EOS P = (gamma-1) rho u."""
+    g = _golden_sod()
+    assert tuple(g["left"][2:]) == inputs.SOD_LEFT and tuple(g["right"][2:]) == inputs.SOD_RIGHT
+    w = inputs.sod(int(g["particles"][0]) // 10)
+    p = oracle_params(orc, w)
+    d = orc.density(p, w.x, w.y, w.z, w.m, w.h)
+    P, _ = orc.eos(p.gamma, d.rho, w.u)
+    for side in ("left", "right"):
+        x0, x1, rho, v, pr = g[side]
+        inner = (w.x > x0 + 0.1) & (w.x < x1 - 0.1)
+        assert inner.sum() > 50
+        assert np.max(np.abs(d.rho[inner] / rho - 1)) < 5e-3
+        assert np.max(np.abs(P[inner] / pr - 1)) < 5e-3
+        assert np.all(w.vx[inner] == v)
+    # at full size the tube holds the paper's particle count, up to rounding
+    # the two states' counts to a spacing ratio of 8 (8,888 + 1,111)
+    w = inputs.sod(int(g["particles"][0]))
+    assert abs(np.count_nonzero(w.x < 1.0) - int(g["particles"][0])) <= 1
