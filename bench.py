@@ -249,25 +249,22 @@ def run_sph(args):
     O = summarize(ms_o, st_o)
     P = summarize(ms_p, st_p)
 
-    # end to end through the C ABI with host buffers: H2D of the state from
-    # pinned memory, the step, D2H of the state, every step
-    fields = ["x", "y", "z", "nnb", "id"] + B._FIELDS
-    host = {f: torch.empty_like(getattr(p, f), device="cpu").pin_memory() for f in fields}
+    # end to end through the C ABI with host buffers: H2D of the whole state
+    # (every particle array, one slab) from pinned memory, the step, D2H of
+    # the whole state, every step
+    host = torch.empty_like(p.slab, device="cpu").pin_memory()
     restore()
-    for f in fields:
-        host[f].copy_(getattr(p, f))
-    h2d = sum(host[f].numel() * host[f].element_size() for f in fields)
+    host.copy_(p.slab)
+    h2d = host.numel()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e_inter = 0
     e0.record(stream)
     for k in range(args.steps):
-        for f in fields:
-            getattr(p, f).copy_(host[f], non_blocking=True)
+        p.slab.copy_(host, non_blocking=True)
         s = B.sph_step(ctx, p, w.dt, use_hnet=B.SPH_HNET_SEED)
         e_inter += s["density"]["interactions"] + s["forces"]["interactions"]
-        for f in fields:
-            host[f].copy_(getattr(p, f), non_blocking=True)
+        host.copy_(p.slab, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_s = e0.elapsed_time(e1) / 1e3

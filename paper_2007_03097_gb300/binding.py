@@ -213,20 +213,31 @@ class Context:
 
 
 class Particles:
-    """Device SoA particle arrays (torch tensors) and the matching C struct."""
+    """Device SoA particle arrays (torch tensors) and the matching C struct.
+
+    All arrays are views into one device slab (``self.slab``, bytes), each
+    starting on a 256-byte boundary, so that the whole state moves between
+    host and device in one copy each way."""
+
+    ALIGN = 256
 
     def __init__(self, n: int, fp64: bool, device="cuda"):
         self.n = int(n)
         self.fp64 = fp64
         self.dtype = torch.float64 if fp64 else torch.float32
         dev = torch.device(device)
-        self.x = torch.zeros(n, dtype=torch.float64, device=dev)
-        self.y = torch.zeros(n, dtype=torch.float64, device=dev)
-        self.z = torch.zeros(n, dtype=torch.float64, device=dev)
-        for f in _FIELDS:
-            setattr(self, f, torch.zeros(n, dtype=self.dtype, device=dev))
-        self.nnb = torch.zeros(n, dtype=torch.int32, device=dev)
-        self.id = torch.arange(n, dtype=torch.int32, device=dev)
+        layout = [(f, torch.float64) for f in ("x", "y", "z")] + [(f, self.dtype) for f in _FIELDS] + \
+                 [("nnb", torch.int32), ("id", torch.int32)]
+        offs, off = [], 0
+        for _, dt in layout:
+            offs.append(off)
+            nbytes = self.n * torch.empty(0, dtype=dt).element_size()
+            off += (nbytes + self.ALIGN - 1) // self.ALIGN * self.ALIGN
+        self.slab = torch.zeros(max(off, self.ALIGN), dtype=torch.uint8, device=dev)
+        for (f, dt), o in zip(layout, offs):
+            nbytes = self.n * torch.empty(0, dtype=dt).element_size()
+            setattr(self, f, self.slab[o:o + nbytes].view(dt))
+        self.id.copy_(torch.arange(n, dtype=torch.int32, device=dev))
 
     @classmethod
     def from_workload(cls, w, fp64: bool, device="cuda") -> "Particles":
