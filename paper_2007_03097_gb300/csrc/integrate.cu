@@ -76,20 +76,25 @@ __global__ void k_kick(T *__restrict__ vx, T *__restrict__ vy, T *__restrict__ v
     else u[i] = u[i] + du[i] * hdt;
 }
 
-constexpr int NT = 9;   // 8 sums + 1 min
+constexpr int NT = 9;    // 8 sums + 1 min
+constexpr int TB = 256;  // threads per block of the partial-totals kernel
 
 // Per-block partial totals in FP64 (fixed grid, fixed order: deterministic).
+// FP64 runs at 1/64 of the FP32 rate, so the kernel spends few FP64
+// instructions: the quotient h / v_sig is formed only where it can lower the
+// running minimum mn, i.e. where h <= mn v_sig (tested against
+// mn (1 + 2^-40) v_sig, which rounding cannot push below the exact mn v_sig),
+// and the per-thread sums meet in shared memory, warp k reducing quantity k.
 template <typename T>
-__global__ void k_totals_partial(const T *__restrict__ m, const T *__restrict__ vx, const T *__restrict__ vy,
-                                 const T *__restrict__ vz, const T *__restrict__ u, const T *__restrict__ ax,
-                                 const T *__restrict__ ay, const T *__restrict__ az, const T *__restrict__ du,
-                                 const T *__restrict__ pvx, const T *__restrict__ pvy,
-                                 const T *__restrict__ pvz, const T *__restrict__ h,
-                                 const T *__restrict__ vsig, int64_t n, double *__restrict__ part, int thermo)
+__global__ void __launch_bounds__(TB) k_totals_partial(
+    const T *__restrict__ m, const T *__restrict__ vx, const T *__restrict__ vy, const T *__restrict__ vz,
+    const T *__restrict__ u, const T *__restrict__ ax, const T *__restrict__ ay, const T *__restrict__ az,
+    const T *__restrict__ du, const T *__restrict__ pvx, const T *__restrict__ pvy, const T *__restrict__ pvz,
+    const T *__restrict__ h, const T *__restrict__ vsig, int64_t n, double *__restrict__ part, int thermo)
 {
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    double mn = DBL_MAX;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double mn = DBL_MAX, mnx = __longlong_as_double(0x7ff0000000000000ll);   // +inf
+    for (int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x; i < n; i += (int64_t)gridDim.x * TB) {
         const double mi = m[i], vxi = vx[i], vyi = vy[i], vzi = vz[i];
         const double axi = ax[i], ayi = ay[i], azi = az[i];
         acc[0] += mi * vxi; acc[1] += mi * vyi; acc[2] += mi * vzi;
@@ -97,22 +102,27 @@ __global__ void k_totals_partial(const T *__restrict__ m, const T *__restrict__ 
         acc[6] += mi * (0.5 * (vxi * vxi + vyi * vyi + vzi * vzi) + (double)u[i]);
         const double wx = pvx ? (double)pvx[i] : vxi, wy = pvx ? (double)pvy[i] : vyi, wz = pvx ? (double)pvz[i] : vzi;
         acc[7] += thermo ? mi * (double)du[i] : mi * (wx * axi + wy * ayi + wz * azi + (double)du[i]);
-        if (vsig) { const double v = vsig[i]; if (v > 0) mn = fmin(mn, (double)h[i] / v); }
+        if (vsig) {
+            const double v = vsig[i], hi = h[i];
+            if (v > 0 && hi <= mnx * v) {
+                mn = fmin(mn, hi / v);
+                mnx = mn * (1.0 + 0x1p-40);
+            }
+        }
     }
-    __shared__ double s[NT][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int k = 0; k < 8; ++k) {
-        double v = acc[k];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) s[k][warp] = v;
-    }
-    for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-    if (lane == 0) s[8][warp] = mn;
+    __shared__ double s[NT][TB];
+    for (int k = 0; k < 8; ++k) s[k][threadIdx.x] = acc[k];
+    s[8][threadIdx.x] = mn;
     __syncthreads();
-    if (threadIdx.x < NT) {
-        double v = s[threadIdx.x][0];
-        for (int w = 1; w < nw; ++w) v = threadIdx.x < 8 ? v + s[threadIdx.x][w] : fmin(v, s[threadIdx.x][w]);
-        part[blockIdx.x * NT + threadIdx.x] = v;
+    const int lane = threadIdx.x & 31;
+    for (int k = threadIdx.x >> 5; k < NT; k += TB / 32) {
+        double v = s[k][lane];
+        for (int j = lane + 32; j < TB; j += 32) v = k < 8 ? v + s[k][j] : fmin(v, s[k][j]);
+        for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = k < 8 ? v + w : fmin(v, w);
+        }
+        if (lane == 0) part[blockIdx.x * NT + k] = v;
     }
 }
 
@@ -172,7 +182,7 @@ int totals_impl(sph_ctx *ctx, const sph_particles *p, const void *pvx, const voi
                 const void *u, cudaStream_t s)
 {
     const int nb = ctx->red_blocks;
-    k_totals_partial<T><<<nb, 256, 0, s>>>((const T *)p->m, (const T *)p->vx, (const T *)p->vy, (const T *)p->vz,
+    k_totals_partial<T><<<nb, TB, 0, s>>>((const T *)p->m, (const T *)p->vx, (const T *)p->vy, (const T *)p->vz,
                                            (const T *)u, (const T *)p->ax, (const T *)p->ay, (const T *)p->az,
                                            (const T *)p->dudt, (const T *)pvx, (const T *)pvy, (const T *)pvz,
                                            (const T *)p->h, (const T *)p->vsig, p->n, ctx->red,

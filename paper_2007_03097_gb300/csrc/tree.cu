@@ -570,8 +570,10 @@ __global__ void __launch_bounds__(NS_THREADS) k_ns_compact(const uint64_t *__res
                                                            const NsTile *__restrict__ t,
                                                            const uint8_t *__restrict__ flag,
                                                            uint64_t *__restrict__ mk, uint32_t *__restrict__ mi,
-                                                           int32_t *__restrict__ mpos)
+                                                           int32_t *__restrict__ mpos, const DevCounters *cnt,
+                                                           int limit)
 {
+    if (cnt->ns_total > limit) return;            // the full sort follows
     __shared__ int sw[NS_THREADS / 32];
     const int64_t b0 = (int64_t)blockIdx.x * NS_TILE + NS_PER * threadIdx.x;
     int f[NS_PER], c = 0;
@@ -604,14 +606,20 @@ __global__ void __launch_bounds__(NS_THREADS) k_ns_compact(const uint64_t *__res
 }
 
 // rank of each misplaced element among the misplaced ones (equal (key, id)
-// pairs ordered by position); it goes to the rank-th misplaced position
+// pairs ordered by position); it goes to the rank-th misplaced position.
+// The grid covers `limit` elements; the count m = cnt->ns_total is read on
+// the device, and above the limit nothing is done (the full sort follows).
 constexpr int NS_RANK_T = 256;
 __global__ void __launch_bounds__(NS_RANK_T) k_ns_rank(const uint64_t *__restrict__ mk,
                                                        const uint32_t *__restrict__ mi,
-                                                       const int32_t *__restrict__ mpos, int m,
+                                                       const int32_t *__restrict__ mpos,
+                                                       const DevCounters *cnt, int limit,
                                                        uint64_t *__restrict__ keys_out,
                                                        uint32_t *__restrict__ src_pos)
 {
+    const long long mt = cnt->ns_total;
+    if (mt > limit) return;                       // uniform over the block
+    const int m = (int)mt;
     __shared__ uint64_t sk[NS_RANK_T];
     __shared__ uint32_t si[NS_RANK_T];
     const int e = blockIdx.x * NS_RANK_T + threadIdx.x;
@@ -639,10 +647,12 @@ __global__ void __launch_bounds__(NS_RANK_T) k_ns_rank(const uint64_t *__restric
 }
 
 // move only the misplaced particles: gather into scratch, then put back
-__global__ void k_ns_gather(FieldTable t, const uint32_t *__restrict__ src_pos, int m)
+// (grids over `limit` elements, m read on the device as in k_ns_rank)
+__global__ void k_ns_gather(FieldTable t, const uint32_t *__restrict__ src_pos, const DevCounters *cnt, int limit)
 {
+    const long long m = cnt->ns_total;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= m) return;
+    if (m > limit || k >= m) return;
     const uint32_t p = src_pos[k];
     for (int f = 0; f < t.nf; ++f) {
         if (t.size[f] == 8) ((double *)t.dst[f])[k] = ((const double *)t.src[f])[p];
@@ -650,10 +660,11 @@ __global__ void k_ns_gather(FieldTable t, const uint32_t *__restrict__ src_pos, 
     }
 }
 
-__global__ void k_ns_put(FieldTable t, const int32_t *__restrict__ mpos, int m)
+__global__ void k_ns_put(FieldTable t, const int32_t *__restrict__ mpos, const DevCounters *cnt, int limit)
 {
+    const long long m = cnt->ns_total;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= m) return;
+    if (m > limit || k >= m) return;
     const int32_t d = mpos[k];
     for (int f = 0; f < t.nf; ++f) {
         if (t.size[f] == 8) ((double *)t.src[f])[d] = ((const double *)t.dst[f])[k];
@@ -962,78 +973,53 @@ int keys_impl(sph_ctx *ctx, const sph_particles *p, uint64_t *keys, uint32_t *va
     return SPH_OK;
 }
 
-// The near-sorted path: *moved = number of particles it moved (0: already in
-// key order), or -1 when more than the limit are misplaced and the full sort
-// is needed (nothing has been moved then).
-int near_sorted(sph_ctx *ctx, sph_particles *p, const FieldTable &t, int64_t *moved, cudaStream_t s)
+// The near-sorted path, launched without a host synchronisation: the
+// detection counts the misplaced particles into cnt->ns_total, and when there
+// are at most `limit` of them the same launches move them into key order
+// (their kernels read the count on the device).  Above the limit nothing
+// moves; the caller learns which case it was at its next synchronisation.
+void near_sorted(sph_ctx *ctx, sph_particles *p, const FieldTable &t, int limit, cudaStream_t s)
 {
     const int64_t n = p->n;
-    *moved = -1;
     const int nt = (int)((n + NS_TILE - 1) / NS_TILE);
     k_ns_tiles<<<nt, NS_THREADS, 0, s>>>(ctx->key_a, p->id, n, ctx->ns_tiles);
-    SPH_CHECK_LAUNCH();
     k_ns_prefix<<<1, 1024, 0, s>>>(ctx->ns_tiles, nt);
-    SPH_CHECK_LAUNCH();
     k_ns_mark<<<nt, NS_THREADS, 0, s>>>(ctx->key_a, p->id, n, ctx->ns_tiles, ctx->dlev);
-    SPH_CHECK_LAUNCH();
     k_ns_offsets<<<1, 1024, 0, s>>>(ctx->ns_tiles, nt, ctx->dcnt);
+    uint64_t *mk = ctx->key_b;
+    uint32_t *mi = ctx->val_b;
+    int32_t *mpos = ctx->itmp0;
+    uint32_t *src_pos = (uint32_t *)ctx->itmp1;
+    k_ns_compact<<<nt, NS_THREADS, 0, s>>>(ctx->key_a, p->id, n, ctx->ns_tiles, ctx->dlev, mk, mi, mpos, ctx->dcnt,
+                                            limit);
+    k_ns_rank<<<(limit + NS_RANK_T - 1) / NS_RANK_T, NS_RANK_T, 0, s>>>(mk, mi, mpos, ctx->dcnt, limit, ctx->key_a,
+                                                                         src_pos);
+    k_ns_gather<<<grid_for(limit, 256), 256, 0, s>>>(t, src_pos, ctx->dcnt, limit);
+    k_ns_put<<<grid_for(limit, 256), 256, 0, s>>>(t, mpos, ctx->dcnt, limit);
+}
+
+// full sort, then permute every particle array into key order
+int full_sort(sph_ctx *ctx, sph_particles *p, const FieldTable &t, cudaStream_t s)
+{
+    const int64_t n = p->n;
+    SPH_TRY(radix_sort(ctx, n, s));
+    k_fix_ties<<<grid_for(n, 256), 256, 0, s>>>(ctx->key_a, ctx->val_a, p->id, n, ctx->dcnt);
     SPH_CHECK_LAUNCH();
-    SPH_TRY(sync_counters(ctx, s));
-    const int64_t m = ctx->hcnt->ns_total;
-    const int64_t limit = std::min<int64_t>(NS_LIMIT, std::max<int64_t>(n / 4, 1024));
-    if (m > limit) return SPH_OK;
-    if (m > 0) {
-        uint64_t *mk = ctx->key_b;
-        uint32_t *mi = ctx->val_b;
-        int32_t *mpos = ctx->itmp0;
-        uint32_t *src_pos = (uint32_t *)ctx->itmp1;
-        k_ns_compact<<<nt, NS_THREADS, 0, s>>>(ctx->key_a, p->id, n, ctx->ns_tiles, ctx->dlev, mk, mi, mpos);
-        SPH_CHECK_LAUNCH();
-        const int mi32 = (int)m;
-        k_ns_rank<<<(mi32 + NS_RANK_T - 1) / NS_RANK_T, NS_RANK_T, 0, s>>>(mk, mi, mpos, mi32, ctx->key_a, src_pos);
-        SPH_CHECK_LAUNCH();
-        k_ns_gather<<<grid_for(m, 256), 256, 0, s>>>(t, src_pos, mi32);
-        SPH_CHECK_LAUNCH();
-        k_ns_put<<<grid_for(m, 256), 256, 0, s>>>(t, mpos, mi32);
-        SPH_CHECK_LAUNCH();
-    }
-    *moved = m;
+    k_gather<<<grid_for(n, 256), 256, 0, s>>>(t, ctx->val_a, n);
+    SPH_CHECK_LAUNCH();
+    k_copy_back<<<grid_for(n, 256), 256, 0, s>>>(t, n);
+    SPH_CHECK_LAUNCH();
     return SPH_OK;
 }
 
+// octree leaves and target groups of the keys in key_a (in bounds for any
+// order of the keys), then one synchronisation for the counts
 template <typename T>
-int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
+int leaves_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
 {
     const int64_t n = p->n;
-    ctx->tree_valid = false;
-    SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->err, 0, sizeof(uint32_t), s));
-    SPH_TRY(keys_impl<T>(ctx, p, ctx->key_a, ctx->val_a, s));
-    FieldTable t = make_table<T>(ctx, p);
-    int64_t m = -1;
-    // after two full sorts in a row (most keys displaced every step) the
-    // detection of a nearly sorted order is skipped for seven builds, then
-    // tried again
-    if (ctx->ns_skip > 0) {
-        --ctx->ns_skip;
-    } else {
-        SPH_TRY(near_sorted(ctx, p, t, &m, s));
-        ctx->ns_full_streak = m < 0 ? ctx->ns_full_streak + 1 : 0;
-        if (ctx->ns_full_streak >= 2) ctx->ns_skip = 7;
-    }
-    if (m < 0) {
-        // full sort, then permute every particle array into key order
-        SPH_TRY(radix_sort(ctx, n, s));
-        k_fix_ties<<<grid_for(n, 256), 256, 0, s>>>(ctx->key_a, ctx->val_a, p->id, n, ctx->dcnt);
-        SPH_CHECK_LAUNCH();
-        k_gather<<<grid_for(n, 256), 256, 0, s>>>(t, ctx->val_a, n);
-        SPH_CHECK_LAUNCH();
-        k_copy_back<<<grid_for(n, 256), 256, 0, s>>>(t, n);
-        SPH_CHECK_LAUNCH();
-    }
-    ctx->ns_moved = m;
     k_pack_pos<T><<<grid_for(n, 256), 256, 0, s>>>(p->x, p->y, p->z, (const T *)p->m, n, ctx->srcA, ctx->srcB);
     SPH_CHECK_LAUNCH();
-    // octree leaves and target groups
     k_dlev<<<grid_for(n, 256), 256, 0, s>>>(ctx->key_a, n, ctx->dlev);
     SPH_CHECK_LAUNCH();
     k_leaf_level<<<grid_for(n, 128), 128, 0, s>>>(ctx->dlev, n, ctx->prm.leaf_size, ctx->plev, ctx->dcnt);
@@ -1050,7 +1036,44 @@ int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
     k_emit<<<grid_for(n, 256), 256, 0, s>>>(ls, gs, lidx, gidx, ctx->plev, n, ctx->leaf_begin, ctx->leaf_level,
                                             ctx->group_begin, ctx->dcnt);
     SPH_CHECK_LAUNCH();
-    SPH_TRY(sync_counters(ctx, s));
+    return sync_counters(ctx, s);
+}
+
+template <typename T>
+int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
+{
+    const int64_t n = p->n;
+    ctx->tree_valid = false;
+    SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->err, 0, sizeof(uint32_t), s));
+    SPH_TRY(keys_impl<T>(ctx, p, ctx->key_a, ctx->val_a, s));
+    FieldTable t = make_table<T>(ctx, p);
+    // after two full sorts in a row (most keys displaced every step) the
+    // detection of a nearly sorted order is skipped for seven builds, then
+    // tried again
+    int limit = -1;                                // >= 0: the near-sorted path was launched
+    if (ctx->ns_skip > 0) {
+        --ctx->ns_skip;
+    } else {
+        limit = (int)std::min<int64_t>(NS_LIMIT, std::max<int64_t>(n / 4, 1024));
+        near_sorted(ctx, p, t, limit, s);
+        SPH_CHECK_LAUNCH();
+    }
+    if (limit < 0) SPH_TRY(full_sort(ctx, p, t, s));
+    SPH_TRY(leaves_impl<T>(ctx, p, s));
+    int64_t m = -1;
+    if (limit >= 0) {
+        m = ctx->hcnt->ns_total <= limit ? ctx->hcnt->ns_total : -1;
+        if (m < 0 && !(ctx->hcnt->err & (ERRB_NONFINITE | ERRB_OFF_AXIS))) {
+            // too many misplaced particles: nothing was moved and the leaves
+            // above describe the unsorted keys; sort in full and build again
+            SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->err, 0, sizeof(uint32_t), s));
+            SPH_TRY(full_sort(ctx, p, t, s));
+            SPH_TRY(leaves_impl<T>(ctx, p, s));
+        }
+        ctx->ns_full_streak = m < 0 ? ctx->ns_full_streak + 1 : 0;
+        if (ctx->ns_full_streak >= 2) ctx->ns_skip = 7;
+    }
+    ctx->ns_moved = m;
     const uint32_t err = ctx->hcnt->err;
     for (int d = 0; d < 4; ++d) ctx->dom[d] = ctx->hcnt->dom[d];
     if (err & ERRB_NONFINITE)
