@@ -132,7 +132,7 @@ typedef struct {
  * id is any set of unique 32-bit labels; sph_build_tree permutes it with the
  * particles so the caller can map results back to its own order.          */
 typedef struct {
-    int64_t n;
+    int64_t n;                       /* 1 <= n <= n_max (0: SPH_ERR_ARG)         */
     double *x, *y, *z;
     void *vx, *vy, *vz;
     void *m, *h, *u;

@@ -141,3 +141,19 @@ def test_single_particle():
     assert p.nnb.item() == 0
     assert p.rho.item() == pytest.approx(w.m[0] / (np.pi * w.h[0] ** 3), rel=1e-14)
     assert p.ax.item() == 0.0
+
+
+def test_empty_input_rejected_and_context_usable():
+    """n = 0 is an argument error (every call needs 1 <= n <= n_max); the
+    context then serves a valid particle set."""
+    B = need_gpu()
+    w = inputs.lattice(4)
+    ctx = B.Context(w.params, w.n)
+    empty = B.Particles(0, fp64=True)
+    for call in (B.sph_build_tree, B.sph_density, B.sph_forces):
+        with pytest.raises(B.SphError) as e:
+            call(ctx, empty)
+        assert e.value.code in (B.SPH_ERR_ARG, B.SPH_ERR_STATE)
+    p = B.Particles.from_workload(w, fp64=True)
+    B.sph_build_tree(ctx, p)
+    assert B.sph_density(ctx, p)["status"] == 0
