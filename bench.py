@@ -240,9 +240,16 @@ def run_sph(args):
                     density_interactions=sum(s["density"]["interactions"] for s in st),
                     force_interactions=sum(s["forces"]["interactions"] for s in st),
                     density_launches=sum(s["density"]["sweeps"] for s in st),
+                    list_builds=sum(s["density"]["list_builds"] for s in st),
                     launches=sum(s["launches"] for s in st),
                     hnet_fallback=sum(s["hnet_fallback"] for s in st),
                     hnet_loss=st[-1]["hnet_loss"], ms_tree=sum(s["ms_tree"] for s in st) / len(st),
+                    # mean per-step phase times from the library's events: kick/drift and
+                    # tree, h seed, density iteration (lists + sweeps), forces and the rest
+                    ms_phase={k: sum(f(s) for s in st) / len(st) for k, f in (
+                        ("tree", lambda s: s["ms_tree"]), ("hnet", lambda s: s["ms_hnet"]),
+                        ("density", lambda s: s["density"]["ms"]), ("forces_kick_totals", lambda s: s["forces"]["ms"]),
+                        ("total", lambda s: s["ms_total"]))},
                     tree_moved=[s["tree_moved"] for s in st])
 
     L = summarize(ms_l, st_l)

@@ -347,8 +347,7 @@ int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet, sph_step_s
     const void *seed = nullptr;
     SPH_TRY(copy_field(ctx, ctx->hold, p->h, p->n, s));
     if (seed_net) {
-        SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->hnet_fallback, 0, sizeof(int32_t), s));
-        SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->hnet_err, 0, sizeof(uint32_t), s));
+        // hnet_fallback and hnet_err were zeroed by the kick-drift kernel
         SPH_TRY(hnet_seed_from_fields(ctx, p, dt, train_net, ctx->hseed, s));
         seed = ctx->hseed;
         local.hnet_used = 1;

@@ -18,9 +18,12 @@ __global__ void k_kick_drift(double *__restrict__ x, double *__restrict__ y, dou
                              T *__restrict__ vx, T *__restrict__ vy, T *__restrict__ vz, T *__restrict__ u,
                              const T *__restrict__ ax, const T *__restrict__ ay, const T *__restrict__ az,
                              const T *__restrict__ du, int64_t n, double dt, int periodic, double3 lo,
-                             double3 hi, int thermo)
+                             double3 hi, int thermo, DevCounters *cnt)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // the step's h-predictor counters start at zero (this is the step's
+    // first kernel; nothing else writes them before the seeding)
+    if (i == 0) { cnt->hnet_fallback = 0; cnt->hnet_err = 0; }
     if (i >= n) return;
     const T hdt = (T)(0.5 * dt);
     const T vx0 = vx[i], vy0 = vy[i], vz0 = vz[i];
@@ -151,7 +154,7 @@ int kd_impl(sph_ctx *ctx, sph_particles *p, double dt, cudaStream_t s)
     k_kick_drift<T><<<grid_for(p->n, 256), 256, 0, s>>>(
         p->x, p->y, p->z, (T *)p->vx, (T *)p->vy, (T *)p->vz, (T *)p->u, (const T *)p->ax, (const T *)p->ay,
         (const T *)p->az, (const T *)p->dudt, p->n, dt, q.periodic, make_double3(q.box_lo[0], q.box_lo[1], q.box_lo[2]),
-        make_double3(q.box_hi[0], q.box_hi[1], q.box_hi[2]), q.energy == SPH_ENERGY_TOTAL);
+        make_double3(q.box_hi[0], q.box_hi[1], q.box_hi[2]), q.energy == SPH_ENERGY_TOTAL, ctx->dcnt);
     SPH_CHECK_LAUNCH();
     return SPH_OK;
 }
