@@ -1,5 +1,5 @@
 // h-predictor network (not part of the paper's method; it only seeds the
-// h-rho iteration of Eq. 9, which stays the judge of the converged h):
+// h-rho iteration of Eq. 9, which stays the arbiter of the converged h):
 //   y = W3 silu(W2 silu(W1 f + b1) + b2) + b3,  5 -> 64 -> 64 -> 1,
 // BF16 weights read by the kernels, FP32 master weights and Adam moments,
 // FP32 activations and accumulation (inference: layer 2 on the tensor cores).  The prediction of log(h_next / h) is
