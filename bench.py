@@ -322,6 +322,12 @@ def run_sph(args):
     lists["slots_per_particle"] = lists["slots_used"] / w.n
     nl, ng = B.sph_tree_info(ctx)
     lists["union_per_group"] = lists["union_used"] / max(ng, 1)
+    # candidates against accepted pairs: every lane of a group visits its
+    # group's list width in the force pass, so the slots used are the
+    # candidate slots of one pass
+    pairs = L["force_interactions"] / max(len(ms_l), 1)
+    lists["force_pairs_per_pass"] = pairs
+    lists["candidate_slots_per_accepted_pair"] = lists["slots_used"] / max(pairs, 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, seconds=12.0, label=args.workload)
@@ -366,7 +372,9 @@ def _oracle_sample(w, n_targets, seed=7):
     P, c = oracle.eos(op.gamma, rho, w.u)
     f = oracle.forces(op, w.x, w.y, w.z, w.vx, w.vy, w.vz, w.m, h, rho, P, c, targets=t)
     dt = time.perf_counter() - t0
-    return int(d.pairs[t].sum()) + f.npairs, dt, t.size, oracle.num_threads()
+    # brute force: every evaluation of a target tests all n sources
+    tests = (int(d.sweeps[t].sum()) + t.size) * w.n
+    return int(d.pairs[t].sum()) + f.npairs, dt, t.size, oracle.num_threads(), tests
 
 
 def cpu_baseline(w, seconds=12.0, label="sedov"):
@@ -374,11 +382,12 @@ def cpu_baseline(w, seconds=12.0, label="sedov"):
     particles sized for about `seconds` of work; interactions/s."""
     nt2 = 64
     for _ in range(3):                        # grow the sample until it takes about `seconds`
-        inter, dt, nt, cores = _oracle_sample(w, nt2)
+        inter, dt, nt, cores, tests = _oracle_sample(w, nt2)
         if dt >= 0.5 * seconds or nt2 >= w.n:
             break
         nt2 = min(w.n, int(nt2 * seconds / max(dt, 1e-3)))
     return {"value": inter / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "candidate_tests_per_s": tests / dt,
             "sample": f"{nt} random targets of the {w.n}-particle {label} state, brute force over all sources: "
                       f"h-rho iteration + force pass, {dt:.1f} s"}
 
@@ -397,7 +406,7 @@ def run_reference(args):
         _oracle_sample(w, per_step, seed=1)
     inter, secs, nt, cores = 0, 0.0, 0, 1
     for k in range(args.steps):
-        i, dt, nt, cores = _oracle_sample(w, per_step, seed=100 + k)
+        i, dt, nt, cores, _ = _oracle_sample(w, per_step, seed=100 + k)
         inter += i
         secs += dt
     v = inter / secs
