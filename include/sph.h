@@ -298,6 +298,15 @@ int sph_hnet_features(sph_ctx *ctx, const sph_particles *p, double dt, float *fe
  * not complete within 1 s (the kernel then frees its tensor memory and
  * returns). */
 int sph_hnet_infer(sph_ctx *ctx, const float *feats, int64_t nb, float *y, void *stream);
+/* the seed of the h iteration that sph_step takes with SPH_HNET_SEED, from
+ * the particle fields in one kernel (features, network, exponential):
+ * h_seed[a] = h_a exp(s_a) with s_a = f3 y(f_a) where s_a is finite and
+ * |s_a| <= ln 2, else h_a (a fallback).  h_seed: device, n entries of the
+ * context's float type (double in SPH_FP64, float in SPH_MIXED), caller-owned.
+ * *fallbacks (host, may be NULL) = the particles that kept h.  Synchronises
+ * the stream; SPH_ERR_CUDA as for sph_hnet_infer. */
+int sph_hnet_seed(sph_ctx *ctx, const sph_particles *p, double dt, void *h_seed, int64_t *fallbacks,
+                  void *stream);
 /* loss = mean (f3 y - t)^2 and its gradient (host, SPH_HNET_NPARAM) at the
  * BF16 weights, FP32 accumulation; no update. */
 int sph_hnet_grad(sph_ctx *ctx, const float *feats, const float *target, int64_t nb,

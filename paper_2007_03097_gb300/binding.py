@@ -81,7 +81,7 @@ class sph_step_stats(_c.Structure):
 EXPORTED = ["sph_create", "sph_destroy", "sph_set_params", "sph_last_error", "sph_version", "sph_build_tree",
             "sph_density", "sph_forces", "sph_step", "sph_totals", "sph_morton_keys", "sph_sort_keys",
             "sph_tree_info", "sph_list_info", "sph_export_leaves", "sph_neighbors", "sph_hnet_set_weights",
-            "sph_hnet_get_weights", "sph_hnet_features", "sph_hnet_infer", "sph_hnet_grad",
+            "sph_hnet_get_weights", "sph_hnet_features", "sph_hnet_infer", "sph_hnet_seed", "sph_hnet_grad",
             "sph_hnet_train_step", "sph_sort_keys_noalloc"]
 SPH_SORT_NOALLOC_MAX = 262144
 
@@ -122,6 +122,7 @@ def load(path: str | None = None):
         "sph_hnet_get_weights": ([V, V, I64], I32),
         "sph_hnet_features": ([V, _c.POINTER(sph_particles), _c.c_double, V, V], I32),
         "sph_hnet_infer": ([V, V, I64, V, V], I32),
+        "sph_hnet_seed": ([V, _c.POINTER(sph_particles), _c.c_double, V, _c.POINTER(I64), V], I32),
         "sph_hnet_grad": ([V, V, V, I64, V, V, V], I32),
         "sph_hnet_train_step": ([V, V, V, I64, _c.c_float, V, V], I32),
         "sph_sort_keys_noalloc": ([I64, V, V, V, V], I32),
@@ -428,6 +429,18 @@ def sph_hnet_infer(ctx: Context, feats: torch.Tensor, stream=None) -> torch.Tens
     y = torch.empty(feats.shape[0], dtype=torch.float32, device=feats.device)
     _check(ctx, load().sph_hnet_infer(ctx.handle, feats.data_ptr(), feats.shape[0], y.data_ptr(), _stream(stream)))
     return y
+
+
+def sph_hnet_seed(ctx: Context, p: Particles, dt: float, stream=None):
+    """The h seed sph_step takes with SPH_HNET_SEED (device tensor of the
+    particles' float type) and the number of particles that kept h."""
+    _match(ctx, p)
+    s = p.struct()
+    seed = torch.empty(p.n, dtype=p.dtype, device=p.x.device)
+    fb = _c.c_int64()
+    _check(ctx, load().sph_hnet_seed(ctx.handle, _c.byref(s), float(dt), seed.data_ptr(), _c.byref(fb),
+                                     _stream(stream)))
+    return seed, int(fb.value)
 
 
 def sph_hnet_grad(ctx: Context, feats: torch.Tensor, target: torch.Tensor, stream=None):

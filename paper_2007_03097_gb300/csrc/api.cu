@@ -542,6 +542,23 @@ int sph_hnet_infer(sph_ctx *ctx, const float *feats, int64_t nb, float *y, void 
     return SPH_OK;
 }
 
+int sph_hnet_seed(sph_ctx *ctx, const sph_particles *p, double dt, void *h_seed, int64_t *fallbacks, void *stream)
+{
+    SPH_TRY(check_particles(ctx, p, false));
+    if (!h_seed) return sph_fail(ctx, SPH_ERR_ARG, "h_seed is NULL");
+    if ((reinterpret_cast<uintptr_t>(h_seed) & 15u) != 0) return sph_fail(ctx, SPH_ERR_ARG, "h_seed must be 16-byte aligned");
+    cudaStream_t s = S(stream);
+    SPH_TRY(join_side(ctx, s));
+    SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->hnet_fallback, 0, sizeof(int32_t), s));
+    SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->hnet_err, 0, sizeof(uint32_t), s));
+    SPH_TRY(hnet_seed_from_fields(ctx, p, dt, false, h_seed, s));
+    SPH_TRY(sync_counters(ctx, s));
+    if (ctx->hcnt->hnet_err)
+        return sph_fail(ctx, SPH_ERR_CUDA, "sph_hnet_seed: a tensor-core MMA did not complete within 1 s");
+    if (fallbacks) *fallbacks = ctx->hcnt->hnet_fallback;
+    return SPH_OK;
+}
+
 int sph_hnet_grad(sph_ctx *ctx, const float *feats, const float *target, int64_t nb, float *grad_host,
                   float *loss_host, void *stream)
 {

@@ -94,3 +94,41 @@ def test_features_match_definition():
     g = p.numpy()
     ref = oracle.hnet_features(g["h"], g["hprev"], g["nnb"], g["rho"], g["m"], g["divv"], dt, w.params["eta"], 1.0)
     assert np.max(np.abs(f - ref)) < 1e-5
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_step_seed_matches_oracle(fp64):
+    """The fused seed of the step path (features, network and exponential in
+    one tensor-core kernel) against the oracle's features and network at the
+    same BF16 weights: h exp(f3 y(f)) where |f3 y| <= ln 2, else h (about 3 %
+    of the particles here take that fallback)."""
+    B = need_gpu()
+    w = inputs.sedov(12)
+    if not fp64:
+        w.params["precision"] = "mixed"
+    rng = np.random.default_rng(6)
+    w.vx, w.vy, w.vz = 0.5 * rng.standard_normal((3, w.n))
+    ctx = B.Context(w.params, w.n)
+    p = B.Particles.from_workload(w, fp64=fp64)
+    B.sph_build_tree(ctx, p)
+    B.sph_density(ctx, p)
+    B.sph_forces(ctx, p)
+    p.hprev.copy_(p.h * torch.from_numpy(1 + 0.02 * rng.standard_normal(w.n)).to(p.h))
+    th = _theta(3)
+    B.sph_hnet_set_weights(ctx, th)
+    dt = 0.2
+    seed, fallbacks = B.sph_hnet_seed(ctx, p, dt)
+    g = p.numpy()
+    f = oracle.hnet_features(g["h"], g["hprev"], g["nnb"], g["rho"], g["m"], g["divv"], dt, w.params["eta"], 1.0)
+    s = oracle.hnet_predict(oracle.bf16_round(th), f)
+    got = seed.cpu().numpy().astype(np.float64)
+    clear = np.abs(np.abs(s) - np.log(2.0)) > 1e-4          # both sides take the same branch
+    inside = clear & (np.abs(s) <= np.log(2.0))
+    outside = clear & (np.abs(s) > np.log(2.0))
+    assert inside.sum() > 0.9 * w.n and outside.sum() > 0.01 * w.n
+    assert np.max(np.abs(got[inside] / (g["h"][inside] * np.exp(s[inside])) - 1)) < 1e-4
+    assert np.array_equal(got[outside], g["h"][outside])
+    assert outside.sum() <= fallbacks <= w.n - inside.sum()
+    # dt = 0: f3 = div v dt = 0, every particle keeps its h exactly
+    seed0, fb0 = B.sph_hnet_seed(ctx, p, 0.0)
+    assert fb0 == 0 and torch.equal(seed0, p.h)
