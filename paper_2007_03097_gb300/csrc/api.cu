@@ -181,6 +181,8 @@ int allocate(sph_ctx *c, int64_t N)
     SPH_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     SPH_CUDA(cudaEventCreateWithFlags(&c->ev_dens, cudaEventDisableTiming));
     SPH_CUDA(cudaEventCreateWithFlags(&c->ev_train, cudaEventDisableTiming));
+    SPH_CUDA(cudaEventCreateWithFlags(&c->ev_order, cudaEventDisableTiming));
+    SPH_CUDA(cudaEventCreateWithFlags(&c->ev_seed, cudaEventDisableTiming));
     for (cudaEvent_t &e : c->kev) SPH_CUDA(cudaEventCreate(&e));
     SPH_TRY(hnet_init(c));
     return SPH_OK;
@@ -206,6 +208,8 @@ void release(sph_ctx *c)
     }
     if (c->ev_dens) cudaEventDestroy(c->ev_dens);
     if (c->ev_train) cudaEventDestroy(c->ev_train);
+    if (c->ev_order) cudaEventDestroy(c->ev_order);
+    if (c->ev_seed) cudaEventDestroy(c->ev_seed);
     if (c->hcnt) cudaFreeHost(c->hcnt);
     for (cudaEvent_t e : c->ev)
         if (e) cudaEventDestroy(e);
@@ -341,14 +345,42 @@ int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet, sph_step_s
     cudaEvent_t *ev = ctx->ev;
     SPH_CUDA(cudaEventRecord(ev[0], s));
     SPH_TRY(kick_drift(ctx, p, dt, s));
-    SPH_TRY(tree_build(ctx, p, s));
+    // The h seed reads only particle fields, so it runs on the side stream as
+    // soon as the particles are in key order, beside the leaf build (a chain
+    // of small kernels that leaves most of the GPU idle); the density
+    // iteration waits for it.  A build that sorts in full after a failed
+    // near-sorted pass orders the particles twice: the seed is computed again
+    // after the second ordering (the side stream runs the two in order).
+    struct SeedHook : OrderHook {
+        sph_ctx *ctx;
+        const sph_particles *p;
+        double dt;
+        bool train;
+        int operator()(cudaStream_t ms) override
+        {
+            SPH_CUDA(cudaEventRecord(ctx->ev_order, ms));
+            SPH_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_order, 0));
+            SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->hnet_fallback, 0, sizeof(int32_t), ctx->side));
+            SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->hnet_err, 0, sizeof(uint32_t), ctx->side));
+            SPH_TRY(hnet_seed_from_fields(ctx, p, dt, train, ctx->hseed, ctx->side));
+            SPH_CUDA(cudaEventRecord(ctx->ev_seed, ctx->side));
+            return SPH_OK;
+        }
+    } hook;
+    hook.ctx = ctx;
+    hook.p = p;
+    hook.dt = dt;
+    hook.train = train_net;
+    const int built = tree_build(ctx, p, s, seed_net ? &hook : nullptr);
+    // the main stream joins the seed before anything else (also on an error,
+    // so that no side-stream work outlives the call)
+    if (seed_net) SPH_CUDA(cudaStreamWaitEvent(s, ctx->ev_seed, 0));
+    SPH_TRY(built);
     local.tree_moved = (int32_t)std::min<int64_t>(ctx->ns_moved, INT32_MAX);
     SPH_CUDA(cudaEventRecord(ev[1], s));
     const void *seed = nullptr;
     SPH_TRY(copy_field(ctx, ctx->hold, p->h, p->n, s));
     if (seed_net) {
-        // hnet_fallback and hnet_err were zeroed by the kick-drift kernel
-        SPH_TRY(hnet_seed_from_fields(ctx, p, dt, train_net, ctx->hseed, s));
         seed = ctx->hseed;
         local.hnet_used = 1;
     } else if (train_net) {

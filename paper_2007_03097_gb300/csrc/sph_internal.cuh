@@ -247,6 +247,7 @@ struct sph_ctx {
     // force pass; the next call on the context waits for it
     cudaStream_t side = nullptr;
     cudaEvent_t ev_dens = nullptr, ev_train = nullptr;
+    cudaEvent_t ev_order = nullptr, ev_seed = nullptr;   // particles in key order; h seed written (side stream)
     bool side_pending = false;
     cudaEvent_t kev[2 * 64] = {};       // per-sweep density kernel events
     int64_t launches = 0;               // kernels launched so far
@@ -423,7 +424,13 @@ __device__ __forceinline__ float wrap_diff(float a, float c, float L, float invL
 
 // ------------------------------------------------------------ launchers
 // tree.cu
-int tree_build(sph_ctx *ctx, sph_particles *p, cudaStream_t s);
+// after_order (may be null) is called with the build's stream once the
+// particle arrays are in their final key order (again if a full sort
+// follows a failed near-sorted pass), before the leaves are built
+struct OrderHook {
+    virtual int operator()(cudaStream_t s) = 0;
+};
+int tree_build(sph_ctx *ctx, sph_particles *p, cudaStream_t s, OrderHook *after_order = nullptr);
 int tree_keys(sph_ctx *ctx, const sph_particles *p, uint64_t *keys_out, cudaStream_t s);
 int tree_sort(sph_ctx *ctx, int64_t n, const uint64_t *keys, const uint32_t *ids, uint32_t *perm,
               cudaStream_t s);

@@ -1040,7 +1040,7 @@ int leaves_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
 }
 
 template <typename T>
-int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
+int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s, OrderHook *after_order)
 {
     const int64_t n = p->n;
     ctx->tree_valid = false;
@@ -1059,6 +1059,7 @@ int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
         SPH_CHECK_LAUNCH();
     }
     if (limit < 0) SPH_TRY(full_sort(ctx, p, t, s));
+    if (after_order) SPH_TRY((*after_order)(s));
     SPH_TRY(leaves_impl<T>(ctx, p, s));
     int64_t m = -1;
     if (limit >= 0) {
@@ -1068,6 +1069,7 @@ int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
             // above describe the unsorted keys; sort in full and build again
             SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->err, 0, sizeof(uint32_t), s));
             SPH_TRY(full_sort(ctx, p, t, s));
+            if (after_order) SPH_TRY((*after_order)(s));
             SPH_TRY(leaves_impl<T>(ctx, p, s));
         }
         ctx->ns_full_streak = m < 0 ? ctx->ns_full_streak + 1 : 0;
@@ -1099,9 +1101,9 @@ int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
 
 }  // namespace
 
-int tree_build(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
+int tree_build(sph_ctx *ctx, sph_particles *p, cudaStream_t s, OrderHook *after_order)
 {
-    return ctx->fp64 ? build_impl<double>(ctx, p, s) : build_impl<float>(ctx, p, s);
+    return ctx->fp64 ? build_impl<double>(ctx, p, s, after_order) : build_impl<float>(ctx, p, s, after_order);
 }
 
 // Boxes of leaves, groups and radix-tree nodes with the largest coverage
