@@ -48,8 +48,8 @@ FP64_PIPE_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # profiles/), with the hash of the sources it was taken on
 TRAFFIC = {
     # k_forces_df on the Sedov 64^3 step (profiles/k_forces_df_sedov64_fp64.md):
-    # 81.09 MB read + 3.59 MB written
-    "forces_fp64_sedov": {"bytes_per_launch": 84688128, "src": "f81ae0d7853b",
+    # 81.07 MB read + 3.14 MB written
+    "forces_fp64_sedov": {"bytes_per_launch": 84208896, "src": "29a20052c842",
                           "files": ["forces.cu", "dfloat.cuh", "sph_internal.cuh"]},
 }
 FP32_PIPE_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
