@@ -80,6 +80,20 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def whole_job(times, units, device="cpu"):
+    """Whole-job figures of N replicas: the maximum over ranks of each time
+    and the sum over ranks of each unit count (one all-reduce each, on the
+    process group's backend); the values themselves on one rank."""
+    import torch
+    import torch.distributed as dist
+    mx = torch.tensor(times, dtype=torch.float64, device=device)
+    sm = torch.tensor(units, dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return [float(v) for v in mx.cpu()], [float(v) for v in sm.cpu()]
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -308,16 +322,8 @@ def run_sph(args):
                 "k_forces_tflops": force_flops / max(L["force_kernel_ms"], 1e-9) / 1e9}}
 
     # whole-job numbers (max time over ranks; units summed over ranks)
-    t_l = L["seconds"]
-    inter_l = L["interactions"]
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_l, e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_l, e2e_s = float(tt[0]), float(tt[1])
-        ii = torch.tensor([inter_l, e_inter], device="cuda", dtype=torch.float64)
-        dist.all_reduce(ii, op=dist.ReduceOp.SUM)
-        inter_l, e_inter = float(ii[0]), float(ii[1])
+    (t_l, e2e_s), (inter_l, e_inter) = whole_job([L["seconds"], e2e_s], [L["interactions"], e_inter],
+                                                  device="cuda")
     lists = B.sph_list_info(ctx)
     lists["slots_per_particle"] = lists["slots_used"] / w.n
     nl, ng = B.sph_tree_info(ctx)
