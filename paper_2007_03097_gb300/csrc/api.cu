@@ -362,6 +362,7 @@ int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet, sph_step_s
             SPH_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_order, 0));
             SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->hnet_fallback, 0, sizeof(int32_t), ctx->side));
             SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->hnet_err, 0, sizeof(uint32_t), ctx->side));
+            SPH_TRY(copy_field(ctx, ctx->hold, p->h, p->n, ctx->side));   // the pre-iteration h
             SPH_TRY(hnet_seed_from_fields(ctx, p, dt, train, ctx->hseed, ctx->side));
             SPH_CUDA(cudaEventRecord(ctx->ev_seed, ctx->side));
             return SPH_OK;
@@ -379,7 +380,7 @@ int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet, sph_step_s
     local.tree_moved = (int32_t)std::min<int64_t>(ctx->ns_moved, INT32_MAX);
     SPH_CUDA(cudaEventRecord(ev[1], s));
     const void *seed = nullptr;
-    SPH_TRY(copy_field(ctx, ctx->hold, p->h, p->n, s));
+    if (!seed_net) SPH_TRY(copy_field(ctx, ctx->hold, p->h, p->n, s));   // else on the side stream
     if (seed_net) {
         seed = ctx->hseed;
         local.hnet_used = 1;

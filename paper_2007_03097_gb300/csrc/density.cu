@@ -669,7 +669,9 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
     // rebuilds the lists at the end of the batch.
     const unsigned grid = std::min<unsigned>(grid_for(ng, DW), (unsigned)ctx->num_sms * resident_blocks<T>(ctx->fp64));
     const int max_launch = 4 * (q.max_sweeps + 2);
-    const int batch = q.fixed_h ? 1 : 4;
+    // a seeded iteration (the h-predictor's guess) typically ends after three
+    // sweeps, the plain one after four
+    const int batch = q.fixed_h ? 1 : (seed ? 3 : 4);
     int cur = 0, launched = 0, rebuilds = 0;
     for (;;) {
         for (int j = 0; j < batch && launched < max_launch; ++j) {
