@@ -22,7 +22,7 @@ __global__ void k_kick_drift(double *__restrict__ x, double *__restrict__ y, dou
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     // the step's h-predictor counters start at zero (this is the step's
-    // first kernel; nothing else writes them before the seeding)
+    // first kernel; the seeding also zeroes them on its own stream)
     if (i == 0) { cnt->hnet_fallback = 0; cnt->hnet_err = 0; }
     if (i >= n) return;
     const T hdt = (T)(0.5 * dt);
