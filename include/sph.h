@@ -226,6 +226,11 @@ int sph_forces(sph_ctx *ctx, sph_particles *p, sph_force_stats *stats, void *str
  *   SPH_HNET_TRAIN after convergence, take hnet_iters Adam steps on the
  *                  step's features and targets log(h_new/h_old) (a strided
  *                  subset of hnet_batch particles).
+ * The network's work runs on a second stream owned by the context: the seed
+ * beside the tree build (joined before the density iteration), the training
+ * round beside the force pass, joined by the next call on the context; until
+ * then it reads the particles' h, so a caller that rewrites h between calls
+ * trains on the rewritten values (nothing is written outside the context).
  * The particle set must already carry a, du/dt from an earlier force pass. */
 #define SPH_HNET_SEED 1
 #define SPH_HNET_TRAIN 2
