@@ -1,13 +1,26 @@
 #!/usr/bin/env python
 """Benchmark of the SPH hot path on GB300: particle-neighbour interactions/s
-and SPH steps/s, learned-h vs plain-h, on the Sedov blast workload (64^3 =
-262,144 particles, Wendland C2, eta = 1.2, h-rho iteration to 1e-6, Monaghan
-viscosity alpha = 1, beta = 2, FP64, fixed step).
+and SPH steps/s, learned-h vs plain-h, on one GPU.
+
+Headline workload (default): the periodic turbulence box, 256^3 = 16,777,216
+particles on a jittered lattice, Gaussian solenoidal velocity field with
+P(k) ~ k^-4, rms Mach 2, gamma 1.01, Wendland C4 (~100 neighbours), FP32 pair
+arithmetic on FP64 positions, h-rho iteration to 1e-6, learned-h seeding.
 
 One timed step = one kick-drift-kick sph_step: tree (keys, sort, permute,
-leaves), h-predictor inference and one online training round, h-rho sweeps,
-forces, kicks, FP64 totals.  Inputs are resident in HBM; L2 is flushed (a
-256 MB write) between timed steps and each step is bracketed by CUDA events.
+leaves), h-predictor inference, neighbour lists, h-rho sweeps, forces, kicks,
+FP64 totals.  Inputs are resident in HBM (far larger than L2); L2 is also
+flushed (a 256 MB write) between timed steps and each step is bracketed by
+CUDA events on the launching stream.
+
+The h-predictor is trained once, before anything is timed, by the library's
+own training kernels on the plain solver's h trajectories: 200 plain steps of
+the 16^3 lattice with variable h (M4, eta 1.2) and 200 plain steps of the
+64^3 Sedov blast; its weights are then frozen and seed every learned step.
+
+Extra keys (N = 1): the two colliding polytropes (2 x 2^21 particles, mixed,
+learned vs plain) and the 64^3 Sedov blast in FP64 (double-float pair sums)
+with its own roofline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sph|reference]
 
@@ -34,43 +47,47 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-neighbor interactions/s and SPH steps/s (learned-h vs plain-h, same GPU)"
 UNIT = "interactions/s"
-# algorithmic FP64 flops per accepted pair, counted from the pair arithmetic of
-# the density sweep and of the force pass (FMA = 2, sqrt/div = 1)
+# algorithmic flops per accepted pair, counted from the pair arithmetic of the
+# density sweep and of the force pass (FMA = 2, sqrt/div = 1)
 F_DENSITY = 28
 F_FORCE = 96
-# Peaks derived from unit counts and the 2.07 GHz maximum SM clock (152 SMs):
-# FP64 pipe 2 DFMA lanes/clk/SM; FP32 pipe 128 lanes/clk/SM.  The FP64 mode
-# evaluates its pair terms in double-float on the FP32 pipe, where one FP64
-# multiply-add (2 flops) costs 18 FP32 instructions (df_mul 7 + df_add 11), so
-# its ceiling in FP64-accurate flops is 152 * 128 * 2.07e9 * 2 / 18.
-FP64_PIPE_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# DRAM bytes per launch of the dominant kernel from one ncu capture (see
-# profiles/), with the hash of the sources it was taken on
+# Ceilings derived from unit counts and the 2.07 GHz maximum SM clock (152
+# SMs): FP64 pipe 2 DFMA lanes/clk/SM; FP32 pipe 128 lanes/clk/SM.  The FP64
+# mode evaluates its pair terms in double-float on the FP32 pipe, where one
+# FP64 multiply-add (2 flops) costs 18 FP32 instructions (df_mul 7 + df_add 11).
+SM_COUNT, SM_MHZ = 152, 2070.0
+FP64_PIPE_TFLOPS = SM_COUNT * 2 * 2 * SM_MHZ * 1e6 / 1e12
+FP32_PIPE_TFLOPS = SM_COUNT * 128 * 2 * SM_MHZ * 1e6 / 1e12
+DF_PER_FP32 = 2.0 / 18.0
+# DRAM bytes per launch of a dominant kernel from one ncu capture (profiles/),
+# with the hash of the sources it was taken on and the particles of the
+# captured launch (traffic scales with the particles at a fixed neighbour
+# number, so a capture on a reduced side is scaled by the particle ratio)
 TRAFFIC = {
-    # k_forces_df on the Sedov 64^3 step (profiles/k_forces_df_sedov64_fp64.md):
-    # 81.07 MB read + 3.14 MB written
-    "forces_fp64_sedov": {"bytes_per_launch": 84208896, "src": "29a20052c842",
+    "forces_fp64_sedov": {"bytes_per_launch": 84208896, "particles": 262144, "src": "29a20052c842",
                           "files": ["forces.cu", "dfloat.cuh", "sph_internal.cuh"]},
 }
-FP32_PIPE_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-DF_EMULATED_TFLOPS = 152 * 128 * 2.07e9 * 2 / 18 / 1e12
+PROTOCOL_TRAIN_STEPS = 200
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sph", choices=["sph", "reference"])
+    ap.add_argument("--workload", default="turbulence",
+                    choices=["turbulence", "collision", "polytrope", "sedov", "sod"],
+                    help="turbulence: 256^3 mixed (headline); collision 2x2^21 and polytrope 2^20: mixed; "
+                         "sedov: 64^3 FP64; sod: the 1D shock tube, 10,000 particles in the tube, FP64")
     ap.add_argument("--n-side", type=int, default=None,
-                    help="lattice side of the sedov (default 64, the headline workload) and turbulence (default 256) "
-                         "workloads; smaller sides serve profiling captures")
-    ap.add_argument("--workload", default="sedov", choices=["sedov", "polytrope", "collision", "turbulence", "sod"],
-                    help="sedov: 64^3 FP64 (headline); polytrope 2^20, collision 2x2^21, turbulence 256^3: "
-                         "FP32 pairs on FP64 positions; sod: the 1D shock tube, 10,000 particles in the tube, FP64")
+                    help="lattice side of the turbulence (default 256) and sedov (default 64) workloads; "
+                         "smaller sides serve profiling captures")
     ap.add_argument("--curve", default="morton", choices=["morton", "hilbert"],
                     help="space-filling curve of the particle keys (Sec. 2.1, Tree topology)")
-    ap.add_argument("--train-steps", type=int, default=16)
+    ap.add_argument("--train-steps", type=int, default=PROTOCOL_TRAIN_STEPS,
+                    help="plain steps of each training workload (16^3 lattice, 64^3 Sedov)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the collision and Sedov extra keys")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -133,32 +150,33 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# ------------------------------------------------------------------ GPU arm
-def make_workload(args):
+# ------------------------------------------------------------------ workloads
+def make_workload(name, n_side=None):
     from paper_2007_03097_gb300 import inputs
-    if args.workload == "sedov":
-        return inputs.sedov(args.n_side or 64)
-    if args.workload == "polytrope":
+    if name == "sedov":
+        return inputs.sedov(n_side or 64)
+    if name == "polytrope":
         return inputs.polytrope(1 << 20)
-    if args.workload == "collision":
+    if name == "collision":
         return inputs.collision(1 << 21)
-    if args.workload == "sod":
+    if name == "sod":
         return inputs.sod(10000)
-    return inputs.turbulence(args.n_side or 256)
+    return inputs.turbulence(n_side or 256)
 
 
-def workload_label(args, w):
-    if args.workload == "sedov":
-        return (f"sedov blast {args.n_side or 64}^3 = {w.n} particles, Wendland C2, eta 1.2, h_tol 1e-6, "
-                f"alpha 1 beta 2, FP64, fixed dt {w.dt:.3e}")
-    if args.workload == "polytrope":
+def workload_label(name, w, n_side=None):
+    if name == "sedov":
+        return (f"sedov blast {n_side or 64}^3 = {w.n} particles, Wendland C2, eta 1.2, h_tol 1e-6, "
+                f"alpha 1 beta 2, FP64 (double-float pair sums), fixed dt {w.dt:.3e}")
+    if name == "polytrope":
         return f"n=1 polytrope, {w.n} particles, Wendland C2, eta 1.2, open boundary, FP32 pairs / FP64 positions"
-    if args.workload == "collision":
+    if name == "collision":
         return f"two colliding n=1 polytropes, {w.n} particles, closing speed 1, FP32 pairs / FP64 positions"
-    if args.workload == "sod":
+    if name == "sod":
         return (f"1D Sod shock tube, {w.info['n_tube']} particles in [0, 1) and its mirror image ({w.n} in the "
                 f"periodic box), M4, eta 1.2, gamma 1.4, FP64")
-    return f"turbulence box {args.n_side or 256}^3 = {w.n} particles, Wendland C4, Mach 2, FP32 pairs / FP64 positions"
+    return (f"periodic turbulence box {n_side or 256}^3 = {w.n} particles, k^-4 solenoidal field, rms Mach 2, "
+            f"gamma 1.01, Wendland C4 (~100 neighbours), h_tol 1e-6, FP32 pairs / FP64 positions, learned-h")
 
 
 def src_hash(files):
@@ -170,11 +188,222 @@ def src_hash(files):
     return hsh.hexdigest()[:12]
 
 
+def initial_theta(seed=1234):
+    """Seeded initial weights of the 5 -> 64 -> 64 -> 1 network (flat layout
+    of include/sph.h: W1, b1, W2, b2, W3, b3)."""
+    rng = np.random.default_rng(seed)
+    return np.concatenate([rng.normal(scale=s, size=k) for s, k in
+                           ((1 / math.sqrt(5), 320), (0, 64), (1 / 8, 4096), (0, 64), (1 / 8, 64), (0, 1))]
+                          ).astype(np.float32)
+
+
+def train_protocol(B, steps):
+    """Train the h-predictor on the plain solver's own h trajectories:
+    `steps` plain steps of the 16^3 lattice with variable h (M4, eta 1.2)
+    and `steps` plain steps of the 64^3 Sedov blast, one online Adam round of
+    40 iterations per step (library kernels).  Returns the frozen weights and
+    the last loss of each run."""
+    from paper_2007_03097_gb300 import inputs
+    theta = initial_theta()
+    losses = {}
+    for name, w in (("lattice16_variable_h", inputs.lattice(16, kernel=inputs.M4, fixed_h=False)),
+                    ("sedov64", inputs.sedov(64))):
+        params = dict(w.params)
+        params.update(hnet_batch=8192, hnet_iters=40, hnet_lr=1e-3)
+        ctx = B.Context(params, w.n)
+        p = B.Particles.from_workload(w, fp64=params.get("precision", "fp64") == "fp64")
+        B.sph_build_tree(ctx, p)
+        B.sph_density(ctx, p)
+        B.sph_forces(ctx, p)
+        B.sph_hnet_set_weights(ctx, theta)
+        # the workload's fixed step, else the initial CFL step kept fixed
+        dt = w.dt if w.dt else float(params["cfl"] * (p.h / p.vsig).min().item())
+        last = None
+        for _ in range(steps):
+            st = B.sph_step(ctx, p, dt, use_hnet=B.SPH_HNET_TRAIN)
+            last = st["hnet_loss"]
+        B.sph_step(ctx, p, dt, use_hnet=0)       # joins the last training round
+        theta = B.sph_hnet_get_weights(ctx)
+        losses[name] = last
+        ctx.close()
+        del p
+    return theta, losses
+
+
+def summarize(ms, st):
+    t = sum(ms) / 1e3
+    inter = sum(s["density"]["interactions"] + s["forces"]["interactions"] for s in st)
+    return dict(seconds=t, interactions=inter, interactions_per_s=inter / t, steps_per_s=len(ms) / t,
+                ms_per_step=1e3 * t / len(ms),
+                sweeps_per_step=sum(s["density"]["sweeps"] for s in st) / len(st),
+                evaluations_per_step=sum(s["density"]["evaluations"] for s in st) / len(st),
+                density_kernel_ms=sum(s["density"]["kernel_ms"] for s in st),
+                force_kernel_ms=sum(s["forces"]["kernel_ms"] for s in st),
+                density_interactions=sum(s["density"]["interactions"] for s in st),
+                force_interactions=sum(s["forces"]["interactions"] for s in st),
+                density_launches=sum(s["density"]["sweeps"] for s in st),
+                list_builds=sum(s["density"]["list_builds"] for s in st),
+                launches=sum(s["launches"] for s in st),
+                hnet_fallback=sum(s["hnet_fallback"] for s in st),
+                hnet_loss=st[-1]["hnet_loss"],
+                # mean per-step phase times from the library's events: kick/drift and
+                # tree, h seed, density iteration (lists + sweeps), forces and the rest
+                ms_phase={k: sum(f(s) for s in st) / len(st) for k, f in (
+                    ("tree", lambda s: s["ms_tree"]), ("hnet", lambda s: s["ms_hnet"]),
+                    ("density", lambda s: s["density"]["ms"]), ("forces_kick_totals", lambda s: s["forces"]["ms"]),
+                    ("total", lambda s: s["ms_total"]))},
+                tree_moved=[s["tree_moved"] for s in st])
+
+
+class Run:
+    """One workload on the GPU: context, particles, a snapshot to restore,
+    and timed learned / plain steps from the same state."""
+
+    def __init__(self, B, torch, name, n_side, curve, theta, warmup):
+        self.B, self.torch = B, torch
+        self.w = make_workload(name, n_side)
+        w = self.w
+        self.fp64 = w.params.get("precision", "fp64") == "fp64"
+        self.params = dict(w.params)
+        self.params.update(hnet_batch=8192, hnet_iters=1, hnet_lr=1e-3, curve=curve)
+        self.ctx = B.Context(self.params, w.n)
+        self.p = B.Particles.from_workload(w, fp64=self.fp64)
+        self.stream = torch.cuda.current_stream()
+        p = self.p
+        B.sph_build_tree(self.ctx, p)
+        B.sph_density(self.ctx, p)
+        B.sph_forces(self.ctx, p)
+        if w.dt is None:                       # fixed step from the initial CFL condition
+            w.dt = float(self.params["cfl"] * torch.min(p.h / p.vsig).item())
+        self.theta = np.asarray(theta, dtype=np.float32)
+        B.sph_hnet_set_weights(self.ctx, self.theta)
+        for _ in range(warmup):
+            B.sph_step(self.ctx, p, w.dt, use_hnet=B.SPH_HNET_SEED)
+        self.snap = {f: getattr(p, f).clone() for f in ["x", "y", "z", "nnb", "id"] + B._FIELDS}
+        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def restore(self):
+        for f, t in self.snap.items():
+            getattr(self.p, f).copy_(t)
+
+    def timed(self, mode, steps, world=1):
+        B, torch, p, w = self.B, self.torch, self.p, self.w
+        self.restore()
+        B.sph_step(self.ctx, p, w.dt, use_hnet=mode)        # re-establish tree/lists in this mode
+        self.restore()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        stats = []
+        for k in range(steps):
+            self.flush.zero_()
+            ev[k][0].record(self.stream)
+            stats.append(B.sph_step(self.ctx, p, w.dt, use_hnet=mode))
+            ev[k][1].record(self.stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        return [a.elapsed_time(b) for a, b in ev], stats
+
+    def e2e(self, steps):
+        """The learned step end to end through the C ABI with host buffers:
+        H2D of the whole state (every particle array, one slab) from pinned
+        memory, the step, D2H of the whole state, every step."""
+        B, torch, p, w = self.B, self.torch, self.p, self.w
+        host = torch.empty_like(p.slab, device="cpu").pin_memory()
+        self.restore()
+        B.sph_hnet_set_weights(self.ctx, self.theta)
+        host.copy_(p.slab)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        inter = 0
+        e0.record(self.stream)
+        for _ in range(steps):
+            p.slab.copy_(host, non_blocking=True)
+            s = B.sph_step(self.ctx, p, w.dt, use_hnet=B.SPH_HNET_SEED)
+            inter += s["density"]["interactions"] + s["forces"]["interactions"]
+            host.copy_(p.slab, non_blocking=True)
+        e1.record(self.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, inter, host.numel()
+
+    def lists(self, force_pairs_per_pass):
+        B, w = self.B, self.w
+        li = B.sph_list_info(self.ctx)
+        li["slots_per_particle"] = li["slots_used"] / w.n
+        _, ng = B.sph_tree_info(self.ctx)
+        li["union_per_group"] = li["union_used"] / max(ng, 1)
+        # every lane of a group visits its group's list width in the force
+        # pass, so the slots used are the candidate slots of one pass
+        li["force_pairs_per_pass"] = force_pairs_per_pass
+        li["candidate_slots_per_accepted_pair"] = li["slots_used"] / max(force_pairs_per_pass, 1)
+        return li
+
+    def close(self):
+        self.ctx.close()
+
+
+def roofline(L, steps, fp64, workload, fp32_measured):
+    """The dominant pair kernel of the learned step against its ALU ceiling."""
+    dens_flops = L["density_interactions"] * F_DENSITY
+    force_flops = L["force_interactions"] * F_FORCE
+    if fp64:
+        names = ("k_density<double> (h-rho sweep, double-float)", "k_forces_df (Eqs. 5-6, double-float)")
+        ratio, what = DF_PER_FP32, "double-float FP64 multiply-adds at 18 FP32 instructions per 2 flops on "
+    else:
+        names = ("k_density<float> (h-rho sweep, FP32)", "k_forces_f32 (Eqs. 5-6, FP32)")
+        ratio, what = 1.0, ""
+    derived = FP32_PIPE_TFLOPS * ratio
+    if fp32_measured:
+        peak = fp32_measured * ratio
+        src = (f"measured: {what}the FP32 FMA-chain rate of this GPU in this run "
+               f"({fp32_measured:.1f} TFLOP/s, sph_peak_fp32)")
+    else:
+        peak, src = derived, f"derived: {what}the FP32 pipe, 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
+    dominant_density = L["density_kernel_ms"] >= L["force_kernel_ms"]
+    if dominant_density:
+        kname, flops, kms, launches = names[0], dens_flops, L["density_kernel_ms"], L["density_launches"]
+    else:
+        kname, flops, kms, launches = names[1], force_flops, L["force_kernel_ms"], steps
+    achieved = flops / (kms / 1e3) / 1e12
+    traffic = None
+    key = ("density" if dominant_density else "forces") + ("_fp64" if fp64 else "_mixed") + "_" + workload["name"]
+    rec = TRAFFIC.get(key)
+    if rec and rec["src"] == src_hash(rec["files"]):
+        traffic = rec["bytes_per_launch"] * workload["n"] / rec["particles"]
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": kname, "launches": launches, "avg_launch_ms": kms / max(launches, 1),
+            "peak_source": src, "derived_peak": derived, "frac_of_derived": achieved / derived,
+            "fp64_pipe_peak": FP64_PIPE_TFLOPS, "fp32_pipe_peak": FP32_PIPE_TFLOPS,
+            "flops_per_pair": F_DENSITY if dominant_density else F_FORCE,
+            "other_kernels": {
+                "k_density_tflops": dens_flops / max(L["density_kernel_ms"], 1e-9) / 1e9,
+                "k_forces_tflops": force_flops / max(L["force_kernel_ms"], 1e-9) / 1e9}}
+
+
+def extra_run(B, torch, name, theta, steps, warmup, fp32_measured):
+    """A secondary workload: learned vs plain steps/s and its roofline."""
+    r = Run(B, torch, name, None, "morton", theta, warmup)
+    ms_l, st_l = r.timed(B.SPH_HNET_SEED, steps)
+    ms_p, st_p = r.timed(0, steps)
+    L, P = summarize(ms_l, st_l), summarize(ms_p, st_p)
+    out = {"workload": workload_label(name, r.w), "n_particles": r.w.n,
+           "dtype": "df64" if r.fp64 else "f32", "steps": steps,
+           "value": L["interactions_per_s"], "unit": UNIT, "ms_per_step": L["ms_per_step"],
+           "steps_per_s": L["steps_per_s"], "learned_h": L, "plain_h": P,
+           "learned_vs_plain_steps_per_s": L["steps_per_s"] / P["steps_per_s"],
+           "learned_vs_plain_evaluations": L["evaluations_per_step"] / P["evaluations_per_step"],
+           "roofline": roofline(L, steps, r.fp64, {"name": name, "n": r.w.n}, fp32_measured)}
+    r.close()
+    return out
+
+
 def run_sph(args):
     import torch
 
     from paper_2007_03097_gb300 import binding as B
-    from paper_2007_03097_gb300 import build, inputs
+    from paper_2007_03097_gb300 import build
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -182,158 +411,45 @@ def run_sph(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
-    w = make_workload(args)
-    fp64 = w.params.get("precision", "fp64") == "fp64"
-    params = dict(w.params)
-    params.update(hnet_batch=8192, hnet_iters=1, hnet_lr=1e-3, curve=args.curve)
-    ctx = B.Context(params, w.n)
-    p = B.Particles.from_workload(w, fp64=fp64)
-    stream = torch.cuda.current_stream()
-    B.sph_build_tree(ctx, p)
-    B.sph_density(ctx, p)
-    B.sph_forces(ctx, p)
-    if w.dt is None:                       # fixed step from the initial CFL condition
-        w.dt = float(w.params["cfl"] * torch.min(p.h / p.vsig).item())
-    rng = np.random.default_rng(1234)
-    theta = np.concatenate([rng.normal(scale=s, size=k) for s, k in
-                            ((1 / math.sqrt(5), 320), (0, 64), (1 / 8, 4096), (0, 64), (1 / 8, 64), (0, 1))])
-    B.sph_hnet_set_weights(ctx, theta.astype(np.float32))
-    # train the h-predictor online on the plain solver's own steps (untimed)
-    p_train = dict(params, hnet_iters=40)
-    ctx.set_params(p_train)
-    for _ in range(args.train_steps):
-        B.sph_step(ctx, p, w.dt, use_hnet=B.SPH_HNET_TRAIN)
-    ctx.set_params(params)
-    for _ in range(args.warmup):
-        B.sph_step(ctx, p, w.dt, use_hnet=B.SPH_HNET_SEED | B.SPH_HNET_TRAIN)
-    snap = {f: getattr(p, f).clone() for f in ["x", "y", "z", "nnb", "id"] + B._FIELDS}
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-
-    def restore():
-        for f, t in snap.items():
-            getattr(p, f).copy_(t)
-
-    def timed(mode):
-        restore()
-        B.sph_step(ctx, p, w.dt, use_hnet=mode)            # re-establish tree/lists in this mode
-        restore()
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        stats = []
-        for k in range(args.steps):
-            flush.zero_()
-            ev[k][0].record(stream)
-            stats.append(B.sph_step(ctx, p, w.dt, use_hnet=mode))
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-        ms = [a.elapsed_time(b) for a, b in ev]
-        return ms, stats
+    # the h-predictor: trained on the plain solver's trajectories (untimed), frozen
+    t0 = time.perf_counter()
+    theta, losses = train_protocol(B, args.train_steps)
+    train_s = time.perf_counter() - t0
+    fp32_peak = B.sph_peak_fp32()
 
     gpu_uuid = str(getattr(torch.cuda.get_device_properties(local), "uuid", local))
     if gpu_uuid and not gpu_uuid.startswith("GPU-") and "-" in gpu_uuid:
         gpu_uuid = "GPU-" + gpu_uuid
+    r = Run(B, torch, args.workload, args.n_side, args.curve, theta, args.warmup)
+    w = r.w
     clocks = ClockSampler(gpu_uuid)
-    # learned h: the seed of the network trained above on the plain solver's
-    # steps (frozen while timed); the same with one online Adam round per step
-    # is timed too
-    ms_l, st_l = timed(B.SPH_HNET_SEED)
-    ms_o, st_o = timed(B.SPH_HNET_SEED | B.SPH_HNET_TRAIN)
-    ms_p, st_p = timed(0)
+    # learned h (frozen network), plain h, and learned h with one online Adam
+    # round per step (on the context's side stream, beside the force pass)
+    ms_l, st_l = r.timed(B.SPH_HNET_SEED, args.steps, world)
+    ms_p, st_p = r.timed(0, args.steps, world)
+    ms_o, st_o = r.timed(B.SPH_HNET_SEED | B.SPH_HNET_TRAIN, args.steps, world)
+    e2e_s, e_inter, h2d = r.e2e(args.steps)
     clk = clocks.stop()
-
-    def summarize(ms, st):
-        t = sum(ms) / 1e3
-        inter = sum(s["density"]["interactions"] + s["forces"]["interactions"] for s in st)
-        return dict(seconds=t, interactions=inter, interactions_per_s=inter / t, steps_per_s=len(ms) / t,
-                    ms_per_step=1e3 * t / len(ms),
-                    sweeps_per_step=sum(s["density"]["sweeps"] for s in st) / len(st),
-                    density_kernel_ms=sum(s["density"]["kernel_ms"] for s in st),
-                    force_kernel_ms=sum(s["forces"]["kernel_ms"] for s in st),
-                    density_interactions=sum(s["density"]["interactions"] for s in st),
-                    force_interactions=sum(s["forces"]["interactions"] for s in st),
-                    density_launches=sum(s["density"]["sweeps"] for s in st),
-                    list_builds=sum(s["density"]["list_builds"] for s in st),
-                    launches=sum(s["launches"] for s in st),
-                    hnet_fallback=sum(s["hnet_fallback"] for s in st),
-                    hnet_loss=st[-1]["hnet_loss"], ms_tree=sum(s["ms_tree"] for s in st) / len(st),
-                    # mean per-step phase times from the library's events: kick/drift and
-                    # tree, h seed, density iteration (lists + sweeps), forces and the rest
-                    ms_phase={k: sum(f(s) for s in st) / len(st) for k, f in (
-                        ("tree", lambda s: s["ms_tree"]), ("hnet", lambda s: s["ms_hnet"]),
-                        ("density", lambda s: s["density"]["ms"]), ("forces_kick_totals", lambda s: s["forces"]["ms"]),
-                        ("total", lambda s: s["ms_total"]))},
-                    tree_moved=[s["tree_moved"] for s in st])
-
-    L = summarize(ms_l, st_l)
-    O = summarize(ms_o, st_o)
-    P = summarize(ms_p, st_p)
-
-    # end to end through the C ABI with host buffers: H2D of the whole state
-    # (every particle array, one slab) from pinned memory, the step, D2H of
-    # the whole state, every step
-    host = torch.empty_like(p.slab, device="cpu").pin_memory()
-    restore()
-    host.copy_(p.slab)
-    h2d = host.numel()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e_inter = 0
-    e0.record(stream)
-    for k in range(args.steps):
-        p.slab.copy_(host, non_blocking=True)
-        s = B.sph_step(ctx, p, w.dt, use_hnet=B.SPH_HNET_SEED)
-        e_inter += s["density"]["interactions"] + s["forces"]["interactions"]
-        host.copy_(p.slab, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_s = e0.elapsed_time(e1) / 1e3
-
-    # dominant kernel of the learned step and its roofline
-    dens_flops = L["density_interactions"] * F_DENSITY
-    force_flops = L["force_interactions"] * F_FORCE
-    if fp64:
-        names = ("k_density<double> (h-rho sweep, double-float)", "k_forces_df (Eqs. 5-6, double-float)")
-        peak, peak_src = DF_EMULATED_TFLOPS, ("derived: FP32 pipe (152 SMs x 128 lanes x 2.07 GHz) running "
-                                              "double-float FP64 multiply-adds at 18 FP32 instructions per 2 flops")
-    else:
-        names = ("k_density<float> (h-rho sweep, FP32)", "k_forces_f32 (Eqs. 5-6, FP32)")
-        peak, peak_src = FP32_PIPE_TFLOPS, "derived: FP32 pipe, 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
-    dominant_density = L["density_kernel_ms"] >= L["force_kernel_ms"]
-    if dominant_density:
-        kname, flops, kms, launches = names[0], dens_flops, L["density_kernel_ms"], L["density_launches"]
-    else:
-        kname, flops, kms, launches = names[1], force_flops, L["force_kernel_ms"], args.steps
-    achieved = flops / (kms / 1e3) / 1e12
-    # DRAM traffic per launch from one ncu capture (profiles/), valid only for
-    # the kernel source it was taken on
-    traffic = None
-    key = ("density" if dominant_density else "forces") + ("_fp64" if fp64 else "_mixed") + "_" + args.workload
-    rec = TRAFFIC.get(key)
-    if rec and rec["src"] == src_hash(rec["files"]):
-        traffic = rec["bytes_per_launch"]
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic, "kernel": kname,
-            "launches": launches, "avg_launch_ms": kms / max(launches, 1), "peak_source": peak_src,
-            "fp64_pipe_peak": FP64_PIPE_TFLOPS, "fp32_pipe_peak": FP32_PIPE_TFLOPS,
-            "other_kernels": {
-                "k_density_tflops": dens_flops / max(L["density_kernel_ms"], 1e-9) / 1e9,
-                "k_forces_tflops": force_flops / max(L["force_kernel_ms"], 1e-9) / 1e9}}
-
-    # whole-job numbers (max time over ranks; units summed over ranks)
+    L, P, O = summarize(ms_l, st_l), summarize(ms_p, st_p), summarize(ms_o, st_o)
+    roof = roofline(L, args.steps, r.fp64, {"name": args.workload, "n": w.n}, fp32_peak["tflops"])
+    lists = r.lists(L["force_interactions"] / max(len(ms_l), 1))
     (t_l, e2e_s), (inter_l, e_inter) = whole_job([L["seconds"], e2e_s], [L["interactions"], e_inter],
                                                   device="cuda")
-    lists = B.sph_list_info(ctx)
-    lists["slots_per_particle"] = lists["slots_used"] / w.n
-    nl, ng = B.sph_tree_info(ctx)
-    lists["union_per_group"] = lists["union_used"] / max(ng, 1)
-    # candidates against accepted pairs: every lane of a group visits its
-    # group's list width in the force pass, so the slots used are the
-    # candidate slots of one pass
-    pairs = L["force_interactions"] / max(len(ms_l), 1)
-    lists["force_pairs_per_pass"] = pairs
-    lists["candidate_slots_per_accepted_pair"] = lists["slots_used"] / max(pairs, 1)
+    config = {"workload": workload_label(args.workload, w, args.n_side), "n_particles": w.n,
+              "precision": "fp64 (double-float pair sums)" if r.fp64 else "mixed (FP32 pairs, FP64 positions)",
+              "parallelism": f"replicas x{world}", "curve": args.curve,
+              "l2": "inputs larger than L2; also flushed between timed steps (256 MB write)",
+              "step": "learned-h sph_step (seed from the frozen network trained on 200 plain steps each of the "
+                      "16^3 lattice and the 64^3 Sedov blast before the timed region)"}
+    r.close()
+    del r
+    torch.cuda.empty_cache()
+
+    extras = {}
+    if world == 1 and not args.no_extras and args.workload == "turbulence":
+        for name in ("collision", "sedov"):
+            extras[name] = extra_run(B, torch, name, theta, args.steps, args.warmup, fp32_peak["tflops"])
+            torch.cuda.empty_cache()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, seconds=12.0, label=args.workload)
@@ -341,27 +457,32 @@ def run_sph(args):
         out = {
             "metric": METRIC, "value": inter_l / t_l, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_l / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
-            "config": {"workload": workload_label(args, w),
-                       "n_particles": w.n, "precision": "fp64" if fp64 else "mixed (FP32 pairs, FP64 positions)",
-                       "parallelism": f"replicas x{world}", "curve": args.curve,
-                       "l2": "flushed between timed steps (256 MB write)",
-                       "step": "learned-h sph_step (seed from the network trained on the plain solver's steps "
-                               "before the timed region)"},
+            "scaling": "weak", "vs_baseline": None, "dtype": "df64" if r_fp64(w) else "f32", "data": "synthetic",
+            "config": config,
             "steps_per_s": world * args.steps / t_l,
             "learned_h": L, "plain_h": P, "learned_online_h": O,
             "learned_vs_plain_steps_per_s": L["steps_per_s"] / P["steps_per_s"],
+            "learned_vs_plain_evaluations": L["evaluations_per_step"] / P["evaluations_per_step"],
+            "hnet_training": {"protocol": f"{args.train_steps} plain steps each of the 16^3 lattice (variable h) "
+                                          f"and the 64^3 Sedov blast, 40 Adam iterations per step",
+                              "last_loss": losses, "seconds": train_s},
             "e2e": {"value": e_inter / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
                     "steps_per_s": world * args.steps / e2e_s},
             "gpu_launches": L["launches"],
             "neighbour_lists": lists,
             "roofline": roof,
+            "fp32_fma_peak": fp32_peak,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "extra": extras,
         }
         print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def r_fp64(w):
+    return w.params.get("precision", "fp64") == "fp64"
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -383,10 +504,10 @@ def _oracle_sample(w, n_targets, seed=7):
     return int(d.pairs[t].sum()) + f.npairs, dt, t.size, oracle.num_threads(), tests
 
 
-def cpu_baseline(w, seconds=12.0, label="sedov"):
+def cpu_baseline(w, seconds=12.0, label="turbulence"):
     """The oracle as it stands on the host cores, on a sample of target
     particles sized for about `seconds` of work; interactions/s."""
-    nt2 = 64
+    nt2 = 16
     for _ in range(3):                        # grow the sample until it takes about `seconds`
         inter, dt, nt, cores, tests = _oracle_sample(w, nt2)
         if dt >= 0.5 * seconds or nt2 >= w.n:
@@ -404,9 +525,10 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    w = make_workload(args)
+    w = make_workload(args.workload, args.n_side)
     if w.dt is None:
         w.dt = 0.0
+    # about 0.2 s of brute force per step on 16 host cores at any size
     per_step = max(16, int(512 * 262144 / w.n))
     for _ in range(args.warmup):
         _oracle_sample(w, per_step, seed=1)
@@ -416,13 +538,20 @@ def run_reference(args):
         inter += i
         secs += dt
     v = inter / secs
+    fp64 = r_fp64(w)
+    config = {"workload": workload_label(args.workload, w, args.n_side), "n_particles": w.n,
+              "precision": "fp64 (double-float pair sums)" if fp64 else "mixed (FP32 pairs, FP64 positions)",
+              "parallelism": f"replicas x{world}", "curve": args.curve,
+              "l2": "inputs larger than L2; also flushed between timed steps (256 MB write)",
+              "step": "learned-h sph_step (seed from the frozen network trained on 200 plain steps each of the "
+                      "16^3 lattice and the 64^3 Sedov blast before the timed region)"}
+    sample = (f"{per_step} random targets per step of the {w.n}-particle state, FP64 oracle h-rho iteration + "
+              f"force pass, brute force over all sources")
     out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": workload_label(args, w), "n_particles": w.n,
-                      "step": f"FP64 oracle h-rho iteration + forces for {per_step} sampled targets"},
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": f"{per_step} random targets per step, brute force over all {w.n} sources"},
+           "config": config,
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

@@ -321,6 +321,18 @@ int sph_hnet_grad(sph_ctx *ctx, const float *feats, const float *target, int64_t
 int sph_hnet_train_step(sph_ctx *ctx, const float *feats, const float *target, int64_t nb,
                         float lr, float *loss_host, void *stream);
 
+/* ---- calibration ------------------------------------------------------------------
+ * The paper has no counterpart to this call: it measures the hardware the
+ * library runs on.  sph_peak_fp32 times independent FP32 fused multiply-add
+ * chains (8 per thread, 2048 threads per SM) on the current device, one
+ * warm-up launch and the best of five, and writes the rate in TFLOP/s
+ * (2 flops per FMA) to *tflops (host) and that launch's duration to *ms
+ * (host, may be NULL).  This is the measured ceiling of the pair kernels,
+ * which are bound by the FP32 pipe.  Unlike the context calls it allocates
+ * (and frees) a small device buffer; it synchronises `stream`.
+ * SPH_ERR_ARG if tflops is NULL, SPH_ERR_CUDA if a CUDA call fails. */
+int sph_peak_fp32(double *tflops, double *ms, void *stream);
+
 /* ---- allocation-free sort ------------------------------------------------------
  * The paper has no counterpart to this call; it exists for callers that cannot
  * allocate device memory: code running under a framework whose caching

@@ -82,7 +82,7 @@ EXPORTED = ["sph_create", "sph_destroy", "sph_set_params", "sph_last_error", "sp
             "sph_density", "sph_forces", "sph_step", "sph_totals", "sph_morton_keys", "sph_sort_keys",
             "sph_tree_info", "sph_list_info", "sph_export_leaves", "sph_neighbors", "sph_hnet_set_weights",
             "sph_hnet_get_weights", "sph_hnet_features", "sph_hnet_infer", "sph_hnet_seed", "sph_hnet_grad",
-            "sph_hnet_train_step", "sph_sort_keys_noalloc"]
+            "sph_hnet_train_step", "sph_sort_keys_noalloc", "sph_peak_fp32"]
 SPH_SORT_NOALLOC_MAX = 262144
 
 
@@ -126,6 +126,7 @@ def load(path: str | None = None):
         "sph_hnet_grad": ([V, V, V, I64, V, V, V], I32),
         "sph_hnet_train_step": ([V, V, V, I64, _c.c_float, V, V], I32),
         "sph_sort_keys_noalloc": ([I64, V, V, V, V], I32),
+        "sph_peak_fp32": ([_c.POINTER(_c.c_double), _c.POINTER(_c.c_double), V], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -364,6 +365,15 @@ def sph_sort_keys_noalloc(keys: torch.Tensor, ids: torch.Tensor | None, stream=N
     if st != SPH_OK:
         raise SphError(st, "sph_sort_keys_noalloc failed (n must be in [1, %d])" % SPH_SORT_NOALLOC_MAX)
     return perm
+
+
+def sph_peak_fp32(stream=None) -> dict:
+    """Measured FP32 fused multiply-add rate of the current device (TFLOP/s)."""
+    tf, ms = _c.c_double(), _c.c_double()
+    st = load().sph_peak_fp32(_c.byref(tf), _c.byref(ms), _stream(stream))
+    if st != SPH_OK:
+        raise SphError(st, "sph_peak_fp32 failed")
+    return {"tflops": float(tf.value), "ms": float(ms.value)}
 
 
 def sph_tree_info(ctx: Context):
