@@ -58,7 +58,9 @@ F_FORCE = 96
 SM_COUNT, SM_MHZ = 152, 2070.0
 FP64_PIPE_TFLOPS = SM_COUNT * 2 * 2 * SM_MHZ * 1e6 / 1e12
 FP32_PIPE_TFLOPS = SM_COUNT * 128 * 2 * SM_MHZ * 1e6 / 1e12
-DF_PER_FP32 = 2.0 / 18.0
+# One FP32 instruction is half an FP32 FMA's 2 flops, so the double-float
+# ceiling in FP64 flops is the FP32 flop rate x (1/2) x (2/18) = rate / 18.
+DF_PER_FP32 = 1.0 / 18.0
 # DRAM bytes per launch of a dominant kernel from one ncu capture (profiles/),
 # with the hash of the sources it was taken on and the particles of the
 # captured launch (traffic scales with the particles at a fixed neighbour
@@ -250,7 +252,9 @@ def summarize(ms, st):
                 # tree, h seed, density iteration (lists + sweeps), forces and the rest
                 ms_phase={k: sum(f(s) for s in st) / len(st) for k, f in (
                     ("tree", lambda s: s["ms_tree"]), ("hnet", lambda s: s["ms_hnet"]),
-                    ("density", lambda s: s["density"]["ms"]), ("forces_kick_totals", lambda s: s["forces"]["ms"]),
+                    ("density", lambda s: s["density"]["ms"]), ("lists", lambda s: s["density"]["lists_ms"]),
+                    ("sweeps", lambda s: s["density"]["kernel_ms"]),
+                    ("forces_kick_totals", lambda s: s["forces"]["ms"]),
                     ("total", lambda s: s["ms_total"]))},
                 tree_moved=[s["tree_moved"] for s in st])
 
@@ -508,7 +512,7 @@ def cpu_baseline(w, seconds=12.0, label="turbulence"):
     """The oracle as it stands on the host cores, on a sample of target
     particles sized for about `seconds` of work; interactions/s."""
     nt2 = 16
-    for _ in range(3):                        # grow the sample until it takes about `seconds`
+    for _ in range(5):                        # grow the sample until it takes about `seconds`
         inter, dt, nt, cores, tests = _oracle_sample(w, nt2)
         if dt >= 0.5 * seconds or nt2 >= w.n:
             break

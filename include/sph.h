@@ -154,6 +154,7 @@ typedef struct {
     int64_t launches;        /* kernels launched by the call                        */
     double ms;               /* device time of the call (CUDA events)               */
     double kernel_ms;        /* device time of the density-sum kernels alone        */
+    double lists_ms;         /* device time of the call's neighbour-list builds     */
 } sph_density_stats;
 
 typedef struct {
@@ -191,6 +192,8 @@ int sph_create(const sph_params *params, int64_t n_max, sph_ctx **out);
 void sph_destroy(sph_ctx *ctx);
 /* Replace the parameters (same validation; precision and capacity fixed). */
 int sph_set_params(sph_ctx *ctx, const sph_params *params);
+/* Message of the last failing call on ctx; with ctx == NULL, the message of
+ * the calling thread's last failing context-free call (sph_sort_keys_noalloc). */
 const char *sph_last_error(const sph_ctx *ctx);
 /* Library build string, e.g. "sph sm_103a". */
 const char *sph_version(void);
@@ -343,18 +346,24 @@ int sph_peak_fp32(double *tflops, double *ms, void *stream);
  * sph_sort_keys_noalloc computes the same permutation as sph_sort_keys
  * ((keys[perm[i]], ids[perm[i]]) ascending; ids may be NULL, then ties keep
  * index order) with no context.  keys (n), ids (n) and perm (n) are caller
- * device arrays.  Its scratch is one static device array of about 6.1 MB in
- * the library, present on every device that loads the library until the
- * process exits; the call itself never calls cudaMalloc or cudaFree.
+ * arrays in device memory of the CURRENT device.  Its scratch is one static
+ * device array of about 6.1 MB in the library, present on every device that
+ * loads the library until the process exits; the call itself never calls
+ * cudaMalloc or cudaFree.
  *   - n must be in [1, SPH_SORT_NOALLOC_MAX]; larger n returns
  *     SPH_ERR_CAPACITY without touching the GPU.  A run of more than 64 equal
  *     keys also returns SPH_ERR_CAPACITY.
- *   - The first call on a device looks up the device address of the static
- *     array; make that first call before any stream capture on the device.
+ *   - keys, perm (and ids when not NULL) must be device memory of the current
+ *     device; otherwise SPH_ERR_ARG, checked before anything is launched.
+ *   - Every call looks up the device address of the static array on the
+ *     current device (a device reset moves it); the first call on a device
+ *     also loads the library's device code there, so make that first call
+ *     before any stream capture on the device.
  *   - Every call uses the same scratch and leaves the last call's contents in
  *     it.  Calls that overlap on the GPU (other streams, other threads, same
  *     device) race: serialise them.
  *   - The call synchronises `stream` before returning (it reads a status word).
+ *   - On failure sph_last_error(NULL) gives the reason (per calling thread).
  */
 #define SPH_SORT_NOALLOC_MAX 262144
 int sph_sort_keys_noalloc(int64_t n, const uint64_t *keys, const uint32_t *ids, uint32_t *perm,

@@ -61,7 +61,7 @@ class sph_density_stats(_c.Structure):
     _fields_ = [("sweeps", _c.c_int32), ("list_builds", _c.c_int32), ("n_unconverged", _c.c_int64),
                 ("n_hbounds", _c.c_int64), ("interactions", _c.c_int64), ("list_entries", _c.c_int64),
                 ("evaluations", _c.c_int64), ("launches", _c.c_int64), ("ms", _c.c_double),
-                ("kernel_ms", _c.c_double)]
+                ("kernel_ms", _c.c_double), ("lists_ms", _c.c_double)]
 
 
 class sph_force_stats(_c.Structure):
@@ -136,9 +136,9 @@ def load(path: str | None = None):
     return lib
 
 
-def _stream(stream) -> int:
+def _stream(stream, device=None) -> int:
     if stream is None:
-        stream = torch.cuda.current_stream()
+        stream = torch.cuda.current_stream(device)
     return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
 
 
@@ -355,15 +355,20 @@ def sph_sort_keys(ctx: Context, keys: torch.Tensor, ids: torch.Tensor | None, st
     return perm
 
 
-def sph_sort_keys_noalloc(keys: torch.Tensor, ids: torch.Tensor | None, stream=None) -> torch.Tensor:
+def sph_sort_keys_noalloc(keys: torch.Tensor, ids: torch.Tensor | None, stream=None,
+                          perm: torch.Tensor | None = None) -> torch.Tensor:
     """(key, id) sort permutation without a context or any device allocation
-    by the library (the permutation tensor here is the caller's own)."""
+    by the library (the permutation tensor here is the caller's own; pass
+    ``perm`` to reuse one).  Runs on the keys' device, on ``stream`` or that
+    device's current stream."""
     n = keys.numel()
-    perm = torch.empty(n, dtype=torch.int32, device=keys.device)
-    st = load().sph_sort_keys_noalloc(n, keys.data_ptr(), ids.data_ptr() if ids is not None else None,
-                                       perm.data_ptr(), _stream(stream))
-    if st != SPH_OK:
-        raise SphError(st, "sph_sort_keys_noalloc failed (n must be in [1, %d])" % SPH_SORT_NOALLOC_MAX)
+    with torch.cuda.device(keys.device):
+        if perm is None:
+            perm = torch.empty(n, dtype=torch.int32, device=keys.device)
+        st = load().sph_sort_keys_noalloc(n, keys.data_ptr(), ids.data_ptr() if ids is not None else None,
+                                           perm.data_ptr(), _stream(stream, keys.device))
+        if st != SPH_OK:
+            raise SphError(st, load().sph_last_error(None).decode())
     return perm
 
 

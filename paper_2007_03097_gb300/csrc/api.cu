@@ -184,6 +184,7 @@ int allocate(sph_ctx *c, int64_t N)
     SPH_CUDA(cudaEventCreateWithFlags(&c->ev_order, cudaEventDisableTiming));
     SPH_CUDA(cudaEventCreateWithFlags(&c->ev_seed, cudaEventDisableTiming));
     for (cudaEvent_t &e : c->kev) SPH_CUDA(cudaEventCreate(&e));
+    for (cudaEvent_t &e : c->lev) SPH_CUDA(cudaEventCreate(&e));
     SPH_TRY(hnet_init(c));
     return SPH_OK;
 }
@@ -215,6 +216,8 @@ void release(sph_ctx *c)
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : c->kev)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->lev)
+        if (e) cudaEventDestroy(e);
 }
 
 inline cudaStream_t S(void *stream) { return (cudaStream_t)stream; }
@@ -235,6 +238,13 @@ int join_side(sph_ctx *ctx, cudaStream_t s, bool host)
     ctx->side_pending = false;
     return SPH_OK;
 }
+
+// message of the last failing context-free call of this thread
+namespace {
+thread_local std::string t_free_err = "no error";
+}
+
+void noalloc_fail(const std::string &msg) { t_free_err = msg; }
 
 extern "C" {
 
@@ -291,7 +301,7 @@ int sph_set_params(sph_ctx *ctx, const sph_params *params)
     return SPH_OK;
 }
 
-const char *sph_last_error(const sph_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+const char *sph_last_error(const sph_ctx *ctx) { return ctx ? ctx->err.c_str() : t_free_err.c_str(); }
 
 int sph_build_tree(sph_ctx *ctx, sph_particles *p, void *stream)
 {
@@ -404,6 +414,7 @@ int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet, sph_step_s
         local.density.n_unconverged = again.n_unconverged;
         local.density.n_hbounds = again.n_hbounds;
         local.density.kernel_ms += again.kernel_ms;
+        local.density.lists_ms += again.lists_ms;
         local.density.launches += again.launches;
     }
     if (st != SPH_OK && st != SPH_ERR_H_BOUNDS) return st;

@@ -631,7 +631,9 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
     k_dens_init<T><<<grid_for(n, 256), 256, 0, s>>>((T *)p->h, (const T *)seed, n, q.fixed_h, ctx->it_flags,
                                                      ctx->it_sweeps, ctx->it_lo, ctx->it_hi, ctx->fp64 ? 1 : 0);
     SPH_CHECK_LAUNCH();
+    SPH_CUDA(cudaEventRecord(ctx->lev[0], s));
     SPH_TRY(lists_build(ctx, p, s));
+    SPH_CUDA(cudaEventRecord(ctx->lev[1], s));
     k_iota_i32<<<grid_for(ng, 256), 256, 0, s>>>(ctx->act_groups[0], ng);
     SPH_CHECK_LAUNCH();
     DensArgs a{};
@@ -673,6 +675,8 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
     // sweeps, the plain one after four
     const int batch = q.fixed_h ? 1 : (seed ? 3 : 4);
     int cur = 0, launched = 0, rebuilds = 0;
+    bool rebuilt = false;                  // a rebuild is timed by lev[2..3] until the next synchronisation
+    double lists_ms = 0.0;
     for (;;) {
         for (int j = 0; j < batch && launched < max_launch; ++j) {
             k_begin_sweep<<<1, 1, 0, s>>>(ctx->dcnt, cur ^ 1);
@@ -703,15 +707,29 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
             ++launched;
         }
         SPH_TRY(sync_counters(ctx, s));
+        if (rebuilt) {
+            float f = 0.f;
+            SPH_CUDA(cudaEventElapsedTime(&f, ctx->lev[2], ctx->lev[3]));
+            lists_ms += f;
+            rebuilt = false;
+        }
         if (ctx->hcnt->err & (ERRB_LIST_CAPACITY | ERRB_STACK))
             return sph_fail(ctx, SPH_ERR_CAPACITY, "sph_density: neighbour-list capacity exceeded");
         if (ctx->hcnt->act_count[cur] == 0 || launched >= max_launch) break;
         if (ctx->hcnt->n_uncovered > 0) {
+            SPH_CUDA(cudaEventRecord(ctx->lev[2], s));
             SPH_TRY(lists_build(ctx, p, s));
+            SPH_CUDA(cudaEventRecord(ctx->lev[3], s));
             k_clear_uncovered<<<1, 1, 0, s>>>(ctx->dcnt);
             SPH_CHECK_LAUNCH();
             ++rebuilds;
+            rebuilt = true;
         }
+    }
+    {
+        float f = 0.f;
+        SPH_CUDA(cudaEventElapsedTime(&f, ctx->lev[0], ctx->lev[1]));
+        lists_ms += f;
     }
     double kernel_ms = 0.0;
     for (int k = 0; k < launched && k < 64; ++k) {
@@ -729,6 +747,7 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
         st->list_entries = (int64_t)ctx->hcnt->list_used;
         st->evaluations = (int64_t)ctx->hcnt->evaluations;
         st->kernel_ms = kernel_ms;
+        st->lists_ms = lists_ms;
         st->launches = ctx->launches - launches0;
     }
     if (ctx->hcnt->act_count[cur] > 0)

@@ -7,9 +7,10 @@
 //   Pi_ab = (-alpha cbar mu + beta mu^2) / rhobar if v_ab.r_ab < 0 else 0.
 // Also: div v_a = -(1/rho_a) sum_{r_ab < 2 h_a} m_b v_ab . grad_a W(r_ab, h_a)
 // and the signal speed vsig_a = max_b (c_a + c_b - 3 min(0, v_ab . rhat_ab)).
-// One warp per target group, one lane per target, each lane walking its own
-// neighbour list and testing every entry exactly.
-// SPH_MIXED: FP32 throughout (reciprocal square root for 1/r).  SPH_FP64: pair terms in double-float on the
+// One lane per target, walking its own neighbour list and testing every entry
+// exactly.  SPH_MIXED: FP32 throughout (reciprocal square root for 1/r), one
+// block per target group with the group's sources staged in shared memory
+// (see k_forces_f32).  SPH_FP64: one warp per group, pair terms in double-float on the
 // FP32 pipes, membership decided in FP32 outside a 1e-5 relative band around
 // each threshold and by the exact FP64 r^2 inside it.
 #include "dfloat.cuh"
@@ -28,6 +29,8 @@ struct ForceArgs {
     const uint32_t *uni;           // group source unions
     const int64_t *uoff;
     const int32_t *group_img;      // 1: the group's sources include periodic images
+    const int32_t *group_union;    // union size per group
+    const float4 *group_lo, *group_hi;
     int n_groups;
     const double *x, *y, *z;
     const float4 *srcA, *srcB, *srcC, *srcD, *srcE, *srcF;
@@ -41,104 +44,198 @@ struct ForceArgs {
     DevCounters *cnt;
 };
 
-// SPH_MIXED force pass in FP32: sources packed as A {xh, xl, yh, yl},
-// B {zh, zl, m, -}, C {vx, vy, vz, h}, D {rho, P/rho^2, c, -}.
-template <int KS>
-__global__ void __launch_bounds__(FW * 32) k_forces_f32(ForceArgs a)
+// ---------------------------------------------------------------- SPH_MIXED
+// One block of FB warps per target group.  The group's source union (the
+// sources any of its targets lists, in list-walk order) is staged once into
+// shared memory, UC sources at most, as three records per source:
+//   sP {x, y, z relative to the group centre (periodic image folded in), h}
+//   sV {vx, vy, vz, m}          copied with cp.async from the packed record C
+//   sT {rho, P/rho^2, c, h}     copied with cp.async from the packed record D
+// Every warp holds the group's 32 targets (one per lane) and walks every FB-th
+// quad of its lanes' lists (quads q = w, w + FB, ...), reading its sources
+// from shared memory; the FB partial sums of each target are added in warp
+// order at the end.  Union entries past UC (a rare, very large union) are
+// read from global memory with the same arithmetic.
+constexpr int FB = 4;          // warps per block (one target group per block)
+constexpr int UC = 512;        // union sources staged per group (24 KB of shared memory)
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
-    const int lane = threadIdx.x & 31;
-    const int g = blockIdx.x * FW + (threadIdx.x >> 5);
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// source b relative to the group centre (gcx, gcy, gcz), its nearest periodic
+// image when the group's sources include images: the same arithmetic as the
+// density sweep's staged sources
+__device__ __forceinline__ float4 rel_pos(const float4 qa, const float4 qb, float gcx, float gcy, float gcz,
+                                          bool img, float L, float invL, float h)
+{
+    float rx = qa.x - gcx, ry = qa.z - gcy, rz = qb.x - gcz;
+    if (img) {
+        rx = wrap_diff(qa.x, gcx, L, invL);
+        ry = wrap_diff(qa.z, gcy, L, invL);
+        rz = wrap_diff(qb.x, gcz, L, invL);
+    }
+    return make_float4(rx + qa.y, ry + qa.w, rz + qb.y, h);
+}
+
+template <int KS>
+__global__ void __launch_bounds__(FB * 32, 8) k_forces_f32(ForceArgs a)
+{
+    __shared__ float4 sP[UC], sV[UC], sT[UC];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int g = blockIdx.x;
     if (g >= a.n_groups) return;
     const int gb = a.group_begin[g], ge = a.group_begin[g + 1];
     const bool tgt = lane < ge - gb;
     const int i = gb + (tgt ? lane : 0);
-    const float4 A = a.srcA[i], Bz = a.srcB[i], C = a.srcC[i], D = a.srcD[i];
-    const float ha = C.w, rhoa = D.x, pra = D.y, ca = D.z;
+    const float4 qlo = a.group_lo[g], qhi = a.group_hi[g];
+    const float gcx = 0.5f * (qlo.x + qhi.x), gcy = 0.5f * (qlo.y + qhi.y), gcz = 0.5f * (qlo.z + qhi.z);
+    const float Lf = (float)a.L, invL = 1.f / Lf;
+    const bool img = a.periodic && a.group_img[g];   // else every source's direct image is the nearest
+    const uint32_t *Ug = a.uni + a.uoff[g];
+    const int U = min(a.group_union[g], UC);
+
+    // ---- stage the union
+    for (int t = threadIdx.x; t < U; t += FB * 32) {
+        const uint32_t b = __ldg(Ug + t);
+        cp_async16(&sV[t], a.srcC + b);
+        cp_async16(&sT[t], a.srcD + b);
+        const float4 qa = __ldg(a.srcA + b), qb = __ldg(a.srcB + b);
+        const float hb = __ldg(reinterpret_cast<const float *>(a.srcD + b) + 3);
+        sP[t] = rel_pos(qa, qb, gcx, gcy, gcz, img, Lf, invL, hb);
+    }
+
+    // ---- the target of this lane (every warp holds the same 32 targets)
+    const float4 A = __ldg(a.srcA + i), Bz = __ldg(a.srcB + i), C = __ldg(a.srcC + i), D = __ldg(a.srcD + i);
+    const float tx = (A.x - gcx) + A.y, ty = (A.z - gcy) + A.w, tz = (Bz.x - gcz) + Bz.y;
+    const float ha = D.w, rhoa = D.x, pra = D.y, ca = D.z;
     const float hainv = 1.f / ha;
-    const float sig = kern_sigma<float>(a.kernel);
-    const float sig_hg = sig * inv_pow_dim(hainv, a.dim) * hainv;     // sigma / h_a^(D+1)
+    const float thr_d = 4.f * ha * ha;
     const float alpha = (float)a.alpha, beta = (float)a.beta, eps = (float)a.eps;
+    const float half_alpha = 0.5f * alpha;
     const int64_t off = a.goff[g];
-    const uint32_t *U = a.uni + a.uoff[g];
-    const int img = a.periodic && a.group_img[g];   // else every source's direct image is the nearest
     int width = tgt ? a.gwidth[g] : 0;
     if (off + 32 * (int64_t)width > a.cap) width = 0;    // never read past the lists
-    const float Lf = (float)a.L, half = 0.5f * Lf;
-    const float thr_d = __fmul_rn(__fmul_rn(4.f, ha), ha);
+    const int nq = width >> 2;
+    const unsigned long long *lq = reinterpret_cast<const unsigned long long *>(a.nbl + off) + lane;
+    cp_async_wait_all();
+    __syncthreads();
 
+    // pair sums without the per-target factors sigma (a, du/dt) and
+    // sigma / h_a^(D+1) (div v), applied once at the end
     float accx = 0.f, accy = 0.f, accz = 0.f, du = 0.f, dv = 0.f, vs = ca;
     int nint = 0;
-    // the list entry of slot k + 2 and the union index of slot k + 1 are in
-    // flight while slot k is processed
-    SlotStream st(a.nbl, off, width, lane);
-    auto index = [&](uint32_t e) -> uint32_t { return e == SPH_LOCAL_NONE ? SPH_SENTINEL : __ldg(U + e); };
-    const uint32_t e0 = st.next();
-    uint32_t e2 = st.next();
-    uint32_t b1 = index(e0);
-    for (int k = 0; k < width; ++k) {
-        const uint32_t b = b1;
-        b1 = index(e2);
-        e2 = st.next();
-        if (b == SPH_SENTINEL) continue;
-        const float4 P = a.srcA[b], Q = a.srcB[b], Cb = a.srcC[b];
-        const float dx = sep_f(A.x, A.y, P.x, P.y, img, Lf, half);
-        const float dy = sep_f(A.z, A.w, P.z, P.w, img, Lf, half);
-        const float dz = sep_f(Bz.x, Bz.y, Q.x, Q.y, img, Lf, half);
-        const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-        const float hb = Cb.w;
-        const float hs = __fadd_rn(ha, hb);
-        const bool in_f = r2 < __fmul_rn(hs, hs);
-        const bool in_d = r2 < thr_d;
-        if (!in_f && !in_d) continue;
-        const float4 Db = a.srcD[b];
-        const float rinv = rsqrtf(r2);
-        const float r = r2 * rinv;
-        const float vabx = C.x - Cb.x, vaby = C.y - Cb.y, vabz = C.z - Cb.z;
-        const float vdotr = (vabx * dx + vaby * dy) + vabz * dz;
-        const float mb = Q.z;
-        if (in_d) {
-            float w, dwq;
-            kern_wdw<float>(KS, r * hainv, w, dwq);      // the kernel form fixed at compile time
-            dv += mb * (sig_hg * dwq) * rinv * vdotr;
-        }
-        if (in_f) {
-            // approximate reciprocals (within 2 ulp): the FP32 pass is held
-            // to relative tolerances far above them
-            const float hab = 0.5f * hs;
-            const float habinv = __fdividef(1.f, hab);
-            float w, dwq;
-            kern_wdw<float>(KS, r * habinv, w, dwq);
-            const float h2 = habinv * habinv;
-            const float gr = sig * (a.dim == 1 ? h2 : h2 * h2) * dwq * rinv;   // grad_a W = gr * r_ab
-            float Pi = 0.f;
-            if (vdotr < 0.f) {
-                const float mu = __fdividef(hab * vdotr, r2 + eps * hab * hab);
-                Pi = __fdividef(-alpha * 0.5f * (ca + Db.z) * mu + beta * mu * mu, 0.5f * (rhoa + Db.x));
+    unsigned long long nxt = w < nq ? __ldg(lq + 32 * (int64_t)w) : ~0ull;
+    for (int q = w; q < nq; q += FB) {
+        const unsigned long long quad = nxt;
+        nxt = q + FB < nq ? __ldg(lq + 32 * (int64_t)(q + FB)) : ~0ull;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t e = (uint32_t)(quad >> (16 * u)) & 0xFFFFu;
+            if (e == SPH_LOCAL_NONE) continue;
+            float4 P, V, T;
+            uint32_t b = 0;
+            const bool far = e >= (uint32_t)UC;
+            if (!far) {
+                P = sP[e];
+            } else {                                   // beyond the staged part of the union
+                b = __ldg(Ug + e);
+                T = __ldg(a.srcD + b);
+                P = rel_pos(__ldg(a.srcA + b), __ldg(a.srcB + b), gcx, gcy, gcz, img, Lf, invL, T.w);
             }
-            const float coef = mb * (pra + Db.y + Pi) * gr;
-            accx -= coef * dx;
-            accy -= coef * dy;
-            accz -= coef * dz;
-            if (a.thermo) {
-                // Eq. thermo: -m_b (P_a/rho_a^2 v_b + P_b/rho_b^2 v_a + (v_a + v_b) Pi/2) . grad_a W
-                const float vb_r = (Cb.x * dx + Cb.y * dy) + Cb.z * dz;
-                const float va_r = (C.x * dx + C.y * dy) + C.z * dz;
-                du -= mb * ((pra * vb_r + Db.y * va_r) + Pi * 0.5f * (va_r + vb_r)) * gr;
+            const float dx = tx - P.x, dy = ty - P.y, dz = tz - P.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float hs = ha + P.w;
+            const bool in_f = r2 < hs * hs;
+            const bool in_d = r2 < thr_d;
+            if (!in_f && !in_d) continue;
+            if (!far) {
+                V = sV[e];
+                T = sT[e];
             } else {
-                du += mb * (pra + 0.5f * Pi) * gr * vdotr;
+                V = __ldg(a.srcC + b);
             }
-            const float vr = vdotr * rinv;
-            const float sgn = ca + Db.z - 3.f * (vr < 0.f ? vr : 0.f);
-            vs = sgn > vs ? sgn : vs;
-            ++nint;
+            const float rinv = rsqrtf(r2);
+            const float r = r2 * rinv;
+            const float vabx = C.x - V.x, vaby = C.y - V.y, vabz = C.z - V.z;
+            const float vdotr = fmaf(vabz, dz, fmaf(vaby, dy, vabx * dx));
+            const float mb = V.w;
+            const float rv = vdotr * rinv;             // v_ab . r_ab / r
+            if (in_d) {
+                float w_, dwq;
+                kern_wdw<float>(KS, r * hainv, w_, dwq);   // the kernel form fixed at compile time
+                dv = fmaf(mb * dwq, rv, dv);
+            }
+            if (in_f) {
+                // approximate reciprocals (within 2 ulp): the FP32 pass is held
+                // to relative tolerances far above them
+                const float hab = 0.5f * hs;
+                const float habinv = __fdividef(1.f, hab);
+                float w_, dwq;
+                kern_wdw<float>(KS, r * habinv, w_, dwq);
+                const float h2 = habinv * habinv;
+                const float mg = mb * (a.dim == 1 ? h2 : h2 * h2) * dwq;   // m_b w'(q) / h_ab^(D+1)
+                const float gr = mg * rinv;                                // m_b grad_a W / sigma = gr r_ab
+                float Pi = 0.f;
+                if (vdotr < 0.f) {
+                    const float mu = __fdividef(hab * vdotr, fmaf(eps * hab, hab, r2));
+                    Pi = __fdividef(mu * fmaf(beta, mu, -half_alpha * (ca + T.z)), 0.5f * (rhoa + T.x));
+                }
+                const float coef = (pra + T.y + Pi) * gr;
+                accx = fmaf(-coef, dx, accx);
+                accy = fmaf(-coef, dy, accy);
+                accz = fmaf(-coef, dz, accz);
+                if (a.thermo) {
+                    // Eq. thermo: -m_b (P_a/rho_a^2 v_b + P_b/rho_b^2 v_a + (v_a + v_b) Pi/2) . grad_a W
+                    const float vb_r = fmaf(V.z, dz, fmaf(V.y, dy, V.x * dx));
+                    const float va_r = fmaf(C.z, dz, fmaf(C.y, dy, C.x * dx));
+                    du -= ((pra * vb_r + T.y * va_r) + Pi * 0.5f * (va_r + vb_r)) * gr;
+                } else {
+                    du = fmaf((pra + 0.5f * Pi) * mg, rv, du);
+                }
+                const float sgn = ca + T.z - 3.f * fminf(rv, 0.f);
+                vs = fmaxf(vs, sgn);
+                ++nint;
+            }
         }
     }
+
+    // ---- the FB partial sums of each target, added in warp order
+    __syncthreads();                                   // the union is no longer read
+    float *red = reinterpret_cast<float *>(sP);        // [FB][7][32]
+    red[(w * 7 + 0) * 32 + lane] = accx;
+    red[(w * 7 + 1) * 32 + lane] = accy;
+    red[(w * 7 + 2) * 32 + lane] = accz;
+    red[(w * 7 + 3) * 32 + lane] = du;
+    red[(w * 7 + 4) * 32 + lane] = dv;
+    red[(w * 7 + 5) * 32 + lane] = vs;
+    red[(w * 7 + 6) * 32 + lane] = __int_as_float(nint);
+    __syncthreads();
+    if (w != 0) return;
+    for (int v = 1; v < FB; ++v) {
+        accx += red[(v * 7 + 0) * 32 + lane];
+        accy += red[(v * 7 + 1) * 32 + lane];
+        accz += red[(v * 7 + 2) * 32 + lane];
+        du += red[(v * 7 + 3) * 32 + lane];
+        dv += red[(v * 7 + 4) * 32 + lane];
+        vs = fmaxf(vs, red[(v * 7 + 5) * 32 + lane]);
+        nint += __float_as_int(red[(v * 7 + 6) * 32 + lane]);
+    }
     if (tgt) {
-        ((float *)a.ax)[i] = accx;
-        ((float *)a.ay)[i] = accy;
-        ((float *)a.az)[i] = accz;
-        ((float *)a.dudt)[i] = du;
-        ((float *)a.divv)[i] = -dv / rhoa;
+        const float sig = kern_sigma<float>(a.kernel);
+        const float sig_hg = sig * inv_pow_dim(hainv, a.dim) * hainv;     // sigma / h_a^(D+1)
+        ((float *)a.ax)[i] = sig * accx;
+        ((float *)a.ay)[i] = sig * accy;
+        ((float *)a.az)[i] = sig * accz;
+        ((float *)a.dudt)[i] = sig * du;
+        ((float *)a.divv)[i] = -sig_hg * dv / rhoa;
         ((float *)a.vsig)[i] = vs;
     }
     for (int o = 16; o > 0; o >>= 1) nint += __shfl_xor_sync(0xffffffffu, nint, o);
@@ -147,12 +244,12 @@ __global__ void __launch_bounds__(FW * 32) k_forces_f32(ForceArgs a)
 
 // Equation of state and packed FP32 force-pass sources: P = (gamma-1) rho u,
 // c = sqrt(gamma (gamma-1) u) to the caller's P and c, and the records
-// C {vx, vy, vz, h}, D {rho, P/rho^2, c, 0}.
+// C {vx, vy, vz, m}, D {rho, P/rho^2, c, h}.
 __global__ void k_pack_force_f32(const float *__restrict__ vx, const float *__restrict__ vy,
-                                 const float *__restrict__ vz, const float *__restrict__ h,
-                                 const float *__restrict__ rho, const float *__restrict__ u, float g1, float gg1,
-                                 int64_t n, float *__restrict__ P, float *__restrict__ c, float4 *__restrict__ C,
-                                 float4 *__restrict__ D)
+                                 const float *__restrict__ vz, const float *__restrict__ m,
+                                 const float *__restrict__ h, const float *__restrict__ rho,
+                                 const float *__restrict__ u, float g1, float gg1, int64_t n, float *__restrict__ P,
+                                 float *__restrict__ c, float4 *__restrict__ C, float4 *__restrict__ D)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -160,8 +257,8 @@ __global__ void k_pack_force_f32(const float *__restrict__ vx, const float *__re
     const float pi = g1 * r * ui, ci = sqrtf(gg1 * ui);
     P[i] = pi;
     c[i] = ci;
-    C[i] = make_float4(vx[i], vy[i], vz[i], h[i]);
-    D[i] = make_float4(r, pi / (r * r), ci, 0.f);
+    C[i] = make_float4(vx[i], vy[i], vz[i], m[i]);
+    D[i] = make_float4(r, pi / (r * r), ci, h[i]);
 }
 
 // SPH_FP64 force pass in double-float (see the file comment).
@@ -359,9 +456,9 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
             ctx->srcC, ctx->srcD, ctx->srcE, ctx->srcF);
     else
         k_pack_force_f32<<<grid_for(p->n, 256), 256, 0, s>>>(
-            (const float *)vx, (const float *)vy, (const float *)vz, (const float *)p->h, (const float *)p->rho,
-            (const float *)u, (float)(g - 1.0), (float)(g * (g - 1.0)), p->n, (float *)p->P, (float *)p->c, ctx->srcC,
-            ctx->srcD);
+            (const float *)vx, (const float *)vy, (const float *)vz, (const float *)p->m, (const float *)p->h,
+            (const float *)p->rho, (const float *)u, (float)(g - 1.0), (float)(g * (g - 1.0)), p->n, (float *)p->P,
+            (float *)p->c, ctx->srcC, ctx->srcD);
     SPH_CHECK_LAUNCH();
     if (!reuse_lists || !ctx->lists_valid) SPH_TRY(lists_build(ctx, p, s));
     ForceArgs a{};
@@ -382,6 +479,9 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
     a.dim = ctx->prm.dim;
     a.periodic = ctx->prm.periodic;
     a.group_img = ctx->group_img;
+    a.group_union = ctx->group_union;
+    a.group_lo = ctx->group_lo;
+    a.group_hi = ctx->group_hi;
     a.thermo = ctx->prm.energy == SPH_ENERGY_TOTAL;
     a.L = ctx->dom[3];
     a.alpha = ctx->prm.alpha; a.beta = ctx->prm.beta; a.eps = ctx->prm.eps_visc;
@@ -392,14 +492,15 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
     SPH_CUDA(cudaEventRecord(ctx->ev[5], s));
     if (ctx->fp64) k_forces_df<<<grid_for(ctx->n_groups, FW), FW * 32, 0, s>>>(a);
     else {
-        // one instantiation per kernel form keeps the pair loop small
-        const unsigned grid = grid_for(ctx->n_groups, FW);
+        // one instantiation per kernel form keeps the pair loop small; one
+        // block per target group
+        const unsigned grid = grid_for(ctx->n_groups, 1);
         switch (a.kernel) {
-        case 1: k_forces_f32<1><<<grid, FW * 32, 0, s>>>(a); break;
-        case 2: k_forces_f32<2><<<grid, FW * 32, 0, s>>>(a); break;
-        case 4: k_forces_f32<4><<<grid, FW * 32, 0, s>>>(a); break;
-        case 5: k_forces_f32<5><<<grid, FW * 32, 0, s>>>(a); break;
-        default: k_forces_f32<0><<<grid, FW * 32, 0, s>>>(a); break;   // M4, either D
+        case 1: k_forces_f32<1><<<grid, FB * 32, 0, s>>>(a); break;
+        case 2: k_forces_f32<2><<<grid, FB * 32, 0, s>>>(a); break;
+        case 4: k_forces_f32<4><<<grid, FB * 32, 0, s>>>(a); break;
+        case 5: k_forces_f32<5><<<grid, FB * 32, 0, s>>>(a); break;
+        default: k_forces_f32<0><<<grid, FB * 32, 0, s>>>(a); break;   // M4, either D
         }
     }
     SPH_CHECK_LAUNCH();

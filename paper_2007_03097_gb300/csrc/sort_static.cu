@@ -6,9 +6,13 @@
 //
 // The kernels are those of the context path (tree.cu, scan.cu): this file
 // points a context-shaped view at the static array and runs the same sort.
-#include <mutex>
+#include <string>
 
 #include "sph_internal.cuh"
+
+// message of the last failing context-free call of this thread
+// (sph_last_error(NULL) returns it)
+void noalloc_fail(const std::string &msg);
 
 namespace {
 
@@ -28,24 +32,35 @@ constexpr size_t SCRATCH_BYTES = OFF_CNT + align256(sizeof(DevCounters));
 // ~6.1 MB, held by every device that loads the library until the process exits
 static __device__ __align__(256) unsigned char g_sort_scratch[SCRATCH_BYTES];
 
-constexpr int MAX_DEVICES = 64;
-std::mutex g_mu;
-void *g_addr[MAX_DEVICES] = {};
-
 // Device address of the static array on the current device.  In host code
-// the symbol is only a host-side stand-in, so it is looked up once per device
-// with cudaGetSymbolAddress (the first call on a device does this).
-int scratch_address(int dev, unsigned char **out)
+// the symbol is only a host-side stand-in, so its device address is looked up
+// with cudaGetSymbolAddress on every call, with the device current: the first
+// call on a device also loads the library's device code there (so it must
+// come before any stream capture on that device), and a device reset gives
+// the array a new address, so none is kept between calls.
+int scratch_address(unsigned char **out)
 {
-    if (dev < 0 || dev >= MAX_DEVICES) return SPH_ERR_ARG;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || !p) return SPH_ERR_CUDA;
-        g_addr[dev] = p;
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
+    if (e != cudaSuccess || !p) {
+        noalloc_fail(std::string("cudaGetSymbolAddress of the sort scratch: ") + cudaGetErrorString(e));
+        return SPH_ERR_CUDA;
     }
-    *out = (unsigned char *)g_addr[dev];
+    *out = (unsigned char *)p;
     return SPH_OK;
+}
+
+// nullptr if ptr is device (or managed) memory of device dev, else the reason
+const char *not_on_device(const void *ptr, int dev)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();                       // clear the error the failed query recorded
+        return "is not a CUDA pointer";
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return "is not device memory";
+    if (at.device != dev) return "lives on another device than the current one";
+    return nullptr;
 }
 
 }  // namespace
@@ -53,12 +68,32 @@ int scratch_address(int dev, unsigned char **out)
 extern "C" int sph_sort_keys_noalloc(int64_t n, const uint64_t *keys, const uint32_t *ids, uint32_t *perm,
                                      void *stream)
 {
-    if (n < 1 || !keys || !perm) return SPH_ERR_ARG;
-    if (n > NOALLOC_MAX) return SPH_ERR_CAPACITY;
+    if (n < 1 || !keys || !perm) {
+        noalloc_fail("sph_sort_keys_noalloc: n must be >= 1 and keys, perm must not be NULL");
+        return SPH_ERR_ARG;
+    }
+    if (n > NOALLOC_MAX) {
+        noalloc_fail("sph_sort_keys_noalloc: n = " + std::to_string(n) + " exceeds the static scratch (at most " +
+                     std::to_string(NOALLOC_MAX) + " keys)");
+        return SPH_ERR_CAPACITY;
+    }
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return SPH_ERR_CUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        noalloc_fail("sph_sort_keys_noalloc: no current CUDA device");
+        return SPH_ERR_CUDA;
+    }
+    const void *ptrs[3] = {keys, ids, perm};
+    const char *names[3] = {"keys", "ids", "perm"};
+    for (int k = 0; k < 3; ++k) {
+        if (!ptrs[k]) continue;                   // ids may be NULL
+        if (const char *why = not_on_device(ptrs[k], dev)) {
+            noalloc_fail(std::string("sph_sort_keys_noalloc: ") + names[k] + " " + why + " (device " +
+                         std::to_string(dev) + ")");
+            return SPH_ERR_ARG;
+        }
+    }
     unsigned char *base = nullptr;
-    const int st = scratch_address(dev, &base);
+    const int st = scratch_address(&base);
     if (st != SPH_OK) return st;
     // a context-shaped view over the static scratch (host object only)
     sph_ctx view;
@@ -74,5 +109,7 @@ extern "C" int sph_sort_keys_noalloc(int64_t n, const uint64_t *keys, const uint
     view.dcnt = (DevCounters *)(base + OFF_CNT);
     DevCounters host_counters{};
     view.hcnt = &host_counters;
-    return tree_sort(&view, n, keys, ids, perm, (cudaStream_t)stream);
+    const int r = tree_sort(&view, n, keys, ids, perm, (cudaStream_t)stream);
+    if (r != SPH_OK) noalloc_fail(view.err.empty() ? std::string("sph_sort_keys_noalloc failed") : view.err);
+    return r;
 }

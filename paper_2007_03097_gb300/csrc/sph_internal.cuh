@@ -250,6 +250,7 @@ struct sph_ctx {
     cudaEvent_t ev_order = nullptr, ev_seed = nullptr;   // particles in key order; h seed written (side stream)
     bool side_pending = false;
     cudaEvent_t kev[2 * 64] = {};       // per-sweep density kernel events
+    cudaEvent_t lev[4] = {};            // list builds of the density iteration (first, rebuild)
     int64_t launches = 0;               // kernels launched so far
     int64_t force_launches = 0;         // kernels of the last force pass
 };
