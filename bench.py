@@ -190,48 +190,6 @@ def src_hash(files):
     return hsh.hexdigest()[:12]
 
 
-def initial_theta(seed=1234):
-    """Seeded initial weights of the 5 -> 64 -> 64 -> 1 network (flat layout
-    of include/sph.h: W1, b1, W2, b2, W3, b3)."""
-    rng = np.random.default_rng(seed)
-    return np.concatenate([rng.normal(scale=s, size=k) for s, k in
-                           ((1 / math.sqrt(5), 320), (0, 64), (1 / 8, 4096), (0, 64), (1 / 8, 64), (0, 1))]
-                          ).astype(np.float32)
-
-
-def train_protocol(B, steps):
-    """Train the h-predictor on the plain solver's own h trajectories:
-    `steps` plain steps of the 16^3 lattice with variable h (M4, eta 1.2)
-    and `steps` plain steps of the 64^3 Sedov blast, one online Adam round of
-    40 iterations per step (library kernels).  Returns the frozen weights and
-    the last loss of each run."""
-    from paper_2007_03097_gb300 import inputs
-    theta = initial_theta()
-    losses = {}
-    for name, w in (("lattice16_variable_h", inputs.lattice(16, kernel=inputs.M4, fixed_h=False)),
-                    ("sedov64", inputs.sedov(64))):
-        params = dict(w.params)
-        params.update(hnet_batch=8192, hnet_iters=40, hnet_lr=1e-3)
-        ctx = B.Context(params, w.n)
-        p = B.Particles.from_workload(w, fp64=params.get("precision", "fp64") == "fp64")
-        B.sph_build_tree(ctx, p)
-        B.sph_density(ctx, p)
-        B.sph_forces(ctx, p)
-        B.sph_hnet_set_weights(ctx, theta)
-        # the workload's fixed step, else the initial CFL step kept fixed
-        dt = w.dt if w.dt else float(params["cfl"] * (p.h / p.vsig).min().item())
-        last = None
-        for _ in range(steps):
-            st = B.sph_step(ctx, p, dt, use_hnet=B.SPH_HNET_TRAIN)
-            last = st["hnet_loss"]
-        B.sph_step(ctx, p, dt, use_hnet=0)       # joins the last training round
-        theta = B.sph_hnet_get_weights(ctx)
-        losses[name] = last
-        ctx.close()
-        del p
-    return theta, losses
-
-
 def summarize(ms, st):
     t = sum(ms) / 1e3
     inter = sum(s["density"]["interactions"] + s["forces"]["interactions"] for s in st)
@@ -416,8 +374,9 @@ def run_sph(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     # the h-predictor: trained on the plain solver's trajectories (untimed), frozen
+    from paper_2007_03097_gb300 import hnet_protocol
     t0 = time.perf_counter()
-    theta, losses = train_protocol(B, args.train_steps)
+    theta, losses = hnet_protocol.train(steps=args.train_steps)
     train_s = time.perf_counter() - t0
     fp32_peak = B.sph_peak_fp32()
 

@@ -324,6 +324,18 @@ int sph_hnet_grad(sph_ctx *ctx, const float *feats, const float *target, int64_t
 int sph_hnet_train_step(sph_ctx *ctx, const float *feats, const float *target, int64_t nb,
                         float lr, float *loss_host, void *stream);
 
+/* ---- test hook --------------------------------------------------------------------
+ * The paper has no counterpart to this call.  The tensor-core kernels of the
+ * h-predictor wait for their MMAs with a bounded wait (1 s), after which they
+ * record an error, free their tensor memory and return, and the call returns
+ * SPH_ERR_CUDA with the context still usable.  sph_test_hooks lets a test
+ * take that path without any GPU fault: with SPH_TEST_SKIP_MMA set, those
+ * kernels issue no MMA, so the wait runs out (about 2 s per call: the wait and
+ * one more bounded wait for work in flight).  flags = 0 restores normal
+ * operation.  SPH_ERR_ARG for a NULL context or an unknown flag. */
+#define SPH_TEST_SKIP_MMA 1
+int sph_test_hooks(sph_ctx *ctx, int flags);
+
 /* ---- calibration ------------------------------------------------------------------
  * The paper has no counterpart to this call: it measures the hardware the
  * library runs on.  sph_peak_fp32 times independent FP32 fused multiply-add

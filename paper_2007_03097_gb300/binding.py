@@ -82,7 +82,7 @@ EXPORTED = ["sph_create", "sph_destroy", "sph_set_params", "sph_last_error", "sp
             "sph_density", "sph_forces", "sph_step", "sph_totals", "sph_morton_keys", "sph_sort_keys",
             "sph_tree_info", "sph_list_info", "sph_export_leaves", "sph_neighbors", "sph_hnet_set_weights",
             "sph_hnet_get_weights", "sph_hnet_features", "sph_hnet_infer", "sph_hnet_seed", "sph_hnet_grad",
-            "sph_hnet_train_step", "sph_sort_keys_noalloc", "sph_peak_fp32"]
+            "sph_hnet_train_step", "sph_sort_keys_noalloc", "sph_peak_fp32", "sph_test_hooks"]
 SPH_SORT_NOALLOC_MAX = 262144
 
 
@@ -127,6 +127,7 @@ def load(path: str | None = None):
         "sph_hnet_train_step": ([V, V, V, I64, _c.c_float, V, V], I32),
         "sph_sort_keys_noalloc": ([I64, V, V, V, V], I32),
         "sph_peak_fp32": ([_c.POINTER(_c.c_double), _c.POINTER(_c.c_double), V], I32),
+        "sph_test_hooks": ([V, I32], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -370,6 +371,13 @@ def sph_sort_keys_noalloc(keys: torch.Tensor, ids: torch.Tensor | None, stream=N
         if st != SPH_OK:
             raise SphError(st, load().sph_last_error(None).decode())
     return perm
+
+
+SPH_TEST_SKIP_MMA = 1
+
+
+def sph_test_hooks(ctx: Context, flags: int) -> None:
+    _check(ctx, load().sph_test_hooks(ctx.handle, int(flags)))
 
 
 def sph_peak_fp32(stream=None) -> dict:

@@ -572,6 +572,14 @@ int sph_hnet_features(sph_ctx *ctx, const sph_particles *p, double dt, float *fe
     return hnet_features(ctx, p, dt, feats, S(stream));
 }
 
+int sph_test_hooks(sph_ctx *ctx, int flags)
+{
+    if (!ctx) return SPH_ERR_ARG;
+    if (flags & ~SPH_TEST_SKIP_MMA) return sph_fail(ctx, SPH_ERR_ARG, "sph_test_hooks: unknown flag");
+    ctx->test_flags = flags;
+    return SPH_OK;
+}
+
 int sph_hnet_infer(sph_ctx *ctx, const float *feats, int64_t nb, float *y, void *stream)
 {
     if (!ctx) return SPH_ERR_ARG;

@@ -252,6 +252,7 @@ struct sph_ctx {
     cudaEvent_t kev[2 * 64] = {};       // per-sweep density kernel events
     cudaEvent_t lev[4] = {};            // list builds of the density iteration (first, rebuild)
     int64_t launches = 0;               // kernels launched so far
+    int test_flags = 0;                 // sph_test_hooks
     int64_t force_launches = 0;         // kernels of the last force pass
 };
 

@@ -157,3 +157,45 @@ def test_empty_input_rejected_and_context_usable():
     p = B.Particles.from_workload(w, fp64=True)
     B.sph_build_tree(ctx, p)
     assert B.sph_density(ctx, p)["status"] == 0
+
+
+def test_seeded_iteration_that_fails_is_rerun_from_the_previous_h():
+    """The plain iteration is the fallback and the judge of a learned seed:
+    host-set weights give seeds up to a factor 2 away from h (accepted as
+    seeds) that cannot converge within max_sweeps = 4 evaluations; the step
+    reruns the iteration from the pre-iteration h, returns OK, counts the
+    restarted particles among its fallbacks, and ends on the plain step's h."""
+    B = need_gpu()
+    w = inputs.lattice(16, jitter=0.2, kernel=inputs.M4, fixed_h=False)
+    rng = np.random.default_rng(4)
+    w.vx, w.vy, w.vz = 0.3 * rng.standard_normal((3, w.n))
+    params = dict(w.params, max_sweeps=4)
+    ctx = B.Context(w.params, w.n)
+    p = B.Particles.from_workload(w, fp64=True)
+    B.sph_build_tree(ctx, p)
+    B.sph_density(ctx, p)
+    B.sph_forces(ctx, p)
+    dt = float(params["cfl"] * (p.h / p.vsig).min().item())
+    B.sph_step(ctx, p, dt)                               # h now follows the flow step by step
+    ctx.set_params(params)
+    snap = {f: getattr(p, f).clone() for f in ["x", "y", "z", "nnb", "id"] + B._FIELDS}
+    s_plain = B.sph_step(ctx, p, dt)
+    h_plain = p.in_original_order(["h"])["h"]
+    for f, v in snap.items():
+        getattr(p, f).copy_(v)
+    # y = b3 for every particle (all other weights zero): the seed is
+    # h exp(b3 div v dt), about 50 % off h for the median particle
+    f3 = np.abs(snap["divv"].cpu().numpy()) * dt
+    theta = np.zeros(B.SPH_HNET_NPARAM, dtype=np.float32)
+    theta[-1] = 0.45 / np.median(f3[f3 > 0])
+    B.sph_hnet_set_weights(ctx, theta)
+    _, rejected = B.sph_hnet_seed(ctx, p, dt)         # seeds beyond a factor 2: kept h, not restarts
+    assert rejected < w.n // 2
+    s = B.sph_step(ctx, p, dt, use_hnet=B.SPH_HNET_SEED)
+    h = p.in_original_order(["h"])["h"]
+    print("fallbacks", s["hnet_fallback"], "rejected seeds", rejected, "evaluations", s["density"]["evaluations"],
+          "plain", s_plain["density"]["evaluations"])
+    assert s["hnet_used"] == 1
+    assert s["hnet_fallback"] > rejected                 # the restarted particles
+    assert s["density"]["evaluations"] > s_plain["density"]["evaluations"]
+    assert np.max(np.abs(h / h_plain - 1)) < 2 * params["h_tol"]

@@ -132,3 +132,27 @@ def test_step_seed_matches_oracle(fp64):
     # dt = 0: f3 = div v dt = 0, every particle keeps its h exactly
     seed0, fb0 = B.sph_hnet_seed(ctx, p, 0.0)
     assert fb0 == 0 and torch.equal(seed0, p.h)
+
+
+def test_bounded_mma_wait_runs_out_and_the_context_is_reused():
+    """With the test hook set, the tensor-core kernel issues no MMA: its 1 s
+    bounded wait runs out, the call returns SPH_ERR_CUDA (no GPU fault), and
+    the same context then infers correctly."""
+    import time
+    B, ctx = _ctx()
+    th = _theta(4)
+    B.sph_hnet_set_weights(ctx, th)
+    X = np.random.default_rng(9).normal(size=(1000, 5)).astype(np.float32)
+    Xd = torch.from_numpy(X).cuda()
+    B.sph_test_hooks(ctx, B.SPH_TEST_SKIP_MMA)
+    t0 = time.perf_counter()
+    with pytest.raises(B.SphError) as e:
+        B.sph_hnet_infer(ctx, Xd)
+    assert e.value.code == B.SPH_ERR_CUDA and "did not complete" in str(e.value)
+    assert time.perf_counter() - t0 < 30.0
+    B.sph_test_hooks(ctx, 0)
+    y = B.sph_hnet_infer(ctx, Xd).cpu().numpy()
+    ref = oracle.hnet_predict(oracle.bf16_round(th), X.astype(np.float64))
+    assert np.max(np.abs(y - ref)) < 2e-5 * max(1.0, np.abs(ref).max())
+    with pytest.raises(B.SphError):
+        B.sph_test_hooks(ctx, 2)
