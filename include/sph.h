@@ -207,8 +207,10 @@ const char *sph_version(void);
  * Returns SPH_ERR_NONFINITE for NaN/Inf positions or h. */
 int sph_build_tree(sph_ctx *ctx, sph_particles *p, void *stream);
 
-/* Eqs. 7 and 9: Newton iteration on h_a until |dh| < h_tol h, then rho,
- * omega = drho/dh and nnb at the final h; P and c from u.  Seeds: h_seed
+/* Eqs. 7 and 9: Newton iteration on h_a until |dh| < h_tol h, then rho and
+ * nnb at the final h (rho to first order in dh when that is exact to the
+ * arithmetic's rounding, else by one more evaluation) and omega = drho/dh at
+ * the last evaluated h (within h_tol h of the final h); P and c from u.  Seeds: h_seed
  * (device, FP64 or FP32 per precision) if not NULL, else the current h.
  * With fixed_h, one evaluation at the given h.  Needs sph_build_tree first. */
 int sph_density(sph_ctx *ctx, sph_particles *p, const void *h_seed,
@@ -263,11 +265,12 @@ int sph_tree_info(sph_ctx *ctx, int64_t *n_leaves, int64_t *n_groups);
  * returned (host out, each may be NULL): slots reserved (32 x the per-group
  * widths the build sized: leaf bounds, or exact counts once exact_sizing is
  * set), slots holding the exact lists, entries of the per-group source
- * unions the lists index, and whether exact sizing is on (set for the rest
- * of the context's life when leaf bounds exceeded nb_capacity).
+ * unions the lists index, whether exact sizing is on (set for the rest of
+ * the context's life when leaf bounds exceeded nb_capacity), and the largest
+ * union of one group.
  * Implementation detail of the list builder; the paper has no counterpart. */
 int sph_list_info(sph_ctx *ctx, int64_t *slots_reserved, int64_t *slots_used, int64_t *union_used,
-                  int32_t *exact_sizing);
+                  int32_t *exact_sizing, int32_t *union_max);
 
 /* After sph_build_tree: leaf_begin (device, n_leaves + 1 entries, the last is
  * n) and level (device, n_leaves; octree level of each leaf cell). */

@@ -115,7 +115,8 @@ def load(path: str | None = None):
         "sph_morton_keys": ([V, _c.POINTER(sph_particles), V, _c.POINTER(_c.c_double), V], I32),
         "sph_sort_keys": ([V, I64, V, V, V, V], I32),
         "sph_tree_info": ([V, _c.POINTER(I64), _c.POINTER(I64)], I32),
-        "sph_list_info": ([V, _c.POINTER(I64), _c.POINTER(I64), _c.POINTER(I64), _c.POINTER(I32)], I32),
+        "sph_list_info": ([V, _c.POINTER(I64), _c.POINTER(I64), _c.POINTER(I64), _c.POINTER(I32), _c.POINTER(I32)],
+                          I32),
         "sph_export_leaves": ([V, V, V, V], I32),
         "sph_neighbors": ([V, _c.POINTER(sph_particles), I32, V, V, V, V], I32),
         "sph_hnet_set_weights": ([V, V, I64], I32),
@@ -398,10 +399,11 @@ def sph_tree_info(ctx: Context):
 def sph_list_info(ctx: Context) -> dict:
     """Neighbour-list slots reserved and used by the last build, and whether
     the context sizes lists by exact counts."""
-    r, u, un, e = _c.c_int64(), _c.c_int64(), _c.c_int64(), _c.c_int32()
-    _check(ctx, load().sph_list_info(ctx.handle, _c.byref(r), _c.byref(u), _c.byref(un), _c.byref(e)))
+    r, u, un, e, um = _c.c_int64(), _c.c_int64(), _c.c_int64(), _c.c_int32(), _c.c_int32()
+    _check(ctx, load().sph_list_info(ctx.handle, _c.byref(r), _c.byref(u), _c.byref(un), _c.byref(e),
+                                     _c.byref(um)))
     return {"slots_reserved": int(r.value), "slots_used": int(u.value), "union_used": int(un.value),
-            "exact_sizing": bool(e.value)}
+            "exact_sizing": bool(e.value), "union_max": int(um.value)}
 
 
 def sph_export_leaves(ctx: Context, stream=None):

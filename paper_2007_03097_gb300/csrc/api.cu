@@ -502,9 +502,10 @@ int sph_tree_info(sph_ctx *ctx, int64_t *n_leaves, int64_t *n_groups)
 }
 
 int sph_list_info(sph_ctx *ctx, int64_t *slots_reserved, int64_t *slots_used, int64_t *union_used,
-                  int32_t *exact_sizing)
+                  int32_t *exact_sizing, int32_t *union_max)
 {
     if (!ctx) return SPH_ERR_ARG;
+    if (union_max) *union_max = ctx->hcnt->union_max;
     if (slots_reserved) *slots_reserved = (int64_t)ctx->hcnt->list_total;
     if (slots_used) *slots_used = (int64_t)ctx->hcnt->list_used;
     if (union_used) *union_used = (int64_t)ctx->hcnt->union_used;

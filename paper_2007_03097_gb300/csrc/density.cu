@@ -61,8 +61,11 @@ struct DensArgs {
     const float *cov;
     int kernel, periodic, fixed_h, max_sweeps;   // kernel: the kernel shape (kern_shape)
     int dim;                                     // D = 1 or 3
-    double L, etaD, h_tol, h_min, h_max;         // etaD = eta^D
-    df Ld, sig_d, etaD_d, hmin_d, hmax_d;        // the same constants as double-floats
+    double L, etaD, h_tol, h_min, h_max;         // etaD = eta^D; L in the packed positions' lengths
+    df Ld, sig_d, etaD_d, hmin_d, hmax_d;        // the same constants as double-floats (h bounds scaled)
+    // SPH_FP64 units (see sph_ctx::len_scale): h_scaled = h ls; the caller's
+    // rho = rho_scaled rho_un, drho/dh = scaled om_un; Lu = L in the caller's units
+    double ls, ls_inv, rho_un, om_un, Lu;
     DevCounters *cnt;
 };
 
@@ -305,7 +308,7 @@ __device__ __forceinline__ void df_pair(const DensArgs &a, const DfTarget &t, ui
     if (r2f >= t.thr_lo) ++band;
     if (r2f >= t.thr_lo || (t.img && fmaxf(fmaxf(fabsf(dxf), fabsf(dyf)), fabsf(dzf)) > guard)) {
         // knife edge: the exact FP64 decision of the plain definition
-        const double L = a.L, hl = 0.5 * a.L;
+        const double L = a.Lu, hl = 0.5 * a.Lu;
         const double dx = sep_d(a.x[t.i], a.x[b], a.periodic, L, hl);
         const double dy = sep_d(a.y[t.i], a.y[b], a.periodic, L, hl);
         const double dz = sep_d(a.z[t.i], a.z[b], a.periodic, L, hl);
@@ -375,7 +378,7 @@ __device__ __forceinline__ bool df_finalize(const DensArgs &a, const DfTarget &t
             const bool conv = adh < (float)a.h_tol * h.hi;
             df_st(a.it_lo + i, lo);
             df_st(a.it_hi + i, hi);
-            hp[i] = clamp < 0 ? a.h_min : clamp > 0 ? a.h_max : df_to_double(hn);
+            hp[i] = clamp < 0 ? a.h_min : clamp > 0 ? a.h_max : df_to_double(hn) * a.ls_inv;
             if (conv) {
                 // first-order finalization as in the mixed path (see there),
                 // for |dh| <= 1e-7 h: the neglected term, a relative
@@ -398,8 +401,8 @@ __device__ __forceinline__ bool df_finalize(const DensArgs &a, const DfTarget &t
             atomicAdd(&a.cnt->n_hbounds, 1);
         }
     }
-    ((double *)a.rho)[i] = df_to_double(rho_out);
-    ((double *)a.omega)[i] = df_to_double(drho);
+    ((double *)a.rho)[i] = df_to_double(rho_out) * a.rho_un;
+    ((double *)a.omega)[i] = df_to_double(drho) * a.om_un;
     a.nnb[i] = cnt;
     a.it_flags[i] = flags;
     return !done;
@@ -421,7 +424,7 @@ __device__ __forceinline__ void density_group_df(const DensArgs &a, const int g,
     int32_t flags = tgt ? a.it_flags[i] : IT_DONE;
     bool active = !(flags & IT_DONE);
     const double hd = active ? ((const double *)a.h)[i] : 1.0;
-    const df h = df_from_double(hd);
+    const df h = df_from_double(hd * a.ls);
     bool waiting = false;
     if (active && df_waiting(a, i, h)) {
         waiting = true;
@@ -479,7 +482,7 @@ __global__ void __launch_bounds__(DW * 32) k_density_sparse(DensArgs a)
         const int32_t flags = a.it_flags[i];
         if (flags & IT_DONE) continue;
         const double hd = ((const double *)a.h)[i];
-        const df h = df_from_double(hd);
+        const df h = df_from_double(hd * a.ls);
         bool still;
         if (df_waiting(a, i, h)) {
             if (lane == 0) atomicAdd(&a.cnt->n_uncovered, 1);
@@ -658,12 +661,18 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
     a.cov = ctx->cov;
     a.kernel = kern_shape(q.kernel, q.dim); a.dim = q.dim;
     a.periodic = q.periodic; a.fixed_h = q.fixed_h; a.max_sweeps = q.max_sweeps;
-    a.L = ctx->dom[3];
+    const double ls = ctx->len_scale;
+    a.ls = ls;
+    a.ls_inv = 1.0 / ls;                           // powers of two: exact
+    a.rho_un = std::ldexp(1.0, q.dim * std::ilogb(ls) - std::ilogb(ctx->mass_scale));   // rho scales as m / L^D
+    a.om_un = a.rho_un * ls;
+    a.Lu = ctx->dom[3];
+    a.L = ctx->dom[3] * ls;
     a.etaD = q.dim == 1 ? q.eta : q.eta * q.eta * q.eta;
     a.h_tol = q.h_tol; a.h_min = q.h_min; a.h_max = q.h_max;
     const double sig = kern_sigma<double>(a.kernel);
     a.Ld = df_host(a.L); a.sig_d = df_host(sig); a.etaD_d = df_host(a.etaD);
-    a.hmin_d = df_host(q.h_min); a.hmax_d = df_host(q.h_max);
+    a.hmin_d = df_host(q.h_min * ls); a.hmax_d = df_host(q.h_max * ls);
     a.cnt = ctx->dcnt;
     // sweeps are queued in batches without a host round trip: each reads the
     // number of active groups left by the previous one on the device.  A
@@ -731,6 +740,8 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
         SPH_CUDA(cudaEventElapsedTime(&f, ctx->lev[0], ctx->lev[1]));
         lists_ms += f;
     }
+    // the lists of this iteration were built before its last synchronisation
+    if (!(ctx->hcnt->err & (ERRB_LIST_CAPACITY | ERRB_STACK))) ctx->lists_union_max = ctx->hcnt->union_max;
     double kernel_ms = 0.0;
     for (int k = 0; k < launched && k < 64; ++k) {
         float f = 0.f;

@@ -37,9 +37,12 @@ struct ForceArgs {
     const void *vx, *vy, *vz, *m, *h, *rho, *c;
     void *ax, *ay, *az, *dudt, *divv, *vsig;
     int kernel, periodic;          // kernel: the kernel shape (kern_shape)
+    int uc;                        // mixed force pass: union sources staged per group
     int dim;                       // D = 1 or 3: grad W = sigma / h^(D+1) w'(q) r_ab / r
     int thermo;                    // 1: dudt receives de/dt of the thermokinetic formulation
-    double L, alpha, beta, eps;
+    double L, alpha, beta, eps;    // L in the packed positions' lengths
+    double Lu, ls;                 // SPH_FP64: L in the caller's units; the length scale (outputs x ls)
+    double rho_sc;                 // SPH_FP64: rho_scaled = rho rho_sc
     df Ld, sig_d, alpha_d, beta_d, eps_d;   // the same constants as double-floats
     DevCounters *cnt;
 };
@@ -47,17 +50,19 @@ struct ForceArgs {
 // ---------------------------------------------------------------- SPH_MIXED
 // One block of FB warps per target group.  The group's source union (the
 // sources any of its targets lists, in list-walk order) is staged once into
-// shared memory, UC sources at most, as three records per source:
+// shared memory (as many sources as the largest union of the lists when that
+// is known, at most UC_MAX, else UC), as three interleaved records per source:
 //   sP {x, y, z relative to the group centre (periodic image folded in), h}
 //   sV {vx, vy, vz, m}          copied with cp.async from the packed record C
-//   sT {rho, P/rho^2, c, h}     copied with cp.async from the packed record D
+//   sT {rho/2, P/rho^2, c, h}   copied with cp.async from the packed record D
 // Every warp holds the group's 32 targets (one per lane) and walks every FB-th
 // quad of its lanes' lists (quads q = w, w + FB, ...), reading its sources
 // from shared memory; the FB partial sums of each target are added in warp
 // order at the end.  Union entries past UC (a rare, very large union) are
 // read from global memory with the same arithmetic.
 constexpr int FB = 4;          // warps per block (one target group per block)
-constexpr int UC = 512;        // union sources staged per group (24 KB of shared memory)
+constexpr int UC = 512;        // union sources staged per group when the largest union is not known
+constexpr int UC_MAX = 1024;   // the most sources staged (48 KB of shared memory)
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
@@ -85,10 +90,17 @@ __device__ __forceinline__ float4 rel_pos(const float4 qa, const float4 qb, floa
     return make_float4(rx + qa.y, ry + qa.w, rz + qb.y, h);
 }
 
-template <int KS>
+// KS: the kernel form (its dimension D with it); THERMO: dudt receives de/dt
+// of Eq. thermo; FAR: some union may exceed the a.uc sources staged (entries
+// past them are read from global memory).  Dynamic shared memory: 3 a.uc
+// float4 (a.uc >= 224, a multiple of 32).
+template <int KS, bool THERMO, bool FAR>
 __global__ void __launch_bounds__(FB * 32, 8) k_forces_f32(ForceArgs a)
 {
-    __shared__ float4 sP[UC], sV[UC], sT[UC];
+    constexpr bool D1 = KS >= 3;
+    constexpr bool M4 = KS == 0 || KS == 3;
+    extern __shared__ float4 s_dyn[];               // source t: sP, sV, sT at 3 t, 3 t + 1, 3 t + 2
+    const int UCd = a.uc;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int g = blockIdx.x;
     if (g >= a.n_groups) return;
@@ -100,26 +112,26 @@ __global__ void __launch_bounds__(FB * 32, 8) k_forces_f32(ForceArgs a)
     const float Lf = (float)a.L, invL = 1.f / Lf;
     const bool img = a.periodic && a.group_img[g];   // else every source's direct image is the nearest
     const uint32_t *Ug = a.uni + a.uoff[g];
-    const int U = min(a.group_union[g], UC);
+    const int U = min(a.group_union[g], UCd);
 
     // ---- stage the union
     for (int t = threadIdx.x; t < U; t += FB * 32) {
         const uint32_t b = __ldg(Ug + t);
-        cp_async16(&sV[t], a.srcC + b);
-        cp_async16(&sT[t], a.srcD + b);
+        cp_async16(&s_dyn[3 * t + 1], a.srcC + b);
+        cp_async16(&s_dyn[3 * t + 2], a.srcD + b);
         const float4 qa = __ldg(a.srcA + b), qb = __ldg(a.srcB + b);
         const float hb = __ldg(reinterpret_cast<const float *>(a.srcD + b) + 3);
-        sP[t] = rel_pos(qa, qb, gcx, gcy, gcz, img, Lf, invL, hb);
+        s_dyn[3 * t] = rel_pos(qa, qb, gcx, gcy, gcz, img, Lf, invL, hb);
     }
 
     // ---- the target of this lane (every warp holds the same 32 targets)
     const float4 A = __ldg(a.srcA + i), Bz = __ldg(a.srcB + i), C = __ldg(a.srcC + i), D = __ldg(a.srcD + i);
     const float tx = (A.x - gcx) + A.y, ty = (A.z - gcy) + A.w, tz = (Bz.x - gcz) + Bz.y;
-    const float ha = D.w, rhoa = D.x, pra = D.y, ca = D.z;
+    const float ha = D.w, rhoa_h = D.x, pra = D.y, ca = D.z;   // rhoa_h = rho_a / 2
     const float hainv = 1.f / ha;
     const float thr_d = 4.f * ha * ha;
-    const float alpha = (float)a.alpha, beta = (float)a.beta, eps = (float)a.eps;
-    const float half_alpha = 0.5f * alpha;
+    const float beta = (float)a.beta, eps = (float)a.eps;
+    const float half_alpha = 0.5f * (float)a.alpha;
     const int64_t off = a.goff[g];
     int width = tgt ? a.gwidth[g] : 0;
     if (off + 32 * (int64_t)width > a.cap) width = 0;    // never read past the lists
@@ -129,7 +141,7 @@ __global__ void __launch_bounds__(FB * 32, 8) k_forces_f32(ForceArgs a)
     __syncthreads();
 
     // pair sums without the per-target factors sigma (a, du/dt) and
-    // sigma / h_a^(D+1) (div v), applied once at the end
+    // sigma / h_a^(D+2) (div v), applied once at the end
     float accx = 0.f, accy = 0.f, accz = 0.f, du = 0.f, dv = 0.f, vs = ca;
     int nint = 0;
     unsigned long long nxt = w < nq ? __ldg(lq + 32 * (int64_t)w) : ~0ull;
@@ -139,14 +151,14 @@ __global__ void __launch_bounds__(FB * 32, 8) k_forces_f32(ForceArgs a)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const uint32_t e = (uint32_t)(quad >> (16 * u)) & 0xFFFFu;
-            if (e == SPH_LOCAL_NONE) continue;
             float4 P, V, T;
             uint32_t b = 0;
-            const bool far = e >= (uint32_t)UC;
+            const bool far = e >= (uint32_t)(FAR ? U : UCd);   // SPH_LOCAL_NONE is beyond every union
             if (!far) {
-                P = sP[e];
-            } else {                                   // beyond the staged part of the union
-                b = __ldg(Ug + e);
+                P = s_dyn[3 * e];
+            } else {
+                if (!FAR || e == SPH_LOCAL_NONE) continue;
+                b = __ldg(Ug + e);                     // beyond the staged part of the union
                 T = __ldg(a.srcD + b);
                 P = rel_pos(__ldg(a.srcA + b), __ldg(a.srcB + b), gcx, gcy, gcz, img, Lf, invL, T.w);
             }
@@ -157,8 +169,8 @@ __global__ void __launch_bounds__(FB * 32, 8) k_forces_f32(ForceArgs a)
             const bool in_d = r2 < thr_d;
             if (!in_f && !in_d) continue;
             if (!far) {
-                V = sV[e];
-                T = sT[e];
+                V = s_dyn[3 * e + 1];
+                T = s_dyn[3 * e + 2];
             } else {
                 V = __ldg(a.srcC + b);
             }
@@ -167,41 +179,41 @@ __global__ void __launch_bounds__(FB * 32, 8) k_forces_f32(ForceArgs a)
             const float vabx = C.x - V.x, vaby = C.y - V.y, vabz = C.z - V.z;
             const float vdotr = fmaf(vabz, dz, fmaf(vaby, dy, vabx * dx));
             const float mb = V.w;
-            const float rv = vdotr * rinv;             // v_ab . r_ab / r
-            if (in_d) {
-                float w_, dwq;
-                kern_wdw<float>(KS, r * hainv, w_, dwq);   // the kernel form fixed at compile time
-                dv = fmaf(mb * dwq, rv, dv);
+            if (in_d) {                                // m_b v_ab . grad_a W(r, h_a) h_a^(D+2) / sigma
+                const float wq = kern_dwq<float>(KS, r * hainv, M4 ? ha * rinv : 0.f);
+                dv = fmaf(mb * wq, vdotr, dv);
             }
             if (in_f) {
                 // approximate reciprocals (within 2 ulp): the FP32 pass is held
                 // to relative tolerances far above them
                 const float hab = 0.5f * hs;
                 const float habinv = __fdividef(1.f, hab);
-                float w_, dwq;
-                kern_wdw<float>(KS, r * habinv, w_, dwq);
+                const float wq = kern_dwq<float>(KS, r * habinv, M4 ? hab * rinv : 0.f);
                 const float h2 = habinv * habinv;
-                const float mg = mb * (a.dim == 1 ? h2 : h2 * h2) * dwq;   // m_b w'(q) / h_ab^(D+1)
-                const float gr = mg * rinv;                                // m_b grad_a W / sigma = gr r_ab
+                const float gr = mb * (D1 ? h2 * habinv : h2 * h2 * habinv) * wq;   // m_b grad_a W / sigma = gr r_ab
+                const float csum = ca + T.z;
                 float Pi = 0.f;
                 if (vdotr < 0.f) {
-                    const float mu = __fdividef(hab * vdotr, fmaf(eps * hab, hab, r2));
-                    Pi = __fdividef(mu * fmaf(beta, mu, -half_alpha * (ca + T.z)), 0.5f * (rhoa + T.x));
+                    // Pi = mu (beta mu - alpha cbar) / rhobar with mu = hv / den:
+                    // hv (beta hv - alpha cbar den) / (den^2 rhobar), one reciprocal
+                    const float hv = hab * vdotr;
+                    const float den = fmaf(eps * hab, hab, r2);
+                    const float num = hv * fmaf(beta, hv, -half_alpha * csum * den);
+                    Pi = __fdividef(num, den * den * (rhoa_h + T.x));
                 }
                 const float coef = (pra + T.y + Pi) * gr;
                 accx = fmaf(-coef, dx, accx);
                 accy = fmaf(-coef, dy, accy);
                 accz = fmaf(-coef, dz, accz);
-                if (a.thermo) {
+                if (THERMO) {
                     // Eq. thermo: -m_b (P_a/rho_a^2 v_b + P_b/rho_b^2 v_a + (v_a + v_b) Pi/2) . grad_a W
                     const float vb_r = fmaf(V.z, dz, fmaf(V.y, dy, V.x * dx));
                     const float va_r = fmaf(C.z, dz, fmaf(C.y, dy, C.x * dx));
                     du -= ((pra * vb_r + T.y * va_r) + Pi * 0.5f * (va_r + vb_r)) * gr;
                 } else {
-                    du = fmaf((pra + 0.5f * Pi) * mg, rv, du);
+                    du = fmaf(fmaf(0.5f, Pi, pra) * gr, vdotr, du);
                 }
-                const float sgn = ca + T.z - 3.f * fminf(rv, 0.f);
-                vs = fmaxf(vs, sgn);
+                vs = fmaxf(vs, fmaf(-3.f, fminf(vdotr * rinv, 0.f), csum));
                 ++nint;
             }
         }
@@ -209,7 +221,7 @@ __global__ void __launch_bounds__(FB * 32, 8) k_forces_f32(ForceArgs a)
 
     // ---- the FB partial sums of each target, added in warp order
     __syncthreads();                                   // the union is no longer read
-    float *red = reinterpret_cast<float *>(sP);        // [FB][7][32]
+    float *red = reinterpret_cast<float *>(s_dyn);     // [FB][7][32]
     red[(w * 7 + 0) * 32 + lane] = accx;
     red[(w * 7 + 1) * 32 + lane] = accy;
     red[(w * 7 + 2) * 32 + lane] = accz;
@@ -229,22 +241,37 @@ __global__ void __launch_bounds__(FB * 32, 8) k_forces_f32(ForceArgs a)
         nint += __float_as_int(red[(v * 7 + 6) * 32 + lane]);
     }
     if (tgt) {
-        const float sig = kern_sigma<float>(a.kernel);
-        const float sig_hg = sig * inv_pow_dim(hainv, a.dim) * hainv;     // sigma / h_a^(D+1)
+        const float sig = kern_sigma<float>(KS);
+        const float h2 = hainv * hainv;
+        const float sig_hg = sig * (D1 ? h2 * hainv : h2 * h2 * hainv);    // sigma / h_a^(D+2)
         ((float *)a.ax)[i] = sig * accx;
         ((float *)a.ay)[i] = sig * accy;
         ((float *)a.az)[i] = sig * accz;
         ((float *)a.dudt)[i] = sig * du;
-        ((float *)a.divv)[i] = -sig_hg * dv / rhoa;
+        ((float *)a.divv)[i] = -sig_hg * dv / (2.f * rhoa_h);
         ((float *)a.vsig)[i] = vs;
     }
     for (int o = 16; o > 0; o >>= 1) nint += __shfl_xor_sync(0xffffffffu, nint, o);
     if (lane == 0) atomicAdd(&a.cnt->force_interactions, (unsigned long long)nint);
 }
 
+template <int KS>
+void launch_f32(const ForceArgs &a, bool thermo, bool far, unsigned grid, cudaStream_t s)
+{
+    const size_t smem = 3 * sizeof(float4) * (size_t)a.uc;      // <= 48 KB: no opt-in needed
+    if (thermo) {
+        if (far) k_forces_f32<KS, true, true><<<grid, FB * 32, smem, s>>>(a);
+        else k_forces_f32<KS, true, false><<<grid, FB * 32, smem, s>>>(a);
+    } else {
+        if (far) k_forces_f32<KS, false, true><<<grid, FB * 32, smem, s>>>(a);
+        else k_forces_f32<KS, false, false><<<grid, FB * 32, smem, s>>>(a);
+    }
+}
+
 // Equation of state and packed FP32 force-pass sources: P = (gamma-1) rho u,
 // c = sqrt(gamma (gamma-1) u) to the caller's P and c, and the records
-// C {vx, vy, vz, m}, D {rho, P/rho^2, c, h}.
+// C {vx, vy, vz, m}, D {rho/2, P/rho^2, c, h} (rho/2: the pair mean of the
+// viscosity is then one addition).
 __global__ void k_pack_force_f32(const float *__restrict__ vx, const float *__restrict__ vy,
                                  const float *__restrict__ vz, const float *__restrict__ m,
                                  const float *__restrict__ h, const float *__restrict__ rho,
@@ -258,7 +285,7 @@ __global__ void k_pack_force_f32(const float *__restrict__ vx, const float *__re
     P[i] = pi;
     c[i] = ci;
     C[i] = make_float4(vx[i], vy[i], vz[i], m[i]);
-    D[i] = make_float4(r, pi / (r * r), ci, h[i]);
+    D[i] = make_float4(0.5f * r, pi / (r * r), ci, h[i]);
 }
 
 // SPH_FP64 force pass in double-float (see the file comment).
@@ -322,7 +349,7 @@ __global__ void __launch_bounds__(FW * 32, 5) k_forces_df(ForceArgs a)
                           (img && fmaxf(fmaxf(fabsf(dxf), fabsf(dyf)), fabsf(dzf)) > guard);
         if (edge) {
             // knife edge: the exact FP64 decisions of the plain definition
-            const double L = a.L, hl = 0.5 * a.L;
+            const double L = a.Lu, hl = 0.5 * a.Lu;
             const double dx = sep_d(a.x[i], a.x[b], a.periodic, L, hl);
             const double dy = sep_d(a.y[i], a.y[b], a.periodic, L, hl);
             const double dz = sep_d(a.z[i], a.z[b], a.periodic, L, hl);
@@ -397,11 +424,15 @@ __global__ void __launch_bounds__(FW * 32, 5) k_forces_df(ForceArgs a)
         }
     }
     if (tgt) {
-        ((double *)a.ax)[i] = df_to_double(df_mul(sig, df_norm(accx)));
-        ((double *)a.ay)[i] = df_to_double(df_mul(sig, df_norm(accy)));
-        ((double *)a.az)[i] = df_to_double(df_mul(sig, df_norm(accz)));
-        ((double *)a.dudt)[i] = df_to_double(df_mul(sig, df_norm(du)));
-        ((double *)a.divv)[i] = -df_to_double(df_mul(sig_hai4, df_norm(dv))) / ((const double *)a.rho)[i];
+        // a, du/dt and div v scale as 1/length (velocities keep the caller's units)
+        ((double *)a.ax)[i] = df_to_double(df_mul(sig, df_norm(accx))) * a.ls;
+        ((double *)a.ay)[i] = df_to_double(df_mul(sig, df_norm(accy))) * a.ls;
+        ((double *)a.az)[i] = df_to_double(df_mul(sig, df_norm(accz))) * a.ls;
+        ((double *)a.dudt)[i] = df_to_double(df_mul(sig, df_norm(du))) * a.ls;
+        // (the sum carries m_b in scaled mass and 1/h^(D+1) in scaled length:
+        // ls / rho_sc brings sum / rho back to the caller's 1/time)
+        ((double *)a.divv)[i] = (-df_to_double(df_mul(sig_hai4, df_norm(dv))) / ((const double *)a.rho)[i]) *
+                                (a.ls / a.rho_sc);
         ((double *)a.vsig)[i] = df_to_double(vs);
     }
     for (int o = 16; o > 0; o >>= 1) nint += __shfl_xor_sync(0xffffffffu, nint, o);
@@ -421,19 +452,21 @@ __device__ __forceinline__ float2 split2(double v)
 __global__ void k_pack_force(const double *__restrict__ vx, const double *__restrict__ vy,
                              const double *__restrict__ vz, const double *__restrict__ h,
                              const double *__restrict__ rho, const double *__restrict__ u, double g1d, df gg1,
-                             int64_t n, double *__restrict__ P, double *__restrict__ c, float4 *__restrict__ C,
-                             float4 *__restrict__ D, float4 *__restrict__ E, float4 *__restrict__ F)
+                             int64_t n, double ls, double rho_sc, double *__restrict__ P, double *__restrict__ c,
+                             float4 *__restrict__ C, float4 *__restrict__ D, float4 *__restrict__ E,
+                             float4 *__restrict__ F)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double rd = rho[i], ud = u[i];
     const double pd = __dmul_rn(__dmul_rn(g1d, rd), ud);      // P exactly as the FP64 definition
-    const df r = df_from_double(rd), ui = df_from_double(ud), pi = df_from_double(pd);
+    // the pair terms take h, rho and P in the scaled units (exact powers of two)
+    const df r = df_from_double(rd * rho_sc), ui = df_from_double(ud), pi = df_from_double(pd * rho_sc);
     const df ci = df_sqrt(df_mul(gg1, ui));
     const df q = df_mul(pi, df_sqr(df_rcp(r)));
     P[i] = pd;
     c[i] = df_to_double(ci);
-    const float2 a = split2(vx[i]), b = split2(vy[i]), cz = split2(vz[i]), hh = split2(h[i]);
+    const float2 a = split2(vx[i]), b = split2(vy[i]), cz = split2(vz[i]), hh = split2(h[i] * ls);
     C[i] = make_float4(a.x, a.y, b.x, b.y);
     D[i] = make_float4(cz.x, cz.y, hh.x, hh.y);
     E[i] = make_float4(r.hi, r.lo, q.hi, q.lo);
@@ -441,6 +474,12 @@ __global__ void k_pack_force(const double *__restrict__ vx, const double *__rest
 }
 
 __global__ void k_reset_inter(DevCounters *c) { c->force_interactions = 0; }
+
+// rho_scaled / rho = mass_scale / len_scale^D (a power of two)
+double rho_scale(const sph_ctx *ctx)
+{
+    return std::ldexp(1.0, std::ilogb(ctx->mass_scale) - ctx->prm.dim * std::ilogb(ctx->len_scale));
+}
 
 template <typename T>
 int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, const void *vz, const void *u,
@@ -452,8 +491,8 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
     if (ctx->fp64)
         k_pack_force<<<grid_for(p->n, 256), 256, 0, s>>>(
             (const double *)vx, (const double *)vy, (const double *)vz, (const double *)p->h, (const double *)p->rho,
-            (const double *)u, g - 1.0, df_host(g * (g - 1.0)), p->n, (double *)p->P, (double *)p->c,
-            ctx->srcC, ctx->srcD, ctx->srcE, ctx->srcF);
+            (const double *)u, g - 1.0, df_host(g * (g - 1.0)), p->n, ctx->len_scale, rho_scale(ctx),
+            (double *)p->P, (double *)p->c, ctx->srcC, ctx->srcD, ctx->srcE, ctx->srcF);
     else
         k_pack_force_f32<<<grid_for(p->n, 256), 256, 0, s>>>(
             (const float *)vx, (const float *)vy, (const float *)vz, (const float *)p->m, (const float *)p->h,
@@ -483,7 +522,10 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
     a.group_lo = ctx->group_lo;
     a.group_hi = ctx->group_hi;
     a.thermo = ctx->prm.energy == SPH_ENERGY_TOTAL;
-    a.L = ctx->dom[3];
+    a.Lu = ctx->dom[3];
+    a.ls = ctx->len_scale;
+    a.rho_sc = rho_scale(ctx);
+    a.L = ctx->dom[3] * ctx->len_scale;
     a.alpha = ctx->prm.alpha; a.beta = ctx->prm.beta; a.eps = ctx->prm.eps_visc;
     const double sig = kern_sigma<double>(a.kernel);
     a.Ld = df_host(a.L); a.sig_d = df_host(sig);
@@ -492,15 +534,23 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
     SPH_CUDA(cudaEventRecord(ctx->ev[5], s));
     if (ctx->fp64) k_forces_df<<<grid_for(ctx->n_groups, FW), FW * 32, 0, s>>>(a);
     else {
-        // one instantiation per kernel form keeps the pair loop small; one
-        // block per target group
+        // one instantiation per kernel form (and energy equation) keeps the
+        // pair loop small; one block per target group.  Lists of this step's
+        // density iteration tell their largest union; otherwise the kernel
+        // reads entries beyond the staged part from global memory.
         const unsigned grid = grid_for(ctx->n_groups, 1);
+        const bool th = a.thermo != 0;
+        // stage the largest union when it is known and fits (the reduction
+        // buffer of 7 x 32 x FB floats needs at least 224 sources' worth)
+        const bool far = !(reuse_lists && ctx->lists_union_max <= UC_MAX);
+        a.uc = far ? UC : std::max(224, (ctx->lists_union_max + 31) & ~31);
         switch (a.kernel) {
-        case 1: k_forces_f32<1><<<grid, FB * 32, 0, s>>>(a); break;
-        case 2: k_forces_f32<2><<<grid, FB * 32, 0, s>>>(a); break;
-        case 4: k_forces_f32<4><<<grid, FB * 32, 0, s>>>(a); break;
-        case 5: k_forces_f32<5><<<grid, FB * 32, 0, s>>>(a); break;
-        default: k_forces_f32<0><<<grid, FB * 32, 0, s>>>(a); break;   // M4, either D
+        case 1: launch_f32<1>(a, th, far, grid, s); break;
+        case 2: launch_f32<2>(a, th, far, grid, s); break;
+        case 3: launch_f32<3>(a, th, far, grid, s); break;
+        case 4: launch_f32<4>(a, th, far, grid, s); break;
+        case 5: launch_f32<5>(a, th, far, grid, s); break;
+        default: launch_f32<0>(a, th, far, grid, s); break;
         }
     }
     SPH_CHECK_LAUNCH();

@@ -393,6 +393,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
             a.group_img[g] = any_img ? 1 : 0;
             atomicAdd(&a.cnt->list_used, 32ull * (unsigned long long)used);
             atomicAdd(&a.cnt->union_used, (unsigned long long)min(uc, ucap));
+            atomicMax(&a.cnt->union_max, min(uc, ucap));
         }
     }
 }
@@ -416,6 +417,7 @@ __global__ void k_list_total(const int64_t *__restrict__ off, const int32_t *__r
     cnt->list_total = (unsigned long long)total;
     cnt->list_used = 0;
     cnt->union_used = 0;
+    cnt->union_max = 0;
     if (total > cap || utotal > ucap) atomicOr(&cnt->err, ERRB_LIST_CAPACITY);
 }
 
@@ -504,10 +506,11 @@ int build_impl(sph_ctx *ctx, cudaStream_t s)
     a.child = ctx->node_child;
     a.node_lo = ctx->node_lo; a.node_hi = ctx->node_hi;
     a.periodic = ctx->prm.periodic;
-    for (int d = 0; d < 3; ++d) a.blo[d] = (float)ctx->dom[d];
-    a.L = (float)ctx->dom[3];
+    const double ls = ctx->len_scale;              // the lengths of the packed positions
+    for (int d = 0; d < 3; ++d) a.blo[d] = (float)(ctx->dom[d] * ls);
+    a.L = (float)(ctx->dom[3] * ls);
     a.invL = 1.f / a.L;
-    a.slack = (float)(1e-6 * ctx->dom[3]);
+    a.slack = (float)(1e-6 * ctx->dom[3] * ls);
     a.group_width = ctx->group_width;
     a.group_off = ctx->group_off;
     a.nbl = ctx->nbl;
@@ -542,7 +545,8 @@ int build_impl(sph_ctx *ctx, cudaStream_t s)
     return SPH_OK;
 }
 
-// coverage radius of each particle's list: 2 h (1 + skin), rounded down
+// coverage radius of each particle's list: 2 h (1 + skin), rounded down, in
+// the lengths of the packed positions (f includes their scale)
 template <typename T>
 __global__ void k_coverage(const T *__restrict__ h, int64_t n, double f, float *__restrict__ cov)
 {
@@ -554,7 +558,8 @@ __global__ void k_coverage(const T *__restrict__ h, int64_t n, double f, float *
 
 int lists_build(sph_ctx *ctx, const sph_particles *p, cudaStream_t s)
 {
-    const double f = 1.0 + ctx->prm.skin;
+    ctx->lists_union_max = INT32_MAX;          // unknown until the next synchronisation
+    const double f = (1.0 + ctx->prm.skin) * ctx->len_scale;
     if (ctx->fp64) k_coverage<double><<<grid_for(p->n, 256), 256, 0, s>>>((const double *)p->h, p->n, f, ctx->cov);
     else k_coverage<float><<<grid_for(p->n, 256), 256, 0, s>>>((const float *)p->h, p->n, f, ctx->cov);
     SPH_CHECK_LAUNCH();

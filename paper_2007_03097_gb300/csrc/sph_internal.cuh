@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <climits>
 #include <string>
 
 #include "sph.h"
@@ -133,7 +134,8 @@ struct DevCounters {
     long long ns_total;                // misplaced keys found by the near-sorted pass
     unsigned long long union_used;     // union slots holding the group unions of the last build
     int32_t sweep_stamp;               // counts density sweeps (group append marks)
-    int32_t pad4;
+    int32_t union_max;                 // largest group source union of the last build
+    double unit_ref[2];                // h and m of the first particle in key order (unit choice)
 };
 
 // near-sorted key pass: (key, id) pairs and per-tile extremes, prefix
@@ -164,6 +166,14 @@ struct sph_ctx {
     bool lists_exact = false;           // size lists by exact counts (set once leaf bounds overflowed)
     double dom[4] = {0, 0, 0, 1};
     double dt_cfl = 0.0;
+    // Units of the double-float arithmetic (SPH_FP64): lengths are multiplied
+    // by len_scale = 2^kL and masses by mass_scale = 2^kM, powers of two chosen
+    // at each tree build so that the first particle's h and m lie in [1, 2).
+    // The scaling is exact, so results are those of the caller's units; it
+    // keeps every intermediate of the pair sums (h^-(D+2), m_b P_b/rho_b^2 ...)
+    // inside the FP32 exponent range that double-float numbers share.  SPH_MIXED
+    // keeps 1 (its pair sums are FP32 by definition).
+    double len_scale = 1.0, mass_scale = 1.0;
 
     // ---- sort / keys
     uint64_t *key_a = nullptr, *key_b = nullptr;
@@ -252,6 +262,7 @@ struct sph_ctx {
     cudaEvent_t kev[2 * 64] = {};       // per-sweep density kernel events
     cudaEvent_t lev[4] = {};            // list builds of the density iteration (first, rebuild)
     int64_t launches = 0;               // kernels launched so far
+    int32_t lists_union_max = INT32_MAX; // largest union of the current lists, when a synchronisation has told
     int test_flags = 0;                 // sph_test_hooks
     int64_t force_launches = 0;         // kernels of the last force pass
 };
@@ -358,6 +369,29 @@ __device__ __forceinline__ void kern_wdw(int k, T q, T &w, T &dw)
         w = s4 * s * (T(1) + q * (T(2.5) + T(2) * q));
         dw = T(-3.5) * q * (T(1) + T(2) * q) * s4;
     }
+}
+
+// w'(q) / q of kernel shape k: the Wendland forms and the inner piece of M4
+// are polynomials in q; the outer piece of M4 takes 1/q from the caller
+// (qinv), which only that shape reads.  The gradient is then
+// grad_a W(r, h) = sigma / h^(D+2) (w'(q)/q) r_ab, with no 1/r.
+template <typename T>
+__device__ __forceinline__ T kern_dwq(int k, T q, T qinv)
+{
+    const T s = T(1) - T(0.5) * q;
+    if (k == 1) return T(-5) * (s * s * s);
+    if (k == 2) {
+        const T s2 = s * s;
+        return T(-14.0 / 3.0) * (T(1) + T(2.5) * q) * (s2 * s2 * s);
+    }
+    if (k == 0 || k == 3) {
+        if (q < T(1)) return T(-3) + T(2.25) * q;
+        const T t = T(2) - q;
+        return T(-0.75) * t * t * qinv;
+    }
+    if (k == 4) return T(-3) * (s * s);
+    const T s2 = s * s;
+    return T(-3.5) * (T(1) + T(2) * q) * (s2 * s2);
 }
 
 // 1 / h^D from 1 / h (D = 1 or 3)

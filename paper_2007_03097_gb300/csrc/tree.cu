@@ -353,14 +353,17 @@ __device__ __forceinline__ float2 split2(double v)
     return make_float2(hi, (float)(v - (double)hi));
 }
 
-// packed pair-kernel sources: {xh, xl, yh, yl} and {zh, zl, m_hi, m_lo}
+// packed pair-kernel sources: {xh, xl, yh, yl} and {zh, zl, m_hi, m_lo} of
+// the positions times ls and the masses times ms (powers of two: exact)
 template <typename T>
 __global__ void k_pack_pos(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
-                           const T *__restrict__ m, int64_t n, float4 *__restrict__ A, float4 *__restrict__ B)
+                           const T *__restrict__ m, int64_t n, double ls, double ms, float4 *__restrict__ A,
+                           float4 *__restrict__ B)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float2 sx = split2(x[i]), sy = split2(y[i]), sz = split2(z[i]), sm = split2((double)m[i]);
+    const float2 sx = split2(x[i] * ls), sy = split2(y[i] * ls), sz = split2(z[i] * ls),
+                 sm = split2((double)m[i] * ms);
     A[i] = make_float4(sx.x, sx.y, sy.x, sy.y);
     B[i] = make_float4(sz.x, sz.y, sm.x, sm.y);
 }
@@ -735,6 +738,14 @@ __global__ void k_mark_groups(int32_t *__restrict__ segbeg_to_flag, int64_t n)
     segbeg_to_flag[i] = (((int32_t)i - sb) % SPH_WARP) == 0 ? 1 : 0;
 }
 
+// h and m of the first particle in key order: the reference of the units
+template <typename T>
+__global__ void k_unit_ref(const T *__restrict__ h, const T *__restrict__ m, DevCounters *cnt)
+{
+    cnt->unit_ref[0] = (double)h[0];
+    cnt->unit_ref[1] = (double)m[0];
+}
+
 __global__ void k_emit(const int32_t *__restrict__ leaf_start, const int32_t *__restrict__ grp_start,
                        const int32_t *__restrict__ leaf_idx, const int32_t *__restrict__ grp_idx,
                        const uint8_t *__restrict__ plev, int64_t n, int32_t *__restrict__ leaf_begin,
@@ -1018,7 +1029,7 @@ template <typename T>
 int leaves_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
 {
     const int64_t n = p->n;
-    k_pack_pos<T><<<grid_for(n, 256), 256, 0, s>>>(p->x, p->y, p->z, (const T *)p->m, n, ctx->srcA, ctx->srcB);
+    k_unit_ref<T><<<1, 1, 0, s>>>((const T *)p->h, (const T *)p->m, ctx->dcnt);
     SPH_CHECK_LAUNCH();
     k_dlev<<<grid_for(n, 256), 256, 0, s>>>(ctx->key_a, n, ctx->dlev);
     SPH_CHECK_LAUNCH();
@@ -1088,6 +1099,17 @@ int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s, OrderHook *after_
     ctx->n = n;
     ctx->n_leaves = ctx->hcnt->n_leaves;
     ctx->n_groups = ctx->hcnt->n_groups;
+    if (ctx->fp64) {
+        // 2^kL h and 2^kM m of the first particle in [1, 2)
+        const double h0 = ctx->hcnt->unit_ref[0], m0 = ctx->hcnt->unit_ref[1];
+        const int kL = (std::isfinite(h0) && h0 > 0.0) ? std::max(-200, std::min(200, -std::ilogb(h0))) : 0;
+        const int kM = (std::isfinite(m0) && m0 > 0.0) ? std::max(-200, std::min(200, -std::ilogb(m0))) : 0;
+        ctx->len_scale = std::ldexp(1.0, kL);
+        ctx->mass_scale = std::ldexp(1.0, kM);
+    }
+    k_pack_pos<T><<<grid_for(n, 256), 256, 0, s>>>(p->x, p->y, p->z, (const T *)p->m, n, ctx->len_scale,
+                                                   ctx->mass_scale, ctx->srcA, ctx->srcB);
+    SPH_CHECK_LAUNCH();
     const int nl = (int)ctx->n_leaves;
     if (nl > 1) {
         k_radix_tree<<<grid_for(nl - 1, 256), 256, 0, s>>>(ctx->key_a, ctx->leaf_begin, nl, ctx->node_child,
