@@ -158,7 +158,7 @@ int allocate(sph_ctx *c, int64_t N)
     const int64_t scan_n = N > c->hist_cap ? N : c->hist_cap;
     c->scan_tmp_bytes = scan_tmp_bytes(scan_n);
     SPH_TRY(alloc(c, (unsigned char **)&c->scan_tmp, c->scan_tmp_bytes));
-    c->red_blocks = 2 * c->num_sms;
+    c->red_blocks = 8 * c->num_sms;
     SPH_TRY(alloc(c, &c->red, (size_t)c->red_blocks * 16));
     SPH_TRY(alloc(c, &c->dcnt, 1));
     SPH_CUDA(cudaMallocHost((void **)&c->hcnt, sizeof(DevCounters)));

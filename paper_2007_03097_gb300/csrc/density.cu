@@ -31,6 +31,7 @@ namespace {
 
 constexpr int DW = 4;          // warps per block
 constexpr int SRC_CAP = 448;   // staged union sources per warp (mixed sweep; 7 KB)
+constexpr int SPARSE_LANES = 10;   // mixed sweep: at most this many targets evaluated -> split lists
 
 struct DensArgs {
     const int32_t *act;            // active groups of this sweep ...
@@ -113,10 +114,15 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
         const float L = (float)a.L, invL = 1.f / L;
         const float hf = (float)h;
         const float thr = __fmul_rn(__fmul_rn(4.f, hf), hf);
+        const float band_lo = thr * (1.f - BAND), band_hi = thr * (1.f + BAND);
         const int U = a.group_union[g];
         const bool img = a.periodic && a.group_img[g];   // else every source's direct image is the nearest
         const uint32_t *Ug = a.uni + a.uoff[g];
         const unsigned long long *lq = reinterpret_cast<const unsigned long long *>(a.nbl + off) + lane;
+        // a group with few targets left to evaluate splits each one's list
+        // over the warp (a lane-per-target walk would leave most lanes idle)
+        const unsigned amask = __ballot_sync(0xffffffffu, active);
+        const bool sparse = __popc(amask) <= SPARSE_LANES;
         for (int c0 = 0; c0 < U; c0 += a.src_cap) {
             const int cn = min(a.src_cap, U - c0);
             __syncwarp();
@@ -132,7 +138,56 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                 s_src[t] = make_float4(rx + qa.y, ry + qa.w, rz + qb.y, qb.z);
             }
             __syncwarp();
-            if (active) {
+            if (sparse) {
+                // few targets still iterate: all 32 lanes split each one's
+                // list (lane l takes its quads l, l + 32, ...) and the partial
+                // sums meet by shuffles in the target's lane
+                const unsigned long long *lq0 = reinterpret_cast<const unsigned long long *>(a.nbl + off);
+                const int nq = width >> 2;
+                for (unsigned m = amask; m; m &= m - 1) {
+                    const int t = __ffs(m) - 1;
+                    const float ttx = __shfl_sync(0xffffffffu, tx, t), tty = __shfl_sync(0xffffffffu, ty, t),
+                                ttz = __shfl_sync(0xffffffffu, tz, t);
+                    const float tthr = __shfl_sync(0xffffffffu, thr, t);
+                    const float tlo = __shfl_sync(0xffffffffu, band_lo, t), thi = __shfl_sync(0xffffffffu, band_hi, t);
+                    const T thinv = __shfl_sync(0xffffffffu, hinv, t);
+                    T sw = T(0), sd = T(0);
+                    int c = 0, bnd = 0;
+                    for (int qi = lane; qi < nq; qi += 32) {
+                        const unsigned long long qd = __ldg(lq0 + 32 * (int64_t)qi + t);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const uint32_t e = (uint32_t)(qd >> (16 * u)) & 0xFFFFu;
+                            const int le = (int)e - c0;
+                            if ((unsigned)le >= (unsigned)cn) continue;
+                            const float4 q = s_src[le];
+                            const float dx = ttx - q.x, dy = tty - q.y, dz = ttz - q.z;
+                            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                            bnd += (r2 >= tlo && r2 <= thi) ? 1 : 0;
+                            if (!(r2 < tthr)) continue;
+                            const T qq = (T)(r2 > 0.f ? r2 * rsqrtf(r2) : 0.f) * thinv;
+                            T w, gg;
+                            kern_wg<T>(KS, qq, w, gg);
+                            const T mb = (T)q.w;
+                            sw = fmaf(mb, w, sw);
+                            sd = fmaf(mb, gg, sd);
+                            ++c;
+                        }
+                    }
+                    for (int o = 16; o > 0; o >>= 1) {
+                        sw += __shfl_xor_sync(0xffffffffu, sw, o);
+                        sd += __shfl_xor_sync(0xffffffffu, sd, o);
+                        c += __shfl_xor_sync(0xffffffffu, c, o);
+                        bnd += __shfl_xor_sync(0xffffffffu, bnd, o);
+                    }
+                    if (lane == t) {
+                        sum_w += sw;
+                        sum_dh += sd;
+                        cnt += c;
+                        band += bnd;
+                    }
+                }
+            } else if (active) {
                 // list entries in batches of LB = 8 (two quads), the next
                 // batch in flight while this one is processed (empty slots
                 // fall outside [0, cn))
@@ -152,15 +207,15 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                     if ((unsigned)le >= (unsigned)cn) continue;
                     const float4 q = s_src[le];
                     const float dx = tx - q.x, dy = ty - q.y, dz = tz - q.z;
-                    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-                    if (fabsf(r2 - thr) <= BAND * thr) ++band;
+                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    band += (r2 >= band_lo && r2 <= band_hi) ? 1 : 0;
                     if (!(r2 < thr)) continue;
                     const T qq = (T)(r2 > 0.f ? r2 * rsqrtf(r2) : 0.f) * hinv;   // r within 2 ulp
-                    T w, dw;
-                    kern_wdw<T>(KS, qq, w, dw);        // the kernel form fixed at compile time
+                    T w, g;
+                    kern_wg<T>(KS, qq, w, g);          // the kernel form fixed at compile time
                     const T mb = (T)q.w;
-                    sum_w += mb * w;
-                    sum_dh += mb * (Dt * w + qq * dw);
+                    sum_w = fmaf(mb, w, sum_w);
+                    sum_dh = fmaf(mb, g, sum_dh);     // m (D w + q w')
                     ++cnt;
                     }
                 }
@@ -705,9 +760,10 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
                 switch (a.kernel) {
                 case 1: k_density<float, false, 1><<<grid, DW * 32, smem, s>>>(a); break;
                 case 2: k_density<float, false, 2><<<grid, DW * 32, smem, s>>>(a); break;
+                case 3: k_density<float, false, 3><<<grid, DW * 32, smem, s>>>(a); break;   // M4, D = 1
                 case 4: k_density<float, false, 4><<<grid, DW * 32, smem, s>>>(a); break;
                 case 5: k_density<float, false, 5><<<grid, DW * 32, smem, s>>>(a); break;
-                default: k_density<float, false, 0><<<grid, DW * 32, smem, s>>>(a); break;   // M4, either D
+                default: k_density<float, false, 0><<<grid, DW * 32, smem, s>>>(a); break;   // M4, D = 3
                 }
             }
             SPH_CHECK_LAUNCH();

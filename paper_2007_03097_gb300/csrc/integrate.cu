@@ -3,7 +3,9 @@
 // totals: sum m v, sum m a, sum m (v^2/2 + u), sum m (v . a + du/dt) and the
 // CFL minimum of h / vsig.
 #include <cfloat>
+#include <type_traits>
 
+#include "dfloat.cuh"
 #include "sph_internal.cuh"
 
 namespace {
@@ -129,6 +131,66 @@ __global__ void __launch_bounds__(TB) k_totals_partial(
     }
 }
 
+// SPH_MIXED partial totals: every field is FP32, so each product is exact as
+// a two-float (two_prod) and the per-thread sums run in double-float on the
+// FP32 pipes (~2^-44 relative per addition, FP64 would take 1/64 of the FP32
+// rate); the thread sums meet in FP64 in shared memory as in
+// k_totals_partial, and the quotient h / v_sig is FP64 where it can lower the
+// running minimum.
+__global__ void __launch_bounds__(TB) k_totals_partial_f32(
+    const float *__restrict__ m, const float *__restrict__ vx, const float *__restrict__ vy,
+    const float *__restrict__ vz, const float *__restrict__ u, const float *__restrict__ ax,
+    const float *__restrict__ ay, const float *__restrict__ az, const float *__restrict__ du,
+    const float *__restrict__ pvx, const float *__restrict__ pvy, const float *__restrict__ pvz,
+    const float *__restrict__ h, const float *__restrict__ vsig, int64_t n, double *__restrict__ part, int thermo)
+{
+    df acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = df{0.f, 0.f};
+    double mn = DBL_MAX, mnx = __longlong_as_double(0x7ff0000000000000ll);   // +inf
+    for (int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x; i < n; i += (int64_t)gridDim.x * TB) {
+        const float mi = m[i], vxi = vx[i], vyi = vy[i], vzi = vz[i];
+        const float axi = ax[i], ayi = ay[i], azi = az[i];
+        acc[0] = df_add(acc[0], two_prod(mi, vxi));
+        acc[1] = df_add(acc[1], two_prod(mi, vyi));
+        acc[2] = df_add(acc[2], two_prod(mi, vzi));
+        acc[3] = df_add(acc[3], two_prod(mi, axi));
+        acc[4] = df_add(acc[4], two_prod(mi, ayi));
+        acc[5] = df_add(acc[5], two_prod(mi, azi));
+        // m (v^2/2 + u) from the exact squares
+        const df v2 = df_add(df_add(two_prod(vxi, vxi), two_prod(vyi, vyi)), two_prod(vzi, vzi));
+        acc[6] = df_add(acc[6], df_mul_f(df_add_f(df_scale(v2, 0.5f), u[i]), mi));
+        const float wx = pvx ? pvx[i] : vxi, wy = pvx ? pvy[i] : vyi, wz = pvx ? pvz[i] : vzi;
+        if (thermo) {
+            acc[7] = df_add(acc[7], two_prod(mi, du[i]));
+        } else {
+            const df wa = df_add(df_add(two_prod(wx, axi), two_prod(wy, ayi)), two_prod(wz, azi));
+            acc[7] = df_add(acc[7], df_mul_f(df_add_f(wa, du[i]), mi));
+        }
+        if (vsig) {
+            const double v = vsig[i], hi = h[i];
+            if (v > 0 && hi <= mnx * v) {
+                mn = fmin(mn, hi / v);
+                mnx = mn * (1.0 + 0x1p-40);
+            }
+        }
+    }
+    __shared__ double s[NT][TB];
+    for (int k = 0; k < 8; ++k) s[k][threadIdx.x] = (double)acc[k].hi + (double)acc[k].lo;
+    s[8][threadIdx.x] = mn;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int k = threadIdx.x >> 5; k < NT; k += TB / 32) {
+        double v = s[k][lane];
+        for (int j = lane + 32; j < TB; j += 32) v = k < 8 ? v + s[k][j] : fmin(v, s[k][j]);
+        for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = k < 8 ? v + w : fmin(v, w);
+        }
+        if (lane == 0) part[blockIdx.x * NT + k] = v;
+    }
+}
+
 // Block partials combined in a fixed order: warp k sums quantity k over the
 // partials with a strided loop and a shuffle tree (deterministic).
 __global__ void k_totals_final(const double *__restrict__ part, int nb, DevCounters *cnt)
@@ -185,11 +247,19 @@ int totals_impl(sph_ctx *ctx, const sph_particles *p, const void *pvx, const voi
                 const void *u, cudaStream_t s)
 {
     const int nb = ctx->red_blocks;
-    k_totals_partial<T><<<nb, TB, 0, s>>>((const T *)p->m, (const T *)p->vx, (const T *)p->vy, (const T *)p->vz,
-                                           (const T *)u, (const T *)p->ax, (const T *)p->ay, (const T *)p->az,
-                                           (const T *)p->dudt, (const T *)pvx, (const T *)pvy, (const T *)pvz,
-                                           (const T *)p->h, (const T *)p->vsig, p->n, ctx->red,
-                                           ctx->prm.energy == SPH_ENERGY_TOTAL);
+    if constexpr (std::is_same<T, float>::value)
+        k_totals_partial_f32<<<nb, TB, 0, s>>>(p->m ? (const float *)p->m : nullptr, (const float *)p->vx,
+                                                (const float *)p->vy, (const float *)p->vz, (const float *)u,
+                                                (const float *)p->ax, (const float *)p->ay, (const float *)p->az,
+                                                (const float *)p->dudt, (const float *)pvx, (const float *)pvy,
+                                                (const float *)pvz, (const float *)p->h, (const float *)p->vsig,
+                                                p->n, ctx->red, ctx->prm.energy == SPH_ENERGY_TOTAL);
+    else
+        k_totals_partial<T><<<nb, TB, 0, s>>>((const T *)p->m, (const T *)p->vx, (const T *)p->vy, (const T *)p->vz,
+                                               (const T *)u, (const T *)p->ax, (const T *)p->ay, (const T *)p->az,
+                                               (const T *)p->dudt, (const T *)pvx, (const T *)pvy, (const T *)pvz,
+                                               (const T *)p->h, (const T *)p->vsig, p->n, ctx->red,
+                                               ctx->prm.energy == SPH_ENERGY_TOTAL);
     SPH_CHECK_LAUNCH();
     k_totals_final<<<1, 32 * NT, 0, s>>>(ctx->red, nb, ctx->dcnt);
     SPH_CHECK_LAUNCH();

@@ -371,6 +371,51 @@ __device__ __forceinline__ void kern_wdw(int k, T q, T &w, T &dw)
     }
 }
 
+// w(q) and g(q) = D w(q) + q w'(q) of kernel shape k (D its dimension), the
+// two terms of the density sum and of its h derivative, each as a power of
+// s = 1 - q/2 times a short polynomial (the same functions as kern_wdw,
+// expanded):
+//   WC2 3D  w = s^3 s (1 + 2q)                 g = s^3 (3 + 9/2 q - 8 q^2)
+//   WC4 3D  w = s^5 (1 + 5/2 q + 17/12 q^2 - 35/24 q^3)
+//           g = s^5 (3 + 15/2 q - 5/12 q^2 - 385/24 q^3)
+//   WC2 1D  w = s^2 (1 + q - 3/4 q^2)          g = s^2 (1 + q - 15/4 q^2)
+//   WC4 1D  w = s^4 (1 + 2q + 3/4 q^2 - q^3)   g = s^4 (1 + 2q - 11/4 q^2 - 8 q^3)
+//   M4      q < 1: g = D - 3 (D + 2)/2 q^2 + 3 (D + 3)/4 q^3;
+//           q >= 1 (t = 2 - q): 3D g = 3/2 t^2 (1 - q), 1D g = t^2 (1 - 2q)/2
+template <typename T>
+__device__ __forceinline__ void kern_wg(int k, T q, T &w, T &g)
+{
+    const T s = T(1) - T(0.5) * q;
+    if (k == 1) {
+        const T s3 = s * s * s;
+        w = s3 * (s * (T(1) + T(2) * q));
+        g = s3 * (T(3) + q * (T(4.5) - T(8) * q));
+    } else if (k == 2) {
+        const T s2 = s * s;
+        const T s5 = s2 * s2 * s;
+        w = s5 * (T(1) + q * (T(2.5) + q * (T(17.0 / 12.0) - T(35.0 / 24.0) * q)));
+        g = s5 * (T(3) + q * (T(7.5) - q * (T(5.0 / 12.0) + T(385.0 / 24.0) * q)));
+    } else if (k == 0 || k == 3) {
+        if (q < T(1)) {
+            w = T(1) + q * q * (T(-1.5) + T(0.75) * q);
+            g = k == 0 ? T(3) + q * q * (T(-7.5) + T(4.5) * q) : T(1) + q * q * (T(-4.5) + T(3) * q);
+        } else {
+            const T t = T(2) - q;
+            w = T(0.25) * t * t * t;
+            g = k == 0 ? T(1.5) * t * t * (T(1) - q) : T(0.5) * t * t * (T(1) - T(2) * q);
+        }
+    } else if (k == 4) {
+        const T s2 = s * s;
+        w = s2 * (T(1) + q * (T(1) - T(0.75) * q));
+        g = s2 * (T(1) + q * (T(1) - T(3.75) * q));
+    } else {
+        const T s2 = s * s;
+        const T s4 = s2 * s2;
+        w = s4 * (T(1) + q * (T(2) + q * (T(0.75) - q)));
+        g = s4 * (T(1) + q * (T(2) - q * (T(2.75) + T(8) * q)));
+    }
+}
+
 // w'(q) / q of kernel shape k: the Wendland forms and the inner piece of M4
 // are polynomials in q; the outer piece of M4 takes 1/q from the caller
 // (qinv), which only that shape reads.  The gradient is then

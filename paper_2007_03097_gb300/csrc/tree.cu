@@ -362,8 +362,10 @@ __global__ void k_pack_pos(const double *__restrict__ x, const double *__restric
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float2 sx = split2(x[i] * ls), sy = split2(y[i] * ls), sz = split2(z[i] * ls),
-                 sm = split2((double)m[i] * ms);
+    // (ls = ms = 1 outside FP64 mode: no FP64 multiplies there)
+    const bool unit = ls == 1.0 && ms == 1.0;
+    const float2 sx = split2(unit ? x[i] : x[i] * ls), sy = split2(unit ? y[i] : y[i] * ls),
+                 sz = split2(unit ? z[i] : z[i] * ls), sm = split2(unit ? (double)m[i] : (double)m[i] * ms);
     A[i] = make_float4(sx.x, sx.y, sy.x, sy.y);
     B[i] = make_float4(sz.x, sz.y, sm.x, sm.y);
 }

@@ -84,6 +84,9 @@ def _base_params(**kw) -> dict:
              fixed_h=False, h_tol=1e-6, max_sweeps=30, h_min=1e-6, h_max=0.25, rho_ref=1.0,
              precision="fp64")
     p.update(kw)
+    # neighbour lists cover 2h (1 + skin); a particle whose h outgrows its
+    # list within a step's iteration makes the iteration rebuild the lists
+    p.setdefault("skin", 0.05)
     return p
 
 
@@ -240,7 +243,9 @@ def turbulence(n_side: int = 256, seed: int = 5001, mach: float = 2.0, gamma: fl
     u0 = 1.0 / (gamma * (gamma - 1.0))
     eta = (300.0 / (32.0 * math.pi)) ** (1.0 / 3.0)
     m = 1.0 / n
-    params = _base_params(kernel=WC4, gamma=gamma, eta=eta, precision=precision)
+    # a thin list skin: h moves by well under 2 % within a step's iteration
+    # here (measured: one list build per step), and every list slot costs
+    params = _base_params(kernel=WC4, gamma=gamma, eta=eta, precision=precision, skin=0.02)
     return Workload("turbulence", x, y, z, vx * scale, vy * scale, vz * scale, np.full(n, m),
                     np.full(n, eta / n_side), np.full(n, u0), params)
 
