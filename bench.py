@@ -90,6 +90,9 @@ def parse():
     ap.add_argument("--train-steps", type=int, default=PROTOCOL_TRAIN_STEPS,
                     help="plain steps of each training workload (16^3 lattice, 64^3 Sedov)")
     ap.add_argument("--no-extras", action="store_true", help="skip the collision and Sedov extra keys")
+    ap.add_argument("--profile-window", action="store_true",
+                    help="start the CUDA profiler only around the timed learned-h steps "
+                         "(for ncu --profile-from-start off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -248,7 +251,7 @@ class Run:
         for f, t in self.snap.items():
             getattr(self.p, f).copy_(t)
 
-    def timed(self, mode, steps, world=1):
+    def timed(self, mode, steps, world=1, window=False):
         B, torch, p, w = self.B, self.torch, self.p, self.w
         self.restore()
         B.sph_step(self.ctx, p, w.dt, use_hnet=mode)        # re-establish tree/lists in this mode
@@ -258,12 +261,16 @@ class Run:
             torch.distributed.barrier()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         stats = []
+        if window:
+            torch.cuda.profiler.start()
         for k in range(steps):
             self.flush.zero_()
             ev[k][0].record(self.stream)
             stats.append(B.sph_step(self.ctx, p, w.dt, use_hnet=mode))
             ev[k][1].record(self.stream)
         torch.cuda.synchronize()
+        if window:
+            torch.cuda.profiler.stop()
         if world > 1:
             torch.distributed.barrier()
         return [a.elapsed_time(b) for a, b in ev], stats
@@ -376,7 +383,10 @@ def run_sph(args):
     # the h-predictor: trained on the plain solver's trajectories (untimed), frozen
     from paper_2007_03097_gb300 import hnet_protocol
     t0 = time.perf_counter()
-    theta, losses = hnet_protocol.train(steps=args.train_steps)
+    if args.train_steps > 0:
+        theta, losses = hnet_protocol.train(steps=args.train_steps)
+    else:                                  # profiling runs: the untrained network
+        theta, losses = hnet_protocol.initial_theta(), {}
     train_s = time.perf_counter() - t0
     fp32_peak = B.sph_peak_fp32()
 
@@ -388,7 +398,7 @@ def run_sph(args):
     clocks = ClockSampler(gpu_uuid)
     # learned h (frozen network), plain h, and learned h with one online Adam
     # round per step (on the context's side stream, beside the force pass)
-    ms_l, st_l = r.timed(B.SPH_HNET_SEED, args.steps, world)
+    ms_l, st_l = r.timed(B.SPH_HNET_SEED, args.steps, world, window=args.profile_window)
     ms_p, st_p = r.timed(0, args.steps, world)
     ms_o, st_o = r.timed(B.SPH_HNET_SEED | B.SPH_HNET_TRAIN, args.steps, world)
     e2e_s, e_inter, h2d = r.e2e(args.steps)

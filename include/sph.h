@@ -236,7 +236,10 @@ int sph_forces(sph_ctx *ctx, sph_particles *p, sph_force_stats *stats, void *str
  * round beside the force pass, joined by the next call on the context; until
  * then it reads the particles' h, so a caller that rewrites h between calls
  * trains on the rewritten values (nothing is written outside the context).
- * The particle set must already carry a, du/dt from an earlier force pass. */
+ * The particle set must already carry a, du/dt from an earlier force pass.
+ * The step's tree build leaves omega, P, c and vsig in the previous order
+ * (its density iteration and force pass rewrite them for every particle), so
+ * after an error return these four arrays hold no particle's values. */
 #define SPH_HNET_SEED 1
 #define SPH_HNET_TRAIN 2
 int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet,

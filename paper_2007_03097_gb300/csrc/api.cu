@@ -358,9 +358,7 @@ int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet, sph_step_s
     // The h seed reads only particle fields, so it runs on the side stream as
     // soon as the particles are in key order, beside the leaf build (a chain
     // of small kernels that leaves most of the GPU idle); the density
-    // iteration waits for it.  A build that sorts in full after a failed
-    // near-sorted pass orders the particles twice: the seed is computed again
-    // after the second ordering (the side stream runs the two in order).
+    // iteration waits for it.
     struct SeedHook : OrderHook {
         sph_ctx *ctx;
         const sph_particles *p;
@@ -382,7 +380,9 @@ int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet, sph_step_s
     hook.p = p;
     hook.dt = dt;
     hook.train = train_net;
-    const int built = tree_build(ctx, p, s, seed_net ? &hook : nullptr);
+    // omega, P, c and vsig are rewritten for every particle by this step's
+    // density iteration and force pass before anything reads them
+    const int built = tree_build(ctx, p, s, seed_net ? &hook : nullptr, false);
     // the main stream joins the seed before anything else (also on an error,
     // so that no side-stream work outlives the call)
     if (seed_net) SPH_CUDA(cudaStreamWaitEvent(s, ctx->ev_seed, 0));

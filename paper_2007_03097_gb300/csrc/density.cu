@@ -31,7 +31,6 @@ namespace {
 
 constexpr int DW = 4;          // warps per block
 constexpr int SRC_CAP = 448;   // staged union sources per warp (mixed sweep; 7 KB)
-constexpr int SPARSE_LANES = 10;   // mixed sweep: at most this many targets evaluated -> split lists
 
 struct DensArgs {
     const int32_t *act;            // active groups of this sweep ...
@@ -70,13 +69,31 @@ struct DensArgs {
     DevCounters *cnt;
 };
 
+// r from r^2 by the hardware's approximate square root (one instruction,
+// exact at 0); the FP32 sweep is held to relative tolerances far above its
+// error
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// A warp's pair and evaluation counts over the groups it claims (lane 0),
+// added to the sweep's counters once when the warp runs out of groups.
+struct SweepTally {
+    unsigned long long inter = 0;
+    unsigned evals = 0;
+};
+
 // SPH_MIXED sweep of one group: FP32 pair terms, FP32 Newton update.  The
 // group's source union is staged in shared memory (s_src, a.src_cap entries
 // per chunk) as FP32 coordinates relative to the group-box centre, with the
 // periodic shift folded in, and the mass; each lane then reads its
 // neighbours there by their local index.
 template <typename T, int KS>
-__device__ __forceinline__ void density_group(const DensArgs &a, const int g, const int lane, float4 *s_src)
+__device__ __forceinline__ void density_group(const DensArgs &a, const int g, const int lane, float4 *s_src,
+                                              SweepTally &tally)
 {
     const int gb = a.group_begin[g], ge = a.group_begin[g + 1];
     const bool tgt = lane < ge - gb;
@@ -114,15 +131,17 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
         const float L = (float)a.L, invL = 1.f / L;
         const float hf = (float)h;
         const float thr = __fmul_rn(__fmul_rn(4.f, hf), hf);
-        const float band_lo = thr * (1.f - BAND), band_hi = thr * (1.f + BAND);
+        const float band_w = thr * BAND;                 // |r^2 - 4 h^2| <= band_w: within the band
         const int U = a.group_union[g];
         const bool img = a.periodic && a.group_img[g];   // else every source's direct image is the nearest
         const uint32_t *Ug = a.uni + a.uoff[g];
         const unsigned long long *lq = reinterpret_cast<const unsigned long long *>(a.nbl + off) + lane;
-        // a group with few targets left to evaluate splits each one's list
-        // over the warp (a lane-per-target walk would leave most lanes idle)
+        // a group with at most 16 targets left to evaluate gives each one a
+        // segment of k = 32 / nextpow2(count) lanes that splits its list (a
+        // lane-per-target walk would leave most lanes idle)
         const unsigned amask = __ballot_sync(0xffffffffu, active);
-        const bool sparse = __popc(amask) <= SPARSE_LANES;
+        const int nact = __popc(amask);
+        const int lk = nact > 16 ? 0 : 5 - (nact > 1 ? 32 - __clz(nact - 1) : 0);   // log2 k
         for (int c0 = 0; c0 < U; c0 += a.src_cap) {
             const int cn = min(a.src_cap, U - c0);
             __syncwarp();
@@ -138,54 +157,68 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                 s_src[t] = make_float4(rx + qa.y, ry + qa.w, rz + qb.y, qb.z);
             }
             __syncwarp();
-            if (sparse) {
-                // few targets still iterate: all 32 lanes split each one's
-                // list (lane l takes its quads l, l + 32, ...) and the partial
-                // sums meet by shuffles in the target's lane
-                const unsigned long long *lq0 = reinterpret_cast<const unsigned long long *>(a.nbl + off);
-                const int nq = width >> 2;
-                for (unsigned m = amask; m; m &= m - 1) {
-                    const int t = __ffs(m) - 1;
-                    const float ttx = __shfl_sync(0xffffffffu, tx, t), tty = __shfl_sync(0xffffffffu, ty, t),
-                                ttz = __shfl_sync(0xffffffffu, tz, t);
-                    const float tthr = __shfl_sync(0xffffffffu, thr, t);
-                    const float tlo = __shfl_sync(0xffffffffu, band_lo, t), thi = __shfl_sync(0xffffffffu, band_hi, t);
-                    const T thinv = __shfl_sync(0xffffffffu, hinv, t);
-                    T sw = T(0), sd = T(0);
-                    int c = 0, bnd = 0;
-                    for (int qi = lane; qi < nq; qi += 32) {
-                        const unsigned long long qd = __ldg(lq0 + 32 * (int64_t)qi + t);
+            if (lk > 0) {
+                // segment s (lanes [s k, s k + k)) takes the s-th active
+                // target; lane r of the segment walks its quads r, r + k, ...
+                // and the segment's partial sums meet by shuffles, then move
+                // to the target's own lane
+                const int k = 1 << lk, seg = lane >> lk, r = lane & (k - 1);
+                const bool has = seg < nact;
+                const int t = has ? (int)__fns(amask, 0u, seg + 1) : 0;
+                const float ttx = __shfl_sync(0xffffffffu, tx, t), tty = __shfl_sync(0xffffffffu, ty, t),
+                            ttz = __shfl_sync(0xffffffffu, tz, t);
+                const float tthr = __shfl_sync(0xffffffffu, thr, t);
+                const float tbw = __shfl_sync(0xffffffffu, band_w, t);
+                const T thinv = __shfl_sync(0xffffffffu, hinv, t);
+                const unsigned long long *lq0 = reinterpret_cast<const unsigned long long *>(a.nbl + off) + t;
+                const int nq = has ? width >> 2 : 0;
+                T sw = T(0), sd = T(0);
+                int c = 0, bnd = 0;
+                // quads r, r + k in one batch, the next two in flight
+                auto quad = [&](int qi) -> unsigned long long {
+                    return qi < nq ? __ldg(lq0 + 32 * (int64_t)qi) : ~0ull;
+                };
+                unsigned long long n0 = quad(r), n1 = quad(r + k);
+                for (int qi = r; qi < nq; qi += 2 * k) {
+                    const unsigned long long q0 = n0, q1 = n1;
+                    n0 = quad(qi + 2 * k);
+                    n1 = quad(qi + 3 * k);
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const uint32_t e = (uint32_t)(qd >> (16 * u)) & 0xFFFFu;
-                            const int le = (int)e - c0;
-                            if ((unsigned)le >= (unsigned)cn) continue;
-                            const float4 q = s_src[le];
-                            const float dx = ttx - q.x, dy = tty - q.y, dz = ttz - q.z;
-                            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                            bnd += (r2 >= tlo && r2 <= thi) ? 1 : 0;
-                            if (!(r2 < tthr)) continue;
-                            const T qq = (T)(r2 > 0.f ? r2 * rsqrtf(r2) : 0.f) * thinv;
-                            T w, gg;
-                            kern_wg<T>(KS, qq, w, gg);
-                            const T mb = (T)q.w;
-                            sw = fmaf(mb, w, sw);
-                            sd = fmaf(mb, gg, sd);
-                            ++c;
-                        }
+                    for (int u = 0; u < 8; ++u) {
+                        const uint32_t e = (uint32_t)((u < 4 ? q0 : q1) >> (16 * (u & 3))) & 0xFFFFu;
+                        const int le = (int)e - c0;
+                        if ((unsigned)le >= (unsigned)cn) continue;
+                        const float4 q = s_src[le];
+                        const float dx = ttx - q.x, dy = tty - q.y, dz = ttz - q.z;
+                        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                        bnd += fabsf(r2 - tthr) <= tbw ? 1 : 0;
+                        if (!(r2 < tthr)) continue;
+                        const T qq = (T)sqrt_approx(r2) * thinv;
+                        T w, gg;
+                        kern_wg<T>(KS, qq, w, gg);
+                        const T mb = (T)q.w;
+                        sw = fmaf(mb, w, sw);
+                        sd = fmaf(mb, gg, sd);
+                        ++c;
                     }
-                    for (int o = 16; o > 0; o >>= 1) {
-                        sw += __shfl_xor_sync(0xffffffffu, sw, o);
-                        sd += __shfl_xor_sync(0xffffffffu, sd, o);
-                        c += __shfl_xor_sync(0xffffffffu, c, o);
-                        bnd += __shfl_xor_sync(0xffffffffu, bnd, o);
-                    }
-                    if (lane == t) {
-                        sum_w += sw;
-                        sum_dh += sd;
-                        cnt += c;
-                        band += bnd;
-                    }
+                }
+                for (int o = k >> 1; o > 0; o >>= 1) {
+                    sw += __shfl_xor_sync(0xffffffffu, sw, o);
+                    sd += __shfl_xor_sync(0xffffffffu, sd, o);
+                    c += __shfl_xor_sync(0xffffffffu, c, o);
+                    bnd += __shfl_xor_sync(0xffffffffu, bnd, o);
+                }
+                // an active lane's segment is its rank among the active lanes
+                const int from = active ? __popc(amask & ((1u << lane) - 1u)) << lk : 0;
+                sw = __shfl_sync(0xffffffffu, sw, from);
+                sd = __shfl_sync(0xffffffffu, sd, from);
+                c = __shfl_sync(0xffffffffu, c, from);
+                bnd = __shfl_sync(0xffffffffu, bnd, from);
+                if (active) {
+                    sum_w += sw;
+                    sum_dh += sd;
+                    cnt += c;
+                    band += bnd;
                 }
             } else if (active) {
                 // list entries in batches of LB = 8 (two quads), the next
@@ -208,9 +241,9 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                     const float4 q = s_src[le];
                     const float dx = tx - q.x, dy = ty - q.y, dz = tz - q.z;
                     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    band += (r2 >= band_lo && r2 <= band_hi) ? 1 : 0;
+                    band += fabsf(r2 - thr) <= band_w ? 1 : 0;
                     if (!(r2 < thr)) continue;
-                    const T qq = (T)(r2 > 0.f ? r2 * rsqrtf(r2) : 0.f) * hinv;   // r within 2 ulp
+                    const T qq = (T)sqrt_approx(r2) * hinv;
                     T w, g;
                     kern_wg<T>(KS, qq, w, g);          // the kernel form fixed at compile time
                     const T mb = (T)q.w;
@@ -308,8 +341,8 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
     const unsigned amask = __ballot_sync(0xffffffffu, active);
     const unsigned smask = __ballot_sync(0xffffffffu, still);
     if (lane == 0) {
-        atomicAdd(&a.cnt->interactions, (unsigned long long)c);
-        atomicAdd(&a.cnt->evaluations, (unsigned long long)__popc(amask));
+        tally.inter += (unsigned long long)c;
+        tally.evals += (unsigned)__popc(amask);
         if (smask) a.act_next[atomicAdd(a.act_next_count, 1)] = g;
     }
 }
@@ -471,7 +504,7 @@ __device__ __forceinline__ bool df_waiting(const DensArgs &a, int64_t i, df h)
 }
 
 // Dense FP64 sweep of one group: one lane per target, each walking its list.
-__device__ __forceinline__ void density_group_df(const DensArgs &a, const int g, const int lane)
+__device__ __forceinline__ void density_group_df(const DensArgs &a, const int g, const int lane, SweepTally &tally)
 {
     const int gb = a.group_begin[g], ge = a.group_begin[g + 1];
     const bool tgt = lane < ge - gb;
@@ -505,8 +538,8 @@ __device__ __forceinline__ void density_group_df(const DensArgs &a, const int g,
     const unsigned amask = __ballot_sync(0xffffffffu, active);
     const unsigned smask = __ballot_sync(0xffffffffu, still);
     if (lane == 0) {
-        atomicAdd(&a.cnt->interactions, (unsigned long long)c);
-        atomicAdd(&a.cnt->evaluations, (unsigned long long)__popc(amask));
+        tally.inter += (unsigned long long)c;
+        tally.evals += (unsigned)__popc(amask);
         if (smask) a.act_next[atomicAdd(a.act_next_count, 1)] = g;
     }
 }
@@ -590,13 +623,18 @@ __global__ void __launch_bounds__(DW * 32) k_density(DensArgs a)
     const int n_act = *a.act_count;
     if (blockIdx.x == 0 && threadIdx.x == 0 && n_act > 0) atomicAdd(&a.cnt->sweeps_done, 1);
     if (FP64POS && n_act < SPARSE_MAX_GROUPS) return;   // k_density_sparse takes this sweep
+    SweepTally tally;
     for (;;) {
         int gi = 0;
         if (lane == 0) gi = atomicAdd(a.work, 1);
         gi = __shfl_sync(0xffffffffu, gi, 0);
         if (gi >= n_act) break;
-        if constexpr (FP64POS) density_group_df(a, a.act[gi], lane);
-        else density_group<T, KS>(a, a.act[gi], lane, s_src);
+        if constexpr (FP64POS) density_group_df(a, a.act[gi], lane, tally);
+        else density_group<T, KS>(a, a.act[gi], lane, s_src, tally);
+    }
+    if (lane == 0 && tally.evals) {
+        atomicAdd(&a.cnt->interactions, tally.inter);
+        atomicAdd(&a.cnt->evaluations, (unsigned long long)tally.evals);
     }
 }
 

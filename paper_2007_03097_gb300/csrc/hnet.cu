@@ -230,16 +230,17 @@ __global__ void __launch_bounds__(TM) k_infer_tc(const __nv_bfloat16 *__restrict
                 out += w3[16 * cc + e] * (z * sigm(z));
             }
         }
-        if (valid) {
-            const float sp = x[3] * out;          // s = f3 * y
-            if (FIELDS) {
-                const bool ok = isfinite(sp) && fabsf(sp) <= 0.69314718f;
+        const float sp = x[3] * out;              // s = f3 * y
+        if (FIELDS) {
+            const bool ok = isfinite(sp) && fabsf(sp) <= 0.69314718f;
+            if (valid) {
                 const T hs = fa.h[s];
                 so.seed[s] = ok ? hs * (T)__expf(sp) : hs;   // a first guess: FP32 exp suffices
-                if (!ok) atomicAdd(&cnt->hnet_fallback, 1);
-            } else {
-                y[s] = sp;
             }
+            const unsigned fb = __ballot_sync(0xffffffffu, valid && !ok);   // one count per warp
+            if (fb && (tid & 31) == 0) atomicAdd(&cnt->hnet_fallback, __popc(fb));
+        } else if (valid) {
+            y[s] = sp;
         }
         tc::fence_before_sync();
         __syncthreads();                          // TMEM read and A tiles free before the next MMA

@@ -137,7 +137,13 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
 
     // this lane's quads, and the entries of the quad being filled
     unsigned long long *qp = FILL ? reinterpret_cast<unsigned long long *>(a.nbl + off) + lane : nullptr;
-    unsigned long long pend = 0ull;
+    // entries enter the quad from the top: after four, entry u sits at bits
+    // 16 u .. 16 u + 15 (pend_lo holds entries 0-1, pend_hi entries 2-3)
+    uint32_t pend_lo = 0u, pend_hi = 0u;
+    auto push = [&](uint32_t e) {
+        pend_lo = __funnelshift_r(pend_lo, pend_hi, 16);
+        pend_hi = __funnelshift_r(pend_hi, e, 16);
+    };
 
     // A batch of at most 32 staged candidates: every lane tests all of them
     // (bit k of `bits` = candidate k within this lane's reach), its own
@@ -155,14 +161,20 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
         __syncwarp();
         const int j = pi[lane];
         if (j >= gb && j < ge) s_self[w][j - gb] = lane;
-        unsigned bits = 0;
+        // candidate k is within reach when d = r^2 - max(cov_a^2, cov_k^2) < 0
+        // (d = 0 sits on the margin-widened radius, outside every exact
+        // support); the sign bit of d shifts in from the right, so after the
+        // batch bit 31 - k holds candidate k and one bit reversal orders them
+        unsigned rbits = 0;
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
             const float4 q = pa[k];                    // .w = cov^2 (1 + MARGIN)
             const float dx = tx - q.x, dy = ty - q.y, dz = tz - q.z;
             const float r2 = (dx * dx + dy * dy) + dz * dz;
-            if (r2 <= fmaxf(ca2, q.w)) bits |= 1u << k;
+            const float d = r2 - fmaxf(ca2, q.w);
+            rbits = __funnelshift_l(__float_as_uint(d), rbits, 1);
         }
+        unsigned bits = __brev(rbits);
         __syncwarp();
         const int me = s_self[w][lane];
         if (me >= 0) bits &= ~(1u << me);
@@ -172,16 +184,15 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
             if (((any >> lane) & 1u) && pos < ucap) a.uni[uoff + pos] = (uint32_t)j;
             s_loc[w][lane] = pos < (int)SPH_LOCAL_NONE ? pos : 0;
             __syncwarp();
-            for (unsigned m = bits; m; m &= m - 1) {
-                if (count < width) {
-                    pend |= (unsigned long long)s_loc[w][__ffs(m) - 1] << (16 * (count & 3));
-                    if ((count & 3) == 3) {
-                        qp[32 * (int64_t)(count >> 2)] = pend;
-                        pend = 0ull;
-                    }
-                }
+            const int take = min(__popc(bits), max(width - count, 0));   // entries within the sized slots
+            for (int t = 0; t < take; ++t) {
+                push((uint32_t)s_loc[w][__ffs(bits) - 1]);
+                bits &= bits - 1;
+                if ((count & 3) == 3)
+                    qp[32 * (int64_t)(count >> 2)] = ((unsigned long long)pend_hi << 32) | pend_lo;
                 ++count;
             }
+            count += __popc(bits);                     // beyond the sized slots: counted, not written
         } else {
             count += __popc(bits);
         }
@@ -322,9 +333,14 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
         // need = the targets within reach of this lane's leaf
         unsigned need = 0;
         const unsigned lmask = __ballot_sync(0xffffffffu, acc && leaf);
+        int lcnt = 0;                        // particles of this lane's accepted leaf (sizing pass)
         if (lmask) {                         // the accepted leaves' boxes, read by every lane
             s_bc[w][lane] = bc;
             s_be[w][lane] = make_float4(be.x + a.slack, be.y + a.slack, be.z + a.slack, 0.f);
+            if (MODE == LM_BOUND && acc && leaf) {
+                const int id = node & 0x7fffffff;
+                lcnt = a.leaf_begin[id + 1] - a.leaf_begin[id];
+            }
             __syncwarp();
         }
         for (unsigned m = lmask; m; m &= m - 1) {
@@ -333,18 +349,19 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
             const float gx = axis_gap(c.x, e.x, PA.x, wrap, a.L, a.invL);
             const float gy = axis_gap(c.y, e.y, PA.z, wrap, a.L, a.invL);
             const float gz = axis_gap(c.z, e.z, PB.x, wrap, a.L, a.invL);
-            const unsigned nm =
-                __ballot_sync(0xffffffffu, tgt && (gx * gx + gy * gy) + gz * gz <= fmaxf(ca2, c.w));
+            const bool reach = tgt && (gx * gx + gy * gy) + gz * gz <= fmaxf(ca2, c.w);
+            const unsigned nm = __ballot_sync(0xffffffffu, reach);
             if (lane == l) need = nm;
+            if (MODE == LM_BOUND) {
+                // every particle of a leaf within a target's reach may be
+                // listed for it, and may join the union
+                const int cl = __shfl_sync(0xffffffffu, lcnt, l);
+                if (reach) count += cl;
+                if (nm) ub += cl;
+            }
         }
         const bool keep = need != 0;
         if (MODE == LM_BOUND) {
-            // every particle of a leaf within a target's reach may be listed for it
-            int cnt = 0;
-            if (keep) {
-                const int id = node & 0x7fffffff;
-                cnt = a.leaf_begin[id + 1] - a.leaf_begin[id];
-            }
             // remember the kept leaves: the fill pass replays them without a walk
             const unsigned km = __ballot_sync(0xffffffffu, keep);
             if (keep && a.kcap > 0) {
@@ -352,13 +369,6 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
                 if (pos < a.kcap) a.kept[(int64_t)g * a.kcap + pos] = node & 0x7fffffff;
             }
             nkept += __popc(km);
-            for (unsigned m = __ballot_sync(0xffffffffu, keep); m; m &= m - 1) {
-                const int l = __ffs(m) - 1;
-                const unsigned nm = __shfl_sync(0xffffffffu, need, l);
-                const int c = __shfl_sync(0xffffffffu, cnt, l);
-                if ((nm >> lane) & 1u) count += c;
-                ub += c;                         // every kept particle may join the union
-            }
             continue;
         }
         stage(keep, node & 0x7fffffff);
@@ -382,8 +392,8 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
         const int used = (min(wmax, width) + 3) & ~3;  // width is a multiple of 4
         int k = min(count, width);
         if (k & 3) {                                   // the partial quad, padded with empty slots
-            for (int j = k & 3; j < 4; ++j) pend |= 0xFFFFull << (16 * j);
-            qp[32 * (int64_t)(k >> 2)] = pend;
+            for (int j = k & 3; j < 4; ++j) push(0xFFFFu);
+            qp[32 * (int64_t)(k >> 2)] = ((unsigned long long)pend_hi << 32) | pend_lo;
             k = (k + 3) & ~3;
         }
         for (; k < used; k += 4) qp[32 * (int64_t)(k >> 2)] = ~0ull;

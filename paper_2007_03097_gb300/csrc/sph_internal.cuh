@@ -98,6 +98,7 @@ enum : uint32_t {
     ERRB_STACK = 8u,             // traversal stack overflow
     ERRB_TIE_RUN = 16u,          // equal-key run too long to order by id
     ERRB_OFF_AXIS = 32u,         // D = 1 with a particle off the x axis
+    ERRB_PREFIX_RUN = 64u,       // a run of equal top key halves too long to order in place
 };
 
 // per-particle density iteration flags
@@ -505,13 +506,16 @@ __device__ __forceinline__ float wrap_diff(float a, float c, float L, float invL
 
 // ------------------------------------------------------------ launchers
 // tree.cu
-// after_order (may be null) is called with the build's stream once the
-// particle arrays are in their final key order (again if a full sort
-// follows a failed near-sorted pass), before the leaves are built
+// after_order (may be null) is called with the build's stream when the
+// particle arrays are in their final key order, before the leaves are built
+// (a second time in the rare build that sorts again on all key bits).
+// derived = false leaves omega, P, c and vsig unpermuted: for a caller that
+// rewrites all four for every particle before reading them (sph_step).
 struct OrderHook {
     virtual int operator()(cudaStream_t s) = 0;
 };
-int tree_build(sph_ctx *ctx, sph_particles *p, cudaStream_t s, OrderHook *after_order = nullptr);
+int tree_build(sph_ctx *ctx, sph_particles *p, cudaStream_t s, OrderHook *after_order = nullptr,
+               bool derived = true);
 int tree_keys(sph_ctx *ctx, const sph_particles *p, uint64_t *keys_out, cudaStream_t s);
 int tree_sort(sph_ctx *ctx, int64_t n, const uint64_t *keys, const uint32_t *ids, uint32_t *perm,
               cudaStream_t s);

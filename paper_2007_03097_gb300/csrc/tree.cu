@@ -325,6 +325,38 @@ __global__ void k_fix_ties(const uint64_t *__restrict__ keys, uint32_t *__restri
     }
 }
 
+// After a sort on the top 32 key bits only (the tree build), runs of equal
+// top halves are put in (key, id) order, which completes the order of the
+// full sort.  Such runs hold particles closer than 2^-10 of the key domain
+// and are tiny in practice; one longer than 64 is left alone and flagged,
+// and the build then sorts on all bits.  Threads inside a run read only
+// keys with the run's top half, so the reordering cannot move a run start.
+constexpr int PREFIX_RUN_MAX = 64;
+__global__ void k_fix_prefix_runs(uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                  const uint32_t *__restrict__ ids, int64_t n, DevCounters *cnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t top = (uint32_t)(keys[i] >> 32);
+    if (i > 0 && (uint32_t)(keys[i - 1] >> 32) == top) return;
+    if (i + 1 >= n || (uint32_t)(keys[i + 1] >> 32) != top) return;
+    int64_t e = i + 1;
+    while (e < n && (uint32_t)(keys[e] >> 32) == top && e - i <= PREFIX_RUN_MAX) ++e;
+    if (e - i > PREFIX_RUN_MAX) { atomicOr(&cnt->err, ERRB_PREFIX_RUN); return; }
+    for (int64_t a = i + 1; a < e; ++a) {          // insertion sort on (key, id)
+        const uint64_t k = keys[a];
+        const uint32_t v = vals[a], idv = ids[v];
+        int64_t b = a - 1;
+        while (b >= i && (keys[b] > k || (keys[b] == k && ids[vals[b]] > idv))) {
+            keys[b + 1] = keys[b];
+            vals[b + 1] = vals[b];
+            --b;
+        }
+        keys[b + 1] = k;
+        vals[b + 1] = v;
+    }
+}
+
 // ------------------------------------------------------------------ gather
 constexpr int MAX_FIELDS = 24;
 struct FieldTable {
@@ -354,18 +386,17 @@ __device__ __forceinline__ float2 split2(double v)
 }
 
 // packed pair-kernel sources: {xh, xl, yh, yl} and {zh, zl, m_hi, m_lo} of
-// the positions times ls and the masses times ms (powers of two: exact)
-template <typename T>
+// the positions times ls and the masses times ms (powers of two: exact;
+// SCALED false: ls = ms = 1, as in mixed mode, without the FP64 multiplies)
+template <typename T, bool SCALED>
 __global__ void k_pack_pos(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
                            const T *__restrict__ m, int64_t n, double ls, double ms, float4 *__restrict__ A,
                            float4 *__restrict__ B)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    // (ls = ms = 1 outside FP64 mode: no FP64 multiplies there)
-    const bool unit = ls == 1.0 && ms == 1.0;
-    const float2 sx = split2(unit ? x[i] : x[i] * ls), sy = split2(unit ? y[i] : y[i] * ls),
-                 sz = split2(unit ? z[i] : z[i] * ls), sm = split2(unit ? (double)m[i] : (double)m[i] * ms);
+    const float2 sx = split2(SCALED ? x[i] * ls : x[i]), sy = split2(SCALED ? y[i] * ls : y[i]),
+                 sz = split2(SCALED ? z[i] * ls : z[i]), sm = split2(SCALED ? (double)m[i] * ms : (double)m[i]);
     A[i] = make_float4(sx.x, sx.y, sy.x, sy.y);
     B[i] = make_float4(sz.x, sz.y, sm.x, sm.y);
 }
@@ -915,7 +946,7 @@ void add_field(FieldTable &t, unsigned char *&buf, int64_t nmax, const void *ptr
 }
 
 template <typename T>
-FieldTable make_table(sph_ctx *ctx, const sph_particles *p)
+FieldTable make_table(sph_ctx *ctx, const sph_particles *p, bool derived)
 {
     FieldTable t{};
     unsigned char *buf = ctx->gbuf;
@@ -923,22 +954,28 @@ FieldTable make_table(sph_ctx *ctx, const sph_particles *p)
     add_field<double>(t, buf, nm, p->x);
     add_field<double>(t, buf, nm, p->y);
     add_field<double>(t, buf, nm, p->z);
-    const void *tf[] = {p->vx, p->vy, p->vz, p->m, p->h, p->u, p->hprev, p->rho, p->omega, p->P, p->c,
-                        p->ax, p->ay, p->az, p->dudt, p->divv, p->vsig};
+    const void *tf[] = {p->vx, p->vy, p->vz, p->m, p->h, p->u, p->hprev, p->rho,
+                        p->ax, p->ay, p->az, p->dudt, p->divv};
     for (const void *f : tf) add_field<T>(t, buf, nm, f);
+    if (derived) {                                 // outputs that a step recomputes before reading
+        const void *td[] = {p->omega, p->P, p->c, p->vsig};
+        for (const void *f : td) add_field<T>(t, buf, nm, f);
+    }
     add_field<int32_t>(t, buf, nm, p->nnb);
     add_field<uint32_t>(t, buf, nm, p->id);
     return t;
 }
 
-int radix_sort(sph_ctx *ctx, int64_t n, cudaStream_t s)
+// LSD passes over the key bytes first_byte..7 (an even number of passes, so
+// the result is back in key_a / val_a)
+int radix_sort(sph_ctx *ctx, int64_t n, cudaStream_t s, int first_byte = 0)
 {
     // the tile staging needs more than 48 KB (set on the current device)
     SPH_CUDA(cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_SCATTER_SMEM));
     const int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
     uint64_t *ka = ctx->key_a, *kb = ctx->key_b;
     uint32_t *va = ctx->val_a, *vb = ctx->val_b;
-    for (int pass = 0; pass < 8; ++pass) {
+    for (int pass = first_byte; pass < 8; ++pass) {
         const int shift = 8 * pass;
         k_rs_hist<<<ntiles, RS_THREADS, 0, s>>>(ka, n, shift, ctx->hist, ntiles);
         SPH_CHECK_LAUNCH();
@@ -949,7 +986,7 @@ int radix_sort(sph_ctx *ctx, int64_t n, cudaStream_t s)
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
     }
-    return SPH_OK;   // 8 passes: the result is back in key_a / val_a
+    return SPH_OK;
 }
 
 int compute_domain(sph_ctx *ctx, const sph_particles *p, cudaStream_t s)
@@ -1011,12 +1048,19 @@ void near_sorted(sph_ctx *ctx, sph_particles *p, const FieldTable &t, int limit,
     k_ns_put<<<grid_for(limit, 256), 256, 0, s>>>(t, mpos, ctx->dcnt, limit);
 }
 
-// full sort, then permute every particle array into key order
-int full_sort(sph_ctx *ctx, sph_particles *p, const FieldTable &t, cudaStream_t s)
+// full sort, then permute every particle array into key order.  prefix: the
+// radix passes cover the top 32 key bits and runs of equal top halves are
+// ordered on the device (ERRB_PREFIX_RUN when one is too long for that)
+int full_sort(sph_ctx *ctx, sph_particles *p, const FieldTable &t, cudaStream_t s, bool prefix)
 {
     const int64_t n = p->n;
-    SPH_TRY(radix_sort(ctx, n, s));
-    k_fix_ties<<<grid_for(n, 256), 256, 0, s>>>(ctx->key_a, ctx->val_a, p->id, n, ctx->dcnt);
+    if (prefix) {
+        SPH_TRY(radix_sort(ctx, n, s, 4));
+        k_fix_prefix_runs<<<grid_for(n, 256), 256, 0, s>>>(ctx->key_a, ctx->val_a, p->id, n, ctx->dcnt);
+    } else {
+        SPH_TRY(radix_sort(ctx, n, s));
+        k_fix_ties<<<grid_for(n, 256), 256, 0, s>>>(ctx->key_a, ctx->val_a, p->id, n, ctx->dcnt);
+    }
     SPH_CHECK_LAUNCH();
     k_gather<<<grid_for(n, 256), 256, 0, s>>>(t, ctx->val_a, n);
     SPH_CHECK_LAUNCH();
@@ -1053,40 +1097,43 @@ int leaves_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
 }
 
 template <typename T>
-int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s, OrderHook *after_order)
+int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s, OrderHook *after_order, bool derived)
 {
     const int64_t n = p->n;
     ctx->tree_valid = false;
     SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->err, 0, sizeof(uint32_t), s));
     SPH_TRY(keys_impl<T>(ctx, p, ctx->key_a, ctx->val_a, s));
-    FieldTable t = make_table<T>(ctx, p);
+    FieldTable t = make_table<T>(ctx, p, derived);
     // after two full sorts in a row (most keys displaced every step) the
     // detection of a nearly sorted order is skipped for seven builds, then
-    // tried again
-    int limit = -1;                                // >= 0: the near-sorted path was launched
+    // tried again.  The host reads the detection's count before anything
+    // else runs, so a failed attempt costs the detection only: the full sort
+    // follows at once and the leaves and after_order run once, on the final
+    // order.
+    int64_t m = -1;                                // >= 0: the near-sorted path moved m particles
     if (ctx->ns_skip > 0) {
         --ctx->ns_skip;
     } else {
-        limit = (int)std::min<int64_t>(NS_LIMIT, std::max<int64_t>(n / 4, 1024));
+        const int limit = (int)std::min<int64_t>(NS_LIMIT, std::max<int64_t>(n / 4, 1024));
         near_sorted(ctx, p, t, limit, s);
         SPH_CHECK_LAUNCH();
-    }
-    if (limit < 0) SPH_TRY(full_sort(ctx, p, t, s));
-    if (after_order) SPH_TRY((*after_order)(s));
-    SPH_TRY(leaves_impl<T>(ctx, p, s));
-    int64_t m = -1;
-    if (limit >= 0) {
-        m = ctx->hcnt->ns_total <= limit ? ctx->hcnt->ns_total : -1;
-        if (m < 0 && !(ctx->hcnt->err & (ERRB_NONFINITE | ERRB_OFF_AXIS))) {
-            // too many misplaced particles: nothing was moved and the leaves
-            // above describe the unsorted keys; sort in full and build again
-            SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->err, 0, sizeof(uint32_t), s));
-            SPH_TRY(full_sort(ctx, p, t, s));
-            if (after_order) SPH_TRY((*after_order)(s));
-            SPH_TRY(leaves_impl<T>(ctx, p, s));
-        }
+        SPH_TRY(sync_counters(ctx, s));
+        if (ctx->hcnt->ns_total <= limit) m = ctx->hcnt->ns_total;
         ctx->ns_full_streak = m < 0 ? ctx->ns_full_streak + 1 : 0;
         if (ctx->ns_full_streak >= 2) ctx->ns_skip = 7;
+    }
+    if (m < 0) SPH_TRY(full_sort(ctx, p, t, s, true));
+    if (after_order) SPH_TRY((*after_order)(s));
+    SPH_TRY(leaves_impl<T>(ctx, p, s));
+    if (ctx->hcnt->err & ERRB_PREFIX_RUN) {
+        // more than 64 particles share the top 32 key bits: the order inside
+        // such a run is not final; sort the (now permuted) particles on all
+        // bits and build the leaves again
+        SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->err, 0, sizeof(uint32_t), s));
+        SPH_TRY(keys_impl<T>(ctx, p, ctx->key_a, ctx->val_a, s));
+        SPH_TRY(full_sort(ctx, p, t, s, false));
+        if (after_order) SPH_TRY((*after_order)(s));
+        SPH_TRY(leaves_impl<T>(ctx, p, s));
     }
     ctx->ns_moved = m;
     const uint32_t err = ctx->hcnt->err;
@@ -1109,8 +1156,12 @@ int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s, OrderHook *after_
         ctx->len_scale = std::ldexp(1.0, kL);
         ctx->mass_scale = std::ldexp(1.0, kM);
     }
-    k_pack_pos<T><<<grid_for(n, 256), 256, 0, s>>>(p->x, p->y, p->z, (const T *)p->m, n, ctx->len_scale,
-                                                   ctx->mass_scale, ctx->srcA, ctx->srcB);
+    if (ctx->len_scale != 1.0 || ctx->mass_scale != 1.0)
+        k_pack_pos<T, true><<<grid_for(n, 256), 256, 0, s>>>(p->x, p->y, p->z, (const T *)p->m, n, ctx->len_scale,
+                                                             ctx->mass_scale, ctx->srcA, ctx->srcB);
+    else
+        k_pack_pos<T, false><<<grid_for(n, 256), 256, 0, s>>>(p->x, p->y, p->z, (const T *)p->m, n, 1.0, 1.0,
+                                                              ctx->srcA, ctx->srcB);
     SPH_CHECK_LAUNCH();
     const int nl = (int)ctx->n_leaves;
     if (nl > 1) {
@@ -1125,9 +1176,10 @@ int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s, OrderHook *after_
 
 }  // namespace
 
-int tree_build(sph_ctx *ctx, sph_particles *p, cudaStream_t s, OrderHook *after_order)
+int tree_build(sph_ctx *ctx, sph_particles *p, cudaStream_t s, OrderHook *after_order, bool derived)
 {
-    return ctx->fp64 ? build_impl<double>(ctx, p, s, after_order) : build_impl<float>(ctx, p, s, after_order);
+    return ctx->fp64 ? build_impl<double>(ctx, p, s, after_order, derived)
+                     : build_impl<float>(ctx, p, s, after_order, derived);
 }
 
 // Boxes of leaves, groups and radix-tree nodes with the largest coverage

@@ -174,3 +174,58 @@ def test_fig1_quadtree_leaves():
     lb, lv = B.sph_export_leaves(ctx)
     assert np.array_equal(lb, np.arange(len(labels) + 1))
     assert list(lv) == [len(c) - 1 for c in got]
+
+
+@pytest.mark.parametrize("cluster,curve", [(0, "morton"), (0, "hilbert"), (40, "morton"), (300, "morton"),
+                                           (300, "hilbert")])
+def test_build_tree_order_with_shared_top_key_bits(cluster, curve):
+    """The build sorts on the top 32 key bits and then orders each run of
+    equal top halves by (key, id); a run longer than 64 sends it to a sort on
+    all bits.  Uniform particles plus pairs and triples closer than 2^-12 of
+    the box (short runs, one pair on the same key: id order), and a cluster of
+    `cluster` particles inside one cell of side 2^-12 (a run of that length):
+    the order must be the (key, id) sort of the oracle's keys, with the
+    leaves of the leaf definition."""
+    B = need_gpu()
+    rng = np.random.default_rng(cluster + (7 if curve == "hilbert" else 0))
+    n0 = 20000
+    x, y, z = rng.random((3, n0))
+    eps = 2.0 ** -14
+    for k in range(0, 300, 3):                           # pairs and triples around particle k
+        for j in (1, 2):
+            if j == 2 and k % 2:
+                continue
+            x[k + j], y[k + j], z[k + j] = x[k] + j * eps, y[k], z[k] + eps * rng.random()
+    x[400], y[400], z[400] = x[399], y[399], z[399]     # two particles on one key
+    if cluster:
+        c = (np.floor(rng.random(3) * 0.9 * 2 ** 11) + 0.25) / 2 ** 11      # inside one level-11 cell
+        cx, cy, cz = (c + rng.random((3, cluster)).T * 2.0 ** -12).T
+        x, y, z = np.concatenate([x, cx]), np.concatenate([y, cy]), np.concatenate([z, cz])
+    n = x.size
+    w = _cloud(n, 0, True)
+    w.x, w.y, w.z = np.mod(x, 1.0), np.mod(y, 1.0), np.mod(z, 1.0)
+    w.params["curve"] = curve
+    w.params["leaf_size"] = 8
+    w.u = rng.random(n) + 0.5
+    ctx = B.Context(w.params, n)
+    p = B.Particles.from_workload(w, fp64=True)
+    ids = rng.permutation(n).astype(np.uint32)
+    p.id.copy_(torch.from_numpy(ids.view(np.int32)))
+    B.sph_build_tree(ctx, p)
+    op = to_oracle_params(oracle, w.params)
+    lo, L = oracle.domain(w.x, w.y, w.z, op)
+    keys = oracle.keys(w.x, w.y, w.z, lo, L, curve)
+    top = keys >> np.uint64(32)
+    runs = np.diff(np.flatnonzero(np.diff(np.concatenate([[-1], np.sort(top).astype(np.float64), [-1]])) != 0))
+    assert runs.max() >= (cluster if cluster else 2)     # the case is the one named
+    perm = oracle.sort_perm(keys, ids)
+    g = p.numpy()
+    assert np.array_equal(g["id"], ids[perm])
+    assert np.array_equal(g["x"], w.x[perm]) and np.array_equal(g["u"], w.u[perm])
+    lvl = oracle.leaf_levels(keys[perm], 8)
+    sk = keys[perm]
+    start = [0] + [i for i in range(1, n)
+                   if (int(sk[i]) >> (63 - 3 * int(lvl[i]))) != (int(sk[i - 1]) >> (63 - 3 * int(lvl[i])))]
+    lb, lv = B.sph_export_leaves(ctx)
+    assert np.array_equal(lb[:-1], np.array(start)) and lb[-1] == n
+    assert np.array_equal(lv, lvl[np.array(start)])
