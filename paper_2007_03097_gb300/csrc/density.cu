@@ -22,6 +22,7 @@
 // without fused multiply-add, so the neighbour sets are those of plain FP64.
 // Groups whose particles are all done drop out of the next sweep.
 #include <algorithm>
+#include <cfloat>
 #include <type_traits>
 
 #include "dfloat.cuh"
@@ -119,10 +120,7 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
 
     T sum_w = T(0), sum_dh = T(0);
     int cnt = 0;
-    int band = 0;        // list entries within a relative BAND of the support radius
-    // the band covers the change of the support over a converged step: a
-    // relative 3e-4 of r^2 (a step of up to 1e-4 h, see below)
-    constexpr float BAND = 3e-4f;
+    float gap = FLT_MAX;  // smallest |r^2 - 4 h^2| over the list entries
     if (__any_sync(0xffffffffu, active)) {
         const float4 qlo = a.group_lo[g], qhi = a.group_hi[g];
         const float gcx = 0.5f * (qlo.x + qhi.x), gcy = 0.5f * (qlo.y + qhi.y), gcz = 0.5f * (qlo.z + qhi.z);
@@ -131,7 +129,6 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
         const float L = (float)a.L, invL = 1.f / L;
         const float hf = (float)h;
         const float thr = __fmul_rn(__fmul_rn(4.f, hf), hf);
-        const float band_w = thr * BAND;                 // |r^2 - 4 h^2| <= band_w: within the band
         const int U = a.group_union[g];
         const bool img = a.periodic && a.group_img[g];   // else every source's direct image is the nearest
         const uint32_t *Ug = a.uni + a.uoff[g];
@@ -168,12 +165,12 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                 const float ttx = __shfl_sync(0xffffffffu, tx, t), tty = __shfl_sync(0xffffffffu, ty, t),
                             ttz = __shfl_sync(0xffffffffu, tz, t);
                 const float tthr = __shfl_sync(0xffffffffu, thr, t);
-                const float tbw = __shfl_sync(0xffffffffu, band_w, t);
                 const T thinv = __shfl_sync(0xffffffffu, hinv, t);
                 const unsigned long long *lq0 = reinterpret_cast<const unsigned long long *>(a.nbl + off) + t;
                 const int nq = has ? width >> 2 : 0;
                 T sw = T(0), sd = T(0);
-                int c = 0, bnd = 0;
+                int c = 0;
+                float gp = FLT_MAX;
                 // quads r, r + k in one batch, the next two in flight
                 auto quad = [&](int qi) -> unsigned long long {
                     return qi < nq ? __ldg(lq0 + 32 * (int64_t)qi) : ~0ull;
@@ -191,7 +188,7 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                         const float4 q = s_src[le];
                         const float dx = ttx - q.x, dy = tty - q.y, dz = ttz - q.z;
                         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                        bnd += fabsf(r2 - tthr) <= tbw ? 1 : 0;
+                        gp = fminf(gp, fabsf(r2 - tthr));
                         if (!(r2 < tthr)) continue;
                         const T qq = (T)sqrt_approx(r2) * thinv;
                         T w, gg;
@@ -206,19 +203,19 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                     sw += __shfl_xor_sync(0xffffffffu, sw, o);
                     sd += __shfl_xor_sync(0xffffffffu, sd, o);
                     c += __shfl_xor_sync(0xffffffffu, c, o);
-                    bnd += __shfl_xor_sync(0xffffffffu, bnd, o);
+                    gp = fminf(gp, __shfl_xor_sync(0xffffffffu, gp, o));
                 }
                 // an active lane's segment is its rank among the active lanes
                 const int from = active ? __popc(amask & ((1u << lane) - 1u)) << lk : 0;
                 sw = __shfl_sync(0xffffffffu, sw, from);
                 sd = __shfl_sync(0xffffffffu, sd, from);
                 c = __shfl_sync(0xffffffffu, c, from);
-                bnd = __shfl_sync(0xffffffffu, bnd, from);
+                gp = __shfl_sync(0xffffffffu, gp, from);
                 if (active) {
                     sum_w += sw;
                     sum_dh += sd;
                     cnt += c;
-                    band += bnd;
+                    gap = fminf(gap, gp);
                 }
             } else if (active) {
                 // list entries in batches of LB = 8 (two quads), the next
@@ -241,7 +238,7 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                     const float4 q = s_src[le];
                     const float dx = tx - q.x, dy = ty - q.y, dz = tz - q.z;
                     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    band += fabsf(r2 - thr) <= band_w ? 1 : 0;
+                    gap = fminf(gap, fabsf(r2 - thr));
                     if (!(r2 < thr)) continue;
                     const T qq = (T)sqrt_approx(r2) * hinv;
                     T w, g;
@@ -305,13 +302,17 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                 hp[i] = hn;
                 if (conv) {
                     // The reading evaluates rho once more at the final h.  When
-                    // no list entry lies within the band of the support radius,
-                    // the neighbour set at h + dh is this one and rho(h + dh) =
-                    // rho + rho' dh up to rho'' dh^2 / 2, a relative
-                    // O(10 (dh/h)^2), below 1e-7 for |dh| < 1e-4 h: within the
-                    // FP32 rounding of this sweep.  That evaluation is taken
-                    // here without another sweep.
-                    if (band == 0) {
+                    // no list entry's r^2 lies between 4 h^2 and 4 (h + dh)^2
+                    // (|4 (h + dh)^2 - 4 h^2| <= 8.0004 h |dh| for |dh| <=
+                    // 1e-4 h; tested with 10 h |dh| plus 4e-6 h^2 for the FP32
+                    // rounding of r^2), the neighbour set at h + dh is this
+                    // one and rho(h + dh) = rho + rho' dh up to rho'' dh^2 / 2,
+                    // a relative O(10 (dh/h)^2), below 1e-7: within the FP32
+                    // rounding of this sweep.  That evaluation is taken here
+                    // without another sweep.
+                    // (and the list must still cover 2 (h + dh))
+                    const double need = (double)h * (10.0 * adh + 4e-6 * (double)h);
+                    if (adh < 1e-4 * (double)h && (double)gap > need && 2.0 * (double)hn <= (double)a.cov[i]) {
                         rho_out = rho + drho * (hn - h);
                         hfin = hn;
                         done = true;

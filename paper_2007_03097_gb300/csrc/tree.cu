@@ -802,31 +802,36 @@ __global__ void k_emit(const int32_t *__restrict__ leaf_start, const int32_t *__
 // Bounding box of each range [begin[r], begin[r+1]) of at most 32 particles
 // from the FP32 high parts of the two-float positions, widened by one ulp
 // (x lies within half an ulp of its high part), and the largest coverage
-// radius in the range (.w of lo); one warp per range.
+// radius in the range (.w of lo); SEG lanes per range (8 for the leaves,
+// whose ranges are short; 32 for the target groups).
+template <int SEG>
 __global__ void k_range_boxes(const int32_t *__restrict__ begin, int nr, const float4 *__restrict__ A,
                               const float4 *__restrict__ B, const float *__restrict__ cov,
                               float4 *__restrict__ lo4, float4 *__restrict__ hi4)
 {
-    const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (r >= nr) return;
-    const int b = begin[r], e = begin[r + 1];
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = (int)(t / SEG);
+    const int sl = threadIdx.x & (SEG - 1);
+    if (t / 32 * (32 / SEG) >= nr) return;          // whole warps leave together
     float mn[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, mx[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
     float cm = 0.f;
-    for (int i = b + lane; i < e; i += 32) {
-        const float4 a = A[i];
-        const float c[3] = {a.x, a.z, B[i].x};
-        for (int d = 0; d < 3; ++d) { mn[d] = fminf(mn[d], c[d]); mx[d] = fmaxf(mx[d], c[d]); }
-        cm = fmaxf(cm, cov[i]);
+    if (r < nr) {
+        const int b = begin[r], e = begin[r + 1];
+        for (int i = b + sl; i < e; i += SEG) {
+            const float4 a = A[i];
+            const float c[3] = {a.x, a.z, B[i].x};
+            for (int d = 0; d < 3; ++d) { mn[d] = fminf(mn[d], c[d]); mx[d] = fmaxf(mx[d], c[d]); }
+            cm = fmaxf(cm, cov[i]);
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = SEG / 2; o > 0; o >>= 1) {
         for (int d = 0; d < 3; ++d) {
             mn[d] = fminf(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
             mx[d] = fmaxf(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
         }
         cm = fmaxf(cm, __shfl_xor_sync(0xffffffffu, cm, o));
     }
-    if (lane == 0) {
+    if (sl == 0 && r < nr) {
         lo4[r] = make_float4(nextafterf(mn[0], -FLT_MAX), nextafterf(mn[1], -FLT_MAX), nextafterf(mn[2], -FLT_MAX), cm);
         hi4[r] = make_float4(nextafterf(mx[0], FLT_MAX), nextafterf(mx[1], FLT_MAX), nextafterf(mx[2], FLT_MAX), 0.f);
     }
@@ -918,11 +923,11 @@ __global__ void k_refit(int nl, const int32_t *__restrict__ child, const int32_t
 int boxes_and_refit(sph_ctx *ctx, cudaStream_t s)
 {
     const int nl = (int)ctx->n_leaves, ng = (int)ctx->n_groups;
-    k_range_boxes<<<grid_for((int64_t)nl * 32, 256), 256, 0, s>>>(ctx->leaf_begin, nl, ctx->srcA, ctx->srcB, ctx->cov,
-                                                                  ctx->leaf_lo, ctx->leaf_hi);
+    k_range_boxes<8><<<grid_for((int64_t)nl * 8, 256), 256, 0, s>>>(ctx->leaf_begin, nl, ctx->srcA, ctx->srcB,
+                                                                     ctx->cov, ctx->leaf_lo, ctx->leaf_hi);
     SPH_CHECK_LAUNCH();
-    k_range_boxes<<<grid_for((int64_t)ng * 32, 256), 256, 0, s>>>(ctx->group_begin, ng, ctx->srcA, ctx->srcB, ctx->cov,
-                                                                  ctx->group_lo, ctx->group_hi);
+    k_range_boxes<32><<<grid_for((int64_t)ng * 32, 256), 256, 0, s>>>(ctx->group_begin, ng, ctx->srcA, ctx->srcB,
+                                                                      ctx->cov, ctx->group_lo, ctx->group_hi);
     SPH_CHECK_LAUNCH();
     if (nl > 1) {
         SPH_CUDA(cudaMemsetAsync(ctx->node_visit, 0, sizeof(unsigned) * (size_t)(nl - 1), s));
