@@ -122,6 +122,8 @@ int allocate(sph_ctx *c, int64_t N)
     SPH_TRY(alloc(c, &c->node_parent, N));
     SPH_TRY(alloc(c, &c->leaf_parent, N));
     SPH_TRY(alloc(c, &c->node_visit, N));
+    SPH_TRY(alloc(c, &c->node_delta, N));
+    SPH_TRY(alloc(c, &c->cell_table, (size_t)cell_table_size()));
     SPH_TRY(alloc(c, &c->node_lo, N));
     SPH_TRY(alloc(c, &c->node_hi, N));
     float4 **packs[] = {&c->srcA, &c->srcB, &c->srcC, &c->srcD, &c->srcE, &c->srcF};
@@ -194,7 +196,7 @@ void release(sph_ctx *c)
     void *ptrs[] = {c->key_a, c->key_b, c->val_a, c->val_b, c->hist, c->ns_tiles, c->dlev, c->plev, c->itmp0, c->itmp1,
                     c->itmp2, c->itmp3, c->leaf_begin, c->leaf_level, c->group_begin, c->leaf_lo, c->leaf_hi,
                     c->group_lo, c->group_hi, c->node_child, c->node_parent, c->leaf_parent, c->node_visit,
-                    c->node_lo, c->node_hi, c->srcA, c->srcB,
+                    c->node_delta, c->cell_table, c->node_lo, c->node_hi, c->srcA, c->srcB,
                     c->srcC, c->srcD, c->srcE, c->srcF, c->nbl, c->group_width, c->uni, c->group_ubound,
                     c->union_off, c->group_union, c->group_img, c->group_mark, c->kept, c->kept_count,
                     c->group_off, c->it_lo, c->it_hi, c->it_flags, c->it_sweeps, c->cov, c->act_groups[0],

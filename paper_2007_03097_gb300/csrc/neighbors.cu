@@ -36,6 +36,7 @@ struct ListArgs {
     int n_leaves, n_groups;
     const int32_t *child;
     const float4 *node_lo, *node_hi;
+    const int32_t *cell_table;     // start cells (null: every walk starts at the root)
     int periodic;
     float L, invL, slack;
     float blo[3];                  // low corner of the periodic box
@@ -287,9 +288,75 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
             stage(k2, k2 ? a.kept[(int64_t)g * a.kcap + c + lane] : 0);
         }
     }
+    // The walk starts at the nodes of the (at most eight) cells of the
+    // finest grid level whose cells are at least as large as the region R
+    // any accepted leaf lies in: the group box grown by the largest coverage
+    // anywhere (an accepted leaf is within max(its coverage, the group's) of
+    // the group box), plus 1e-5 L for the FP32 cell arithmetic.  Every leaf
+    // that meets R lies in (or is) the node of a cell that meets R, so the
+    // nodes above those cells need no visit.
     int sp = 0;
-    if (lane == 0) stack[0] = a.n_leaves > 1 ? 0 : (int)0x80000000;
-    sp = replay ? 0 : 1;
+    if (!replay) {
+        int lg = 0;
+        int64_t c0[3] = {0, 0, 0}, c1[3] = {0, 0, 0};
+        if (a.cell_table && a.n_leaves > 1) {
+            const float rroot = a.node_lo[0].w;
+            const float grow = fmaxf(qcov, rroot) * (1.f + MARGIN) + a.slack + 1e-5f * a.L;
+            const float lo3[3] = {gcx - gex - grow, gcy - gey - grow, gcz - gez - grow};
+            const float hi3[3] = {gcx + gex + grow, gcy + gey + grow, gcz + gez + grow};
+            const float E = fmaxf(fmaxf(hi3[0] - lo3[0], hi3[1] - lo3[1]), hi3[2] - lo3[2]);
+            if (E > 0.f && a.L >= 2.f * E) {
+                lg = min(CELL_LEVELS, (int)floorf(log2f(a.L / E)));
+                while (lg > 0 && ldexpf(a.L, -lg) < E) --lg;
+            }
+            if (lg > 0) {
+                const float inv = ldexpf(1.f, lg) / a.L;
+                const int64_t nc = (int64_t)1 << lg;
+                for (int d = 0; d < 3; ++d) {
+                    c0[d] = (int64_t)floorf((lo3[d] - a.blo[d]) * inv);
+                    c1[d] = (int64_t)floorf((hi3[d] - a.blo[d]) * inv);
+                    if (!a.periodic) {                 // the key domain holds every particle
+                        c0[d] = max(c0[d], (int64_t)0);
+                        c1[d] = min(c1[d], nc - 1);
+                    }
+                    if (c1[d] - c0[d] > 1 || c1[d] < c0[d]) lg = 0;   // not two cells: start at the root
+                }
+            }
+        }
+        if (lg > 0) {
+            int e = -1;
+            if (lane < 8) {
+                const int64_t nc = (int64_t)1 << lg;
+                int64_t c[3];
+                bool ok = true;
+                for (int d = 0; d < 3; ++d) {
+                    c[d] = c0[d] + ((lane >> d) & 1);
+                    ok = ok && c[d] <= c1[d];
+                    c[d] = ((c[d] % nc) + nc) % nc;        // periodic images of the grid
+                }
+                if (ok) {
+                    e = a.cell_table[cell_table_offset(lg) + c[0] + (c[1] << lg) + (c[2] << (2 * lg))];
+                    // an empty entry: the cell is empty, or it lies in a coarser leaf
+                    for (int l = lg - 1; e == -1 && l >= 1; --l) {
+                        for (int d = 0; d < 3; ++d) c[d] >>= 1;
+                        const int f = a.cell_table[cell_table_offset(l) + c[0] + (c[1] << l) + (c[2] << (2 * l))];
+                        if (f == -1) continue;
+                        if (f < 0) e = f;
+                        break;
+                    }
+                }
+            }
+            // a coarse leaf can be the node of several cells: push it once
+            const unsigned same = __match_any_sync(0xffffffffu, e);
+            const bool keep = e != -1 && __ffs(same) - 1 == lane;
+            const unsigned km = __ballot_sync(0xffffffffu, keep);
+            if (keep) stack[__popc(km & ((1u << lane) - 1u))] = e;
+            sp = __popc(km);
+        } else {
+            if (lane == 0) stack[0] = a.n_leaves > 1 ? 0 : (int)0x80000000;
+            sp = 1;
+        }
+    }
     // a correct radix tree visits each node at most once; the bound guards a
     // corrupted tree against an endless walk
     int64_t budget = 4 * (int64_t)a.n_leaves + 64;
@@ -515,6 +582,7 @@ int build_impl(sph_ctx *ctx, cudaStream_t s)
     a.n_groups = ng;
     a.child = ctx->node_child;
     a.node_lo = ctx->node_lo; a.node_hi = ctx->node_hi;
+    a.cell_table = ctx->cell_table;
     a.periodic = ctx->prm.periodic;
     const double ls = ctx->len_scale;              // the lengths of the packed positions
     for (int d = 0; d < 3; ++d) a.blo[d] = (float)(ctx->dom[d] * ls);

@@ -139,6 +139,12 @@ struct DevCounters {
     double unit_ref[2];                // h and m of the first particle in key order (unit choice)
 };
 
+// Start-cell table of the neighbour search: levels 1..CELL_LEVELS of the
+// key grid, 8^l int32 entries for level l, stored one level after another.
+constexpr int CELL_LEVELS = 7;
+__host__ __device__ constexpr int64_t cell_table_offset(int l) { return ((int64_t(1) << (3 * l)) - 8) / 7; }
+__host__ __device__ constexpr int64_t cell_table_size() { return cell_table_offset(CELL_LEVELS + 1); }
+
 // near-sorted key pass: (key, id) pairs and per-tile extremes, prefix
 // maximum, suffix minimum and misplaced counts
 struct NsKey {
@@ -198,6 +204,9 @@ struct sph_ctx {
     int32_t *node_parent = nullptr;     // internal nodes
     int32_t *leaf_parent = nullptr;
     uint32_t *node_visit = nullptr;
+    int32_t *node_delta = nullptr;      // leading key bits shared by an internal node's leaves
+    int32_t *cell_table = nullptr;      // start cells of the neighbour search (cell_table_offset)
+    int pow2_shift = -1;                // the key grid by shifts (>= 0) or by FP64 scaling
     float4 *node_lo = nullptr, *node_hi = nullptr;   // .w of lo = max coverage
     float4 *group_lo = nullptr, *group_hi = nullptr; // .w of lo = max coverage
     // ---- two-float split of the positions (padded)

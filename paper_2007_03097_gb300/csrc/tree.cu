@@ -149,6 +149,24 @@ __device__ __forceinline__ bool finite_bits(double v)
     return (((uint64_t)__double_as_longlong(v) >> 52) & 0x7FF) != 0x7FF;
 }
 
+// the 21-bit cell coordinates of a point on the key grid (the same cells
+// for the keys and for the start-cell table of the neighbour search)
+__device__ __forceinline__ void grid_cell(double xi, double yi, double zi, int pow2_shift, const DevCounters *cnt,
+                                          uint64_t &cx, uint64_t &cy, uint64_t &cz)
+{
+    if (pow2_shift >= 0) {
+        cx = cell_pow2(xi, pow2_shift);
+        cy = cell_pow2(yi, pow2_shift);
+        cz = cell_pow2(zi, pow2_shift);
+    } else {
+        const double lx = cnt->dom[0], ly = cnt->dom[1], lz = cnt->dom[2];
+        const double scale = 2097152.0 / cnt->dom[3];
+        cx = cell_of(xi, lx, scale);
+        cy = cell_of(yi, ly, scale);
+        cz = cell_of(zi, lz, scale);
+    }
+}
+
 template <typename T>
 __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ y,
                        const double *__restrict__ z, const T *__restrict__ h,
@@ -164,17 +182,7 @@ __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ 
     if (!ok) atomicOr(&cnt->err, ERRB_NONFINITE);
     if (dim == 1 && (yi != 0.0 || zi != 0.0)) atomicOr(&cnt->err, ERRB_OFF_AXIS);
     uint64_t cx, cy, cz;
-    if (pow2_shift >= 0) {
-        cx = cell_pow2(xi, pow2_shift);
-        cy = cell_pow2(yi, pow2_shift);
-        cz = cell_pow2(zi, pow2_shift);
-    } else {
-        const double lx = cnt->dom[0], ly = cnt->dom[1], lz = cnt->dom[2];
-        const double scale = 2097152.0 / cnt->dom[3];
-        cx = cell_of(xi, lx, scale);
-        cy = cell_of(yi, ly, scale);
-        cz = cell_of(zi, lz, scale);
-    }
+    grid_cell(xi, yi, zi, pow2_shift, cnt, cx, cy, cz);
     const uint64_t key = (curve == SPH_CURVE_HILBERT ? hilbert3((uint32_t)cx, (uint32_t)cy, (uint32_t)cz)
                                                      : spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2)) |
                          (1ull << 63);
@@ -749,6 +757,42 @@ __global__ void k_leaf_level(const uint8_t *__restrict__ dlev, int64_t n, int S,
     plev[i] = best;
 }
 
+// The same for a leaf size S known at compile time: the block's window of
+// dlev sits in shared memory and the forward minima in registers.
+template <int S>
+__global__ void __launch_bounds__(256) k_leaf_level_s(const uint8_t *__restrict__ dlev, int64_t n,
+                                                      uint8_t *__restrict__ plev, DevCounters *cnt)
+{
+    __shared__ uint8_t w[256 + 2 * S];              // w[k] = dlev[base - S + 1 + k], 0 outside [0, n)
+    const int64_t base = (int64_t)blockIdx.x * 256;
+    for (int k = threadIdx.x; k < 256 + 2 * S - 1; k += 256) {
+        const int64_t j = base - S + 1 + k;
+        w[k] = (j >= 0 && j < n) ? dlev[j] : (uint8_t)0;
+    }
+    __syncthreads();
+    const int64_t i = base + threadIdx.x;
+    if (i >= n) return;
+    const int c = threadIdx.x + S - 1;              // w[c] = dlev[i]
+    uint8_t F[S + 1];
+    uint8_t m = 255;
+#pragma unroll
+    for (int t = 1; t <= S; ++t) {
+        const uint8_t d = w[c + t];
+        m = d < m ? d : m;
+        F[t] = m;
+    }
+    uint8_t B = 255, best = 255;
+#pragma unroll
+    for (int tb = 0; tb < S; ++tb) {
+        const uint8_t d = w[c - tb];
+        B = d < B ? d : B;
+        const uint8_t v = B > F[S - tb] ? B : F[S - tb];
+        best = v < best ? v : best;
+    }
+    if (best > 21) { atomicOr(&cnt->err, ERRB_LEAF_DEGENERATE); best = 21; }
+    plev[i] = best;
+}
+
 // leaf start flag (itmp0) and sibling-segment start index (itmp1, -1 if none)
 __global__ void k_mark(const uint8_t *__restrict__ dlev, const uint8_t *__restrict__ plev, int64_t n,
                        int32_t *__restrict__ leaf_start, int32_t *__restrict__ seg_val)
@@ -851,7 +895,7 @@ __device__ __forceinline__ int delta_key(const uint64_t *__restrict__ keys, cons
 // split is the first differing bit; children with index bit 31 are leaves.
 __global__ void k_radix_tree(const uint64_t *__restrict__ keys, const int32_t *__restrict__ lb, int nl,
                              int32_t *__restrict__ child, int32_t *__restrict__ node_parent,
-                             int32_t *__restrict__ leaf_parent)
+                             int32_t *__restrict__ leaf_parent, int32_t *__restrict__ node_delta)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nl - 1) return;
@@ -864,6 +908,7 @@ __global__ void k_radix_tree(const uint64_t *__restrict__ keys, const int32_t *_
         if (delta_key(keys, lb, nl, i, i + (l + t) * d) > dmin) l += t;
     const int j = i + l * d;
     const int dnode = delta_key(keys, lb, nl, i, j);
+    node_delta[i] = dnode;                       // leading key bits the node's leaves share
     int s = 0;
     int t = l;
     do {
@@ -880,6 +925,37 @@ __global__ void k_radix_tree(const uint64_t *__restrict__ keys, const int32_t *_
     child[2 * i] = c0;
     child[2 * i + 1] = c1;
     if (i == 0) node_parent[0] = -1;
+}
+
+// Start-cell table of the neighbour search: for each level l = 1..CELL_LEVELS
+// and each cell of the level-l grid (index x + 2^l (y + 2^l z)), the tree
+// node that holds exactly the cell's particles: the internal node whose
+// leaves share the cell's 1 + 3 l key bits while its parent's do not, or a
+// leaf alone in its cell (leaf | 1 << 31); -1 where the cell holds no
+// particle or lies inside a coarser leaf (the lookup then finds that leaf at
+// the coarser level).  Cells come from a particle of the node (leaf i's first
+// particle lies in internal node i), with the key arithmetic.
+__global__ void k_cell_table(int nl, const int32_t *__restrict__ lb, const int32_t *__restrict__ leaf_level,
+                             const int32_t *__restrict__ node_parent, const int32_t *__restrict__ leaf_parent,
+                             const int32_t *__restrict__ node_delta, const double *__restrict__ x,
+                             const double *__restrict__ y, const double *__restrict__ z, int pow2_shift,
+                             const DevCounters *cnt, int32_t *__restrict__ table)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * nl - 1) return;
+    const bool leaf = t >= nl - 1;
+    const int id = leaf ? t - (nl - 1) : t;
+    const int dp = leaf ? node_delta[leaf_parent[id]] : (id == 0 ? 0 : node_delta[node_parent[id]]);
+    const int dself = leaf ? 1 + 3 * leaf_level[id] : node_delta[id];
+    const int p = lb[id];
+    uint64_t cx, cy, cz;
+    grid_cell(x[p], y[p], z[p], pow2_shift, cnt, cx, cy, cz);
+    for (int l = 1; l <= CELL_LEVELS; ++l) {
+        if (!(dp < 1 + 3 * l && 1 + 3 * l <= dself)) continue;
+        const int sh = 21 - l;
+        const int64_t c = (int64_t)(cx >> sh) + ((int64_t)(cy >> sh) << l) + ((int64_t)(cz >> sh) << (2 * l));
+        table[cell_table_offset(l) + c] = leaf ? (id | (int)0x80000000) : id;
+    }
 }
 
 __device__ __forceinline__ void load_box(int c, const float4 *leaf_lo, const float4 *leaf_hi,
@@ -1022,6 +1098,7 @@ int keys_impl(sph_ctx *ctx, const sph_particles *p, uint64_t *keys, uint32_t *va
         const double fr = std::frexp(q.box_hi[0], &ex);        // L = fr 2^ex, fr in [0.5, 1)
         if (fr == 0.5 && 22 - ex >= 0 && 22 - ex <= 60) pow2_shift = 22 - ex;   // L = 2^(ex - 1)
     }
+    ctx->pow2_shift = pow2_shift;
     k_keys<T><<<grid_for(p->n, 256), 256, 0, s>>>(p->x, p->y, p->z, (const T *)p->h, (const T *)p->m, p->n,
                                                   ctx->prm.curve, ctx->prm.dim, pow2_shift, ctx->dcnt, keys, vals);
     SPH_CHECK_LAUNCH();
@@ -1084,7 +1161,10 @@ int leaves_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s)
     SPH_CHECK_LAUNCH();
     k_dlev<<<grid_for(n, 256), 256, 0, s>>>(ctx->key_a, n, ctx->dlev);
     SPH_CHECK_LAUNCH();
-    k_leaf_level<<<grid_for(n, 128), 128, 0, s>>>(ctx->dlev, n, ctx->prm.leaf_size, ctx->plev, ctx->dcnt);
+    if (ctx->prm.leaf_size == 32)
+        k_leaf_level_s<32><<<grid_for(n, 256), 256, 0, s>>>(ctx->dlev, n, ctx->plev, ctx->dcnt);
+    else
+        k_leaf_level<<<grid_for(n, 128), 128, 0, s>>>(ctx->dlev, n, ctx->prm.leaf_size, ctx->plev, ctx->dcnt);
     SPH_CHECK_LAUNCH();
     int32_t *ls = ctx->itmp0, *gs = ctx->itmp1;
     int32_t *lidx = ctx->itmp2, *gidx = ctx->itmp3;
@@ -1171,7 +1251,12 @@ int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s, OrderHook *after_
     const int nl = (int)ctx->n_leaves;
     if (nl > 1) {
         k_radix_tree<<<grid_for(nl - 1, 256), 256, 0, s>>>(ctx->key_a, ctx->leaf_begin, nl, ctx->node_child,
-                                                           ctx->node_parent, ctx->leaf_parent);
+                                                           ctx->node_parent, ctx->leaf_parent, ctx->node_delta);
+        SPH_CHECK_LAUNCH();
+        SPH_CUDA(cudaMemsetAsync(ctx->cell_table, 0xFF, sizeof(int32_t) * (size_t)cell_table_size(), s));
+        k_cell_table<<<grid_for(2 * (int64_t)nl - 1, 256), 256, 0, s>>>(
+            nl, ctx->leaf_begin, ctx->leaf_level, ctx->node_parent, ctx->leaf_parent, ctx->node_delta, p->x, p->y,
+            p->z, ctx->pow2_shift, ctx->dcnt, ctx->cell_table);
         SPH_CHECK_LAUNCH();
     }
     ctx->tree_valid = true;

@@ -45,6 +45,42 @@ def test_neighbour_sets_bit_exact(kind, wname, curve):
         assert np.array_equal(s1, s2), a
 
 
+@pytest.mark.parametrize("wname,curve", [("lattice", "morton"), ("lattice", "hilbert"), ("polytrope", "morton"),
+                                         ("polytrope", "hilbert")])
+def test_neighbour_sets_of_large_sets(wname, curve):
+    """The list walk starts at the nodes of grid cells a few levels below the
+    root (the finest level whose cells cover a group's reach), looked up in a
+    per-level cell table; cells inside a coarser leaf resolve to that leaf.
+    A 64^3 periodic lattice (cells of level 2-3) and a 200,000-particle
+    polytrope in its bounding cube (dense core: deep levels; sparse envelope:
+    coarse leaves): the density and force sets of 4,000 sampled particles,
+    including the extremes of each coordinate, equal the oracle's."""
+    w = (inputs.lattice(64, jitter=0.3) if wname == "lattice"
+         else inputs.polytrope(200000, seed=12, precision="fp64"))
+    w.params["curve"] = curve
+    B = need_gpu()
+    ctx = B.Context(w.params, w.n)
+    p = B.Particles.from_workload(w, fp64=True)
+    B.sph_build_tree(ctx, p)
+    B.sph_density(ctx, p)
+    g = p.numpy()
+    rng = np.random.default_rng(3)
+    t = set(rng.choice(w.n, size=4000, replace=False).tolist())
+    for c in ("x", "y", "z"):
+        o = np.argsort(g[c])
+        t.update(o[:20].tolist())
+        t.update(o[-20:].tolist())
+    t = np.array(sorted(t), dtype=np.int64)
+    op = to_oracle_params(oracle, w.params)
+    for kind in (0, 1):
+        counts, offsets, idx = B.sph_neighbors(ctx, p, kind)
+        oc, oo, oi = oracle.neighbors(op, kind, g["x"], g["y"], g["z"], g["h"], targets=t)
+        assert np.array_equal(counts[t], oc)
+        for k, a in enumerate(t):
+            got = np.sort(idx[offsets[a]:offsets[a + 1]])
+            assert np.array_equal(got, np.sort(oi[oo[k]:oo[k + 1]])), (kind, a)
+
+
 def test_lattice_fixed_h_fp64():
     """16^3 jittered periodic lattice, M4, fixed h: floats to 1e-12."""
     w = inputs.lattice(16)
