@@ -375,8 +375,8 @@ int sph_peak_fp32(double *tflops, double *ms, void *stream);
  *     device; otherwise SPH_ERR_ARG, checked before anything is launched.
  *   - Every call looks up the device address of the static array on the
  *     current device (a device reset moves it); the first call on a device
- *     also loads the library's device code there, so make that first call
- *     before any stream capture on the device.
+ *     also loads the library's device code there, which can synchronise
+ *     that device.
  *   - Every call uses the same scratch and leaves the last call's contents in
  *     it.  Calls that overlap on the GPU (other streams, other threads, same
  *     device) race: serialise them.

@@ -358,28 +358,32 @@ int sph_step(sph_ctx *ctx, sph_particles *p, double dt, int use_hnet, sph_step_s
     SPH_CUDA(cudaEventRecord(ev[0], s));
     SPH_TRY(kick_drift(ctx, p, dt, s));
     // The h seed reads only particle fields, so it runs on the side stream as
-    // soon as the particles are in key order, beside the leaf build (a chain
-    // of small kernels that leaves most of the GPU idle); the density
-    // iteration waits for it.
+    // soon as the fields exist in key order (in a full sort, on the scratch
+    // copy before it is copied back), beside the copy back and the leaf
+    // build (chains of small kernels that leave most of the GPU idle); the
+    // density iteration waits for it.
     struct SeedHook : OrderHook {
         sph_ctx *ctx;
-        const sph_particles *p;
         double dt;
         bool train;
-        int operator()(cudaStream_t ms) override
+        int operator()(cudaStream_t ms, const sph_particles *view) override
         {
             SPH_CUDA(cudaEventRecord(ctx->ev_order, ms));
             SPH_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_order, 0));
             SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->hnet_fallback, 0, sizeof(int32_t), ctx->side));
             SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->hnet_err, 0, sizeof(uint32_t), ctx->side));
-            SPH_TRY(copy_field(ctx, ctx->hold, p->h, p->n, ctx->side));   // the pre-iteration h
-            SPH_TRY(hnet_seed_from_fields(ctx, p, dt, train, ctx->hseed, ctx->side));
+            SPH_TRY(copy_field(ctx, ctx->hold, view->h, view->n, ctx->side));   // the pre-iteration h
+            SPH_TRY(hnet_seed_from_fields(ctx, view, dt, train, ctx->hseed, ctx->side));
             SPH_CUDA(cudaEventRecord(ctx->ev_seed, ctx->side));
+            return SPH_OK;
+        }
+        int join(cudaStream_t ms) override
+        {
+            SPH_CUDA(cudaStreamWaitEvent(ms, ctx->ev_seed, 0));
             return SPH_OK;
         }
     } hook;
     hook.ctx = ctx;
-    hook.p = p;
     hook.dt = dt;
     hook.train = train_net;
     // omega, P, c and vsig are rewritten for every particle by this step's

@@ -35,9 +35,8 @@ static __device__ __align__(256) unsigned char g_sort_scratch[SCRATCH_BYTES];
 // Device address of the static array on the current device.  In host code
 // the symbol is only a host-side stand-in, so its device address is looked up
 // with cudaGetSymbolAddress on every call, with the device current: the first
-// call on a device also loads the library's device code there (so it must
-// come before any stream capture on that device), and a device reset gives
-// the array a new address, so none is kept between calls.
+// call on a device also loads the library's device code there, and a device
+// reset gives the array a new address, so none is kept between calls.
 int scratch_address(unsigned char **out)
 {
     void *p = nullptr;

@@ -515,13 +515,20 @@ __device__ __forceinline__ float wrap_diff(float a, float c, float L, float invL
 
 // ------------------------------------------------------------ launchers
 // tree.cu
-// after_order (may be null) is called with the build's stream when the
-// particle arrays are in their final key order, before the leaves are built
-// (a second time in the rare build that sorts again on all key bits).
+// after_order (may be null) is called with the build's stream as soon as
+// the particle fields exist in their final key order, before the leaves are
+// built (a second time in the rare build that sorts again on all key bits).
+// view holds them: the caller's arrays, or the tree build's scratch copy
+// that the full sort gathers into and copies back from (unchanged until the
+// next tree build; fields the build does not permute keep the caller's
+// pointers).
 // derived = false leaves omega, P, c and vsig unpermuted: for a caller that
 // rewrites all four for every particle before reading them (sph_step).
+// join(s) makes s wait for the work the hook queued elsewhere (before the
+// build overwrites its scratch copy again).
 struct OrderHook {
-    virtual int operator()(cudaStream_t s) = 0;
+    virtual int operator()(cudaStream_t s, const sph_particles *view) = 0;
+    virtual int join(cudaStream_t) { return SPH_OK; }
 };
 int tree_build(sph_ctx *ctx, sph_particles *p, cudaStream_t s, OrderHook *after_order = nullptr,
                bool derived = true);

@@ -1130,10 +1130,26 @@ void near_sorted(sph_ctx *ctx, sph_particles *p, const FieldTable &t, int limit,
     k_ns_put<<<grid_for(limit, 256), 256, 0, s>>>(t, mpos, ctx->dcnt, limit);
 }
 
+// The particle arrays as the scratch copy of the table holds them (the
+// fields the table does not permute keep the caller's pointers).
+sph_particles scratch_view(const FieldTable &t, const sph_particles *p)
+{
+    sph_particles v = *p;
+    void **fields[] = {(void **)&v.x, (void **)&v.y, (void **)&v.z, &v.vx, &v.vy, &v.vz, &v.m, &v.h, &v.u,
+                       &v.hprev, &v.rho, &v.omega, &v.P, &v.c, &v.ax, &v.ay, &v.az, &v.dudt, &v.divv,
+                       &v.vsig, (void **)&v.nnb, (void **)&v.id};
+    for (void **f : fields)
+        for (int k = 0; k < t.nf; ++k)
+            if (*f && t.src[k] == *f) { *f = t.dst[k]; break; }
+    return v;
+}
+
 // full sort, then permute every particle array into key order.  prefix: the
 // radix passes cover the top 32 key bits and runs of equal top halves are
-// ordered on the device (ERRB_PREFIX_RUN when one is too long for that)
-int full_sort(sph_ctx *ctx, sph_particles *p, const FieldTable &t, cudaStream_t s, bool prefix)
+// ordered on the device (ERRB_PREFIX_RUN when one is too long for that).
+// hook (may be null) runs on the scratch copy between the gather and the
+// copy back.
+int full_sort(sph_ctx *ctx, sph_particles *p, const FieldTable &t, cudaStream_t s, bool prefix, OrderHook *hook)
 {
     const int64_t n = p->n;
     if (prefix) {
@@ -1146,6 +1162,10 @@ int full_sort(sph_ctx *ctx, sph_particles *p, const FieldTable &t, cudaStream_t 
     SPH_CHECK_LAUNCH();
     k_gather<<<grid_for(n, 256), 256, 0, s>>>(t, ctx->val_a, n);
     SPH_CHECK_LAUNCH();
+    if (hook) {
+        const sph_particles v = scratch_view(t, p);
+        SPH_TRY((*hook)(s, &v));
+    }
     k_copy_back<<<grid_for(n, 256), 256, 0, s>>>(t, n);
     SPH_CHECK_LAUNCH();
     return SPH_OK;
@@ -1207,17 +1227,17 @@ int build_impl(sph_ctx *ctx, sph_particles *p, cudaStream_t s, OrderHook *after_
         ctx->ns_full_streak = m < 0 ? ctx->ns_full_streak + 1 : 0;
         if (ctx->ns_full_streak >= 2) ctx->ns_skip = 7;
     }
-    if (m < 0) SPH_TRY(full_sort(ctx, p, t, s, true));
-    if (after_order) SPH_TRY((*after_order)(s));
+    if (m < 0) SPH_TRY(full_sort(ctx, p, t, s, true, after_order));
+    else if (after_order) SPH_TRY((*after_order)(s, p));
     SPH_TRY(leaves_impl<T>(ctx, p, s));
     if (ctx->hcnt->err & ERRB_PREFIX_RUN) {
         // more than 64 particles share the top 32 key bits: the order inside
         // such a run is not final; sort the (now permuted) particles on all
         // bits and build the leaves again
         SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->err, 0, sizeof(uint32_t), s));
+        if (after_order) SPH_TRY(after_order->join(s));   // its reads of the scratch copy end first
         SPH_TRY(keys_impl<T>(ctx, p, ctx->key_a, ctx->val_a, s));
-        SPH_TRY(full_sort(ctx, p, t, s, false));
-        if (after_order) SPH_TRY((*after_order)(s));
+        SPH_TRY(full_sort(ctx, p, t, s, false, after_order));
         SPH_TRY(leaves_impl<T>(ctx, p, s));
     }
     ctx->ns_moved = m;
