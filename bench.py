@@ -66,8 +66,14 @@ DF_PER_FP32 = 1.0 / 18.0
 # captured launch (traffic scales with the particles at a fixed neighbour
 # number, so a capture on a reduced side is scaled by the particle ratio)
 TRAFFIC = {
-    "forces_fp64_sedov": {"bytes_per_launch": 84208896, "particles": 262144, "src": "29a20052c842",
-                          "files": ["forces.cu", "dfloat.cuh", "sph_internal.cuh"]},
+    # dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu, see profiles/), with the
+    # particles of the captured workload; valid while the listed sources hash as recorded
+    "forces_fp64_sedov": {"bytes_per_launch": 84855296, "particles": 262144, "src": "ee07d7cffc96",
+                          "files": ["forces.cu", "dfloat.cuh", "neighbors.cu", "sph_internal.cuh"]},
+    # captured on the 128^3 box, scaled by the particles (per-particle lists and unions
+    # are the same at 256^3)
+    "forces_mixed_turbulence": {"bytes_per_launch": 799481344, "particles": 2097152, "src": "ef9be64f39cc",
+                                "files": ["forces.cu", "neighbors.cu", "sph_internal.cuh"]},
 }
 PROTOCOL_TRAIN_STEPS = 200
 
