@@ -132,8 +132,11 @@ int allocate(sph_ctx *c, int64_t N)
     SPH_TRY(alloc(c, &c->nbl, (size_t)c->nbl_cap));
     SPH_TRY(alloc(c, &c->group_width, N));
     SPH_TRY(alloc(c, &c->group_off, N + 1));
-    c->uni_cap = c->prm.nb_capacity > 0 ? c->prm.nb_capacity : 128 * N;   // exact unions never exceed the exact lists
+    // union slots: exact unions never exceed the exact lists; the leaf-bound
+    // sizing needs about 30 per particle at ~100 neighbours
+    c->uni_cap = c->prm.nb_capacity > 0 ? c->prm.nb_capacity : 64 * N;
     SPH_TRY(alloc(c, &c->uni, (size_t)c->uni_cap));
+    if (!c->fp64) SPH_TRY(alloc(c, &c->urec, (size_t)c->uni_cap));
     SPH_TRY(alloc(c, &c->group_ubound, N));
     SPH_TRY(alloc(c, &c->union_off, N + 1));
     SPH_TRY(alloc(c, &c->group_union, N));
@@ -197,7 +200,7 @@ void release(sph_ctx *c)
                     c->itmp2, c->itmp3, c->leaf_begin, c->leaf_level, c->group_begin, c->leaf_lo, c->leaf_hi,
                     c->group_lo, c->group_hi, c->node_child, c->node_parent, c->leaf_parent, c->node_visit,
                     c->node_delta, c->cell_table, c->node_lo, c->node_hi, c->srcA, c->srcB,
-                    c->srcC, c->srcD, c->srcE, c->srcF, c->nbl, c->group_width, c->uni, c->group_ubound,
+                    c->srcC, c->srcD, c->srcE, c->srcF, c->nbl, c->group_width, c->uni, c->urec, c->group_ubound,
                     c->union_off, c->group_union, c->group_img, c->group_mark, c->kept, c->kept_count,
                     c->group_off, c->it_lo, c->it_hi, c->it_flags, c->it_sweeps, c->cov, c->act_groups[0],
                     c->act_groups[1], c->vpx, c->vpy, c->vpz, c->upred, c->hold, c->hseed, c->hstart, c->gbuf,

@@ -46,6 +46,7 @@ struct DensArgs {
     const uint16_t *nbl;
     int64_t cap;
     const uint32_t *uni;           // group source unions
+    const float4 *urec;            // their staged records (mixed: written by the list fill)
     const int64_t *uoff;
     const int32_t *group_union;    // union size per group
     const int32_t *group_img;      // 1: the group's sources include periodic images
@@ -126,12 +127,10 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
         const float gcx = 0.5f * (qlo.x + qhi.x), gcy = 0.5f * (qlo.y + qhi.y), gcz = 0.5f * (qlo.z + qhi.z);
         const float4 A = a.srcA[i], Bz = a.srcB[i];
         const float tx = (A.x - gcx) + A.y, ty = (A.z - gcy) + A.w, tz = (Bz.x - gcz) + Bz.y;
-        const float L = (float)a.L, invL = 1.f / L;
         const float hf = (float)h;
         const float thr = __fmul_rn(__fmul_rn(4.f, hf), hf);
         const int U = a.group_union[g];
-        const bool img = a.periodic && a.group_img[g];   // else every source's direct image is the nearest
-        const uint32_t *Ug = a.uni + a.uoff[g];
+        const float4 *Rg = a.urec + a.uoff[g];
         const unsigned long long *lq = reinterpret_cast<const unsigned long long *>(a.nbl + off) + lane;
         // a group with at most 16 targets left to evaluate gives each one a
         // segment of k = 32 / nextpow2(count) lanes that splits its list (a
@@ -142,17 +141,11 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
         for (int c0 = 0; c0 < U; c0 += a.src_cap) {
             const int cn = min(a.src_cap, U - c0);
             __syncwarp();
-            for (int t = lane; t < cn; t += 32) {
-                const uint32_t b = __ldg(Ug + c0 + t);
-                const float4 qa = __ldg(a.srcA + b), qb = __ldg(a.srcB + b);
-                float rx = qa.x - gcx, ry = qa.z - gcy, rz = qb.x - gcz;
-                if (img) {                     // the image nearest the group
-                    rx = wrap_diff(qa.x, gcx, L, invL);
-                    ry = wrap_diff(qa.z, gcy, L, invL);
-                    rz = wrap_diff(qb.x, gcz, L, invL);
-                }
-                s_src[t] = make_float4(rx + qa.y, ry + qa.w, rz + qb.y, qb.z);
-            }
+            // the list fill wrote each union member's record {x, y, z
+            // relative to the group-box centre, nearest image, m}: one
+            // asynchronous 16-byte copy per source, all of them in flight
+            for (int t = lane; t < cn; t += 32) cp_async16(&s_src[t], Rg + c0 + t);
+            cp_async_wait_all();
             __syncwarp();
             if (lk > 0) {
                 // segment s (lanes [s k, s k + k)) takes the s-th active
@@ -740,6 +733,7 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
     a.nbl = ctx->nbl;
     a.cap = ctx->nbl_cap;
     a.uni = ctx->uni;
+    a.urec = ctx->urec;
     a.uoff = ctx->union_off;
     a.group_union = ctx->group_union;
     a.group_img = ctx->group_img;

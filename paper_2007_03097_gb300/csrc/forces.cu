@@ -64,16 +64,6 @@ constexpr int FB = 4;          // warps per block (one target group per block)
 constexpr int UC = 512;        // union sources staged per group when the largest union is not known
 constexpr int UC_MAX = 1024;   // the most sources staged (48 KB of shared memory)
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all()
-{
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
 
 // source b relative to the group centre (gcx, gcy, gcz), its nearest periodic
 // image when the group's sources include images: the same arithmetic as the

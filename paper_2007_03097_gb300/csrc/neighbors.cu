@@ -49,6 +49,7 @@ struct ListArgs {
     int32_t *group_union;          // union size of each group (fill pass)
     int32_t *group_img;            // 1: a candidate lies across a periodic face (fill pass)
     uint32_t *uni;
+    float4 *urec;                  // the union members' staged records (null: not written)
     int64_t ucap;
     int32_t *kept;                 // leaves kept by the sizing pass, kcap per group (0: not cached)
     int32_t *kept_count;
@@ -74,12 +75,13 @@ __device__ __forceinline__ float axis_gap(float c, float e, float p, int periodi
 enum { LM_BOUND = 0, LM_EXACT = 1, LM_FILL = 2 };
 
 template <int MODE>
-__global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
+__global__ void __launch_bounds__(LW * 32, 7) k_lists(ListArgs a)
 {
     constexpr bool FILL = MODE == LM_FILL;
     __shared__ int32_t s_stack[LW][STACK];
     __shared__ float4 s_pa[LW][TILE];   // source {x, y, z} relative to the group centre, cov^2 (1 + MARGIN)
     __shared__ int32_t s_pi[LW][TILE];  // source index
+    __shared__ float s_pm[LW][TILE];    // source mass
     __shared__ int32_t s_lb[LW][32], s_incl[LW][32];
     __shared__ float4 s_bc[LW][32], s_be[LW][32];     // leaves one walk step accepted: centre, cov^2 (1 + MARGIN);
                                                       // half-extent + slack
@@ -90,6 +92,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
     if (g >= a.n_groups) return;
     int32_t *stack = s_stack[w];
     float4 *pa = s_pa[w];
+    float *pm = s_pm[w];
     int32_t *pi = s_pi[w];
 
     const int gb = a.group_begin[g], ge = a.group_begin[g + 1];
@@ -182,7 +185,13 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
         const unsigned any = __reduce_or_sync(0xffffffffu, bits);
         if (FILL) {
             const int pos = uc + __popc(any & ((1u << lane) - 1u));
-            if (((any >> lane) & 1u) && pos < ucap) a.uni[uoff + pos] = (uint32_t)j;
+            if (((any >> lane) & 1u) && pos < ucap) {
+                a.uni[uoff + pos] = (uint32_t)j;
+                if (a.urec) {                          // the density sweeps' staged record
+                    const float4 r = pa[lane];
+                    a.urec[uoff + pos] = make_float4(r.x, r.y, r.z, pm[lane]);
+                }
+            }
             s_loc[w][lane] = pos < (int)SPH_LOCAL_NONE ? pos : 0;
             __syncwarp();
             const int take = min(__popc(bits), max(width - count, 0));   // entries within the sized slots
@@ -227,6 +236,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
             const int take2 = min(32, total - base);
             bool within = false;
             float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
+            float mj = 0.f;
             int j = 0;
             if (lane < take2) {
                 // owner: first lane whose inclusive end exceeds item
@@ -247,6 +257,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
                 }
                 const float cj = a.cov[j];
                 rec = make_float4(rx + qa.y, ry + qa.w, rz + qb.y, cj * cj * (1.f + MARGIN));
+                mj = qb.z;
                 // every target lies in the group box: a candidate farther than
                 // max(largest target coverage, its own) from the box is
                 // within no target's reach and is not staged (in a
@@ -261,6 +272,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
                 const int t = ns + __popc(km & ((1u << lane) - 1u));
                 pa[t] = rec;
                 pi[t] = j;
+                pm[t] = mj;
             }
             ns += __popc(km);
             __syncwarp();
@@ -271,6 +283,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(ListArgs a)
                 if (lane < rest) {
                     pa[lane] = pa[32 + lane];
                     pi[lane] = pi[32 + lane];
+                    pm[lane] = pm[32 + lane];
                 }
                 ns = rest;
                 __syncwarp();
@@ -598,6 +611,7 @@ int build_impl(sph_ctx *ctx, cudaStream_t s)
     a.group_union = ctx->group_union;
     a.group_img = ctx->group_img;
     a.uni = ctx->uni;
+    a.urec = ctx->urec;
     a.ucap = ctx->uni_cap;
     a.kept = ctx->kept;
     a.kept_count = ctx->kept_count;

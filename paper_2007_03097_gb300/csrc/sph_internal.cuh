@@ -221,6 +221,8 @@ struct sph_ctx {
     int32_t *group_width = nullptr;
     int64_t *group_off = nullptr;       // n_groups + 1
     uint32_t *uni = nullptr;            // union slots
+    float4 *urec = nullptr;             // SPH_MIXED: per union slot {x, y, z relative to the group-box
+                                        // centre (nearest image), m}, as the sweeps stage them
     int64_t uni_cap = 0;
     int32_t *group_ubound = nullptr;    // union slots sized per group
     int64_t *union_off = nullptr;       // n_groups + 1
@@ -511,6 +513,19 @@ __device__ __forceinline__ float wrap_diff(float a, float c, float L, float invL
         d = (d - k * L) + err;
     }
     return d;
+}
+
+// 16-byte global -> shared copy without a register round trip (cp.async;
+// both addresses 16-byte aligned), and the wait for all of a thread's copies
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 // ------------------------------------------------------------ launchers
