@@ -27,6 +27,7 @@ struct ForceArgs {
     const uint16_t *nbl;
     int64_t cap;
     const uint32_t *uni;           // group source unions
+    const float4 *urec;            // their position records (mixed: written by the list fill)
     const int64_t *uoff;
     const int32_t *group_img;      // 1: the group's sources include periodic images
     const int32_t *group_union;    // union size per group
@@ -53,6 +54,9 @@ struct ForceArgs {
 // shared memory (as many sources as the largest union of the lists when that
 // is known, at most UC_MAX, else UC), as three interleaved records per source:
 //   sP {x, y, z relative to the group centre (periodic image folded in), h}
+//                               copied with cp.async from the record the list
+//                               fill wrote for the union entry ({x, y, z, m};
+//                               h from sT replaces m)
 //   sV {vx, vy, vz, m}          copied with cp.async from the packed record C
 //   sT {rho/2, P/rho^2, c, h}   copied with cp.async from the packed record D
 // Every warp holds the group's 32 targets (one per lane) and walks every FB-th
@@ -102,16 +106,17 @@ __global__ void __launch_bounds__(FB * 32, 8) k_forces_f32(ForceArgs a)
     const float Lf = (float)a.L, invL = 1.f / Lf;
     const bool img = a.periodic && a.group_img[g];   // else every source's direct image is the nearest
     const uint32_t *Ug = a.uni + a.uoff[g];
+    const float4 *Rg = a.urec + a.uoff[g];
     const int U = min(a.group_union[g], UCd);
 
-    // ---- stage the union
+    // ---- stage the union: the position record the list fill wrote (relative
+    // to the group-box centre, nearest image; m in .w until h replaces it
+    // below) and the two records of the force pass, all by asynchronous copies
     for (int t = threadIdx.x; t < U; t += FB * 32) {
         const uint32_t b = __ldg(Ug + t);
+        cp_async16(&s_dyn[3 * t], Rg + t);
         cp_async16(&s_dyn[3 * t + 1], a.srcC + b);
         cp_async16(&s_dyn[3 * t + 2], a.srcD + b);
-        const float4 qa = __ldg(a.srcA + b), qb = __ldg(a.srcB + b);
-        const float hb = __ldg(reinterpret_cast<const float *>(a.srcD + b) + 3);
-        s_dyn[3 * t] = rel_pos(qa, qb, gcx, gcy, gcz, img, Lf, invL, hb);
     }
 
     // ---- the target of this lane (every warp holds the same 32 targets)
@@ -128,6 +133,7 @@ __global__ void __launch_bounds__(FB * 32, 8) k_forces_f32(ForceArgs a)
     const int nq = width >> 2;
     const unsigned long long *lq = reinterpret_cast<const unsigned long long *>(a.nbl + off) + lane;
     cp_async_wait_all();
+    for (int t = threadIdx.x; t < U; t += FB * 32) s_dyn[3 * t].w = s_dyn[3 * t + 2].w;   // h of the source
     __syncthreads();
 
     // pair sums without the per-target factors sigma (a, du/dt) and
@@ -497,6 +503,7 @@ int run_impl(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, con
     a.nbl = ctx->nbl;
     a.cap = ctx->nbl_cap;
     a.uni = ctx->uni;
+    a.urec = ctx->urec;
     a.uoff = ctx->union_off;
     a.n_groups = (int)ctx->n_groups;
     a.x = p->x; a.y = p->y; a.z = p->z;
