@@ -15,6 +15,15 @@ __device__ __forceinline__ T kinetic(T vx, T vy, T vz) { return T(0.5) * (vx * v
 
 // First half kick and drift.  thermo: du holds de/dt; e = u + v^2/2 gets the
 // half kick and u = e - v_half^2/2.
+// p wrapped into [0, L) as `if (p >= L) p -= L; else if (p < 0) p += L`
+__device__ __forceinline__ double wrap_origin(double p, double L)
+{
+    const long long b = __double_as_longlong(p);
+    if (b >= __double_as_longlong(L)) return p - L;
+    if (b < 0 && b != (long long)0x8000000000000000ull) return p + L;
+    return p;
+}
+
 template <typename T>
 __global__ void k_kick_drift(double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
                              T *__restrict__ vx, T *__restrict__ vy, T *__restrict__ vz, T *__restrict__ u,
@@ -34,7 +43,14 @@ __global__ void k_kick_drift(double *__restrict__ x, double *__restrict__ y, dou
     if (thermo) u[i] = (u[i] + kinetic(vx0, vy0, vz0) + du[i] * hdt) - kinetic(vxh, vyh, vzh);
     else u[i] = u[i] + du[i] * hdt;
     double px = x[i] + (double)vxh * dt, py = y[i] + (double)vyh * dt, pz = z[i] + (double)vzh * dt;
-    if (periodic) {
+    if (periodic == 2) {
+        // box [0, L)^3: the same decisions from the bits (IEEE order is the
+        // integer order for non-negative doubles; -0 is not below 0), which
+        // keeps the FP64 pipe, 1/64 of the FP32 rate on GB300, for the drift
+        px = wrap_origin(px, hi.x);
+        py = wrap_origin(py, hi.y);
+        pz = wrap_origin(pz, hi.z);
+    } else if (periodic) {
         if (px >= hi.x) px -= hi.x - lo.x; else if (px < lo.x) px += hi.x - lo.x;
         if (py >= hi.y) py -= hi.y - lo.y; else if (py < lo.y) py += hi.y - lo.y;
         if (pz >= hi.z) pz -= hi.z - lo.z; else if (pz < lo.z) pz += hi.z - lo.z;
@@ -215,7 +231,9 @@ int kd_impl(sph_ctx *ctx, sph_particles *p, double dt, cudaStream_t s)
     const sph_params &q = ctx->prm;
     k_kick_drift<T><<<grid_for(p->n, 256), 256, 0, s>>>(
         p->x, p->y, p->z, (T *)p->vx, (T *)p->vy, (T *)p->vz, (T *)p->u, (const T *)p->ax, (const T *)p->ay,
-        (const T *)p->az, (const T *)p->dudt, p->n, dt, q.periodic, make_double3(q.box_lo[0], q.box_lo[1], q.box_lo[2]),
+        (const T *)p->az, (const T *)p->dudt, p->n, dt,
+        q.periodic ? (q.box_lo[0] == 0.0 && q.box_lo[1] == 0.0 && q.box_lo[2] == 0.0 ? 2 : 1) : 0,
+        make_double3(q.box_lo[0], q.box_lo[1], q.box_lo[2]),
         make_double3(q.box_hi[0], q.box_hi[1], q.box_hi[2]), q.energy == SPH_ENERGY_TOTAL, ctx->dcnt);
     SPH_CHECK_LAUNCH();
     return SPH_OK;

@@ -167,15 +167,16 @@ __global__ void __launch_bounds__(LW * 32, 7) k_lists(ListArgs a)
         if (j >= gb && j < ge) s_self[w][j - gb] = lane;
         // candidate k is within reach when d = r^2 - max(cov_a^2, cov_k^2) < 0
         // (d = 0 sits on the margin-widened radius, outside every exact
-        // support); the sign bit of d shifts in from the right, so after the
-        // batch bit 31 - k holds candidate k and one bit reversal orders them
+        // support; d is one chain of three fused multiply-adds, its rounding
+        // far inside the margin); the sign bit of d shifts in from the right,
+        // so after the batch bit 31 - k holds candidate k and one bit
+        // reversal orders them
         unsigned rbits = 0;
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
             const float4 q = pa[k];                    // .w = cov^2 (1 + MARGIN)
             const float dx = tx - q.x, dy = ty - q.y, dz = tz - q.z;
-            const float r2 = (dx * dx + dy * dy) + dz * dz;
-            const float d = r2 - fmaxf(ca2, q.w);
+            const float d = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, -fmaxf(ca2, q.w))));   // r^2 - max
             rbits = __funnelshift_l(__float_as_uint(d), rbits, 1);
         }
         unsigned bits = __brev(rbits);
