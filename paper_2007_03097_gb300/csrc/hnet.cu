@@ -5,7 +5,10 @@
 // FP32 activations and accumulation (inference: layer 2 on the tensor cores).  The prediction of log(h_next / h) is
 // s = f3 * y with f3 = div v * dt: a particle at rest keeps its h exactly, and
 // the network learns the gain of the continuity estimate div v dt / 3.
+#include <algorithm>
 #include <cmath>
+
+#include <cuda_fp16.h>
 
 #include "sph_internal.cuh"
 #include "tc.cuh"
@@ -68,21 +71,25 @@ __global__ void k_features(FeatArgs<T> fa, int64_t stride, int64_t count, float 
 // One warpgroup per tile of 128 samples (a persistent loop over tiles).  Each
 // thread owns one sample: it evaluates layer 1 (5 -> 64, FP32) and writes the
 // activations to shared memory as the A operand of the layer-2 contraction,
-// split into three BF16 terms a = hi + mid + lo (hi = bf16(a), mid =
-// bf16(a - hi), lo = bf16(a - hi - mid)), which carry the FP32 activation to
-// within 2^-24 of its value.  One thread issues the 12 tcgen05 MMAs
-// (M = 128, N = 64, K = 16 each; three terms x four K steps) that accumulate
-// z2 = a1 W2^T in FP32 in tensor memory; each thread then reads its sample's
-// row back (tcgen05.ld), applies b2, SiLU and layer 3 and writes f3 * y.
-// The products with the BF16 weights are exact and accumulate in FP32, as in
-// the CUDA-core evaluation.
+// split into two FP16 terms a = hi + lo (hi = fp16(a), lo = fp16(a - hi)),
+// which carry the FP32 activation to about 2^-22 of its value (the SiLU
+// activations lie far inside FP16's range).  W2 enters as FP16 too: every
+// BF16 weight within FP16's normal range is an FP16 value, so the weights are
+// the BF16 ones exactly (a weight below 2^-14 in magnitude rounds to FP16's
+// subnormal grid, 2^-24; one beyond 65504 becomes infinite and the seed falls
+// back to h).  One thread issues the 8 tcgen05 MMAs (M = 128, N = 64, K = 16
+// each; two terms x four K steps) that accumulate z2 = a1 W2^T in FP32 in
+// tensor memory; each thread then reads its sample's row back (tcgen05.ld),
+// applies b2, SiLU and layer 3 and writes f3 * y.  (Three BF16 terms held
+// 48 KB of shared memory per tile and three blocks per SM; two FP16 terms
+// hold 32 KB, and four blocks run per SM.)
 constexpr int TM = 128;                          // samples per tile (MMA M)
-constexpr int NSPLIT = 3;                        // BF16 terms per activation
+constexpr int NSPLIT = 2;                        // FP16 terms per activation
 constexpr uint32_t CM_LBO = 128;                 // K-adjacent core matrices
 constexpr uint32_t CM_SBO = (H / 8) * 128;       // next 8 rows: 1024 bytes
 constexpr int A_TILE = TM * H * 2;               // 16 KB per term
 constexpr int B_TILE = H * H * 2;                // 8 KB
-constexpr int B_PAD = 1024;                      // slack after B
+constexpr int B_PAD = 0;                         // A follows B (B_TILE keeps A 1024-aligned)
 constexpr int WF = 320 + 64 + 64 + 64 + 1;       // FP32 W1, b1, b2, w3, b3
 constexpr uint32_t TM_COLS = 64;                 // TMEM columns: D is 128 x 64 FP32
 constexpr uint64_t MMA_WAIT_NS = 1000000000ull;  // give up on an MMA after 1 s
@@ -98,9 +105,9 @@ __device__ __forceinline__ uint32_t cm_off(int row, int k)
     return (uint32_t)((row >> 3) * CM_SBO + (k >> 3) * CM_LBO + (row & 7) * 16 + (k & 7) * 2);
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+__device__ __forceinline__ uint32_t pack_f16(float lo, float hi)
 {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    const __half2 v = __floats2half2_rn(lo, hi);
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
@@ -131,7 +138,12 @@ __global__ void __launch_bounds__(TM) k_infer_tc(const __nv_bfloat16 *__restrict
     // (O_W2 = 384 elements: 16-byte aligned)
     for (int v = tid; v < H * H / 8; v += TM) {
         const int n = v / (H / 8), k = 8 * (v % (H / 8));
-        *reinterpret_cast<uint4 *>(sB + cm_off(n, k)) = *reinterpret_cast<const uint4 *>(wb + O_W2 + n * H + k);
+        const __nv_bfloat16 *w8 = wb + O_W2 + n * H + k;      // eight BF16 weights -> FP16
+        *reinterpret_cast<uint4 *>(sB + cm_off(n, k)) =
+            make_uint4(pack_f16(__bfloat162float(w8[0]), __bfloat162float(w8[1])),
+                       pack_f16(__bfloat162float(w8[2]), __bfloat162float(w8[3])),
+                       pack_f16(__bfloat162float(w8[4]), __bfloat162float(w8[5])),
+                       pack_f16(__bfloat162float(w8[6]), __bfloat162float(w8[7])));
     }
     for (int k = tid; k < 320 + 64; k += TM) wf[k] = __bfloat162float(wb[O_W1 + k]);          // W1, b1
     for (int k = tid; k < 64 + 64 + 1; k += TM) wf[384 + k] = __bfloat162float(wb[O_B2 + k]);  // b2, W3, b3
@@ -144,7 +156,7 @@ __global__ void __launch_bounds__(TM) k_infer_tc(const __nv_bfloat16 *__restrict
     tc::fence_after_sync();
     const uint32_t tbase = tslot;
     const uint32_t sA_a = tc::smem_addr(sA), sB_a = tc::smem_addr(sB);
-    constexpr uint32_t IDESC = tc::idesc_bf16_f32(TM, H);
+    constexpr uint32_t IDESC = tc::idesc_f16_f32(TM, H);
 
     const int64_t ntiles = (nb + TM - 1) / TM;
     uint32_t parity = 0;
@@ -182,12 +194,9 @@ __global__ void __launch_bounds__(TM) k_infer_tc(const __nv_bfloat16 *__restrict
                     for (int k = 0; k < 5; ++k) z += W1[5 * j + k] * x[k];
                     a[u] = z * sigm(z);
                 }
-                const __nv_bfloat162 hi = __floats2bfloat162_rn(a[0], a[1]);
-                const float r0 = a[0] - __low2float(hi), r1 = a[1] - __high2float(hi);
-                const __nv_bfloat162 mid = __floats2bfloat162_rn(r0, r1);
+                const __half2 hi = __floats2half2_rn(a[0], a[1]);
                 q[0][e / 2] = *reinterpret_cast<const uint32_t *>(&hi);
-                q[1][e / 2] = *reinterpret_cast<const uint32_t *>(&mid);
-                q[2][e / 2] = pack_bf16(r0 - __low2float(mid), r1 - __high2float(mid));
+                q[1][e / 2] = pack_f16(a[0] - __low2float(hi), a[1] - __high2float(hi));
             }
 #pragma unroll
             for (int t = 0; t < NSPLIT; ++t)
@@ -559,6 +568,24 @@ int hnet_init(sph_ctx *ctx)
                                   infer_tc_smem()));
     SPH_CUDA(cudaFuncSetAttribute(k_infer_tc<true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   infer_tc_smem()));
+    // the persistent inference grid: the blocks that fit on an SM at once,
+    // with the SM's memory split in favour of shared memory
+    for (const void *f : {(const void *)k_infer_tc<false, float>, (const void *)k_infer_tc<true, float>,
+                          (const void *)k_infer_tc<true, double>})
+        SPH_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+    int sm_smem = 0, reserved = 0;
+    SPH_CUDA(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
+    SPH_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, ctx->device));
+    // what the shared memory holds and what tensor memory holds (512 columns
+    // per SM, TM_COLS per block; 128 threads and ~50 registers per block are
+    // never the limit), and at most four: the seed runs beside the copy back
+    // and the leaf build, which need room on the same SMs (256^3 turbulence,
+    // tree phase of a learned step: 5.45 ms with five blocks, 5.05 with four,
+    // 5.35 with three); blocks beyond the resident ones only run later
+    const int by_smem = sm_smem / (infer_tc_smem() + reserved);
+    const int by_tmem = 512 / (int)TM_COLS;
+    ctx->infer_per_sm = std::max(1, std::min(4, std::min(by_smem, by_tmem)));
     return SPH_OK;
 }
 
@@ -576,7 +603,7 @@ namespace {
 unsigned infer_blocks(const sph_ctx *ctx, int64_t nb)
 {
     int64_t blocks = (nb + TM - 1) / TM;
-    const int64_t cap = (int64_t)ctx->num_sms * 3;       // 3 resident blocks of ~60 KB per SM
+    const int64_t cap = (int64_t)ctx->num_sms * ctx->infer_per_sm;   // the resident blocks
     return (unsigned)(blocks > cap ? cap : blocks);
 }
 }  // namespace

@@ -207,6 +207,7 @@ struct sph_ctx {
     int32_t *node_delta = nullptr;      // leading key bits shared by an internal node's leaves
     int32_t *cell_table = nullptr;      // start cells of the neighbour search (cell_table_offset)
     int pow2_shift = -1;                // the key grid by shifts (>= 0) or by FP64 scaling
+    int infer_per_sm = 1;               // resident blocks per SM of the seed inference
     float4 *node_lo = nullptr, *node_hi = nullptr;   // .w of lo = max coverage
     float4 *group_lo = nullptr, *group_hi = nullptr; // .w of lo = max coverage
     // ---- two-float split of the positions (padded)
