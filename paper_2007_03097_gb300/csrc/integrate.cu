@@ -164,6 +164,7 @@ __global__ void __launch_bounds__(TB) k_totals_partial_f32(
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc[k] = df{0.f, 0.f};
     double mn = DBL_MAX, mnx = __longlong_as_double(0x7ff0000000000000ll);   // +inf
+    float mnf = __int_as_float(0x7f800000);                                    // +inf
     for (int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x; i < n; i += (int64_t)gridDim.x * TB) {
         const float mi = m[i], vxi = vx[i], vyi = vy[i], vzi = vz[i];
         const float axi = ax[i], ayi = ay[i], azi = az[i];
@@ -184,10 +185,17 @@ __global__ void __launch_bounds__(TB) k_totals_partial_f32(
             acc[7] = df_add(acc[7], df_mul_f(df_add_f(wa, du[i]), mi));
         }
         if (vsig) {
-            const double v = vsig[i], hi = h[i];
-            if (v > 0 && hi <= mnx * v) {
-                mn = fmin(mn, hi / v);
-                mnx = mn * (1.0 + 0x1p-40);
+            // an FP32 screen (the threshold grown by 2^-20, far beyond the
+            // FP32 product's rounding) keeps the FP64 test and quotient for
+            // the few particles that can lower the minimum
+            const float vf = vsig[i], hf = h[i];
+            if (vf > 0.f && hf <= mnf * vf) {
+                const double v = vf, hi = hf;
+                if (hi <= mnx * v) {
+                    mn = fmin(mn, hi / v);
+                    mnx = mn * (1.0 + 0x1p-40);
+                    mnf = (float)mnx * (1.f + 0x1p-20f);
+                }
             }
         }
     }
