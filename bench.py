@@ -72,7 +72,7 @@ TRAFFIC = {
                           "files": ["forces.cu", "dfloat.cuh", "neighbors.cu", "sph_internal.cuh"]},
     # captured on the 128^3 box, scaled by the particles (per-particle lists and unions
     # are the same at 256^3)
-    "forces_mixed_turbulence": {"bytes_per_launch": 799481344, "particles": 2097152, "src": "ef9be64f39cc",
+    "forces_mixed_turbulence": {"bytes_per_launch": 1190839040, "particles": 2097152, "src": "d0d7d4fe40b5",
                                 "files": ["forces.cu", "neighbors.cu", "sph_internal.cuh"]},
 }
 PROTOCOL_TRAIN_STEPS = 200
