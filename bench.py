@@ -68,7 +68,7 @@ DF_PER_FP32 = 1.0 / 18.0
 TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu, see profiles/), with the
     # particles of the captured workload; valid while the listed sources hash as recorded
-    "forces_fp64_sedov": {"bytes_per_launch": 84855296, "particles": 262144, "src": "ee07d7cffc96",
+    "forces_fp64_sedov": {"bytes_per_launch": 84944896, "particles": 262144, "src": "7745970d2658",
                           "files": ["forces.cu", "dfloat.cuh", "neighbors.cu", "sph_internal.cuh"]},
     # captured on the 128^3 box, scaled by the particles (per-particle lists and unions
     # are the same at 256^3)
