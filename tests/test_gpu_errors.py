@@ -52,14 +52,18 @@ def test_list_capacity_exhausted():
     assert e.value.code == B.SPH_ERR_CAPACITY
 
 
-def test_bounded_lists_fall_back_to_exact_sizing():
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_bounded_lists_fall_back_to_exact_sizing(precision):
     """Lists are first sized by the particles of the leaves within reach; a
     capacity that holds the exact lists but not those bounds makes the
-    context switch to exact counts and restart, with the same result."""
+    context switch to exact counts and restart, with the same result (in
+    mixed precision the unions' position records share that capacity)."""
     B = need_gpu()
     w = inputs.sedov(16)
+    w.params["precision"] = precision
+    fp64 = precision == "fp64"
     ctx = B.Context(w.params, w.n)
-    p = B.Particles.from_workload(w, fp64=True)
+    p = B.Particles.from_workload(w, fp64=fp64)
     B.sph_build_tree(ctx, p)
     st = B.sph_density(ctx, p)
     fa = B.sph_forces(ctx, p)
@@ -69,7 +73,7 @@ def test_bounded_lists_fall_back_to_exact_sizing():
     assert not info["exact_sizing"] and info["slots_reserved"] > info["slots_used"] == fa["list_entries"]
     tight = dict(w.params, nb_capacity=int(used * 1.05))
     ctx2 = B.Context(tight, w.n)
-    q = B.Particles.from_workload(w, fp64=True)
+    q = B.Particles.from_workload(w, fp64=fp64)
     B.sph_build_tree(ctx2, q)
     st2 = B.sph_density(ctx2, q)
     fb = B.sph_forces(ctx2, q)
