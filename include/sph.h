@@ -266,14 +266,22 @@ int sph_tree_info(sph_ctx *ctx, int64_t *n_leaves, int64_t *n_groups);
 
 /* Neighbour-list storage of the last list build, as of the last call that
  * returned (host out, each may be NULL): slots reserved (32 x the per-group
- * widths the build sized: leaf bounds, or exact counts once exact_sizing is
- * set), slots holding the exact lists, entries of the per-group source
- * unions the lists index, whether exact sizing is on (set for the rest of
- * the context's life when leaf bounds exceeded nb_capacity), and the largest
- * union of one group.
+ * widths the build sized), slots holding the exact lists, entries of the
+ * per-group source unions the lists index, whether exact sizing is on, the
+ * largest union of one group, whether the last build predicted its widths,
+ * and how many predicted builds overflowed.
+ * A target's list is predicted to hold at most 1.25 n + 16 entries, n its
+ * length in the previous build (the lengths follow the particles through
+ * every tree build); the first build of a context, and every build after 4
+ * predicted builds overflowed, sizes by the particles of the leaves within
+ * reach (leaf bounds).  A build that
+ * outgrows predicted widths is taken again with leaf bounds; one that
+ * outgrows leaf bounds within nb_capacity switches the context to exact
+ * counts for the rest of its life.  Results do not depend on the sizing.
  * Implementation detail of the list builder; the paper has no counterpart. */
 int sph_list_info(sph_ctx *ctx, int64_t *slots_reserved, int64_t *slots_used, int64_t *union_used,
-                  int32_t *exact_sizing, int32_t *union_max);
+                  int32_t *exact_sizing, int32_t *union_max, int32_t *predicted,
+                  int32_t *pred_failures);
 
 /* After sph_build_tree: leaf_begin (device, n_leaves + 1 entries, the last is
  * n) and level (device, n_leaves; octree level of each leaf cell). */

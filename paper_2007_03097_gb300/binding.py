@@ -115,7 +115,8 @@ def load(path: str | None = None):
         "sph_morton_keys": ([V, _c.POINTER(sph_particles), V, _c.POINTER(_c.c_double), V], I32),
         "sph_sort_keys": ([V, I64, V, V, V, V], I32),
         "sph_tree_info": ([V, _c.POINTER(I64), _c.POINTER(I64)], I32),
-        "sph_list_info": ([V, _c.POINTER(I64), _c.POINTER(I64), _c.POINTER(I64), _c.POINTER(I32), _c.POINTER(I32)],
+        "sph_list_info": ([V, _c.POINTER(I64), _c.POINTER(I64), _c.POINTER(I64), _c.POINTER(I32), _c.POINTER(I32),
+                           _c.POINTER(I32), _c.POINTER(I32)],
                           I32),
         "sph_export_leaves": ([V, V, V, V], I32),
         "sph_neighbors": ([V, _c.POINTER(sph_particles), I32, V, V, V, V], I32),
@@ -397,13 +398,17 @@ def sph_tree_info(ctx: Context):
 
 
 def sph_list_info(ctx: Context) -> dict:
-    """Neighbour-list slots reserved and used by the last build, and whether
-    the context sizes lists by exact counts."""
-    r, u, un, e, um = _c.c_int64(), _c.c_int64(), _c.c_int64(), _c.c_int32(), _c.c_int32()
+    """Neighbour-list slots reserved and used by the last build, whether the
+    context sizes lists by exact counts, and whether the last build predicted
+    its widths from the neighbour counts (with the predicted builds that
+    overflowed)."""
+    r, u, un = _c.c_int64(), _c.c_int64(), _c.c_int64()
+    e, um, pr, pf = _c.c_int32(), _c.c_int32(), _c.c_int32(), _c.c_int32()
     _check(ctx, load().sph_list_info(ctx.handle, _c.byref(r), _c.byref(u), _c.byref(un), _c.byref(e),
-                                     _c.byref(um)))
+                                     _c.byref(um), _c.byref(pr), _c.byref(pf)))
     return {"slots_reserved": int(r.value), "slots_used": int(u.value), "union_used": int(un.value),
-            "exact_sizing": bool(e.value), "union_max": int(um.value)}
+            "exact_sizing": bool(e.value), "union_max": int(um.value), "predicted": bool(pr.value),
+            "pred_failures": int(pf.value)}
 
 
 def sph_export_leaves(ctx: Context, stream=None):

@@ -152,6 +152,7 @@ int allocate(sph_ctx *c, int64_t N)
     SPH_TRY(alloc(c, &c->it_flags, N));
     SPH_TRY(alloc(c, &c->it_sweeps, N));
     SPH_TRY(alloc(c, &c->cov, N));
+    SPH_TRY(alloc(c, &c->lcount, N));
     SPH_TRY(alloc(c, &c->act_groups[0], N));
     SPH_TRY(alloc(c, &c->act_groups[1], N));
     double **d8[] = {(double **)&c->vpx, (double **)&c->vpy, (double **)&c->vpz, (double **)&c->upred,
@@ -202,7 +203,7 @@ void release(sph_ctx *c)
                     c->node_delta, c->cell_table, c->node_lo, c->node_hi, c->srcA, c->srcB,
                     c->srcC, c->srcD, c->srcE, c->srcF, c->nbl, c->group_width, c->uni, c->urec, c->group_ubound,
                     c->union_off, c->group_union, c->group_img, c->group_mark, c->kept, c->kept_count,
-                    c->group_off, c->it_lo, c->it_hi, c->it_flags, c->it_sweeps, c->cov, c->act_groups[0],
+                    c->group_off, c->it_lo, c->it_hi, c->it_flags, c->it_sweeps, c->cov, c->lcount, c->act_groups[0],
                     c->act_groups[1], c->vpx, c->vpy, c->vpz, c->upred, c->hold, c->hseed, c->hstart, c->gbuf,
                     c->scan_tmp, c->red, c->dcnt, c->hn_master, c->hn_bf16, c->hn_m, c->hn_v, c->hn_grad,
                     c->hn_part, c->hn_sample};
@@ -511,10 +512,12 @@ int sph_tree_info(sph_ctx *ctx, int64_t *n_leaves, int64_t *n_groups)
 }
 
 int sph_list_info(sph_ctx *ctx, int64_t *slots_reserved, int64_t *slots_used, int64_t *union_used,
-                  int32_t *exact_sizing, int32_t *union_max)
+                  int32_t *exact_sizing, int32_t *union_max, int32_t *predicted, int32_t *pred_failures)
 {
     if (!ctx) return SPH_ERR_ARG;
     if (union_max) *union_max = ctx->hcnt->union_max;
+    if (predicted) *predicted = ctx->lists_pred ? 1 : 0;
+    if (pred_failures) *pred_failures = ctx->lists_pred_fail;
     if (slots_reserved) *slots_reserved = (int64_t)ctx->hcnt->list_total;
     if (slots_used) *slots_used = (int64_t)ctx->hcnt->list_used;
     if (union_used) *union_used = (int64_t)ctx->hcnt->union_used;

@@ -862,23 +862,22 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
     return SPH_OK;
 }
 
-// Lists sized by leaf bounds can exceed nb_capacity where exact counts fit:
-// the context then sizes them exactly from now on and the iteration restarts
-// from its first guess.
+// Lists sized by prediction or by leaf bounds can outgrow their sizes where
+// exact counts fit in nb_capacity: the iteration then restarts from its first
+// guess with the safer sizing (leaf bounds for this call after a prediction,
+// exact counts from now on after leaf bounds).
 template <typename T>
 int run_impl(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats *st, bool eos, cudaStream_t s)
 {
-    const bool bounded = !ctx->lists_exact;
     const void *first = seed;
-    if (bounded && !seed) {
+    if (!ctx->lists_exact && !seed) {
         SPH_TRY(copy_field(ctx, ctx->hstart, p->h, p->n, s));
         first = ctx->hstart;
     }
-    const int r = run_once<T>(ctx, p, seed, st, eos, s);
-    if (r != SPH_ERR_CAPACITY || !bounded) return r;
-    ctx->lists_exact = true;
-    ctx->err.clear();
-    return run_once<T>(ctx, p, first, st, eos, s);
+    int r = run_once<T>(ctx, p, seed, st, eos, s);
+    while (r == SPH_ERR_CAPACITY && lists_escalate(ctx)) r = run_once<T>(ctx, p, first, st, eos, s);
+    ctx->lists_pred_skip = false;
+    return r;
 }
 
 }  // namespace

@@ -584,13 +584,12 @@ int forces_run(sph_ctx *ctx, sph_particles *p, const void *vx, const void *vy, c
         return ctx->fp64 ? run_impl<double>(ctx, p, vx, vy, vz, u, st, reuse_lists, s)
                          : run_impl<float>(ctx, p, vx, vy, vz, u, st, reuse_lists, s);
     };
-    const bool bounded = !ctx->lists_exact;
-    const int r = run();
-    // lists sized by leaf bounds overflowed nb_capacity: size them exactly
-    if (r != SPH_ERR_CAPACITY || !bounded || !st) return r;
-    ctx->lists_exact = true;
-    ctx->lists_valid = false;
-    ctx->err.clear();
-    SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->err, 0, sizeof(uint32_t), s));
-    return run();
+    int r = run();
+    // lists that outgrew their predicted or bounded sizes: size them more safely
+    while (r == SPH_ERR_CAPACITY && st && lists_escalate(ctx)) {
+        SPH_CUDA(cudaMemsetAsync(&ctx->dcnt->err, 0, sizeof(uint32_t), s));
+        r = run();
+    }
+    ctx->lists_pred_skip = false;
+    return r;
 }

@@ -37,6 +37,11 @@ struct ListArgs {
     const int32_t *child;
     const float4 *node_lo, *node_hi;
     const int32_t *cell_table;     // start cells (null: every walk starts at the root)
+    const uint32_t *pred_len;      // sizing pass: list lengths of the previous build, which
+                                   // predict the widths (null: per-target culling, leaf bounds)
+    uint32_t *len_out;             // fill: each target's list length (low 16 bits) and the low
+                                   // 16 bits of its id (high 16 bits)
+    const uint32_t *pid;           // particle ids
     int periodic;
     float L, invL, slack;
     float blo[3];                  // low corner of the periodic box
@@ -137,6 +142,19 @@ __global__ void __launch_bounds__(LW * 32, 7) k_lists(ListArgs a)
     int nkept = 0;                                 // leaves kept by the sizing pass (warp-uniform)
     int uc = 0;                                    // union members so far (warp-uniform)
     int ub = 0;                                    // union slots needed (sizing passes)
+    int ub_lane = 0;                               // this lane's leaves' part of it (predicted widths)
+    // Predicted widths (sizing pass): from the previous build's list lengths
+    // when their id bits match this group's particles (a group whose
+    // particles changed is sized by leaf bounds).  The group then keeps every accepted
+    // leaf, the fill's candidate tests do the rest, and only the union bound
+    // counts the leaves' particles.
+    int plen = 0;
+    bool predict = false;
+    if (MODE == LM_BOUND && a.pred_len) {
+        const uint32_t l = a.pred_len[ia];
+        plen = (int)(l & 0xFFFFu);
+        predict = __all_sync(0xffffffffu, !tgt || (l >> 16) == (a.pid[ia] & 0xFFFFu));
+    }
     bool overflow = false;
 
     // this lane's quads, and the entries of the quad being filled
@@ -414,8 +432,14 @@ __global__ void __launch_bounds__(LW * 32, 7) k_lists(ListArgs a)
         // need = the targets within reach of this lane's leaf
         unsigned need = 0;
         const unsigned lmask = __ballot_sync(0xffffffffu, acc && leaf);
+        const bool cull = !predict;
+        if (predict && acc && leaf) {
+            const int id = node & 0x7fffffff;
+            need = 1u;
+            ub_lane += a.leaf_begin[id + 1] - a.leaf_begin[id];
+        }
         int lcnt = 0;                        // particles of this lane's accepted leaf (sizing pass)
-        if (lmask) {                         // the accepted leaves' boxes, read by every lane
+        if (cull && lmask) {                 // the accepted leaves' boxes, read by every lane
             s_bc[w][lane] = bc;
             s_be[w][lane] = make_float4(be.x + a.slack, be.y + a.slack, be.z + a.slack, 0.f);
             if (MODE == LM_BOUND && acc && leaf) {
@@ -424,7 +448,7 @@ __global__ void __launch_bounds__(LW * 32, 7) k_lists(ListArgs a)
             }
             __syncwarp();
         }
-        for (unsigned m = lmask; m; m &= m - 1) {
+        for (unsigned m = cull ? lmask : 0u; m; m &= m - 1) {
             const int l = __ffs(m) - 1;
             const float4 c = s_bc[w][l], e = s_be[w][l];
             const float gx = axis_gap(c.x, e.x, PA.x, wrap, a.L, a.invL);
@@ -457,6 +481,15 @@ __global__ void __launch_bounds__(LW * 32, 7) k_lists(ListArgs a)
     if (MODE != LM_BOUND && ns > 0) process(ns);
 
     if (overflow && lane == 0) atomicOr(&a.cnt->err, ERRB_STACK);
+    if (predict) {
+        // a list is predicted to hold at most 1.25 n + 16 entries, n its
+        // length in the previous build; a longer one makes the fill flag the
+        // capacity and the build is taken again with leaf bounds
+        const int nb = tgt ? plen : 0;
+        count = nb + (nb >> 2) + 16;
+        for (int o = 16; o > 0; o >>= 1) ub_lane += __shfl_xor_sync(0xffffffffu, ub_lane, o);
+        ub = ub_lane;
+    }
     int wmax = count;
     for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
     if (!FILL) {
@@ -478,6 +511,7 @@ __global__ void __launch_bounds__(LW * 32, 7) k_lists(ListArgs a)
             k = (k + 3) & ~3;
         }
         for (; k < used; k += 4) qp[32 * (int64_t)(k >> 2)] = ~0ull;
+        if (tgt) a.len_out[ia] = (a.pid[ia] << 16) | (uint32_t)min(count, 0xFFFF);   // the next build's prediction
         if (lane == 0) {
             a.group_width[g] = used;          // the exact width, within the sized slots
             a.group_union[g] = min(uc, ucap);
@@ -581,7 +615,7 @@ __global__ void k_export(const int32_t *__restrict__ group_begin, int ng, const 
     counts[ia] = c;
 }
 
-int build_impl(sph_ctx *ctx, cudaStream_t s)
+int build_impl(sph_ctx *ctx, const uint32_t *pid, bool predict, cudaStream_t s)
 {
     const int ng = (int)ctx->n_groups;
     SPH_TRY(tree_boxes(ctx, s));
@@ -597,6 +631,10 @@ int build_impl(sph_ctx *ctx, cudaStream_t s)
     a.child = ctx->node_child;
     a.node_lo = ctx->node_lo; a.node_hi = ctx->node_hi;
     a.cell_table = ctx->cell_table;
+    ctx->lists_pred = predict && !ctx->lists_exact && ctx->lcount_valid;
+    a.pred_len = ctx->lists_pred ? ctx->lcount : nullptr;
+    a.len_out = ctx->lcount;
+    a.pid = pid;
     a.periodic = ctx->prm.periodic;
     const double ls = ctx->len_scale;              // the lengths of the packed positions
     for (int d = 0; d < 3; ++d) a.blo[d] = (float)(ctx->dom[d] * ls);
@@ -635,6 +673,7 @@ int build_impl(sph_ctx *ctx, cudaStream_t s)
     k_guard_widths<<<grid_for(ng, 256), 256, 0, s>>>(ctx->group_width, ng, ctx->dcnt);
     SPH_CHECK_LAUNCH();
     ctx->lists_valid = true;
+    ctx->lcount_valid = true;
     return SPH_OK;
 }
 
@@ -656,7 +695,7 @@ int lists_build(sph_ctx *ctx, const sph_particles *p, cudaStream_t s)
     if (ctx->fp64) k_coverage<double><<<grid_for(p->n, 256), 256, 0, s>>>((const double *)p->h, p->n, f, ctx->cov);
     else k_coverage<float><<<grid_for(p->n, 256), 256, 0, s>>>((const float *)p->h, p->n, f, ctx->cov);
     SPH_CHECK_LAUNCH();
-    return build_impl(ctx, s);
+    return build_impl(ctx, p->id, !ctx->lists_pred_skip && ctx->lists_pred_fail < PRED_FAIL_MAX, s);
 }
 
 namespace {
@@ -697,11 +736,9 @@ int export_once(sph_ctx *ctx, const sph_particles *p, int kind, int64_t *counts,
 int neighbors_export(sph_ctx *ctx, const sph_particles *p, int kind, int64_t *counts, const int64_t *offsets,
                      uint32_t *idx, cudaStream_t s)
 {
-    const bool bounded = !ctx->lists_exact;
-    const int r = export_once(ctx, p, kind, counts, offsets, idx, s);
-    // lists sized by leaf bounds overflowed nb_capacity: size them exactly
-    if (r != SPH_ERR_CAPACITY || !bounded) return r;
-    ctx->lists_exact = true;
-    ctx->err.clear();
-    return export_once(ctx, p, kind, counts, offsets, idx, s);
+    int r = export_once(ctx, p, kind, counts, offsets, idx, s);
+    // lists that outgrew their predicted or bounded sizes: size them more safely
+    while (r == SPH_ERR_CAPACITY && lists_escalate(ctx)) r = export_once(ctx, p, kind, counts, offsets, idx, s);
+    ctx->lists_pred_skip = false;
+    return r;
 }

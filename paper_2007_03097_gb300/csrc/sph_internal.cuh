@@ -171,6 +171,19 @@ struct sph_ctx {
     bool tree_valid = false;
     bool lists_valid = false;           // lists cover 2h of every particle
     bool lists_exact = false;           // size lists by exact counts (set once leaf bounds overflowed)
+    // Predicted sizing: each target's list is sized from its length in the
+    // previous build (lcount: the length in the low 16 bits, the low 16 bits
+    // of the particle's id in the high ones; written by every fill, permuted
+    // with the particles by every tree build), with no per-target culling in
+    // the sizing pass; a group whose id bits do not match is sized by leaf
+    // bounds.  A build whose lists outgrow the prediction is taken again
+    // with leaf bounds; after PRED_FAIL_MAX such builds the context stops
+    // predicting.
+    uint32_t *lcount = nullptr;
+    bool lcount_valid = false;          // a fill has written lcount for the current particles
+    bool lists_pred = false;            // the last build used predicted widths
+    bool lists_pred_skip = false;       // the call being retried sizes by leaf bounds
+    int lists_pred_fail = 0;
     double dom[4] = {0, 0, 0, 1};
     double dt_cfl = 0.0;
     // Units of the double-float arithmetic (SPH_FP64): lengths are multiplied
@@ -559,6 +572,27 @@ int scan_inclusive_max_i32(sph_ctx *ctx, const int32_t *in, int32_t *out, int64_
 size_t scan_tmp_bytes(int64_t n);
 // neighbors.cu
 int lists_build(sph_ctx *ctx, const sph_particles *p, cudaStream_t s);
+
+constexpr int PRED_FAIL_MAX = 4;
+
+// After a list-capacity error: choose the safer sizing for the call's retry
+// (leaf bounds after a prediction, exact counts after leaf bounds).  False
+// when the lists were already sized exactly, so the error stands.
+inline bool lists_escalate(sph_ctx *ctx)
+{
+    if (ctx->lists_pred) {
+        ++ctx->lists_pred_fail;
+        ctx->lists_pred_skip = true;
+    } else if (!ctx->lists_exact) {
+        ctx->lists_exact = true;
+    } else {
+        return false;
+    }
+    ctx->lists_pred = false;
+    ctx->lists_valid = false;
+    ctx->err.clear();
+    return true;
+}
 // device copy of n elements of the context's precision
 int copy_field(sph_ctx *ctx, void *dst, const void *src, int64_t n, cudaStream_t s);
 // order stream s (or the host, for s == nullptr with host = true) after the

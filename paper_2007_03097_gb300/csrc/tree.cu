@@ -1044,6 +1044,8 @@ FieldTable make_table(sph_ctx *ctx, const sph_particles *p, bool derived)
     }
     add_field<int32_t>(t, buf, nm, p->nnb);
     add_field<uint32_t>(t, buf, nm, p->id);
+    // the last list lengths, which size the next lists, follow their particles
+    if (ctx->lcount_valid) add_field<uint32_t>(t, buf, nm, ctx->lcount);
     return t;
 }
 

@@ -86,6 +86,76 @@ def test_bounded_lists_fall_back_to_exact_sizing(precision):
     assert B.sph_list_info(ctx2)["slots_reserved"] == B.sph_list_info(ctx2)["slots_used"]
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_predicted_widths_fall_back_to_leaf_bounds(precision):
+    """A list build sizes each target's list by 1.25 n + 16, n its length in
+    the previous build.  Lists built for h scaled by 0.7 (a third of the
+    neighbours) predict too little for the next build at the full h: that
+    build is taken again with leaf bounds and its forces equal those of a
+    context whose prediction held.  After four such builds the context
+    stops predicting."""
+    B = need_gpu()
+    w = inputs.sedov(16)
+    w.params["precision"] = precision
+    fp64 = precision == "fp64"
+    runs = []
+    for _ in range(2):
+        ctx = B.Context(w.params, w.n)
+        p = B.Particles.from_workload(w, fp64=fp64)
+        B.sph_build_tree(ctx, p)
+        B.sph_density(ctx, p)
+        assert not B.sph_list_info(ctx)["predicted"]      # no lengths before the first build
+        runs.append((ctx, p))
+    (ctx, p), (ctx2, q) = runs
+    fa = B.sph_forces(ctx, p)
+    info = B.sph_list_info(ctx)
+    assert info["predicted"] and info["pred_failures"] == 0
+    assert info["slots_reserved"] >= info["slots_used"] == fa["list_entries"]
+    h = q.h.clone()
+    for k in range(1, 6):
+        q.h.mul_(0.7)
+        B.sph_forces(ctx2, q)
+        assert B.sph_list_info(ctx2)["predicted"] == (k < 5)
+        q.h.copy_(h)
+        fb = B.sph_forces(ctx2, q)
+        info2 = B.sph_list_info(ctx2)
+        assert not info2["predicted"] and not info2["exact_sizing"]
+        assert info2["pred_failures"] == min(k, 4)
+        assert fb["list_entries"] == fa["list_entries"]
+        for f in ("ax", "ay", "az", "dudt", "divv", "vsig"):
+            assert torch.equal(getattr(p, f), getattr(q, f)), f
+    B.sph_step(ctx2, q, w.dt)
+    assert not B.sph_list_info(ctx2)["predicted"] and B.sph_list_info(ctx2)["pred_failures"] == 4
+
+
+def test_predicted_widths_after_the_caller_reorders():
+    """The previous lengths carry id bits of their particles: particle arrays that
+    the caller puts in another order between steps size the groups whose
+    particles moved by leaf bounds, with no failed build, and the steps
+    repeat bit for bit (every tree build sorts by key and id)."""
+    B = need_gpu()
+    w = inputs.sedov(16)
+    ctx = B.Context(w.params, w.n)
+    p = B.Particles.from_workload(w, fp64=True)
+    B.sph_build_tree(ctx, p)
+    B.sph_density(ctx, p)
+    B.sph_forces(ctx, p)
+    fields = ["x", "y", "z", "nnb", "id"] + list(B._FIELDS)
+    snap = {f: getattr(p, f).clone() for f in fields}
+    for _ in range(2):
+        B.sph_step(ctx, p, w.dt)
+    ref = {f: getattr(p, f).clone() for f in fields}
+    perm = torch.from_numpy(np.random.default_rng(3).permutation(w.n)).to(p.x.device)
+    for f, t in snap.items():
+        getattr(p, f).copy_(t[perm])
+    for _ in range(2):
+        B.sph_step(ctx, p, w.dt)
+    info = B.sph_list_info(ctx)
+    assert info["predicted"] and info["pred_failures"] == 0
+    for f in fields:
+        assert torch.equal(getattr(p, f), ref[f]), f
+
+
 def test_iteration_cap_and_h_bounds():
     B = need_gpu()
     w = inputs.sedov(10)
