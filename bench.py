@@ -68,11 +68,11 @@ DF_PER_FP32 = 1.0 / 18.0
 TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu, see profiles/), with the
     # particles of the captured workload; valid while the listed sources hash as recorded
-    "forces_fp64_sedov": {"bytes_per_launch": 84944896, "particles": 262144, "src": "7745970d2658",
+    "forces_fp64_sedov": {"bytes_per_launch": 84201984, "particles": 262144, "src": "a58b3fa41db4",
                           "files": ["forces.cu", "dfloat.cuh", "neighbors.cu", "sph_internal.cuh"]},
     # captured on the 128^3 box, scaled by the particles (per-particle lists and unions
     # are the same at 256^3)
-    "forces_mixed_turbulence": {"bytes_per_launch": 1190839040, "particles": 2097152, "src": "d0d7d4fe40b5",
+    "forces_mixed_turbulence": {"bytes_per_launch": 1190083072, "particles": 2097152, "src": "bf6059d14433",
                                 "files": ["forces.cu", "neighbors.cu", "sph_internal.cuh"]},
 }
 PROTOCOL_TRAIN_STEPS = 200
