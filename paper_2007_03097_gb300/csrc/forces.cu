@@ -62,7 +62,12 @@ struct ForceArgs {
 // Every warp holds the group's 32 targets (one per lane) and walks every FB-th
 // quad of its lanes' lists (quads q = w, w + FB, ...), reading its sources
 // from shared memory; the FB partial sums of each target are added in warp
-// order at the end.  Union entries past UC (a rare, very large union) are
+// order at the end.  A group of at most 16 targets gives each one a segment
+// of k = 32 / nextpow2(count) lanes: lane r of a segment walks the quads
+// w + FB r, w + FB (r + k), ... of its target, and the segment's partial sums
+// meet by shuffles before the warps' sums are added (a lane per target would
+// leave most lanes idle; groups of 1-8 targets hold about 12 % of the list
+// rows of a turbulence box).  Union entries past UC (a rare, very large union) are
 // read from global memory with the same arithmetic.
 constexpr int FB = 4;          // warps per block (one target group per block)
 constexpr int UC = 512;        // union sources staged per group when the largest union is not known
@@ -99,8 +104,11 @@ __global__ void __launch_bounds__(FB * 32, 8) k_forces_f32(ForceArgs a)
     const int g = blockIdx.x;
     if (g >= a.n_groups) return;
     const int gb = a.group_begin[g], ge = a.group_begin[g + 1];
-    const bool tgt = lane < ge - gb;
-    const int i = gb + (tgt ? lane : 0);
+    const int nt = ge - gb;
+    const int lk = nt > 16 ? 0 : 5 - (nt > 1 ? 32 - __clz(nt - 1) : 0);   // log2 of the segment length
+    const int tl = lane >> lk, r = lane & ((1 << lk) - 1);                // this lane's target, its rank
+    const bool tgt = tl < nt;
+    const int i = gb + (tgt ? tl : 0);
     const float4 qlo = a.group_lo[g], qhi = a.group_hi[g];
     const float gcx = 0.5f * (qlo.x + qhi.x), gcy = 0.5f * (qlo.y + qhi.y), gcz = 0.5f * (qlo.z + qhi.z);
     const float Lf = (float)a.L, invL = 1.f / Lf;
@@ -119,7 +127,7 @@ __global__ void __launch_bounds__(FB * 32, 8) k_forces_f32(ForceArgs a)
         cp_async16(&s_dyn[3 * t + 2], a.srcD + b);
     }
 
-    // ---- the target of this lane (every warp holds the same 32 targets)
+    // ---- the target of this lane (every warp holds the same targets)
     const float4 A = __ldg(a.srcA + i), Bz = __ldg(a.srcB + i), C = __ldg(a.srcC + i), D = __ldg(a.srcD + i);
     const float tx = (A.x - gcx) + A.y, ty = (A.z - gcy) + A.w, tz = (Bz.x - gcz) + Bz.y;
     const float ha = D.w, rhoa_h = D.x, pra = D.y, ca = D.z;   // rhoa_h = rho_a / 2
@@ -131,7 +139,7 @@ __global__ void __launch_bounds__(FB * 32, 8) k_forces_f32(ForceArgs a)
     int width = tgt ? a.gwidth[g] : 0;
     if (off + 32 * (int64_t)width > a.cap) width = 0;    // never read past the lists
     const int nq = width >> 2;
-    const unsigned long long *lq = reinterpret_cast<const unsigned long long *>(a.nbl + off) + lane;
+    const unsigned long long *lq = reinterpret_cast<const unsigned long long *>(a.nbl + off) + tl;
     cp_async_wait_all();
     for (int t = threadIdx.x; t < U; t += FB * 32) s_dyn[3 * t].w = s_dyn[3 * t + 2].w;   // h of the source
     __syncthreads();
@@ -140,10 +148,11 @@ __global__ void __launch_bounds__(FB * 32, 8) k_forces_f32(ForceArgs a)
     // sigma / h_a^(D+2) (div v), applied once at the end
     float accx = 0.f, accy = 0.f, accz = 0.f, du = 0.f, dv = 0.f, vs = ca;
     int nint = 0;
-    unsigned long long nxt = w < nq ? __ldg(lq + 32 * (int64_t)w) : ~0ull;
-    for (int q = w; q < nq; q += FB) {
+    const int q0 = w + FB * r, qs = FB << lk;          // this lane's quads: q0, q0 + qs, ...
+    unsigned long long nxt = q0 < nq ? __ldg(lq + 32 * (int64_t)q0) : ~0ull;
+    for (int q = q0; q < nq; q += qs) {
         const unsigned long long quad = nxt;
-        nxt = q + FB < nq ? __ldg(lq + 32 * (int64_t)(q + FB)) : ~0ull;
+        nxt = q + qs < nq ? __ldg(lq + 32 * (int64_t)(q + qs)) : ~0ull;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const uint32_t e = (uint32_t)(quad >> (16 * u)) & 0xFFFFu;
@@ -215,18 +224,35 @@ __global__ void __launch_bounds__(FB * 32, 8) k_forces_f32(ForceArgs a)
         }
     }
 
+    // ---- the partial sums of a segment meet in its first lane
+    for (int o = (1 << lk) >> 1; o > 0; o >>= 1) {
+        accx += __shfl_xor_sync(0xffffffffu, accx, o);
+        accy += __shfl_xor_sync(0xffffffffu, accy, o);
+        accz += __shfl_xor_sync(0xffffffffu, accz, o);
+        du += __shfl_xor_sync(0xffffffffu, du, o);
+        dv += __shfl_xor_sync(0xffffffffu, dv, o);
+        vs = fmaxf(vs, __shfl_xor_sync(0xffffffffu, vs, o));
+        nint += __shfl_xor_sync(0xffffffffu, nint, o);
+    }
     // ---- the FB partial sums of each target, added in warp order
     __syncthreads();                                   // the union is no longer read
-    float *red = reinterpret_cast<float *>(s_dyn);     // [FB][7][32]
-    red[(w * 7 + 0) * 32 + lane] = accx;
-    red[(w * 7 + 1) * 32 + lane] = accy;
-    red[(w * 7 + 2) * 32 + lane] = accz;
-    red[(w * 7 + 3) * 32 + lane] = du;
-    red[(w * 7 + 4) * 32 + lane] = dv;
-    red[(w * 7 + 5) * 32 + lane] = vs;
-    red[(w * 7 + 6) * 32 + lane] = __int_as_float(nint);
+    float *red = reinterpret_cast<float *>(s_dyn);     // [FB][7][32], column = target
+    if (r == 0) {
+        red[(w * 7 + 0) * 32 + tl] = accx;
+        red[(w * 7 + 1) * 32 + tl] = accy;
+        red[(w * 7 + 2) * 32 + tl] = accz;
+        red[(w * 7 + 3) * 32 + tl] = du;
+        red[(w * 7 + 4) * 32 + tl] = dv;
+        red[(w * 7 + 5) * 32 + tl] = vs;
+        red[(w * 7 + 6) * 32 + tl] = __int_as_float(nint);
+    }
     __syncthreads();
     if (w != 0) return;
+    // lane t of the first warp finishes target t
+    const bool to = lane < nt;
+    accx = red[lane]; accy = red[32 + lane]; accz = red[64 + lane];
+    du = red[96 + lane]; dv = red[128 + lane]; vs = red[160 + lane];
+    nint = to ? __float_as_int(red[192 + lane]) : 0;
     for (int v = 1; v < FB; ++v) {
         accx += red[(v * 7 + 0) * 32 + lane];
         accy += red[(v * 7 + 1) * 32 + lane];
@@ -234,18 +260,21 @@ __global__ void __launch_bounds__(FB * 32, 8) k_forces_f32(ForceArgs a)
         du += red[(v * 7 + 3) * 32 + lane];
         dv += red[(v * 7 + 4) * 32 + lane];
         vs = fmaxf(vs, red[(v * 7 + 5) * 32 + lane]);
-        nint += __float_as_int(red[(v * 7 + 6) * 32 + lane]);
+        if (to) nint += __float_as_int(red[(v * 7 + 6) * 32 + lane]);
     }
-    if (tgt) {
+    if (to) {
+        const int io = gb + lane;
+        const float4 Do = lk ? __ldg(a.srcD + io) : D;            // target io's {rho/2, P/rho^2, c, h}
+        const float hoinv = lk ? 1.f / Do.w : hainv;
         const float sig = kern_sigma<float>(KS);
-        const float h2 = hainv * hainv;
-        const float sig_hg = sig * (D1 ? h2 * hainv : h2 * h2 * hainv);    // sigma / h_a^(D+2)
-        ((float *)a.ax)[i] = sig * accx;
-        ((float *)a.ay)[i] = sig * accy;
-        ((float *)a.az)[i] = sig * accz;
-        ((float *)a.dudt)[i] = sig * du;
-        ((float *)a.divv)[i] = -sig_hg * dv / (2.f * rhoa_h);
-        ((float *)a.vsig)[i] = vs;
+        const float h2 = hoinv * hoinv;
+        const float sig_hg = sig * (D1 ? h2 * hoinv : h2 * h2 * hoinv);    // sigma / h_a^(D+2)
+        ((float *)a.ax)[io] = sig * accx;
+        ((float *)a.ay)[io] = sig * accy;
+        ((float *)a.az)[io] = sig * accz;
+        ((float *)a.dudt)[io] = sig * du;
+        ((float *)a.divv)[io] = -sig_hg * dv / (2.f * Do.x);
+        ((float *)a.vsig)[io] = vs;
     }
     for (int o = 16; o > 0; o >>= 1) nint += __shfl_xor_sync(0xffffffffu, nint, o);
     if (lane == 0) atomicAdd(&a.cnt->force_interactions, (unsigned long long)nint);
