@@ -23,6 +23,7 @@
 // Groups whose particles are all done drop out of the next sweep.
 #include <algorithm>
 #include <cfloat>
+#include <cmath>
 #include <type_traits>
 
 #include "dfloat.cuh"
@@ -32,6 +33,10 @@ namespace {
 
 constexpr int DW = 4;          // warps per block
 constexpr int SRC_CAP = 448;   // staged union sources per warp (mixed sweep; 7 KB)
+// Mixed sweep: the largest Newton step |dh| / h accepted as converged and
+// taken to first order, sqrt(h_tol / 10) (at most 1e-3): the error of the new
+// h, about 2 dh^2 / h, stays below h_tol / 5 (3.2e-4 for h_tol = 1e-6)
+inline double fo_step(double h_tol) { return std::min(std::sqrt(0.1 * h_tol), 1e-3); }
 
 struct DensArgs {
     const int32_t *act;            // active groups of this sweep ...
@@ -64,6 +69,7 @@ struct DensArgs {
     int kernel, periodic, fixed_h, max_sweeps;   // kernel: the kernel shape (kern_shape)
     int dim;                                     // D = 1 or 3
     double L, etaD, h_tol, h_min, h_max;         // etaD = eta^D; L in the packed positions' lengths
+    double fo_step;                              // fo_step(h_tol)
     df Ld, sig_d, etaD_d, hmin_d, hmax_d;        // the same constants as double-floats (h bounds scaled)
     // SPH_FP64 units (see sph_ctx::len_scale): h_scaled = h ls; the caller's
     // rho = rho_scaled rho_un, drho/dh = scaled om_un; Lu = L in the caller's units
@@ -285,27 +291,29 @@ __device__ __forceinline__ void density_group(const DensArgs &a, const int g, co
                 if (hn < (T)a.h_min) { hn = (T)a.h_min; ok = false; }
                 if (hn > (T)a.h_max) { hn = (T)a.h_max; ok = false; }
                 // Newton converges quadratically: after a Newton step of
-                // |dh| < 1e-4 h the error of the new h is about dh^2 / h
-                // (f''/f' ~ 1/h for f = m eta^D / h^D - rho), below 1e-8 h and
-                // far inside h_tol; the FP32 sweep accepts such a step
+                // |dh| < fo_step h the error of the new h is about 2 dh^2 / h
+                // (f''/2f' ~ -2/h for f = m eta^D / h^D - rho near the root,
+                // rho nearly constant in h), below h_tol / 5; the FP32 sweep
+                // accepts such a step
                 const double adh = fabs((double)(hn - h));
-                const bool conv = adh < a.h_tol * (double)h || (ok && adh < 1e-4 * (double)h);
+                const bool conv = adh < a.h_tol * (double)h || (ok && adh < a.fo_step * (double)h);
                 a.it_lo[i] = lo;
                 a.it_hi[i] = hi;
                 hp[i] = hn;
                 if (conv) {
                     // The reading evaluates rho once more at the final h.  When
                     // no list entry's r^2 lies between 4 h^2 and 4 (h + dh)^2
-                    // (|4 (h + dh)^2 - 4 h^2| <= 8.0004 h |dh| for |dh| <=
-                    // 1e-4 h; tested with 10 h |dh| plus 4e-6 h^2 for the FP32
-                    // rounding of r^2), the neighbour set at h + dh is this
-                    // one and rho(h + dh) = rho + rho' dh up to rho'' dh^2 / 2,
-                    // a relative O(10 (dh/h)^2), below 1e-7: within the FP32
-                    // rounding of this sweep.  That evaluation is taken here
-                    // without another sweep.
+                    // (|4 (h + dh)^2 - 4 h^2| <= 8.004 h |dh| for |dh| <=
+                    // fo_step h <= 1e-3 h; tested with 10 h |dh| plus 4e-6 h^2
+                    // for the FP32 rounding of r^2), the neighbour set at
+                    // h + dh is this one and rho(h + dh) = rho + rho' dh up to
+                    // rho'' dh^2 / 2, a relative O(10 (dh/h)^2) <= h_tol (1e-6
+                    // by default: inside the mixed mode's stated density
+                    // error).  That evaluation is taken here without another
+                    // sweep.
                     // (and the list must still cover 2 (h + dh))
                     const double need = (double)h * (10.0 * adh + 4e-6 * (double)h);
-                    if (adh < 1e-4 * (double)h && (double)gap > need && 2.0 * (double)hn <= (double)a.cov[i]) {
+                    if (adh < a.fo_step * (double)h && (double)gap > need && 2.0 * (double)hn <= (double)a.cov[i]) {
                         rho_out = rho + drho * (hn - h);
                         hfin = hn;
                         done = true;
@@ -758,6 +766,7 @@ int run_once(sph_ctx *ctx, sph_particles *p, const void *seed, sph_density_stats
     a.L = ctx->dom[3] * ls;
     a.etaD = q.dim == 1 ? q.eta : q.eta * q.eta * q.eta;
     a.h_tol = q.h_tol; a.h_min = q.h_min; a.h_max = q.h_max;
+    a.fo_step = fo_step(q.h_tol);
     const double sig = kern_sigma<double>(a.kernel);
     a.Ld = df_host(a.L); a.sig_d = df_host(sig); a.etaD_d = df_host(a.etaD);
     a.hmin_d = df_host(q.h_min * ls); a.hmax_d = df_host(q.h_max * ls);
