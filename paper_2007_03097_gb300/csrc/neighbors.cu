@@ -15,6 +15,7 @@
 // <= max(2 h_a, 2 h_b)), so the h iteration and the force pass share it and
 // it is rebuilt only when some h outgrows its coverage.
 #include <algorithm>
+#include <climits>
 
 #include "sph_internal.cuh"
 
@@ -247,25 +248,31 @@ __global__ void __launch_bounds__(LW * 32, 7) k_lists(ListArgs a)
             if (lane >= o) incl += v;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
-        s_lb[w][lane] = lb;
-        s_incl[w][lane] = incl;
+        // the kept leaves' ranges in the first K slots: every leaf holds a
+        // particle, so their ends increase strictly
+        const unsigned kmask = __ballot_sync(0xffffffffu, cnt > 0);
+        if (cnt > 0) {
+            const int c = __popc(kmask & ((1u << lane) - 1u));
+            s_lb[w][c] = lb;
+            s_incl[w][c] = incl;
+        }
         __syncwarp();
+        const int end = lane < __popc(kmask) ? s_incl[w][lane] : INT_MAX;   // end of range `lane`
         for (int base = 0; base < total; base += 32) {
             const int item = base + lane;
             const int take2 = min(32, total - base);
+            // the wave starts in range r0 (the ranges that end by its start);
+            // a range ending at base + p, 0 < p < 32, hands item p to the next
+            const int r0 = __popc(__ballot_sync(0xffffffffu, end <= base));
+            const unsigned ends = __reduce_or_sync(0xffffffffu, end > base && end - base < 32 ? 1u << (end - base) : 0u);
             bool within = false;
             float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
             float mj = 0.f;
             int j = 0;
             if (lane < take2) {
-                // owner: first lane whose inclusive end exceeds item
-                int lo2 = 0, hi2 = 31;
-                while (lo2 < hi2) {
-                    const int mid = (lo2 + hi2) >> 1;
-                    if (s_incl[w][mid] > item) hi2 = mid; else lo2 = mid + 1;
-                }
-                const int start = lo2 > 0 ? s_incl[w][lo2 - 1] : 0;       // exclusive start of the owner
-                j = s_lb[w][lo2] + (item - start);
+                const int own = r0 + __popc(ends & ((2u << lane) - 2u));  // the range holding item
+                const int start = own > 0 ? s_incl[w][own - 1] : 0;       // exclusive start of the owner
+                j = s_lb[w][own] + (item - start);
                 const float4 qa = a.srcA[j], qb = a.srcB[j];
                 float rx = qa.x - gcx, ry = qa.z - gcy, rz = qb.x - gcz;
                 if (wrap && fmaxf(fmaxf(fabsf(rx), fabsf(ry)), fabsf(rz)) > 0.5f * a.L) {
