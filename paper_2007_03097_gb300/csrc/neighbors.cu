@@ -409,11 +409,22 @@ __global__ void __launch_bounds__(LW * 32, 7) k_lists(ListArgs a)
         bool acc = false;
         const bool leaf = node < 0;
         float4 bc = make_float4(0.f, 0.f, 0.f, 0.f), be = bc;
+        // the node's children, or the leaf's particle count in the sizing
+        // pass, load beside its box (one memory latency per walk step)
+        int2 ch = make_int2(0, 0);
+        int lsz = 0;
         if (lane < take) {
             float4 lo, hi;
             const int id = node & 0x7fffffff;
-            if (leaf) { lo = a.leaf_lo[id]; hi = a.leaf_hi[id]; }
-            else { lo = a.node_lo[id]; hi = a.node_hi[id]; }
+            if (leaf) {
+                lo = a.leaf_lo[id];
+                hi = a.leaf_hi[id];
+                if (MODE == LM_BOUND) lsz = a.leaf_begin[id + 1] - a.leaf_begin[id];
+            } else {
+                lo = a.node_lo[id];
+                hi = a.node_hi[id];
+                ch = reinterpret_cast<const int2 *>(a.child)[node];
+            }
             const float r = fmaxf(qcov, lo.w);
             bc = make_float4(0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z),
                              lo.w * lo.w * (1.f + MARGIN));
@@ -427,8 +438,8 @@ __global__ void __launch_bounds__(LW * 32, 7) k_lists(ListArgs a)
         if (acc && !leaf) {
             const int pos = sp + 2 * __popc(mint & ((1u << lane) - 1u));
             if (pos + 1 < STACK) {
-                stack[pos] = a.child[2 * node];
-                stack[pos + 1] = a.child[2 * node + 1];
+                stack[pos] = ch.x;
+                stack[pos + 1] = ch.y;
             }
         }
         sp += 2 * __popc(mint);
@@ -441,18 +452,14 @@ __global__ void __launch_bounds__(LW * 32, 7) k_lists(ListArgs a)
         const unsigned lmask = __ballot_sync(0xffffffffu, acc && leaf);
         const bool cull = !predict;
         if (predict && acc && leaf) {
-            const int id = node & 0x7fffffff;
             need = 1u;
-            ub_lane += a.leaf_begin[id + 1] - a.leaf_begin[id];
+            ub_lane += lsz;
         }
         int lcnt = 0;                        // particles of this lane's accepted leaf (sizing pass)
         if (cull && lmask) {                 // the accepted leaves' boxes, read by every lane
             s_bc[w][lane] = bc;
             s_be[w][lane] = make_float4(be.x + a.slack, be.y + a.slack, be.z + a.slack, 0.f);
-            if (MODE == LM_BOUND && acc && leaf) {
-                const int id = node & 0x7fffffff;
-                lcnt = a.leaf_begin[id + 1] - a.leaf_begin[id];
-            }
+            if (MODE == LM_BOUND && acc && leaf) lcnt = lsz;
             __syncwarp();
         }
         for (unsigned m = cull ? lmask : 0u; m; m &= m - 1) {
