@@ -626,13 +626,23 @@ __global__ void __launch_bounds__(DW * 32) k_density(DensArgs a)
     if (blockIdx.x == 0 && threadIdx.x == 0 && n_act > 0) atomicAdd(&a.cnt->sweeps_done, 1);
     if (FP64POS && n_act < SPARSE_MAX_GROUPS) return;   // k_density_sparse takes this sweep
     SweepTally tally;
-    for (;;) {
+    auto claim = [&]() {
         int gi = 0;
         if (lane == 0) gi = atomicAdd(a.work, 1);
         gi = __shfl_sync(0xffffffffu, gi, 0);
-        if (gi >= n_act) break;
-        if constexpr (FP64POS) density_group_df(a, a.act[gi], lane, tally);
-        else density_group<T, KS>(a, a.act[gi], lane, s_src, tally);
+        return gi < n_act ? a.act[gi] : -1;
+    };
+    if constexpr (FP64POS) {
+        for (int g = claim(); g >= 0; g = claim()) density_group_df(a, g, lane, tally);
+    } else {
+        // the next group is claimed (and its index read) before this one is
+        // evaluated, so the claim's round trip overlaps the evaluation
+        int g = claim();
+        while (g >= 0) {
+            const int next = claim();
+            density_group<T, KS>(a, g, lane, s_src, tally);
+            g = next;
+        }
     }
     if (lane == 0 && tally.evals) {
         atomicAdd(&a.cnt->interactions, tally.inter);
