@@ -57,7 +57,8 @@ struct ListArgs {
     uint32_t *uni;
     float4 *urec;                  // the union members' staged records (null: not written)
     int64_t ucap;
-    int32_t *kept;                 // leaves kept by the sizing pass, kcap per group (0: not cached)
+    int2 *kept;                    // leaves kept by the sizing pass as {first particle, count},
+                                   // kcap per group (0: not cached)
     int32_t *kept_count;
     int kcap;
     DevCounters *cnt;
@@ -232,15 +233,10 @@ __global__ void __launch_bounds__(LW * 32, 7) k_lists(ListArgs a)
 
     int ns = 0;
     bool img = false;                              // this lane staged a source across a periodic face
-    auto stage = [&](bool keep, int id) {
+    auto stage_range = [&](int lb, int cnt) {
         // particles of all kept leaves, loaded in warp-wide waves: lane L
-        // owns a leaf range [lb, lb + cnt) placed at [incl - cnt, incl) of
-        // the step's item sequence
-        int lb = 0, cnt = 0;
-        if (keep) {
-            lb = a.leaf_begin[id];
-            cnt = a.leaf_begin[id + 1] - lb;
-        }
+        // owns a leaf range [lb, lb + cnt) (cnt = 0: none) placed at
+        // [incl - cnt, incl) of the step's item sequence
         int incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -317,6 +313,15 @@ __global__ void __launch_bounds__(LW * 32, 7) k_lists(ListArgs a)
         }
     };
 
+    auto stage = [&](bool keep, int id) {
+        int lb = 0, cnt = 0;
+        if (keep) {
+            lb = a.leaf_begin[id];
+            cnt = a.leaf_begin[id + 1] - lb;
+        }
+        stage_range(lb, cnt);
+    };
+
     // the fill pass replays the leaves the sizing pass kept (same order), or
     // walks the tree when they were not cached
     const bool replay = FILL && a.kcap > 0 && a.kept_count[g] <= a.kcap;
@@ -324,7 +329,8 @@ __global__ void __launch_bounds__(LW * 32, 7) k_lists(ListArgs a)
         const int nk = a.kept_count[g];
         for (int c = 0; c < nk; c += 32) {
             const bool k2 = c + lane < nk;
-            stage(k2, k2 ? a.kept[(int64_t)g * a.kcap + c + lane] : 0);
+            const int2 r = k2 ? a.kept[(int64_t)g * a.kcap + c + lane] : make_int2(0, 0);
+            stage_range(r.x, r.y);
         }
     }
     // The walk starts at the nodes of the (at most eight) cells of the
@@ -412,14 +418,17 @@ __global__ void __launch_bounds__(LW * 32, 7) k_lists(ListArgs a)
         // the node's children, or the leaf's particle count in the sizing
         // pass, load beside its box (one memory latency per walk step)
         int2 ch = make_int2(0, 0);
-        int lsz = 0;
+        int lb0 = 0, lsz = 0;
         if (lane < take) {
             float4 lo, hi;
             const int id = node & 0x7fffffff;
             if (leaf) {
                 lo = a.leaf_lo[id];
                 hi = a.leaf_hi[id];
-                if (MODE == LM_BOUND) lsz = a.leaf_begin[id + 1] - a.leaf_begin[id];
+                if (MODE == LM_BOUND) {
+                    lb0 = a.leaf_begin[id];
+                    lsz = a.leaf_begin[id + 1] - lb0;
+                }
             } else {
                 lo = a.node_lo[id];
                 hi = a.node_hi[id];
@@ -485,7 +494,7 @@ __global__ void __launch_bounds__(LW * 32, 7) k_lists(ListArgs a)
             const unsigned km = __ballot_sync(0xffffffffu, keep);
             if (keep && a.kcap > 0) {
                 const int pos = nkept + __popc(km & ((1u << lane) - 1u));
-                if (pos < a.kcap) a.kept[(int64_t)g * a.kcap + pos] = node & 0x7fffffff;
+                if (pos < a.kcap) a.kept[(int64_t)g * a.kcap + pos] = make_int2(lb0, lsz);
             }
             nkept += __popc(km);
             continue;

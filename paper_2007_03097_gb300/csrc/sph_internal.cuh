@@ -243,7 +243,7 @@ struct sph_ctx {
     int32_t *group_union = nullptr;     // union size per group
     int32_t *group_img = nullptr;       // 1: a list candidate of the group lies across a periodic face
     int32_t *group_mark = nullptr;      // sweep stamp of a group's last append to the active list
-    int32_t *kept = nullptr;            // leaves kept by the list sizing pass, per group
+    int2 *kept = nullptr;               // leaves kept by the list sizing pass, per group: {first particle, count}
     int32_t *kept_count = nullptr;
     int64_t kept_cap = 0;
     // ---- density iteration state
