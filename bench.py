@@ -68,11 +68,11 @@ DF_PER_FP32 = 1.0 / 18.0
 TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu, see profiles/), with the
     # particles of the captured workload; valid while the listed sources hash as recorded
-    "forces_fp64_sedov": {"bytes_per_launch": 84190464, "particles": 262144, "src": "afc5bd4f5eed",
+    "forces_fp64_sedov": {"bytes_per_launch": 84436224, "particles": 262144, "src": "e61daca242b6",
                           "files": ["forces.cu", "dfloat.cuh", "neighbors.cu", "sph_internal.cuh"]},
     # captured on the 128^3 box, scaled by the particles (per-particle lists and unions
     # are the same at 256^3)
-    "forces_mixed_turbulence": {"bytes_per_launch": 1230075136, "particles": 2097152, "src": "7a7a9d6a19b5",
+    "forces_mixed_turbulence": {"bytes_per_launch": 1229722112, "particles": 2097152, "src": "858cf9be8c94",
                                 "files": ["forces.cu", "neighbors.cu", "sph_internal.cuh"]},
 }
 PROTOCOL_TRAIN_STEPS = 200
